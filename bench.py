@@ -1,0 +1,424 @@
+"""Benchmark of the FFT-Galerkin staggered step on one GB300 (or N replicas).
+
+Workload: seeded random fractal carpet 729 x 729 (3^6, each level keeps 6-9
+of 9 sub-cells solid, porosity 0.30 +- 0.02, seed 2305), solid E = 20 GPa,
+nu = 0.2, pores 1e-3 x solid, transient diffusion from a source held at
+c = 1 on the left face (pore D = 1, solid D = 1e-3, dt = (n/4)^2 / 200),
+precipitate eigenstrain, equilibrium PCG to a 1e-8 relative residual,
+history and AT2 phase field, l0 = 2 voxels, Gc = 10 J/m^2. A "step" is one
+staggered load step (diffusion -> precipitation -> eigenstrain ->
+equilibrium -> history -> phase field) through fftmech_staggered_step.
+
+value: FFT-Galerkin CG voxel-iterations per second = voxels x (PCG
+iterations of the diffusion, equilibrium and phase-field solves) / device
+time of the timed steps, summed over ranks (each rank solves its own RVE:
+independent problems, weak scaling, no collective on the data path).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 729
+SEED = 2305
+TOTAL_STEPS = 200
+L2_FLUSH_BYTES = 512 << 20
+METRIC = "FFT-Galerkin CG voxel-iterations/s"
+UNIT = "voxel-iterations/s"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- workload
+
+def workload(rank):
+    from microstructures.workloads import carpet_transient
+    return carpet_transient(n=N_SIDE, seed=SEED + rank, steps=TOTAL_STEPS, tol=1e-8)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+
+def kernel_bytes(kind, cls, s, variant="full"):
+    """Algorithmic bytes per voxel of one launch: what the kernel must read
+    and write once (float or double fields of s bytes, double iterates,
+    uint8 phase / mask). kind: 'elastic' (2 components, degradation field),
+    'diffusion' (1 component, Dirichlet mask), 'phasefield' (1 component,
+    history field as reaction coefficient)."""
+    D = 2 if kind == "elastic" else 1
+    extra = {"elastic": s + 1, "diffusion": 2, "phasefield": s + 1}[kind]  # g / mask / H, + phase
+    if cls == "direction":   # read S, p_old, material; write p_new
+        return 2 * s + D * s + extra + D * s
+    if cls == "update":
+        if variant == "u_only":  # read p, u; write u
+            return D * s + 16 * D
+        # read p, u, r, material; write u, r, S
+        return D * s + 8 * D + D * s + extra + 8 * D + D * s + 2 * s
+    if cls == "column":      # read + write the packed spectrum
+        return 4 * s
+    raise ValueError(cls)
+
+
+def class_bytes(infos_per_step, N, s, replace_every):
+    """Total algorithmic bytes per kernel class over the timed steps."""
+    tot = {"direction": 0.0, "update": 0.0, "column": 0.0}
+    kinds = ["diffusion", "elastic", "phasefield"]
+    for infos in infos_per_step:
+        for kind, info in zip(kinds, infos):
+            it = info["iters"]
+            rep = (it // replace_every) if replace_every else 0
+            tot["direction"] += N * it * kernel_bytes(kind, "direction", s)
+            tot["update"] += N * ((it - rep) * kernel_bytes(kind, "update", s)
+                                  + rep * kernel_bytes(kind, "update", s, "u_only"))
+            tot["column"] += N * (it + 2) * kernel_bytes(kind, "column", s)
+    return tot
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def make_state(torch, fm, w, prec, device, pinned_host=False):
+    N = w.voxels
+    ft = torch.float64 if prec == fm.FFTMECH_FP64 else torch.float32
+    spec = [("c", 1, torch.float64), ("c_ppt", 1, ft), ("eig", 1, ft), ("u", 2, torch.float64),
+            ("strain", 3, ft), ("stress", 3, ft), ("H", 1, ft), ("damage", 1, torch.float64)]
+    bufs = {}
+    for k, n, dt in spec:
+        t = torch.zeros(n * N, dtype=dt)
+        bufs[k] = t.pin_memory() if pinned_host else t.to(device)
+    ph = torch.as_tensor(np.ascontiguousarray(w.phase.ravel()))
+    mask = torch.as_tensor(np.ascontiguousarray(w.dirichlet_mask.ravel()))
+    if pinned_host:
+        bufs["phase"] = ph.pin_memory()
+        bufs["mask"] = mask.pin_memory()
+    else:
+        bufs["phase"] = ph.to(device)
+        bufs["mask"] = mask.to(device)
+    st = fm.fftmech_state()
+    for k in ("phase", "c", "c_ppt", "eig", "u", "strain", "stress", "H", "damage"):
+        setattr(st, k, bufs[k].data_ptr())
+    p = fm.fftmech_step_params()
+    p.diffusion_mode = fm.FFTMECH_DIFF_TRANSIENT
+    p.dt = w.dt
+    p.dirichlet_mask = bufs["mask"].data_ptr()
+    p.dirichlet_value = w.dirichlet_value
+    p.eig_mode = fm.FFTMECH_EIG_FROM_PRECIPITATE
+    p.eig_scale = 1.0
+    return bufs, st, p
+
+
+def run_arm(torch, fm, w, prec, steps, warmup, device, profile=True, flush=None):
+    """W warm-up steps, then `steps` timed staggered steps (L2 flushed before
+    each). Returns per-step infos, device ms per step and profile data."""
+    stream = torch.cuda.current_stream(device)
+    ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=w.tol,
+                     max_iter=20000, replace_every=50, check_every=16, stream=stream.cuda_stream)
+    bufs, st, p = make_state(torch, fm, w, prec, device)
+    for _ in range(warmup):
+        fm.fftmech_staggered_step(ctx.handle, st, p)
+    torch.cuda.synchronize(device)
+    fm.fftmech_profile_enable(ctx.handle, 1 if profile else 0)
+    infos, ms = [], []
+    for _ in range(steps):
+        if flush is not None:
+            flush.add_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf = fm.fftmech_staggered_step(ctx.handle, st, p)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        infos.append([i.as_dict() for i in inf])
+    torch.cuda.synchronize(device)
+    prof = {}
+    for k, name in enumerate(fm.KERNEL_CLASS_NAMES):
+        prof[name] = fm.fftmech_profile_read(ctx.handle, k)
+    total_launches, _ = fm.fftmech_profile_read(ctx.handle, fm.FFTMECH_K_COUNT)
+    fm.fftmech_profile_enable(ctx.handle, 0)
+    state = {k: bufs[k].double().cpu().numpy() for k in ("c", "strain", "stress", "damage")}
+    ctx.close()
+    return {"infos": infos, "ms": ms, "prof": prof, "launches": total_launches, "state": state}
+
+
+def run_e2e(torch, fm, w, prec, steps, warmup, device):
+    """The same steps through the C ABI with pinned HOST buffers: every call
+    copies the state in and out (host <-> device inside the timed region)."""
+    ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=w.tol,
+                     max_iter=20000, replace_every=50, check_every=16)
+    bufs, st, p = make_state(torch, fm, w, prec, device, pinned_host=True)
+    for _ in range(warmup):
+        fm.fftmech_staggered_step(ctx.handle, st, p)
+    torch.cuda.synchronize(device)
+    iters = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        inf = fm.fftmech_staggered_step(ctx.handle, st, p)
+        iters += sum(i.iters for i in inf)
+    torch.cuda.synchronize(device)
+    dt = time.perf_counter() - t0
+    ctx.close()
+    N = w.voxels
+    s = 8 if prec == fm.FFTMECH_FP64 else 4
+    h2d = N * (1 + 1 + 8 + s + s + 16 + 3 * s + 3 * s + s + 8)  # phase, mask, c, c_ppt, eig, u, strain, stress, H, d
+    d2h = N * (8 + s + s + 16 + 3 * s + 3 * s + s + 8)
+    return {"value": N * iters / dt, "seconds": dt, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(w, cg_iters):
+    """The FP64 CPU oracle as it stands: `cg_iters` iterations of its
+    gradient-space equilibrium CG (Algorithm 1) on the benchmark geometry
+    with a 1e-3 pore eigenstrain. Returns voxel-iterations/s and seconds."""
+    from oracle import elasticity
+    eig = np.where(w.phase == 0, 1e-3, 0.0)
+    t0 = time.perf_counter()
+    out = elasticity.equilibrium_solve(w.phase, eig, np.ones(w.phase.shape), [0, 0, 0], w.materials,
+                                       w.h, tol=1e-14, max_newton=1, max_iter=cg_iters)
+    dt = time.perf_counter() - t0
+    return w.voxels * out["iters"] / dt, dt, out["iters"]
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed on the host cores: each step is a bounded sample of
+    the workload (a few oracle CG iterations on the 729^2 geometry)."""
+    if rank != 0:
+        return
+    w = workload(0)
+    per = []
+    for s in range(args.warmup + args.steps):
+        v, dt, it = oracle_sample(w, 4)
+        if s >= args.warmup:
+            per.append((v, dt, it))
+    secs = sum(p[1] for p in per)
+    iters = sum(p[2] for p in per)
+    value = w.voxels * iters / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(per),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"random-carpet-{N_SIDE}x{N_SIDE}-transient-staggered",
+                                        "seed": SEED, "voxels": w.voxels, "sample": "4 oracle CG iterations per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "4 iterations of the oracle's gradient-space equilibrium CG on the 729^2 carpet per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=40)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs CUDA devices")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2305_13081_gb300 import fftmech as fm
+
+    w = workload(rank)
+    N = w.voxels
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(device)
+
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    t_wall = time.perf_counter()
+    mixed = run_arm(torch, fm, w, fm.FFTMECH_MIXED, args.steps, args.warmup, device, flush=flush)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+
+    iters = sum(sum(i["iters"] for i in inf) for inf in mixed["infos"])
+    dev_s = sum(mixed["ms"]) / 1e3
+    local_vals = torch.tensor([N * iters, dev_s], dtype=torch.float64, device=device)
+    if dist is not None:
+        tot = local_vals.clone()
+        dist.all_reduce(tot[:1], op=dist.ReduceOp.SUM)
+        mx = local_vals[1:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        total_vi, max_s = float(tot[0]), float(mx[0])
+    else:
+        total_vi, max_s = float(local_vals[0]), float(local_vals[1])
+    value = total_vi / max_s
+
+    # per-solve breakdown
+    kinds = ["diffusion", "equilibrium", "phasefield"]
+    breakdown = {}
+    for j, k in enumerate(kinds):
+        it = sum(inf[j]["iters"] for inf in mixed["infos"])
+        ms = sum(inf[j]["device_ms"] for inf in mixed["infos"])
+        breakdown[k] = {"iters": it, "device_ms": ms,
+                        "voxel_iterations_per_s": N * it / (ms / 1e3) if ms > 0 else None}
+
+    # roofline of the dominant kernel class (CUDA events inside the timed region)
+    from json import load as _jl
+    peaks = {}
+    try:
+        peaks = _jl(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        hbm_peak, peak_src = 6800.0, "fallback"
+    cb = class_bytes(mixed["infos"], N, 4, 50)
+    kernels = {}
+    for name in ("direction", "update", "column"):
+        n, ms = mixed["prof"][name]
+        if n and ms > 0:
+            kernels[name] = {"launches": n, "total_ms": ms, "avg_us": 1e3 * ms / n,
+                             "algorithmic_bytes_per_launch": cb[name] / n,
+                             "achieved_gbs": cb[name] / (ms / 1e3) / 1e9}
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"]) if kernels else None
+    roofline = None
+    if dom:
+        a = kernels[dom]["achieved_gbs"]
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": a / hbm_peak, "peak_source": peak_src, "traffic": None,
+                    "note": "729^2 working set is L2-resident; achieved counts algorithmic bytes"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields / f64 iterates+reductions",
+        "data": "synthetic",
+        "config": {"workload": f"random-carpet-{N_SIDE}x{N_SIDE}-transient-staggered", "voxels": N,
+                   "seed": SEED, "precision": "mixed", "tol": w.tol, "porosity": w.extra["porosity"],
+                   "steps_per_run": TOTAL_STEPS, "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before each timed step",
+                   "parallelism": f"{world} independent RVE replicas"},
+        "breakdown": breakdown,
+        "kernels": kernels,
+        "roofline": roofline,
+        "gpu_launches": mixed["launches"],
+        "clocks": clocks,
+        "wall_s_timed": t_wall,
+    }
+
+    if rank == 0 and not args.no_fp64:
+        fp64 = run_arm(torch, fm, w, fm.FFTMECH_FP64, args.steps, args.warmup, device, profile=False,
+                       flush=flush)
+        it64 = sum(sum(i["iters"] for i in inf) for inf in fp64["infos"])
+        v64 = N * it64 / (sum(fp64["ms"]) / 1e3)
+        errs = {}
+        for k in ("strain", "stress", "c"):
+            a, b = mixed["state"][k], fp64["state"][k]
+            errs[k] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        errs["damage_maxabs"] = float(np.abs(mixed["state"]["damage"] - fp64["state"]["damage"]).max())
+        out["fp64"] = {"value": v64, "ms_per_step": float(np.mean(fp64["ms"])),
+                       "speedup_mixed_over_fp64": value / world / v64 if world == 1 else (value / world) / v64,
+                       "mixed_vs_fp64_rel_err": errs}
+    if rank == 0 and not args.no_e2e:
+        e2e = run_e2e(torch, fm, w, fm.FFTMECH_MIXED, max(3, args.steps // 4), 1, device)
+        out["e2e"] = {"value": e2e["value"] * world, "unit": UNIT,
+                      "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                      "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]}
+    if rank == 0 and not args.no_cpu:
+        v, secs, it = oracle_sample(w, args.cpu_iters)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{it} iterations of the FP64 oracle's gradient-space equilibrium CG "
+                                         f"on the {N_SIDE}^2 carpet ({secs:.1f} s, numpy, 1 thread)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

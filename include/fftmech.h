@@ -1,0 +1,280 @@
+/*
+ * fftmech: FFT-Galerkin corrosion-fracture hot path on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the library libfftmech.so. It computes, on voxel grids of a
+ * two-phase porous microstructure, the steps of one staggered load step of
+ * Pundir, Kammer & Angst, "An FFT-based framework for predicting
+ * corrosion-driven damage in fractal porous media" (arXiv 2305.13081):
+ * ionic diffusion (Sec. 2.1), precipitation and eigenstrain (Sec. 2.2),
+ * mechanical equilibrium (Sec. 2.3) and the phase-field damage (Sec. 2.4), in
+ * the order of Algorithm 1 (Sec. 2.5).
+ *
+ * Discretisation (Sec. 2.1, 2.6, App. A). Fields live on the voxels of a
+ * periodic grid with spacing h. Gradients use the forward-difference symbol
+ * D_a(k) = (exp(i 2 pi k_a / n_a) - 1) / h of Sec. 2.6; the compatibility
+ * projections G and GG of App. A (Eq. g-42) are applied as
+ * "backward-difference divergence -> Fourier multiplier 1/|D|^2 ->
+ * forward-difference gradient", which is the same operator, so each
+ * Galerkin system is solved as a preconditioned CG on the potential
+ * (displacement u, concentration fluctuation phi, damage d) whose iterates map
+ * one to one onto the paper's gradient-space CG iterates.
+ *
+ * Conventions shared by every entry point
+ * - Layout: structure of arrays, C order, x fastest: a scalar field is
+ *   n[1]*n[0] (2D) or n[2]*n[1]*n[0] (3D) elements; a d-component field is d
+ *   such blocks back to back. Tensor fields use Voigt order xx, yy, xy (2D)
+ *   or xx, yy, zz, yz, xz, xy (3D) with TENSOR shear components (not
+ *   engineering strains).
+ * - Phase indicator omega (uint8 per voxel): 1 = solid, 0 = pore (Sec. 2.1).
+ * - Element types: "iterate" fields (u, c, damage) are always double.
+ *   "Field" arrays (eigenstrain, strain, stress, history H, c_ppt) are
+ *   double for FFTMECH_FP64 and float for FFTMECH_MIXED.
+ * - Pointers may be device pointers (cudaMalloc, torch CUDA tensors) or host
+ *   pointers (pageable or pinned); host buffers are staged through
+ *   library-owned device memory on the context's stream.
+ * - Ownership: the caller owns every field buffer; the library owns only its
+ *   workspace (allocated in fftmech_create, freed in fftmech_destroy).
+ * - Synchronisation: every compute entry point enqueues its work on the
+ *   context's CUDA stream and returns after that work has completed, with
+ *   `info` filled in on the host.
+ * - Errors: argument errors return before any work is enqueued. Solver
+ *   outcomes (converged, not converged, non-finite) are returned as the
+ *   status and also stored in info->status. A CUDA failure returns
+ *   FFTMECH_ERR_CUDA; fftmech_last_error() gives the message.
+ * - No CPU fallback: without a CUDA device fftmech_create fails.
+ */
+#ifndef FFTMECH_H
+#define FFTMECH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FFTMECH_OK = 0,
+  FFTMECH_ERR_INVALID_ARG = 1,
+  FFTMECH_ERR_UNSUPPORTED_SIZE = 2, /* grid size not 2^a 3^b in [2, 4096], or dim unsupported */
+  FFTMECH_ERR_NOT_CONVERGED = 3,    /* PCG hit max_iter before tol */
+  FFTMECH_ERR_NONFINITE = 4,        /* NaN/Inf residual or breakdown */
+  FFTMECH_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+  FFTMECH_ERR_CUDA = 6,
+  FFTMECH_ERR_OOM = 7
+} fftmech_status;
+
+typedef enum {
+  FFTMECH_FP64 = 0,  /* every field, FFT and stencil in double */
+  FFTMECH_MIXED = 1  /* float fields, FFTs and stencils; double iterates, dot products,
+                        averages and periodic true-residual replacement */
+} fftmech_precision;
+
+/* Grid. dim = 2 or 3; n[0] = nx, n[1] = ny, n[2] = nz (n[2] = 1 in 2D).
+ * h: voxel size for mechanics and the phase field; h_diff: voxel size for
+ * diffusion (the paper's diffusion runs in its own units). */
+typedef struct {
+  int dim;
+  int n[3];
+  double h;
+  double h_diff;
+} fftmech_grid;
+
+/* Phase properties (Sec. 3) and model constants.
+ * E, nu: Young's modulus and Poisson ratio of each phase (plane strain in 2D).
+ * D_solid, D_pore: diffusivities (Sec. 2.1). Gc, l0: fracture energy and
+ * regularisation length (Eq. crack). kappa: residual stiffness in
+ * g(d) = (1 - d)^2 + kappa (Sec. 2.4). S_sol, M_ppt: solubility limit and
+ * molar volume of the precipitate (Sec. 2.2, Eq. eigen-simplify). */
+typedef struct {
+  double E_solid, nu_solid, E_pore, nu_pore;
+  double D_solid, D_pore;
+  double Gc, l0, kappa;
+  double S_sol, M_ppt;
+} fftmech_materials;
+
+/* PCG controls. Stop when the gradient-space residual norm (the paper's CG
+ * residual, equal to sqrt(r.M^-1 r) of the potential PCG) has dropped by
+ * `tol` relative to that of the right-hand side. replace_every: MIXED only,
+ * replace the recursive residual by the FP64 true residual every that many
+ * iterations (0 = never). check_every: iterations between host polls of the
+ * device convergence flag. */
+typedef struct {
+  double tol;
+  int max_iter;
+  int replace_every;
+  int check_every;
+} fftmech_solver_opts;
+
+/* Per-solve report (host struct). All averages in FP64 over every voxel. */
+typedef struct {
+  int status;               /* fftmech_status of the solve */
+  int iters;                /* PCG iterations (operator applications) */
+  double rel_res;           /* final recursive relative residual */
+  double true_rel_res;      /* final FP64 true relative residual (MIXED with replacement), else = rel_res */
+  double mean_stress[6];    /* <sigma>, Voigt */
+  double mean_strain[6];    /* <eps>, Voigt (equals eps_mac up to rounding) */
+  double mean_flux[3];      /* <j> of the diffusion step (HOMOGENISE) */
+  double mean_c;            /* <c> after the diffusion step */
+  double porosity;          /* eta = |Omega_p| / |Omega| */
+  double elastic_energy;    /* sum 1/2 (eps - e I) : sigma h^dim */
+  double total_damage;      /* sum of d over the voxels */
+  double frac_damaged;      /* fraction of solid voxels with d > 0.9 */
+  double device_ms;         /* device time of the solve (CUDA events on the context stream) */
+} fftmech_solve_info;
+
+typedef struct fftmech_ctx fftmech_ctx;
+
+/* Create a context for one grid. `stream` is a cudaStream_t (NULL = a new
+ * stream owned by the context). Allocates the workspace (about 60 bytes per
+ * voxel for MIXED 2D) on the current CUDA device.
+ * Returns INVALID_ARG for bad pointers or materials, UNSUPPORTED_SIZE for a
+ * grid dimension that is not 2^a 3^b (at most 2187 for powers of three,
+ * 2048 for powers of two and mixed sizes within the same per-line limits)
+ * or dim not in {2, 3} (dim 3 is not built yet), OOM if the workspace does
+ * not fit, CUDA if no device is usable. */
+fftmech_status fftmech_create(fftmech_ctx** ctx, const fftmech_grid* grid,
+                              const fftmech_materials* mat, fftmech_precision precision,
+                              const fftmech_solver_opts* opts, void* stream);
+
+/* Free the workspace (and the stream, if the context created it). */
+fftmech_status fftmech_destroy(fftmech_ctx* ctx);
+
+/* Replace the solver options of an existing context. */
+fftmech_status fftmech_set_solver_opts(fftmech_ctx* ctx, const fftmech_solver_opts* opts);
+
+/* Human-readable name of a status code, and the last error message of a
+ * context (empty string if none). Both strings are owned by the library. */
+const char* fftmech_status_string(int status);
+const char* fftmech_last_error(const fftmech_ctx* ctx);
+
+enum { FFTMECH_DIFF_NONE = 0, FFTMECH_DIFF_HOMOGENISE = 1, FFTMECH_DIFF_TRANSIENT = 2 };
+enum { FFTMECH_EIG_FROM_PRECIPITATE = 0, FFTMECH_EIG_PRESCRIBED = 1 };
+
+/* Diffusion step (Sec. 2.1; Algorithm 1, "Diffusion of chemical species").
+ * mode FFTMECH_DIFF_HOMOGENISE (the paper): solves div j = 0,
+ *   j = -D(x) grad c, <grad c> = grad_c_mac (Eqs. diffusion, diffusion-final)
+ *   for the fluctuation phi (Eq. micro-gradient), then writes
+ *   c = grad_c_mac . x + phi + beta with beta_pore / beta_solid of
+ *   Eq. (psi-two-values), so <c>_pore = c_macro / eta and <c>_solid = 0
+ *   (Eq. concentration-correct). x is the voxel position k * h_diff.
+ *   dt, dirichlet_mask, dirichlet_value are ignored; c is output only.
+ *   info->mean_flux = <j>.
+ * mode FFTMECH_DIFF_TRANSIENT (an extension, not in the paper, whose RVE
+ *   diffusion is steady): one backward-Euler step of
+ *   dc/dt = div(D(x) grad c) with the same forward-difference Galerkin
+ *   operator; voxels with dirichlet_mask != 0 are held at dirichlet_value.
+ *   c is the concentration at the old time on input, the new one on output.
+ * phase: uint8 [N]; c: double [N]; dirichlet_mask: uint8 [N] or NULL. */
+fftmech_status fftmech_diffusion_step(fftmech_ctx* ctx, const uint8_t* phase, int mode,
+                                      const double grad_c_mac[3], double c_macro, double dt,
+                                      const uint8_t* dirichlet_mask, double dirichlet_value,
+                                      double* c, fftmech_solve_info* info);
+
+/* Mechanical equilibrium with eigenstrain (Sec. 2.3; Algorithm 1,
+ * "Development of stresses"): div[g(d) C(x) : (eps - e I)] = 0 with
+ * <eps> = eps_mac (Eqs. solid, solid-final), C(x) = omega C_solid +
+ * (1 - omega) C_pore isotropic, g(d) = (1 - d)^2 + kappa (Sec. 2.4),
+ * isotropic eigenstrain e(x) I (Eq. eigen-simplify; in-plane identity in 2D
+ * plane strain).
+ * phase: uint8 [N]; eig: field [N] (NULL = 0); damage: double [N] (NULL = 0);
+ * eps_mac: Voigt (3 used in 2D, 6 in 3D); u: double [dim * N], the
+ * displacement fluctuation: warm start on input (zero-mean), solution on
+ * output; strain, stress: field [nv * N] outputs (NULL = not written),
+ * strain = eps_mac + sym grad+ u, stress = g C : (strain - e I).
+ * info: iterations, residuals, <sigma>, <eps>, elastic energy. */
+fftmech_status fftmech_equilibrium_solve(fftmech_ctx* ctx, const uint8_t* phase, const void* eig,
+                                         const double* damage, const double eps_mac[6], double* u,
+                                         void* strain, void* stress, fftmech_solve_info* info);
+
+/* History update and phase-field solve (Sec. 2.4; Algorithm 1, "Crack
+ * initiation and propagation"). First H = max(H, psi+(strain - e I))
+ * with psi+ of Eq. (energy) (undegraded phase Lame constants; in 3D the bulk
+ * factor lambda + 2 mu / 3 and the 3D deviator), then solves
+ * (Gc / (2 l0) + H) d - (Gc l0 / 2) div grad d = H (Eqs. crack, crack-fft) with
+ * the Laplacian's symbol read as -|D|^2 (symmetric positive definite).
+ * strain: field [nv * N]; eig: field [N] (NULL = 0); phase: uint8 [N];
+ * H: field [N] in/out; damage: double [N], warm start in, solution out.
+ * info: iterations, residuals, total damage, fraction of damaged solid. */
+fftmech_status fftmech_phasefield_solve(fftmech_ctx* ctx, const void* strain, const void* eig,
+                                        const uint8_t* phase, void* H, double* damage,
+                                        fftmech_solve_info* info);
+
+/* State carried across staggered steps (all caller-owned, N voxels). */
+typedef struct {
+  const uint8_t* phase; /* uint8 [N] */
+  double* c;            /* concentration, double [N] */
+  void* c_ppt;          /* precipitate concentration, field [N] (NULL = not kept) */
+  void* eig;            /* eigenstrain e(x), field [N] */
+  double* u;            /* displacement fluctuation, double [dim * N] */
+  void* strain;         /* field [nv * N] */
+  void* stress;         /* field [nv * N] */
+  void* H;              /* history field, field [N] */
+  double* damage;       /* phase field d, double [N] */
+} fftmech_state;
+
+/* Loads of one staggered step.
+ * diffusion_mode: FFTMECH_DIFF_*; the HOMOGENISE / TRANSIENT inputs as in
+ * fftmech_diffusion_step. eig_mode FFTMECH_EIG_FROM_PRECIPITATE:
+ * c_ppt = (c - S_sol)_+ and e = (c_ppt M_ppt - 1)_+ in the pores, 0 in the
+ * solid (Sec. 2.2); FFTMECH_EIG_PRESCRIBED: e = eig_scale * eig_field
+ * (eig_field: field [N]). eps_mac: macro strain (Voigt). */
+typedef struct {
+  int diffusion_mode;
+  double grad_c_mac[3];
+  double c_macro;
+  double dt;
+  const uint8_t* dirichlet_mask;
+  double dirichlet_value;
+  int eig_mode;
+  const void* eig_field;
+  double eig_scale;
+  double eps_mac[6];
+} fftmech_step_params;
+
+/* One staggered load step in Algorithm 1's order (Sec. 2.5): diffusion ->
+ * precipitation -> eigenstrain -> equilibrium (stiffness degraded by the
+ * damage of the previous step) -> history -> phase field. The degradation
+ * by the new damage (Algorithm 1, last line) takes effect in the next call.
+ * info[0] = diffusion, info[1] = equilibrium, info[2] = phase field. */
+fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
+                                      const fftmech_step_params* params,
+                                      fftmech_solve_info info[3]);
+
+/* Instrumentation (no counterpart in the paper): kernel classes of the PCG
+ * loop. When profiling is enabled, every launch of a class is bracketed by
+ * CUDA events on the context's stream and its duration accumulated; launch
+ * counts are kept whether or not profiling is on. */
+enum {
+  FFTMECH_K_DIRECTION = 0, /* row IFFT + new search direction + <p, K p> */
+  FFTMECH_K_UPDATE = 1,    /* iterate / residual update + stencil + row FFT */
+  FFTMECH_K_COLUMN = 2,    /* column FFT, Fourier multiplier, <r, M^-1 r>, column IFFT */
+  FFTMECH_K_RESIDUAL = 3,  /* FP64 true residual + row FFT */
+  FFTMECH_K_OTHER = 4,     /* pointwise and post-processing kernels */
+  FFTMECH_K_COUNT = 5
+};
+
+/* Enable (1) or disable (0) per-launch event timing; resets the counters. */
+fftmech_status fftmech_profile_enable(fftmech_ctx* ctx, int enable);
+
+/* Launches and summed device time (ms) of one kernel class since the last
+ * fftmech_profile_enable; kclass = FFTMECH_K_COUNT gives the totals over
+ * all classes. total_ms is 0 while profiling is disabled. */
+fftmech_status fftmech_profile_read(fftmech_ctx* ctx, int kclass, long long* launches,
+                                    double* total_ms);
+
+/* Stand-alone complex-to-complex FFT with the library's Stockham kernels
+ * (the transform every solve uses; exposed for testing and comparison).
+ * data: interleaved complex, device memory, n[1] rows of n[0] points (2D,
+ * ndim = 2) or one line of n[0] points (ndim = 1), in place.
+ * precision: FFTMECH_FP64 (complex double) or FFTMECH_MIXED (complex
+ * float). inverse = 0: X[k] = sum_j x[j] exp(-2 pi i jk/n); inverse = 1: the
+ * same with +i and no 1/n factor. stream: cudaStream_t (NULL = default).
+ * Synchronises the stream before returning. */
+fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse, void* data,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTMECH_H */

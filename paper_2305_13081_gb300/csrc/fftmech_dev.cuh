@@ -1,0 +1,312 @@
+// Device building blocks: complex arithmetic, small DFT butterflies, the
+// mixed-radix (2, 3, 4, 8, 9) Stockham autosort FFT on lines held in shared
+// memory, and deterministic FP64 block reductions.
+//
+// The Stockham pass used here: with sub-transform length Ns before the pass
+// and radix r, butterfly j (0 <= j < n/r) reads x[j + t n/r] (t < r),
+// multiplies input t by w_{Ns r}^{t (j mod Ns)}, takes a radix-r DFT and
+// writes output t to (j div Ns) Ns r + (j mod Ns) + t Ns. Passes run in place
+// in shared memory: every thread loads all of its butterflies' inputs into
+// registers, the block synchronises, then every thread writes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fftmech {
+
+template <typename T>
+struct __align__(2 * sizeof(T)) cx {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> c; c.re = a; c.im = b; return c; }
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> scal(cx<T> a, T s) { return mk(a.re * s, a.im * s); }
+// multiply by s*i for s = +1 / -1
+template <typename T, int S>
+__device__ __forceinline__ cx<T> muli(cx<T> a) { return S > 0 ? mk(-a.im, a.re) : mk(a.im, -a.re); }
+
+// ---------------------------------------------------------------- butterflies
+// S = -1: forward exp(-2 pi i / r); S = +1: inverse.
+template <typename T, int S>
+__device__ __forceinline__ void dft2(cx<T>* v) {
+  cx<T> a = v[0], b = v[1];
+  v[0] = a + b;
+  v[1] = a - b;
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void dft3(cx<T>& a, cx<T>& b, cx<T>& c) {
+  const T h3 = T(0.8660254037844386);  // sin(2 pi / 3)
+  cx<T> t1 = b + c;
+  cx<T> t2 = a - scal(t1, T(0.5));
+  cx<T> t3 = scal(b - c, T(S) * h3);  // times i below
+  a = a + t1;
+  b = t2 + muli<T, 1>(t3);
+  c = t2 - muli<T, 1>(t3);
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void dft4(cx<T>& a, cx<T>& b, cx<T>& c, cx<T>& d) {
+  cx<T> s0 = a + c, s1 = a - c, s2 = b + d, s3 = muli<T, S>(b - d);
+  a = s0 + s2;
+  c = s0 - s2;
+  b = s1 + s3;
+  d = s1 - s3;
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void dft8(cx<T>* v) {
+  const T r2 = T(0.7071067811865476);
+  cx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  cx<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<T, S>(e0, e1, e2, e3);
+  dft4<T, S>(o0, o1, o2, o3);
+  // w8^m = exp(S i 2 pi m / 8)
+  cx<T> w1 = mk(r2, T(S) * r2);
+  cx<T> w3 = mk(-r2, T(S) * r2);
+  o1 = cmul(o1, w1);
+  o2 = muli<T, S>(o2);
+  o3 = cmul(o3, w3);
+  v[0] = e0 + o0; v[4] = e0 - o0;
+  v[1] = e1 + o1; v[5] = e1 - o1;
+  v[2] = e2 + o2; v[6] = e2 - o2;
+  v[3] = e3 + o3; v[7] = e3 - o3;
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void dft9(cx<T>* v) {
+  // 9 = 3 x 3: inner DFT3 over n1 for each n2 (x[3 n1 + n2]), twiddle
+  // w9^(n2 k1), outer DFT3 over n2 for each k1; output X[k1 + 3 k2].
+  const T c1 = T(0.766044443118978), s1 = T(0.6427876096865393);    // 2 pi / 9
+  const T c2 = T(0.17364817766693041), s2 = T(0.984807753012208);   // 4 pi / 9
+  const T c4 = T(-0.9396926207859083), s4 = T(0.3420201433256689);  // 8 pi / 9
+  cx<T> a0 = v[0], a1 = v[3], a2 = v[6];
+  cx<T> b0 = v[1], b1 = v[4], b2 = v[7];
+  cx<T> d0 = v[2], d1 = v[5], d2 = v[8];
+  dft3<T, S>(a0, a1, a2);
+  dft3<T, S>(b0, b1, b2);
+  dft3<T, S>(d0, d1, d2);
+  b1 = cmul(b1, mk(c1, T(S) * s1));
+  b2 = cmul(b2, mk(c2, T(S) * s2));
+  d1 = cmul(d1, mk(c2, T(S) * s2));
+  d2 = cmul(d2, mk(c4, T(S) * s4));
+  dft3<T, S>(a0, b0, d0);
+  dft3<T, S>(a1, b1, d1);
+  dft3<T, S>(a2, b2, d2);
+  v[0] = a0; v[3] = b0; v[6] = d0;
+  v[1] = a1; v[4] = b1; v[7] = d1;
+  v[2] = a2; v[5] = b2; v[8] = d2;
+}
+
+template <typename T, int R, int S>
+__device__ __forceinline__ void dft(cx<T>* v) {
+  if constexpr (R == 2) dft2<T, S>(v);
+  else if constexpr (R == 3) dft3<T, S>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<T, S>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<T, S>(v);
+  else dft9<T, S>(v);
+}
+
+// ---------------------------------------------------------------- plans
+constexpr int kMaxPass = 12;
+
+// One 1D transform length, factored into passes. The radix of pass s is the
+// 4-bit field s of `rcode`; the twiddles of pass s start after those of the
+// earlier passes (sum of Ns (r - 1)): entry k (r - 1) + t - 1 =
+// exp(-2 pi i k t / (Ns r)).
+template <typename T>
+struct FftPlanDev {
+  int n;
+  int npass;
+  unsigned long long rcode;
+  const cx<T>* tw;
+};
+
+// Butterflies a thread keeps in registers per pass: about nine points for
+// every radix, so one launch shape serves all passes.
+template <int R>
+struct PassBatch {
+  static constexpr int value = R >= 8 ? 1 : (R == 4 ? 2 : (R == 3 ? 3 : 4));
+};
+
+// Element (line, i) of a batch of lines sits at buf[line * ls + i * is].
+// lines_fast: consecutive threads take consecutive lines (column batches
+// stored [i][line]); otherwise consecutive butterflies of one line.
+template <typename T, int R, int S>
+__device__ __forceinline__ void stockham_pass(cx<T>* buf, int n, int Ns, const cx<T>* __restrict__ tw,
+                                              int nlines, int ls, int is, bool lines_fast) {
+  constexpr int BM = PassBatch<R>::value;
+  const int nb = n / R;
+  const int total = nb * nlines;
+  cx<T> v[BM][R];
+#pragma unroll
+  for (int b = 0; b < BM; ++b) {
+    const int idx = threadIdx.x + b * blockDim.x;
+    if (idx < total) {
+      int line, j;
+      if (lines_fast) { j = idx / nlines; line = idx - j * nlines; }
+      else { line = idx / nb; j = idx - line * nb; }
+      const cx<T>* src = buf + (size_t)line * ls;
+#pragma unroll
+      for (int t = 0; t < R; ++t) v[b][t] = src[(j + t * nb) * is];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BM; ++b) {
+    const int idx = threadIdx.x + b * blockDim.x;
+    if (idx < total) {
+      int line, j;
+      if (lines_fast) { j = idx / nlines; line = idx - j * nlines; }
+      else { line = idx / nb; j = idx - line * nb; }
+      const int q = j / Ns;
+      const int k = j - q * Ns;
+      if (Ns > 1) {
+        const cx<T>* w = tw + k * (R - 1);
+#pragma unroll
+        for (int t = 1; t < R; ++t) {
+          const cx<T> wt = w[t - 1];
+          v[b][t] = (S < 0) ? cmul(v[b][t], wt) : cmulc(v[b][t], wt);
+        }
+      }
+      dft<T, R, S>(v[b]);
+      cx<T>* dst = buf + (size_t)line * ls;
+      const int base = q * Ns * R + k;
+#pragma unroll
+      for (int t = 0; t < R; ++t) dst[(base + t * Ns) * is] = v[b][t];
+    }
+  }
+  __syncthreads();
+}
+
+// Radix families: a kernel is compiled for the radices its transform
+// lengths use, which keeps register pressure at that of the largest
+// butterfly instead of the sum over all five.
+enum RadixFamily { FAM_9 = 1, FAM_93 = 2, FAM_842 = 3, FAM_ALL = 4 };
+
+template <int FAM, int R>
+struct FamilyHas {
+  static constexpr bool value =
+      FAM == FAM_ALL || (FAM == FAM_9 && R == 9) || (FAM == FAM_93 && (R == 9 || R == 3)) ||
+      (FAM == FAM_842 && (R == 8 || R == 4 || R == 2));
+};
+
+// Full transform of `nlines` lines in place. Requires, for every pass,
+// nlines * n / r <= PassBatch<r> * blockDim.x (checked by the host), and
+// every radix of the plan in family FAM.
+template <typename T, int S, int FAM>
+__device__ void fft_lines(cx<T>* buf, const FftPlanDev<T>& p, int nlines, int ls, int is,
+                          bool lines_fast) {
+  int Ns = 1;
+  int off = 0;
+  const int n = p.n;
+  const unsigned long long code = p.rcode;
+  for (int s = 0; s < p.npass; ++s) {
+    const int r = (int)((code >> (4 * s)) & 15ull);
+    const cx<T>* tw = p.tw + off;
+    if constexpr (FamilyHas<FAM, 9>::value) {
+      if (r == 9) stockham_pass<T, 9, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+    }
+    if constexpr (FamilyHas<FAM, 8>::value) {
+      if (r == 8) stockham_pass<T, 8, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+    }
+    if constexpr (FamilyHas<FAM, 4>::value) {
+      if (r == 4) stockham_pass<T, 4, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+    }
+    if constexpr (FamilyHas<FAM, 3>::value) {
+      if (r == 3) stockham_pass<T, 3, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+    }
+    if constexpr (FamilyHas<FAM, 2>::value) {
+      if (r == 2) stockham_pass<T, 2, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+    }
+    off += Ns * (r - 1);
+    Ns *= r;
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+// Sum of K doubles over the block; result valid in thread 0. Uses `scratch`
+// (>= 32 * K doubles of shared memory). Deterministic for a fixed launch.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) scratch[k * 32 + wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = (lane < nw) ? scratch[k * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Publish this block's K partial sums; returns true in every thread of the
+// last block to finish, after which partials of all blocks are visible.
+template <int K>
+__device__ __forceinline__ bool publish_partials(const double (&v)[K], double* partials,
+                                                 unsigned int* counter) {
+  __shared__ int am_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)blockIdx.x * K + k] = v[k];
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  return am_last != 0;
+}
+
+// In the last block: totals[k] = sum over blocks in index order (thread 0
+// returns them; the counter is reset for the next launch).
+template <int K>
+__device__ __forceinline__ void gather_partials(double (&tot)[K], const double* partials,
+                                                unsigned int* counter, double* scratch) {
+  __threadfence();
+  double v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = 0.0;
+  // fixed assignment: thread t sums blocks t, t + bd, ... in order
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __ldcg(partials + (size_t)b * K + k);
+  }
+  block_sum<K>(v, scratch);
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = v[k];
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+}  // namespace fftmech

@@ -1,0 +1,207 @@
+// Internal declarations shared by the kernel translation units and the C ABI
+// layer: operator / vector parameter blocks, device-side solver scalars and
+// the host launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fftmech_dev.cuh"
+
+namespace fftmech {
+
+// Scalars of one PCG run, resident in device memory. The last block of a
+// reduction kernel updates them; every iteration kernel reads `done` first.
+struct SolverScalars {
+  double rz;       // <r, M^-1 r> of the current residual
+  double rz0;      // <f, M^-1 f> of the right-hand side (the normaliser)
+  double pq;       // <p, K p>
+  double alpha, beta;
+  double tol2;     // tol^2
+  double rz_true;  // <r, M^-1 r> right after the last true-residual replacement
+  int iter, max_iter, done, status;
+  unsigned int cnt[4];  // last-block counters: 0 direction, 1 column pass, 2 stats
+};
+
+// Column-pass modes: ITER (one PCG iteration: beta, convergence), NORM
+// (<f, M^-1 f> -> rz0, no store), INIT (first residual), PLAIN (bare column
+// FFT), TRUE (iteration right after a true-residual replacement),
+// TRUENORM (<r, M^-1 r> of a true residual -> rz_true, no store).
+enum ColMode { COL_ITER = 0, COL_NORM = 1, COL_INIT = 2, COL_PLAIN = 3, COL_TRUE = 4, COL_TRUENORM = 5 };
+
+// Material / operator description for the 2D row kernels.
+// Vector (D = 2, elasticity): K u = grad+^T [g C_omega : sym grad+ u];
+//   residual r = -grad+^T [g C_omega : (E + sym grad+ u - e I)].
+// Scalar (D = 1): K u = c0(x) u + grad+^T [kap_omega grad+ u];
+//   residual r = P (src - c0 u - grad+^T [kap_omega (grad+ u + G)]),
+//   c0 = c0c + c0f(x), src = src_scale * (srcd or srct), P zeroes masked voxels.
+template <typename T>
+struct Op2 {
+  int nx, ny;
+  double h;
+  const uint8_t* phase;
+  // elasticity
+  const T* g;  // degradation per voxel (NULL = 1)
+  double lam[2], mu[2];  // by phase: [0] pore, [1] solid
+  const T* eig;  // isotropic eigenstrain (NULL = 0)
+  double E[3];   // macro strain xx, yy, xy
+  // scalar problems
+  double kap[2];
+  double c0c;
+  const T* c0f;
+  const uint8_t* mask;
+  double G[2];
+  const double* srcd;
+  const T* srct;
+  double src_scale;
+};
+
+template <typename T>
+struct Vec2 {
+  double* u;      // iterate, D x N
+  T* r;           // residual, D x N
+  const T* p_in;  // previous direction
+  T* p_out;       // new direction
+  cx<T>* S;       // spectral rows, N complex (components packed re / im)
+  double* partials;
+  SolverScalars* sc;
+};
+
+// Fourier multiplier 1 / (m0 + m1 lambda(k)), lambda = lamx[kx] + lamy[ky]
+// (the symbol of grad+^T grad+); 0 where the denominator is 0 (k = 0 when
+// m0 = 0), scaled by 1/N to fold the inverse transform's normalisation.
+template <typename T>
+struct Spec2 {
+  const T* lamx;
+  const T* lamy;
+  double m0, m1;
+  double invN;
+};
+
+// Launch shapes chosen by the host.
+struct Shape2 {
+  int rows_update, threads_update;
+  int rows_dir, threads_dir;
+  int rows_res, threads_res;
+  int cols, threads_col;
+  int threads_plain;
+};
+
+// ---------------------------------------------------------------- launchers
+// Row kernels take the radix family of the x transform (FX), column kernels
+// that of the y transform (FY); see RadixFamily.
+template <typename T, int D, int FX>
+cudaError_t launch_residual(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                            const Shape2& sh, int zero_u, cudaStream_t st);
+template <typename T, int D, int FX>
+cudaError_t launch_update(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                          const Shape2& sh, int u_only, cudaStream_t st);
+template <typename T, int D, int FX>
+cudaError_t launch_direction(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                             const Shape2& sh, cudaStream_t st);
+template <typename T, int FY>
+cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec2<T>& sp,
+                           const Shape2& sh, int mode, int inverse, double* partials,
+                           SolverScalars* sc, cudaStream_t st);
+template <typename T, int FX>
+cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int inverse,
+                          const Shape2& sh, cudaStream_t st);
+
+#define FFTMECH_FAMILY_SWITCH(fam, CALL)      \
+  switch (fam) {                              \
+    case FAM_9: return CALL(FAM_9);           \
+    case FAM_93: return CALL(FAM_93);         \
+    case FAM_842: return CALL(FAM_842);       \
+    default: return CALL(FAM_ALL);            \
+  }
+
+template <typename T, int D>
+inline cudaError_t launch_residual_f(int fx, const Op2<T>& op, const Vec2<T>& v,
+                                     const FftPlanDev<T>& px, const Shape2& sh, int zero_u,
+                                     cudaStream_t st) {
+#define FFTMECH_C(F) launch_residual<T, D, F>(op, v, px, sh, zero_u, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T, int D>
+inline cudaError_t launch_update_f(int fx, const Op2<T>& op, const Vec2<T>& v,
+                                   const FftPlanDev<T>& px, const Shape2& sh, int u_only,
+                                   cudaStream_t st) {
+#define FFTMECH_C(F) launch_update<T, D, F>(op, v, px, sh, u_only, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T, int D>
+inline cudaError_t launch_direction_f(int fx, const Op2<T>& op, const Vec2<T>& v,
+                                      const FftPlanDev<T>& px, const Shape2& sh, cudaStream_t st) {
+#define FFTMECH_C(F) launch_direction<T, D, F>(op, v, px, sh, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T>
+inline cudaError_t launch_colpass_f(int fy, int nx, int ny, cx<T>* S, const FftPlanDev<T>& py,
+                                    const Spec2<T>& sp, const Shape2& sh, int mode, int inverse,
+                                    double* partials, SolverScalars* sc, cudaStream_t st) {
+#define FFTMECH_C(F) launch_colpass<T, F>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, st)
+  FFTMECH_FAMILY_SWITCH(fy, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T>
+inline cudaError_t launch_rowfft_f(int fx, int nx, int ny, cx<T>* S, const FftPlanDev<T>& px,
+                                   int inverse, const Shape2& sh, cudaStream_t st) {
+#define FFTMECH_C(F) launch_rowfft<T, F>(nx, ny, S, px, inverse, sh, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+
+// Post-processing and pointwise kernels (2D).
+template <typename T>
+cudaError_t launch_el_output(const Op2<T>& op, const double* u, T* strain, T* stress,
+                             double* partials, double* results, unsigned int* cnt,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_diff_stats(const Op2<T>& op, const double* phi, double hdiff, double c_macro,
+                              double* partials, double* results, unsigned int* cnt,
+                              cudaStream_t st);
+cudaError_t launch_diff_write_c(int nx, int ny, const uint8_t* phase, const double* phi,
+                                double hdiff, double G0, double G1, const double* beta_dev,
+                                double* c, cudaStream_t st);
+template <typename T>
+cudaError_t launch_history(long long N, const uint8_t* phase, double lam0, double lam1, double mu0,
+                           double mu1, const T* strain, const T* eig, T* H, double* Hd,
+                           double* partials, double* results, unsigned int* cnt, cudaStream_t st);
+cudaError_t launch_pf_stats(long long N, const uint8_t* phase, const double* d, double* partials,
+                            double* results, unsigned int* cnt, cudaStream_t st);
+template <typename T>
+cudaError_t launch_degradation(long long N, const double* d, double kappa, T* g, cudaStream_t st);
+template <typename T>
+cudaError_t launch_precipitate(long long N, const uint8_t* phase, const double* c, double S,
+                               double M, T* c_ppt, T* eig, cudaStream_t st);
+template <typename T>
+cudaError_t launch_scale_copy(long long N, const T* src, double scale, T* dst, cudaStream_t st);
+cudaError_t launch_set_masked(long long N, const uint8_t* mask, double value, double* c,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t st);
+
+// Shared-memory footprints of the row kernels (bytes) for R rows of nx:
+// residual: [max(D (R+2) doubles, 2 R T)] + [3 (R+1) doubles] per column;
+// update: [max(D (R+2), 2 R) T] + [3 (R+1) T]; direction: [2 (R+1) T] +
+// [D (R+1) T].
+inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+template <typename T, int D>
+inline size_t smem_residual(int nx, int R) {
+  const size_t a = (size_t)D * (R + 2) * sizeof(double), b = (size_t)2 * R * sizeof(T);
+  return align16((a > b ? a : b) * nx) + (size_t)3 * (R + 1) * nx * sizeof(double);
+}
+template <typename T, int D>
+inline size_t smem_update(int nx, int R) {
+  const size_t a = (size_t)(D * (R + 2) > 2 * R ? D * (R + 2) : 2 * R);
+  return align16(a * nx * sizeof(T)) + (size_t)3 * (R + 1) * nx * sizeof(T);
+}
+template <typename T, int D>
+inline size_t smem_direction(int nx, int R) {
+  return align16((size_t)2 * (R + 1) * nx * sizeof(T)) + (size_t)D * (R + 1) * nx * sizeof(T);
+}
+
+}  // namespace fftmech

@@ -1,0 +1,521 @@
+// 2D kernels of the FFT-Galerkin preconditioned CG (potential form).
+//
+// One PCG iteration is three launches on the row-major grid [ny][nx]:
+//   direction (rows): z = row-IFFT(S); p = z + beta p_old; <p, K p> (energy form)
+//   update    (rows): u += alpha p; r -= alpha K p; S = row-FFT(r packed re/im)
+//   column    (strips of columns): S = col-IFFT(m(k) col-FFT(S)); <r, M^-1 r>
+// where M^-1 = F^-1 diag(m) F is the Fourier multiplier 1 / (m0 + m1 |D|^2)
+// applied per component (two real components packed as one complex field,
+// exact because m is real and even). Equivalence with the paper's projected
+// gradient-space CG: G = D (D^-1) of App. A (Eq. g-42) maps potential PCG
+// iterates onto gradient CG iterates one to one.
+#pragma once
+
+#include "fftmech_internal.cuh"
+#include "fftmech.h"
+
+namespace fftmech {
+
+// Threads per block are capped at 512 (128 registers per thread available).
+#define FFTMECH_BOUNDS(T) __launch_bounds__(512)
+
+static __device__ __forceinline__ int wrap_y(int y, int ny) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); }
+
+static __device__ __forceinline__ int done_flag(const SolverScalars* sc) {
+  return *reinterpret_cast<const volatile int*>(&sc->done);
+}
+
+static __device__ __forceinline__ double vol_read(const double* p) {
+  return *reinterpret_cast<const volatile double*>(p);
+}
+
+// ---------------------------------------------------------------- finalisers
+static __device__ void finalize_direction(SolverScalars* sc, double pq) {
+  sc->pq = pq;
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    sc->done = 1;
+    sc->status = FFTMECH_ERR_NONFINITE;
+    return;
+  }
+  sc->alpha = sc->rz / pq;
+}
+
+static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
+  if (mode == COL_NORM) { sc->rz0 = tot; return; }
+  if (mode == COL_PLAIN) return;
+  if (mode == COL_TRUENORM) { sc->rz_true = tot; return; }
+  if (!isfinite(tot)) {
+    sc->rz = tot;
+    sc->done = 1;
+    sc->status = FFTMECH_ERR_NONFINITE;
+    return;
+  }
+  if (mode == COL_INIT) {
+    sc->rz = tot;
+    sc->beta = 0.0;
+    sc->iter = 0;
+    if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
+    else if (sc->max_iter <= 0) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
+    return;
+  }
+  sc->iter += 1;
+  if (mode == COL_TRUE) sc->rz_true = tot;
+  const double rz_old = sc->rz;
+  sc->rz = tot;
+  if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; return; }
+  if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; return; }
+  sc->beta = tot / rz_old;
+}
+
+// ---------------------------------------------------------------- residual
+// r = b - K u in FP64 (u from the iterate, zero_u: u = 0 except Dirichlet
+// voxels), written as T and row-transformed into S. Shared memory:
+// [max(D (R+2) doubles, 2 R T) per column] + [3 (R+1) doubles per column].
+template <typename T, int D, int FX>
+__global__ void FFTMECH_BOUNDS(T) k_residual(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int zero_u) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nx = op.nx, ny = op.ny;
+  const size_t N = (size_t)nx * ny;
+  const int y0 = blockIdx.x * R;
+  const int rows = min(R, ny - y0);
+  const int W = rows + 2;
+  const size_t reg0 = (size_t)max(D * (R + 2) * (int)sizeof(double), 2 * R * (int)sizeof(T)) * nx;
+  double* P = reinterpret_cast<double*>(smem);
+  double* SG = reinterpret_cast<double*>(smem + ((reg0 + 15) & ~size_t(15)));
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
+  const int SR = (rows + 1) * nx;  // stride of one SG component
+  const double ih = 1.0 / op.h;
+
+  for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
+    const int yy = i / nx, x = i - yy * nx;
+    const size_t gi = (size_t)wrap_y(y0 - 1 + yy, ny) * nx + x;
+    const bool keep = (D == 1) && op.mask && op.mask[gi];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double val = v.u[c * N + gi];
+      if (zero_u && !keep) val = 0.0;
+      P[(size_t)c * W * nx + i] = val;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < SR; i += blockDim.x) {
+    const int yy = i / nx, x = i - yy * nx;
+    const int xp = (x + 1 == nx) ? 0 : x + 1;
+    const size_t gi = (size_t)wrap_y(y0 - 1 + yy, ny) * nx + x;
+    const int ph = op.phase[gi] ? 1 : 0;
+    if constexpr (D == 2) {
+      const double* Ux = P;
+      const double* Uy = P + (size_t)W * nx;
+      const int c0 = yy * nx + x;
+      double exx = (Ux[yy * nx + xp] - Ux[c0]) * ih + op.E[0];
+      double eyy = (Uy[c0 + nx] - Uy[c0]) * ih + op.E[1];
+      const double exy = 0.5 * ((Ux[c0 + nx] - Ux[c0]) + (Uy[yy * nx + xp] - Uy[c0])) * ih + op.E[2];
+      const double e = op.eig ? (double)op.eig[gi] : 0.0;
+      exx -= e;
+      eyy -= e;
+      const double gg = op.g ? (double)op.g[gi] : 1.0;
+      const double lam = gg * op.lam[ph], mu = gg * op.mu[ph];
+      const double tr = exx + eyy;
+      SG[i] = lam * tr + 2.0 * mu * exx;
+      SG[SR + i] = lam * tr + 2.0 * mu * eyy;
+      SG[2 * SR + i] = 2.0 * mu * exy;
+    } else {
+      const int c0 = yy * nx + x;
+      const double u = P[c0];
+      const double kap = op.kap[ph];
+      SG[i] = kap * ((P[yy * nx + xp] - u) * ih + op.G[0]);
+      SG[SR + i] = kap * ((P[c0 + nx] - u) * ih + op.G[1]);
+      SG[2 * SR + i] = u;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
+    const int yr = i / nx, x = i - yr * nx;
+    const int yy = yr + 1;
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const size_t gi = (size_t)(y0 + yr) * nx + x;
+    const int c = yy * nx + x;
+    double r0, r1 = 0.0;
+    if constexpr (D == 2) {
+      const double* Sxx = SG;
+      const double* Syy = SG + SR;
+      const double* Sxy = SG + 2 * SR;
+      r0 = -((Sxx[yy * nx + xm] - Sxx[c]) + (Sxy[c - nx] - Sxy[c])) * ih;
+      r1 = -((Sxy[yy * nx + xm] - Sxy[c]) + (Syy[c - nx] - Syy[c])) * ih;
+    } else {
+      const double* Jx = SG;
+      const double* Jy = SG + SR;
+      const double div = ((Jx[yy * nx + xm] - Jx[c]) + (Jy[c - nx] - Jy[c])) * ih;
+      const double u = SG[2 * SR + c];
+      const double c0 = op.c0c + (op.c0f ? (double)op.c0f[gi] : 0.0);
+      const double src = op.srcd ? op.srcd[gi] : (op.srct ? (double)op.srct[gi] : 0.0);
+      r0 = op.src_scale * src - c0 * u - div;
+      if (op.mask && op.mask[gi]) r0 = 0.0;
+    }
+    const T t0 = (T)r0, t1 = (T)r1;
+    v.r[gi] = t0;
+    if constexpr (D == 2) v.r[N + gi] = t1;
+    F[i] = mk(t0, t1);
+  }
+  __syncthreads();
+  fft_lines<T, -1, FX>(F, px, rows, nx, 1, false);
+  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) v.S[(size_t)y0 * nx + i] = F[i];
+}
+
+// ---------------------------------------------------------------- update
+// u += alpha p (FP64 iterate); r -= alpha K p; S = row-FFT(r). Shared
+// memory: [max(D (R+2), 2 R) T per column] + [3 (R+1) T per column].
+template <typename T, int D, int FX>
+__global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int u_only) {
+  if (done_flag(v.sc)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const double alpha = vol_read(&v.sc->alpha);
+  const T a = (T)alpha;
+  const int nx = op.nx, ny = op.ny;
+  const size_t N = (size_t)nx * ny;
+  const int y0 = blockIdx.x * R;
+  const int rows = min(R, ny - y0);
+  if (u_only) {
+    for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
+      const size_t gi = (size_t)y0 * nx + i;
+#pragma unroll
+      for (int c = 0; c < D; ++c) v.u[c * N + gi] += alpha * (double)v.p_in[c * N + gi];
+    }
+    return;
+  }
+  const int W = rows + 2;
+  const size_t reg0 = (size_t)max(D * (R + 2), 2 * R) * nx * sizeof(T);
+  T* P = reinterpret_cast<T*>(smem);
+  T* SG = reinterpret_cast<T*>(smem + ((reg0 + 15) & ~size_t(15)));
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
+  const int SR = (rows + 1) * nx;
+  const T ih = (T)(1.0 / op.h);
+
+  for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
+    const int yy = i / nx, x = i - yy * nx;
+    const size_t gi = (size_t)wrap_y(y0 - 1 + yy, ny) * nx + x;
+#pragma unroll
+    for (int c = 0; c < D; ++c) P[(size_t)c * W * nx + i] = v.p_in[c * N + gi];
+  }
+  __syncthreads();
+  const T lam0 = (T)op.lam[0], lam1 = (T)op.lam[1], mu0 = (T)op.mu[0], mu1 = (T)op.mu[1];
+  const T kap0 = (T)op.kap[0], kap1 = (T)op.kap[1];
+  for (int i = threadIdx.x; i < SR; i += blockDim.x) {
+    const int yy = i / nx, x = i - yy * nx;
+    const int xp = (x + 1 == nx) ? 0 : x + 1;
+    const size_t gi = (size_t)wrap_y(y0 - 1 + yy, ny) * nx + x;
+    const bool sol = op.phase[gi] != 0;
+    const int c0 = yy * nx + x;
+    if constexpr (D == 2) {
+      const T* Ux = P;
+      const T* Uy = P + (size_t)W * nx;
+      const T exx = (Ux[yy * nx + xp] - Ux[c0]) * ih;
+      const T eyy = (Uy[c0 + nx] - Uy[c0]) * ih;
+      const T exy = T(0.5) * ((Ux[c0 + nx] - Ux[c0]) + (Uy[yy * nx + xp] - Uy[c0])) * ih;
+      const T gg = op.g ? op.g[gi] : T(1);
+      const T lam = gg * (sol ? lam1 : lam0), mu = gg * (sol ? mu1 : mu0);
+      const T tr = exx + eyy;
+      SG[i] = lam * tr + T(2) * mu * exx;
+      SG[SR + i] = lam * tr + T(2) * mu * eyy;
+      SG[2 * SR + i] = T(2) * mu * exy;
+      if (yy >= 1) {
+        v.u[gi] += alpha * (double)Ux[c0];
+        v.u[N + gi] += alpha * (double)Uy[c0];
+      }
+    } else {
+      const T p = P[c0];
+      const T kap = sol ? kap1 : kap0;
+      SG[i] = kap * (P[yy * nx + xp] - p) * ih;
+      SG[SR + i] = kap * (P[c0 + nx] - p) * ih;
+      const T c0v = (T)op.c0c + (op.c0f ? op.c0f[gi] : T(0));
+      SG[2 * SR + i] = c0v * p;
+      if (yy >= 1) v.u[gi] += alpha * (double)p;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
+    const int yr = i / nx, x = i - yr * nx;
+    const int yy = yr + 1;
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const size_t gi = (size_t)(y0 + yr) * nx + x;
+    const int c = yy * nx + x;
+    T r0, r1 = T(0);
+    if constexpr (D == 2) {
+      const T* Sxx = SG;
+      const T* Syy = SG + SR;
+      const T* Sxy = SG + 2 * SR;
+      const T q0 = ((Sxx[yy * nx + xm] - Sxx[c]) + (Sxy[c - nx] - Sxy[c])) * ih;
+      const T q1 = ((Sxy[yy * nx + xm] - Sxy[c]) + (Syy[c - nx] - Syy[c])) * ih;
+      r0 = v.r[gi] - a * q0;
+      r1 = v.r[N + gi] - a * q1;
+      v.r[gi] = r0;
+      v.r[N + gi] = r1;
+    } else {
+      const T* Jx = SG;
+      const T* Jy = SG + SR;
+      T q0 = SG[2 * SR + c] + ((Jx[yy * nx + xm] - Jx[c]) + (Jy[c - nx] - Jy[c])) * ih;
+      if (op.mask && op.mask[gi]) q0 = T(0);
+      r0 = v.r[gi] - a * q0;
+      v.r[gi] = r0;
+    }
+    F[i] = mk(r0, r1);
+  }
+  __syncthreads();
+  fft_lines<T, -1, FX>(F, px, rows, nx, 1, false);
+  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) v.S[(size_t)y0 * nx + i] = F[i];
+}
+
+// ---------------------------------------------------------------- direction
+// z = row-IFFT(S) (rows y0 .. y0 + rows, one halo row), p = z + beta p_old,
+// <p, K p> = sum of the energy density over the tile. Shared memory:
+// [2 (R+1) T per column] + [D (R+1) T per column].
+template <typename T, int D, int FX>
+__global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R) {
+  if (done_flag(v.sc)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  const double beta = vol_read(&v.sc->beta);
+  const T b = (T)beta;
+  const int nx = op.nx, ny = op.ny;
+  const size_t N = (size_t)nx * ny;
+  const int y0 = blockIdx.x * R;
+  const int rows = min(R, ny - y0);
+  const int W = rows + 1;
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
+  T* P = reinterpret_cast<T*>(smem + (((size_t)2 * (R + 1) * nx * sizeof(T) + 15) & ~size_t(15)));
+  for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
+    const int yy = i / nx, x = i - yy * nx;
+    F[i] = v.S[(size_t)wrap_y(y0 + yy, ny) * nx + x];
+  }
+  __syncthreads();
+  fft_lines<T, 1, FX>(F, px, W, nx, 1, false);
+  for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
+    const int yy = i / nx, x = i - yy * nx;
+    const size_t gi = (size_t)wrap_y(y0 + yy, ny) * nx + x;
+    const cx<T> z = F[i];
+    T p0 = z.re;
+    if constexpr (D == 1) {
+      if (op.mask && op.mask[gi]) p0 = T(0);
+    }
+    if (beta != 0.0) p0 += b * v.p_in[gi];
+    P[i] = p0;
+    if (yy < rows) v.p_out[gi] = p0;
+    if constexpr (D == 2) {
+      T p1 = z.im;
+      if (beta != 0.0) p1 += b * v.p_in[N + gi];
+      P[(size_t)W * nx + i] = p1;
+      if (yy < rows) v.p_out[N + gi] = p1;
+    }
+  }
+  __syncthreads();
+  const T ih = (T)(1.0 / op.h);
+  const T lam0 = (T)op.lam[0], lam1 = (T)op.lam[1], mu0 = (T)op.mu[0], mu1 = (T)op.mu[1];
+  const T kap0 = (T)op.kap[0], kap1 = (T)op.kap[1];
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
+    const int yy = i / nx, x = i - yy * nx;
+    const int xp = (x + 1 == nx) ? 0 : x + 1;
+    const size_t gi = (size_t)(y0 + yy) * nx + x;
+    const bool sol = op.phase[gi] != 0;
+    T w;
+    if constexpr (D == 2) {
+      const T* Ux = P;
+      const T* Uy = P + (size_t)W * nx;
+      const T exx = (Ux[yy * nx + xp] - Ux[i]) * ih;
+      const T eyy = (Uy[i + nx] - Uy[i]) * ih;
+      const T exy = T(0.5) * ((Ux[i + nx] - Ux[i]) + (Uy[yy * nx + xp] - Uy[i])) * ih;
+      const T gg = op.g ? op.g[gi] : T(1);
+      const T lam = sol ? lam1 : lam0, mu = sol ? mu1 : mu0;
+      const T tr = exx + eyy;
+      w = gg * (lam * tr * tr + T(2) * mu * (exx * exx + eyy * eyy + T(2) * exy * exy));
+    } else {
+      const T p = P[i];
+      const T gx = (P[yy * nx + xp] - p) * ih, gy = (P[i + nx] - p) * ih;
+      const T c0v = (T)op.c0c + (op.c0f ? op.c0f[gi] : T(0));
+      w = c0v * p * p + (sol ? kap1 : kap0) * (gx * gx + gy * gy);
+    }
+    acc[0] += (double)w;
+  }
+  block_sum<1>(acc, red);
+  if (publish_partials<1>(acc, v.partials, &v.sc->cnt[0])) {
+    double tot[1];
+    gather_partials<1>(tot, v.partials, &v.sc->cnt[0], red);
+    if (threadIdx.x == 0) finalize_direction(v.sc, tot[0]);
+  }
+}
+
+// ---------------------------------------------------------------- column pass
+// Strip of up to CW columns of S (stored [ky][c] in shared memory). Forward
+// column FFT, multiply by m(k) / N, accumulate sum m |S|^2 (Parseval:
+// <r, M^-1 r> = (1/N) sum_k m(k) |S(k)|^2 for the packed field), inverse
+// column FFT. COL_PLAIN: one column FFT only (sign from `inverse`).
+template <typename T, int FY>
+__global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev<T> py, Spec2<T> sp, int CW,
+                          int mode, int inverse, double* partials, SolverScalars* sc) {
+  if (mode != COL_PLAIN && mode != COL_NORM && mode != COL_TRUENORM && done_flag(sc)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  cx<T>* B = reinterpret_cast<cx<T>*>(smem);
+  const int x0 = blockIdx.x * CW;
+  const int nc = min(CW, nx - x0);
+  for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
+    const int y = i / nc, c = i - y * nc;
+    B[i] = S[(size_t)y * nx + x0 + c];
+  }
+  __syncthreads();
+  if (mode == COL_PLAIN) {
+    if (inverse) fft_lines<T, 1, FY>(B, py, nc, 1, nc, true);
+    else fft_lines<T, -1, FY>(B, py, nc, 1, nc, true);
+    for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
+      const int y = i / nc, c = i - y * nc;
+      S[(size_t)y * nx + x0 + c] = B[i];
+    }
+    return;
+  }
+  fft_lines<T, -1, FY>(B, py, nc, 1, nc, true);
+  const bool store = (mode != COL_NORM && mode != COL_TRUENORM);
+  const T m0 = (T)sp.m0, m1 = (T)sp.m1, invN = (T)sp.invN;
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
+    const int ky = i / nc, c = i - ky * nc;
+    const T den = m0 + m1 * (sp.lamx[x0 + c] + sp.lamy[ky]);
+    const T m = den > T(0) ? T(1) / den : T(0);
+    const cx<T> w = B[i];
+    acc[0] += (double)(m * (w.re * w.re + w.im * w.im));
+    if (store) B[i] = scal(w, m * invN);
+  }
+  if (store) {
+    __syncthreads();
+    fft_lines<T, 1, FY>(B, py, nc, 1, nc, true);
+    for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
+      const int y = i / nc, c = i - y * nc;
+      S[(size_t)y * nx + x0 + c] = B[i];
+    }
+  }
+  block_sum<1>(acc, red);
+  if (publish_partials<1>(acc, partials, &sc->cnt[1])) {
+    double tot[1];
+    gather_partials<1>(tot, partials, &sc->cnt[1], red);
+    if (threadIdx.x == 0) finalize_col(sc, mode, tot[0] * sp.invN);
+  }
+}
+
+// Plain row FFT of S (used by the stand-alone transform).
+template <typename T, int FX>
+__global__ void FFTMECH_BOUNDS(T) k_rowfft(int nx, int ny, cx<T>* S, FftPlanDev<T> px, int R, int inverse) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
+  const int y0 = blockIdx.x * R;
+  const int rows = min(R, ny - y0);
+  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) F[i] = S[(size_t)y0 * nx + i];
+  __syncthreads();
+  if (inverse) fft_lines<T, 1, FX>(F, px, rows, nx, 1, false);
+  else fft_lines<T, -1, FX>(F, px, rows, nx, 1, false);
+  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) S[(size_t)y0 * nx + i] = F[i];
+}
+
+// ---------------------------------------------------------------- launchers
+// Opt every row / column kernel into the device's full dynamic shared memory
+// once per process (launches then pass their own, smaller, sizes).
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes, int& configured) {
+  if (configured) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) configured = 1;
+  return e;
+}
+
+template <typename T, int D, int FX>
+cudaError_t launch_residual(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                            const Shape2& sh, int zero_u, cudaStream_t st) {
+  const int R = sh.rows_res;
+  const size_t sm = smem_residual<T, D>(op.nx, R);
+  static int cfg = 0;
+  cudaError_t e = set_smem(k_residual<T, D, FX>, sm, cfg);
+  if (e != cudaSuccess) return e;
+  const int grid = (op.ny + R - 1) / R;
+  k_residual<T, D, FX><<<grid, sh.threads_res, sm, st>>>(op, v, px, R, zero_u);
+  return cudaGetLastError();
+}
+
+template <typename T, int D, int FX>
+cudaError_t launch_update(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                          const Shape2& sh, int u_only, cudaStream_t st) {
+  const int R = sh.rows_update;
+  const size_t sm = u_only ? 0 : smem_update<T, D>(op.nx, R);
+  static int cfg = 0;
+  cudaError_t e = set_smem(k_update<T, D, FX>, smem_update<T, D>(op.nx, R), cfg);
+  if (e != cudaSuccess) return e;
+  const int grid = (op.ny + R - 1) / R;
+  k_update<T, D, FX><<<grid, sh.threads_update, sm, st>>>(op, v, px, R, u_only);
+  return cudaGetLastError();
+}
+
+template <typename T, int D, int FX>
+cudaError_t launch_direction(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                             const Shape2& sh, cudaStream_t st) {
+  const int R = sh.rows_dir;
+  const size_t sm = smem_direction<T, D>(op.nx, R);
+  static int cfg = 0;
+  cudaError_t e = set_smem(k_direction<T, D, FX>, sm, cfg);
+  if (e != cudaSuccess) return e;
+  const int grid = (op.ny + R - 1) / R;
+  k_direction<T, D, FX><<<grid, sh.threads_dir, sm, st>>>(op, v, px, R);
+  return cudaGetLastError();
+}
+
+template <typename T, int FY>
+cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec2<T>& sp,
+                           const Shape2& sh, int mode, int inverse, double* partials,
+                           SolverScalars* sc, cudaStream_t st) {
+  const int CW = sh.cols;
+  const size_t sm = (size_t)ny * CW * sizeof(cx<T>);
+  static int cfg = 0;
+  cudaError_t e = set_smem(k_colpass<T, FY>, sm, cfg);
+  if (e != cudaSuccess) return e;
+  const int grid = (nx + CW - 1) / CW;
+  k_colpass<T, FY><<<grid, sh.threads_col, sm, st>>>(nx, ny, S, py, sp, CW, mode, inverse, partials, sc);
+  return cudaGetLastError();
+}
+
+template <typename T, int FX>
+cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int inverse,
+                          const Shape2& sh, cudaStream_t st) {
+  const int R = sh.rows_update;
+  const size_t sm = (size_t)R * nx * sizeof(cx<T>);
+  static int cfg = 0;
+  cudaError_t e = set_smem(k_rowfft<T, FX>, sm, cfg);
+  if (e != cudaSuccess) return e;
+  const int grid = (ny + R - 1) / R;
+  k_rowfft<T, FX><<<grid, sh.threads_update, sm, st>>>(nx, ny, S, px, R, inverse);
+  return cudaGetLastError();
+}
+
+// Explicit instantiations for one radix family (one translation unit each).
+#define FFTMECH_INST_TD(T, D, F)                                                                   \
+  template cudaError_t launch_residual<T, D, F>(const Op2<T>&, const Vec2<T>&,                    \
+                                                const FftPlanDev<T>&, const Shape2&, int,         \
+                                                cudaStream_t);                                    \
+  template cudaError_t launch_update<T, D, F>(const Op2<T>&, const Vec2<T>&, const FftPlanDev<T>&, \
+                                              const Shape2&, int, cudaStream_t);                  \
+  template cudaError_t launch_direction<T, D, F>(const Op2<T>&, const Vec2<T>&,                   \
+                                                 const FftPlanDev<T>&, const Shape2&, cudaStream_t);
+#define FFTMECH_INST_T(T, F)                                                                       \
+  FFTMECH_INST_TD(T, 1, F)                                                                         \
+  FFTMECH_INST_TD(T, 2, F)                                                                         \
+  template cudaError_t launch_colpass<T, F>(int, int, cx<T>*, const FftPlanDev<T>&,               \
+                                            const Spec2<T>&, const Shape2&, int, int, double*,    \
+                                            SolverScalars*, cudaStream_t);                        \
+  template cudaError_t launch_rowfft<T, F>(int, int, cx<T>*, const FftPlanDev<T>&, int,           \
+                                           const Shape2&, cudaStream_t);
+#define FFTMECH_INST_FAMILY(F) \
+  FFTMECH_INST_T(float, F)     \
+  FFTMECH_INST_T(double, F)
+
+}  // namespace fftmech

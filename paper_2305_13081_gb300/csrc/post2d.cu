@@ -1,0 +1,294 @@
+// Pointwise physics and FP64 post-processing reductions (2D).
+#include "fftmech_internal.cuh"
+#include "fftmech.h"
+
+namespace fftmech {
+
+static constexpr int kPostThreads = 256;
+
+static inline int post_grid(long long n) {
+  long long g = (n + kPostThreads - 1) / kPostThreads;
+  if (g > 4096) g = 4096;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// strain = E + sym grad+ u, stress = g C : (strain - e I) (Eq. solid);
+// sums of stress, strain and the energy density 1/2 (strain - e I) : stress.
+template <typename T>
+__global__ void k_el_output(Op2<T> op, const double* __restrict__ u, T* strain, T* stress,
+                            double* partials, double* results, unsigned int* cnt) {
+  __shared__ double red[32 * 7];
+  const int nx = op.nx, ny = op.ny;
+  const long long N = (long long)nx * ny;
+  const double ih = 1.0 / op.h;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(gi / nx), x = (int)(gi - (long long)y * nx);
+    const long long ixp = (long long)y * nx + (x + 1 == nx ? 0 : x + 1);
+    const long long iyp = (long long)(y + 1 == ny ? 0 : y + 1) * nx + x;
+    const double exx = op.E[0] + (u[ixp] - u[gi]) * ih;
+    const double eyy = op.E[1] + (u[N + iyp] - u[N + gi]) * ih;
+    const double exy = op.E[2] + 0.5 * ((u[iyp] - u[gi]) + (u[N + ixp] - u[N + gi])) * ih;
+    const double e = op.eig ? (double)op.eig[gi] : 0.0;
+    const int ph = op.phase[gi] ? 1 : 0;
+    const double gg = op.g ? (double)op.g[gi] : 1.0;
+    const double lam = gg * op.lam[ph], mu = gg * op.mu[ph];
+    const double axx = exx - e, ayy = eyy - e;
+    const double tr = axx + ayy;
+    const double sxx = lam * tr + 2 * mu * axx, syy = lam * tr + 2 * mu * ayy, sxy = 2 * mu * exy;
+    if (strain) { strain[gi] = (T)exx; strain[N + gi] = (T)eyy; strain[2 * N + gi] = (T)exy; }
+    if (stress) { stress[gi] = (T)sxx; stress[N + gi] = (T)syy; stress[2 * N + gi] = (T)sxy; }
+    acc[0] += sxx; acc[1] += syy; acc[2] += sxy;
+    acc[3] += exx; acc[4] += eyy; acc[5] += exy;
+    acc[6] += 0.5 * (axx * sxx + ayy * syy + 2 * exy * sxy);
+  }
+  block_sum<7>(acc, red);
+  if (publish_partials<7>(acc, partials, cnt)) {
+    double tot[7];
+    gather_partials<7>(tot, partials, cnt, red);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 7; ++k) results[k] = tot[k];
+  }
+}
+
+// Phase statistics of the homogenised diffusion solution (Eq. psi-two-values)
+// and the mean flux; the last block turns them into beta_pore, beta_solid.
+// results: [0] beta_pore [1] beta_solid [2] <jx> [3] <jy> [4] porosity.
+template <typename T>
+__global__ void k_diff_stats(Op2<T> op, const double* __restrict__ phi, double hdiff,
+                             double c_macro, double* partials, double* results, unsigned int* cnt) {
+  __shared__ double red[32 * 10];
+  const int nx = op.nx, ny = op.ny;
+  const long long N = (long long)nx * ny;
+  const double ih = 1.0 / hdiff;
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(gi / nx), x = (int)(gi - (long long)y * nx);
+    const long long ixp = (long long)y * nx + (x + 1 == nx ? 0 : x + 1);
+    const long long iyp = (long long)(y + 1 == ny ? 0 : y + 1) * nx + x;
+    const int s = op.phase[gi] ? 1 : 0;  // 0 pore, 1 solid
+    const double ramp = op.G[0] * (x * hdiff) + op.G[1] * (y * hdiff);
+    acc[s] += 1.0;
+    acc[2 + s] += phi[gi];
+    acc[4 + s] += ramp;
+    const double D = op.kap[s];
+    acc[6] += -D * (op.G[0] + (phi[ixp] - phi[gi]) * ih);
+    acc[7] += -D * (op.G[1] + (phi[iyp] - phi[gi]) * ih);
+  }
+  block_sum<10>(acc, red);
+  if (publish_partials<10>(acc, partials, cnt)) {
+    double tot[10];
+    gather_partials<10>(tot, partials, cnt, red);
+    if (threadIdx.x == 0) {
+      const double np = tot[0], ns = tot[1];
+      const double eta = np / (double)N;
+      results[0] = np > 0 ? c_macro / eta - (tot[4] + tot[2]) / np : 0.0;
+      results[1] = ns > 0 ? -(tot[5] + tot[3]) / ns : 0.0;
+      results[2] = tot[6] / (double)N;
+      results[3] = tot[7] / (double)N;
+      results[4] = eta;
+    }
+  }
+}
+
+// c = grad c_mac . x + phi + beta_phase (Eqs. concentration, concentration-correct).
+__global__ void k_diff_write_c(int nx, int ny, const uint8_t* __restrict__ phase,
+                               const double* __restrict__ phi, double hdiff, double G0, double G1,
+                               const double* __restrict__ beta, double* __restrict__ c) {
+  const long long N = (long long)nx * ny;
+  for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(gi / nx), x = (int)(gi - (long long)y * nx);
+    const double b = phase[gi] ? beta[1] : beta[0];
+    c[gi] = G0 * (x * hdiff) + G1 * (y * hdiff) + phi[gi] + b;
+  }
+}
+
+// H = max(H, psi+(eps - e I)) with Eq. (energy) in 2D; Hd = H as double;
+// results[0] = sum of H (for the preconditioner's mean history).
+template <typename T>
+__global__ void k_history(long long N, const uint8_t* __restrict__ phase, double lam0, double lam1,
+                          double mu0, double mu1, const T* __restrict__ strain,
+                          const T* __restrict__ eig, T* H, double* Hd, double* partials,
+                          double* results, unsigned int* cnt) {
+  __shared__ double red[32];
+  double acc[1] = {0.0};
+  for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const bool sol = phase[gi] != 0;
+    const double lam = sol ? lam1 : lam0, mu = sol ? mu1 : mu0;
+    const double e = eig ? (double)eig[gi] : 0.0;
+    const double exx = (double)strain[gi] - e, eyy = (double)strain[N + gi] - e;
+    const double exy = (double)strain[2 * N + gi];
+    const double tr = exx + eyy;
+    const double dx = exx - 0.5 * tr, dy = eyy - 0.5 * tr;
+    const double trp = tr > 0 ? tr : 0.0;
+    const double psi = 0.5 * (lam + mu) * trp * trp + mu * (dx * dx + dy * dy + 2 * exy * exy);
+    const double h = (double)(T)fmax((double)H[gi], psi);
+    H[gi] = (T)h;
+    Hd[gi] = h;
+    acc[0] += h;
+  }
+  block_sum<1>(acc, red);
+  if (publish_partials<1>(acc, partials, cnt)) {
+    double tot[1];
+    gather_partials<1>(tot, partials, cnt, red);
+    if (threadIdx.x == 0) results[0] = tot[0];
+  }
+}
+
+// results: [0] sum d, [1] solid voxels with d > 0.9, [2] solid voxels.
+__global__ void k_pf_stats(long long N, const uint8_t* __restrict__ phase, const double* __restrict__ d,
+                           double* partials, double* results, unsigned int* cnt) {
+  __shared__ double red[32 * 3];
+  double acc[3] = {0, 0, 0};
+  for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const double v = d ? d[gi] : 0.0;
+    acc[0] += v;
+    if (phase[gi]) {
+      acc[2] += 1.0;
+      if (v > 0.9) acc[1] += 1.0;
+    }
+  }
+  block_sum<3>(acc, red);
+  if (publish_partials<3>(acc, partials, cnt)) {
+    double tot[3];
+    gather_partials<3>(tot, partials, cnt, red);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 3; ++k) results[k] = tot[k];
+  }
+}
+
+// g(d) = (1 - d)^2 + kappa (Sec. 2.4).
+template <typename T>
+__global__ void k_degradation(long long N, const double* __restrict__ d, double kappa, T* g) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double a = 1.0 - d[i];
+    g[i] = (T)(a * a + kappa);
+  }
+}
+
+// c_ppt = (c - S)_+ and e = (c_ppt M - 1)_+ in the pores, 0 in the solid (Sec. 2.2).
+template <typename T>
+__global__ void k_precipitate(long long N, const uint8_t* __restrict__ phase, const double* __restrict__ c,
+                              double S, double M, T* c_ppt, T* eig) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double cp = 0.0, e = 0.0;
+    if (!phase[i]) {
+      cp = c[i] - S;
+      cp = cp > 0 ? cp : 0.0;
+      e = cp * M - 1.0;
+      e = e > 0 ? e : 0.0;
+    }
+    if (c_ppt) c_ppt[i] = (T)cp;
+    eig[i] = (T)e;
+  }
+}
+
+template <typename T>
+__global__ void k_scale_copy(long long N, const T* __restrict__ src, double s, T* dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (T)(s * (double)src[i]);
+}
+
+__global__ void k_set_masked(long long N, const uint8_t* __restrict__ mask, double value, double* c) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    if (mask[i]) c[i] = value;
+}
+
+template <typename T>
+__global__ void k_to_real(long long N, const double* __restrict__ src, T* dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t launch_el_output(const Op2<T>& op, const double* u, T* strain, T* stress,
+                             double* partials, double* results, unsigned int* cnt,
+                             cudaStream_t st) {
+  k_el_output<T><<<post_grid((long long)op.nx * op.ny), kPostThreads, 0, st>>>(op, u, strain, stress,
+                                                                              partials, results, cnt);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_diff_stats(const Op2<T>& op, const double* phi, double hdiff, double c_macro,
+                              double* partials, double* results, unsigned int* cnt,
+                              cudaStream_t st) {
+  k_diff_stats<T><<<post_grid((long long)op.nx * op.ny), kPostThreads, 0, st>>>(
+      op, phi, hdiff, c_macro, partials, results, cnt);
+  return cudaGetLastError();
+}
+cudaError_t launch_diff_write_c(int nx, int ny, const uint8_t* phase, const double* phi,
+                                double hdiff, double G0, double G1, const double* beta_dev,
+                                double* c, cudaStream_t st) {
+  k_diff_write_c<<<post_grid((long long)nx * ny), kPostThreads, 0, st>>>(nx, ny, phase, phi, hdiff,
+                                                                        G0, G1, beta_dev, c);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_history(long long N, const uint8_t* phase, double lam0, double lam1, double mu0,
+                           double mu1, const T* strain, const T* eig, T* H, double* Hd,
+                           double* partials, double* results, unsigned int* cnt, cudaStream_t st) {
+  k_history<T><<<post_grid(N), kPostThreads, 0, st>>>(N, phase, lam0, lam1, mu0, mu1, strain, eig,
+                                                      H, Hd, partials, results, cnt);
+  return cudaGetLastError();
+}
+cudaError_t launch_pf_stats(long long N, const uint8_t* phase, const double* d, double* partials,
+                            double* results, unsigned int* cnt, cudaStream_t st) {
+  k_pf_stats<<<post_grid(N), kPostThreads, 0, st>>>(N, phase, d, partials, results, cnt);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_degradation(long long N, const double* d, double kappa, T* g, cudaStream_t st) {
+  k_degradation<T><<<post_grid(N), kPostThreads, 0, st>>>(N, d, kappa, g);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_precipitate(long long N, const uint8_t* phase, const double* c, double S,
+                               double M, T* c_ppt, T* eig, cudaStream_t st) {
+  k_precipitate<T><<<post_grid(N), kPostThreads, 0, st>>>(N, phase, c, S, M, c_ppt, eig);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_scale_copy(long long N, const T* src, double scale, T* dst, cudaStream_t st) {
+  k_scale_copy<T><<<post_grid(N), kPostThreads, 0, st>>>(N, src, scale, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_set_masked(long long N, const uint8_t* mask, double value, double* c,
+                              cudaStream_t st) {
+  k_set_masked<<<post_grid(N), kPostThreads, 0, st>>>(N, mask, value, c);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t st) {
+  k_to_real<T><<<post_grid(N), kPostThreads, 0, st>>>(N, src, dst);
+  return cudaGetLastError();
+}
+
+#define FFTMECH_POST_INST(T)                                                                       \
+  template cudaError_t launch_el_output<T>(const Op2<T>&, const double*, T*, T*, double*, double*, \
+                                           unsigned int*, cudaStream_t);                           \
+  template cudaError_t launch_diff_stats<T>(const Op2<T>&, const double*, double, double, double*, \
+                                            double*, unsigned int*, cudaStream_t);                 \
+  template cudaError_t launch_history<T>(long long, const uint8_t*, double, double, double,        \
+                                         double, const T*, const T*, T*, double*, double*, double*, \
+                                         unsigned int*, cudaStream_t);                             \
+  template cudaError_t launch_degradation<T>(long long, const double*, double, T*, cudaStream_t);  \
+  template cudaError_t launch_precipitate<T>(long long, const uint8_t*, const double*, double,     \
+                                             double, T*, T*, cudaStream_t);                        \
+  template cudaError_t launch_scale_copy<T>(long long, const T*, double, T*, cudaStream_t);        \
+  template cudaError_t launch_to_real<T>(long long, const double*, T*, cudaStream_t);
+
+FFTMECH_POST_INST(float)
+FFTMECH_POST_INST(double)
+
+}  // namespace fftmech

@@ -1,0 +1,323 @@
+"""ctypes binding of libfftmech (include/fftmech.h): the same entry points,
+structs and constants, argument marshalling only. Every computation runs in
+the CUDA library; there is no Python or CPU fallback, and loading fails
+loudly when the library has not been built.
+
+Buffers may be torch CUDA tensors (passed by data_ptr()), numpy arrays or
+host torch tensors (passed as host pointers; the library stages them through
+device memory), or raw integer addresses.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfftmech.so")
+
+# status codes
+FFTMECH_OK = 0
+FFTMECH_ERR_INVALID_ARG = 1
+FFTMECH_ERR_UNSUPPORTED_SIZE = 2
+FFTMECH_ERR_NOT_CONVERGED = 3
+FFTMECH_ERR_NONFINITE = 4
+FFTMECH_ERR_TIMEOUT = 5
+FFTMECH_ERR_CUDA = 6
+FFTMECH_ERR_OOM = 7
+# precisions
+FFTMECH_FP64 = 0
+FFTMECH_MIXED = 1
+# diffusion / eigenstrain modes
+FFTMECH_DIFF_NONE = 0
+FFTMECH_DIFF_HOMOGENISE = 1
+FFTMECH_DIFF_TRANSIENT = 2
+FFTMECH_EIG_FROM_PRECIPITATE = 0
+FFTMECH_EIG_PRESCRIBED = 1
+# kernel classes (instrumentation)
+FFTMECH_K_DIRECTION = 0
+FFTMECH_K_UPDATE = 1
+FFTMECH_K_COLUMN = 2
+FFTMECH_K_RESIDUAL = 3
+FFTMECH_K_OTHER = 4
+FFTMECH_K_COUNT = 5
+KERNEL_CLASS_NAMES = ["direction", "update", "column", "residual", "other"]
+
+c_double3 = ctypes.c_double * 3
+c_double6 = ctypes.c_double * 6
+c_int3 = ctypes.c_int * 3
+
+
+class fftmech_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", c_int3), ("h", ctypes.c_double),
+                ("h_diff", ctypes.c_double)]
+
+
+class fftmech_materials(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("E_solid", "nu_solid", "E_pore", "nu_pore", "D_solid", "D_pore",
+                 "Gc", "l0", "kappa", "S_sol", "M_ppt")]
+
+
+class fftmech_solver_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("replace_every", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class fftmech_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
+                ("mean_stress", c_double6), ("mean_strain", c_double6),
+                ("mean_flux", c_double3), ("mean_c", ctypes.c_double),
+                ("porosity", ctypes.c_double), ("elastic_energy", ctypes.c_double),
+                ("total_damage", ctypes.c_double), ("frac_damaged", ctypes.c_double),
+                ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+class fftmech_state(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_void_p), ("c", ctypes.c_void_p), ("c_ppt", ctypes.c_void_p),
+                ("eig", ctypes.c_void_p), ("u", ctypes.c_void_p), ("strain", ctypes.c_void_p),
+                ("stress", ctypes.c_void_p), ("H", ctypes.c_void_p), ("damage", ctypes.c_void_p)]
+
+
+class fftmech_step_params(ctypes.Structure):
+    _fields_ = [("diffusion_mode", ctypes.c_int), ("grad_c_mac", c_double3),
+                ("c_macro", ctypes.c_double), ("dt", ctypes.c_double),
+                ("dirichlet_mask", ctypes.c_void_p), ("dirichlet_value", ctypes.c_double),
+                ("eig_mode", ctypes.c_int), ("eig_field", ctypes.c_void_p),
+                ("eig_scale", ctypes.c_double), ("eps_mac", c_double6)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libfftmech.so (built by paper_2305_13081_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"libfftmech.so not found at {path}: build it with "
+            "`python -m paper_2305_13081_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    i = ctypes.c_int
+    d = ctypes.c_double
+    sigs = {
+        "fftmech_create": (i, [P(vp), P(fftmech_grid), P(fftmech_materials), i,
+                               P(fftmech_solver_opts), vp]),
+        "fftmech_destroy": (i, [vp]),
+        "fftmech_set_solver_opts": (i, [vp, P(fftmech_solver_opts)]),
+        "fftmech_status_string": (ctypes.c_char_p, [i]),
+        "fftmech_last_error": (ctypes.c_char_p, [vp]),
+        "fftmech_diffusion_step": (i, [vp, vp, i, P(d), d, d, vp, d, vp, P(fftmech_solve_info)]),
+        "fftmech_equilibrium_solve": (i, [vp, vp, vp, vp, P(d), vp, vp, vp, P(fftmech_solve_info)]),
+        "fftmech_phasefield_solve": (i, [vp, vp, vp, vp, vp, vp, P(fftmech_solve_info)]),
+        "fftmech_staggered_step": (i, [vp, P(fftmech_state), P(fftmech_step_params),
+                                       P(fftmech_solve_info)]),
+        "fftmech_fft": (i, [i, P(i), i, i, vp, vp]),
+        "fftmech_profile_enable": (i, [vp, i]),
+        "fftmech_profile_read": (i, [vp, i, P(ctypes.c_longlong), P(d)]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def ptr(x):
+    """Address of a buffer: torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffers must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _check(rc, ctx=None, allow=(FFTMECH_OK,)):
+    if rc in allow:
+        return rc
+    lib = load_library()
+    msg = lib.fftmech_status_string(rc).decode()
+    if ctx is not None:
+        detail = lib.fftmech_last_error(ctx).decode()
+        if detail:
+            msg += ": " + detail
+    raise FftmechError(rc, msg)
+
+
+class FftmechError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fftmech status {status}: {msg}")
+        self.status = status
+
+
+# ---------------------------------------------------------------- same names as the C ABI
+
+def fftmech_create(grid, mat, precision, opts, stream=None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rc = lib.fftmech_create(ctypes.byref(h), ctypes.byref(grid), ctypes.byref(mat), int(precision),
+                            ctypes.byref(opts), stream)
+    _check(rc)
+    return h
+
+
+def fftmech_destroy(ctx):
+    return load_library().fftmech_destroy(ctx)
+
+
+def fftmech_set_solver_opts(ctx, opts):
+    return _check(load_library().fftmech_set_solver_opts(ctx, ctypes.byref(opts)), ctx)
+
+
+def fftmech_status_string(status):
+    return load_library().fftmech_status_string(int(status)).decode()
+
+
+def fftmech_last_error(ctx):
+    return load_library().fftmech_last_error(ctx).decode()
+
+
+_SOLVER_OK = (FFTMECH_OK, FFTMECH_ERR_NOT_CONVERGED, FFTMECH_ERR_NONFINITE)
+
+
+def fftmech_diffusion_step(ctx, phase, mode, grad_c_mac, c_macro, dt, dirichlet_mask,
+                           dirichlet_value, c, info=None):
+    info = info or fftmech_solve_info()
+    g = c_double3(*(list(grad_c_mac) + [0.0] * 3)[:3])
+    rc = load_library().fftmech_diffusion_step(ctx, ptr(phase), int(mode), g, float(c_macro),
+                                               float(dt), ptr(dirichlet_mask),
+                                               float(dirichlet_value), ptr(c), ctypes.byref(info))
+    _check(rc, ctx, _SOLVER_OK)
+    return info
+
+
+def fftmech_equilibrium_solve(ctx, phase, eig, damage, eps_mac, u, strain, stress, info=None):
+    info = info or fftmech_solve_info()
+    e = c_double6(*(list(eps_mac) + [0.0] * 6)[:6])
+    rc = load_library().fftmech_equilibrium_solve(ctx, ptr(phase), ptr(eig), ptr(damage), e, ptr(u),
+                                                  ptr(strain), ptr(stress), ctypes.byref(info))
+    _check(rc, ctx, _SOLVER_OK)
+    return info
+
+
+def fftmech_phasefield_solve(ctx, strain, eig, phase, H, damage, info=None):
+    info = info or fftmech_solve_info()
+    rc = load_library().fftmech_phasefield_solve(ctx, ptr(strain), ptr(eig), ptr(phase), ptr(H),
+                                                 ptr(damage), ctypes.byref(info))
+    _check(rc, ctx, _SOLVER_OK)
+    return info
+
+
+def fftmech_staggered_step(ctx, state, params, infos=None):
+    infos = infos or (fftmech_solve_info * 3)()
+    rc = load_library().fftmech_staggered_step(ctx, ctypes.byref(state), ctypes.byref(params), infos)
+    _check(rc, ctx, _SOLVER_OK)
+    return infos
+
+
+def fftmech_fft(ndim, n, precision, inverse, data, stream=None):
+    nn = c_int3(*(list(n) + [1, 1, 1])[:3])
+    rc = load_library().fftmech_fft(int(ndim), nn, int(precision), int(inverse), ptr(data), stream)
+    _check(rc)
+    return rc
+
+
+def fftmech_profile_enable(ctx, enable):
+    return _check(load_library().fftmech_profile_enable(ctx, int(enable)), ctx)
+
+
+def fftmech_profile_read(ctx, kclass):
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    _check(load_library().fftmech_profile_read(ctx, int(kclass), ctypes.byref(n), ctypes.byref(ms)), ctx)
+    return n.value, ms.value
+
+
+# ---------------------------------------------------------------- small conveniences
+
+def make_grid(shape, h, h_diff=1.0):
+    """shape in array order (ny, nx) or (nz, ny, nx)."""
+    g = fftmech_grid()
+    g.dim = len(shape)
+    n = list(reversed(shape)) + [1] * (3 - len(shape))
+    g.n = c_int3(*n)
+    g.h = h
+    g.h_diff = h_diff
+    return g
+
+
+def make_materials(m):
+    """From any object with the fftmech_materials field names as attributes."""
+    out = fftmech_materials()
+    for k, _ in fftmech_materials._fields_:
+        setattr(out, k, float(getattr(m, k)))
+    return out
+
+
+def make_opts(tol=1e-8, max_iter=20000, replace_every=50, check_every=16):
+    o = fftmech_solver_opts()
+    o.tol = tol
+    o.max_iter = max_iter
+    o.replace_every = replace_every
+    o.check_every = check_every
+    return o
+
+
+class Context:
+    """Owns one fftmech context (create / destroy)."""
+
+    def __init__(self, shape, materials, precision=FFTMECH_FP64, h=5e-6, h_diff=1.0,
+                 tol=1e-8, max_iter=20000, replace_every=50, check_every=16, stream=None):
+        self.shape = tuple(shape)
+        self.precision = precision
+        self.grid = make_grid(shape, h, h_diff)
+        self.mat = make_materials(materials)
+        self.opts = make_opts(tol, max_iter, replace_every, check_every)
+        self.handle = fftmech_create(self.grid, self.mat, precision, self.opts, stream)
+
+    @property
+    def field_dtype(self):
+        return np.float64 if self.precision == FFTMECH_FP64 else np.float32
+
+    def set_opts(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opts, k, v)
+        fftmech_set_solver_opts(self.handle, self.opts)
+
+    def close(self):
+        if self.handle:
+            fftmech_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
