@@ -94,14 +94,16 @@ typedef struct {
 
 /* PCG controls. Stop when the gradient-space residual norm (the paper's CG
  * residual, equal to sqrt(r.M^-1 r) of the potential PCG) has dropped by
- * `tol` relative to that of the right-hand side. replace_every: MIXED only,
- * replace the recursive residual by the FP64 true residual every that many
- * iterations (0 = never). check_every: iterations between host polls of the
- * device convergence flag. */
+ * `tol` relative to that of the right-hand side, or after max_iter
+ * iterations (status NOT_CONVERGED). replace_residual (MIXED only, 0/1):
+ * reliable updates; at every host poll (every check_every iterations) the
+ * library checks whether r.M^-1 r has fallen 100-fold since the last
+ * replacement and, if so, replaces the float recursive residual by the FP64
+ * true residual b - K u at the next iteration (search direction kept). */
 typedef struct {
   double tol;
   int max_iter;
-  int replace_every;
+  int replace_residual;
   int check_every;
 } fftmech_solver_opts;
 
@@ -110,7 +112,7 @@ typedef struct {
   int status;               /* fftmech_status of the solve */
   int iters;                /* PCG iterations (operator applications) */
   double rel_res;           /* final recursive relative residual */
-  double true_rel_res;      /* final FP64 true relative residual (MIXED with replacement), else = rel_res */
+  double true_rel_res;      /* FP64 true relative residual of the returned iterate */
   double mean_stress[6];    /* <sigma>, Voigt */
   double mean_strain[6];    /* <eps>, Voigt (equals eps_mac up to rounding) */
   double mean_flux[3];      /* <j> of the diffusion step (HOMOGENISE) */

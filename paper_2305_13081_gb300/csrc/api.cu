@@ -132,8 +132,9 @@ int need_threads(const HostPlan& p, int nlines) {
 // budget, and enough threads for the widest FFT pass. Returns false if even
 // one row / one column does not fit.
 template <typename T>
-bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin, Shape2& s) {
+bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_total, Shape2& s) {
   const int nx = px.n, ny = py.n;
+  const size_t optin = optin_total - 1024;  // room for the kernels' static shared memory
   const int tmax = 512;
   const size_t budget = std::min<size_t>(optin, sizeof(T) == 4 ? 100 * 1024 : 110 * 1024);
   auto fits = [&](int r, size_t lim) {
@@ -152,6 +153,7 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin,
   if (smem_residual<T, 2>(nx, 1) > optin || smem_residual<T, 1>(nx, 1) > optin) return false;
   s.threads_res = std::min(tmax, std::max(256, round32(need_threads(px, 1))));
   int CW = sizeof(T) == 4 ? 8 : 4;
+  while (CW > 2 && (nx + CW - 1) / CW < 2 * nsm) CW /= 2;  // at least two strips per SM when possible
   while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) > budget || need_threads(py, CW) > tmax)) CW /= 2;
   if ((size_t)ny * CW * sizeof(cx<T>) > optin || need_threads(py, CW) > tmax) return false;
   s.cols = CW;
@@ -393,41 +395,65 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, double m0,
     return FFTMECH_OK;
   }
   const int check = std::max(1, ctx->opts.check_every);
-  const int repl = (sizeof(T) == 4) ? ctx->opts.replace_every : 0;
+  const bool reliable = (sizeof(T) == 4) && ctx->opts.replace_residual != 0;
+  double rz_rep = ctx->h_sc->rz;  // r.M^-1 r right after the last (true) residual
+  bool pending = false;
   int pi = 0;
   int it = 0;
   bool done = ctx->h_sc->done != 0;
-  while (!done && it < ctx->opts.max_iter) {
-    Vec2<T> va = v;
-    va.p_in = pbuf[pi];
-    va.p_out = pbuf[1 - pi];
-    FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, (launch_direction_f<T, D>(ctx->px.fam, op, va, px, sh, st)));
-    Vec2<T> vb = v;
-    vb.p_in = pbuf[1 - pi];
-    const bool replace = repl > 0 && ((it + 1) % repl == 0);
-    if (replace) {
-      FFTMECH_LAUNCH(FFTMECH_K_UPDATE, (launch_update_f<T, D>(ctx->px.fam, op, vb, px, sh, 1, st)));
-      FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
-      FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_TRUE, 0, ctx->partials, ctx->sc, st));
-    } else {
-      FFTMECH_LAUNCH(FFTMECH_K_UPDATE, (launch_update_f<T, D>(ctx->px.fam, op, vb, px, sh, 0, st)));
-      FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_ITER, 0, ctx->partials, ctx->sc, st));
+  for (int restart = 0;; ++restart) {
+    while (!done && it < ctx->opts.max_iter) {
+      Vec2<T> va = v;
+      va.p_in = pbuf[pi];
+      va.p_out = pbuf[1 - pi];
+      FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, (launch_direction_f<T, D>(ctx->px.fam, op, va, px, sh, st)));
+      Vec2<T> vb = v;
+      vb.p_in = pbuf[1 - pi];
+      const bool replace = pending;
+      pending = false;
+      if (replace) {
+        // reliable update: u += alpha p only, then the FP64 true residual
+        FFTMECH_LAUNCH(FFTMECH_K_UPDATE, (launch_update_f<T, D>(ctx->px.fam, op, vb, px, sh, 1, st)));
+        FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
+        FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_TRUE, 0, ctx->partials, ctx->sc, st));
+      } else {
+        FFTMECH_LAUNCH(FFTMECH_K_UPDATE, (launch_update_f<T, D>(ctx->px.fam, op, vb, px, sh, 0, st)));
+        FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_ITER, 0, ctx->partials, ctx->sc, st));
+      }
+      pi = 1 - pi;
+      ++it;
+      if (it % check == 0 || it >= ctx->opts.max_iter || replace) {
+        CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        prof_flush(ctx);
+        done = ctx->h_sc->done != 0;
+        if (replace) rz_rep = ctx->h_sc->rz_true;
+        else if (reliable && ctx->h_sc->rz < 1e-2 * rz_rep) pending = true;
+      }
     }
-    pi = 1 - pi;
-    ++it;
-    if (it % check == 0 || it >= ctx->opts.max_iter) {
-      CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      prof_flush(ctx);
-      done = ctx->h_sc->done != 0;
-    }
+    // FP64 true residual of the iterate
+    FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
+    FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_TRUENORM, 0, ctx->partials, ctx->sc, st));
+    CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    prof_flush(ctx);
+    const SolverScalars& q = *ctx->h_sc;
+    const bool gate = reliable && q.status == FFTMECH_OK && restart < 3 && q.iter < ctx->opts.max_iter &&
+                      q.rz_true > 4.0 * q.tol2 * q.rz0;
+    if (!gate) break;
+    // the float recursion met tol but the true residual did not: continue
+    // from the true residual with a fresh direction
+    const int zero = 0;
+    CK(cudaMemcpyAsync(&ctx->sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
+    FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_RESTART, 0, ctx->partials, ctx->sc, st));
+    CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    prof_flush(ctx);
+    done = ctx->h_sc->done != 0;
+    rz_rep = ctx->h_sc->rz;
+    pending = false;
   }
-  // final FP64 true residual of the returned iterate
-  FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
-  FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_TRUENORM, 0, ctx->partials, ctx->sc, st));
-  CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  prof_flush(ctx);
   const SolverScalars& f = *ctx->h_sc;
   out.iters = f.iter;
   out.status = f.done ? f.status : FFTMECH_ERR_NOT_CONVERGED;

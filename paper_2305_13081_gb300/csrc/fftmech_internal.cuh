@@ -26,8 +26,12 @@ struct SolverScalars {
 // Column-pass modes: ITER (one PCG iteration: beta, convergence), NORM
 // (<f, M^-1 f> -> rz0, no store), INIT (first residual), PLAIN (bare column
 // FFT), TRUE (iteration right after a true-residual replacement),
-// TRUENORM (<r, M^-1 r> of a true residual -> rz_true, no store).
-enum ColMode { COL_ITER = 0, COL_NORM = 1, COL_INIT = 2, COL_PLAIN = 3, COL_TRUE = 4, COL_TRUENORM = 5 };
+// TRUENORM (<r, M^-1 r> of a true residual -> rz_true, no store), RESTART
+// (true residual after a recursive convergence: restart with beta = 0).
+enum ColMode {
+  COL_ITER = 0, COL_NORM = 1, COL_INIT = 2, COL_PLAIN = 3, COL_TRUE = 4, COL_TRUENORM = 5,
+  COL_RESTART = 6
+};
 
 // Material / operator description for the 2D row kernels.
 // Vector (D = 2, elasticity): K u = grad+^T [g C_omega : sym grad+ u];

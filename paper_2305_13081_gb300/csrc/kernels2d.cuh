@@ -58,13 +58,26 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
     else if (sc->max_iter <= 0) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
     return;
   }
+  if (mode == COL_RESTART) {
+    // the true residual replaced r after a recursive convergence: restart
+    sc->rz = tot;
+    sc->rz_true = tot;
+    sc->beta = 0.0;
+    if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
+    else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
+    return;
+  }
   sc->iter += 1;
   if (mode == COL_TRUE) sc->rz_true = tot;
   const double rz_old = sc->rz;
   sc->rz = tot;
   if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; return; }
   if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; return; }
-  sc->beta = tot / rz_old;
+  double beta = tot / rz_old;
+  // a replaced residual larger than the recursive one it replaces means the
+  // float recursion had drifted: restart the direction instead of mixing
+  if (mode == COL_TRUE && beta > 1.0) beta = 0.0;
+  sc->beta = beta;
 }
 
 // ---------------------------------------------------------------- residual
@@ -425,8 +438,12 @@ static cudaError_t set_smem(K kernel, size_t bytes, int& configured) {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  if (bytes > (size_t)optin) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in limit
+  if ((long long)bytes > (long long)dyn_max) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
   if (e == cudaSuccess) configured = 1;
   return e;
 }

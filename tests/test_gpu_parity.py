@@ -59,10 +59,10 @@ def case(shape, seed, eig_mean=1e-3):
     return phase, eig, dmg
 
 
-def gpu_equilibrium(phase, eig, dmg, E, prec, tol, mat=MAT, host=False, replace_every=50):
+def gpu_equilibrium(phase, eig, dmg, E, prec, tol, mat=MAT, host=False, replace_residual=1):
     shape = phase.shape
     N = phase.size
-    ctx = fm.Context(shape, mat, prec, h=H, tol=tol, max_iter=50000, replace_every=replace_every)
+    ctx = fm.Context(shape, mat, prec, h=H, tol=tol, max_iter=50000, replace_residual=replace_residual)
     ft = ftype(prec)
     if host:
         npt = np.float64 if prec == fm.FFTMECH_FP64 else np.float32
