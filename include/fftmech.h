@@ -275,6 +275,30 @@ fftmech_status fftmech_profile_read(fftmech_ctx* ctx, int kclass, long long* lau
 fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse, void* data,
                            void* stream);
 
+/* Allocation-free variant of fftmech_fft. The paper has no counterpart: it
+ * exists for callers that must not allocate device memory themselves or
+ * through this library, e.g. code that runs while other streams must keep
+ * running (cudaMalloc and cudaFree can synchronise the whole device), code
+ * whose device memory belongs to another allocator or to a fixed budget (a
+ * framework's memory pool, where a raw cudaMalloc can fail or fragment the
+ * pool), or code that must not meet an out-of-memory error in mid-run.
+ * fftmech_fft allocates its twiddle tables on every call; this entry point
+ * keeps them in one fixed device array inside the library instead (about
+ * 103 KiB, held on every GPU that loads the library until the process exits)
+ * and calls no cudaMalloc, cudaFree or other allocating routine.
+ * Same arguments, layout and results as fftmech_fft, with each n[i] at most
+ * FFTMECH_FFT_NOALLOC_MAX_N; larger sizes return
+ * FFTMECH_ERR_UNSUPPORTED_SIZE before any work.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the array and it keeps the last call's twiddles:
+ * two calls whose transforms overlapped on the GPU would race, so calls are
+ * serialised by a process-wide lock and each returns only after its
+ * transform has completed on `stream`. */
+#define FFTMECH_FFT_NOALLOC_MAX_N 2187
+fftmech_status fftmech_fft_noalloc(int ndim, const int n[3], int precision, int inverse,
+                                   void* data, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

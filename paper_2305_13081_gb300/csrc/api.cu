@@ -9,6 +9,7 @@
 
 #include "fftmech.h"
 #include "fftmech_internal.cuh"
+#include "host_plan.cuh"
 
 using namespace fftmech;
 
@@ -18,73 +19,17 @@ constexpr int kMaxBlocks = 8192;     // upper bound on reduction partials per la
 constexpr int kPartialSlots = 16;    // doubles per block in `partials`
 
 // ---------------------------------------------------------------- plans
-struct HostPlan {
-  int n = 1;
-  int npass = 0;
-  int radix[kMaxPass] = {0};
-  int twoff[kMaxPass] = {0};
-  unsigned long long rcode = 0;
-  int rmin = 1;
-  int fam = FAM_9;
-  cx<float>* tw_f = nullptr;
-  cx<double>* tw_d = nullptr;
-};
-
-bool factor_ok(int n) {
-  if (n < 1 || n > 4096) return false;
-  int m = n;
-  while (m % 2 == 0) m /= 2;
-  while (m % 3 == 0) m /= 3;
-  return m == 1;
-}
-
-// Factor n = 2^a 3^b into passes (radix 9 and 3 for the powers of three,
-// 8, 4, 2 for the powers of two) and build the twiddle tables in FP64 on the
-// host: pass s, entry k (r - 1) + t - 1 = exp(-2 pi i k t / (Ns r)).
+// Device twiddles for a context (FP64 values from the host, also rounded to
+// float).
 cudaError_t make_plan(int n, HostPlan& p) {
-  p = HostPlan();
-  p.n = n;
-  int m = n;
-  std::vector<int> rs;
-  while (m % 9 == 0) { rs.push_back(9); m /= 9; }
-  while (m % 3 == 0) { rs.push_back(3); m /= 3; }
-  while (m % 8 == 0) { rs.push_back(8); m /= 8; }
-  while (m % 4 == 0) { rs.push_back(4); m /= 4; }
-  while (m % 2 == 0) { rs.push_back(2); m /= 2; }
-  p.npass = (int)rs.size();
-  p.rmin = 9;
-  std::vector<double> wr, wi;
-  int Ns = 1;
-  for (int s = 0; s < p.npass; ++s) {
-    const int r = rs[s];
-    p.radix[s] = r;
-    p.rcode |= (unsigned long long)r << (4 * s);
-    p.rmin = std::min(p.rmin, r);
-    p.twoff[s] = (int)wr.size();
-    const long long L = (long long)Ns * r;
-    for (int k = 0; k < Ns; ++k)
-      for (int t = 1; t < r; ++t) {
-        const long long kt = ((long long)k * t) % L;
-        const double ang = -2.0 * M_PI * (double)kt / (double)L;
-        wr.push_back(std::cos(ang));
-        wi.push_back(std::sin(ang));
-      }
-    Ns *= r;
-  }
-  if (p.npass == 0) p.rmin = n;
-  bool only9 = true, only93 = true, only842 = true;
-  for (int r : rs) {
-    only9 = only9 && r == 9;
-    only93 = only93 && (r == 9 || r == 3);
-    only842 = only842 && (r == 8 || r == 4 || r == 2);
-  }
-  p.fam = only9 ? FAM_9 : (only93 ? FAM_93 : (only842 ? FAM_842 : FAM_ALL));
-  const size_t nt = std::max<size_t>(wr.size(), 1);
-  std::vector<cx<float>> hf(nt);
+  factor_plan(n, p);
+  const int nt = std::max(twiddle_count(p), 1);
   std::vector<cx<double>> hd(nt);
-  for (size_t i = 0; i < wr.size(); ++i) {
-    hf[i].re = (float)wr[i]; hf[i].im = (float)wi[i];
-    hd[i].re = wr[i]; hd[i].im = wi[i];
+  std::vector<cx<float>> hf(nt);
+  fill_twiddles(p, hd.data());
+  for (int i = 0; i < nt; ++i) {
+    hf[i].re = (float)hd[i].re;
+    hf[i].im = (float)hd[i].im;
   }
   cudaError_t e = cudaMalloc(&p.tw_f, nt * sizeof(cx<float>));
   if (e != cudaSuccess) return e;
@@ -100,66 +45,6 @@ void free_plan(HostPlan& p) {
   if (p.tw_d) cudaFree(p.tw_d);
   p.tw_f = nullptr;
   p.tw_d = nullptr;
-}
-
-template <typename T>
-FftPlanDev<T> dev_plan(const HostPlan& p) {
-  FftPlanDev<T> d;
-  d.n = p.n;
-  d.npass = p.npass;
-  d.rcode = p.rcode;
-  if constexpr (sizeof(T) == 4) d.tw = p.tw_f; else d.tw = p.tw_d;
-  return d;
-}
-
-int round32(int x) { return ((x + 31) / 32) * 32; }
-
-int pass_batch(int r) { return r >= 8 ? 1 : (r == 4 ? 2 : (r == 3 ? 3 : 4)); }
-
-// Threads needed so that every pass of `nlines` lines of plan p fits the
-// per-thread register batch of the device FFT.
-int need_threads(const HostPlan& p, int nlines) {
-  int need = 1;
-  for (int s = 0; s < p.npass; ++s) {
-    const int bf = nlines * (p.n / p.radix[s]);
-    need = std::max(need, (bf + pass_batch(p.radix[s]) - 1) / pass_batch(p.radix[s]));
-  }
-  return need;
-}
-
-// Launch shapes for an nx x ny grid: rows per block so that the row grids
-// have about two blocks per SM while the shared memory stays within the
-// budget, and enough threads for the widest FFT pass. Returns false if even
-// one row / one column does not fit.
-template <typename T>
-bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_total, Shape2& s) {
-  const int nx = px.n, ny = py.n;
-  const size_t optin = optin_total - 1024;  // room for the kernels' static shared memory
-  const int tmax = 512;
-  const size_t budget = std::min<size_t>(optin, sizeof(T) == 4 ? 100 * 1024 : 110 * 1024);
-  auto fits = [&](int r, size_t lim) {
-    return smem_update<T, 2>(nx, r) <= lim && smem_direction<T, 2>(nx, r) <= lim &&
-           smem_update<T, 1>(nx, r) <= lim && smem_direction<T, 1>(nx, r) <= lim &&
-           need_threads(px, r + 1) <= tmax;
-  };
-  int R = std::max(1, std::min(ny, ny / (2 * nsm)));
-  while (R > 1 && !fits(R, budget)) --R;
-  if (!fits(R, optin)) return false;
-  s.rows_update = R;
-  s.rows_dir = R;
-  s.threads_update = std::min(tmax, std::max(256, round32(need_threads(px, R + 1))));
-  s.threads_dir = s.threads_update;
-  s.rows_res = 1;
-  if (smem_residual<T, 2>(nx, 1) > optin || smem_residual<T, 1>(nx, 1) > optin) return false;
-  s.threads_res = std::min(tmax, std::max(256, round32(need_threads(px, 1))));
-  int CW = sizeof(T) == 4 ? 8 : 4;
-  while (CW > 2 && (nx + CW - 1) / CW < 2 * nsm) CW /= 2;  // at least two strips per SM when possible
-  while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) > budget || need_threads(py, CW) > tmax)) CW /= 2;
-  if ((size_t)ny * CW * sizeof(cx<T>) > optin || need_threads(py, CW) > tmax) return false;
-  s.cols = CW;
-  s.threads_col = std::min(tmax, std::max(128, round32(need_threads(py, CW))));
-  s.threads_plain = s.threads_update;
-  return true;
 }
 
 }  // namespace

@@ -1,0 +1,130 @@
+// fftmech_fft_noalloc: the stand-alone Stockham transform of fftmech_fft
+// without any device allocation. fftmech_fft allocates its twiddle tables
+// with cudaMalloc on every call; this variant keeps them in one file-scope
+// device array of fixed size instead (no counterpart in the paper).
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "fftmech.h"
+#include "fftmech_internal.cuh"
+#include "host_plan.cuh"
+
+using namespace fftmech;
+
+namespace {
+
+constexpr int kMaxN = FFTMECH_FFT_NOALLOC_MAX_N;
+// Layout: x and y twiddles in double, then x and y twiddles in float, each
+// slot kMaxN entries (a plan of length n uses n - 1 of them).
+constexpr size_t kSlotD = (size_t)kMaxN * sizeof(cx<double>);
+constexpr size_t kSlotF = (size_t)kMaxN * sizeof(cx<float>);
+constexpr size_t kScratchBytes = 2 * kSlotD + 2 * kSlotF;
+constexpr int kMaxDevices = 64;
+
+}  // namespace
+
+// The scratch array. Every GPU that loads the library holds it until the
+// process exits; each call overwrites the entries it uses.
+static __device__ __align__(256) unsigned char g_fft_noalloc_scratch[kScratchBytes];
+
+namespace {
+
+std::mutex g_mu;                      // serialises calls: host buffers and the device array
+void* g_scratch_dev[kMaxDevices];     // device address of the array, per device
+cx<double> g_tw_d[2 * kMaxN];         // host staging of the twiddles (no heap use)
+cx<float> g_tw_f[2 * kMaxN];
+
+// Device address of the scratch array on `dev` (current device). The first
+// call on a device looks it up; later calls reuse it.
+cudaError_t scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_scratch_dev[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_fft_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_dev[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_dev[dev]);
+  return cudaSuccess;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t run(HostPlan& px, HostPlan& py, int inverse, void* data, int nsm, size_t optin,
+                cudaStream_t st) {
+  Shape2 sh{};
+  if (!choose_shape<T>(px, py, nsm, optin, sh)) return cudaErrorInvalidConfiguration;
+  const int nx = px.n, ny = py.n;
+  cudaError_t e = launch_rowfft_f<T>(px.fam, nx, ny, (cx<T>*)data, dev_plan<T>(px), inverse, sh, st);
+  if (e == cudaSuccess && ny > 1) {
+    Spec2<T> sp{};
+    e = launch_colpass_f<T>(py.fam, nx, ny, (cx<T>*)data, dev_plan<T>(py), sp, sh, COL_PLAIN, inverse,
+                            nullptr, nullptr, st);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" fftmech_status fftmech_fft_noalloc(int ndim, const int n[3], int precision, int inverse,
+                                              void* data, void* stream) {
+  if (!n || !data || (ndim != 1 && ndim != 2)) return FFTMECH_ERR_INVALID_ARG;
+  if (precision != FFTMECH_FP64 && precision != FFTMECH_MIXED) return FFTMECH_ERR_INVALID_ARG;
+  const int nx = n[0], ny = ndim == 2 ? n[1] : 1;
+  if (!factor_ok(nx) || !factor_ok(ny) || nx < 2) return FFTMECH_ERR_UNSUPPORTED_SIZE;
+  if (nx > kMaxN || ny > kMaxN) return FFTMECH_ERR_UNSUPPORTED_SIZE;  // beyond the fixed array
+  if (!on_device(data)) return FFTMECH_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0, nsm = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return FFTMECH_ERR_CUDA;
+  unsigned char* base = nullptr;
+  if (scratch_address(dev, &base) != cudaSuccess) return FFTMECH_ERR_CUDA;
+  HostPlan px, py;
+  factor_plan(nx, px);
+  factor_plan(ny, py);
+  const int cx_ = twiddle_count(px), cy = twiddle_count(py);
+  fill_twiddles(px, g_tw_d);
+  fill_twiddles(py, g_tw_d + kMaxN);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fp64 = precision == FFTMECH_FP64;
+  px.tw_d = reinterpret_cast<cx<double>*>(base);
+  py.tw_d = reinterpret_cast<cx<double>*>(base + kSlotD);
+  px.tw_f = reinterpret_cast<cx<float>*>(base + 2 * kSlotD);
+  py.tw_f = reinterpret_cast<cx<float>*>(base + 2 * kSlotD + kSlotF);
+  // Every twiddle a launch reads is written here first, so nothing in the
+  // array has to start at zero; entries past n - 1 are never read.
+  cudaError_t e = cudaSuccess;
+  if (fp64) {
+    if (cx_) e = cudaMemcpyAsync(px.tw_d, g_tw_d, cx_ * sizeof(cx<double>), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && cy)
+      e = cudaMemcpyAsync(py.tw_d, g_tw_d + kMaxN, cy * sizeof(cx<double>), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = run<double>(px, py, inverse, data, nsm, (size_t)optin, st);
+  } else {
+    for (int i = 0; i < cx_; ++i) { g_tw_f[i].re = (float)g_tw_d[i].re; g_tw_f[i].im = (float)g_tw_d[i].im; }
+    for (int i = 0; i < cy; ++i) {
+      g_tw_f[kMaxN + i].re = (float)g_tw_d[kMaxN + i].re;
+      g_tw_f[kMaxN + i].im = (float)g_tw_d[kMaxN + i].im;
+    }
+    if (cx_) e = cudaMemcpyAsync(px.tw_f, g_tw_f, cx_ * sizeof(cx<float>), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && cy)
+      e = cudaMemcpyAsync(py.tw_f, g_tw_f + kMaxN, cy * sizeof(cx<float>), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = run<float>(px, py, inverse, data, nsm, (size_t)optin, st);
+  }
+  if (e == cudaErrorInvalidConfiguration) return FFTMECH_ERR_UNSUPPORTED_SIZE;
+  // the transform completes before the lock is released, so the next call
+  // cannot overwrite twiddles that are still being read
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? FFTMECH_OK : FFTMECH_ERR_CUDA;
+}

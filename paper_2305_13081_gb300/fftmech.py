@@ -125,6 +125,7 @@ def load_library(path=LIB_PATH):
         "fftmech_staggered_step": (i, [vp, P(fftmech_state), P(fftmech_step_params),
                                        P(fftmech_solve_info)]),
         "fftmech_fft": (i, [i, P(i), i, i, vp, vp]),
+        "fftmech_fft_noalloc": (i, [i, P(i), i, i, vp, vp]),
         "fftmech_profile_enable": (i, [vp, i]),
         "fftmech_profile_read": (i, [vp, i, P(ctypes.c_longlong), P(d)]),
     }
@@ -239,6 +240,19 @@ def fftmech_staggered_step(ctx, state, params, infos=None):
 def fftmech_fft(ndim, n, precision, inverse, data, stream=None):
     nn = c_int3(*(list(n) + [1, 1, 1])[:3])
     rc = load_library().fftmech_fft(int(ndim), nn, int(precision), int(inverse), ptr(data), stream)
+    _check(rc)
+    return rc
+
+
+FFTMECH_FFT_NOALLOC_MAX_N = 2187
+
+
+def fftmech_fft_noalloc(ndim, n, precision, inverse, data, stream=None):
+    """Same transform as fftmech_fft without any device allocation (twiddles
+    in a fixed array inside the library; sizes up to FFTMECH_FFT_NOALLOC_MAX_N)."""
+    nn = c_int3(*(list(n) + [1, 1, 1])[:3])
+    rc = load_library().fftmech_fft_noalloc(int(ndim), nn, int(precision), int(inverse), ptr(data),
+                                            stream)
     _check(rc)
     return rc
 
