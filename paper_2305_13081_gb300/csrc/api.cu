@@ -80,6 +80,8 @@ struct fftmech_ctx {
   void* p[2] = {nullptr, nullptr};
   void* S = nullptr;
   void* g = nullptr;
+  float* uh = nullptr;  // MIXED iterate, high part (2 N)
+  float* ul = nullptr;  // MIXED iterate, low part (2 N)
   double* phi = nullptr;
   double* Hd = nullptr;
   double* cn = nullptr;
@@ -249,6 +251,10 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, double m0,
   T* pbuf[2] = {(T*)ctx->p[0], (T*)ctx->p[1]};
   Vec2<T> v;
   v.u = u;
+  v.uh = ctx->uh;
+  v.ul = ctx->ul;
+  const long long nU = (long long)D * ctx->N;
+  if (sizeof(T) == 4) CK(launch_df_split(nU, u, ctx->uh, ctx->ul, st));
   v.r = (T*)ctx->r;
   v.p_in = pbuf[0];
   v.p_out = pbuf[1];
@@ -338,6 +344,9 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, double m0,
     done = ctx->h_sc->done != 0;
     rz_rep = ctx->h_sc->rz;
     pending = false;
+  }
+  if (sizeof(T) == 4) {
+    CK(launch_df_merge(nU, ctx->uh, ctx->ul, u, st));
   }
   const SolverScalars& f = *ctx->h_sc;
   out.iters = f.iter;
@@ -632,6 +641,8 @@ fftmech_status fftmech_create(fftmech_ctx** out, const fftmech_grid* grid,
   alloc(&ctx->p[1], 2 * N * es);
   alloc(&ctx->S, 2 * N * es);
   alloc(&ctx->g, N * es);
+  alloc((void**)&ctx->uh, 2 * N * sizeof(float));
+  alloc((void**)&ctx->ul, 2 * N * sizeof(float));
   alloc((void**)&ctx->phi, N * 8);
   alloc((void**)&ctx->Hd, N * 8);
   alloc((void**)&ctx->cn, N * 8);
@@ -655,7 +666,7 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
   if (!ctx) return FFTMECH_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  void* bufs[] = {ctx->r, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->phi, ctx->Hd, ctx->cn,
+  void* bufs[] = {ctx->r, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd, ctx->cn,
                   ctx->lamx, ctx->lamy, ctx->partials, ctx->results, ctx->sc};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -923,8 +934,8 @@ fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse,
   const bool fp64 = precision == FFTMECH_FP64;
   fftmech_status rc = FFTMECH_OK;
   Shape2 sh{};
-  const bool shp = fp64 ? choose_shape<double>(px, py, prop.multiProcessorCount, prop.sharedMemPerBlockOptin, sh)
-                        : choose_shape<float>(px, py, prop.multiProcessorCount, prop.sharedMemPerBlockOptin, sh);
+  const bool shp = fp64 ? choose_shape_fft<double>(px, py, prop.multiProcessorCount, prop.sharedMemPerBlockOptin, sh)
+                        : choose_shape_fft<float>(px, py, prop.multiProcessorCount, prop.sharedMemPerBlockOptin, sh);
   if (!shp) {
     rc = FFTMECH_ERR_UNSUPPORTED_SIZE;
   } else {

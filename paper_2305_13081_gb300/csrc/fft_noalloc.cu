@@ -62,7 +62,7 @@ template <typename T>
 cudaError_t run(HostPlan& px, HostPlan& py, int inverse, void* data, int nsm, size_t optin,
                 cudaStream_t st) {
   Shape2 sh{};
-  if (!choose_shape<T>(px, py, nsm, optin, sh)) return cudaErrorInvalidConfiguration;
+  if (!choose_shape_fft<T>(px, py, nsm, optin, sh)) return cudaErrorInvalidConfiguration;
   const int nx = px.n, ny = py.n;
   cudaError_t e = launch_rowfft_f<T>(px.fam, nx, ny, (cx<T>*)data, dev_plan<T>(px), inverse, sh, st);
   if (e == cudaSuccess && ny > 1) {

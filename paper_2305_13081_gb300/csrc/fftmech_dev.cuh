@@ -123,6 +123,108 @@ __device__ __forceinline__ void dft(cx<T>* v) {
   else dft9<T, S>(v);
 }
 
+// ---------------------------------------------------------------- index helpers
+// Division by a block-invariant divisor 1 <= d < 2^16 for 0 <= x < 2^16:
+// q = floor(x * m / 2^32) with m = ceil(2^32 / d). Writing m = 2^32/d + e
+// (0 <= e < 1), x m / 2^32 = x/d + x e / 2^32 < x/d + 2^-16, while the
+// fractional part of x/d is at most 1 - 1/d <= 1 - 2^-16, so the floor is
+// exact. Integer-only (one multiply-high per division).
+struct FastDiv {
+  unsigned int m;
+  int d;
+  __device__ __forceinline__ explicit FastDiv(int d_) : m(d_ > 1 ? 0xFFFFFFFFu / (unsigned)d_ + 1u : 0u), d(d_) {}
+  __device__ __forceinline__ int div(int x) const { return d > 1 ? (int)__umulhi((unsigned)x, m) : x; }
+};
+
+// ---------------------------------------------------------------- double-float
+// (hi, lo) += a * p for a = ah + al (a double split into two floats), p a
+// float: the product's rounding error comes from one FMA (Dekker), the sum's
+// from TwoSum (Knuth), and the result is renormalised (FastTwoSum).
+__device__ __forceinline__ void df_axpy(float& hi, float& lo, float ah, float al, float p) {
+  const float prod = ah * p;
+  const float perr = fmaf(ah, p, -prod);
+  const float dlo = fmaf(al, p, perr);
+  const float s = hi + prod;
+  const float bb = s - hi;
+  float e = (hi - (s - bb)) + (prod - bb);
+  e += lo + dlo;
+  const float h2 = s + e;
+  lo = e - (h2 - s);
+  hi = h2;
+}
+
+// ---------------------------------------------------------------- staged copies
+// Contiguous global -> shared copy with U loads in flight per thread.
+template <int U, typename E>
+__device__ __forceinline__ void g2s(E* __restrict__ dst, const E* __restrict__ src, int n) {
+  const int bd = blockDim.x;
+  for (int i = threadIdx.x; i < n; i += U * bd) {
+    E v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (i + k * bd < n) v[k] = src[i + k * bd];
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (i + k * bd < n) dst[i + k * bd] = v[k];
+  }
+}
+
+// Rows ys .. ys + W - 1 (periodic in ny) of a [ny][nx] field into dst[W][nx].
+template <int U, typename E>
+__device__ __forceinline__ void g2s_rows(E* dst, const E* __restrict__ src, int ys, int W, int nx,
+                                         int ny) {
+  int y = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+  int done = 0;
+  while (done < W) {
+    const int run = min(W - done, ny - y);
+    g2s<U>(dst + (size_t)done * nx, src + (size_t)y * nx, run * nx);
+    done += run;
+    y = 0;
+  }
+}
+
+// Contiguous shared -> global copy.
+template <typename E>
+__device__ __forceinline__ void s2g(E* __restrict__ dst, const E* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// u[i] += a * p[i] for a double iterate in global memory and a direction in
+// shared memory, U read-modify-writes in flight per thread.
+template <int U, typename T>
+__device__ __forceinline__ void axpy_g(double* __restrict__ u, const T* __restrict__ p, double a, int n) {
+  const int bd = blockDim.x;
+  for (int i = threadIdx.x; i < n; i += U * bd) {
+    double v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (i + k * bd < n) v[k] = u[i + k * bd];
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (i + k * bd < n) u[i + k * bd] = v[k] + a * (double)p[i + k * bd];
+  }
+}
+
+// (uh, ul)[i] += a * p[i] in double-float, U updates in flight per thread.
+template <int U>
+__device__ __forceinline__ void df_axpy_g(float* __restrict__ uh, float* __restrict__ ul,
+                                          const float* __restrict__ p, float ah, float al, int n) {
+  const int bd = blockDim.x;
+  for (int i = threadIdx.x; i < n; i += U * bd) {
+    float h[U], l[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (i + k * bd < n) { h[k] = uh[i + k * bd]; l[k] = ul[i + k * bd]; }
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (i + k * bd < n) {
+        df_axpy(h[k], l[k], ah, al, p[i + k * bd]);
+        uh[i + k * bd] = h[k];
+        ul[i + k * bd] = l[k];
+      }
+  }
+}
+
 // ---------------------------------------------------------------- plans
 constexpr int kMaxPass = 12;
 
@@ -155,27 +257,29 @@ __device__ __forceinline__ void stockham_pass(cx<T>* buf, int n, int Ns, const c
   const int nb = n / R;
   const int total = nb * nlines;
   cx<T> v[BM][R];
+  int lj[BM];
+  const FastDiv dl(lines_fast ? nlines : nb);
 #pragma unroll
   for (int b = 0; b < BM; ++b) {
     const int idx = threadIdx.x + b * blockDim.x;
     if (idx < total) {
       int line, j;
-      if (lines_fast) { j = idx / nlines; line = idx - j * nlines; }
-      else { line = idx / nb; j = idx - line * nb; }
+      if (lines_fast) { j = dl.div(idx); line = idx - j * nlines; }
+      else { line = dl.div(idx); j = idx - line * nb; }
+      lj[b] = line * 65536 + j;
       const cx<T>* src = buf + (size_t)line * ls;
 #pragma unroll
       for (int t = 0; t < R; ++t) v[b][t] = src[(j + t * nb) * is];
     }
   }
   __syncthreads();
+  const FastDiv dn(Ns);
 #pragma unroll
   for (int b = 0; b < BM; ++b) {
     const int idx = threadIdx.x + b * blockDim.x;
     if (idx < total) {
-      int line, j;
-      if (lines_fast) { j = idx / nlines; line = idx - j * nlines; }
-      else { line = idx / nb; j = idx - line * nb; }
-      const int q = j / Ns;
+      const int line = lj[b] >> 16, j = lj[b] & 0xFFFF;
+      const int q = dn.div(j);
       const int k = j - q * Ns;
       if (Ns > 1) {
         const cx<T>* w = tw + k * (R - 1);

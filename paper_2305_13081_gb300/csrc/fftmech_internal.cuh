@@ -60,9 +60,14 @@ struct Op2 {
   double src_scale;
 };
 
+// The iterate: double in FP64; in MIXED an unevaluated float pair
+// u = uh + ul (double-float arithmetic: Knuth's TwoSum, Dekker's product
+// split via FMA) so the hot loop needs no FP64 instruction.
 template <typename T>
 struct Vec2 {
-  double* u;      // iterate, D x N
+  double* u;      // iterate, D x N (FP64 path)
+  float* uh;      // MIXED: high part, D x N
+  float* ul;      // MIXED: low part, D x N
   T* r;           // residual, D x N
   const T* p_in;  // previous direction
   T* p_out;       // new direction
@@ -187,25 +192,54 @@ cudaError_t launch_set_masked(long long N, const uint8_t* mask, double value, do
                               cudaStream_t st);
 template <typename T>
 cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t st);
+cudaError_t launch_df_split(long long n, const double* u, float* uh, float* ul, cudaStream_t st);
+cudaError_t launch_df_merge(long long n, const float* uh, const float* ul, double* u, cudaStream_t st);
 
-// Shared-memory footprints of the row kernels (bytes) for R rows of nx:
-// residual: [max(D (R+2) doubles, 2 R T)] + [3 (R+1) doubles] per column;
-// update: [max(D (R+2), 2 R) T] + [3 (R+1) T]; direction: [2 (R+1) T] +
-// [D (R+1) T].
-inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+// Shared-memory layouts of the row kernels for tiles of R rows of nx
+// (byte offsets, each region 16-byte aligned), used by host and device.
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// update: [P: D (R+2) rows, reused by the packed row spectrum (R complex
+// rows)] [SG: 3 (R+1) rows] [RS: old residual, D R rows] [MG: g or c0 field,
+// R+1 rows] [PH: phase bytes, R+1 rows] [MK: mask bytes, R rows]
+struct UpdLayout {
+  size_t a, b, c, d, e, f, total;
+  __host__ __device__ UpdLayout(int nx, int R, int es, int D) {
+    const size_t rowsA = (size_t)(D * (R + 2) > 2 * R ? D * (R + 2) : 2 * R);
+    a = 0;
+    b = a + align16(rowsA * nx * es);
+    c = b + align16((size_t)3 * (R + 1) * nx * es);
+    d = c + align16((size_t)D * R * nx * es);
+    e = d + align16((size_t)(R + 1) * nx * es);
+    f = e + align16((size_t)(R + 1) * nx);
+    total = f + align16((size_t)R * nx);
+  }
+};
+
+// direction: [F: R+1 complex rows] [P: D (R+1) rows] [MG: R rows]
+// [PH: R byte rows] [MK: R+1 byte rows]
+struct DirLayout {
+  size_t a, b, c, d, e, total;
+  __host__ __device__ DirLayout(int nx, int R, int es, int D) {
+    a = 0;
+    b = a + align16((size_t)2 * (R + 1) * nx * es);
+    c = b + align16((size_t)D * (R + 1) * nx * es);
+    d = c + align16((size_t)R * nx * es);
+    e = d + align16((size_t)R * nx);
+    total = e + align16((size_t)(R + 1) * nx);
+  }
+};
+
+// residual (FP64 stencil): [P: max(D (R+2) doubles, 2 R T) per column]
+// [SG: 3 (R+1) doubles per column]
 template <typename T, int D>
 inline size_t smem_residual(int nx, int R) {
   const size_t a = (size_t)D * (R + 2) * sizeof(double), b = (size_t)2 * R * sizeof(T);
   return align16((a > b ? a : b) * nx) + (size_t)3 * (R + 1) * nx * sizeof(double);
 }
 template <typename T, int D>
-inline size_t smem_update(int nx, int R) {
-  const size_t a = (size_t)(D * (R + 2) > 2 * R ? D * (R + 2) : 2 * R);
-  return align16(a * nx * sizeof(T)) + (size_t)3 * (R + 1) * nx * sizeof(T);
-}
+inline size_t smem_update(int nx, int R) { return UpdLayout(nx, R, (int)sizeof(T), D).total; }
 template <typename T, int D>
-inline size_t smem_direction(int nx, int R) {
-  return align16((size_t)2 * (R + 1) * nx * sizeof(T)) + (size_t)D * (R + 1) * nx * sizeof(T);
-}
+inline size_t smem_direction(int nx, int R) { return DirLayout(nx, R, (int)sizeof(T), D).total; }
 
 }  // namespace fftmech

@@ -147,4 +147,31 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   return true;
 }
 
+// Launch shapes for the bare transform (row FFT + column FFT only), which
+// needs far less shared memory than the solver's row kernels.
+template <typename T>
+bool choose_shape_fft(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_total, Shape2& s) {
+  const int nx = px.n, ny = py.n;
+  const int tmax = 512;
+  const size_t optin = optin_total - 1024;
+  int R = std::max(1, std::min(ny, ny / (2 * nsm)));
+  auto fits = [&](int r) {
+    return (size_t)r * nx * sizeof(cx<T>) <= optin && need_threads(px, r) <= tmax;
+  };
+  while (R > 1 && !fits(R)) --R;
+  if (!fits(R)) return false;
+  s.rows_update = s.rows_dir = R;
+  s.threads_update = s.threads_dir = s.threads_plain =
+      std::min(tmax, std::max(128, round32(need_threads(px, R))));
+  s.rows_res = 1;
+  s.threads_res = s.threads_update;
+  int CW = sizeof(T) == 4 ? 8 : 4;
+  while (CW > 2 && (nx + CW - 1) / CW < 2 * nsm) CW /= 2;
+  while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) > optin || need_threads(py, CW) > tmax)) CW /= 2;
+  if ((size_t)ny * CW * sizeof(cx<T>) > optin || need_threads(py, CW) > tmax) return false;
+  s.cols = CW;
+  s.threads_col = std::min(tmax, std::max(128, round32(need_threads(py, CW))));
+  return true;
+}
+
 }  // namespace fftmech

@@ -105,7 +105,9 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op2<T> op, Vec2<T> v, FftPlanDev<T>
     const bool keep = (D == 1) && op.mask && op.mask[gi];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      double val = v.u[c * N + gi];
+      double val;
+      if constexpr (sizeof(T) == 4) val = (double)v.uh[c * N + gi] + (double)v.ul[c * N + gi];
+      else val = v.u[c * N + gi];
       if (zero_u && !keep) val = 0.0;
       P[(size_t)c * W * nx + i] = val;
     }
@@ -176,8 +178,10 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op2<T> op, Vec2<T> v, FftPlanDev<T>
 }
 
 // ---------------------------------------------------------------- update
-// u += alpha p (FP64 iterate); r -= alpha K p; S = row-FFT(r). Shared
-// memory: [max(D (R+2), 2 R) T per column] + [3 (R+1) T per column].
+// u += alpha p (FP64 iterate); r -= alpha K p; S = row-FFT(r). Every input
+// of the tile (direction rows with halos, old residual, phase, degradation or
+// reaction field, mask) is staged into shared memory first with many loads in
+// flight; the stencil then runs out of shared memory (layout UpdLayout).
 template <typename T, int D, int FX>
 __global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int u_only) {
   if (done_flag(v.sc)) return;
@@ -188,100 +192,129 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> p
   const size_t N = (size_t)nx * ny;
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const size_t t0 = (size_t)y0 * nx;
   if (u_only) {
-    for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
-      const size_t gi = (size_t)y0 * nx + i;
-#pragma unroll
-      for (int c = 0; c < D; ++c) v.u[c * N + gi] += alpha * (double)v.p_in[c * N + gi];
+    // reliable-update iteration: only the iterate moves (direction from global)
+    for (int c = 0; c < D; ++c) {
+      const T* p = v.p_in + c * N + t0;
+      if constexpr (sizeof(T) == 4) {
+        const float ah = (float)alpha, al = (float)(alpha - (double)ah);
+        float* uh = v.uh + c * N + t0;
+        float* ul = v.ul + c * N + t0;
+        for (int i = tid; i < rows * nx; i += bd) {
+          float h = uh[i], l = ul[i];
+          df_axpy(h, l, ah, al, (float)p[i]);
+          uh[i] = h;
+          ul[i] = l;
+        }
+      } else {
+        double* u = v.u + c * N + t0;
+        for (int i = tid; i < rows * nx; i += bd) u[i] += alpha * (double)p[i];
+      }
     }
     return;
   }
+  const UpdLayout L(nx, R, (int)sizeof(T), D);
+  T* P = reinterpret_cast<T*>(smem + L.a);
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem + L.a);
+  T* SG = reinterpret_cast<T*>(smem + L.b);
+  T* RS = reinterpret_cast<T*>(smem + L.c);
+  T* MG = reinterpret_cast<T*>(smem + L.d);
+  uint8_t* PH = smem + L.e;
+  uint8_t* MK = smem + L.f;
   const int W = rows + 2;
-  const size_t reg0 = (size_t)max(D * (R + 2), 2 * R) * nx * sizeof(T);
-  T* P = reinterpret_cast<T*>(smem);
-  T* SG = reinterpret_cast<T*>(smem + ((reg0 + 15) & ~size_t(15)));
-  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   const int SR = (rows + 1) * nx;
-  const T ih = (T)(1.0 / op.h);
-
-  for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
-    const int yy = i / nx, x = i - yy * nx;
-    const size_t gi = (size_t)wrap_y(y0 - 1 + yy, ny) * nx + x;
+  const T* matg = (D == 2) ? op.g : op.c0f;
+  // stage the tile
 #pragma unroll
-    for (int c = 0; c < D; ++c) P[(size_t)c * W * nx + i] = v.p_in[c * N + gi];
-  }
+  for (int c = 0; c < D; ++c) g2s_rows<8>(P + (size_t)c * W * nx, v.p_in + c * N, y0 - 1, W, nx, ny);
+#pragma unroll
+  for (int c = 0; c < D; ++c) g2s<8>(RS + (size_t)c * rows * nx, v.r + c * N + t0, rows * nx);
+  if (matg) g2s_rows<8>(MG, matg, y0 - 1, rows + 1, nx, ny);
+  g2s_rows<8>(PH, op.phase, y0 - 1, rows + 1, nx, ny);
+  const bool masked = (D == 1) && op.mask;
+  if (masked) g2s<8>(MK, op.mask + t0, rows * nx);
   __syncthreads();
+  // iterate update on the tile rows (rows 1 .. rows of P)
+  if constexpr (sizeof(T) == 4) {
+    const float ah = (float)alpha, al = (float)(alpha - (double)ah);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      df_axpy_g<8>(v.uh + c * N + t0, v.ul + c * N + t0, P + (size_t)c * W * nx + nx, ah, al, rows * nx);
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c) axpy_g<8>(v.u + c * N + t0, P + (size_t)c * W * nx + nx, alpha, rows * nx);
+  }
+  // stresses (D = 2) or fluxes (D = 1) at rows y0 - 1 .. y0 + rows - 1
+  const T ih = (T)(1.0 / op.h);
   const T lam0 = (T)op.lam[0], lam1 = (T)op.lam[1], mu0 = (T)op.mu[0], mu1 = (T)op.mu[1];
   const T kap0 = (T)op.kap[0], kap1 = (T)op.kap[1];
-  for (int i = threadIdx.x; i < SR; i += blockDim.x) {
-    const int yy = i / nx, x = i - yy * nx;
-    const int xp = (x + 1 == nx) ? 0 : x + 1;
-    const size_t gi = (size_t)wrap_y(y0 - 1 + yy, ny) * nx + x;
-    const bool sol = op.phase[gi] != 0;
-    const int c0 = yy * nx + x;
-    if constexpr (D == 2) {
-      const T* Ux = P;
-      const T* Uy = P + (size_t)W * nx;
-      const T exx = (Ux[yy * nx + xp] - Ux[c0]) * ih;
-      const T eyy = (Uy[c0 + nx] - Uy[c0]) * ih;
-      const T exy = T(0.5) * ((Ux[c0 + nx] - Ux[c0]) + (Uy[yy * nx + xp] - Uy[c0])) * ih;
-      const T gg = op.g ? op.g[gi] : T(1);
-      const T lam = gg * (sol ? lam1 : lam0), mu = gg * (sol ? mu1 : mu0);
-      const T tr = exx + eyy;
-      SG[i] = lam * tr + T(2) * mu * exx;
-      SG[SR + i] = lam * tr + T(2) * mu * eyy;
-      SG[2 * SR + i] = T(2) * mu * exy;
-      if (yy >= 1) {
-        v.u[gi] += alpha * (double)Ux[c0];
-        v.u[N + gi] += alpha * (double)Uy[c0];
+  const T c0c = (T)op.c0c;
+  for (int yy = 0; yy <= rows; ++yy) {
+    for (int x = tid; x < nx; x += bd) {
+      const int xp = (x + 1 == nx) ? 0 : x + 1;
+      const int i = yy * nx + x;
+      const bool sol = PH[i] != 0;
+      if constexpr (D == 2) {
+        const T* Ux = P;
+        const T* Uy = P + (size_t)W * nx;
+        const T exx = (Ux[yy * nx + xp] - Ux[i]) * ih;
+        const T eyy = (Uy[i + nx] - Uy[i]) * ih;
+        const T exy = T(0.5) * ((Ux[i + nx] - Ux[i]) + (Uy[yy * nx + xp] - Uy[i])) * ih;
+        const T gg = matg ? MG[i] : T(1);
+        const T lam = gg * (sol ? lam1 : lam0), mu = gg * (sol ? mu1 : mu0);
+        const T tr = exx + eyy;
+        SG[i] = lam * tr + T(2) * mu * exx;
+        SG[SR + i] = lam * tr + T(2) * mu * eyy;
+        SG[2 * SR + i] = T(2) * mu * exy;
+      } else {
+        const T p = P[i];
+        const T kap = sol ? kap1 : kap0;
+        SG[i] = kap * (P[yy * nx + xp] - p) * ih;
+        SG[SR + i] = kap * (P[i + nx] - p) * ih;
+        SG[2 * SR + i] = (c0c + (matg ? MG[i] : T(0))) * p;
       }
-    } else {
-      const T p = P[c0];
-      const T kap = sol ? kap1 : kap0;
-      SG[i] = kap * (P[yy * nx + xp] - p) * ih;
-      SG[SR + i] = kap * (P[c0 + nx] - p) * ih;
-      const T c0v = (T)op.c0c + (op.c0f ? op.c0f[gi] : T(0));
-      SG[2 * SR + i] = c0v * p;
-      if (yy >= 1) v.u[gi] += alpha * (double)p;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
-    const int yr = i / nx, x = i - yr * nx;
-    const int yy = yr + 1;
-    const int xm = (x == 0) ? nx - 1 : x - 1;
-    const size_t gi = (size_t)(y0 + yr) * nx + x;
-    const int c = yy * nx + x;
-    T r0, r1 = T(0);
-    if constexpr (D == 2) {
-      const T* Sxx = SG;
-      const T* Syy = SG + SR;
-      const T* Sxy = SG + 2 * SR;
-      const T q0 = ((Sxx[yy * nx + xm] - Sxx[c]) + (Sxy[c - nx] - Sxy[c])) * ih;
-      const T q1 = ((Sxy[yy * nx + xm] - Sxy[c]) + (Syy[c - nx] - Syy[c])) * ih;
-      r0 = v.r[gi] - a * q0;
-      r1 = v.r[N + gi] - a * q1;
-      v.r[gi] = r0;
-      v.r[N + gi] = r1;
-    } else {
-      const T* Jx = SG;
-      const T* Jy = SG + SR;
-      T q0 = SG[2 * SR + c] + ((Jx[yy * nx + xm] - Jx[c]) + (Jy[c - nx] - Jy[c])) * ih;
-      if (op.mask && op.mask[gi]) q0 = T(0);
-      r0 = v.r[gi] - a * q0;
-      v.r[gi] = r0;
+  // K p, residual update and packing (F reuses the direction rows)
+  for (int yr = 0; yr < rows; ++yr) {
+    for (int x = tid; x < nx; x += bd) {
+      const int yy = yr + 1;
+      const int xm = (x == 0) ? nx - 1 : x - 1;
+      const int c = yy * nx + x;
+      const int j = yr * nx + x;
+      T r0, r1 = T(0);
+      if constexpr (D == 2) {
+        const T* Sxx = SG;
+        const T* Syy = SG + SR;
+        const T* Sxy = SG + 2 * SR;
+        const T q0 = ((Sxx[yy * nx + xm] - Sxx[c]) + (Sxy[c - nx] - Sxy[c])) * ih;
+        const T q1 = ((Sxy[yy * nx + xm] - Sxy[c]) + (Syy[c - nx] - Syy[c])) * ih;
+        r0 = RS[j] - a * q0;
+        r1 = RS[rows * nx + j] - a * q1;
+        v.r[t0 + j] = r0;
+        v.r[N + t0 + j] = r1;
+      } else {
+        const T* Jx = SG;
+        const T* Jy = SG + SR;
+        T q0 = SG[2 * SR + c] + ((Jx[yy * nx + xm] - Jx[c]) + (Jy[c - nx] - Jy[c])) * ih;
+        if (masked && MK[j]) q0 = T(0);
+        r0 = RS[j] - a * q0;
+        v.r[t0 + j] = r0;
+      }
+      F[j] = mk(r0, r1);
     }
-    F[i] = mk(r0, r1);
   }
   __syncthreads();
   fft_lines<T, -1, FX>(F, px, rows, nx, 1, false);
-  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) v.S[(size_t)y0 * nx + i] = F[i];
+  s2g(v.S + t0, F, rows * nx);
 }
 
 // ---------------------------------------------------------------- direction
 // z = row-IFFT(S) (rows y0 .. y0 + rows, one halo row), p = z + beta p_old,
-// <p, K p> = sum of the energy density over the tile. Shared memory:
-// [2 (R+1) T per column] + [D (R+1) T per column].
+// <p, K p> = sum of the energy density over the tile (layout DirLayout).
 template <typename T, int D, int FX>
 __global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R) {
   if (done_flag(v.sc)) return;
@@ -294,60 +327,76 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
   const int W = rows + 1;
-  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
-  T* P = reinterpret_cast<T*>(smem + (((size_t)2 * (R + 1) * nx * sizeof(T) + 15) & ~size_t(15)));
-  for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
-    const int yy = i / nx, x = i - yy * nx;
-    F[i] = v.S[(size_t)wrap_y(y0 + yy, ny) * nx + x];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const size_t t0 = (size_t)y0 * nx;
+  const DirLayout L(nx, R, (int)sizeof(T), D);
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem + L.a);
+  T* P = reinterpret_cast<T*>(smem + L.b);
+  T* MG = reinterpret_cast<T*>(smem + L.c);
+  uint8_t* PH = smem + L.d;
+  uint8_t* MK = smem + L.e;
+  const T* matg = (D == 2) ? op.g : op.c0f;
+  const bool masked = (D == 1) && op.mask;
+  g2s_rows<8>(F, v.S, y0, W, nx, ny);
+  if (beta != 0.0) {  // the first iteration has p = z
+#pragma unroll
+    for (int c = 0; c < D; ++c) g2s_rows<8>(P + (size_t)c * W * nx, v.p_in + c * N, y0, W, nx, ny);
   }
+  if (matg) g2s<8>(MG, matg + t0, rows * nx);
+  g2s<8>(PH, op.phase + t0, rows * nx);
+  if (masked) g2s_rows<8>(MK, op.mask, y0, W, nx, ny);
   __syncthreads();
   fft_lines<T, 1, FX>(F, px, W, nx, 1, false);
-  for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
-    const int yy = i / nx, x = i - yy * nx;
-    const size_t gi = (size_t)wrap_y(y0 + yy, ny) * nx + x;
-    const cx<T> z = F[i];
-    T p0 = z.re;
-    if constexpr (D == 1) {
-      if (op.mask && op.mask[gi]) p0 = T(0);
-    }
-    if (beta != 0.0) p0 += b * v.p_in[gi];
-    P[i] = p0;
-    if (yy < rows) v.p_out[gi] = p0;
-    if constexpr (D == 2) {
-      T p1 = z.im;
-      if (beta != 0.0) p1 += b * v.p_in[N + gi];
-      P[(size_t)W * nx + i] = p1;
-      if (yy < rows) v.p_out[N + gi] = p1;
+  const bool with_old = beta != 0.0;  // hoisted: no FP64 compare in the loop
+  for (int yy = 0; yy < W; ++yy) {
+    for (int x = tid; x < nx; x += bd) {
+      const int i = yy * nx + x;
+      const cx<T> z = F[i];
+      T p0 = z.re;
+      if (masked && MK[i]) p0 = T(0);
+      if (with_old) p0 += b * P[i];
+      P[i] = p0;
+      if (yy < rows) v.p_out[t0 + i] = p0;
+      if constexpr (D == 2) {
+        T p1 = z.im;
+        if (with_old) p1 += b * P[(size_t)W * nx + i];
+        P[(size_t)W * nx + i] = p1;
+        if (yy < rows) v.p_out[N + t0 + i] = p1;
+      }
     }
   }
   __syncthreads();
   const T ih = (T)(1.0 / op.h);
   const T lam0 = (T)op.lam[0], lam1 = (T)op.lam[1], mu0 = (T)op.mu[0], mu1 = (T)op.mu[1];
   const T kap0 = (T)op.kap[0], kap1 = (T)op.kap[1];
+  const T c0c = (T)op.c0c;
   double acc[1] = {0.0};
-  for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
-    const int yy = i / nx, x = i - yy * nx;
-    const int xp = (x + 1 == nx) ? 0 : x + 1;
-    const size_t gi = (size_t)(y0 + yy) * nx + x;
-    const bool sol = op.phase[gi] != 0;
-    T w;
-    if constexpr (D == 2) {
-      const T* Ux = P;
-      const T* Uy = P + (size_t)W * nx;
-      const T exx = (Ux[yy * nx + xp] - Ux[i]) * ih;
-      const T eyy = (Uy[i + nx] - Uy[i]) * ih;
-      const T exy = T(0.5) * ((Ux[i + nx] - Ux[i]) + (Uy[yy * nx + xp] - Uy[i])) * ih;
-      const T gg = op.g ? op.g[gi] : T(1);
-      const T lam = sol ? lam1 : lam0, mu = sol ? mu1 : mu0;
-      const T tr = exx + eyy;
-      w = gg * (lam * tr * tr + T(2) * mu * (exx * exx + eyy * eyy + T(2) * exy * exy));
-    } else {
-      const T p = P[i];
-      const T gx = (P[yy * nx + xp] - p) * ih, gy = (P[i + nx] - p) * ih;
-      const T c0v = (T)op.c0c + (op.c0f ? op.c0f[gi] : T(0));
-      w = c0v * p * p + (sol ? kap1 : kap0) * (gx * gx + gy * gy);
+  for (int yy = 0; yy < rows; ++yy) {
+    T part = T(0);
+    for (int x = tid; x < nx; x += bd) {
+      const int xp = (x + 1 == nx) ? 0 : x + 1;
+      const int i = yy * nx + x;
+      const bool sol = PH[i] != 0;
+      T w;
+      if constexpr (D == 2) {
+        const T* Ux = P;
+        const T* Uy = P + (size_t)W * nx;
+        const T exx = (Ux[yy * nx + xp] - Ux[i]) * ih;
+        const T eyy = (Uy[i + nx] - Uy[i]) * ih;
+        const T exy = T(0.5) * ((Ux[i + nx] - Ux[i]) + (Uy[yy * nx + xp] - Uy[i])) * ih;
+        const T gg = matg ? MG[i] : T(1);
+        const T lam = sol ? lam1 : lam0, mu = sol ? mu1 : mu0;
+        const T tr = exx + eyy;
+        w = gg * (lam * tr * tr + T(2) * mu * (exx * exx + eyy * eyy + T(2) * exy * exy));
+      } else {
+        const T p = P[i];
+        const T gx = (P[yy * nx + xp] - p) * ih, gy = (P[i + nx] - p) * ih;
+        const T c0v = c0c + (matg ? MG[i] : T(0));
+        w = c0v * p * p + (sol ? kap1 : kap0) * (gx * gx + gy * gy);
+      }
+      part += w;  // a few terms per thread and row, all non-negative
     }
-    acc[0] += (double)w;
+    acc[0] += (double)part;
   }
   block_sum<1>(acc, red);
   if (publish_partials<1>(acc, v.partials, &v.sc->cnt[0])) {
@@ -364,47 +413,68 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T
 // column FFT. COL_PLAIN: one column FFT only (sign from `inverse`).
 template <typename T, int FY>
 __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev<T> py, Spec2<T> sp, int CW,
-                          int mode, int inverse, double* partials, SolverScalars* sc) {
+                                            int mode, int inverse, double* partials, SolverScalars* sc) {
   if (mode != COL_PLAIN && mode != COL_NORM && mode != COL_TRUENORM && done_flag(sc)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   cx<T>* B = reinterpret_cast<cx<T>*>(smem);
   const int x0 = blockIdx.x * CW;
   const int nc = min(CW, nx - x0);
-  for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
-    const int y = i / nc, c = i - y * nc;
-    B[i] = S[(size_t)y * nx + x0 + c];
+  const int n = ny * nc;
+  const int bd = blockDim.x;
+  const FastDiv dc(nc);
+  // staged strip load, 8 loads in flight per thread
+  for (int i = threadIdx.x; i < n; i += 8 * bd) {
+    cx<T> t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int ii = i + k * bd;
+      if (ii < n) {
+        const int y = dc.div(ii), c = ii - y * nc;
+        t[k] = S[(size_t)y * nx + x0 + c];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (i + k * bd < n) B[i + k * bd] = t[k];
   }
   __syncthreads();
   if (mode == COL_PLAIN) {
     if (inverse) fft_lines<T, 1, FY>(B, py, nc, 1, nc, true);
     else fft_lines<T, -1, FY>(B, py, nc, 1, nc, true);
-    for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
-      const int y = i / nc, c = i - y * nc;
-      S[(size_t)y * nx + x0 + c] = B[i];
-    }
-    return;
+  } else {
+    fft_lines<T, -1, FY>(B, py, nc, 1, nc, true);
   }
-  fft_lines<T, -1, FY>(B, py, nc, 1, nc, true);
   const bool store = (mode != COL_NORM && mode != COL_TRUENORM);
-  const T m0 = (T)sp.m0, m1 = (T)sp.m1, invN = (T)sp.invN;
   double acc[1] = {0.0};
-  for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
-    const int ky = i / nc, c = i - ky * nc;
-    const T den = m0 + m1 * (sp.lamx[x0 + c] + sp.lamy[ky]);
-    const T m = den > T(0) ? T(1) / den : T(0);
-    const cx<T> w = B[i];
-    acc[0] += (double)(m * (w.re * w.re + w.im * w.im));
-    if (store) B[i] = scal(w, m * invN);
+  if (mode != COL_PLAIN) {
+    const T m0 = (T)sp.m0, m1 = (T)sp.m1, invN = (T)sp.invN;
+    T part = T(0);
+    int cnt = 0;
+    for (int i = threadIdx.x; i < n; i += bd) {
+      const int ky = dc.div(i), c = i - ky * nc;
+      const T den = m0 + m1 * (sp.lamx[x0 + c] + sp.lamy[ky]);
+      T m;
+      if constexpr (sizeof(T) == 4) m = den > T(0) ? __fdividef(1.0f, den) : T(0);
+      else m = den > T(0) ? T(1) / den : T(0);
+      const cx<T> w = B[i];
+      part += m * (w.re * w.re + w.im * w.im);
+      if (++cnt == 16) { acc[0] += (double)part; part = T(0); cnt = 0; }  // non-negative terms
+      if (store) B[i] = scal(w, m * invN);
+    }
+    acc[0] += (double)part;
+    if (store) {
+      __syncthreads();
+      fft_lines<T, 1, FY>(B, py, nc, 1, nc, true);
+    }
   }
   if (store) {
-    __syncthreads();
-    fft_lines<T, 1, FY>(B, py, nc, 1, nc, true);
-    for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
-      const int y = i / nc, c = i - y * nc;
+    for (int i = threadIdx.x; i < n; i += bd) {
+      const int y = dc.div(i), c = i - y * nc;
       S[(size_t)y * nx + x0 + c] = B[i];
     }
   }
+  if (mode == COL_PLAIN) return;
   block_sum<1>(acc, red);
   if (publish_partials<1>(acc, partials, &sc->cnt[1])) {
     double tot[1];

@@ -210,6 +210,23 @@ __global__ void k_to_real(long long N, const double* __restrict__ src, T* dst) {
     dst[i] = (T)src[i];
 }
 
+// Double iterate <-> float pair (hi = round(u), lo = round(u - hi)).
+__global__ void k_df_split(long long n, const double* __restrict__ u, float* uh, float* ul) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double x = u[i];
+    const float h = (float)x;
+    uh[i] = h;
+    ul[i] = (float)(x - (double)h);
+  }
+}
+__global__ void k_df_merge(long long n, const float* __restrict__ uh, const float* __restrict__ ul,
+                           double* u) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    u[i] = (double)uh[i] + (double)ul[i];
+}
+
 // ---------------------------------------------------------------- launchers
 template <typename T>
 cudaError_t launch_el_output(const Op2<T>& op, const double* u, T* strain, T* stress,
@@ -266,6 +283,14 @@ cudaError_t launch_scale_copy(long long N, const T* src, double scale, T* dst, c
 cudaError_t launch_set_masked(long long N, const uint8_t* mask, double value, double* c,
                               cudaStream_t st) {
   k_set_masked<<<post_grid(N), kPostThreads, 0, st>>>(N, mask, value, c);
+  return cudaGetLastError();
+}
+cudaError_t launch_df_split(long long n, const double* u, float* uh, float* ul, cudaStream_t st) {
+  k_df_split<<<post_grid(n), kPostThreads, 0, st>>>(n, u, uh, ul);
+  return cudaGetLastError();
+}
+cudaError_t launch_df_merge(long long n, const float* uh, const float* ul, double* u, cudaStream_t st) {
+  k_df_merge<<<post_grid(n), kPostThreads, 0, st>>>(n, uh, ul, u);
   return cudaGetLastError();
 }
 template <typename T>

@@ -191,7 +191,7 @@ def test_transient_matches_oracle(prec, tol):
     ctx.close()
     got = c.cpu().numpy().reshape(shape)
     assert rel(got, c_ref) < tol
-    assert got.min() >= -1e-9 and got.max() <= 1 + 1e-9
+    assert got.min() >= -tol and got.max() <= 1 + tol  # discrete maximum principle
 
 
 # ---------------------------------------------------------------- phase field
