@@ -132,7 +132,8 @@ def class_bytes(infos_per_step, N, s):
     tot = {"direction": 0.0, "update": 0.0, "column": 0.0}
     kinds = ["diffusion", "elastic", "phasefield"]
     for infos in infos_per_step:
-        for kind, info in zip(kinds, infos):
+        for idx, info in enumerate(infos):
+            kind = kinds[idx % 3]
             it = info["iters"]
             tot["direction"] += N * it * kernel_bytes(kind, "direction", s)
             tot["update"] += N * it * kernel_bytes(kind, "update", s)
@@ -143,7 +144,10 @@ def class_bytes(infos_per_step, N, s):
 # ---------------------------------------------------------------- GPU arm
 
 def make_state(torch, fm, w, prec, device, pinned_host=False):
-    N = w.voxels
+    """State buffers for a workload or a list of same-size workloads (a batch)."""
+    ws = w if isinstance(w, list) else [w]
+    w = ws[0]
+    N = w.voxels * len(ws)
     ft = torch.float64 if prec == fm.FFTMECH_FP64 else torch.float32
     spec = [("c", 1, torch.float64), ("c_ppt", 1, ft), ("eig", 1, ft), ("u", 2, torch.float64),
             ("strain", 3, ft), ("stress", 3, ft), ("H", 1, ft), ("damage", 1, torch.float64)]
@@ -151,8 +155,8 @@ def make_state(torch, fm, w, prec, device, pinned_host=False):
     for k, n, dt in spec:
         t = torch.zeros(n * N, dtype=dt)
         bufs[k] = t.pin_memory() if pinned_host else t.to(device)
-    ph = torch.as_tensor(np.ascontiguousarray(w.phase.ravel()))
-    mask = torch.as_tensor(np.ascontiguousarray(w.dirichlet_mask.ravel()))
+    ph = torch.as_tensor(np.ascontiguousarray(np.concatenate([x.phase.ravel() for x in ws])))
+    mask = torch.as_tensor(np.ascontiguousarray(np.concatenate([x.dirichlet_mask.ravel() for x in ws])))
     if pinned_host:
         bufs["phase"] = ph.pin_memory()
         bufs["mask"] = mask.pin_memory()
@@ -174,11 +178,15 @@ def make_state(torch, fm, w, prec, device, pinned_host=False):
 
 def run_arm(torch, fm, w, prec, steps, warmup, device, profile=True, flush=None):
     """W warm-up steps, then `steps` timed staggered steps (L2 flushed before
-    each). Returns per-step infos, device ms per step and profile data."""
+    each). Returns per-step infos, device ms per step and profile data.
+    `w` may be a list of same-size workloads, solved as one batch."""
     stream = torch.cuda.current_stream(device)
+    ws = w if isinstance(w, list) else [w]
+    w = ws[0]
     ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=w.tol,
-                     max_iter=20000, replace_residual=1, check_every=16, stream=stream.cuda_stream)
-    bufs, st, p = make_state(torch, fm, w, prec, device)
+                     max_iter=20000, replace_residual=1, check_every=16, stream=stream.cuda_stream,
+                     batch=len(ws))
+    bufs, st, p = make_state(torch, fm, ws, prec, device)
     for _ in range(warmup):
         fm.fftmech_staggered_step(ctx.handle, st, p)
     torch.cuda.synchronize(device)
@@ -194,7 +202,8 @@ def run_arm(torch, fm, w, prec, steps, warmup, device, profile=True, flush=None)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-        infos.append([i.as_dict() for i in inf])
+        # per problem: [diffusion, equilibrium, phase field]
+        infos.append([inf[i].as_dict() for i in range(len(inf))])
     torch.cuda.synchronize(device)
     prof = {}
     for k, name in enumerate(fm.KERNEL_CLASS_NAMES):
@@ -209,9 +218,11 @@ def run_arm(torch, fm, w, prec, steps, warmup, device, profile=True, flush=None)
 def run_e2e(torch, fm, w, prec, steps, warmup, device):
     """The same steps through the C ABI with pinned HOST buffers: every call
     copies the state in and out (host <-> device inside the timed region)."""
+    ws = w if isinstance(w, list) else [w]
+    w = ws[0]
     ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=w.tol,
-                     max_iter=20000, replace_residual=1, check_every=16)
-    bufs, st, p = make_state(torch, fm, w, prec, device, pinned_host=True)
+                     max_iter=20000, replace_residual=1, check_every=16, batch=len(ws))
+    bufs, st, p = make_state(torch, fm, ws, prec, device, pinned_host=True)
     for _ in range(warmup):
         fm.fftmech_staggered_step(ctx.handle, st, p)
     torch.cuda.synchronize(device)
@@ -219,15 +230,15 @@ def run_e2e(torch, fm, w, prec, steps, warmup, device):
     t0 = time.perf_counter()
     for _ in range(steps):
         inf = fm.fftmech_staggered_step(ctx.handle, st, p)
-        iters += sum(i.iters for i in inf)
+        iters += sum(inf[i].iters for i in range(len(inf)))
     torch.cuda.synchronize(device)
     dt = time.perf_counter() - t0
     ctx.close()
-    N = w.voxels
+    N = w.voxels * len(ws)
     s = 8 if prec == fm.FFTMECH_FP64 else 4
     h2d = N * (1 + 1 + 8 + s + s + 16 + 3 * s + 3 * s + s + 8)  # phase, mask, c, c_ppt, eig, u, strain, stress, H, d
     d2h = N * (8 + s + s + 16 + 3 * s + 3 * s + s + 8)
-    return {"value": N * iters / dt, "seconds": dt, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    return {"value": w.voxels * iters / dt, "seconds": dt, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -284,6 +295,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=1,
+                    help="solve this many independent RVEs of the workload size (seeds differ) "
+                         "as one batch per rank")
     ap.add_argument("--n", type=int, default=N_SIDE,
                     help="grid side (3^k); the default 729 is the benchmark workload, larger "
                          "sides (2187) give working sets above L2 for profiling")
@@ -312,9 +326,13 @@ def main():
     __graft_entry__.build()
     from paper_2305_13081_gb300 import fftmech as fm
 
-    w = workload(rank, args.n)
     side = args.n
-    N = w.voxels
+    if args.batch > 1:
+        ws = [workload(rank * 1000 + b, args.n) for b in range(args.batch)]
+    else:
+        ws = workload(rank, args.n)
+    w = ws[0] if isinstance(ws, list) else ws
+    N = w.voxels * args.batch
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
 
     def barrier():
@@ -326,19 +344,20 @@ def main():
     barrier()
     sampler.start()
     t_wall = time.perf_counter()
-    mixed = run_arm(torch, fm, w, fm.FFTMECH_MIXED, args.steps, args.warmup, device, profile=False,
+    mixed = run_arm(torch, fm, ws, fm.FFTMECH_MIXED, args.steps, args.warmup, device, profile=False,
                     flush=flush)
     barrier()
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     # second timed region over the same steps with per-launch CUDA events
     # (the events cost time, so the headline value comes from the first one)
-    prof_run = run_arm(torch, fm, w, fm.FFTMECH_MIXED, args.steps, args.warmup, device, profile=True,
+    prof_run = run_arm(torch, fm, ws, fm.FFTMECH_MIXED, args.steps, args.warmup, device, profile=True,
                        flush=flush)
 
-    iters = sum(sum(i["iters"] for i in inf) for inf in mixed["infos"])
+    iters = sum(sum(i["iters"] for i in inf) for inf in mixed["infos"])  # all problems, all solves
     dev_s = sum(mixed["ms"]) / 1e3
-    local_vals = torch.tensor([N * iters, dev_s], dtype=torch.float64, device=device)
+    Np = w.voxels  # voxels of one problem; iterations are summed over problems
+    local_vals = torch.tensor([Np * iters, dev_s], dtype=torch.float64, device=device)
     if dist is not None:
         tot = local_vals.clone()
         dist.all_reduce(tot[:1], op=dist.ReduceOp.SUM)
@@ -353,10 +372,10 @@ def main():
     kinds = ["diffusion", "equilibrium", "phasefield"]
     breakdown = {}
     for j, k in enumerate(kinds):
-        it = sum(inf[j]["iters"] for inf in mixed["infos"])
+        it = sum(inf[3 * b + j]["iters"] for inf in mixed["infos"] for b in range(len(inf) // 3))
         ms = sum(inf[j]["device_ms"] for inf in mixed["infos"])
         breakdown[k] = {"iters": it, "device_ms": ms,
-                        "voxel_iterations_per_s": N * it / (ms / 1e3) if ms > 0 else None}
+                        "voxel_iterations_per_s": Np * it / (ms / 1e3) if ms > 0 else None}
 
     # roofline of the dominant kernel class (CUDA events inside the timed region)
     from json import load as _jl
@@ -366,7 +385,7 @@ def main():
         hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         hbm_peak, peak_src = 6800.0, "fallback"
-    cb = class_bytes(prof_run["infos"], N, 4)
+    cb = class_bytes(prof_run["infos"], Np, 4)
     kernels = {}
     for name in ("direction", "update", "column"):
         n, ms = prof_run["prof"][name]
@@ -388,7 +407,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields / f64 iterates+reductions",
         "data": "synthetic",
-        "config": {"workload": f"random-carpet-{side}x{side}-transient-staggered", "voxels": N,
+        "config": {"workload": f"random-carpet-{side}x{side}-transient-staggered"
+                               + (f"-batch{args.batch}" if args.batch > 1 else ""), "voxels": N,
                    "seed": SEED, "precision": "mixed", "tol": w.tol, "porosity": w.extra["porosity"],
                    "steps_per_run": TOTAL_STEPS, "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before each timed step",
                    "parallelism": f"{world} independent RVE replicas"},
@@ -402,10 +422,10 @@ def main():
     }
 
     if rank == 0 and not args.no_fp64:
-        fp64 = run_arm(torch, fm, w, fm.FFTMECH_FP64, args.steps, args.warmup, device, profile=False,
+        fp64 = run_arm(torch, fm, ws, fm.FFTMECH_FP64, args.steps, args.warmup, device, profile=False,
                        flush=flush)
         it64 = sum(sum(i["iters"] for i in inf) for inf in fp64["infos"])
-        v64 = N * it64 / (sum(fp64["ms"]) / 1e3)
+        v64 = Np * it64 / (sum(fp64["ms"]) / 1e3)
         errs = {}
         for k in ("strain", "stress", "c"):
             a, b = mixed["state"][k], fp64["state"][k]
@@ -415,7 +435,7 @@ def main():
                        "speedup_mixed_over_fp64": value / world / v64 if world == 1 else (value / world) / v64,
                        "mixed_vs_fp64_rel_err": errs}
     if rank == 0 and not args.no_e2e:
-        e2e = run_e2e(torch, fm, w, fm.FFTMECH_MIXED, max(3, args.steps // 4), 1, device)
+        e2e = run_e2e(torch, fm, ws, fm.FFTMECH_MIXED, max(3, args.steps // 4), 1, device)
         out["e2e"] = {"value": e2e["value"] * world, "unit": UNIT,
                       "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
                       "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]}

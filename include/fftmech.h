@@ -42,6 +42,13 @@
  *   status and also stored in info->status. A CUDA failure returns
  *   FFTMECH_ERR_CUDA; fftmech_last_error() gives the message.
  * - No CPU fallback: without a CUDA device fftmech_create fails.
+ * - Batches: a context made by fftmech_create_batched holds B problems of
+ *   the same grid (independent RVEs, e.g. one per macroscale point, Sec. 3.2).
+ *   Every field argument then holds the B problems back to back (problem b's
+ *   scalar fields at offset b N, its d-component fields at b d N, with N the
+ *   voxels of one problem), every `info` argument is an array of B records
+ *   (3 B for the staggered step, problem-major), and each problem converges
+ *   on its own: its iterations stop when it has, while the others continue.
  */
 #ifndef FFTMECH_H
 #define FFTMECH_H
@@ -137,6 +144,17 @@ typedef struct fftmech_ctx fftmech_ctx;
 fftmech_status fftmech_create(fftmech_ctx** ctx, const fftmech_grid* grid,
                               const fftmech_materials* mat, fftmech_precision precision,
                               const fftmech_solver_opts* opts, void* stream);
+
+/* A context for `batch` >= 1 independent problems of the same grid, solved
+ * together (every kernel launch covers all of them; grid.y = problem).
+ * The workspace grows linearly with batch. fftmech_create(...) equals
+ * fftmech_create_batched(..., 1, ...). */
+fftmech_status fftmech_create_batched(fftmech_ctx** ctx, const fftmech_grid* grid, int batch,
+                                      const fftmech_materials* mat, fftmech_precision precision,
+                                      const fftmech_solver_opts* opts, void* stream);
+
+/* Number of problems of a context (0 for NULL). */
+int fftmech_batch_size(const fftmech_ctx* ctx);
 
 /* Free the workspace (and the stream, if the context created it). */
 fftmech_status fftmech_destroy(fftmech_ctx* ctx);
@@ -237,10 +255,12 @@ typedef struct {
  * precipitation -> eigenstrain -> equilibrium (stiffness degraded by the
  * damage of the previous step) -> history -> phase field. The degradation
  * by the new damage (Algorithm 1, last line) takes effect in the next call.
- * info[0] = diffusion, info[1] = equilibrium, info[2] = phase field. */
+ * info[3 b + 0] = diffusion, info[3 b + 1] = equilibrium, info[3 b + 2] =
+ * phase field of problem b (3 records per problem of the batch). The step
+ * parameters are shared by the problems of a batch. */
 fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
                                       const fftmech_step_params* params,
-                                      fftmech_solve_info info[3]);
+                                      fftmech_solve_info* info);
 
 /* Instrumentation (no counterpart in the paper): kernel classes of the PCG
  * loop. When profiling is enabled, every launch of a class is bracketed by

@@ -63,7 +63,8 @@ enum StageSlot {
 struct fftmech_ctx {
   int dim = 2;
   int nx = 1, ny = 1, nz = 1;
-  long long N = 0;
+  long long N = 0;  // voxels of one problem
+  int B = 1;        // problems in the (uniform) batch
   double h = 1, h_diff = 1;
   fftmech_materials mat{};
   fftmech_precision prec = FFTMECH_FP64;
@@ -74,25 +75,34 @@ struct fftmech_ctx {
   int nsm = 0;
   size_t optin = 0;
   HostPlan px, py;
-  Shape2 shape_f{}, shape_d{};
-  // workspace
+  Shape2 shape{};
+  // workspace (B problems back to back)
   void* r = nullptr;
   void* p[2] = {nullptr, nullptr};
   void* S = nullptr;
   void* g = nullptr;
-  float* uh = nullptr;  // MIXED iterate, high part (2 N)
-  float* ul = nullptr;  // MIXED iterate, low part (2 N)
+  float* uh = nullptr;   // MIXED iterate, high part
+  float* ul = nullptr;   // MIXED iterate, low part
   double* phi = nullptr;
   double* Hd = nullptr;
   double* cn = nullptr;
   void* lamx = nullptr;
   void* lamy = nullptr;
   double* partials = nullptr;
-  double* results = nullptr;
+  double* results = nullptr;   // 16 per problem
+  double* m0b = nullptr;       // per-problem preconditioner constants
+  double* m1b = nullptr;
+  int* mode = nullptr;         // per-problem reliable-update / restart flags
   SolverScalars* sc = nullptr;
-  unsigned int* cnt = nullptr;
   SolverScalars* h_sc = nullptr;   // pinned
   double* h_results = nullptr;     // pinned
+  int* h_mode = nullptr;           // host copy of the modes, edited freely
+  // pinned ring the mode pushes copy from: an asynchronous copy reads its
+  // pinned source when it runs, so a slot is reused only after its copy ran
+  static constexpr int kModeSlots = 4;
+  int* h_mode_ring = nullptr;
+  cudaEvent_t mode_ev[kModeSlots] = {nullptr, nullptr, nullptr, nullptr};
+  int mode_slot = 0;
   Staging stage[ST_COUNT];
   // instrumentation
   bool prof = false;
@@ -106,6 +116,8 @@ struct fftmech_ctx {
 };
 
 namespace {
+
+constexpr int kResultsPerProblem = 16;
 
 fftmech_status set_err(fftmech_ctx* ctx, fftmech_status s, const char* fmt, ...) {
   if (ctx) {
@@ -214,145 +226,201 @@ void prof_flush(fftmech_ctx* ctx) {
   ctx->pending.clear();
 }
 
+#define FFTMECH_LAUNCH(KC, CALL) \
+  do {                           \
+    ProfScope _ps(ctx, KC);      \
+    CK(CALL);                    \
+  } while (0)
+
 void lame(double E, double nu, double& lam, double& mu) {
   lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   mu = E / (2.0 * (1.0 + nu));
 }
 
-void fill_info_defaults(fftmech_solve_info* info) {
-  if (!info) return;
-  std::memset(info, 0, sizeof(*info));
+fftmech_status sync_scalars(fftmech_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars) * ctx->B, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  return FFTMECH_OK;
+}
+
+fftmech_status push_modes(fftmech_ctx* ctx) {
+  const int k = ctx->mode_slot;
+  ctx->mode_slot = (k + 1) % fftmech_ctx::kModeSlots;
+  CK(cudaEventSynchronize(ctx->mode_ev[k]));  // the slot's previous copy has run
+  int* slot = ctx->h_mode_ring + (size_t)k * ctx->B;
+  std::memcpy(slot, ctx->h_mode, sizeof(int) * ctx->B);
+  CK(cudaMemcpyAsync(ctx->mode, slot, sizeof(int) * ctx->B, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaEventRecord(ctx->mode_ev[k], ctx->stream));
+  return FFTMECH_OK;
 }
 
 // ---------------------------------------------------------------- PCG driver
-template <typename T>
 struct Solve {
   int iters = 0;
   int status = FFTMECH_OK;
   double rel = 0, true_rel = 0;
 };
 
+// Preconditioned CG on the potential for every problem of the batch (see
+// the kernels for the per-iteration launches). The host polls the device
+// scalars every check_every iterations; a problem that has converged (or
+// failed) stops moving while the others continue. MIXED: the iterate is a
+// float pair, with reliable updates and a final FP64 true-residual gate.
 template <typename T, int D>
-fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, double m0, double m1,
-                       Solve<T>& out) {
+fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, const Spec2<T>& sp_in,
+                       std::vector<Solve>& out) {
   cudaStream_t st = ctx->stream;
-  const Shape2& sh = sizeof(T) == 4 ? ctx->shape_f : ctx->shape_d;
+  const int B = ctx->B;
+  const Shape2& sh = ctx->shape;
   FftPlanDev<T> px = dev_plan<T>(ctx->px), py = dev_plan<T>(ctx->py);
-  Spec2<T> sp;
+  Spec2<T> sp = sp_in;
   sp.lamx = (const T*)ctx->lamx;
   sp.lamy = (const T*)ctx->lamy;
-  sp.m0 = m0;
-  sp.m1 = m1;
   sp.invN = 1.0 / (double)ctx->N;
-  SolverScalars h{};
-  h.tol2 = ctx->opts.tol * ctx->opts.tol;
-  h.max_iter = ctx->opts.max_iter;
-  CK(cudaMemcpyAsync(ctx->sc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+  for (int b = 0; b < B; ++b) {
+    SolverScalars h{};
+    h.tol2 = ctx->opts.tol * ctx->opts.tol;
+    h.max_iter = ctx->opts.max_iter;
+    ctx->h_sc[b] = h;
+    ctx->h_mode[b] = 0;
+  }
+  CK(cudaMemcpyAsync(ctx->sc, ctx->h_sc, sizeof(SolverScalars) * B, cudaMemcpyHostToDevice, st));
+  if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
   T* pbuf[2] = {(T*)ctx->p[0], (T*)ctx->p[1]};
   Vec2<T> v;
   v.u = u;
   v.uh = ctx->uh;
   v.ul = ctx->ul;
-  const long long nU = (long long)D * ctx->N;
-  if (sizeof(T) == 4) CK(launch_df_split(nU, u, ctx->uh, ctx->ul, st));
   v.r = (T*)ctx->r;
   v.p_in = pbuf[0];
   v.p_out = pbuf[1];
   v.S = (cx<T>*)ctx->S;
   v.partials = ctx->partials;
   v.sc = ctx->sc;
+  v.mode = ctx->mode;
+  const long long nU = (long long)D * ctx->N * B;
+  const bool mixed = sizeof(T) == 4;
+  if (mixed) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_df_split(nU, u, ctx->uh, ctx->ul, st));
   const int nx = ctx->nx, ny = ctx->ny;
-#define FFTMECH_LAUNCH(KC, CALL) \
-  do {                           \
-    ProfScope _ps(ctx, KC);      \
-    CK(CALL);                    \
-  } while (0)
-  FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 1, st)));
-  FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_NORM, 0, ctx->partials, ctx->sc, st));
-  FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
-  FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_INIT, 0, ctx->partials, ctx->sc, st));
-  CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  prof_flush(ctx);
-  if (ctx->h_sc->rz0 == 0.0 && ctx->h_sc->rz > 0.0) {
-    // zero right-hand side: the solution is zero (outside Dirichlet voxels)
-    if (op.mask) {
-      return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "zero right-hand side with a Dirichlet mask");
+  const int fx = ctx->px.fam, fy = ctx->py.fam;
+  auto residual = [&](int zero_u, int filter) {
+    return launch_residual_f<T, D>(fx, op, v, px, sh, zero_u, filter, st);
+  };
+  auto colpass = [&](int mode) {
+    return launch_colpass_f<T>(fy, nx, ny, v.S, py, sp, sh, mode, 0, ctx->partials, ctx->sc, ctx->mode, st);
+  };
+  FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(1, 0));
+  FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_NORM));
+  FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 0));
+  FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_INIT));
+  if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
+  // a zero right-hand side has the zero solution (outside Dirichlet voxels)
+  for (int b = 0; b < B; ++b) {
+    const SolverScalars& q = ctx->h_sc[b];
+    if (q.rz0 == 0.0 && q.rz > 0.0) {
+      if (op.mask) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "zero right-hand side with a Dirichlet mask");
+      CK(cudaMemsetAsync(u + (size_t)b * D * ctx->N, 0, sizeof(double) * D * ctx->N, st));
+      if (mixed) {
+        CK(cudaMemsetAsync(ctx->uh + (size_t)b * D * ctx->N, 0, sizeof(float) * D * ctx->N, st));
+        CK(cudaMemsetAsync(ctx->ul + (size_t)b * D * ctx->N, 0, sizeof(float) * D * ctx->N, st));
+      }
+      SolverScalars z = q;
+      z.done = 1;
+      z.status = FFTMECH_OK;
+      z.rz = 0.0;
+      CK(cudaMemcpyAsync(ctx->sc + b, &z, sizeof(SolverScalars), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+      ctx->h_sc[b] = z;
     }
-    CK(cudaMemsetAsync(u, 0, sizeof(double) * D * ctx->N, st));
-    out.iters = 0;
-    out.status = FFTMECH_OK;
-    out.rel = out.true_rel = 0.0;
-    return FFTMECH_OK;
   }
   const int check = std::max(1, ctx->opts.check_every);
-  const bool reliable = (sizeof(T) == 4) && ctx->opts.replace_residual != 0;
-  double rz_rep = ctx->h_sc->rz;  // r.M^-1 r right after the last (true) residual
-  bool pending = false;
+  const bool reliable = mixed && ctx->opts.replace_residual != 0;
+  std::vector<double> rz_rep(B);
+  for (int b = 0; b < B; ++b) rz_rep[b] = ctx->h_sc[b].rz;
+  auto all_done = [&]() {
+    for (int b = 0; b < B; ++b)
+      if (!ctx->h_sc[b].done) return false;
+    return true;
+  };
+  bool pending = false;  // some problem has mode 1 queued for the next iteration
   int pi = 0;
   int it = 0;
-  bool done = ctx->h_sc->done != 0;
   for (int restart = 0;; ++restart) {
-    while (!done && it < ctx->opts.max_iter) {
+    while (!all_done() && it < ctx->opts.max_iter) {
       Vec2<T> va = v;
       va.p_in = pbuf[pi];
       va.p_out = pbuf[1 - pi];
-      FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, (launch_direction_f<T, D>(ctx->px.fam, op, va, px, sh, st)));
+      FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, (launch_direction_f<T, D>(fx, op, va, px, sh, st)));
       Vec2<T> vb = v;
       vb.p_in = pbuf[1 - pi];
+      FFTMECH_LAUNCH(FFTMECH_K_UPDATE, (launch_update_f<T, D>(fx, op, vb, px, sh, st)));
       const bool replace = pending;
-      pending = false;
-      if (replace) {
-        // reliable update: u += alpha p only, then the FP64 true residual
-        FFTMECH_LAUNCH(FFTMECH_K_UPDATE, (launch_update_f<T, D>(ctx->px.fam, op, vb, px, sh, 1, st)));
-        FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
-        FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_TRUE, 0, ctx->partials, ctx->sc, st));
-      } else {
-        FFTMECH_LAUNCH(FFTMECH_K_UPDATE, (launch_update_f<T, D>(ctx->px.fam, op, vb, px, sh, 0, st)));
-        FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_ITER, 0, ctx->partials, ctx->sc, st));
-      }
+      // reliable update: u += alpha p only (update kernel), then the FP64 true residual
+      if (replace) FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 1));
+      FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_ITER));
       pi = 1 - pi;
       ++it;
+      if (replace) {
+        for (int b = 0; b < B; ++b) ctx->h_mode[b] = 0;
+        if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
+        pending = false;
+      }
       if (it % check == 0 || it >= ctx->opts.max_iter || replace) {
-        CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        prof_flush(ctx);
-        done = ctx->h_sc->done != 0;
-        if (replace) rz_rep = ctx->h_sc->rz_true;
-        else if (reliable && ctx->h_sc->rz < 1e-2 * rz_rep) pending = true;
+        if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
+        bool any = false;
+        for (int b = 0; b < B; ++b) {
+          const SolverScalars& q = ctx->h_sc[b];
+          if (replace) rz_rep[b] = q.rz_true > 0 ? q.rz_true : rz_rep[b];
+          if (reliable && !replace && !q.done && q.rz < 1e-2 * rz_rep[b]) {
+            ctx->h_mode[b] = 1;
+            any = true;
+          }
+        }
+        if (any) {
+          if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
+          pending = true;
+        }
       }
     }
-    // FP64 true residual of the iterate
-    FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
-    FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_TRUENORM, 0, ctx->partials, ctx->sc, st));
-    CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    prof_flush(ctx);
-    const SolverScalars& q = *ctx->h_sc;
-    const bool gate = reliable && q.status == FFTMECH_OK && restart < 3 && q.iter < ctx->opts.max_iter &&
-                      q.rz_true > 4.0 * q.tol2 * q.rz0;
-    if (!gate) break;
-    // the float recursion met tol but the true residual did not: continue
-    // from the true residual with a fresh direction
-    const int zero = 0;
-    CK(cudaMemcpyAsync(&ctx->sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-    FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, (launch_residual_f<T, D>(ctx->px.fam, op, v, px, sh, 0, st)));
-    FFTMECH_LAUNCH(FFTMECH_K_COLUMN, launch_colpass_f<T>(ctx->py.fam, nx, ny, v.S, py, sp, sh, COL_RESTART, 0, ctx->partials, ctx->sc, st));
-    CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    prof_flush(ctx);
-    done = ctx->h_sc->done != 0;
-    rz_rep = ctx->h_sc->rz;
+    // FP64 true residual of every iterate
+    FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 0));
+    FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_TRUENORM));
+    if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
+    // problems whose float recursion met tol while the true residual did not:
+    // continue from the true residual with a fresh direction
+    bool any = false;
+    for (int b = 0; b < B; ++b) {
+      const SolverScalars& q = ctx->h_sc[b];
+      const bool gate = reliable && q.status == FFTMECH_OK && restart < 3 && q.iter < ctx->opts.max_iter &&
+                        q.rz_true > 4.0 * q.tol2 * q.rz0;
+      ctx->h_mode[b] = gate ? 2 : 0;
+      if (gate) {
+        const int zero = 0;
+        CK(cudaMemcpyAsync(&ctx->sc[b].done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        any = true;
+      }
+    }
+    if (!any) break;
+    if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
+    FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 1));
+    FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_RESTART));
+    for (int b = 0; b < B; ++b) ctx->h_mode[b] = 0;
+    if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
+    if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
+    for (int b = 0; b < B; ++b) rz_rep[b] = ctx->h_sc[b].rz;
     pending = false;
   }
-  if (sizeof(T) == 4) {
-    CK(launch_df_merge(nU, ctx->uh, ctx->ul, u, st));
+  if (mixed) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_df_merge(nU, ctx->uh, ctx->ul, u, st));
+  out.assign(B, Solve());
+  for (int b = 0; b < B; ++b) {
+    const SolverScalars& f = ctx->h_sc[b];
+    out[b].iters = f.iter;
+    out[b].status = f.done ? f.status : FFTMECH_ERR_NOT_CONVERGED;
+    out[b].rel = f.rz0 > 0 ? std::sqrt(std::max(f.rz, 0.0) / f.rz0) : 0.0;
+    out[b].true_rel = f.rz0 > 0 ? std::sqrt(std::max(f.rz_true, 0.0) / f.rz0) : 0.0;
   }
-  const SolverScalars& f = *ctx->h_sc;
-  out.iters = f.iter;
-  out.status = f.done ? f.status : FFTMECH_ERR_NOT_CONVERGED;
-  out.rel = f.rz0 > 0 ? std::sqrt(std::max(f.rz, 0.0) / f.rz0) : 0.0;
-  out.true_rel = f.rz0 > 0 ? std::sqrt(std::max(f.rz_true, 0.0) / f.rz0) : 0.0;
   return FFTMECH_OK;
 }
 
@@ -368,9 +436,9 @@ void base_op(const fftmech_ctx* ctx, Op2<T>& op, const uint8_t* phase) {
   op.src_scale = 1.0;
 }
 
-fftmech_status read_results(fftmech_ctx* ctx, int n) {
-  CK(cudaMemcpyAsync(ctx->h_results, ctx->results, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                     ctx->stream));
+fftmech_status read_results(fftmech_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_results, ctx->results, sizeof(double) * kResultsPerProblem * ctx->B,
+                     cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   prof_flush(ctx);
   return FFTMECH_OK;
@@ -395,21 +463,38 @@ double solve_timer_ms(fftmech_ctx* ctx) {
   return (double)ms;
 }
 
-void copy_solve(const Solve<float>& s, fftmech_solve_info* info) {
-  info->status = s.status; info->iters = s.iters; info->rel_res = s.rel; info->true_rel_res = s.true_rel;
+// Per-problem info records sit `stride` apart (1 for single solves, 3 in a
+// staggered step).
+fftmech_solve_info& info_at(fftmech_solve_info* info, int b, int stride) { return info[(size_t)b * stride]; }
+
+fftmech_status worst_status(const std::vector<Solve>& s) {
+  fftmech_status w = FFTMECH_OK;
+  for (const Solve& x : s)
+    if (x.status != FFTMECH_OK && w == FFTMECH_OK) w = (fftmech_status)x.status;
+  return w;
 }
-void copy_solve(const Solve<double>& s, fftmech_solve_info* info) {
-  info->status = s.status; info->iters = s.iters; info->rel_res = s.rel; info->true_rel_res = s.true_rel;
+
+void copy_solves(const std::vector<Solve>& s, fftmech_solve_info* info, int stride, double ms) {
+  for (size_t b = 0; b < s.size(); ++b) {
+    fftmech_solve_info& i = info_at(info, (int)b, stride);
+    i.status = s[b].status;
+    i.iters = s[b].iters;
+    i.rel_res = s[b].rel;
+    i.true_rel_res = s[b].true_rel;
+    i.device_ms = ms;
+  }
 }
 
 // ---------------------------------------------------------------- solves
 template <typename T>
 fftmech_status equilibrium_impl(fftmech_ctx* ctx, const uint8_t* phase, const T* eig,
                                 const double* damage, const double* eps_mac, double* u, T* strain,
-                                T* stress, fftmech_solve_info* info) {
+                                T* stress, fftmech_solve_info* info, int stride) {
   cudaStream_t st = ctx->stream;
-  fftmech_status rc0 = solve_timer_start(ctx);
-  if (rc0 != FFTMECH_OK) return rc0;
+  fftmech_status rc = solve_timer_start(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  const int B = ctx->B;
+  const long long NB = ctx->N * B;
   Op2<T> op;
   base_op<T>(ctx, op, phase);
   op.eig = eig;
@@ -417,121 +502,136 @@ fftmech_status equilibrium_impl(fftmech_ctx* ctx, const uint8_t* phase, const T*
   op.E[1] = eps_mac[1];
   op.E[2] = eps_mac[2];
   if (damage) {
-    { ProfScope _ps(ctx, FFTMECH_K_OTHER); CK(launch_degradation<T>(ctx->N, damage, ctx->mat.kappa, (T*)ctx->g, st)); }
+    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_degradation<T>(NB, damage, ctx->mat.kappa, (T*)ctx->g, st));
     op.g = (const T*)ctx->g;
   }
-  Solve<T> s;
-  fftmech_status rc = run_pcg<T, 2>(ctx, op, u, 0.0, 1.0 / (ctx->h * ctx->h), s);
+  Spec2<T> sp{};
+  sp.m0 = 0.0;
+  sp.m1 = 1.0 / (ctx->h * ctx->h);
+  std::vector<Solve> s;
+  rc = run_pcg<T, 2>(ctx, op, u, sp, s);
   if (rc != FFTMECH_OK) return rc;
-  { ProfScope _ps(ctx, FFTMECH_K_OTHER); CK(launch_el_output<T>(op, u, strain, stress, ctx->partials, ctx->results, &ctx->sc->cnt[2], st)); }
+  FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_el_output<T>(op, B, u, strain, stress, ctx->partials, ctx->results, ctx->sc, st));
   if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
-  rc = read_results(ctx, 7);
-  if (rc != FFTMECH_OK) return rc;
-  info->device_ms = solve_timer_ms(ctx);
-  const double* R = ctx->h_results;
+  if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
+  const double ms = solve_timer_ms(ctx);
+  copy_solves(s, info, stride, ms);
   const double N = (double)ctx->N;
-  copy_solve(s, info);
-  for (int k = 0; k < 3; ++k) {
-    info->mean_stress[k] = R[k] / N;
-    info->mean_strain[k] = R[3 + k] / N;
+  for (int b = 0; b < B; ++b) {
+    const double* R = ctx->h_results + b * 7;
+    fftmech_solve_info& i = info_at(info, b, stride);
+    for (int k = 0; k < 3; ++k) {
+      i.mean_stress[k] = R[k] / N;
+      i.mean_strain[k] = R[3 + k] / N;
+    }
+    i.elastic_energy = R[6] * ctx->h * ctx->h;
   }
-  info->elastic_energy = R[6] * ctx->h * ctx->h;
-  return (fftmech_status)s.status;
+  return worst_status(s);
 }
 
 template <typename T>
 fftmech_status diffusion_impl(fftmech_ctx* ctx, const uint8_t* phase, int mode,
                               const double* grad_c_mac, double c_macro, double dt,
                               const uint8_t* mask, double cD, double* c,
-                              fftmech_solve_info* info) {
+                              fftmech_solve_info* info, int stride) {
   cudaStream_t st = ctx->stream;
-  fftmech_status rc0 = solve_timer_start(ctx);
-  if (rc0 != FFTMECH_OK) return rc0;
+  fftmech_status rc = solve_timer_start(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  const int B = ctx->B;
+  const long long NB = ctx->N * B;
   Op2<T> op;
   base_op<T>(ctx, op, phase);
   op.h = ctx->h_diff;
   op.kap[0] = ctx->mat.D_pore;
   op.kap[1] = ctx->mat.D_solid;
   const double ih2 = 1.0 / (ctx->h_diff * ctx->h_diff);
-  Solve<T> s;
-  fftmech_status rc;
+  std::vector<Solve> s;
+  Spec2<T> sp{};
   if (mode == FFTMECH_DIFF_HOMOGENISE) {
     op.G[0] = grad_c_mac[0];
     op.G[1] = grad_c_mac[1];
-    rc = run_pcg<T, 1>(ctx, op, ctx->phi, 0.0, ih2, s);
+    sp.m0 = 0.0;
+    sp.m1 = ih2;
+    rc = run_pcg<T, 1>(ctx, op, ctx->phi, sp, s);
     if (rc != FFTMECH_OK) return rc;
-    { ProfScope _ps(ctx, FFTMECH_K_OTHER); CK(launch_diff_stats<T>(op, ctx->phi, ctx->h_diff, c_macro, ctx->partials, ctx->results,
-                            &ctx->sc->cnt[2], st)); }
-    { ProfScope _ps(ctx, FFTMECH_K_OTHER); CK(launch_diff_write_c(ctx->nx, ctx->ny, phase, ctx->phi, ctx->h_diff, op.G[0], op.G[1],
-                           ctx->results, c, st)); }
+    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials,
+                                                         ctx->results, ctx->sc, st));
+    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_diff_write_c(ctx->nx, ctx->ny, B, phase, ctx->phi, ctx->h_diff,
+                                                        op.G[0], op.G[1], ctx->results, c, st));
     if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
-    rc = read_results(ctx, 5);
-    if (rc != FFTMECH_OK) return rc;
-    info->device_ms = solve_timer_ms(ctx);
-    copy_solve(s, info);
-    info->mean_flux[0] = ctx->h_results[2];
-    info->mean_flux[1] = ctx->h_results[3];
-    info->porosity = ctx->h_results[4];
-    info->mean_c = c_macro;
-    return (fftmech_status)s.status;
+    if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
+    copy_solves(s, info, stride, solve_timer_ms(ctx));
+    for (int b = 0; b < B; ++b) {
+      const double* R = ctx->h_results + b * 5;
+      fftmech_solve_info& i = info_at(info, b, stride);
+      i.mean_flux[0] = R[2];
+      i.mean_flux[1] = R[3];
+      i.porosity = R[4];
+      i.mean_c = c_macro;
+    }
+    return worst_status(s);
   }
   // TRANSIENT (backward Euler, not in the paper)
   if (!(dt > 0)) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "dt must be > 0 for TRANSIENT");
-  { ProfScope _ps(ctx, FFTMECH_K_OTHER); CK(launch_pf_stats(ctx->N, phase, nullptr, ctx->partials, ctx->results, &ctx->sc->cnt[2], st)); }
-  rc = read_results(ctx, 3);
-  if (rc != FFTMECH_OK) return rc;
-  const double eta = 1.0 - ctx->h_results[2] / (double)ctx->N;
-  const double Dbar = eta * ctx->mat.D_pore + (1.0 - eta) * ctx->mat.D_solid;
-  if (mask) {
-    ProfScope _ps(ctx, FFTMECH_K_OTHER);
-    CK(launch_set_masked(ctx->N, mask, cD, c, st));
-  }
-  CK(cudaMemcpyAsync(ctx->cn, c, sizeof(double) * ctx->N, cudaMemcpyDeviceToDevice, st));
+  // per-problem porosity -> mean diffusivity of the preconditioner (on device)
+  FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_pf_stats(ctx->N, B, phase, nullptr, ctx->partials, ctx->results, ctx->sc,
+                                                  ctx->mat.D_pore, ctx->mat.D_solid, ih2, ctx->m1b, st));
+  if (mask) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_set_masked(NB, mask, cD, c, st));
+  CK(cudaMemcpyAsync(ctx->cn, c, sizeof(double) * NB, cudaMemcpyDeviceToDevice, st));
   op.c0c = 1.0 / dt;
   op.srcd = ctx->cn;
   op.src_scale = 1.0 / dt;
   op.mask = mask;
-  rc = run_pcg<T, 1>(ctx, op, c, 1.0 / dt, Dbar * ih2, s);
+  sp.m0 = 1.0 / dt;
+  sp.m1b = ctx->m1b;
+  rc = run_pcg<T, 1>(ctx, op, c, sp, s);
   if (rc != FFTMECH_OK) return rc;
   if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
-  copy_solve(s, info);
-  info->device_ms = solve_timer_ms(ctx);
-  info->porosity = eta;
-  return (fftmech_status)s.status;
+  if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
+  copy_solves(s, info, stride, solve_timer_ms(ctx));
+  for (int b = 0; b < B; ++b)
+    info_at(info, b, stride).porosity = 1.0 - ctx->h_results[b * 3 + 2] / (double)ctx->N;
+  return worst_status(s);
 }
 
 template <typename T>
 fftmech_status phasefield_impl(fftmech_ctx* ctx, const T* strain, const T* eig,
-                               const uint8_t* phase, T* H, double* d, fftmech_solve_info* info) {
+                               const uint8_t* phase, T* H, double* d, fftmech_solve_info* info,
+                               int stride) {
   cudaStream_t st = ctx->stream;
-  fftmech_status rc0 = solve_timer_start(ctx);
-  if (rc0 != FFTMECH_OK) return rc0;
+  fftmech_status rc = solve_timer_start(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  const int B = ctx->B;
   Op2<T> op;
   base_op<T>(ctx, op, phase);
-  { ProfScope _ps(ctx, FFTMECH_K_OTHER); CK(launch_history<T>(ctx->N, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1], strain, eig, H,
-                       ctx->Hd, ctx->partials, ctx->results, &ctx->sc->cnt[2], st)); }
-  fftmech_status rc = read_results(ctx, 1);
-  if (rc != FFTMECH_OK) return rc;
-  const double Hbar = ctx->h_results[0] / (double)ctx->N;
   const double a = ctx->mat.Gc / (2.0 * ctx->mat.l0);
   const double b = ctx->mat.Gc * ctx->mat.l0 / 2.0;
+  // history update; m0b[p] = a + mean(H) of each problem (on device)
+  FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_history<T>(ctx->N, B, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1],
+                                                    strain, eig, H, ctx->Hd, a, ctx->m0b, ctx->partials, ctx->sc, st));
   op.kap[0] = op.kap[1] = b;
   op.c0c = a;
   op.c0f = H;
   op.srcd = ctx->Hd;
   op.src_scale = 1.0;
-  Solve<T> s;
-  rc = run_pcg<T, 1>(ctx, op, d, a + Hbar, b / (ctx->h * ctx->h), s);
+  Spec2<T> sp{};
+  sp.m0b = ctx->m0b;
+  sp.m1 = b / (ctx->h * ctx->h);
+  std::vector<Solve> s;
+  rc = run_pcg<T, 1>(ctx, op, d, sp, s);
   if (rc != FFTMECH_OK) return rc;
-  { ProfScope _ps(ctx, FFTMECH_K_OTHER); CK(launch_pf_stats(ctx->N, phase, d, ctx->partials, ctx->results, &ctx->sc->cnt[2], st)); }
+  FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_pf_stats(ctx->N, B, phase, d, ctx->partials, ctx->results, ctx->sc,
+                                                  0.0, 0.0, 0.0, nullptr, st));
   if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
-  rc = read_results(ctx, 3);
-  if (rc != FFTMECH_OK) return rc;
-  info->device_ms = solve_timer_ms(ctx);
-  copy_solve(s, info);
-  info->total_damage = ctx->h_results[0];
-  info->frac_damaged = ctx->h_results[2] > 0 ? ctx->h_results[1] / ctx->h_results[2] : 0.0;
-  return (fftmech_status)s.status;
+  if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
+  copy_solves(s, info, stride, solve_timer_ms(ctx));
+  for (int p = 0; p < B; ++p) {
+    const double* R = ctx->h_results + p * 3;
+    fftmech_solve_info& i = info_at(info, p, stride);
+    i.total_damage = R[0];
+    i.frac_damaged = R[2] > 0 ? R[1] / R[2] : 0.0;
+  }
+  return worst_status(s);
 }
 
 fftmech_status check_ctx(fftmech_ctx* ctx) {
@@ -550,6 +650,10 @@ fftmech_status fill_lam(fftmech_ctx* ctx) {
   CK(cudaMemcpy(ctx->lamx, lx.data(), sizeof(T) * ctx->nx, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->lamy, ly.data(), sizeof(T) * ctx->ny, cudaMemcpyHostToDevice));
   return FFTMECH_OK;
+}
+
+bool is_hard_error(fftmech_status s) {
+  return s == FFTMECH_ERR_CUDA || s == FFTMECH_ERR_OOM || s == FFTMECH_ERR_INVALID_ARG;
 }
 
 }  // namespace
@@ -573,11 +677,12 @@ const char* fftmech_status_string(int s) {
 
 const char* fftmech_last_error(const fftmech_ctx* ctx) { return ctx ? ctx->err : ""; }
 
-fftmech_status fftmech_create(fftmech_ctx** out, const fftmech_grid* grid,
-                              const fftmech_materials* mat, fftmech_precision precision,
-                              const fftmech_solver_opts* opts, void* stream) {
+fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* grid, int batch,
+                                      const fftmech_materials* mat, fftmech_precision precision,
+                                      const fftmech_solver_opts* opts, void* stream) {
   if (!out || !grid || !mat || !opts) return FFTMECH_ERR_INVALID_ARG;
   *out = nullptr;
+  if (batch < 1) return FFTMECH_ERR_INVALID_ARG;
   if (precision != FFTMECH_FP64 && precision != FFTMECH_MIXED) return FFTMECH_ERR_INVALID_ARG;
   if (grid->dim != 2) return FFTMECH_ERR_UNSUPPORTED_SIZE;
   if (!(grid->h > 0) || !(grid->h_diff > 0)) return FFTMECH_ERR_INVALID_ARG;
@@ -600,6 +705,7 @@ fftmech_status fftmech_create(fftmech_ctx** out, const fftmech_grid* grid,
   ctx->ny = grid->n[1];
   ctx->nz = 1;
   ctx->N = (long long)ctx->nx * ctx->ny;
+  ctx->B = batch;
   ctx->h = grid->h;
   ctx->h_diff = grid->h_diff;
   ctx->mat = *mat;
@@ -625,59 +731,87 @@ fftmech_status fftmech_create(fftmech_ctx** out, const fftmech_grid* grid,
   if (make_plan(ctx->nx, ctx->px) != cudaSuccess || make_plan(ctx->ny, ctx->py) != cudaSuccess)
     return fail(FFTMECH_ERR_OOM);
   const bool fp64 = precision == FFTMECH_FP64;
-  const bool shp = fp64 ? choose_shape<double>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape_d)
-                        : choose_shape<float>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape_f);
+  const bool shp = fp64 ? choose_shape<double>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape)
+                        : choose_shape<float>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape);
   if (!shp) return fail(FFTMECH_ERR_UNSUPPORTED_SIZE);
+  ctx->shape.batch = batch;
   const size_t es = fp64 ? 8 : 4;
-  const size_t N = (size_t)ctx->N;
+  const size_t NB = (size_t)ctx->N * batch;
+  // reduction partials: per problem, one slot group per block of the widest launch
+  const size_t row_tiles = (ctx->ny + ctx->shape.rows_dir - 1) / ctx->shape.rows_dir;
+  const size_t strips = (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;
+  const size_t post_blocks = batch > 1 ? 512 : 4096;
+  const size_t slots = (size_t)batch * std::max(std::max(row_tiles, strips), post_blocks) * 16;
   bool ok = true;
   auto alloc = [&](void** p, size_t bytes) {
     if (!ok) return;
     if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); ok = false; return; }
     if (cudaMemset(*p, 0, bytes) != cudaSuccess) ok = false;
   };
-  alloc(&ctx->r, 2 * N * es);
-  alloc(&ctx->p[0], 2 * N * es);
-  alloc(&ctx->p[1], 2 * N * es);
-  alloc(&ctx->S, 2 * N * es);
-  alloc(&ctx->g, N * es);
-  alloc((void**)&ctx->uh, 2 * N * sizeof(float));
-  alloc((void**)&ctx->ul, 2 * N * sizeof(float));
-  alloc((void**)&ctx->phi, N * 8);
-  alloc((void**)&ctx->Hd, N * 8);
-  alloc((void**)&ctx->cn, N * 8);
+  alloc(&ctx->r, 2 * NB * es);
+  alloc(&ctx->p[0], 2 * NB * es);
+  alloc(&ctx->p[1], 2 * NB * es);
+  alloc(&ctx->S, 2 * NB * es);
+  alloc(&ctx->g, NB * es);
+  alloc((void**)&ctx->uh, 2 * NB * sizeof(float));
+  alloc((void**)&ctx->ul, 2 * NB * sizeof(float));
+  alloc((void**)&ctx->phi, NB * 8);
+  alloc((void**)&ctx->Hd, NB * 8);
+  alloc((void**)&ctx->cn, NB * 8);
   alloc(&ctx->lamx, ctx->nx * es);
   alloc(&ctx->lamy, ctx->ny * es);
-  alloc((void**)&ctx->partials, (size_t)kMaxBlocks * kPartialSlots * 8);
-  alloc((void**)&ctx->results, 64 * 8);
-  alloc((void**)&ctx->sc, sizeof(SolverScalars));
+  alloc((void**)&ctx->partials, slots * 8);
+  alloc((void**)&ctx->results, (size_t)kResultsPerProblem * batch * 8);
+  alloc((void**)&ctx->m0b, (size_t)batch * 8);
+  alloc((void**)&ctx->m1b, (size_t)batch * 8);
+  alloc((void**)&ctx->mode, (size_t)batch * sizeof(int));
+  alloc((void**)&ctx->sc, sizeof(SolverScalars) * batch);
   if (!ok) return fail(FFTMECH_ERR_OOM);
-  if (cudaMallocHost((void**)&ctx->h_sc, sizeof(SolverScalars)) != cudaSuccess) return fail(FFTMECH_ERR_OOM);
+  if (cudaMallocHost((void**)&ctx->h_sc, sizeof(SolverScalars) * batch) != cudaSuccess) return fail(FFTMECH_ERR_OOM);
+  if (cudaMallocHost((void**)&ctx->h_results, (size_t)kResultsPerProblem * batch * 8) != cudaSuccess)
+    return fail(FFTMECH_ERR_OOM);
+  ctx->h_mode = new (std::nothrow) int[batch];
+  if (!ctx->h_mode) return fail(FFTMECH_ERR_OOM);
+  if (cudaMallocHost((void**)&ctx->h_mode_ring, sizeof(int) * batch * fftmech_ctx::kModeSlots) != cudaSuccess)
+    return fail(FFTMECH_ERR_OOM);
+  for (int k = 0; k < fftmech_ctx::kModeSlots; ++k)
+    if (cudaEventCreateWithFlags(&ctx->mode_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(FFTMECH_ERR_CUDA);
   if (cudaEventCreate(&ctx->solve_ev[0]) != cudaSuccess || cudaEventCreate(&ctx->solve_ev[1]) != cudaSuccess)
     return fail(FFTMECH_ERR_CUDA);
-  if (cudaMallocHost((void**)&ctx->h_results, 64 * 8) != cudaSuccess) return fail(FFTMECH_ERR_OOM);
   fftmech_status rc = fp64 ? fill_lam<double>(ctx) : fill_lam<float>(ctx);
   if (rc != FFTMECH_OK) return fail(rc);
   *out = ctx;
   return FFTMECH_OK;
 }
 
+fftmech_status fftmech_create(fftmech_ctx** out, const fftmech_grid* grid,
+                              const fftmech_materials* mat, fftmech_precision precision,
+                              const fftmech_solver_opts* opts, void* stream) {
+  return fftmech_create_batched(out, grid, 1, mat, precision, opts, stream);
+}
+
 fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
   if (!ctx) return FFTMECH_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  void* bufs[] = {ctx->r, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd, ctx->cn,
-                  ctx->lamx, ctx->lamy, ctx->partials, ctx->results, ctx->sc};
+  void* bufs[] = {ctx->r, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
+                  ctx->cn, ctx->lamx, ctx->lamy, ctx->partials, ctx->results, ctx->m0b, ctx->m1b,
+                  ctx->mode, ctx->sc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < ST_COUNT; ++i)
     if (ctx->stage[i].dev) cudaFree(ctx->stage[i].dev);
   if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
+  if (ctx->h_results) cudaFreeHost(ctx->h_results);
+  delete[] ctx->h_mode;
+  if (ctx->h_mode_ring) cudaFreeHost(ctx->h_mode_ring);
+  for (cudaEvent_t e : ctx->mode_ev)
+    if (e) cudaEventDestroy(e);
   for (auto& pe : ctx->pending) { ctx->ev_free.push_back(pe.a); ctx->ev_free.push_back(pe.b); }
   for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->solve_ev)
     if (e) cudaEventDestroy(e);
-  if (ctx->h_results) cudaFreeHost(ctx->h_results);
   free_plan(ctx->px);
   free_plan(ctx->py);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -693,14 +827,16 @@ fftmech_status fftmech_set_solver_opts(fftmech_ctx* ctx, const fftmech_solver_op
   return FFTMECH_OK;
 }
 
+int fftmech_batch_size(const fftmech_ctx* ctx) { return ctx ? ctx->B : 0; }
+
 fftmech_status fftmech_equilibrium_solve(fftmech_ctx* ctx, const uint8_t* phase, const void* eig,
                                          const double* damage, const double eps_mac[6], double* u,
                                          void* strain, void* stress, fftmech_solve_info* info) {
   fftmech_status rc = check_ctx(ctx);
   if (rc != FFTMECH_OK) return rc;
   if (!phase || !eps_mac || !u || !info) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
-  fill_info_defaults(info);
-  const size_t N = (size_t)ctx->N, es = esize(ctx), nv = nvoigt(ctx);
+  std::memset(info, 0, sizeof(fftmech_solve_info) * ctx->B);
+  const size_t N = (size_t)ctx->N * ctx->B, es = esize(ctx), nv = nvoigt(ctx);
   void *dphase, *deig, *ddmg, *du, *dstrain, *dstress;
   if ((rc = stage_in(ctx, ST_PHASE, phase, N, true, &dphase)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_EIG, eig, N * es, true, &deig)) != FFTMECH_OK) return rc;
@@ -710,14 +846,12 @@ fftmech_status fftmech_equilibrium_solve(fftmech_ctx* ctx, const uint8_t* phase,
   if ((rc = stage_in(ctx, ST_STRESS, stress, nv * N * es, false, &dstress)) != FFTMECH_OK) return rc;
   fftmech_status s;
   if (ctx->prec == FFTMECH_FP64)
-    s = equilibrium_impl<double>(ctx, (const uint8_t*)dphase, (const double*)deig,
-                                 (const double*)ddmg, eps_mac, (double*)du, (double*)dstrain,
-                                 (double*)dstress, info);
+    s = equilibrium_impl<double>(ctx, (const uint8_t*)dphase, (const double*)deig, (const double*)ddmg,
+                                 eps_mac, (double*)du, (double*)dstrain, (double*)dstress, info, 1);
   else
-    s = equilibrium_impl<float>(ctx, (const uint8_t*)dphase, (const float*)deig,
-                                (const double*)ddmg, eps_mac, (double*)du, (float*)dstrain,
-                                (float*)dstress, info);
-  if (s == FFTMECH_ERR_CUDA || s == FFTMECH_ERR_OOM || s == FFTMECH_ERR_INVALID_ARG) return s;
+    s = equilibrium_impl<float>(ctx, (const uint8_t*)dphase, (const float*)deig, (const double*)ddmg,
+                                eps_mac, (double*)du, (float*)dstrain, (float*)dstress, info, 1);
+  if (is_hard_error(s)) return s;
   if ((rc = stage_out(ctx, u, du, 2 * N * 8)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, strain, dstrain, nv * N * es)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, stress, dstress, nv * N * es)) != FFTMECH_OK) return rc;
@@ -736,8 +870,8 @@ fftmech_status fftmech_diffusion_step(fftmech_ctx* ctx, const uint8_t* phase, in
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "diffusion mode %d", mode);
   if (mode == FFTMECH_DIFF_HOMOGENISE && !grad_c_mac)
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "grad_c_mac is required");
-  fill_info_defaults(info);
-  const size_t N = (size_t)ctx->N;
+  std::memset(info, 0, sizeof(fftmech_solve_info) * ctx->B);
+  const size_t N = (size_t)ctx->N * ctx->B;
   void *dphase, *dc, *dmask = nullptr;
   if ((rc = stage_in(ctx, ST_PHASE, phase, N, true, &dphase)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_C, c, N * 8, mode == FFTMECH_DIFF_TRANSIENT, &dc)) != FFTMECH_OK) return rc;
@@ -747,12 +881,12 @@ fftmech_status fftmech_diffusion_step(fftmech_ctx* ctx, const uint8_t* phase, in
   const double zero[3] = {0, 0, 0};
   fftmech_status s;
   if (ctx->prec == FFTMECH_FP64)
-    s = diffusion_impl<double>(ctx, (const uint8_t*)dphase, mode, grad_c_mac ? grad_c_mac : zero,
-                               c_macro, dt, (const uint8_t*)dmask, dirichlet_value, (double*)dc, info);
+    s = diffusion_impl<double>(ctx, (const uint8_t*)dphase, mode, grad_c_mac ? grad_c_mac : zero, c_macro, dt,
+                               (const uint8_t*)dmask, dirichlet_value, (double*)dc, info, 1);
   else
-    s = diffusion_impl<float>(ctx, (const uint8_t*)dphase, mode, grad_c_mac ? grad_c_mac : zero,
-                              c_macro, dt, (const uint8_t*)dmask, dirichlet_value, (double*)dc, info);
-  if (s == FFTMECH_ERR_CUDA || s == FFTMECH_ERR_OOM || s == FFTMECH_ERR_INVALID_ARG) return s;
+    s = diffusion_impl<float>(ctx, (const uint8_t*)dphase, mode, grad_c_mac ? grad_c_mac : zero, c_macro, dt,
+                              (const uint8_t*)dmask, dirichlet_value, (double*)dc, info, 1);
+  if (is_hard_error(s)) return s;
   if ((rc = stage_out(ctx, c, dc, N * 8)) != FFTMECH_OK) return rc;
   CK(cudaStreamSynchronize(ctx->stream));
   return s;
@@ -765,8 +899,8 @@ fftmech_status fftmech_phasefield_solve(fftmech_ctx* ctx, const void* strain, co
   if (rc != FFTMECH_OK) return rc;
   if (!strain || !phase || !H || !damage || !info)
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
-  fill_info_defaults(info);
-  const size_t N = (size_t)ctx->N, es = esize(ctx), nv = nvoigt(ctx);
+  std::memset(info, 0, sizeof(fftmech_solve_info) * ctx->B);
+  const size_t N = (size_t)ctx->N * ctx->B, es = esize(ctx), nv = nvoigt(ctx);
   void *dstrain, *deig, *dphase, *dH, *dd;
   if ((rc = stage_in(ctx, ST_STRAIN, strain, nv * N * es, true, &dstrain)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_EIG, eig, N * es, true, &deig)) != FFTMECH_OK) return rc;
@@ -775,12 +909,12 @@ fftmech_status fftmech_phasefield_solve(fftmech_ctx* ctx, const void* strain, co
   if ((rc = stage_in(ctx, ST_DAMAGE, damage, N * 8, true, &dd)) != FFTMECH_OK) return rc;
   fftmech_status s;
   if (ctx->prec == FFTMECH_FP64)
-    s = phasefield_impl<double>(ctx, (const double*)dstrain, (const double*)deig,
-                                (const uint8_t*)dphase, (double*)dH, (double*)dd, info);
+    s = phasefield_impl<double>(ctx, (const double*)dstrain, (const double*)deig, (const uint8_t*)dphase,
+                                (double*)dH, (double*)dd, info, 1);
   else
-    s = phasefield_impl<float>(ctx, (const float*)dstrain, (const float*)deig,
-                               (const uint8_t*)dphase, (float*)dH, (double*)dd, info);
-  if (s == FFTMECH_ERR_CUDA || s == FFTMECH_ERR_OOM || s == FFTMECH_ERR_INVALID_ARG) return s;
+    s = phasefield_impl<float>(ctx, (const float*)dstrain, (const float*)deig, (const uint8_t*)dphase,
+                               (float*)dH, (double*)dd, info, 1);
+  if (is_hard_error(s)) return s;
   if ((rc = stage_out(ctx, H, dH, N * es)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, damage, dd, N * 8)) != FFTMECH_OK) return rc;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -788,7 +922,7 @@ fftmech_status fftmech_phasefield_solve(fftmech_ctx* ctx, const void* strain, co
 }
 
 fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
-                                      const fftmech_step_params* prm, fftmech_solve_info info[3]) {
+                                      const fftmech_step_params* prm, fftmech_solve_info* info) {
   fftmech_status rc = check_ctx(ctx);
   if (rc != FFTMECH_OK) return rc;
   if (!state || !prm || !info || !state->phase || !state->c || !state->eig || !state->u ||
@@ -796,10 +930,9 @@ fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
   if (prm->eig_mode == FFTMECH_EIG_PRESCRIBED && !prm->eig_field)
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "eig_field is required for PRESCRIBED");
-  for (int i = 0; i < 3; ++i) fill_info_defaults(&info[i]);
-  const size_t N = (size_t)ctx->N, es = esize(ctx), nv = nvoigt(ctx);
+  std::memset(info, 0, sizeof(fftmech_solve_info) * 3 * ctx->B);
+  const size_t N = (size_t)ctx->N * ctx->B, es = esize(ctx), nv = nvoigt(ctx);
   cudaStream_t st = ctx->stream;
-  // stage everything once for the whole step
   void *dphase, *dc, *dcppt, *deig, *du, *dstrain, *dstress, *dH, *dd, *dmask = nullptr, *deigf = nullptr;
   if ((rc = stage_in(ctx, ST_PHASE, state->phase, N, true, &dphase)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_C, state->c, N * 8, true, &dc)) != FFTMECH_OK) return rc;
@@ -826,47 +959,47 @@ fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
     fftmech_status s = fp64
         ? diffusion_impl<double>(ctx, (const uint8_t*)dphase, prm->diffusion_mode, prm->grad_c_mac,
                                  prm->c_macro, prm->dt, (const uint8_t*)dmask, prm->dirichlet_value,
-                                 (double*)dc, &info[0])
+                                 (double*)dc, info + 0, 3)
         : diffusion_impl<float>(ctx, (const uint8_t*)dphase, prm->diffusion_mode, prm->grad_c_mac,
                                 prm->c_macro, prm->dt, (const uint8_t*)dmask, prm->dirichlet_value,
-                                (double*)dc, &info[0]);
-    if (s == FFTMECH_ERR_CUDA || s == FFTMECH_ERR_OOM || s == FFTMECH_ERR_INVALID_ARG) return s;
+                                (double*)dc, info + 0, 3);
+    if (is_hard_error(s)) return s;
     track(s);
   }
   // 2. precipitation and eigenstrain
   if (prm->eig_mode == FFTMECH_EIG_FROM_PRECIPITATE) {
     ProfScope _ps(ctx, FFTMECH_K_OTHER);
     if (fp64)
-      CK(launch_precipitate<double>(ctx->N, (const uint8_t*)dphase, (const double*)dc, ctx->mat.S_sol,
+      CK(launch_precipitate<double>(N, (const uint8_t*)dphase, (const double*)dc, ctx->mat.S_sol,
                                     ctx->mat.M_ppt, (double*)dcppt, (double*)deig, st));
     else
-      CK(launch_precipitate<float>(ctx->N, (const uint8_t*)dphase, (const double*)dc, ctx->mat.S_sol,
+      CK(launch_precipitate<float>(N, (const uint8_t*)dphase, (const double*)dc, ctx->mat.S_sol,
                                    ctx->mat.M_ppt, (float*)dcppt, (float*)deig, st));
   } else {
     ProfScope _ps(ctx, FFTMECH_K_OTHER);
     if (fp64)
-      CK(launch_scale_copy<double>(ctx->N, (const double*)deigf, prm->eig_scale, (double*)deig, st));
+      CK(launch_scale_copy<double>(N, (const double*)deigf, prm->eig_scale, (double*)deig, st));
     else
-      CK(launch_scale_copy<float>(ctx->N, (const float*)deigf, prm->eig_scale, (float*)deig, st));
+      CK(launch_scale_copy<float>(N, (const float*)deigf, prm->eig_scale, (float*)deig, st));
   }
   // 3. equilibrium with the stiffness degraded by the current damage
   {
     fftmech_status s = fp64
         ? equilibrium_impl<double>(ctx, (const uint8_t*)dphase, (const double*)deig, (const double*)dd,
-                                   prm->eps_mac, (double*)du, (double*)dstrain, (double*)dstress, &info[1])
+                                   prm->eps_mac, (double*)du, (double*)dstrain, (double*)dstress, info + 1, 3)
         : equilibrium_impl<float>(ctx, (const uint8_t*)dphase, (const float*)deig, (const double*)dd,
-                                  prm->eps_mac, (double*)du, (float*)dstrain, (float*)dstress, &info[1]);
-    if (s == FFTMECH_ERR_CUDA || s == FFTMECH_ERR_OOM || s == FFTMECH_ERR_INVALID_ARG) return s;
+                                  prm->eps_mac, (double*)du, (float*)dstrain, (float*)dstress, info + 1, 3);
+    if (is_hard_error(s)) return s;
     track(s);
   }
   // 4. history and phase field
   {
     fftmech_status s = fp64
         ? phasefield_impl<double>(ctx, (const double*)dstrain, (const double*)deig, (const uint8_t*)dphase,
-                                  (double*)dH, (double*)dd, &info[2])
+                                  (double*)dH, (double*)dd, info + 2, 3)
         : phasefield_impl<float>(ctx, (const float*)dstrain, (const float*)deig, (const uint8_t*)dphase,
-                                 (float*)dH, (double*)dd, &info[2]);
-    if (s == FFTMECH_ERR_CUDA || s == FFTMECH_ERR_OOM || s == FFTMECH_ERR_INVALID_ARG) return s;
+                                 (float*)dH, (double*)dd, info + 2, 3);
+    if (is_hard_error(s)) return s;
     track(s);
   }
   if ((rc = stage_out(ctx, state->c, dc, N * 8)) != FFTMECH_OK) return rc;
@@ -946,13 +1079,13 @@ fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse,
       e = launch_rowfft_f<double>(px.fam, nx, ny, (cx<double>*)data, dev_plan<double>(px), inverse, sh, st);
       if (e == cudaSuccess && ny > 1)
         e = launch_colpass_f<double>(py.fam, nx, ny, (cx<double>*)data, dev_plan<double>(py), sp, sh, COL_PLAIN,
-                                   inverse, nullptr, nullptr, st);
+                                   inverse, nullptr, nullptr, nullptr, st);
     } else {
       Spec2<float> sp{};
       e = launch_rowfft_f<float>(px.fam, nx, ny, (cx<float>*)data, dev_plan<float>(px), inverse, sh, st);
       if (e == cudaSuccess && ny > 1)
         e = launch_colpass_f<float>(py.fam, nx, ny, (cx<float>*)data, dev_plan<float>(py), sp, sh, COL_PLAIN,
-                                  inverse, nullptr, nullptr, st);
+                                  inverse, nullptr, nullptr, nullptr, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = FFTMECH_ERR_CUDA;

@@ -68,7 +68,7 @@ cudaError_t run(HostPlan& px, HostPlan& py, int inverse, void* data, int nsm, si
   if (e == cudaSuccess && ny > 1) {
     Spec2<T> sp{};
     e = launch_colpass_f<T>(py.fam, nx, ny, (cx<T>*)data, dev_plan<T>(py), sp, sh, COL_PLAIN, inverse,
-                            nullptr, nullptr, st);
+                            nullptr, nullptr, nullptr, st);
   }
   return e;
 }

@@ -169,6 +169,40 @@ __device__ __forceinline__ void g2s(E* __restrict__ dst, const E* __restrict__ s
   }
 }
 
+// Contiguous global -> shared copy with 16-byte vector loads (U in flight
+// per thread): a misaligned head and the tail are copied element by element.
+// RO: the source is not written during the kernel (read-only data path).
+template <int U, bool RO, typename E>
+__device__ __forceinline__ void g2s_vec(E* __restrict__ dst, const E* __restrict__ src, int n) {
+  constexpr int PER = 16 / (int)sizeof(E);
+  if constexpr (PER <= 1) {
+    g2s<U>(dst, src, n);
+  } else {
+    const int mis = (int)((reinterpret_cast<uintptr_t>(src) / sizeof(E)) % PER);
+    const int head = min(n, (PER - mis) % PER);
+    const int nv = (n - head) / PER;
+    const int bd = blockDim.x;
+    for (int i = threadIdx.x; i < head; i += bd) dst[i] = src[i];
+    const int tail0 = head + nv * PER;
+    for (int i = tail0 + threadIdx.x; i < n; i += bd) dst[i] = src[i];
+    const int4* s4 = reinterpret_cast<const int4*>(src + head);
+    E* d = dst + head;
+    for (int i = threadIdx.x; i < nv; i += U * bd) {
+      int4 v[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (i + k * bd < nv) v[k] = RO ? __ldg(s4 + i + k * bd) : s4[i + k * bd];
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (i + k * bd < nv) {
+          const E* e = reinterpret_cast<const E*>(&v[k]);
+#pragma unroll
+          for (int j = 0; j < PER; ++j) d[(i + k * bd) * PER + j] = e[j];
+        }
+    }
+  }
+}
+
 // Rows ys .. ys + W - 1 (periodic in ny) of a [ny][nx] field into dst[W][nx].
 template <int U, typename E>
 __device__ __forceinline__ void g2s_rows(E* dst, const E* __restrict__ src, int ys, int W, int nx,
@@ -177,7 +211,7 @@ __device__ __forceinline__ void g2s_rows(E* dst, const E* __restrict__ src, int 
   int done = 0;
   while (done < W) {
     const int run = min(W - done, ny - y);
-    g2s<U>(dst + (size_t)done * nx, src + (size_t)y * nx, run * nx);
+    g2s_vec<U, true>(dst + (size_t)done * nx, src + (size_t)y * nx, run * nx);
     done += run;
     y = 0;
   }

@@ -73,8 +73,32 @@ struct Vec2 {
   T* p_out;       // new direction
   cx<T>* S;       // spectral rows, N complex (components packed re / im)
   double* partials;
-  SolverScalars* sc;
+  SolverScalars* sc;  // one per problem of the batch
+  const int* mode;    // per problem: 0 normal, 1 reliable update, 2 restart (NULL = all 0)
 };
+
+// Problems of a uniform batch sit back to back: problem b's scalar fields at
+// b N, its d-component fields at b d N, its spectrum at b N, its scalars at
+// sc + b; launches put the problem index in blockIdx.y.
+template <typename T, int D>
+__device__ __forceinline__ void problem_views(Op2<T>& op, Vec2<T>& v, int b, size_t N) {
+  const size_t o1 = (size_t)b * N, oD = (size_t)b * D * N;
+  op.phase += o1;
+  if (op.g) op.g += o1;
+  if (op.eig) op.eig += o1;
+  if (op.c0f) op.c0f += o1;
+  if (op.mask) op.mask += o1;
+  if (op.srcd) op.srcd += o1;
+  if (op.srct) op.srct += o1;
+  if (v.u) v.u += oD;
+  if (v.uh) v.uh += oD;
+  if (v.ul) v.ul += oD;
+  v.r += oD;
+  if (v.p_in) v.p_in += oD;
+  if (v.p_out) v.p_out += oD;
+  v.S += o1;
+  v.sc += b;
+}
 
 // Fourier multiplier 1 / (m0 + m1 lambda(k)), lambda = lamx[kx] + lamy[ky]
 // (the symbol of grad+^T grad+); 0 where the denominator is 0 (k = 0 when
@@ -85,10 +109,13 @@ struct Spec2 {
   const T* lamy;
   double m0, m1;
   double invN;
+  const double* m0b;  // per-problem m0 (NULL = m0 for all)
+  const double* m1b;  // per-problem m1 (NULL = m1 for all)
 };
 
 // Launch shapes chosen by the host.
 struct Shape2 {
+  int batch;  // problems of a uniform batch (grid.y of the solver kernels)
   int rows_update, threads_update;
   int rows_dir, threads_dir;
   int rows_res, threads_res;
@@ -101,17 +128,17 @@ struct Shape2 {
 // that of the y transform (FY); see RadixFamily.
 template <typename T, int D, int FX>
 cudaError_t launch_residual(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
-                            const Shape2& sh, int zero_u, cudaStream_t st);
+                            const Shape2& sh, int zero_u, int filter, cudaStream_t st);
 template <typename T, int D, int FX>
 cudaError_t launch_update(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
-                          const Shape2& sh, int u_only, cudaStream_t st);
+                          const Shape2& sh, cudaStream_t st);
 template <typename T, int D, int FX>
 cudaError_t launch_direction(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                              const Shape2& sh, cudaStream_t st);
 template <typename T, int FY>
 cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec2<T>& sp,
                            const Shape2& sh, int mode, int inverse, double* partials,
-                           SolverScalars* sc, cudaStream_t st);
+                           SolverScalars* sc, const int* pmode, cudaStream_t st);
 template <typename T, int FX>
 cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int inverse,
                           const Shape2& sh, cudaStream_t st);
@@ -127,16 +154,15 @@ cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int
 template <typename T, int D>
 inline cudaError_t launch_residual_f(int fx, const Op2<T>& op, const Vec2<T>& v,
                                      const FftPlanDev<T>& px, const Shape2& sh, int zero_u,
-                                     cudaStream_t st) {
-#define FFTMECH_C(F) launch_residual<T, D, F>(op, v, px, sh, zero_u, st)
+                                     int filter, cudaStream_t st) {
+#define FFTMECH_C(F) launch_residual<T, D, F>(op, v, px, sh, zero_u, filter, st)
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
 template <typename T, int D>
 inline cudaError_t launch_update_f(int fx, const Op2<T>& op, const Vec2<T>& v,
-                                   const FftPlanDev<T>& px, const Shape2& sh, int u_only,
-                                   cudaStream_t st) {
-#define FFTMECH_C(F) launch_update<T, D, F>(op, v, px, sh, u_only, st)
+                                   const FftPlanDev<T>& px, const Shape2& sh, cudaStream_t st) {
+#define FFTMECH_C(F) launch_update<T, D, F>(op, v, px, sh, st)
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
@@ -150,8 +176,9 @@ inline cudaError_t launch_direction_f(int fx, const Op2<T>& op, const Vec2<T>& v
 template <typename T>
 inline cudaError_t launch_colpass_f(int fy, int nx, int ny, cx<T>* S, const FftPlanDev<T>& py,
                                     const Spec2<T>& sp, const Shape2& sh, int mode, int inverse,
-                                    double* partials, SolverScalars* sc, cudaStream_t st) {
-#define FFTMECH_C(F) launch_colpass<T, F>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, st)
+                                    double* partials, SolverScalars* sc, const int* pmode,
+                                    cudaStream_t st) {
+#define FFTMECH_C(F) launch_colpass<T, F>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st)
   FFTMECH_FAMILY_SWITCH(fy, FFTMECH_C)
 #undef FFTMECH_C
 }
@@ -163,24 +190,25 @@ inline cudaError_t launch_rowfft_f(int fx, int nx, int ny, cx<T>* S, const FftPl
 #undef FFTMECH_C
 }
 
-// Post-processing and pointwise kernels (2D).
+// Post-processing and pointwise kernels (2D); `batch` problems (grid.y).
 template <typename T>
-cudaError_t launch_el_output(const Op2<T>& op, const double* u, T* strain, T* stress,
-                             double* partials, double* results, unsigned int* cnt,
-                             cudaStream_t st);
+cudaError_t launch_el_output(const Op2<T>& op, int batch, const double* u, T* strain, T* stress,
+                             double* partials, double* results, SolverScalars* sc, cudaStream_t st);
 template <typename T>
-cudaError_t launch_diff_stats(const Op2<T>& op, const double* phi, double hdiff, double c_macro,
-                              double* partials, double* results, unsigned int* cnt,
+cudaError_t launch_diff_stats(const Op2<T>& op, int batch, const double* phi, double hdiff,
+                              double c_macro, double* partials, double* results, SolverScalars* sc,
                               cudaStream_t st);
-cudaError_t launch_diff_write_c(int nx, int ny, const uint8_t* phase, const double* phi,
+cudaError_t launch_diff_write_c(int nx, int ny, int batch, const uint8_t* phase, const double* phi,
                                 double hdiff, double G0, double G1, const double* beta_dev,
                                 double* c, cudaStream_t st);
 template <typename T>
-cudaError_t launch_history(long long N, const uint8_t* phase, double lam0, double lam1, double mu0,
-                           double mu1, const T* strain, const T* eig, T* H, double* Hd,
-                           double* partials, double* results, unsigned int* cnt, cudaStream_t st);
-cudaError_t launch_pf_stats(long long N, const uint8_t* phase, const double* d, double* partials,
-                            double* results, unsigned int* cnt, cudaStream_t st);
+cudaError_t launch_history(long long N, int batch, const uint8_t* phase, double lam0, double lam1,
+                           double mu0, double mu1, const T* strain, const T* eig, T* H, double* Hd,
+                           double a, double* m0b, double* partials, SolverScalars* sc,
+                           cudaStream_t st);
+cudaError_t launch_pf_stats(long long N, int batch, const uint8_t* phase, const double* d,
+                            double* partials, double* results, SolverScalars* sc, double Dp,
+                            double Ds, double ih2, double* m1b, cudaStream_t st);
 template <typename T>
 cudaError_t launch_degradation(long long N, const double* d, double kappa, T* g, cudaStream_t st);
 template <typename T>

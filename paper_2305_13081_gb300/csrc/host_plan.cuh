@@ -130,6 +130,7 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   int R = std::max(1, std::min(ny, ny / (2 * nsm)));
   while (R > 1 && !fits(R, budget)) --R;
   if (!fits(R, optin)) return false;
+  s.batch = 1;
   s.rows_update = R;
   s.rows_dir = R;
   s.threads_update = std::min(tmax, std::max(256, round32(need_threads(px, R + 1))));
@@ -160,6 +161,7 @@ bool choose_shape_fft(const HostPlan& px, const HostPlan& py, int nsm, size_t op
   };
   while (R > 1 && !fits(R)) --R;
   if (!fits(R)) return false;
+  s.batch = 1;
   s.rows_update = s.rows_dir = R;
   s.threads_update = s.threads_dir = s.threads_plain =
       std::min(tmax, std::max(128, round32(need_threads(px, R))));

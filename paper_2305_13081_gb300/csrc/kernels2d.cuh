@@ -85,10 +85,14 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
 // voxels), written as T and row-transformed into S. Shared memory:
 // [max(D (R+2) doubles, 2 R T) per column] + [3 (R+1) doubles per column].
 template <typename T, int D, int FX>
-__global__ void FFTMECH_BOUNDS(T) k_residual(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int zero_u) {
+__global__ void FFTMECH_BOUNDS(T) k_residual(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int zero_u,
+                                             int filter) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
+  const int bp = blockIdx.y;
+  if (filter && !(v.mode && v.mode[bp] != 0)) return;  // only problems being replaced / restarted
+  problem_views<T, D>(op, v, bp, N);
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
   const int W = rows + 2;
@@ -183,13 +187,16 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op2<T> op, Vec2<T> v, FftPlanDev<T>
 // reaction field, mask) is staged into shared memory first with many loads in
 // flight; the stencil then runs out of shared memory (layout UpdLayout).
 template <typename T, int D, int FX>
-__global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int u_only) {
+__global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R) {
+  const int nx = op.nx, ny = op.ny;
+  const size_t N = (size_t)nx * ny;
+  const int bp = blockIdx.y;
+  const int u_only = v.mode ? (v.mode[bp] == 1) : 0;  // reliable update: iterate only
+  problem_views<T, D>(op, v, bp, N);
   if (done_flag(v.sc)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const double alpha = vol_read(&v.sc->alpha);
   const T a = (T)alpha;
-  const int nx = op.nx, ny = op.ny;
-  const size_t N = (size_t)nx * ny;
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
   const int tid = threadIdx.x, bd = blockDim.x;
@@ -230,11 +237,11 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> p
 #pragma unroll
   for (int c = 0; c < D; ++c) g2s_rows<8>(P + (size_t)c * W * nx, v.p_in + c * N, y0 - 1, W, nx, ny);
 #pragma unroll
-  for (int c = 0; c < D; ++c) g2s<8>(RS + (size_t)c * rows * nx, v.r + c * N + t0, rows * nx);
+  for (int c = 0; c < D; ++c) g2s_vec<8, false>(RS + (size_t)c * rows * nx, v.r + c * N + t0, rows * nx);
   if (matg) g2s_rows<8>(MG, matg, y0 - 1, rows + 1, nx, ny);
   g2s_rows<8>(PH, op.phase, y0 - 1, rows + 1, nx, ny);
   const bool masked = (D == 1) && op.mask;
-  if (masked) g2s<8>(MK, op.mask + t0, rows * nx);
+  if (masked) g2s_vec<8, true>(MK, op.mask + t0, rows * nx);
   __syncthreads();
   // iterate update on the tile rows (rows 1 .. rows of P)
   if constexpr (sizeof(T) == 4) {
@@ -317,13 +324,16 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> p
 // <p, K p> = sum of the energy density over the tile (layout DirLayout).
 template <typename T, int D, int FX>
 __global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R) {
+  const int nx = op.nx, ny = op.ny;
+  const size_t N = (size_t)nx * ny;
+  const int bp = blockIdx.y;
+  problem_views<T, D>(op, v, bp, N);
   if (done_flag(v.sc)) return;
+  double* partials = v.partials + (size_t)bp * gridDim.x;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   const double beta = vol_read(&v.sc->beta);
   const T b = (T)beta;
-  const int nx = op.nx, ny = op.ny;
-  const size_t N = (size_t)nx * ny;
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
   const int W = rows + 1;
@@ -342,8 +352,8 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T
 #pragma unroll
     for (int c = 0; c < D; ++c) g2s_rows<8>(P + (size_t)c * W * nx, v.p_in + c * N, y0, W, nx, ny);
   }
-  if (matg) g2s<8>(MG, matg + t0, rows * nx);
-  g2s<8>(PH, op.phase + t0, rows * nx);
+  if (matg) g2s_vec<8, true>(MG, matg + t0, rows * nx);
+  g2s_vec<8, true>(PH, op.phase + t0, rows * nx);
   if (masked) g2s_rows<8>(MK, op.mask, y0, W, nx, ny);
   __syncthreads();
   fft_lines<T, 1, FX>(F, px, W, nx, 1, false);
@@ -399,9 +409,9 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T
     acc[0] += (double)part;
   }
   block_sum<1>(acc, red);
-  if (publish_partials<1>(acc, v.partials, &v.sc->cnt[0])) {
+  if (publish_partials<1>(acc, partials, &v.sc->cnt[0])) {
     double tot[1];
-    gather_partials<1>(tot, v.partials, &v.sc->cnt[0], red);
+    gather_partials<1>(tot, partials, &v.sc->cnt[0], red);
     if (threadIdx.x == 0) finalize_direction(v.sc, tot[0]);
   }
 }
@@ -413,8 +423,17 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T
 // column FFT. COL_PLAIN: one column FFT only (sign from `inverse`).
 template <typename T, int FY>
 __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev<T> py, Spec2<T> sp, int CW,
-                                            int mode, int inverse, double* partials, SolverScalars* sc) {
-  if (mode != COL_PLAIN && mode != COL_NORM && mode != COL_TRUENORM && done_flag(sc)) return;
+                                            int mode, int inverse, double* partials, SolverScalars* sc,
+                                            const int* pmode) {
+  const int bp = blockIdx.y;
+  S += (size_t)bp * nx * ny;
+  if (sc) sc += bp;
+  if (partials) partials += (size_t)bp * gridDim.x;
+  if (mode == COL_ITER && pmode && pmode[bp] == 1) mode = COL_TRUE;  // reliable update of this problem
+  if (mode == COL_RESTART && !(pmode && pmode[bp] == 2)) return;      // only restarting problems
+  if (mode != COL_PLAIN && mode != COL_NORM && mode != COL_TRUENORM && mode != COL_RESTART &&
+      done_flag(sc))
+    return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   cx<T>* B = reinterpret_cast<cx<T>*>(smem);
@@ -448,7 +467,8 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   const bool store = (mode != COL_NORM && mode != COL_TRUENORM);
   double acc[1] = {0.0};
   if (mode != COL_PLAIN) {
-    const T m0 = (T)sp.m0, m1 = (T)sp.m1, invN = (T)sp.invN;
+    const T m0 = (T)(sp.m0b ? sp.m0b[bp] : sp.m0), m1 = (T)(sp.m1b ? sp.m1b[bp] : sp.m1);
+    const T invN = (T)sp.invN;
     T part = T(0);
     int cnt = 0;
     for (int i = threadIdx.x; i < n; i += bd) {
@@ -520,27 +540,27 @@ static cudaError_t set_smem(K kernel, size_t bytes, int& configured) {
 
 template <typename T, int D, int FX>
 cudaError_t launch_residual(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
-                            const Shape2& sh, int zero_u, cudaStream_t st) {
+                            const Shape2& sh, int zero_u, int filter, cudaStream_t st) {
   const int R = sh.rows_res;
   const size_t sm = smem_residual<T, D>(op.nx, R);
   static int cfg = 0;
   cudaError_t e = set_smem(k_residual<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
-  const int grid = (op.ny + R - 1) / R;
-  k_residual<T, D, FX><<<grid, sh.threads_res, sm, st>>>(op, v, px, R, zero_u);
+  const dim3 grid((op.ny + R - 1) / R, sh.batch);
+  k_residual<T, D, FX><<<grid, sh.threads_res, sm, st>>>(op, v, px, R, zero_u, filter);
   return cudaGetLastError();
 }
 
 template <typename T, int D, int FX>
 cudaError_t launch_update(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
-                          const Shape2& sh, int u_only, cudaStream_t st) {
+                          const Shape2& sh, cudaStream_t st) {
   const int R = sh.rows_update;
-  const size_t sm = u_only ? 0 : smem_update<T, D>(op.nx, R);
+  const size_t sm = smem_update<T, D>(op.nx, R);
   static int cfg = 0;
-  cudaError_t e = set_smem(k_update<T, D, FX>, smem_update<T, D>(op.nx, R), cfg);
+  cudaError_t e = set_smem(k_update<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
-  const int grid = (op.ny + R - 1) / R;
-  k_update<T, D, FX><<<grid, sh.threads_update, sm, st>>>(op, v, px, R, u_only);
+  const dim3 grid((op.ny + R - 1) / R, sh.batch);
+  k_update<T, D, FX><<<grid, sh.threads_update, sm, st>>>(op, v, px, R);
   return cudaGetLastError();
 }
 
@@ -552,7 +572,7 @@ cudaError_t launch_direction(const Op2<T>& op, const Vec2<T>& v, const FftPlanDe
   static int cfg = 0;
   cudaError_t e = set_smem(k_direction<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
-  const int grid = (op.ny + R - 1) / R;
+  const dim3 grid((op.ny + R - 1) / R, sh.batch);
   k_direction<T, D, FX><<<grid, sh.threads_dir, sm, st>>>(op, v, px, R);
   return cudaGetLastError();
 }
@@ -560,14 +580,15 @@ cudaError_t launch_direction(const Op2<T>& op, const Vec2<T>& v, const FftPlanDe
 template <typename T, int FY>
 cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec2<T>& sp,
                            const Shape2& sh, int mode, int inverse, double* partials,
-                           SolverScalars* sc, cudaStream_t st) {
+                           SolverScalars* sc, const int* pmode, cudaStream_t st) {
   const int CW = sh.cols;
   const size_t sm = (size_t)ny * CW * sizeof(cx<T>);
   static int cfg = 0;
   cudaError_t e = set_smem(k_colpass<T, FY>, sm, cfg);
   if (e != cudaSuccess) return e;
-  const int grid = (nx + CW - 1) / CW;
-  k_colpass<T, FY><<<grid, sh.threads_col, sm, st>>>(nx, ny, S, py, sp, CW, mode, inverse, partials, sc);
+  const dim3 grid((nx + CW - 1) / CW, sh.batch > 0 ? sh.batch : 1);
+  k_colpass<T, FY><<<grid, sh.threads_col, sm, st>>>(nx, ny, S, py, sp, CW, mode, inverse, partials, sc,
+                                                     pmode);
   return cudaGetLastError();
 }
 
@@ -587,10 +608,10 @@ cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int
 // Explicit instantiations for one radix family (one translation unit each).
 #define FFTMECH_INST_TD(T, D, F)                                                                   \
   template cudaError_t launch_residual<T, D, F>(const Op2<T>&, const Vec2<T>&,                    \
-                                                const FftPlanDev<T>&, const Shape2&, int,         \
+                                                const FftPlanDev<T>&, const Shape2&, int, int,    \
                                                 cudaStream_t);                                    \
   template cudaError_t launch_update<T, D, F>(const Op2<T>&, const Vec2<T>&, const FftPlanDev<T>&, \
-                                              const Shape2&, int, cudaStream_t);                  \
+                                              const Shape2&, cudaStream_t);                       \
   template cudaError_t launch_direction<T, D, F>(const Op2<T>&, const Vec2<T>&,                   \
                                                  const FftPlanDev<T>&, const Shape2&, cudaStream_t);
 #define FFTMECH_INST_T(T, F)                                                                       \
@@ -598,7 +619,7 @@ cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int
   FFTMECH_INST_TD(T, 2, F)                                                                         \
   template cudaError_t launch_colpass<T, F>(int, int, cx<T>*, const FftPlanDev<T>&,               \
                                             const Spec2<T>&, const Shape2&, int, int, double*,    \
-                                            SolverScalars*, cudaStream_t);                        \
+                                            SolverScalars*, const int*, cudaStream_t);            \
   template cudaError_t launch_rowfft<T, F>(int, int, cx<T>*, const FftPlanDev<T>&, int,           \
                                            const Shape2&, cudaStream_t);
 #define FFTMECH_INST_FAMILY(F) \

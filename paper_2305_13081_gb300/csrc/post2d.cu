@@ -13,13 +13,23 @@ static inline int post_grid(long long n) {
 }
 
 // strain = E + sym grad+ u, stress = g C : (strain - e I) (Eq. solid);
-// sums of stress, strain and the energy density 1/2 (strain - e I) : stress.
+// per problem (blockIdx.y) sums of stress, strain and the energy density
+// 1/2 (strain - e I) : stress -> results[b * 7 + k].
 template <typename T>
 __global__ void k_el_output(Op2<T> op, const double* __restrict__ u, T* strain, T* stress,
-                            double* partials, double* results, unsigned int* cnt) {
+                            double* partials, double* results, SolverScalars* sc) {
   __shared__ double red[32 * 7];
   const int nx = op.nx, ny = op.ny;
   const long long N = (long long)nx * ny;
+  const int b = blockIdx.y;
+  const size_t o1 = (size_t)b * N;
+  u += 2 * o1;
+  if (strain) strain += 3 * o1;
+  if (stress) stress += 3 * o1;
+  const uint8_t* phase = op.phase + o1;
+  const T* g = op.g ? op.g + o1 : nullptr;
+  const T* eig = op.eig ? op.eig + o1 : nullptr;
+  partials += (size_t)b * gridDim.x * 7;
   const double ih = 1.0 / op.h;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
@@ -30,9 +40,9 @@ __global__ void k_el_output(Op2<T> op, const double* __restrict__ u, T* strain, 
     const double exx = op.E[0] + (u[ixp] - u[gi]) * ih;
     const double eyy = op.E[1] + (u[N + iyp] - u[N + gi]) * ih;
     const double exy = op.E[2] + 0.5 * ((u[iyp] - u[gi]) + (u[N + ixp] - u[N + gi])) * ih;
-    const double e = op.eig ? (double)op.eig[gi] : 0.0;
-    const int ph = op.phase[gi] ? 1 : 0;
-    const double gg = op.g ? (double)op.g[gi] : 1.0;
+    const double e = eig ? (double)eig[gi] : 0.0;
+    const int ph = phase[gi] ? 1 : 0;
+    const double gg = g ? (double)g[gi] : 1.0;
     const double lam = gg * op.lam[ph], mu = gg * op.mu[ph];
     const double axx = exx - e, ayy = eyy - e;
     const double tr = axx + ayy;
@@ -44,23 +54,28 @@ __global__ void k_el_output(Op2<T> op, const double* __restrict__ u, T* strain, 
     acc[6] += 0.5 * (axx * sxx + ayy * syy + 2 * exy * sxy);
   }
   block_sum<7>(acc, red);
-  if (publish_partials<7>(acc, partials, cnt)) {
+  if (publish_partials<7>(acc, partials, &sc[b].cnt[2])) {
     double tot[7];
-    gather_partials<7>(tot, partials, cnt, red);
+    gather_partials<7>(tot, partials, &sc[b].cnt[2], red);
     if (threadIdx.x == 0)
-      for (int k = 0; k < 7; ++k) results[k] = tot[k];
+      for (int k = 0; k < 7; ++k) results[b * 7 + k] = tot[k];
   }
 }
 
 // Phase statistics of the homogenised diffusion solution (Eq. psi-two-values)
-// and the mean flux; the last block turns them into beta_pore, beta_solid.
-// results: [0] beta_pore [1] beta_solid [2] <jx> [3] <jy> [4] porosity.
+// and the mean flux; the last block of each problem turns them into
+// beta_pore, beta_solid. results[b * 5 + .]: beta_pore, beta_solid, <jx>,
+// <jy>, porosity.
 template <typename T>
 __global__ void k_diff_stats(Op2<T> op, const double* __restrict__ phi, double hdiff,
-                             double c_macro, double* partials, double* results, unsigned int* cnt) {
+                             double c_macro, double* partials, double* results, SolverScalars* sc) {
   __shared__ double red[32 * 10];
   const int nx = op.nx, ny = op.ny;
   const long long N = (long long)nx * ny;
+  const int b = blockIdx.y;
+  phi += (size_t)b * N;
+  const uint8_t* phase = op.phase + (size_t)b * N;
+  partials += (size_t)b * gridDim.x * 10;
   const double ih = 1.0 / hdiff;
   double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
@@ -68,7 +83,7 @@ __global__ void k_diff_stats(Op2<T> op, const double* __restrict__ phi, double h
     const int y = (int)(gi / nx), x = (int)(gi - (long long)y * nx);
     const long long ixp = (long long)y * nx + (x + 1 == nx ? 0 : x + 1);
     const long long iyp = (long long)(y + 1 == ny ? 0 : y + 1) * nx + x;
-    const int s = op.phase[gi] ? 1 : 0;  // 0 pore, 1 solid
+    const int s = phase[gi] ? 1 : 0;  // 0 pore, 1 solid
     const double ramp = op.G[0] * (x * hdiff) + op.G[1] * (y * hdiff);
     acc[s] += 1.0;
     acc[2 + s] += phi[gi];
@@ -78,42 +93,53 @@ __global__ void k_diff_stats(Op2<T> op, const double* __restrict__ phi, double h
     acc[7] += -D * (op.G[1] + (phi[iyp] - phi[gi]) * ih);
   }
   block_sum<10>(acc, red);
-  if (publish_partials<10>(acc, partials, cnt)) {
+  if (publish_partials<10>(acc, partials, &sc[b].cnt[2])) {
     double tot[10];
-    gather_partials<10>(tot, partials, cnt, red);
+    gather_partials<10>(tot, partials, &sc[b].cnt[2], red);
     if (threadIdx.x == 0) {
       const double np = tot[0], ns = tot[1];
       const double eta = np / (double)N;
-      results[0] = np > 0 ? c_macro / eta - (tot[4] + tot[2]) / np : 0.0;
-      results[1] = ns > 0 ? -(tot[5] + tot[3]) / ns : 0.0;
-      results[2] = tot[6] / (double)N;
-      results[3] = tot[7] / (double)N;
-      results[4] = eta;
+      double* r = results + b * 5;
+      r[0] = np > 0 ? c_macro / eta - (tot[4] + tot[2]) / np : 0.0;
+      r[1] = ns > 0 ? -(tot[5] + tot[3]) / ns : 0.0;
+      r[2] = tot[6] / (double)N;
+      r[3] = tot[7] / (double)N;
+      r[4] = eta;
     }
   }
 }
 
-// c = grad c_mac . x + phi + beta_phase (Eqs. concentration, concentration-correct).
-__global__ void k_diff_write_c(int nx, int ny, const uint8_t* __restrict__ phase,
+// c = grad c_mac . x + phi + beta_phase (Eqs. concentration, concentration-correct),
+// beta of problem b from results[b * 5 + 0 / 1].
+__global__ void k_diff_write_c(int nx, int ny, long long total, const uint8_t* __restrict__ phase,
                                const double* __restrict__ phi, double hdiff, double G0, double G1,
                                const double* __restrict__ beta, double* __restrict__ c) {
   const long long N = (long long)nx * ny;
-  for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
+  for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
        gi += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(gi / nx), x = (int)(gi - (long long)y * nx);
-    const double b = phase[gi] ? beta[1] : beta[0];
-    c[gi] = G0 * (x * hdiff) + G1 * (y * hdiff) + phi[gi] + b;
+    const long long b = gi / N, li = gi - b * N;
+    const int y = (int)(li / nx), x = (int)(li - (long long)y * nx);
+    const double bt = phase[gi] ? beta[b * 5 + 1] : beta[b * 5 + 0];
+    c[gi] = G0 * (x * hdiff) + G1 * (y * hdiff) + phi[gi] + bt;
   }
 }
 
 // H = max(H, psi+(eps - e I)) with Eq. (energy) in 2D; Hd = H as double;
-// results[0] = sum of H (for the preconditioner's mean history).
+// per problem, m0b[b] = a + mean(H) (the phase-field preconditioner).
 template <typename T>
 __global__ void k_history(long long N, const uint8_t* __restrict__ phase, double lam0, double lam1,
                           double mu0, double mu1, const T* __restrict__ strain,
-                          const T* __restrict__ eig, T* H, double* Hd, double* partials,
-                          double* results, unsigned int* cnt) {
+                          const T* __restrict__ eig, T* H, double* Hd, double a, double* m0b,
+                          double* partials, SolverScalars* sc) {
   __shared__ double red[32];
+  const int b = blockIdx.y;
+  const size_t o1 = (size_t)b * N;
+  phase += o1;
+  strain += 3 * o1;
+  if (eig) eig += o1;
+  H += o1;
+  Hd += o1;
+  partials += (size_t)b * gridDim.x;
   double acc[1] = {0.0};
   for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
        gi += (long long)gridDim.x * blockDim.x) {
@@ -132,17 +158,24 @@ __global__ void k_history(long long N, const uint8_t* __restrict__ phase, double
     acc[0] += h;
   }
   block_sum<1>(acc, red);
-  if (publish_partials<1>(acc, partials, cnt)) {
+  if (publish_partials<1>(acc, partials, &sc[b].cnt[2])) {
     double tot[1];
-    gather_partials<1>(tot, partials, cnt, red);
-    if (threadIdx.x == 0) results[0] = tot[0];
+    gather_partials<1>(tot, partials, &sc[b].cnt[2], red);
+    if (threadIdx.x == 0) m0b[b] = a + tot[0] / (double)N;
   }
 }
 
-// results: [0] sum d, [1] solid voxels with d > 0.9, [2] solid voxels.
+// Per problem: results[b * 3 + .] = sum d, solid voxels with d > 0.9,
+// solid voxels; if m1b, also m1b[b] = (eta D_pore + (1 - eta) D_solid) ih2,
+// the mean-diffusivity coefficient of the transient preconditioner.
 __global__ void k_pf_stats(long long N, const uint8_t* __restrict__ phase, const double* __restrict__ d,
-                           double* partials, double* results, unsigned int* cnt) {
+                           double* partials, double* results, SolverScalars* sc, double Dp, double Ds,
+                           double ih2, double* m1b) {
   __shared__ double red[32 * 3];
+  const int b = blockIdx.y;
+  phase += (size_t)b * N;
+  if (d) d += (size_t)b * N;
+  partials += (size_t)b * gridDim.x * 3;
   double acc[3] = {0, 0, 0};
   for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
        gi += (long long)gridDim.x * blockDim.x) {
@@ -154,11 +187,16 @@ __global__ void k_pf_stats(long long N, const uint8_t* __restrict__ phase, const
     }
   }
   block_sum<3>(acc, red);
-  if (publish_partials<3>(acc, partials, cnt)) {
+  if (publish_partials<3>(acc, partials, &sc[b].cnt[2])) {
     double tot[3];
-    gather_partials<3>(tot, partials, cnt, red);
-    if (threadIdx.x == 0)
-      for (int k = 0; k < 3; ++k) results[k] = tot[k];
+    gather_partials<3>(tot, partials, &sc[b].cnt[2], red);
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < 3; ++k) results[b * 3 + k] = tot[k];
+      if (m1b) {
+        const double eta = 1.0 - tot[2] / (double)N;
+        m1b[b] = (eta * Dp + (1.0 - eta) * Ds) * ih2;
+      }
+    }
   }
 }
 
@@ -228,40 +266,50 @@ __global__ void k_df_merge(long long n, const float* __restrict__ uh, const floa
 }
 
 // ---------------------------------------------------------------- launchers
+static inline dim3 post_grid_b(long long n, int batch) {
+  long long g = (n + kPostThreads - 1) / kPostThreads;
+  const long long cap = batch > 1 ? 512 : 4096;
+  if (g > cap) g = cap;
+  return dim3((unsigned)(g < 1 ? 1 : g), (unsigned)batch);
+}
+
 template <typename T>
-cudaError_t launch_el_output(const Op2<T>& op, const double* u, T* strain, T* stress,
-                             double* partials, double* results, unsigned int* cnt,
-                             cudaStream_t st) {
-  k_el_output<T><<<post_grid((long long)op.nx * op.ny), kPostThreads, 0, st>>>(op, u, strain, stress,
-                                                                              partials, results, cnt);
+cudaError_t launch_el_output(const Op2<T>& op, int batch, const double* u, T* strain, T* stress,
+                             double* partials, double* results, SolverScalars* sc, cudaStream_t st) {
+  k_el_output<T><<<post_grid_b((long long)op.nx * op.ny, batch), kPostThreads, 0, st>>>(
+      op, u, strain, stress, partials, results, sc);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_diff_stats(const Op2<T>& op, const double* phi, double hdiff, double c_macro,
-                              double* partials, double* results, unsigned int* cnt,
+cudaError_t launch_diff_stats(const Op2<T>& op, int batch, const double* phi, double hdiff,
+                              double c_macro, double* partials, double* results, SolverScalars* sc,
                               cudaStream_t st) {
-  k_diff_stats<T><<<post_grid((long long)op.nx * op.ny), kPostThreads, 0, st>>>(
-      op, phi, hdiff, c_macro, partials, results, cnt);
+  k_diff_stats<T><<<post_grid_b((long long)op.nx * op.ny, batch), kPostThreads, 0, st>>>(
+      op, phi, hdiff, c_macro, partials, results, sc);
   return cudaGetLastError();
 }
-cudaError_t launch_diff_write_c(int nx, int ny, const uint8_t* phase, const double* phi,
+cudaError_t launch_diff_write_c(int nx, int ny, int batch, const uint8_t* phase, const double* phi,
                                 double hdiff, double G0, double G1, const double* beta_dev,
                                 double* c, cudaStream_t st) {
-  k_diff_write_c<<<post_grid((long long)nx * ny), kPostThreads, 0, st>>>(nx, ny, phase, phi, hdiff,
-                                                                        G0, G1, beta_dev, c);
+  const long long total = (long long)nx * ny * batch;
+  k_diff_write_c<<<post_grid(total), kPostThreads, 0, st>>>(nx, ny, total, phase, phi, hdiff, G0, G1,
+                                                            beta_dev, c);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_history(long long N, const uint8_t* phase, double lam0, double lam1, double mu0,
-                           double mu1, const T* strain, const T* eig, T* H, double* Hd,
-                           double* partials, double* results, unsigned int* cnt, cudaStream_t st) {
-  k_history<T><<<post_grid(N), kPostThreads, 0, st>>>(N, phase, lam0, lam1, mu0, mu1, strain, eig,
-                                                      H, Hd, partials, results, cnt);
+cudaError_t launch_history(long long N, int batch, const uint8_t* phase, double lam0, double lam1,
+                           double mu0, double mu1, const T* strain, const T* eig, T* H, double* Hd,
+                           double a, double* m0b, double* partials, SolverScalars* sc,
+                           cudaStream_t st) {
+  k_history<T><<<post_grid_b(N, batch), kPostThreads, 0, st>>>(N, phase, lam0, lam1, mu0, mu1, strain,
+                                                               eig, H, Hd, a, m0b, partials, sc);
   return cudaGetLastError();
 }
-cudaError_t launch_pf_stats(long long N, const uint8_t* phase, const double* d, double* partials,
-                            double* results, unsigned int* cnt, cudaStream_t st) {
-  k_pf_stats<<<post_grid(N), kPostThreads, 0, st>>>(N, phase, d, partials, results, cnt);
+cudaError_t launch_pf_stats(long long N, int batch, const uint8_t* phase, const double* d,
+                            double* partials, double* results, SolverScalars* sc, double Dp,
+                            double Ds, double ih2, double* m1b, cudaStream_t st) {
+  k_pf_stats<<<post_grid_b(N, batch), kPostThreads, 0, st>>>(N, phase, d, partials, results, sc, Dp, Ds,
+                                                            ih2, m1b);
   return cudaGetLastError();
 }
 template <typename T>
@@ -300,13 +348,13 @@ cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t 
 }
 
 #define FFTMECH_POST_INST(T)                                                                       \
-  template cudaError_t launch_el_output<T>(const Op2<T>&, const double*, T*, T*, double*, double*, \
-                                           unsigned int*, cudaStream_t);                           \
-  template cudaError_t launch_diff_stats<T>(const Op2<T>&, const double*, double, double, double*, \
-                                            double*, unsigned int*, cudaStream_t);                 \
-  template cudaError_t launch_history<T>(long long, const uint8_t*, double, double, double,        \
-                                         double, const T*, const T*, T*, double*, double*, double*, \
-                                         unsigned int*, cudaStream_t);                             \
+  template cudaError_t launch_el_output<T>(const Op2<T>&, int, const double*, T*, T*, double*,     \
+                                           double*, SolverScalars*, cudaStream_t);                 \
+  template cudaError_t launch_diff_stats<T>(const Op2<T>&, int, const double*, double, double,     \
+                                            double*, double*, SolverScalars*, cudaStream_t);       \
+  template cudaError_t launch_history<T>(long long, int, const uint8_t*, double, double, double,   \
+                                         double, const T*, const T*, T*, double*, double, double*, \
+                                         double*, SolverScalars*, cudaStream_t);                   \
   template cudaError_t launch_degradation<T>(long long, const double*, double, T*, cudaStream_t);  \
   template cudaError_t launch_precipitate<T>(long long, const uint8_t*, const double*, double,     \
                                              double, T*, T*, cudaStream_t);                        \

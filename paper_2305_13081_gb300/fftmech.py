@@ -115,6 +115,9 @@ def load_library(path=LIB_PATH):
     sigs = {
         "fftmech_create": (i, [P(vp), P(fftmech_grid), P(fftmech_materials), i,
                                P(fftmech_solver_opts), vp]),
+        "fftmech_create_batched": (i, [P(vp), P(fftmech_grid), i, P(fftmech_materials), i,
+                                       P(fftmech_solver_opts), vp]),
+        "fftmech_batch_size": (i, [vp]),
         "fftmech_destroy": (i, [vp]),
         "fftmech_set_solver_opts": (i, [vp, P(fftmech_solver_opts)]),
         "fftmech_status_string": (ctypes.c_char_p, [i]),
@@ -183,6 +186,19 @@ def fftmech_create(grid, mat, precision, opts, stream=None):
     return h
 
 
+def fftmech_create_batched(grid, batch, mat, precision, opts, stream=None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rc = lib.fftmech_create_batched(ctypes.byref(h), ctypes.byref(grid), int(batch), ctypes.byref(mat),
+                                    int(precision), ctypes.byref(opts), stream)
+    _check(rc)
+    return h
+
+
+def fftmech_batch_size(ctx):
+    return load_library().fftmech_batch_size(ctx)
+
+
 def fftmech_destroy(ctx):
     return load_library().fftmech_destroy(ctx)
 
@@ -202,36 +218,47 @@ def fftmech_last_error(ctx):
 _SOLVER_OK = (FFTMECH_OK, FFTMECH_ERR_NOT_CONVERGED, FFTMECH_ERR_NONFINITE)
 
 
+def _infos(ctx, per_problem):
+    n = max(1, fftmech_batch_size(ctx)) * per_problem
+    return (fftmech_solve_info * n)()
+
+
+def _one_or_all(arr):
+    return arr[0] if len(arr) == 1 else arr
+
+
 def fftmech_diffusion_step(ctx, phase, mode, grad_c_mac, c_macro, dt, dirichlet_mask,
                            dirichlet_value, c, info=None):
-    info = info or fftmech_solve_info()
+    """Returns the solve record (a ctypes array of them for a batch)."""
+    infos = _infos(ctx, 1)
     g = c_double3(*(list(grad_c_mac) + [0.0] * 3)[:3])
     rc = load_library().fftmech_diffusion_step(ctx, ptr(phase), int(mode), g, float(c_macro),
                                                float(dt), ptr(dirichlet_mask),
-                                               float(dirichlet_value), ptr(c), ctypes.byref(info))
+                                               float(dirichlet_value), ptr(c), infos)
     _check(rc, ctx, _SOLVER_OK)
-    return info
+    return _one_or_all(infos)
 
 
 def fftmech_equilibrium_solve(ctx, phase, eig, damage, eps_mac, u, strain, stress, info=None):
-    info = info or fftmech_solve_info()
+    infos = _infos(ctx, 1)
     e = c_double6(*(list(eps_mac) + [0.0] * 6)[:6])
     rc = load_library().fftmech_equilibrium_solve(ctx, ptr(phase), ptr(eig), ptr(damage), e, ptr(u),
-                                                  ptr(strain), ptr(stress), ctypes.byref(info))
+                                                  ptr(strain), ptr(stress), infos)
     _check(rc, ctx, _SOLVER_OK)
-    return info
+    return _one_or_all(infos)
 
 
 def fftmech_phasefield_solve(ctx, strain, eig, phase, H, damage, info=None):
-    info = info or fftmech_solve_info()
+    infos = _infos(ctx, 1)
     rc = load_library().fftmech_phasefield_solve(ctx, ptr(strain), ptr(eig), ptr(phase), ptr(H),
-                                                 ptr(damage), ctypes.byref(info))
+                                                 ptr(damage), infos)
     _check(rc, ctx, _SOLVER_OK)
-    return info
+    return _one_or_all(infos)
 
 
 def fftmech_staggered_step(ctx, state, params, infos=None):
-    infos = infos or (fftmech_solve_info * 3)()
+    """Returns 3 records per problem: [diffusion, equilibrium, phase field]."""
+    infos = infos or _infos(ctx, 3)
     rc = load_library().fftmech_staggered_step(ctx, ctypes.byref(state), ctypes.byref(params), infos)
     _check(rc, ctx, _SOLVER_OK)
     return infos
@@ -302,13 +329,17 @@ class Context:
     """Owns one fftmech context (create / destroy)."""
 
     def __init__(self, shape, materials, precision=FFTMECH_FP64, h=5e-6, h_diff=1.0,
-                 tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, stream=None):
+                 tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, stream=None, batch=1):
         self.shape = tuple(shape)
         self.precision = precision
+        self.batch = batch
         self.grid = make_grid(shape, h, h_diff)
         self.mat = make_materials(materials)
         self.opts = make_opts(tol, max_iter, replace_residual, check_every)
-        self.handle = fftmech_create(self.grid, self.mat, precision, self.opts, stream)
+        if batch == 1:
+            self.handle = fftmech_create(self.grid, self.mat, precision, self.opts, stream)
+        else:
+            self.handle = fftmech_create_batched(self.grid, batch, self.mat, precision, self.opts, stream)
 
     @property
     def field_dtype(self):

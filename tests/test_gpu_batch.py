@@ -1,0 +1,132 @@
+"""Uniform batches (independent RVEs of one grid solved together): every
+problem of a batch gives the fields and iteration counts it gets when solved
+alone, and the batched staggered step matches the oracle per problem."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from microstructures import random_carpet
+from microstructures.workloads import Materials, left_face_mask
+from oracle import elasticity, phasefield, staggered
+from paper_2305_13081_gb300 import build
+from paper_2305_13081_gb300 import fftmech as fm
+
+pytestmark = pytest.mark.gpu
+
+H = 5e-6
+MAT = Materials()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    fm.load_library()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def problems(n, seeds):
+    out = []
+    for s in seeds:
+        ph, _ = random_carpet(n, 0.30, s)
+        rng = np.random.default_rng(s)
+        eig = np.where(ph == 0, 1e-3 * (1 + 0.2 * rng.standard_normal(ph.shape)), 0.0)
+        dmg = np.clip(0.5 * rng.random(ph.shape) ** 3, 0, 1)
+        out.append((ph, eig, dmg))
+    return out
+
+
+def solve_equilibrium(probs, prec, tol, batch):
+    n = probs[0][0].shape
+    N = probs[0][0].size
+    B = len(probs)
+    ft = torch.float64 if prec == fm.FFTMECH_FP64 else torch.float32
+    ctx = fm.Context(n, MAT, prec, h=H, tol=tol, batch=B if batch else 1)
+    if batch:
+        phase = torch.as_tensor(np.concatenate([p[0].ravel() for p in probs])).cuda()
+        eig = torch.as_tensor(np.concatenate([p[1].ravel() for p in probs])).to(ft).cuda()
+        dmg = torch.as_tensor(np.concatenate([p[2].ravel() for p in probs])).cuda()
+        u = torch.zeros(2 * N * B, dtype=torch.float64, device="cuda")
+        strain = torch.zeros(3 * N * B, dtype=ft, device="cuda")
+        infos = fm.fftmech_equilibrium_solve(ctx.handle, phase, eig, dmg, [1e-4, 0, 0], u, strain, None)
+        infos = [infos[b] for b in range(B)] if B > 1 else [infos]
+        st = strain.double().cpu().numpy().reshape(B, 3, *n)
+        out = [(st[b], infos[b].iters, infos[b].status) for b in range(B)]
+    else:
+        out = []
+        for ph, e, d in probs:
+            u = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+            strain = torch.zeros(3 * N, dtype=ft, device="cuda")
+            info = fm.fftmech_equilibrium_solve(ctx.handle, torch.as_tensor(ph.ravel()).cuda(),
+                                                torch.as_tensor(e.ravel()).to(ft).cuda(),
+                                                torch.as_tensor(d.ravel()).cuda(), [1e-4, 0, 0], u, strain,
+                                                None)
+            out.append((strain.double().cpu().numpy().reshape(3, *n), info.iters, info.status))
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [(fm.FFTMECH_FP64, 1e-11), (fm.FFTMECH_MIXED, 1e-8)])
+def test_batched_equilibrium_equals_single_solves(prec, tol):
+    probs = problems(81, [3, 4, 5])
+    a = solve_equilibrium(probs, prec, tol, batch=True)
+    b = solve_equilibrium(probs, prec, tol, batch=False)
+    for (sa, ia, ka), (sb, ib, kb) in zip(a, b):
+        assert ka == fm.FFTMECH_OK and kb == fm.FFTMECH_OK
+        assert ia == ib
+        assert np.array_equal(sa, sb)
+
+
+def test_batched_staggered_step_matches_oracle():
+    """Three random carpets, transient diffusion -> precipitate eigenstrain ->
+    equilibrium -> phase field, 2 steps, FP64, each against the oracle."""
+    n = 81
+    B = 3
+    mat = Materials(E_pore=2e9, M_ppt=2.2)
+    phases = [random_carpet(n, 0.30, s)[0] for s in (7, 8, 9)]
+    masks = [left_face_mask(p) for p in phases]
+    dt = (n / 4.0) ** 2 / 10
+    refs = []
+    for ph, mk in zip(phases, masks):
+        r = staggered.initial_state(ph)
+        for _ in range(2):
+            r, _ = staggered.step(r, ph, mat, H, 1.0, staggered.DIFF_TRANSIENT,
+                                  staggered.EIG_FROM_PRECIPITATE, dt=dt, mask=mk, c_dirichlet=1.0,
+                                  tol=1e-12)
+        refs.append(r)
+    N = n * n
+    ctx = fm.Context((n, n), mat, fm.FFTMECH_FP64, h=H, h_diff=1.0, tol=1e-12, batch=B)
+    f64 = torch.float64
+    bufs = {k: torch.zeros(m * N * B, dtype=f64, device="cuda") for k, m in
+            [("c", 1), ("c_ppt", 1), ("eig", 1), ("u", 2), ("strain", 3), ("stress", 3), ("H", 1),
+             ("damage", 1)]}
+    bufs["phase"] = torch.as_tensor(np.concatenate([p.ravel() for p in phases])).cuda()
+    mask = torch.as_tensor(np.concatenate([m.ravel() for m in masks])).cuda()
+    st = fm.fftmech_state()
+    for k, v in bufs.items():
+        setattr(st, k, v.data_ptr())
+    p = fm.fftmech_step_params()
+    p.diffusion_mode = fm.FFTMECH_DIFF_TRANSIENT
+    p.dt = dt
+    p.dirichlet_mask = mask.data_ptr()
+    p.dirichlet_value = 1.0
+    p.eig_mode = fm.FFTMECH_EIG_FROM_PRECIPITATE
+    for _ in range(2):
+        infos = fm.fftmech_staggered_step(ctx.handle, st, p)
+        assert all(infos[i].status == fm.FFTMECH_OK for i in range(3 * B))
+    torch.cuda.synchronize()
+    ctx.close()
+    c = bufs["c"].cpu().numpy().reshape(B, n, n)
+    strain = bufs["strain"].cpu().numpy().reshape(B, 3, n, n)
+    d = bufs["damage"].cpu().numpy().reshape(B, n, n)
+    for b in range(B):
+        assert rel(c[b], refs[b]["c"]) < 1e-10
+        assert rel(strain[b], refs[b]["strain"]) < 1e-9
+        assert rel(d[b], refs[b]["d"]) < 1e-9
+    assert refs[0]["eig"].max() > 0 and refs[0]["d"].max() > 1e-4
