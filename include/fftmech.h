@@ -135,12 +135,13 @@ typedef struct fftmech_ctx fftmech_ctx;
 
 /* Create a context for one grid. `stream` is a cudaStream_t (NULL = a new
  * stream owned by the context). Allocates the workspace (about 60 bytes per
- * voxel for MIXED 2D) on the current CUDA device.
+ * voxel for MIXED 2D, about 100 for MIXED 3D) on the current CUDA device.
  * Returns INVALID_ARG for bad pointers or materials, UNSUPPORTED_SIZE for a
  * grid dimension that is not 2^a 3^b (at most 2187 for powers of three,
- * 2048 for powers of two and mixed sizes within the same per-line limits)
- * or dim not in {2, 3} (dim 3 is not built yet), OOM if the workspace does
- * not fit, CUDA if no device is usable. */
+ * 2048 for powers of two and mixed sizes within the same per-line limits;
+ * in 3D every n >= 2 and x lines short enough for the brick kernels' shared
+ * memory) or dim not in {2, 3}, OOM if the workspace does not fit, CUDA if
+ * no device is usable. */
 fftmech_status fftmech_create(fftmech_ctx** ctx, const fftmech_grid* grid,
                               const fftmech_materials* mat, fftmech_precision precision,
                               const fftmech_solver_opts* opts, void* stream);

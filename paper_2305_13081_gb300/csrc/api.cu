@@ -74,8 +74,9 @@ struct fftmech_ctx {
   int device = 0;
   int nsm = 0;
   size_t optin = 0;
-  HostPlan px, py;
+  HostPlan px, py, pz;
   Shape2 shape{};
+  Shape3 shape3{};
   // workspace (B problems back to back)
   void* r = nullptr;
   void* p[2] = {nullptr, nullptr};
@@ -88,6 +89,11 @@ struct fftmech_ctx {
   double* cn = nullptr;
   void* lamx = nullptr;
   void* lamy = nullptr;
+  void* lamz = nullptr;     // 3D: lambda_z(kz)
+  void* lamc3 = nullptr;    // 3D: lambda_x per spectral column, D = 3 / D = 1 rows
+  void* lamc1 = nullptr;
+  void* wcol3 = nullptr;    // 3D: Parseval weight per spectral column
+  void* wcol1 = nullptr;
   double* partials = nullptr;
   double* results = nullptr;   // 16 per problem
   double* m0b = nullptr;       // per-problem preconditioner constants
@@ -269,13 +275,13 @@ struct Solve {
 // failed) stops moving while the others continue. MIXED: the iterate is a
 // float pair, with reliable updates and a final FP64 true-residual gate.
 template <typename T, int D>
-fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, const Spec2<T>& sp_in,
+fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op, double* u, const Spec<T>& sp_in,
                        std::vector<Solve>& out) {
   cudaStream_t st = ctx->stream;
   const int B = ctx->B;
   const Shape2& sh = ctx->shape;
   FftPlanDev<T> px = dev_plan<T>(ctx->px), py = dev_plan<T>(ctx->py);
-  Spec2<T> sp = sp_in;
+  Spec<T> sp = sp_in;
   sp.lamx = (const T*)ctx->lamx;
   sp.lamy = (const T*)ctx->lamy;
   sp.invN = 1.0 / (double)ctx->N;
@@ -304,12 +310,45 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, const Spec
   const bool mixed = sizeof(T) == 4;
   if (mixed) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_df_split(nU, u, ctx->uh, ctx->ul, st));
   const int nx = ctx->nx, ny = ctx->ny;
-  const int fx = ctx->px.fam, fy = ctx->py.fam;
-  auto residual = [&](int zero_u, int filter) {
-    return launch_residual_f<T, D>(fx, op, v, px, sh, zero_u, filter, st);
+  const int fx = ctx->px.fam, fy = ctx->py.fam, fz = ctx->pz.fam;
+  const bool three = ctx->dim == 3;
+  const Shape3& sh3 = ctx->shape3;
+  FftPlanDev<T> pz = dev_plan<T>(ctx->pz);
+  if (three) {
+    sp.lamc = (const T*)(D == 1 ? ctx->lamc1 : ctx->lamc3);
+    sp.wcol = (const T*)(D == 1 ? ctx->wcol1 : ctx->wcol3);
+    sp.lamj = (const T*)ctx->lamy;
+    sp.laml = (const T*)ctx->lamz;
+  }
+  auto residual = [&](int zero_u, int filter) -> cudaError_t {
+    if constexpr (D == 3) return launch3_residual_f<T, 3>(fx, op, v, px, sh3, zero_u, filter, st);
+    else if constexpr (D == 2) return launch_residual_f<T, 2>(fx, op, v, px, sh, zero_u, filter, st);
+    else
+      return three ? launch3_residual_f<T, 1>(fx, op, v, px, sh3, zero_u, filter, st)
+                   : launch_residual_f<T, 1>(fx, op, v, px, sh, zero_u, filter, st);
   };
-  auto colpass = [&](int mode) {
-    return launch_colpass_f<T>(fy, nx, ny, v.S, py, sp, sh, mode, 0, ctx->partials, ctx->sc, ctx->mode, st);
+  auto direction = [&](const Vec2<T>& va) -> cudaError_t {
+    if constexpr (D == 3) return launch3_direction_f<T, 3>(fx, op, va, px, sh3, st);
+    else if constexpr (D == 2) return launch_direction_f<T, 2>(fx, op, va, px, sh, st);
+    else
+      return three ? launch3_direction_f<T, 1>(fx, op, va, px, sh3, st)
+                   : launch_direction_f<T, 1>(fx, op, va, px, sh, st);
+  };
+  auto update = [&](const Vec2<T>& vb) -> cudaError_t {
+    if constexpr (D == 3) return launch3_update_f<T, 3>(fx, op, vb, px, sh3, st);
+    else if constexpr (D == 2) return launch_update_f<T, 2>(fx, op, vb, px, sh, st);
+    else
+      return three ? launch3_update_f<T, 1>(fx, op, vb, px, sh3, st) : launch_update_f<T, 1>(fx, op, vb, px, sh, st);
+  };
+  // 2D: one column pass; 3D: y-FFT, z pass (multiplier, <r, M^-1 r>), y-IFFT
+  auto colpass = [&](int mode) -> cudaError_t {
+    if (!three)
+      return launch_colpass_f<T>(fy, nx, ny, v.S, py, sp, sh, mode, 0, ctx->partials, ctx->sc, ctx->mode, st);
+    cudaError_t e = launch3_lines_f<T>(fy, v.S, sh3, D, 1, 0, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
+    if (e != cudaSuccess) return e;
+    e = launch3_lines_f<T>(fz, v.S, sh3, D, 2, 1, pz, sp, mode, ctx->partials, ctx->sc, ctx->mode, st);
+    if (e != cudaSuccess || mode == COL_NORM || mode == COL_TRUENORM) return e;
+    return launch3_lines_f<T>(fy, v.S, sh3, D, 1, 2, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
   };
   FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(1, 0));
   FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_NORM));
@@ -352,10 +391,10 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, const Spec
       Vec2<T> va = v;
       va.p_in = pbuf[pi];
       va.p_out = pbuf[1 - pi];
-      FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, (launch_direction_f<T, D>(fx, op, va, px, sh, st)));
+      FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, direction(va));
       Vec2<T> vb = v;
       vb.p_in = pbuf[1 - pi];
-      FFTMECH_LAUNCH(FFTMECH_K_UPDATE, (launch_update_f<T, D>(fx, op, vb, px, sh, st)));
+      FFTMECH_LAUNCH(FFTMECH_K_UPDATE, update(vb));
       const bool replace = pending;
       // reliable update: u += alpha p only (update kernel), then the FP64 true residual
       if (replace) FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 1));
@@ -425,10 +464,11 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op2<T>& op, double* u, const Spec
 }
 
 template <typename T>
-void base_op(const fftmech_ctx* ctx, Op2<T>& op, const uint8_t* phase) {
+void base_op(const fftmech_ctx* ctx, Op<T>& op, const uint8_t* phase) {
   std::memset(&op, 0, sizeof(op));
   op.nx = ctx->nx;
   op.ny = ctx->ny;
+  op.nz = ctx->nz;
   op.h = ctx->h;
   op.phase = phase;
   lame(ctx->mat.E_pore, ctx->mat.nu_pore, op.lam[0], op.mu[0]);
@@ -495,36 +535,40 @@ fftmech_status equilibrium_impl(fftmech_ctx* ctx, const uint8_t* phase, const T*
   if (rc != FFTMECH_OK) return rc;
   const int B = ctx->B;
   const long long NB = ctx->N * B;
-  Op2<T> op;
+  Op<T> op;
   base_op<T>(ctx, op, phase);
   op.eig = eig;
-  op.E[0] = eps_mac[0];
-  op.E[1] = eps_mac[1];
-  op.E[2] = eps_mac[2];
+  for (int k = 0; k < nvoigt(ctx); ++k) op.E[k] = eps_mac[k];
   if (damage) {
     FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_degradation<T>(NB, damage, ctx->mat.kappa, (T*)ctx->g, st));
     op.g = (const T*)ctx->g;
   }
-  Spec2<T> sp{};
+  Spec<T> sp{};
   sp.m0 = 0.0;
   sp.m1 = 1.0 / (ctx->h * ctx->h);
   std::vector<Solve> s;
-  rc = run_pcg<T, 2>(ctx, op, u, sp, s);
+  const bool three = ctx->dim == 3;
+  rc = three ? run_pcg<T, 3>(ctx, op, u, sp, s) : run_pcg<T, 2>(ctx, op, u, sp, s);
   if (rc != FFTMECH_OK) return rc;
-  FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_el_output<T>(op, B, u, strain, stress, ctx->partials, ctx->results, ctx->sc, st));
+  if (three)
+    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch3_el_output<T>(op, B, u, strain, stress, ctx->partials, ctx->results, ctx->sc, st));
+  else
+    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_el_output<T>(op, B, u, strain, stress, ctx->partials, ctx->results, ctx->sc, st));
   if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
   if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
   const double ms = solve_timer_ms(ctx);
   copy_solves(s, info, stride, ms);
   const double N = (double)ctx->N;
+  const int nv = nvoigt(ctx);
+  const double vox = three ? ctx->h * ctx->h * ctx->h : ctx->h * ctx->h;
   for (int b = 0; b < B; ++b) {
-    const double* R = ctx->h_results + b * 7;
+    const double* R = ctx->h_results + b * (2 * nv + 1);
     fftmech_solve_info& i = info_at(info, b, stride);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < nv; ++k) {
       i.mean_stress[k] = R[k] / N;
-      i.mean_strain[k] = R[3 + k] / N;
+      i.mean_strain[k] = R[nv + k] / N;
     }
-    i.elastic_energy = R[6] * ctx->h * ctx->h;
+    i.elastic_energy = R[2 * nv] * vox;
   }
   return worst_status(s);
 }
@@ -539,34 +583,43 @@ fftmech_status diffusion_impl(fftmech_ctx* ctx, const uint8_t* phase, int mode,
   if (rc != FFTMECH_OK) return rc;
   const int B = ctx->B;
   const long long NB = ctx->N * B;
-  Op2<T> op;
+  Op<T> op;
   base_op<T>(ctx, op, phase);
   op.h = ctx->h_diff;
   op.kap[0] = ctx->mat.D_pore;
   op.kap[1] = ctx->mat.D_solid;
   const double ih2 = 1.0 / (ctx->h_diff * ctx->h_diff);
   std::vector<Solve> s;
-  Spec2<T> sp{};
+  Spec<T> sp{};
   if (mode == FFTMECH_DIFF_HOMOGENISE) {
+    const bool three = ctx->dim == 3;
     op.G[0] = grad_c_mac[0];
     op.G[1] = grad_c_mac[1];
+    op.G[2] = three ? grad_c_mac[2] : 0.0;
     sp.m0 = 0.0;
     sp.m1 = ih2;
     rc = run_pcg<T, 1>(ctx, op, ctx->phi, sp, s);
     if (rc != FFTMECH_OK) return rc;
-    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials,
-                                                         ctx->results, ctx->sc, st));
-    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_diff_write_c(ctx->nx, ctx->ny, B, phase, ctx->phi, ctx->h_diff,
-                                                        op.G[0], op.G[1], ctx->results, c, st));
+    if (three) {
+      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch3_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials,
+                                                            ctx->results, ctx->sc, st));
+      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch3_diff_write_c(ctx->nx, ctx->ny, ctx->nz, B, phase, ctx->phi,
+                                                           ctx->h_diff, op.G, ctx->results, c, st));
+    } else {
+      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials,
+                                                           ctx->results, ctx->sc, st));
+      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_diff_write_c(ctx->nx, ctx->ny, B, phase, ctx->phi, ctx->h_diff,
+                                                          op.G[0], op.G[1], ctx->results, c, st));
+    }
     if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
     if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
     copy_solves(s, info, stride, solve_timer_ms(ctx));
+    const int nr = three ? 6 : 5, nd = three ? 3 : 2;
     for (int b = 0; b < B; ++b) {
-      const double* R = ctx->h_results + b * 5;
+      const double* R = ctx->h_results + b * nr;
       fftmech_solve_info& i = info_at(info, b, stride);
-      i.mean_flux[0] = R[2];
-      i.mean_flux[1] = R[3];
-      i.porosity = R[4];
+      for (int k = 0; k < nd; ++k) i.mean_flux[k] = R[2 + k];
+      i.porosity = R[2 + nd];
       i.mean_c = c_macro;
     }
     return worst_status(s);
@@ -602,19 +655,25 @@ fftmech_status phasefield_impl(fftmech_ctx* ctx, const T* strain, const T* eig,
   fftmech_status rc = solve_timer_start(ctx);
   if (rc != FFTMECH_OK) return rc;
   const int B = ctx->B;
-  Op2<T> op;
+  Op<T> op;
   base_op<T>(ctx, op, phase);
   const double a = ctx->mat.Gc / (2.0 * ctx->mat.l0);
   const double b = ctx->mat.Gc * ctx->mat.l0 / 2.0;
   // history update; m0b[p] = a + mean(H) of each problem (on device)
-  FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_history<T>(ctx->N, B, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1],
-                                                    strain, eig, H, ctx->Hd, a, ctx->m0b, ctx->partials, ctx->sc, st));
+  if (ctx->dim == 3)
+    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch3_history<T>(ctx->N, B, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1],
+                                                       strain, eig, H, ctx->Hd, a, ctx->m0b, ctx->partials, ctx->sc,
+                                                       st));
+  else
+    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_history<T>(ctx->N, B, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1],
+                                                      strain, eig, H, ctx->Hd, a, ctx->m0b, ctx->partials, ctx->sc,
+                                                      st));
   op.kap[0] = op.kap[1] = b;
   op.c0c = a;
   op.c0f = H;
   op.srcd = ctx->Hd;
   op.src_scale = 1.0;
-  Spec2<T> sp{};
+  Spec<T> sp{};
   sp.m0b = ctx->m0b;
   sp.m1 = b / (ctx->h * ctx->h);
   std::vector<Solve> s;
@@ -642,13 +701,33 @@ fftmech_status check_ctx(fftmech_ctx* ctx) {
   return FFTMECH_OK;
 }
 
+// |D_alpha|^2 h^2 = 2 - 2 cos(2 pi k / n) per direction (Sec. 2.6, forward
+// difference); 3D also the per-spectral-column tables of the line passes.
 template <typename T>
 fftmech_status fill_lam(fftmech_ctx* ctx) {
+  auto sym = [](int k, int n) { return (T)(2.0 - 2.0 * std::cos(2.0 * M_PI * k / n)); };
   std::vector<T> lx(ctx->nx), ly(ctx->ny);
-  for (int k = 0; k < ctx->nx; ++k) lx[k] = (T)(2.0 - 2.0 * std::cos(2.0 * M_PI * k / ctx->nx));
-  for (int k = 0; k < ctx->ny; ++k) ly[k] = (T)(2.0 - 2.0 * std::cos(2.0 * M_PI * k / ctx->ny));
+  for (int k = 0; k < ctx->nx; ++k) lx[k] = sym(k, ctx->nx);
+  for (int k = 0; k < ctx->ny; ++k) ly[k] = sym(k, ctx->ny);
   CK(cudaMemcpy(ctx->lamx, lx.data(), sizeof(T) * ctx->nx, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->lamy, ly.data(), sizeof(T) * ctx->ny, cudaMemcpyHostToDevice));
+  if (ctx->dim == 3) {
+    const int nx = ctx->nx, nxh = nx / 2 + 1;
+    std::vector<T> lz(ctx->nz), c3, c1, w3, w1;
+    for (int k = 0; k < ctx->nz; ++k) lz[k] = sym(k, ctx->nz);
+    // half-spectrum column kx counts for kx and nx - kx unless they coincide
+    auto half_w = [&](int k) { return (T)((k == 0 || 2 * k == nx) ? 1.0 : 2.0); };
+    for (int k = 0; k < nx; ++k) { c3.push_back(lx[k]); w3.push_back((T)1); }
+    for (int k = 0; k < nxh; ++k) {
+      c3.push_back(lx[k]); w3.push_back(half_w(k));
+      c1.push_back(lx[k]); w1.push_back(half_w(k));
+    }
+    CK(cudaMemcpy(ctx->lamz, lz.data(), sizeof(T) * ctx->nz, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->lamc3, c3.data(), sizeof(T) * c3.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->wcol3, w3.data(), sizeof(T) * w3.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->lamc1, c1.data(), sizeof(T) * c1.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->wcol1, w1.data(), sizeof(T) * w1.size(), cudaMemcpyHostToDevice));
+  }
   return FFTMECH_OK;
 }
 
@@ -684,9 +763,11 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   *out = nullptr;
   if (batch < 1) return FFTMECH_ERR_INVALID_ARG;
   if (precision != FFTMECH_FP64 && precision != FFTMECH_MIXED) return FFTMECH_ERR_INVALID_ARG;
-  if (grid->dim != 2) return FFTMECH_ERR_UNSUPPORTED_SIZE;
+  if (grid->dim != 2 && grid->dim != 3) return FFTMECH_ERR_UNSUPPORTED_SIZE;
   if (!(grid->h > 0) || !(grid->h_diff > 0)) return FFTMECH_ERR_INVALID_ARG;
   if (!factor_ok(grid->n[0]) || !factor_ok(grid->n[1]) || grid->n[0] < 2)
+    return FFTMECH_ERR_UNSUPPORTED_SIZE;
+  if (grid->dim == 3 && (!factor_ok(grid->n[2]) || grid->n[1] < 2 || grid->n[2] < 2))
     return FFTMECH_ERR_UNSUPPORTED_SIZE;
   if (!(mat->E_solid > 0) || !(mat->E_pore > 0) || !(mat->nu_solid < 0.5) || !(mat->nu_pore < 0.5) ||
       !(mat->nu_solid > -1) || !(mat->nu_pore > -1) || !(mat->D_solid > 0) || !(mat->D_pore > 0) ||
@@ -703,8 +784,8 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   ctx->dim = grid->dim;
   ctx->nx = grid->n[0];
   ctx->ny = grid->n[1];
-  ctx->nz = 1;
-  ctx->N = (long long)ctx->nx * ctx->ny;
+  ctx->nz = grid->dim == 3 ? grid->n[2] : 1;
+  ctx->N = (long long)ctx->nx * ctx->ny * ctx->nz;
   ctx->B = batch;
   ctx->h = grid->h;
   ctx->h_diff = grid->h_diff;
@@ -728,38 +809,67 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
       return fail(FFTMECH_ERR_CUDA);
     ctx->own_stream = true;
   }
-  if (make_plan(ctx->nx, ctx->px) != cudaSuccess || make_plan(ctx->ny, ctx->py) != cudaSuccess)
+  const bool three = grid->dim == 3;
+  if (make_plan(ctx->nx, ctx->px) != cudaSuccess || make_plan(ctx->ny, ctx->py) != cudaSuccess ||
+      (three && make_plan(ctx->nz, ctx->pz) != cudaSuccess))
     return fail(FFTMECH_ERR_OOM);
   const bool fp64 = precision == FFTMECH_FP64;
-  const bool shp = fp64 ? choose_shape<double>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape)
-                        : choose_shape<float>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape);
+  bool shp;
+  if (three)
+    shp = fp64 ? choose_shape3<double>(ctx->px, ctx->py, ctx->pz, ctx->nsm, ctx->optin, batch, ctx->shape3)
+               : choose_shape3<float>(ctx->px, ctx->py, ctx->pz, ctx->nsm, ctx->optin, batch, ctx->shape3);
+  else
+    shp = fp64 ? choose_shape<double>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape)
+               : choose_shape<float>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape);
   if (!shp) return fail(FFTMECH_ERR_UNSUPPORTED_SIZE);
   ctx->shape.batch = batch;
   const size_t es = fp64 ? 8 : 4;
   const size_t NB = (size_t)ctx->N * batch;
+  const size_t nd = (size_t)grid->dim;  // displacement components
+  // spectral buffer: 2D one packed complex field; 3D the rows of Shape3
+  const size_t s_complex = three ? (size_t)ctx->shape3.sst * batch : NB;
   // reduction partials: per problem, one slot group per block of the widest launch
-  const size_t row_tiles = (ctx->ny + ctx->shape.rows_dir - 1) / ctx->shape.rows_dir;
-  const size_t strips = (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;
+  size_t widest;
+  if (three) {
+    const Shape3& t = ctx->shape3;
+    const size_t bricks = (size_t)((ctx->ny + t.ry_upd - 1) / t.ry_upd) * ((ctx->nz + t.zc_upd - 1) / t.zc_upd);
+    const size_t bricks_d = (size_t)((ctx->ny + t.ry_dir - 1) / t.ry_dir) * ((ctx->nz + t.zc_dir - 1) / t.zc_dir);
+    const size_t zstrips = (size_t)ctx->ny * ((nxs_of(ctx->nx, 3) + t.cw_z - 1) / t.cw_z);
+    widest = std::max(std::max(bricks, bricks_d), zstrips);
+  } else {
+    const size_t row_tiles = (ctx->ny + ctx->shape.rows_dir - 1) / ctx->shape.rows_dir;
+    const size_t strips = (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;
+    widest = std::max(row_tiles, strips);
+  }
   const size_t post_blocks = batch > 1 ? 512 : 4096;
-  const size_t slots = (size_t)batch * std::max(std::max(row_tiles, strips), post_blocks) * 16;
+  const size_t slots = (size_t)batch * std::max(widest, post_blocks) * 16;
   bool ok = true;
   auto alloc = [&](void** p, size_t bytes) {
     if (!ok) return;
     if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); ok = false; return; }
     if (cudaMemset(*p, 0, bytes) != cudaSuccess) ok = false;
   };
-  alloc(&ctx->r, 2 * NB * es);
-  alloc(&ctx->p[0], 2 * NB * es);
-  alloc(&ctx->p[1], 2 * NB * es);
-  alloc(&ctx->S, 2 * NB * es);
+  alloc(&ctx->r, nd * NB * es);
+  alloc(&ctx->p[0], nd * NB * es);
+  alloc(&ctx->p[1], nd * NB * es);
+  alloc(&ctx->S, 2 * s_complex * es);
   alloc(&ctx->g, NB * es);
-  alloc((void**)&ctx->uh, 2 * NB * sizeof(float));
-  alloc((void**)&ctx->ul, 2 * NB * sizeof(float));
+  if (!fp64) {
+    alloc((void**)&ctx->uh, nd * NB * sizeof(float));
+    alloc((void**)&ctx->ul, nd * NB * sizeof(float));
+  }
   alloc((void**)&ctx->phi, NB * 8);
   alloc((void**)&ctx->Hd, NB * 8);
   alloc((void**)&ctx->cn, NB * 8);
   alloc(&ctx->lamx, ctx->nx * es);
   alloc(&ctx->lamy, ctx->ny * es);
+  if (three) {
+    alloc(&ctx->lamz, ctx->nz * es);
+    alloc(&ctx->lamc3, (size_t)nxs_of(ctx->nx, 3) * es);
+    alloc(&ctx->wcol3, (size_t)nxs_of(ctx->nx, 3) * es);
+    alloc(&ctx->lamc1, (size_t)nxs_of(ctx->nx, 1) * es);
+    alloc(&ctx->wcol1, (size_t)nxs_of(ctx->nx, 1) * es);
+  }
   alloc((void**)&ctx->partials, slots * 8);
   alloc((void**)&ctx->results, (size_t)kResultsPerProblem * batch * 8);
   alloc((void**)&ctx->m0b, (size_t)batch * 8);
@@ -796,8 +906,8 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   void* bufs[] = {ctx->r, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
-                  ctx->cn, ctx->lamx, ctx->lamy, ctx->partials, ctx->results, ctx->m0b, ctx->m1b,
-                  ctx->mode, ctx->sc};
+                  ctx->cn, ctx->lamx, ctx->lamy, ctx->lamz, ctx->lamc3, ctx->lamc1, ctx->wcol3, ctx->wcol1,
+                  ctx->partials, ctx->results, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < ST_COUNT; ++i)
@@ -814,6 +924,7 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   free_plan(ctx->px);
   free_plan(ctx->py);
+  free_plan(ctx->pz);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return FFTMECH_OK;
@@ -841,7 +952,7 @@ fftmech_status fftmech_equilibrium_solve(fftmech_ctx* ctx, const uint8_t* phase,
   if ((rc = stage_in(ctx, ST_PHASE, phase, N, true, &dphase)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_EIG, eig, N * es, true, &deig)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_DAMAGE, damage, N * 8, true, &ddmg)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_U, u, 2 * N * 8, true, &du)) != FFTMECH_OK) return rc;
+  if ((rc = stage_in(ctx, ST_U, u, (size_t)ctx->dim * N * 8, true, &du)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_STRAIN, strain, nv * N * es, false, &dstrain)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_STRESS, stress, nv * N * es, false, &dstress)) != FFTMECH_OK) return rc;
   fftmech_status s;
@@ -852,7 +963,7 @@ fftmech_status fftmech_equilibrium_solve(fftmech_ctx* ctx, const uint8_t* phase,
     s = equilibrium_impl<float>(ctx, (const uint8_t*)dphase, (const float*)deig, (const double*)ddmg,
                                 eps_mac, (double*)du, (float*)dstrain, (float*)dstress, info, 1);
   if (is_hard_error(s)) return s;
-  if ((rc = stage_out(ctx, u, du, 2 * N * 8)) != FFTMECH_OK) return rc;
+  if ((rc = stage_out(ctx, u, du, (size_t)ctx->dim * N * 8)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, strain, dstrain, nv * N * es)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, stress, dstress, nv * N * es)) != FFTMECH_OK) return rc;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -938,7 +1049,7 @@ fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
   if ((rc = stage_in(ctx, ST_C, state->c, N * 8, true, &dc)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_CPPT, state->c_ppt, N * es, true, &dcppt)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_EIG, state->eig, N * es, true, &deig)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_U, state->u, 2 * N * 8, true, &du)) != FFTMECH_OK) return rc;
+  if ((rc = stage_in(ctx, ST_U, state->u, (size_t)ctx->dim * N * 8, true, &du)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_STRAIN, state->strain, nv * N * es, true, &dstrain)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_STRESS, state->stress, nv * N * es, true, &dstress)) != FFTMECH_OK) return rc;
   if ((rc = stage_in(ctx, ST_H, state->H, N * es, true, &dH)) != FFTMECH_OK) return rc;
@@ -1005,7 +1116,7 @@ fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
   if ((rc = stage_out(ctx, state->c, dc, N * 8)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, state->c_ppt, dcppt, N * es)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, state->eig, deig, N * es)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, state->u, du, 2 * N * 8)) != FFTMECH_OK) return rc;
+  if ((rc = stage_out(ctx, state->u, du, (size_t)ctx->dim * N * 8)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, state->strain, dstrain, nv * N * es)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, state->stress, dstress, nv * N * es)) != FFTMECH_OK) return rc;
   if ((rc = stage_out(ctx, state->H, dH, N * es)) != FFTMECH_OK) return rc;
@@ -1075,13 +1186,13 @@ fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse,
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (fp64) {
-      Spec2<double> sp{};
+      Spec<double> sp{};
       e = launch_rowfft_f<double>(px.fam, nx, ny, (cx<double>*)data, dev_plan<double>(px), inverse, sh, st);
       if (e == cudaSuccess && ny > 1)
         e = launch_colpass_f<double>(py.fam, nx, ny, (cx<double>*)data, dev_plan<double>(py), sp, sh, COL_PLAIN,
                                    inverse, nullptr, nullptr, nullptr, st);
     } else {
-      Spec2<float> sp{};
+      Spec<float> sp{};
       e = launch_rowfft_f<float>(px.fam, nx, ny, (cx<float>*)data, dev_plan<float>(px), inverse, sh, st);
       if (e == cudaSuccess && ny > 1)
         e = launch_colpass_f<float>(py.fam, nx, ny, (cx<float>*)data, dev_plan<float>(py), sp, sh, COL_PLAIN,

@@ -66,7 +66,7 @@ cudaError_t run(HostPlan& px, HostPlan& py, int inverse, void* data, int nsm, si
   const int nx = px.n, ny = py.n;
   cudaError_t e = launch_rowfft_f<T>(px.fam, nx, ny, (cx<T>*)data, dev_plan<T>(px), inverse, sh, st);
   if (e == cudaSuccess && ny > 1) {
-    Spec2<T> sp{};
+    Spec<T> sp{};
     e = launch_colpass_f<T>(py.fam, nx, ny, (cx<T>*)data, dev_plan<T>(py), sp, sh, COL_PLAIN, inverse,
                             nullptr, nullptr, nullptr, st);
   }

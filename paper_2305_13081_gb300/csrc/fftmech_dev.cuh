@@ -378,6 +378,15 @@ __device__ void fft_lines(cx<T>* buf, const FftPlanDev<T>& p, int nlines, int ls
   }
 }
 
+// fft_lines as a real call: a kernel that keeps much state live across a
+// loop around the transform saves it once per call instead of spilling
+// inside the butterflies.
+template <typename T, int S, int FAM>
+__device__ __noinline__ void fft_lines_call(cx<T>* buf, const FftPlanDev<T> p, int nlines, int ls, int is,
+                                            bool lines_fast) {
+  fft_lines<T, S, FAM>(buf, p, nlines, ls, is, lines_fast);
+}
+
 // ---------------------------------------------------------------- reductions
 // Sum of K doubles over the block; result valid in thread 0. Uses `scratch`
 // (>= 32 * K doubles of shared memory). Deterministic for a fixed launch.

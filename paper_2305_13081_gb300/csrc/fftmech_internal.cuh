@@ -33,28 +33,28 @@ enum ColMode {
   COL_RESTART = 6
 };
 
-// Material / operator description for the 2D row kernels.
-// Vector (D = 2, elasticity): K u = grad+^T [g C_omega : sym grad+ u];
+// Material / operator description for the row kernels (2D: nz = 1).
+// Vector (D = d, elasticity): K u = grad+^T [g C_omega : sym grad+ u];
 //   residual r = -grad+^T [g C_omega : (E + sym grad+ u - e I)].
 // Scalar (D = 1): K u = c0(x) u + grad+^T [kap_omega grad+ u];
 //   residual r = P (src - c0 u - grad+^T [kap_omega (grad+ u + G)]),
 //   c0 = c0c + c0f(x), src = src_scale * (srcd or srct), P zeroes masked voxels.
 template <typename T>
-struct Op2 {
-  int nx, ny;
+struct Op {
+  int nx, ny, nz;
   double h;
   const uint8_t* phase;
   // elasticity
   const T* g;  // degradation per voxel (NULL = 1)
   double lam[2], mu[2];  // by phase: [0] pore, [1] solid
   const T* eig;  // isotropic eigenstrain (NULL = 0)
-  double E[3];   // macro strain xx, yy, xy
+  double E[6];   // macro strain: 2D xx, yy, xy; 3D xx, yy, zz, yz, xz, xy
   // scalar problems
   double kap[2];
   double c0c;
   const T* c0f;
   const uint8_t* mask;
-  double G[2];
+  double G[3];
   const double* srcd;
   const T* srct;
   double src_scale;
@@ -81,7 +81,7 @@ struct Vec2 {
 // b N, its d-component fields at b d N, its spectrum at b N, its scalars at
 // sc + b; launches put the problem index in blockIdx.y.
 template <typename T, int D>
-__device__ __forceinline__ void problem_views(Op2<T>& op, Vec2<T>& v, int b, size_t N) {
+__device__ __forceinline__ void problem_views(Op<T>& op, Vec2<T>& v, int b, size_t N) {
   const size_t o1 = (size_t)b * N, oD = (size_t)b * D * N;
   op.phase += o1;
   if (op.g) op.g += o1;
@@ -103,14 +103,20 @@ __device__ __forceinline__ void problem_views(Op2<T>& op, Vec2<T>& v, int b, siz
 // Fourier multiplier 1 / (m0 + m1 lambda(k)), lambda = lamx[kx] + lamy[ky]
 // (the symbol of grad+^T grad+); 0 where the denominator is 0 (k = 0 when
 // m0 = 0), scaled by 1/N to fold the inverse transform's normalisation.
+// 3D line passes: lambda = lamc[spectral column] + lamj[line set] +
+// laml[line], Parseval weight wcol[spectral column].
 template <typename T>
-struct Spec2 {
+struct Spec {
   const T* lamx;
   const T* lamy;
   double m0, m1;
   double invN;
   const double* m0b;  // per-problem m0 (NULL = m0 for all)
   const double* m1b;  // per-problem m1 (NULL = m1 for all)
+  const T* lamc;
+  const T* lamj;
+  const T* laml;
+  const T* wcol;
 };
 
 // Launch shapes chosen by the host.
@@ -123,20 +129,33 @@ struct Shape2 {
   int threads_plain;
 };
 
+// 3D launch shapes: x-line bricks of ry lines x zc planes, and strips of
+// cw spectral columns for the y and z passes.
+struct Shape3 {
+  int batch;
+  int nx, ny, nz;
+  long long sst;  // complex numbers per problem in the spectral buffer
+  int ry_upd, zc_upd, thr_upd;
+  int ry_dir, zc_dir, thr_dir;
+  int ry_res, zc_res, thr_res;
+  int cw_y, thr_y;
+  int cw_z, thr_z;
+};
+
 // ---------------------------------------------------------------- launchers
 // Row kernels take the radix family of the x transform (FX), column kernels
 // that of the y transform (FY); see RadixFamily.
 template <typename T, int D, int FX>
-cudaError_t launch_residual(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+cudaError_t launch_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                             const Shape2& sh, int zero_u, int filter, cudaStream_t st);
 template <typename T, int D, int FX>
-cudaError_t launch_update(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+cudaError_t launch_update(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                           const Shape2& sh, cudaStream_t st);
 template <typename T, int D, int FX>
-cudaError_t launch_direction(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+cudaError_t launch_direction(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                              const Shape2& sh, cudaStream_t st);
 template <typename T, int FY>
-cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec2<T>& sp,
+cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec<T>& sp,
                            const Shape2& sh, int mode, int inverse, double* partials,
                            SolverScalars* sc, const int* pmode, cudaStream_t st);
 template <typename T, int FX>
@@ -152,7 +171,7 @@ cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int
   }
 
 template <typename T, int D>
-inline cudaError_t launch_residual_f(int fx, const Op2<T>& op, const Vec2<T>& v,
+inline cudaError_t launch_residual_f(int fx, const Op<T>& op, const Vec2<T>& v,
                                      const FftPlanDev<T>& px, const Shape2& sh, int zero_u,
                                      int filter, cudaStream_t st) {
 #define FFTMECH_C(F) launch_residual<T, D, F>(op, v, px, sh, zero_u, filter, st)
@@ -160,14 +179,14 @@ inline cudaError_t launch_residual_f(int fx, const Op2<T>& op, const Vec2<T>& v,
 #undef FFTMECH_C
 }
 template <typename T, int D>
-inline cudaError_t launch_update_f(int fx, const Op2<T>& op, const Vec2<T>& v,
+inline cudaError_t launch_update_f(int fx, const Op<T>& op, const Vec2<T>& v,
                                    const FftPlanDev<T>& px, const Shape2& sh, cudaStream_t st) {
 #define FFTMECH_C(F) launch_update<T, D, F>(op, v, px, sh, st)
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
 template <typename T, int D>
-inline cudaError_t launch_direction_f(int fx, const Op2<T>& op, const Vec2<T>& v,
+inline cudaError_t launch_direction_f(int fx, const Op<T>& op, const Vec2<T>& v,
                                       const FftPlanDev<T>& px, const Shape2& sh, cudaStream_t st) {
 #define FFTMECH_C(F) launch_direction<T, D, F>(op, v, px, sh, st)
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
@@ -175,7 +194,7 @@ inline cudaError_t launch_direction_f(int fx, const Op2<T>& op, const Vec2<T>& v
 }
 template <typename T>
 inline cudaError_t launch_colpass_f(int fy, int nx, int ny, cx<T>* S, const FftPlanDev<T>& py,
-                                    const Spec2<T>& sp, const Shape2& sh, int mode, int inverse,
+                                    const Spec<T>& sp, const Shape2& sh, int mode, int inverse,
                                     double* partials, SolverScalars* sc, const int* pmode,
                                     cudaStream_t st) {
 #define FFTMECH_C(F) launch_colpass<T, F>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st)
@@ -190,12 +209,58 @@ inline cudaError_t launch_rowfft_f(int fx, int nx, int ny, cx<T>* S, const FftPl
 #undef FFTMECH_C
 }
 
+// 3D launchers (kernels3d.cuh); axis 1 = y pass, 2 = z pass; stage 0 / 1 / 2
+// = forward FFT / multiplier pass / inverse FFT.
+template <typename T, int D, int FX>
+cudaError_t launch3_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
+                             int zero_u, int filter, cudaStream_t st);
+template <typename T, int D, int FX>
+cudaError_t launch3_update(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
+                           cudaStream_t st);
+template <typename T, int D, int FX>
+cudaError_t launch3_direction(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
+                              cudaStream_t st);
+template <typename T, int FL>
+cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage, const FftPlanDev<T>& pl,
+                          const Spec<T>& sp, int mode, double* partials, SolverScalars* sc, const int* pmode,
+                          cudaStream_t st);
+
+template <typename T, int D>
+inline cudaError_t launch3_residual_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                                      const Shape3& sh, int zero_u, int filter, cudaStream_t st) {
+#define FFTMECH_C(F) launch3_residual<T, D, F>(op, v, px, sh, zero_u, filter, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T, int D>
+inline cudaError_t launch3_update_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                                    const Shape3& sh, cudaStream_t st) {
+#define FFTMECH_C(F) launch3_update<T, D, F>(op, v, px, sh, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T, int D>
+inline cudaError_t launch3_direction_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                                       const Shape3& sh, cudaStream_t st) {
+#define FFTMECH_C(F) launch3_direction<T, D, F>(op, v, px, sh, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T>
+inline cudaError_t launch3_lines_f(int fl, cx<T>* S, const Shape3& sh, int D, int axis, int stage,
+                                   const FftPlanDev<T>& pl, const Spec<T>& sp, int mode, double* partials,
+                                   SolverScalars* sc, const int* pmode, cudaStream_t st) {
+#define FFTMECH_C(F) launch3_lines<T, F>(S, sh, D, axis, stage, pl, sp, mode, partials, sc, pmode, st)
+  FFTMECH_FAMILY_SWITCH(fl, FFTMECH_C)
+#undef FFTMECH_C
+}
+
 // Post-processing and pointwise kernels (2D); `batch` problems (grid.y).
 template <typename T>
-cudaError_t launch_el_output(const Op2<T>& op, int batch, const double* u, T* strain, T* stress,
+cudaError_t launch_el_output(const Op<T>& op, int batch, const double* u, T* strain, T* stress,
                              double* partials, double* results, SolverScalars* sc, cudaStream_t st);
 template <typename T>
-cudaError_t launch_diff_stats(const Op2<T>& op, int batch, const double* phi, double hdiff,
+cudaError_t launch_diff_stats(const Op<T>& op, int batch, const double* phi, double hdiff,
                               double c_macro, double* partials, double* results, SolverScalars* sc,
                               cudaStream_t st);
 cudaError_t launch_diff_write_c(int nx, int ny, int batch, const uint8_t* phase, const double* phi,
@@ -222,6 +287,23 @@ template <typename T>
 cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t st);
 cudaError_t launch_df_split(long long n, const double* u, float* uh, float* ul, cudaStream_t st);
 cudaError_t launch_df_merge(long long n, const float* uh, const float* ul, double* u, cudaStream_t st);
+
+// 3D post-processing (post3d.cu): results[b * 13 + k] (6 stress sums, 6
+// strain sums, energy) and results[b * 6 + k] (beta_pore, beta_solid, 3 mean
+// fluxes, porosity).
+template <typename T>
+cudaError_t launch3_el_output(const Op<T>& op, int batch, const double* u, T* strain, T* stress, double* partials,
+                              double* results, SolverScalars* sc, cudaStream_t st);
+template <typename T>
+cudaError_t launch3_diff_stats(const Op<T>& op, int batch, const double* phi, double hdiff, double c_macro,
+                               double* partials, double* results, SolverScalars* sc, cudaStream_t st);
+cudaError_t launch3_diff_write_c(int nx, int ny, int nz, int batch, const uint8_t* phase, const double* phi,
+                                 double hdiff, const double G[3], const double* beta_dev, double* c,
+                                 cudaStream_t st);
+template <typename T>
+cudaError_t launch3_history(long long N, int batch, const uint8_t* phase, double lam0, double lam1, double mu0,
+                            double mu1, const T* strain, const T* eig, T* H, double* Hd, double a, double* m0b,
+                            double* partials, SolverScalars* sc, cudaStream_t st);
 
 // Shared-memory layouts of the row kernels for tiles of R rows of nx
 // (byte offsets, each region 16-byte aligned), used by host and device.
@@ -265,6 +347,49 @@ inline size_t smem_residual(int nx, int R) {
   const size_t a = (size_t)D * (R + 2) * sizeof(double), b = (size_t)2 * R * sizeof(T);
   return align16((a > b ? a : b) * nx) + (size_t)3 * (R + 1) * nx * sizeof(double);
 }
+// 3D spectral rows: D = 3 stores the packed (x, y) components (nx complex)
+// and the z component's half spectrum (nx/2 + 1); D = 1 the half spectrum.
+__host__ __device__ inline int nxs_of(int nx, int D) { return (D == 3 ? nx : 0) + nx / 2 + 1; }
+
+// 3D x-line kernels (stencil rows: update, kind 0, and FP64 residual, kind
+// 1): [P: two planes x D (R+2) lines, compute type] [SP: in-plane stress or
+// flux, NP (R+1) lines] [SZ: z-differenced components, two planes x NZ
+// (R+1) lines] [RS: old residual, D R lines (kind 0)] [F: NF R complex
+// lines] [MG: g or c0 field, R+1 lines] [PH: phase bytes, R+1 lines]
+// [MK: mask bytes, R lines]
+struct Row3Layout {
+  size_t P, SP, SZ, RS, F, MG, PH, MK, total;
+  __host__ __device__ Row3Layout(int nx, int R, int cs, int ts, int D, int kind) {
+    const size_t np = D == 3 ? 3 : 2, nzc = D == 3 ? 3 : 1, nf = D == 3 ? 2 : 1;
+    const size_t L = (size_t)nx;
+    P = 0;
+    SP = P + align16((size_t)2 * D * (R + 2) * L * cs);
+    SZ = SP + align16(np * (R + 1) * L * cs);
+    RS = SZ + align16(2 * nzc * (R + 1) * L * cs);
+    F = RS + (kind == 0 ? align16((size_t)D * R * L * cs) : 0);
+    MG = F + align16(nf * R * L * 2 * ts);
+    PH = MG + align16((size_t)(R + 1) * L * ts);
+    MK = PH + align16((size_t)(R + 1) * L);
+    total = MK + align16((size_t)R * L);
+  }
+};
+
+// 3D direction: [F: NF (R+1) complex lines] [P: two planes x D (R+1) lines]
+// [MG: R lines] [PH: R byte lines] [MK: R+1 byte lines]
+struct Dir3Layout {
+  size_t F, P, MG, PH, MK, total;
+  __host__ __device__ Dir3Layout(int nx, int R, int ts, int D) {
+    const size_t nf = D == 3 ? 2 : 1;
+    const size_t L = (size_t)nx;
+    F = 0;
+    P = F + align16(nf * (R + 1) * L * 2 * ts);
+    MG = P + align16((size_t)2 * D * (R + 1) * L * ts);
+    PH = MG + align16((size_t)R * L * ts);
+    MK = PH + align16((size_t)R * L);
+    total = MK + align16((size_t)(R + 1) * L);
+  }
+};
+
 template <typename T, int D>
 inline size_t smem_update(int nx, int R) { return UpdLayout(nx, R, (int)sizeof(T), D).total; }
 template <typename T, int D>

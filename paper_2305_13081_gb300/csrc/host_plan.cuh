@@ -148,6 +148,78 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   return true;
 }
 
+// Launch shapes for an nx x ny x nz grid (3D kernels). Bricks of R lines:
+// the largest R whose shared memory stays within a budget that lets two
+// blocks share an SM (for both D = 1 and D = 3), with (R + 2) nx < 2^16 for
+// the kernels' integer division; Zc planes per brick so that a launch has
+// about six blocks per SM. Line passes: strips of CW spectral columns.
+template <typename T>
+bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, int nsm, size_t optin_total,
+                   int batch, Shape3& s) {
+  const int nx = px.n, ny = py.n, nz = pz.n;
+  const size_t optin = optin_total - 1024;
+  const int tmax = 512;
+  const int es = (int)sizeof(T);
+  const size_t budget = std::min<size_t>(optin, 110 * 1024);
+  s = Shape3();
+  s.batch = batch;
+  s.nx = nx;
+  s.ny = ny;
+  s.nz = nz;
+  s.sst = (long long)(nx + nx / 2 + 1) * ny * nz;
+  auto idx_ok = [&](int r) { return (long long)(r + 2) * nx < 65536 && (long long)r * nxs_of(nx, 3) < 65536; };
+  auto upd_fits = [&](int r, size_t lim) {
+    return idx_ok(r) && Row3Layout(nx, r, es, es, 3, 0).total <= lim && Row3Layout(nx, r, es, es, 1, 0).total <= lim &&
+           need_threads(px, 2 * r) <= 256;
+  };
+  auto dir_fits = [&](int r, size_t lim) {
+    return idx_ok(r) && Dir3Layout(nx, r, es, 3).total <= lim && Dir3Layout(nx, r, es, 1).total <= lim &&
+           need_threads(px, 2 * (r + 1)) <= 256;
+  };
+  auto res_fits = [&](int r, size_t lim) {
+    return idx_ok(r) && Row3Layout(nx, r, 8, es, 3, 1).total <= lim && Row3Layout(nx, r, 8, es, 1, 1).total <= lim &&
+           need_threads(px, 2 * r) <= tmax;
+  };
+  auto pick = [&](auto fits) {
+    int r = std::min(ny, 8);
+    while (r > 1 && !fits(r, budget)) --r;
+    return fits(r, optin) ? r : 0;
+  };
+  s.ry_upd = pick(upd_fits);
+  s.ry_dir = pick(dir_fits);
+  int rr = std::min(ny, 4);
+  while (rr > 1 && !res_fits(rr, optin)) --rr;
+  s.ry_res = res_fits(rr, optin) ? rr : 0;
+  if (!s.ry_upd || !s.ry_dir || !s.ry_res) return false;
+  auto zchunk = [&](int r) {
+    const long long nty = (ny + r - 1) / r;
+    const long long target = 6LL * nsm;
+    long long nzc = (target + nty * batch - 1) / (nty * batch);
+    nzc = std::max(1LL, std::min<long long>(nzc, nz));
+    int zc = (int)((nz + nzc - 1) / nzc);
+    return std::max(std::min(4, nz), zc);
+  };
+  s.zc_upd = zchunk(s.ry_upd);
+  s.zc_dir = zchunk(s.ry_dir);
+  s.zc_res = zchunk(s.ry_res);
+  s.thr_upd = std::max(128, round32(need_threads(px, 2 * s.ry_upd)));
+  s.thr_dir = std::max(128, round32(need_threads(px, 2 * (s.ry_dir + 1))));
+  s.thr_res = std::min(tmax, std::max(128, round32(need_threads(px, 2 * s.ry_res))));
+  auto strip = [&](const HostPlan& pl, int& cw, int& thr) {
+    int c = sizeof(T) == 4 ? 16 : 8;
+    while (c > 1 && ((size_t)pl.n * c * sizeof(cx<T>) > budget || need_threads(pl, c) > tmax ||
+                     (long long)pl.n * c >= 65536))
+      c /= 2;
+    if ((size_t)pl.n * c * sizeof(cx<T>) > optin || need_threads(pl, c) > tmax) return false;
+    cw = c;
+    thr = std::min(tmax, std::max(128, round32(need_threads(pl, c))));
+    return true;
+  };
+  if (!strip(py, s.cw_y, s.thr_y) || !strip(pz, s.cw_z, s.thr_z)) return false;
+  if ((long long)batch * std::max(ny, nz) > 65535) return false;  // grid.y of the line passes
+  return true;
+}
+
 // Launch shapes for the bare transform (row FFT + column FFT only), which
 // needs far less shared memory than the solver's row kernels.
 template <typename T>

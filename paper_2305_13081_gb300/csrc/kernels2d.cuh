@@ -13,79 +13,19 @@
 
 #include "fftmech_internal.cuh"
 #include "fftmech.h"
+#include "pcg_dev.cuh"
 
 namespace fftmech {
 
 // Threads per block are capped at 512 (128 registers per thread available).
 #define FFTMECH_BOUNDS(T) __launch_bounds__(512)
 
-static __device__ __forceinline__ int wrap_y(int y, int ny) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); }
-
-static __device__ __forceinline__ int done_flag(const SolverScalars* sc) {
-  return *reinterpret_cast<const volatile int*>(&sc->done);
-}
-
-static __device__ __forceinline__ double vol_read(const double* p) {
-  return *reinterpret_cast<const volatile double*>(p);
-}
-
-// ---------------------------------------------------------------- finalisers
-static __device__ void finalize_direction(SolverScalars* sc, double pq) {
-  sc->pq = pq;
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    sc->done = 1;
-    sc->status = FFTMECH_ERR_NONFINITE;
-    return;
-  }
-  sc->alpha = sc->rz / pq;
-}
-
-static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
-  if (mode == COL_NORM) { sc->rz0 = tot; return; }
-  if (mode == COL_PLAIN) return;
-  if (mode == COL_TRUENORM) { sc->rz_true = tot; return; }
-  if (!isfinite(tot)) {
-    sc->rz = tot;
-    sc->done = 1;
-    sc->status = FFTMECH_ERR_NONFINITE;
-    return;
-  }
-  if (mode == COL_INIT) {
-    sc->rz = tot;
-    sc->beta = 0.0;
-    sc->iter = 0;
-    if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
-    else if (sc->max_iter <= 0) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
-    return;
-  }
-  if (mode == COL_RESTART) {
-    // the true residual replaced r after a recursive convergence: restart
-    sc->rz = tot;
-    sc->rz_true = tot;
-    sc->beta = 0.0;
-    if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
-    else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
-    return;
-  }
-  sc->iter += 1;
-  if (mode == COL_TRUE) sc->rz_true = tot;
-  const double rz_old = sc->rz;
-  sc->rz = tot;
-  if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; return; }
-  if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; return; }
-  double beta = tot / rz_old;
-  // a replaced residual larger than the recursive one it replaces means the
-  // float recursion had drifted: restart the direction instead of mixing
-  if (mode == COL_TRUE && beta > 1.0) beta = 0.0;
-  sc->beta = beta;
-}
-
 // ---------------------------------------------------------------- residual
 // r = b - K u in FP64 (u from the iterate, zero_u: u = 0 except Dirichlet
 // voxels), written as T and row-transformed into S. Shared memory:
 // [max(D (R+2) doubles, 2 R T) per column] + [3 (R+1) doubles per column].
 template <typename T, int D, int FX>
-__global__ void FFTMECH_BOUNDS(T) k_residual(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int zero_u,
+__global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int zero_u,
                                              int filter) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nx = op.nx, ny = op.ny;
@@ -187,7 +127,7 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op2<T> op, Vec2<T> v, FftPlanDev<T>
 // reaction field, mask) is staged into shared memory first with many loads in
 // flight; the stencil then runs out of shared memory (layout UpdLayout).
 template <typename T, int D, int FX>
-__global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R) {
+__global__ void FFTMECH_BOUNDS(T) k_update(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int R) {
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
   const int bp = blockIdx.y;
@@ -323,7 +263,7 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op2<T> op, Vec2<T> v, FftPlanDev<T> p
 // z = row-IFFT(S) (rows y0 .. y0 + rows, one halo row), p = z + beta p_old,
 // <p, K p> = sum of the energy density over the tile (layout DirLayout).
 template <typename T, int D, int FX>
-__global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T> px, int R) {
+__global__ void FFTMECH_BOUNDS(T) k_direction(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int R) {
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
   const int bp = blockIdx.y;
@@ -422,7 +362,7 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op2<T> op, Vec2<T> v, FftPlanDev<T
 // <r, M^-1 r> = (1/N) sum_k m(k) |S(k)|^2 for the packed field), inverse
 // column FFT. COL_PLAIN: one column FFT only (sign from `inverse`).
 template <typename T, int FY>
-__global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev<T> py, Spec2<T> sp, int CW,
+__global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev<T> py, Spec<T> sp, int CW,
                                             int mode, int inverse, double* partials, SolverScalars* sc,
                                             const int* pmode) {
   const int bp = blockIdx.y;
@@ -539,7 +479,7 @@ static cudaError_t set_smem(K kernel, size_t bytes, int& configured) {
 }
 
 template <typename T, int D, int FX>
-cudaError_t launch_residual(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+cudaError_t launch_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                             const Shape2& sh, int zero_u, int filter, cudaStream_t st) {
   const int R = sh.rows_res;
   const size_t sm = smem_residual<T, D>(op.nx, R);
@@ -552,7 +492,7 @@ cudaError_t launch_residual(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev
 }
 
 template <typename T, int D, int FX>
-cudaError_t launch_update(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+cudaError_t launch_update(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                           const Shape2& sh, cudaStream_t st) {
   const int R = sh.rows_update;
   const size_t sm = smem_update<T, D>(op.nx, R);
@@ -565,7 +505,7 @@ cudaError_t launch_update(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T
 }
 
 template <typename T, int D, int FX>
-cudaError_t launch_direction(const Op2<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+cudaError_t launch_direction(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                              const Shape2& sh, cudaStream_t st) {
   const int R = sh.rows_dir;
   const size_t sm = smem_direction<T, D>(op.nx, R);
@@ -578,7 +518,7 @@ cudaError_t launch_direction(const Op2<T>& op, const Vec2<T>& v, const FftPlanDe
 }
 
 template <typename T, int FY>
-cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec2<T>& sp,
+cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec<T>& sp,
                            const Shape2& sh, int mode, int inverse, double* partials,
                            SolverScalars* sc, const int* pmode, cudaStream_t st) {
   const int CW = sh.cols;
@@ -607,18 +547,18 @@ cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int
 
 // Explicit instantiations for one radix family (one translation unit each).
 #define FFTMECH_INST_TD(T, D, F)                                                                   \
-  template cudaError_t launch_residual<T, D, F>(const Op2<T>&, const Vec2<T>&,                    \
+  template cudaError_t launch_residual<T, D, F>(const Op<T>&, const Vec2<T>&,                    \
                                                 const FftPlanDev<T>&, const Shape2&, int, int,    \
                                                 cudaStream_t);                                    \
-  template cudaError_t launch_update<T, D, F>(const Op2<T>&, const Vec2<T>&, const FftPlanDev<T>&, \
+  template cudaError_t launch_update<T, D, F>(const Op<T>&, const Vec2<T>&, const FftPlanDev<T>&, \
                                               const Shape2&, cudaStream_t);                       \
-  template cudaError_t launch_direction<T, D, F>(const Op2<T>&, const Vec2<T>&,                   \
+  template cudaError_t launch_direction<T, D, F>(const Op<T>&, const Vec2<T>&,                   \
                                                  const FftPlanDev<T>&, const Shape2&, cudaStream_t);
 #define FFTMECH_INST_T(T, F)                                                                       \
   FFTMECH_INST_TD(T, 1, F)                                                                         \
   FFTMECH_INST_TD(T, 2, F)                                                                         \
   template cudaError_t launch_colpass<T, F>(int, int, cx<T>*, const FftPlanDev<T>&,               \
-                                            const Spec2<T>&, const Shape2&, int, int, double*,    \
+                                            const Spec<T>&, const Shape2&, int, int, double*,    \
                                             SolverScalars*, const int*, cudaStream_t);            \
   template cudaError_t launch_rowfft<T, F>(int, int, cx<T>*, const FftPlanDev<T>&, int,           \
                                            const Shape2&, cudaStream_t);

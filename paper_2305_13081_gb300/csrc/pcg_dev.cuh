@@ -1,0 +1,113 @@
+// Device-side PCG bookkeeping shared by the 2D and 3D kernels: the
+// finalisers that the last block of a reduction runs on the solver scalars.
+#pragma once
+
+#include "fftmech_internal.cuh"
+#include "fftmech.h"
+
+namespace fftmech {
+
+static __device__ __forceinline__ int wrap_y(int y, int ny) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); }
+
+static __device__ __forceinline__ int done_flag(const SolverScalars* sc) {
+  return *reinterpret_cast<const volatile int*>(&sc->done);
+}
+
+static __device__ __forceinline__ double vol_read(const double* p) {
+  return *reinterpret_cast<const volatile double*>(p);
+}
+
+// ---------------------------------------------------------------- finalisers
+static __device__ void finalize_direction(SolverScalars* sc, double pq) {
+  sc->pq = pq;
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    sc->done = 1;
+    sc->status = FFTMECH_ERR_NONFINITE;
+    return;
+  }
+  sc->alpha = sc->rz / pq;
+}
+
+static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
+  if (mode == COL_NORM) { sc->rz0 = tot; return; }
+  if (mode == COL_PLAIN) return;
+  if (mode == COL_TRUENORM) { sc->rz_true = tot; return; }
+  if (!isfinite(tot)) {
+    sc->rz = tot;
+    sc->done = 1;
+    sc->status = FFTMECH_ERR_NONFINITE;
+    return;
+  }
+  if (mode == COL_INIT) {
+    sc->rz = tot;
+    sc->beta = 0.0;
+    sc->iter = 0;
+    if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
+    else if (sc->max_iter <= 0) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
+    return;
+  }
+  if (mode == COL_RESTART) {
+    // the true residual replaced r after a recursive convergence: restart
+    sc->rz = tot;
+    sc->rz_true = tot;
+    sc->beta = 0.0;
+    if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
+    else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
+    return;
+  }
+  sc->iter += 1;
+  if (mode == COL_TRUE) sc->rz_true = tot;
+  const double rz_old = sc->rz;
+  sc->rz = tot;
+  if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; return; }
+  if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; return; }
+  double beta = tot / rz_old;
+  // a replaced residual larger than the recursive one it replaces means the
+  // float recursion had drifted: restart the direction instead of mixing
+  if (mode == COL_TRUE && beta > 1.0) beta = 0.0;
+  sc->beta = beta;
+}
+
+// A column / line pass runs for problem b in this mode: ITER and TRUE skip
+// converged problems, RESTART runs only for the problems being restarted.
+static __device__ __forceinline__ bool col_active(int mode, const int* pmode, const SolverScalars* sc) {
+  if (mode == COL_RESTART) return pmode && *pmode == 2;
+  if (mode == COL_ITER || mode == COL_TRUE) return !done_flag(sc);
+  return true;
+}
+
+// publish_partials / gather_partials for launches whose blocks of one
+// problem are not just blockIdx.x: this block writes slot `slot` of `total`.
+template <int K>
+__device__ __forceinline__ bool publish_partials_at(const double (&v)[K], double* partials, int slot,
+                                                    int total, unsigned int* counter) {
+  __shared__ int am_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)slot * K + k] = v[k];
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    am_last = (prev == (unsigned int)total - 1);
+  }
+  __syncthreads();
+  return am_last != 0;
+}
+
+template <int K>
+__device__ __forceinline__ void gather_partials_n(double (&tot)[K], const double* partials, int total,
+                                                  unsigned int* counter, double* scratch) {
+  __threadfence();
+  double v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = 0.0;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __ldcg(partials + (size_t)b * K + k);
+  }
+  block_sum<K>(v, scratch);
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = v[k];
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+}  // namespace fftmech

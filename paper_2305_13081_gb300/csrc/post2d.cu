@@ -16,7 +16,7 @@ static inline int post_grid(long long n) {
 // per problem (blockIdx.y) sums of stress, strain and the energy density
 // 1/2 (strain - e I) : stress -> results[b * 7 + k].
 template <typename T>
-__global__ void k_el_output(Op2<T> op, const double* __restrict__ u, T* strain, T* stress,
+__global__ void k_el_output(Op<T> op, const double* __restrict__ u, T* strain, T* stress,
                             double* partials, double* results, SolverScalars* sc) {
   __shared__ double red[32 * 7];
   const int nx = op.nx, ny = op.ny;
@@ -67,7 +67,7 @@ __global__ void k_el_output(Op2<T> op, const double* __restrict__ u, T* strain, 
 // beta_pore, beta_solid. results[b * 5 + .]: beta_pore, beta_solid, <jx>,
 // <jy>, porosity.
 template <typename T>
-__global__ void k_diff_stats(Op2<T> op, const double* __restrict__ phi, double hdiff,
+__global__ void k_diff_stats(Op<T> op, const double* __restrict__ phi, double hdiff,
                              double c_macro, double* partials, double* results, SolverScalars* sc) {
   __shared__ double red[32 * 10];
   const int nx = op.nx, ny = op.ny;
@@ -274,14 +274,14 @@ static inline dim3 post_grid_b(long long n, int batch) {
 }
 
 template <typename T>
-cudaError_t launch_el_output(const Op2<T>& op, int batch, const double* u, T* strain, T* stress,
+cudaError_t launch_el_output(const Op<T>& op, int batch, const double* u, T* strain, T* stress,
                              double* partials, double* results, SolverScalars* sc, cudaStream_t st) {
   k_el_output<T><<<post_grid_b((long long)op.nx * op.ny, batch), kPostThreads, 0, st>>>(
       op, u, strain, stress, partials, results, sc);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_diff_stats(const Op2<T>& op, int batch, const double* phi, double hdiff,
+cudaError_t launch_diff_stats(const Op<T>& op, int batch, const double* phi, double hdiff,
                               double c_macro, double* partials, double* results, SolverScalars* sc,
                               cudaStream_t st) {
   k_diff_stats<T><<<post_grid_b((long long)op.nx * op.ny, batch), kPostThreads, 0, st>>>(
@@ -348,9 +348,9 @@ cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t 
 }
 
 #define FFTMECH_POST_INST(T)                                                                       \
-  template cudaError_t launch_el_output<T>(const Op2<T>&, int, const double*, T*, T*, double*,     \
+  template cudaError_t launch_el_output<T>(const Op<T>&, int, const double*, T*, T*, double*,     \
                                            double*, SolverScalars*, cudaStream_t);                 \
-  template cudaError_t launch_diff_stats<T>(const Op2<T>&, int, const double*, double, double,     \
+  template cudaError_t launch_diff_stats<T>(const Op<T>&, int, const double*, double, double,     \
                                             double*, double*, SolverScalars*, cudaStream_t);       \
   template cudaError_t launch_history<T>(long long, int, const uint8_t*, double, double, double,   \
                                          double, const T*, const T*, T*, double*, double, double*, \
