@@ -275,7 +275,7 @@ struct Solve {
 // failed) stops moving while the others continue. MIXED: the iterate is a
 // float pair, with reliable updates and a final FP64 true-residual gate.
 template <typename T, int D>
-fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op, double* u, const Spec<T>& sp_in,
+fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Spec<T>& sp_in,
                        std::vector<Solve>& out) {
   cudaStream_t st = ctx->stream;
   const int B = ctx->B;
@@ -285,6 +285,17 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op, double* u, const Spec<
   sp.lamx = (const T*)ctx->lamx;
   sp.lamy = (const T*)ctx->lamy;
   sp.invN = 1.0 / (double)ctx->N;
+  sp.m0_t = (T)sp.m0;
+  sp.m1_t = (T)sp.m1;
+  sp.invN_t = (T)sp.invN;
+  Op<T> op = op_in;  // with the constants rounded to T
+  op.ih_t = (T)(1.0 / op.h);
+  for (int k = 0; k < 2; ++k) {
+    op.lam_t[k] = (T)op.lam[k];
+    op.mu_t[k] = (T)op.mu[k];
+    op.kap_t[k] = (T)op.kap[k];
+  }
+  op.c0c_t = (T)op.c0c;
   for (int b = 0; b < B; ++b) {
     SolverScalars h{};
     h.tol2 = ctx->opts.tol * ctx->opts.tol;

@@ -378,6 +378,21 @@ __device__ void fft_lines(cx<T>* buf, const FftPlanDev<T>& p, int nlines, int ls
   }
 }
 
+// Twiddles of a plan in shared memory: kernels copy the n - 1 entries to
+// the start of their dynamic shared memory (with the other staged loads,
+// before their first barrier) so the passes read them with short latency.
+template <typename T>
+__host__ __device__ inline size_t tw_smem_bytes(int n) {
+  return ((size_t)(n > 1 ? n - 1 : 0) * sizeof(cx<T>) + 15) & ~size_t(15);
+}
+template <typename T>
+__device__ __forceinline__ FftPlanDev<T> plan_to_smem(const FftPlanDev<T>& p, cx<T>* dst) {
+  g2s_vec<4, true>(dst, p.tw, p.n > 1 ? p.n - 1 : 0);
+  FftPlanDev<T> q = p;
+  q.tw = dst;
+  return q;
+}
+
 // fft_lines as a real call: a kernel that keeps much state live across a
 // loop around the transform saves it once per call instead of spilling
 // inside the butterflies.
@@ -415,6 +430,56 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
     }
   }
   __syncthreads();
+}
+
+// Double-float accumulator (h + l, |l| <= ulp(h) / 2): error-free TwoSum
+// (Knuth) keeps FP64-like accuracy with float instructions only, which
+// float kernels use so that their reductions need no FP64 pipe.
+struct dfloat {
+  float h, l;
+};
+__device__ __forceinline__ dfloat df_add(dfloat a, float b) {
+  const float s = a.h + b;
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b - bb);
+  const float l = a.l + e;
+  const float h2 = s + l;
+  return dfloat{h2, l - (h2 - s)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb);
+  const float l = a.l + b.l + e;
+  const float h2 = s + l;
+  return dfloat{h2, l - (h2 - s)};
+}
+// Block sum of double-float values, returned as double in thread 0 (others
+// get a partial). scratch: 64 floats of shared memory.
+__device__ __forceinline__ double block_sum_df(dfloat v, float* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const dfloat w{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+    v = df_add(v, w);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    scratch[2 * wid] = v.h;
+    scratch[2 * wid + 1] = v.l;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < nw ? dfloat{scratch[2 * lane], scratch[2 * lane + 1]} : dfloat{0.f, 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const dfloat w{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+      v = df_add(v, w);
+    }
+  }
+  __syncthreads();
+  return (double)v.h + (double)v.l;
 }
 
 // Publish this block's K partial sums; returns true in every thread of the

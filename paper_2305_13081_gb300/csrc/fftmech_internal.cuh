@@ -21,6 +21,9 @@ struct SolverScalars {
   double rz_true;  // <r, M^-1 r> right after the last true-residual replacement
   int iter, max_iter, done, status;
   unsigned int cnt[4];  // last-block counters: 0 direction, 1 column pass, 2 stats
+  // float copies for the float kernels (no FP64 instruction in their hot
+  // path): alpha = alpha_h + alpha_l, beta rounded
+  float alpha_h, alpha_l, beta_f, pad_f;
 };
 
 // Column-pass modes: ITER (one PCG iteration: beta, convergence), NORM
@@ -58,6 +61,9 @@ struct Op {
   const double* srcd;
   const T* srct;
   double src_scale;
+  // the constants above rounded to T by the host (the float kernels use
+  // these, so they convert nothing per thread): 1/h, lam, mu, kap, c0c
+  T ih_t, lam_t[2], mu_t[2], kap_t[2], c0c_t;
 };
 
 // The iterate: double in FP64; in MIXED an unevaluated float pair
@@ -117,6 +123,7 @@ struct Spec {
   const T* lamj;
   const T* laml;
   const T* wcol;
+  T m0_t, m1_t, invN_t;  // m0, m1, invN rounded to T by the host
 };
 
 // Launch shapes chosen by the host.

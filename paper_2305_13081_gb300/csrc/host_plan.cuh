@@ -122,9 +122,10 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   const size_t optin = optin_total - 1024;  // room for the kernels' static shared memory
   const int tmax = 512;
   const size_t budget = std::min<size_t>(optin, sizeof(T) == 4 ? 100 * 1024 : 110 * 1024);
+  const size_t twx = tw_smem_bytes<T>(nx), twy = tw_smem_bytes<T>(ny);
   auto fits = [&](int r, size_t lim) {
-    return smem_update<T, 2>(nx, r) <= lim && smem_direction<T, 2>(nx, r) <= lim &&
-           smem_update<T, 1>(nx, r) <= lim && smem_direction<T, 1>(nx, r) <= lim &&
+    return smem_update<T, 2>(nx, r) + twx <= lim && smem_direction<T, 2>(nx, r) + twx <= lim &&
+           smem_update<T, 1>(nx, r) + twx <= lim && smem_direction<T, 1>(nx, r) + twx <= lim &&
            need_threads(px, r + 1) <= tmax;
   };
   int R = std::max(1, std::min(ny, ny / (2 * nsm)));
@@ -136,12 +137,12 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   s.threads_update = std::min(tmax, std::max(256, round32(need_threads(px, R + 1))));
   s.threads_dir = s.threads_update;
   s.rows_res = 1;
-  if (smem_residual<T, 2>(nx, 1) > optin || smem_residual<T, 1>(nx, 1) > optin) return false;
+  if (smem_residual<T, 2>(nx, 1) + twx > optin || smem_residual<T, 1>(nx, 1) + twx > optin) return false;
   s.threads_res = std::min(tmax, std::max(256, round32(need_threads(px, 1))));
   int CW = sizeof(T) == 4 ? 8 : 4;
   while (CW > 2 && (nx + CW - 1) / CW < 2 * nsm) CW /= 2;  // at least two strips per SM when possible
-  while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) > budget || need_threads(py, CW) > tmax)) CW /= 2;
-  if ((size_t)ny * CW * sizeof(cx<T>) > optin || need_threads(py, CW) > tmax) return false;
+  while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) + twy > budget || need_threads(py, CW) > tmax)) CW /= 2;
+  if ((size_t)ny * CW * sizeof(cx<T>) + twy > optin || need_threads(py, CW) > tmax) return false;
   s.cols = CW;
   s.threads_col = std::min(tmax, std::max(128, round32(need_threads(py, CW))));
   s.threads_plain = s.threads_update;
@@ -168,17 +169,18 @@ bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, i
   s.nz = nz;
   s.sst = (long long)(nx + nx / 2 + 1) * ny * nz;
   auto idx_ok = [&](int r) { return (long long)(r + 2) * nx < 65536 && (long long)r * nxs_of(nx, 3) < 65536; };
+  const size_t twx = tw_smem_bytes<T>(nx);
   auto upd_fits = [&](int r, size_t lim) {
-    return idx_ok(r) && Row3Layout(nx, r, es, es, 3, 0).total <= lim && Row3Layout(nx, r, es, es, 1, 0).total <= lim &&
-           need_threads(px, 2 * r) <= 256;
+    return idx_ok(r) && Row3Layout(nx, r, es, es, 3, 0).total + twx <= lim &&
+           Row3Layout(nx, r, es, es, 1, 0).total + twx <= lim && need_threads(px, 2 * r) <= 256;
   };
   auto dir_fits = [&](int r, size_t lim) {
-    return idx_ok(r) && Dir3Layout(nx, r, es, 3).total <= lim && Dir3Layout(nx, r, es, 1).total <= lim &&
+    return idx_ok(r) && Dir3Layout(nx, r, es, 3).total + twx <= lim && Dir3Layout(nx, r, es, 1).total + twx <= lim &&
            need_threads(px, 2 * (r + 1)) <= 256;
   };
   auto res_fits = [&](int r, size_t lim) {
-    return idx_ok(r) && Row3Layout(nx, r, 8, es, 3, 1).total <= lim && Row3Layout(nx, r, 8, es, 1, 1).total <= lim &&
-           need_threads(px, 2 * r) <= tmax;
+    return idx_ok(r) && Row3Layout(nx, r, 8, es, 3, 1).total + twx <= lim &&
+           Row3Layout(nx, r, 8, es, 1, 1).total + twx <= lim && need_threads(px, 2 * r) <= tmax;
   };
   auto pick = [&](auto fits) {
     int r = std::min(ny, 8);
@@ -207,10 +209,11 @@ bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, i
   s.thr_res = std::min(tmax, std::max(128, round32(need_threads(px, 2 * s.ry_res))));
   auto strip = [&](const HostPlan& pl, int& cw, int& thr) {
     int c = sizeof(T) == 4 ? 16 : 8;
-    while (c > 1 && ((size_t)pl.n * c * sizeof(cx<T>) > budget || need_threads(pl, c) > tmax ||
+    const size_t tw = tw_smem_bytes<T>(pl.n);
+    while (c > 1 && ((size_t)pl.n * c * sizeof(cx<T>) + tw > budget || need_threads(pl, c) > tmax ||
                      (long long)pl.n * c >= 65536))
       c /= 2;
-    if ((size_t)pl.n * c * sizeof(cx<T>) > optin || need_threads(pl, c) > tmax) return false;
+    if ((size_t)pl.n * c * sizeof(cx<T>) + tw > optin || need_threads(pl, c) > tmax) return false;
     cw = c;
     thr = std::min(tmax, std::max(128, round32(need_threads(pl, c))));
     return true;
@@ -229,7 +232,7 @@ bool choose_shape_fft(const HostPlan& px, const HostPlan& py, int nsm, size_t op
   const size_t optin = optin_total - 1024;
   int R = std::max(1, std::min(ny, ny / (2 * nsm)));
   auto fits = [&](int r) {
-    return (size_t)r * nx * sizeof(cx<T>) <= optin && need_threads(px, r) <= tmax;
+    return (size_t)r * nx * sizeof(cx<T>) + tw_smem_bytes<T>(nx) <= optin && need_threads(px, r) <= tmax;
   };
   while (R > 1 && !fits(R)) --R;
   if (!fits(R)) return false;
@@ -241,8 +244,9 @@ bool choose_shape_fft(const HostPlan& px, const HostPlan& py, int nsm, size_t op
   s.threads_res = s.threads_update;
   int CW = sizeof(T) == 4 ? 8 : 4;
   while (CW > 2 && (nx + CW - 1) / CW < 2 * nsm) CW /= 2;
-  while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) > optin || need_threads(py, CW) > tmax)) CW /= 2;
-  if ((size_t)ny * CW * sizeof(cx<T>) > optin || need_threads(py, CW) > tmax) return false;
+  const size_t twy = tw_smem_bytes<T>(ny);
+  while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) + twy > optin || need_threads(py, CW) > tmax)) CW /= 2;
+  if ((size_t)ny * CW * sizeof(cx<T>) + twy > optin || need_threads(py, CW) > tmax) return false;
   s.cols = CW;
   s.threads_col = std::min(tmax, std::max(128, round32(need_threads(py, CW))));
   return true;

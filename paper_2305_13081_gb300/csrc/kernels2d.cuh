@@ -27,7 +27,9 @@ namespace fftmech {
 template <typename T, int D, int FX>
 __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int zero_u,
                                              int filter) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
   const int bp = blockIdx.y;
@@ -117,7 +119,7 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
     F[i] = mk(t0, t1);
   }
   __syncthreads();
-  fft_lines<T, -1, FX>(F, px, rows, nx, 1, false);
+  fft_lines<T, -1, FX>(F, px_s, rows, nx, 1, false);
   for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) v.S[(size_t)y0 * nx + i] = F[i];
 }
 
@@ -134,9 +136,19 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op<T> op, Vec2<T> v, FftPlanDev<T> px
   const int u_only = v.mode ? (v.mode[bp] == 1) : 0;  // reliable update: iterate only
   problem_views<T, D>(op, v, bp, N);
   if (done_flag(v.sc)) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const double alpha = vol_read(&v.sc->alpha);
-  const T a = (T)alpha;
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
+  // alpha: a double for the FP64 path, a float pair (ah + al) for MIXED
+  double alpha = 0.0;
+  float ah = 0.f, al = 0.f;
+  if constexpr (sizeof(T) == 4) {
+    ah = vol_readf(&v.sc->alpha_h);
+    al = vol_readf(&v.sc->alpha_l);
+  } else {
+    alpha = vol_read(&v.sc->alpha);
+  }
+  const T a = sizeof(T) == 4 ? (T)ah : (T)alpha;
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
   const int tid = threadIdx.x, bd = blockDim.x;
@@ -146,7 +158,6 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op<T> op, Vec2<T> v, FftPlanDev<T> px
     for (int c = 0; c < D; ++c) {
       const T* p = v.p_in + c * N + t0;
       if constexpr (sizeof(T) == 4) {
-        const float ah = (float)alpha, al = (float)(alpha - (double)ah);
         float* uh = v.uh + c * N + t0;
         float* ul = v.ul + c * N + t0;
         for (int i = tid; i < rows * nx; i += bd) {
@@ -185,7 +196,6 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op<T> op, Vec2<T> v, FftPlanDev<T> px
   __syncthreads();
   // iterate update on the tile rows (rows 1 .. rows of P)
   if constexpr (sizeof(T) == 4) {
-    const float ah = (float)alpha, al = (float)(alpha - (double)ah);
 #pragma unroll
     for (int c = 0; c < D; ++c)
       df_axpy_g<8>(v.uh + c * N + t0, v.ul + c * N + t0, P + (size_t)c * W * nx + nx, ah, al, rows * nx);
@@ -194,10 +204,10 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op<T> op, Vec2<T> v, FftPlanDev<T> px
     for (int c = 0; c < D; ++c) axpy_g<8>(v.u + c * N + t0, P + (size_t)c * W * nx + nx, alpha, rows * nx);
   }
   // stresses (D = 2) or fluxes (D = 1) at rows y0 - 1 .. y0 + rows - 1
-  const T ih = (T)(1.0 / op.h);
-  const T lam0 = (T)op.lam[0], lam1 = (T)op.lam[1], mu0 = (T)op.mu[0], mu1 = (T)op.mu[1];
-  const T kap0 = (T)op.kap[0], kap1 = (T)op.kap[1];
-  const T c0c = (T)op.c0c;
+  const T ih = op.ih_t;
+  const T lam0 = op.lam_t[0], lam1 = op.lam_t[1], mu0 = op.mu_t[0], mu1 = op.mu_t[1];
+  const T kap0 = op.kap_t[0], kap1 = op.kap_t[1];
+  const T c0c = op.c0c_t;
   for (int yy = 0; yy <= rows; ++yy) {
     for (int x = tid; x < nx; x += bd) {
       const int xp = (x + 1 == nx) ? 0 : x + 1;
@@ -255,7 +265,7 @@ __global__ void FFTMECH_BOUNDS(T) k_update(Op<T> op, Vec2<T> v, FftPlanDev<T> px
     }
   }
   __syncthreads();
-  fft_lines<T, -1, FX>(F, px, rows, nx, 1, false);
+  fft_lines<T, -1, FX>(F, px_s, rows, nx, 1, false);
   s2g(v.S + t0, F, rows * nx);
 }
 
@@ -270,10 +280,14 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op<T> op, Vec2<T> v, FftPlanDev<T>
   problem_views<T, D>(op, v, bp, N);
   if (done_flag(v.sc)) return;
   double* partials = v.partials + (size_t)bp * gridDim.x;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   __shared__ double red[32];
-  const double beta = vol_read(&v.sc->beta);
-  const T b = (T)beta;
+  __shared__ float redf[64];
+  T b;
+  if constexpr (sizeof(T) == 4) b = vol_readf(&v.sc->beta_f);
+  else b = vol_read(&v.sc->beta);
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
   const int W = rows + 1;
@@ -288,7 +302,8 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op<T> op, Vec2<T> v, FftPlanDev<T>
   const T* matg = (D == 2) ? op.g : op.c0f;
   const bool masked = (D == 1) && op.mask;
   g2s_rows<8>(F, v.S, y0, W, nx, ny);
-  if (beta != 0.0) {  // the first iteration has p = z
+  const bool with_old = b != T(0);  // the first iteration has p = z
+  if (with_old) {
 #pragma unroll
     for (int c = 0; c < D; ++c) g2s_rows<8>(P + (size_t)c * W * nx, v.p_in + c * N, y0, W, nx, ny);
   }
@@ -296,8 +311,7 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op<T> op, Vec2<T> v, FftPlanDev<T>
   g2s_vec<8, true>(PH, op.phase + t0, rows * nx);
   if (masked) g2s_rows<8>(MK, op.mask, y0, W, nx, ny);
   __syncthreads();
-  fft_lines<T, 1, FX>(F, px, W, nx, 1, false);
-  const bool with_old = beta != 0.0;  // hoisted: no FP64 compare in the loop
+  fft_lines<T, 1, FX>(F, px_s, W, nx, 1, false);
   for (int yy = 0; yy < W; ++yy) {
     for (int x = tid; x < nx; x += bd) {
       const int i = yy * nx + x;
@@ -316,11 +330,11 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op<T> op, Vec2<T> v, FftPlanDev<T>
     }
   }
   __syncthreads();
-  const T ih = (T)(1.0 / op.h);
-  const T lam0 = (T)op.lam[0], lam1 = (T)op.lam[1], mu0 = (T)op.mu[0], mu1 = (T)op.mu[1];
-  const T kap0 = (T)op.kap[0], kap1 = (T)op.kap[1];
-  const T c0c = (T)op.c0c;
-  double acc[1] = {0.0};
+  const T ih = op.ih_t;
+  const T lam0 = op.lam_t[0], lam1 = op.lam_t[1], mu0 = op.mu_t[0], mu1 = op.mu_t[1];
+  const T kap0 = op.kap_t[0], kap1 = op.kap_t[1];
+  const T c0c = op.c0c_t;
+  Acc<T> acc;
   for (int yy = 0; yy < rows; ++yy) {
     T part = T(0);
     for (int x = tid; x < nx; x += bd) {
@@ -346,10 +360,10 @@ __global__ void FFTMECH_BOUNDS(T) k_direction(Op<T> op, Vec2<T> v, FftPlanDev<T>
       }
       part += w;  // a few terms per thread and row, all non-negative
     }
-    acc[0] += (double)part;
+    acc.add(part);
   }
-  block_sum<1>(acc, red);
-  if (publish_partials<1>(acc, partials, &v.sc->cnt[0])) {
+  const double bt[1] = {acc.block_total(redf, red)};
+  if (publish_partials<1>(bt, partials, &v.sc->cnt[0])) {
     double tot[1];
     gather_partials<1>(tot, partials, &v.sc->cnt[0], red);
     if (threadIdx.x == 0) finalize_direction(v.sc, tot[0]);
@@ -374,8 +388,11 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   if (mode != COL_PLAIN && mode != COL_NORM && mode != COL_TRUENORM && mode != COL_RESTART &&
       done_flag(sc))
     return;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(py.n);
+  const FftPlanDev<T> py_s = plan_to_smem(py, reinterpret_cast<cx<T>*>(smem_all));
   __shared__ double red[32];
+  __shared__ float redf[64];
   cx<T>* B = reinterpret_cast<cx<T>*>(smem);
   const int x0 = blockIdx.x * CW;
   const int nc = min(CW, nx - x0);
@@ -399,16 +416,16 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   }
   __syncthreads();
   if (mode == COL_PLAIN) {
-    if (inverse) fft_lines<T, 1, FY>(B, py, nc, 1, nc, true);
-    else fft_lines<T, -1, FY>(B, py, nc, 1, nc, true);
+    if (inverse) fft_lines<T, 1, FY>(B, py_s, nc, 1, nc, true);
+    else fft_lines<T, -1, FY>(B, py_s, nc, 1, nc, true);
   } else {
-    fft_lines<T, -1, FY>(B, py, nc, 1, nc, true);
+    fft_lines<T, -1, FY>(B, py_s, nc, 1, nc, true);
   }
   const bool store = (mode != COL_NORM && mode != COL_TRUENORM);
-  double acc[1] = {0.0};
+  Acc<T> acc;
   if (mode != COL_PLAIN) {
-    const T m0 = (T)(sp.m0b ? sp.m0b[bp] : sp.m0), m1 = (T)(sp.m1b ? sp.m1b[bp] : sp.m1);
-    const T invN = (T)sp.invN;
+    const T m0 = sp.m0b ? (T)sp.m0b[bp] : sp.m0_t, m1 = sp.m1b ? (T)sp.m1b[bp] : sp.m1_t;
+    const T invN = sp.invN_t;
     T part = T(0);
     int cnt = 0;
     for (int i = threadIdx.x; i < n; i += bd) {
@@ -419,13 +436,13 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
       else m = den > T(0) ? T(1) / den : T(0);
       const cx<T> w = B[i];
       part += m * (w.re * w.re + w.im * w.im);
-      if (++cnt == 16) { acc[0] += (double)part; part = T(0); cnt = 0; }  // non-negative terms
+      if (++cnt == 16) { acc.add(part); part = T(0); cnt = 0; }  // non-negative terms
       if (store) B[i] = scal(w, m * invN);
     }
-    acc[0] += (double)part;
+    acc.add(part);
     if (store) {
       __syncthreads();
-      fft_lines<T, 1, FY>(B, py, nc, 1, nc, true);
+      fft_lines<T, 1, FY>(B, py_s, nc, 1, nc, true);
     }
   }
   if (store) {
@@ -435,8 +452,8 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
     }
   }
   if (mode == COL_PLAIN) return;
-  block_sum<1>(acc, red);
-  if (publish_partials<1>(acc, partials, &sc->cnt[1])) {
+  const double bt[1] = {acc.block_total(redf, red)};
+  if (publish_partials<1>(bt, partials, &sc->cnt[1])) {
     double tot[1];
     gather_partials<1>(tot, partials, &sc->cnt[1], red);
     if (threadIdx.x == 0) finalize_col(sc, mode, tot[0] * sp.invN);
@@ -446,14 +463,16 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
 // Plain row FFT of S (used by the stand-alone transform).
 template <typename T, int FX>
 __global__ void FFTMECH_BOUNDS(T) k_rowfft(int nx, int ny, cx<T>* S, FftPlanDev<T> px, int R, int inverse) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
   for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) F[i] = S[(size_t)y0 * nx + i];
   __syncthreads();
-  if (inverse) fft_lines<T, 1, FX>(F, px, rows, nx, 1, false);
-  else fft_lines<T, -1, FX>(F, px, rows, nx, 1, false);
+  if (inverse) fft_lines<T, 1, FX>(F, px_s, rows, nx, 1, false);
+  else fft_lines<T, -1, FX>(F, px_s, rows, nx, 1, false);
   for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) S[(size_t)y0 * nx + i] = F[i];
 }
 
@@ -482,7 +501,7 @@ template <typename T, int D, int FX>
 cudaError_t launch_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                             const Shape2& sh, int zero_u, int filter, cudaStream_t st) {
   const int R = sh.rows_res;
-  const size_t sm = smem_residual<T, D>(op.nx, R);
+  const size_t sm = smem_residual<T, D>(op.nx, R) + tw_smem_bytes<T>(op.nx);
   static int cfg = 0;
   cudaError_t e = set_smem(k_residual<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
@@ -495,7 +514,7 @@ template <typename T, int D, int FX>
 cudaError_t launch_update(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                           const Shape2& sh, cudaStream_t st) {
   const int R = sh.rows_update;
-  const size_t sm = smem_update<T, D>(op.nx, R);
+  const size_t sm = smem_update<T, D>(op.nx, R) + tw_smem_bytes<T>(op.nx);
   static int cfg = 0;
   cudaError_t e = set_smem(k_update<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
@@ -508,7 +527,7 @@ template <typename T, int D, int FX>
 cudaError_t launch_direction(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                              const Shape2& sh, cudaStream_t st) {
   const int R = sh.rows_dir;
-  const size_t sm = smem_direction<T, D>(op.nx, R);
+  const size_t sm = smem_direction<T, D>(op.nx, R) + tw_smem_bytes<T>(op.nx);
   static int cfg = 0;
   cudaError_t e = set_smem(k_direction<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
@@ -522,7 +541,7 @@ cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, co
                            const Shape2& sh, int mode, int inverse, double* partials,
                            SolverScalars* sc, const int* pmode, cudaStream_t st) {
   const int CW = sh.cols;
-  const size_t sm = (size_t)ny * CW * sizeof(cx<T>);
+  const size_t sm = (size_t)ny * CW * sizeof(cx<T>) + tw_smem_bytes<T>(ny);
   static int cfg = 0;
   cudaError_t e = set_smem(k_colpass<T, FY>, sm, cfg);
   if (e != cudaSuccess) return e;
@@ -536,7 +555,7 @@ template <typename T, int FX>
 cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int inverse,
                           const Shape2& sh, cudaStream_t st) {
   const int R = sh.rows_update;
-  const size_t sm = (size_t)R * nx * sizeof(cx<T>);
+  const size_t sm = (size_t)R * nx * sizeof(cx<T>) + tw_smem_bytes<T>(nx);
   static int cfg = 0;
   cudaError_t e = set_smem(k_rowfft<T, FX>, sm, cfg);
   if (e != cudaSuccess) return e;

@@ -117,20 +117,27 @@ __global__ void FFTMECH_BOUNDS3 k3_rows(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   if (KIND == 1 && filter && !(v.mode && v.mode[bp] != 0)) return;
   problem_views3<T, D>(op, v, bp, N, sst);
   int u_only = 0;
-  double alpha = 0.0;
+  double alpha = 0.0;  // FP64 path
+  float ah = 0.f, al = 0.f;  // MIXED: alpha = ah + al
   if constexpr (KIND == 0) {
     u_only = v.mode ? (v.mode[bp] == 1) : 0;
     if (done_flag(v.sc)) return;
-    alpha = vol_read(&v.sc->alpha);
+    if constexpr (sizeof(T) == 4) {
+      ah = vol_readf(&v.sc->alpha_h);
+      al = vol_readf(&v.sc->alpha_l);
+    } else {
+      alpha = vol_read(&v.sc->alpha);
+    }
   }
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   const int nty = (ny + R - 1) / R;
   const int tz = blockIdx.x / nty, ty = blockIdx.x - tz * nty;
   const int y0 = ty * R, rows = min(R, ny - y0);
   const int z0 = tz * Zc, planes = min(Zc, nz - z0);
   const int tid = threadIdx.x, bd = blockDim.x;
   const int nxa = D == 3 ? nx : 0, nxh = nx / 2 + 1, nxs = nxa + nxh;
-  const float ah = (float)alpha, al = (float)(alpha - (double)ah);
   if constexpr (KIND == 0) {
     if (u_only) {  // reliable-update iteration: only the iterate moves
       for (int zz = z0; zz < z0 + planes; ++zz) {
@@ -169,11 +176,13 @@ __global__ void FFTMECH_BOUNDS3 k3_rows(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const size_t SS = (size_t)(R + 1) * nx;   // one stress component of one plane
   const T* matg = (D == 3) ? op.g : op.c0f;
   const bool masked = (D == 1) && op.mask;
-  const CT ih = (CT)(1.0 / op.h);
-  const CT lam0 = (CT)op.lam[0], lam1 = (CT)op.lam[1], mu0 = (CT)op.mu[0], mu1 = (CT)op.mu[1];
-  const CT kap0 = (CT)op.kap[0], kap1 = (CT)op.kap[1];
-  const CT c0c = (CT)op.c0c;
-  const CT a = (CT)alpha;
+  // KIND 0 computes in T with the host-rounded constants; KIND 1 in FP64
+  const CT ih = KIND == 0 ? (CT)op.ih_t : (CT)(1.0 / op.h);
+  const CT lam0 = KIND == 0 ? (CT)op.lam_t[0] : (CT)op.lam[0], lam1 = KIND == 0 ? (CT)op.lam_t[1] : (CT)op.lam[1];
+  const CT mu0 = KIND == 0 ? (CT)op.mu_t[0] : (CT)op.mu[0], mu1 = KIND == 0 ? (CT)op.mu_t[1] : (CT)op.mu[1];
+  const CT kap0 = KIND == 0 ? (CT)op.kap_t[0] : (CT)op.kap[0], kap1 = KIND == 0 ? (CT)op.kap_t[1] : (CT)op.kap[1];
+  const CT c0c = KIND == 0 ? (CT)op.c0c_t : (CT)op.c0c;
+  const CT a = sizeof(T) == 4 ? (CT)ah : (CT)alpha;
   const FastDiv dnx(nx);
 
   load_plane3<T, CT, D, KIND>(P, op, v, z0 - 1, 0, y0, W, PS, N, zero_u);
@@ -320,7 +329,7 @@ __global__ void FFTMECH_BOUNDS3 k3_rows(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
       }
     }
     __syncthreads();
-    fft_lines_call<T, -1, FX>(F, px, C::NF * rows, nx, 1, false);
+    fft_lines_call<T, -1, FX>(F, px_s, C::NF * rows, nx, 1, false);
     // store: packed field in full, the real field's half spectrum
     cx<T>* Srow = v.S + ((size_t)zw * ny + y0) * nxs;
     const FastDiv dns(nxs);
@@ -420,11 +429,15 @@ __global__ void FFTMECH_BOUNDS3 k3_direction(Op<T> op, Vec2<T> v, FftPlanDev<T> 
   problem_views3<T, D>(op, v, bp, N, sst);
   if (done_flag(v.sc)) return;
   double* partials = v.partials + (size_t)bp * gridDim.x;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   __shared__ double red[32];
-  const double beta = vol_read(&v.sc->beta);
-  const T b = (T)beta;
-  const bool with_old = beta != 0.0;  // the first iteration has p = z
+  __shared__ float redf[64];
+  T b;
+  if constexpr (sizeof(T) == 4) b = vol_readf(&v.sc->beta_f);
+  else b = vol_read(&v.sc->beta);
+  const bool with_old = b != T(0);  // the first iteration has p = z
   const int nty = (ny + R - 1) / R;
   const int tz = blockIdx.x / nty, ty = blockIdx.x - tz * nty;
   const int y0 = ty * R, rows = min(R, ny - y0);
@@ -444,15 +457,15 @@ __global__ void FFTMECH_BOUNDS3 k3_direction(Op<T> op, Vec2<T> v, FftPlanDev<T> 
   const FastDiv dnx(nx);
   cx<T>* FB = F + (size_t)(C::NF - 1) * W * nx;  // the real field's lines
 
-  const T ih = (T)(1.0 / op.h);
-  const T lam0 = (T)op.lam[0], lam1 = (T)op.lam[1], mu0 = (T)op.mu[0], mu1 = (T)op.mu[1];
-  const T kap0 = (T)op.kap[0], kap1 = (T)op.kap[1];
-  const T c0c = (T)op.c0c;
-  double acc[1] = {0.0};
-  make_p3<T, D, FX>(F, P, MK, op, v, px, z0, 0, z0 + planes, y0, rows, R, with_old, b, N);
+  const T ih = op.ih_t;
+  const T lam0 = op.lam_t[0], lam1 = op.lam_t[1], mu0 = op.mu_t[0], mu1 = op.mu_t[1];
+  const T kap0 = op.kap_t[0], kap1 = op.kap_t[1];
+  const T c0c = op.c0c_t;
+  Acc<T> acc;
+  make_p3<T, D, FX>(F, P, MK, op, v, px_s, z0, 0, z0 + planes, y0, rows, R, with_old, b, N);
   for (int zz = z0; zz < z0 + planes; ++zz) {
     const int cur = (zz - z0) & 1, nxt = cur ^ 1;
-    make_p3<T, D, FX>(F, P, MK, op, v, px, zz + 1, nxt, z0 + planes, y0, rows, R, with_old, b, N);
+    make_p3<T, D, FX>(F, P, MK, op, v, px_s, zz + 1, nxt, z0 + planes, y0, rows, R, with_old, b, N);
     const size_t t0 = (size_t)zz * plane + (size_t)y0 * nx;
     if (matg) g2s_vec<4, true>(MG, matg + t0, rows * nx);
     g2s_vec<4, true>(PH, op.phase + t0, rows * nx);
@@ -489,13 +502,13 @@ __global__ void FFTMECH_BOUNDS3 k3_direction(Op<T> op, Vec2<T> v, FftPlanDev<T> 
         w = c0v * p * p + (sol ? kap1 : kap0) * (gx * gx + gy * gy + gz * gz);
       }
       part += w;  // non-negative terms
-      if (++cnt == 16) { acc[0] += (double)part; part = T(0); cnt = 0; }
+      if (++cnt == 16) { acc.add(part); part = T(0); cnt = 0; }
     }
-    acc[0] += (double)part;
+    acc.add(part);
     __syncthreads();
   }
-  block_sum<1>(acc, red);
-  if (publish_partials<1>(acc, partials, &v.sc->cnt[0])) {
+  const double bt[1] = {acc.block_total(redf, red)};
+  if (publish_partials<1>(bt, partials, &v.sc->cnt[0])) {
     double tot[1];
     gather_partials<1>(tot, partials, &v.sc->cnt[0], red);
     if (threadIdx.x == 0) finalize_direction(v.sc, tot[0]);
@@ -521,8 +534,11 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
   if (sc && !col_active(mode, pmode ? pmode + b : nullptr, sc + b)) return;
   if (stage == 1 && mode == COL_ITER && pmode && pmode[b] == 1) mode = COL_TRUE;  // reliable update
   S += (size_t)b * sst + (size_t)j * set_stride;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(pl.n);
+  const FftPlanDev<T> pl_s = plan_to_smem(pl, reinterpret_cast<cx<T>*>(smem_all));
   __shared__ double red[32];
+  __shared__ float redf[64];
   cx<T>* B = reinterpret_cast<cx<T>*>(smem);
   const int x0 = blockIdx.x * CW;
   const int nc = min(CW, ncols - x0);
@@ -544,13 +560,13 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
       if (i + k * bd < n) B[i + k * bd] = t[k];
   }
   __syncthreads();
-  if (stage == 2) fft_lines<T, 1, FL>(B, pl, nc, 1, nc, true);
-  else fft_lines<T, -1, FL>(B, pl, nc, 1, nc, true);
+  if (stage == 2) fft_lines<T, 1, FL>(B, pl_s, nc, 1, nc, true);
+  else fft_lines<T, -1, FL>(B, pl_s, nc, 1, nc, true);
   const bool store = stage != 1 || (mode != COL_NORM && mode != COL_TRUENORM);
-  double acc[1] = {0.0};
+  Acc<T> acc;
   if (stage == 1) {
-    const T m0 = (T)(sp.m0b ? sp.m0b[b] : sp.m0), m1 = (T)(sp.m1b ? sp.m1b[b] : sp.m1);
-    const T invN = (T)sp.invN;
+    const T m0 = sp.m0b ? (T)sp.m0b[b] : sp.m0_t, m1 = sp.m1b ? (T)sp.m1b[b] : sp.m1_t;
+    const T invN = sp.invN_t;
     const T lj = sp.lamj[j];
     T part = T(0);
     int cnt = 0;
@@ -562,13 +578,13 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
       else m = den > T(0) ? T(1) / den : T(0);
       const cx<T> w = B[i];
       part += sp.wcol[x0 + c] * m * (w.re * w.re + w.im * w.im);
-      if (++cnt == 16) { acc[0] += (double)part; part = T(0); cnt = 0; }
+      if (++cnt == 16) { acc.add(part); part = T(0); cnt = 0; }
       if (store) B[i] = scal(w, m * invN);
     }
-    acc[0] += (double)part;
+    acc.add(part);
     if (store) {
       __syncthreads();
-      fft_lines<T, 1, FL>(B, pl, nc, 1, nc, true);
+      fft_lines<T, 1, FL>(B, pl_s, nc, 1, nc, true);
     }
   }
   if (store) {
@@ -578,10 +594,10 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
     }
   }
   if (stage != 1) return;
-  block_sum<1>(acc, red);
+  const double bt[1] = {acc.block_total(redf, red)};
   double* part_b = partials + (size_t)b * nset * gridDim.x;
   const int slot = j * gridDim.x + blockIdx.x, total = nset * gridDim.x;
-  if (publish_partials_at<1>(acc, part_b, slot, total, &sc[b].cnt[1])) {
+  if (publish_partials_at<1>(bt, part_b, slot, total, &sc[b].cnt[1])) {
     double tot[1];
     gather_partials_n<1>(tot, part_b, total, &sc[b].cnt[1], red);
     if (threadIdx.x == 0) finalize_col(sc + b, mode, tot[0] * sp.invN);
@@ -611,7 +627,7 @@ template <typename T, int D, int FX>
 cudaError_t launch3_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
                              int zero_u, int filter, cudaStream_t st) {
   const int R = sh.ry_res, Z = sh.zc_res;
-  const size_t sm = Row3Layout(op.nx, R, 8, (int)sizeof(T), D, 1).total;
+  const size_t sm = Row3Layout(op.nx, R, 8, (int)sizeof(T), D, 1).total + tw_smem_bytes<T>(op.nx);
   static int cfg = 0;
   cudaError_t e = set_smem3(k3_rows<T, D, FX, 1>, sm, cfg);
   if (e != cudaSuccess) return e;
@@ -624,7 +640,7 @@ template <typename T, int D, int FX>
 cudaError_t launch3_update(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
                            cudaStream_t st) {
   const int R = sh.ry_upd, Z = sh.zc_upd;
-  const size_t sm = Row3Layout(op.nx, R, (int)sizeof(T), (int)sizeof(T), D, 0).total;
+  const size_t sm = Row3Layout(op.nx, R, (int)sizeof(T), (int)sizeof(T), D, 0).total + tw_smem_bytes<T>(op.nx);
   static int cfg = 0;
   cudaError_t e = set_smem3(k3_rows<T, D, FX, 0>, sm, cfg);
   if (e != cudaSuccess) return e;
@@ -637,7 +653,7 @@ template <typename T, int D, int FX>
 cudaError_t launch3_direction(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
                               cudaStream_t st) {
   const int R = sh.ry_dir, Z = sh.zc_dir;
-  const size_t sm = Dir3Layout(op.nx, R, (int)sizeof(T), D).total;
+  const size_t sm = Dir3Layout(op.nx, R, (int)sizeof(T), D).total + tw_smem_bytes<T>(op.nx);
   static int cfg = 0;
   cudaError_t e = set_smem3(k3_direction<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
@@ -658,7 +674,7 @@ cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage
   const int nset = axis == 1 ? nz : ny;
   const long long set_stride = axis == 1 ? (long long)ny * nxs : nxs;
   const long long line_stride = axis == 1 ? nxs : (long long)ny * nxs;
-  const size_t sm = (size_t)nl * CW * sizeof(cx<T>);
+  const size_t sm = (size_t)nl * CW * sizeof(cx<T>) + tw_smem_bytes<T>(nl);
   static int cfg = 0;
   cudaError_t e = set_smem3(k3_lines<T, FL>, sm, cfg);
   if (e != cudaSuccess) return e;

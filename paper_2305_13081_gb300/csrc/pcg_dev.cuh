@@ -16,6 +16,9 @@ static __device__ __forceinline__ int done_flag(const SolverScalars* sc) {
 static __device__ __forceinline__ double vol_read(const double* p) {
   return *reinterpret_cast<const volatile double*>(p);
 }
+static __device__ __forceinline__ float vol_readf(const float* p) {
+  return *reinterpret_cast<const volatile float*>(p);
+}
 
 // ---------------------------------------------------------------- finalisers
 static __device__ void finalize_direction(SolverScalars* sc, double pq) {
@@ -25,7 +28,15 @@ static __device__ void finalize_direction(SolverScalars* sc, double pq) {
     sc->status = FFTMECH_ERR_NONFINITE;
     return;
   }
-  sc->alpha = sc->rz / pq;
+  const double a = sc->rz / pq;
+  sc->alpha = a;
+  sc->alpha_h = (float)a;
+  sc->alpha_l = (float)(a - (double)sc->alpha_h);
+}
+
+static __device__ __forceinline__ void set_beta(SolverScalars* sc, double b) {
+  sc->beta = b;
+  sc->beta_f = (float)b;
 }
 
 static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
@@ -40,7 +51,7 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
   }
   if (mode == COL_INIT) {
     sc->rz = tot;
-    sc->beta = 0.0;
+    set_beta(sc, 0.0);
     sc->iter = 0;
     if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
     else if (sc->max_iter <= 0) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
@@ -50,7 +61,7 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
     // the true residual replaced r after a recursive convergence: restart
     sc->rz = tot;
     sc->rz_true = tot;
-    sc->beta = 0.0;
+    set_beta(sc, 0.0);
     if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
     else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
     return;
@@ -65,8 +76,29 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
   // a replaced residual larger than the recursive one it replaces means the
   // float recursion had drifted: restart the direction instead of mixing
   if (mode == COL_TRUE && beta > 1.0) beta = 0.0;
-  sc->beta = beta;
+  set_beta(sc, beta);
 }
+
+// Per-thread accumulator of a block reduction: double-float for float
+// kernels (no FP64 instruction), double for the FP64 path.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<float> {
+  dfloat v{0.f, 0.f};
+  __device__ __forceinline__ void add(float x) { v = df_add(v, x); }
+  __device__ __forceinline__ double block_total(float* scr_f, double*) { return block_sum_df(v, scr_f); }
+};
+template <>
+struct Acc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double block_total(float*, double* scr_d) {
+    double a[1] = {v};
+    block_sum<1>(a, scr_d);
+    return a[0];
+  }
+};
 
 // A column / line pass runs for problem b in this mode: ITER and TRUE skip
 // converged problems, RESTART runs only for the problems being restarted.
