@@ -140,13 +140,16 @@ def kernel_bytes(kind, cls, s, dim=2, variant="full"):
     D = dim if kind == "elastic" else 1
     extra = {"elastic": s + 1, "diffusion": 2, "phasefield": s + 1}[kind]  # g / mask / H, + phase
     spec = 2 * s if dim == 2 else D * s  # spectral bytes per voxel
-    if cls == "direction":   # read S, p_old, material; write p_new
-        return spec + D * s + extra + D * s
+    mask = 1 if kind == "diffusion" else 0
+    if cls == "direction":   # read S, p_old (mask); write p_new
+        return spec + D * s + mask + D * s
+    if cls == "stencil":     # read p, material; write q = K p
+        return D * s + extra + D * s
     if cls == "update":
         if variant == "u_only":  # read p, u; write u
             return D * s + 16 * D
-        # read p, u, r, material; write u, r, S
-        return D * s + 8 * D + D * s + extra + 8 * D + D * s + spec
+        # read p, q, r, u; write r, u, S
+        return D * s + D * s + D * s + 8 * D + D * s + 8 * D + spec
     if cls == "column":      # read + write the spectrum, per launch
         return 2 * spec
     raise ValueError(cls)
@@ -157,7 +160,7 @@ def class_bytes(infos_per_step, N, s, dim=2):
     reliable-update iterations (2-4 per solve) run a lighter u-only update;
     they are counted as full updates (an overcount below 1 %). 3D runs three
     line passes per iteration (y, z with the multiplier, y inverse)."""
-    tot = {"direction": 0.0, "update": 0.0, "column": 0.0}
+    tot = {"direction": 0.0, "stencil": 0.0, "update": 0.0, "column": 0.0}
     kinds = ["diffusion", "elastic", "phasefield"]
     passes = 1 if dim == 2 else 3
     for infos in infos_per_step:
@@ -165,6 +168,7 @@ def class_bytes(infos_per_step, N, s, dim=2):
             kind = kinds[idx % 3]
             it = info["iters"]
             tot["direction"] += N * it * kernel_bytes(kind, "direction", s, dim)
+            tot["stencil"] += N * it * kernel_bytes(kind, "stencil", s, dim)
             tot["update"] += N * it * kernel_bytes(kind, "update", s, dim)
             tot["column"] += N * (it + 2) * passes * kernel_bytes(kind, "column", s, dim)
     return tot
@@ -448,7 +452,7 @@ def main():
         hbm_peak, peak_src = 6800.0, "fallback"
     cb = class_bytes(prof_run["infos"], Np, 4, w.dim)
     kernels = {}
-    for name in ("direction", "update", "column"):
+    for name in ("direction", "stencil", "update", "column"):
         n, ms = prof_run["prof"][name]
         if n and ms > 0:
             kernels[name] = {"launches": n, "total_ms": ms, "avg_us": 1e3 * ms / n,

@@ -268,12 +268,13 @@ fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
  * CUDA events on the context's stream and its duration accumulated; launch
  * counts are kept whether or not profiling is on. */
 enum {
-  FFTMECH_K_DIRECTION = 0, /* row IFFT + new search direction + <p, K p> */
-  FFTMECH_K_UPDATE = 1,    /* iterate / residual update + stencil + row FFT */
-  FFTMECH_K_COLUMN = 2,    /* column FFT, Fourier multiplier, <r, M^-1 r>, column IFFT */
-  FFTMECH_K_RESIDUAL = 3,  /* FP64 true residual + row FFT */
+  FFTMECH_K_DIRECTION = 0, /* x-line IFFT + new search direction */
+  FFTMECH_K_UPDATE = 1,    /* iterate / residual update + x-line FFT */
+  FFTMECH_K_COLUMN = 2,    /* y (and z) line FFTs, Fourier multiplier, <r, M^-1 r>, inverse */
+  FFTMECH_K_RESIDUAL = 3,  /* FP64 true residual + x-line FFT */
   FFTMECH_K_OTHER = 4,     /* pointwise and post-processing kernels */
-  FFTMECH_K_COUNT = 5
+  FFTMECH_K_STENCIL = 5,   /* q = K p and <p, K p> (stencil tiles) */
+  FFTMECH_K_COUNT = 6
 };
 
 /* Enable (1) or disable (0) per-launch event timing; resets the counters. */

@@ -77,10 +77,13 @@ struct fftmech_ctx {
   HostPlan px, py, pz;
   Shape2 shape{};
   Shape3 shape3{};
+  LineShape lshape{};
+  StenShape sshape{};
   // workspace (B problems back to back)
   void* r = nullptr;
   void* p[2] = {nullptr, nullptr};
   void* S = nullptr;
+  void* q = nullptr;     // K p of the split iteration
   void* g = nullptr;
   float* uh = nullptr;   // MIXED iterate, high part
   float* ul = nullptr;   // MIXED iterate, low part
@@ -314,6 +317,7 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
   v.p_in = pbuf[0];
   v.p_out = pbuf[1];
   v.S = (cx<T>*)ctx->S;
+  v.q = (T*)ctx->q;
   v.partials = ctx->partials;
   v.sc = ctx->sc;
   v.mode = ctx->mode;
@@ -338,18 +342,26 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
       return three ? launch3_residual_f<T, 1>(fx, op, v, px, sh3, zero_u, filter, st)
                    : launch_residual_f<T, 1>(fx, op, v, px, sh, zero_u, filter, st);
   };
+  // split iteration: x-line IFFT + direction, stencil q = K p + alpha,
+  // x-line update + FFT
+  const LineShape& lsh = ctx->lshape;
+  const StenShape& ssh = ctx->sshape;
   auto direction = [&](const Vec2<T>& va) -> cudaError_t {
-    if constexpr (D == 3) return launch3_direction_f<T, 3>(fx, op, va, px, sh3, st);
-    else if constexpr (D == 2) return launch_direction_f<T, 2>(fx, op, va, px, sh, st);
+    if constexpr (D == 3) return launch_xdir_f<T, 3, 3>(fx, op, va, px, lsh, st);
+    else if constexpr (D == 2) return launch_xdir_f<T, 2, 2>(fx, op, va, px, lsh, st);
     else
-      return three ? launch3_direction_f<T, 1>(fx, op, va, px, sh3, st)
-                   : launch_direction_f<T, 1>(fx, op, va, px, sh, st);
+      return three ? launch_xdir_f<T, 1, 3>(fx, op, va, px, lsh, st) : launch_xdir_f<T, 1, 2>(fx, op, va, px, lsh, st);
+  };
+  auto stencil = [&](const Vec2<T>& vs) -> cudaError_t {
+    if constexpr (D == 3) return launch_sten3<T, 3>(op, vs, ssh, st);
+    else if constexpr (D == 2) return launch_sten2<T, 2>(op, vs, ssh, st);
+    else return three ? launch_sten3<T, 1>(op, vs, ssh, st) : launch_sten2<T, 1>(op, vs, ssh, st);
   };
   auto update = [&](const Vec2<T>& vb) -> cudaError_t {
-    if constexpr (D == 3) return launch3_update_f<T, 3>(fx, op, vb, px, sh3, st);
-    else if constexpr (D == 2) return launch_update_f<T, 2>(fx, op, vb, px, sh, st);
+    if constexpr (D == 3) return launch_xupd_f<T, 3, 3>(fx, op, vb, px, lsh, st);
+    else if constexpr (D == 2) return launch_xupd_f<T, 2, 2>(fx, op, vb, px, lsh, st);
     else
-      return three ? launch3_update_f<T, 1>(fx, op, vb, px, sh3, st) : launch_update_f<T, 1>(fx, op, vb, px, sh, st);
+      return three ? launch_xupd_f<T, 1, 3>(fx, op, vb, px, lsh, st) : launch_xupd_f<T, 1, 2>(fx, op, vb, px, lsh, st);
   };
   // 2D: one column pass; 3D: y-FFT, z pass (multiplier, <r, M^-1 r>), y-IFFT
   auto colpass = [&](int mode) -> cudaError_t {
@@ -405,6 +417,7 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
       FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, direction(va));
       Vec2<T> vb = v;
       vb.p_in = pbuf[1 - pi];
+      FFTMECH_LAUNCH(FFTMECH_K_STENCIL, stencil(vb));
       FFTMECH_LAUNCH(FFTMECH_K_UPDATE, update(vb));
       const bool replace = pending;
       // reliable update: u += alpha p only (update kernel), then the FP64 true residual
@@ -821,10 +834,10 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
     ctx->own_stream = true;
   }
   const bool three = grid->dim == 3;
+  const bool fp64 = precision == FFTMECH_FP64;
   if (make_plan(ctx->nx, ctx->px) != cudaSuccess || make_plan(ctx->ny, ctx->py) != cudaSuccess ||
       (three && make_plan(ctx->nz, ctx->pz) != cudaSuccess))
     return fail(FFTMECH_ERR_OOM);
-  const bool fp64 = precision == FFTMECH_FP64;
   bool shp;
   if (three)
     shp = fp64 ? choose_shape3<double>(ctx->px, ctx->py, ctx->pz, ctx->nsm, ctx->optin, batch, ctx->shape3)
@@ -832,6 +845,15 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   else
     shp = fp64 ? choose_shape<double>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape)
                : choose_shape<float>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape);
+  if (shp) {
+    const int spec3 = three ? (int)nxs_of(ctx->nx, 3) : ctx->nx;
+    shp = fp64 ? choose_line_shape<double>(ctx->px, ctx->ny * ctx->nz, grid->dim, spec3, ctx->nsm, ctx->optin,
+                                           batch, ctx->lshape)
+               : choose_line_shape<float>(ctx->px, ctx->ny * ctx->nz, grid->dim, spec3, ctx->nsm, ctx->optin,
+                                          batch, ctx->lshape);
+    ctx->lshape.sst = three ? ctx->shape3.sst : ctx->N;
+    choose_sten_shape(ctx->nx, ctx->ny, ctx->nz, grid->dim, ctx->nsm, batch, ctx->sshape);
+  }
   if (!shp) return fail(FFTMECH_ERR_UNSUPPORTED_SIZE);
   ctx->shape.batch = batch;
   const size_t es = fp64 ? 8 : 4;
@@ -852,6 +874,12 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
     const size_t strips = (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;
     widest = std::max(row_tiles, strips);
   }
+  {
+    const StenShape& t = ctx->sshape;
+    size_t tiles = (size_t)((ctx->nx + t.tx - 1) / t.tx) * ((ctx->ny + t.ty - 1) / t.ty);
+    if (three) tiles *= (size_t)((ctx->nz + t.zc - 1) / t.zc);
+    widest = std::max(widest, tiles);
+  }
   const size_t post_blocks = batch > 1 ? 512 : 4096;
   const size_t slots = (size_t)batch * std::max(widest, post_blocks) * 16;
   bool ok = true;
@@ -860,6 +888,7 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
     if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); ok = false; return; }
     if (cudaMemset(*p, 0, bytes) != cudaSuccess) ok = false;
   };
+  alloc(&ctx->q, nd * NB * es);
   alloc(&ctx->r, nd * NB * es);
   alloc(&ctx->p[0], nd * NB * es);
   alloc(&ctx->p[1], nd * NB * es);
@@ -916,7 +945,7 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
   if (!ctx) return FFTMECH_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  void* bufs[] = {ctx->r, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
+  void* bufs[] = {ctx->r, ctx->q, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
                   ctx->cn, ctx->lamx, ctx->lamy, ctx->lamz, ctx->lamc3, ctx->lamc1, ctx->wcol3, ctx->wcol1,
                   ctx->partials, ctx->results, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc};
   for (void* b : bufs)

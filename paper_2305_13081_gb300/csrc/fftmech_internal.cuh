@@ -78,6 +78,7 @@ struct Vec2 {
   const T* p_in;  // previous direction
   T* p_out;       // new direction
   cx<T>* S;       // spectral rows, N complex (components packed re / im)
+  T* q;           // K p (split iteration), D x N
   double* partials;
   SolverScalars* sc;  // one per problem of the batch
   const int* mode;    // per problem: 0 normal, 1 reliable update, 2 restart (NULL = all 0)
@@ -147,6 +148,19 @@ struct Shape3 {
   int ry_res, zc_res, thr_res;
   int cw_y, thr_y;
   int cw_z, thr_z;
+};
+
+// Split iteration (lines.cuh, stencil.cuh): x-line kernels take L whole
+// lines per block; stencil kernels TX x TY tiles (x TZ planes in 3D).
+struct LineShape {
+  int batch;
+  long long sst;  // complex numbers per problem in the spectral buffer
+  int L_dir, thr_dir;
+  int L_upd, thr_upd;
+};
+struct StenShape {
+  int batch;
+  int tx, ty, zc, threads;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -259,6 +273,34 @@ inline cudaError_t launch3_lines_f(int fl, cx<T>* S, const Shape3& sh, int D, in
                                    SolverScalars* sc, const int* pmode, cudaStream_t st) {
 #define FFTMECH_C(F) launch3_lines<T, F>(S, sh, D, axis, stage, pl, sp, mode, partials, sc, pmode, st)
   FFTMECH_FAMILY_SWITCH(fl, FFTMECH_C)
+#undef FFTMECH_C
+}
+
+// Split iteration launchers; x-line kernels take the radix family of the x
+// transform, DIM the grid dimension.
+template <typename T, int D, int FX, int DIM>
+cudaError_t launch_xdir(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
+                        cudaStream_t st);
+template <typename T, int D, int FX, int DIM>
+cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
+                        cudaStream_t st);
+template <typename T, int D>
+cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss, cudaStream_t st);
+template <typename T, int D>
+cudaError_t launch_sten3(const Op<T>& op, const Vec2<T>& v, const StenShape& ss, cudaStream_t st);
+
+template <typename T, int D, int DIM>
+inline cudaError_t launch_xdir_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                                 const LineShape& ls, cudaStream_t st) {
+#define FFTMECH_C(F) launch_xdir<T, D, F, DIM>(op, v, px, ls, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T, int D, int DIM>
+inline cudaError_t launch_xupd_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                                 const LineShape& ls, cudaStream_t st) {
+#define FFTMECH_C(F) launch_xupd<T, D, F, DIM>(op, v, px, ls, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
 
@@ -396,6 +438,29 @@ struct Dir3Layout {
     total = MK + align16((size_t)(R + 1) * L);
   }
 };
+
+// Split-iteration shared memory (bytes, including the staged twiddles).
+template <typename T>
+inline size_t xdir_smem(int nx, int L, int D, int dim) {
+  const int nf = (dim == 3 && D == 3) ? 2 : 1;
+  return tw_smem_bytes<T>(nx) + align16((size_t)nf * L * nx * sizeof(cx<T>)) + (size_t)D * L * nx * sizeof(T);
+}
+template <typename T>
+inline size_t xupd_smem(int nx, int L, int D, int dim) {
+  const int nf = (dim == 3 && D == 3) ? 2 : 1;
+  return tw_smem_bytes<T>(nx) + (size_t)nf * L * nx * sizeof(cx<T>);
+}
+template <typename T>
+inline size_t sten2_smem(int tx, int ty, int D) {
+  const size_t sgs = (size_t)(ty + 1) * (tx + 1);
+  return ((size_t)D * (ty + 2) * (tx + 2) + 3 * sgs + sgs) * sizeof(T) + sgs;
+}
+template <typename T>
+inline size_t sten3_smem(int tx, int ty, int D) {
+  const size_t np = D == 3 ? 3 : 2, nzc = D == 3 ? 3 : 1;
+  const size_t sgs = (size_t)(ty + 1) * (tx + 1);
+  return ((size_t)2 * D * (ty + 2) * (tx + 2) + np * sgs + 2 * nzc * sgs + sgs) * sizeof(T) + sgs;
+}
 
 template <typename T, int D>
 inline size_t smem_update(int nx, int R) { return UpdLayout(nx, R, (int)sizeof(T), D).total; }

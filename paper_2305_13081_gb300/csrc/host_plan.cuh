@@ -223,6 +223,59 @@ bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, i
   return true;
 }
 
+// Split iteration: lines per block for the x-line kernels. The largest L
+// (at most 16) whose shared memory leaves room for three blocks per SM and
+// whose widest FFT pass fits 512 threads, lowered while the launch would
+// have fewer than two blocks per SM; the stencil tiles are fixed (64 x 16
+// in 2D; 32 x 8 marching through Zc planes in 3D, Zc giving about eight
+// blocks per SM).
+template <typename T>
+bool choose_line_shape(const HostPlan& px, int nlines, int dim, int nxs3, int nsm, size_t optin_total, int batch,
+                       LineShape& s) {
+  const int nx = px.n;
+  const size_t optin = optin_total - 1024;
+  const size_t budget = std::min<size_t>(optin, 72 * 1024);
+  const int nf = dim == 3 ? 2 : 1;  // D = 3 rows carry two complex fields
+  const int Dmax = dim == 3 ? 3 : 2;
+  auto ok = [&](int L, bool dir, size_t lim) {
+    const size_t sm = dir ? xdir_smem<T>(nx, L, Dmax, dim) : xupd_smem<T>(nx, L, Dmax, dim);
+    return sm <= lim && need_threads(px, nf * L) <= 512 && (long long)L * nxs3 < 65536 &&
+           (long long)L * nx < 65536;
+  };
+  auto pick = [&](bool dir) {
+    int L = std::min(nlines, 16);
+    while (L > 1 && !ok(L, dir, budget)) --L;
+    while (L > 1 && (long long)((nlines + L - 1) / L) * batch < 2LL * nsm) --L;
+    return ok(L, dir, optin) ? L : 0;
+  };
+  s = LineShape();
+  s.batch = batch;
+  s.L_dir = pick(true);
+  s.L_upd = pick(false);
+  if (!s.L_dir || !s.L_upd) return false;
+  s.thr_dir = std::min(512, std::max(256, round32(need_threads(px, nf * s.L_dir))));
+  s.thr_upd = std::min(512, std::max(256, round32(need_threads(px, nf * s.L_upd))));
+  return true;
+}
+
+inline void choose_sten_shape(int nx, int ny, int nz, int dim, int nsm, int batch, StenShape& s) {
+  s = StenShape();
+  s.batch = batch;
+  s.threads = 256;
+  if (dim == 2) {
+    s.tx = std::min(nx, 64);
+    s.ty = std::min(ny, 16);
+    s.zc = 1;
+    return;
+  }
+  s.tx = std::min(nx, 32);
+  s.ty = std::min(ny, 8);
+  const long long tiles = (long long)((nx + s.tx - 1) / s.tx) * ((ny + s.ty - 1) / s.ty) * batch;
+  long long nzc = (8LL * nsm + tiles - 1) / tiles;
+  nzc = std::max(1LL, std::min<long long>(nzc, nz));
+  s.zc = std::max(std::min(nz, 4), (int)((nz + nzc - 1) / nzc));
+}
+
 // Launch shapes for the bare transform (row FFT + column FFT only), which
 // needs far less shared memory than the solver's row kernels.
 template <typename T>

@@ -1,0 +1,285 @@
+// x-line kernels of the split PCG iteration (2D and 3D): the direction
+// kernel (z = x-IFFT(S), p = z + beta p_old) and the update kernel
+// (u += alpha p, r -= alpha q, S = x-FFT(r)). Neither needs a neighbour
+// line, so a block takes L whole lines with no halo and no transform is
+// computed twice; the stencil q = K p and <p, K p> run in their own kernel
+// (stencil.cuh) between the two.
+//
+// Spectral rows. DIM = 2: one complex row of nx per x line, the D = 2
+// components packed as (r_x + i r_y), a scalar as (r + 0 i). DIM = 3: the
+// packed (x, y) pair as nx complex numbers (D = 3) followed by the half
+// spectrum (nx/2 + 1 numbers) of the remaining real component (r_z, or the
+// scalar for D = 1); a real line's transform is Hermitian, so the other
+// half is rebuilt by conjugate symmetry before the inverse transform.
+#pragma once
+
+#include "fftmech_internal.cuh"
+#include "fftmech.h"
+#include "pcg_dev.cuh"
+
+namespace fftmech {
+
+#define FFTMECH_BOUNDS_L __launch_bounds__(512, 2)
+
+template <int DIM, int D>
+struct LineLayout {
+  // complex fields through the x transform: DIM 2 one packed field; DIM 3
+  // the packed pair (D = 3) and the half-spectrum field
+  static constexpr int NF = DIM == 2 ? 1 : (D == 3 ? 2 : 1);
+  static constexpr bool HALF = DIM == 3;  // last field stored as a half spectrum
+};
+
+__host__ __device__ inline int spec_row(int nx, int D, int dim) { return dim == 2 ? nx : nxs_of(nx, D); }
+
+// Problem b of a uniform batch: fields at b N (d-component fields at b D N),
+// spectrum at b sst.
+template <typename T, int D>
+__device__ __forceinline__ void line_views(Op<T>& op, Vec2<T>& v, int b, size_t N, long long sst) {
+  const size_t o1 = (size_t)b * N, oD = (size_t)b * D * N;
+  op.phase += o1;
+  if (op.g) op.g += o1;
+  if (op.c0f) op.c0f += o1;
+  if (op.mask) op.mask += o1;
+  if (v.u) v.u += oD;
+  if (v.uh) v.uh += oD;
+  if (v.ul) v.ul += oD;
+  v.r += oD;
+  if (v.p_in) v.p_in += oD;
+  if (v.p_out) v.p_out += oD;
+  if (v.q) v.q += oD;
+  v.S += (size_t)b * sst;
+  v.sc += b;
+}
+
+// ---------------------------------------------------------------- direction
+// Lines l0 .. l0 + L - 1 (flattened (z, y) index): z = x-IFFT(S), masked
+// voxels (D = 1) 0, p = z + beta p_old. Shared memory: [twiddles]
+// [F: NF L complex lines] [PO: old direction, D L lines].
+template <typename T, int D, int FX, int DIM>
+__global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst) {
+  using LL = LineLayout<DIM, D>;
+  const int nx = op.nx;
+  const int nlines = op.ny * op.nz;
+  const size_t N = (size_t)nx * nlines;
+  const int bp = blockIdx.y;
+  line_views<T, D>(op, v, bp, N, sst);
+  if (done_flag(v.sc)) return;
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
+  T b;
+  if constexpr (sizeof(T) == 4) b = vol_readf(&v.sc->beta_f);
+  else b = vol_read(&v.sc->beta);
+  const bool with_old = b != T(0);  // the first iteration has p = z
+  const int l0 = blockIdx.x * L;
+  const int nl = min(L, nlines - l0);
+  const int nxs = spec_row(nx, D, DIM);
+  const int nxa = (DIM == 3 && D == 3) ? nx : 0;  // packed field's length in a 3D row
+  const int nxh = nx / 2 + 1;
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
+  cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;  // the half-spectrum field's lines (DIM 3)
+  T* PO = reinterpret_cast<T*>(smem + align16((size_t)LL::NF * L * nx * sizeof(cx<T>)));
+  const size_t t0 = (size_t)l0 * nx;
+  if constexpr (DIM == 2) {
+    g2s_vec<8, true>(F, v.S + t0, nl * nx);
+  } else {
+    for (int l = 0; l < nl; ++l) {
+      const cx<T>* Srow = v.S + (size_t)(l0 + l) * nxs;
+      if constexpr (D == 3) g2s_vec<8, true>(F + (size_t)l * nx, Srow, nx);
+      g2s_vec<8, true>(FB + (size_t)l * nx, Srow + nxa, nxh);
+    }
+  }
+  if (with_old) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) g2s_vec<8, true>(PO + (size_t)c * nl * nx, v.p_in + c * N + t0, nl * nx);
+  }
+  __syncthreads();
+  if constexpr (LL::HALF) {
+    const int nup = nx - nxh;
+    for (int i = threadIdx.x; i < nl * nup; i += blockDim.x) {
+      const int l = i / nup, k = nxh + (i - l * nup);
+      const cx<T> w = FB[(size_t)l * nx + (nx - k)];
+      FB[(size_t)l * nx + k] = mk(w.re, -w.im);
+    }
+    __syncthreads();
+  }
+  fft_lines<T, 1, FX>(F, px_s, LL::NF * nl, nx, 1, false);
+  const bool masked = (D == 1) && op.mask;
+  for (int i = threadIdx.x; i < nl * nx; i += blockDim.x) {
+    T z[D];
+    if constexpr (DIM == 2) {
+      z[0] = F[i].re;
+      if constexpr (D == 2) z[1] = F[i].im;
+    } else {
+      if constexpr (D == 3) {
+        z[0] = F[i].re;
+        z[1] = F[i].im;
+        z[2] = FB[i].re;
+      } else {
+        z[0] = FB[i].re;
+      }
+    }
+    if (masked && op.mask[t0 + i]) z[0] = T(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T p = z[c];
+      if (with_old) p += b * PO[(size_t)c * nl * nx + i];
+      v.p_out[c * N + t0 + i] = p;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- update
+// u += alpha p (double or double-float iterate), r -= alpha q, S = x-FFT(r)
+// on lines l0 .. l0 + L - 1. Reliable-update iterations (mode 1) move the
+// iterate only. Shared memory: [twiddles] [F: NF L complex lines].
+template <typename T, int D, int FX, int DIM>
+__global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst) {
+  using LL = LineLayout<DIM, D>;
+  const int nx = op.nx;
+  const int nlines = op.ny * op.nz;
+  const size_t N = (size_t)nx * nlines;
+  const int bp = blockIdx.y;
+  const int u_only = v.mode ? (v.mode[bp] == 1) : 0;
+  line_views<T, D>(op, v, bp, N, sst);
+  if (done_flag(v.sc)) return;
+  double alpha = 0.0;
+  float ah = 0.f, al = 0.f;
+  if constexpr (sizeof(T) == 4) {
+    ah = vol_readf(&v.sc->alpha_h);
+    al = vol_readf(&v.sc->alpha_l);
+  } else {
+    alpha = vol_read(&v.sc->alpha);
+  }
+  const T a = sizeof(T) == 4 ? (T)ah : (T)alpha;
+  const int l0 = blockIdx.x * L;
+  const int nl = min(L, nlines - l0);
+  const size_t t0 = (size_t)l0 * nx;
+  const int n = nl * nx;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  // iterate update (every mode)
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const T* p = v.p_in + c * N + t0;
+    if constexpr (sizeof(T) == 4) {
+      float* uh = v.uh + c * N + t0;
+      float* ul = v.ul + c * N + t0;
+      for (int i = tid; i < n; i += 2 * bd) {
+        const int i2 = i + bd;
+        float h0 = uh[i], l0v = ul[i];
+        const float p0 = (float)p[i];
+        float h1 = 0.f, l1 = 0.f, p1 = 0.f;
+        if (i2 < n) { h1 = uh[i2]; l1 = ul[i2]; p1 = (float)p[i2]; }
+        df_axpy(h0, l0v, ah, al, p0);
+        uh[i] = h0;
+        ul[i] = l0v;
+        if (i2 < n) {
+          df_axpy(h1, l1, ah, al, p1);
+          uh[i2] = h1;
+          ul[i2] = l1;
+        }
+      }
+    } else {
+      double* u = v.u + c * N + t0;
+      for (int i = tid; i < n; i += bd) u[i] += alpha * (double)p[i];
+    }
+  }
+  if (u_only) return;
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
+  cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;
+  // residual update and packing
+  for (int i = tid; i < n; i += bd) {
+    T r[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) r[c] = v.r[c * N + t0 + i] - a * v.q[c * N + t0 + i];
+#pragma unroll
+    for (int c = 0; c < D; ++c) v.r[c * N + t0 + i] = r[c];
+    if constexpr (DIM == 2) {
+      F[i] = mk(r[0], D == 2 ? r[D - 1] : T(0));
+    } else {
+      if constexpr (D == 3) {
+        F[i] = mk(r[0], r[1]);
+        FB[i] = mk(r[2], T(0));
+      } else {
+        FB[i] = mk(r[0], T(0));
+      }
+    }
+  }
+  __syncthreads();
+  fft_lines<T, -1, FX>(F, px_s, LL::NF * nl, nx, 1, false);
+  if constexpr (DIM == 2) {
+    s2g(v.S + t0, F, n);
+  } else {
+    const int nxs = spec_row(nx, D, DIM);
+    const int nxa = D == 3 ? nx : 0;
+    cx<T>* Srow = v.S + (size_t)l0 * nxs;
+    const FastDiv dns(nxs);
+    for (int i = tid; i < nl * nxs; i += bd) {
+      const int l = dns.div(i), k = i - l * nxs;
+      Srow[i] = k < nxa ? F[(size_t)l * nx + k] : FB[(size_t)l * nx + (k - nxa)];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename K>
+static cudaError_t set_smem_l(K kernel, size_t bytes, int& configured) {
+  if (configured) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
+  if ((long long)bytes > (long long)dyn_max) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  if (e == cudaSuccess) configured = 1;
+  return e;
+}
+
+template <typename T, int D, int FX, int DIM>
+cudaError_t launch_xdir(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
+                        cudaStream_t st) {
+  const int L = ls.L_dir;
+  const size_t sm = xdir_smem<T>(op.nx, L, D, DIM);
+  static int cfg = 0;
+  cudaError_t e = set_smem_l(k_xdir<T, D, FX, DIM>, sm, cfg);
+  if (e != cudaSuccess) return e;
+  const int nlines = op.ny * op.nz;
+  const dim3 grid((nlines + L - 1) / L, ls.batch);
+  k_xdir<T, D, FX, DIM><<<grid, ls.thr_dir, sm, st>>>(op, v, px, L, ls.sst);
+  return cudaGetLastError();
+}
+
+template <typename T, int D, int FX, int DIM>
+cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
+                        cudaStream_t st) {
+  const int L = ls.L_upd;
+  const size_t sm = xupd_smem<T>(op.nx, L, D, DIM);
+  static int cfg = 0;
+  cudaError_t e = set_smem_l(k_xupd<T, D, FX, DIM>, sm, cfg);
+  if (e != cudaSuccess) return e;
+  const int nlines = op.ny * op.nz;
+  const dim3 grid((nlines + L - 1) / L, ls.batch);
+  k_xupd<T, D, FX, DIM><<<grid, ls.thr_upd, sm, st>>>(op, v, px, L, ls.sst);
+  return cudaGetLastError();
+}
+
+#define FFTMECH_INST_LINES_TD(T, D, F, DIM)                                                                     \
+  template cudaError_t launch_xdir<T, D, F, DIM>(const Op<T>&, const Vec2<T>&, const FftPlanDev<T>&,          \
+                                                 const LineShape&, cudaStream_t);                             \
+  template cudaError_t launch_xupd<T, D, F, DIM>(const Op<T>&, const Vec2<T>&, const FftPlanDev<T>&,          \
+                                                 const LineShape&, cudaStream_t);
+#define FFTMECH_INST_LINES_T(T, F)      \
+  FFTMECH_INST_LINES_TD(T, 1, F, 2)     \
+  FFTMECH_INST_LINES_TD(T, 2, F, 2)     \
+  FFTMECH_INST_LINES_TD(T, 1, F, 3)     \
+  FFTMECH_INST_LINES_TD(T, 3, F, 3)
+
+}  // namespace fftmech

@@ -40,8 +40,9 @@ FFTMECH_K_UPDATE = 1
 FFTMECH_K_COLUMN = 2
 FFTMECH_K_RESIDUAL = 3
 FFTMECH_K_OTHER = 4
-FFTMECH_K_COUNT = 5
-KERNEL_CLASS_NAMES = ["direction", "update", "column", "residual", "other"]
+FFTMECH_K_STENCIL = 5
+FFTMECH_K_COUNT = 6
+KERNEL_CLASS_NAMES = ["direction", "update", "column", "residual", "other", "stencil"]
 
 c_double3 = ctypes.c_double * 3
 c_double6 = ctypes.c_double * 6
