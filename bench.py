@@ -267,6 +267,69 @@ def run_arm(torch, fm, w, prec, steps, warmup, device, profile=True, flush=None)
     return {"infos": infos, "ms": ms, "prof": prof, "launches": total_launches, "state": state}
 
 
+def group_by_size(ws):
+    groups = {}
+    for w in ws:
+        groups.setdefault(w.phase.shape, []).append(w)
+    return [groups[k] for k in sorted(groups)]
+
+
+def run_many(torch, fm, ws, prec, steps, warmup, device, profile=False, flush=None):
+    """Uneven grids: one uniform-batch context per grid size, all stepped
+    together through fftmech_staggered_step_many (one host thread and one
+    stream per context). Timed with events on the current stream between
+    device-synchronised points (the call returns when every context's
+    stream is done)."""
+    groups = group_by_size(ws)
+    ctxs, states, params, keep = [], [], [], []
+    for g in groups:
+        w = g[0]
+        ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=w.tol, max_iter=20000,
+                         replace_residual=1, check_every=16, batch=len(g))
+        bufs, st, p = make_state(torch, fm, g, prec, device)
+        ctxs.append(ctx)
+        states.append(st)
+        params.append(p)
+        keep.append(bufs)
+    handles = [c.handle for c in ctxs]
+    for s in range(warmup):
+        for g, p in zip(groups, params):
+            set_step(p, g[0], s)
+        fm.fftmech_staggered_step_many(handles, states, params)
+    torch.cuda.synchronize(device)
+    for c in ctxs:
+        fm.fftmech_profile_enable(c.handle, 1 if profile else 0)
+    stream = torch.cuda.current_stream(device)
+    infos, ms = [], []
+    for s in range(steps):
+        for g, p in zip(groups, params):
+            set_step(p, g[0], warmup + s)
+        if flush is not None:
+            flush.add_(1)
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf = fm.fftmech_staggered_step_many(handles, states, params)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        infos.append([(g[0].voxels, [x[i].as_dict() for i in range(len(x))]) for g, x in zip(groups, inf)])
+    torch.cuda.synchronize(device)
+    prof = {name: [0, 0.0] for name in fm.KERNEL_CLASS_NAMES}
+    launches = 0
+    for c in ctxs:
+        for k, name in enumerate(fm.KERNEL_CLASS_NAMES):
+            n, t = fm.fftmech_profile_read(c.handle, k)
+            prof[name][0] += n
+            prof[name][1] += t
+        launches += fm.fftmech_profile_read(c.handle, fm.FFTMECH_K_COUNT)[0]
+        fm.fftmech_profile_enable(c.handle, 0)
+        c.close()
+    return {"infos": infos, "ms": ms, "prof": {k: tuple(v) for k, v in prof.items()}, "launches": launches,
+            "groups": [(g[0].phase.shape[0], len(g)) for g in groups]}
+
+
 def run_e2e(torch, fm, w, prec, steps, warmup, device):
     """The same steps through the C ABI with pinned HOST buffers: every call
     copies the state in and out (host <-> device inside the timed region)."""
@@ -345,6 +408,89 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- uneven batch
+
+def mixed_main(args, torch, fm, device, rank, world, dist):
+    """--workload mixed: the uneven batch (one context per grid size)."""
+    from microstructures.workloads import mixed_batch
+    n3, n2 = args.mixed_counts
+    ws = mixed_batch(n3=n3, n2=n2, seed3=rank * 10000, seed2=rank * 10000 + 1000)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    sampler.start()
+    run = run_many(torch, fm, ws, fm.FFTMECH_MIXED, args.steps, args.warmup, device, profile=False, flush=flush)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    clocks = sampler.stop()
+    prof_run = run_many(torch, fm, ws, fm.FFTMECH_MIXED, max(1, args.steps // 4), 1, device, profile=True,
+                        flush=flush)
+    vi = sum(nv * sum(i["iters"] for i in recs) for step in run["infos"] for nv, recs in step)
+    dev_s = sum(run["ms"]) / 1e3
+    local = torch.tensor([vi, dev_s], dtype=torch.float64, device=device)
+    if dist is not None:
+        tot = local.clone()
+        dist.all_reduce(tot[:1], op=dist.ReduceOp.SUM)
+        mx = local[1:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        total_vi, max_s = float(tot[0]), float(mx[0])
+    else:
+        total_vi, max_s = float(local[0]), float(local[1])
+    value = total_vi / max_s
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        peak_src = "measured"
+    except (OSError, KeyError, ValueError):
+        hbm_peak, peak_src = 6800.0, "fallback"
+    tot = {"direction": 0.0, "stencil": 0.0, "update": 0.0, "column": 0.0}
+    for step in prof_run["infos"]:
+        for nv, recs in step:
+            cb = class_bytes([recs], nv, 4, 2)
+            for k in tot:
+                tot[k] += cb[k]
+    kernels = {}
+    for name in tot:
+        n, t = prof_run["prof"][name]
+        if n and t > 0:
+            kernels[name] = {"launches": n, "total_ms": t, "avg_us": 1e3 * t / n,
+                             "achieved_gbs": tot[name] / (t / 1e3) / 1e9}
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"]) if kernels else None
+    roofline = None
+    if dom:
+        a = kernels[dom]["achieved_gbs"]
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": a / hbm_peak, "peak_source": peak_src, "traffic": None,
+                    "note": "achieved counts algorithmic bytes; contexts overlap on separate streams, so "
+                            "per-class event times include that overlap"}
+    voxels = sum(w.voxels for w in ws)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields / f64 iterates+reductions",
+        "data": "synthetic",
+        "config": {"workload": f"mixed-batch-{n3}x3x3-{n2}x2x2-transient-staggered", "problems": len(ws),
+                   "voxels": voxels, "groups": prof_run["groups"], "precision": "mixed", "tol": 1e-8,
+                   "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before each timed step",
+                   "parallelism": f"{world} independent replicas; one context per grid size, "
+                                  "stepped concurrently (one host thread and stream each)"},
+        "kernels": kernels, "roofline": roofline, "gpu_launches": run["launches"], "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu:
+        big = max(ws, key=lambda w: w.voxels)
+        v, secs, it = oracle_sample(big, min(args.cpu_iters, 20))
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{it} iterations of the FP64 oracle's gradient-space equilibrium CG "
+                                         f"on the largest grid of the batch ({big.phase.shape[0]}^2, {secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -360,9 +506,12 @@ def main():
     ap.add_argument("--batch", type=int, default=1,
                     help="solve this many independent RVEs of the workload size (seeds differ) "
                          "as one batch per rank")
-    ap.add_argument("--workload", default="carpet", choices=["carpet", "sponge"],
+    ap.add_argument("--workload", default="carpet", choices=["carpet", "sponge", "mixed"],
                     help="carpet: 729^2 transient carpet (the headline workload); sponge: 243^3 "
-                         "sponge with a ramped pore eigenstrain")
+                         "sponge with a ramped pore eigenstrain; mixed: 256 3x3 carpets of 81^2, 243^2, "
+                         "729^2 and 64 2x2 carpets of 128^2 .. 1024^2, all stepped together")
+    ap.add_argument("--mixed-counts", type=int, nargs=2, default=[256, 64],
+                    help="--workload mixed: numbers of 3x3 and 2x2 carpets")
     ap.add_argument("--n", type=int, default=None,
                     help="grid side (3^k); defaults 729 (carpet) and 243 (sponge); larger carpet "
                          "sides (2187) give working sets above L2 for profiling")
@@ -391,6 +540,9 @@ def main():
     __graft_entry__.build()
     from paper_2305_13081_gb300 import fftmech as fm
 
+    if args.workload == "mixed":
+        mixed_main(args, torch, fm, device, rank, world, dist)
+        return
     if args.batch > 1:
         ws = [workload(rank * 1000 + b, args.n, args.workload) for b in range(args.batch)]
     else:

@@ -263,6 +263,20 @@ fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
                                       const fftmech_step_params* params,
                                       fftmech_solve_info* info);
 
+/* Staggered steps of several contexts at once: a batch of uneven grids is
+ * one uniform-batch context per grid size (Sec. 3.2 treats every RVE as an
+ * independent problem). Each context's step (fftmech_staggered_step) runs
+ * on its own host thread and its own stream, so the GPU overlaps the
+ * contexts' kernels; the call returns when all have finished. states[i],
+ * params[i] and infos[i] (3 * fftmech_batch_size(ctxs[i]) records) belong
+ * to ctxs[i]; contexts must be distinct and use distinct streams. Returns
+ * INVALID_ARG for bad arguments, else the first hard error (INVALID_ARG,
+ * CUDA, OOM) of any context, else the first solver status that is not OK.
+ * No counterpart in the paper. */
+fftmech_status fftmech_staggered_step_many(fftmech_ctx* const* ctxs, int n, fftmech_state* const* states,
+                                           const fftmech_step_params* const* params,
+                                           fftmech_solve_info* const* infos);
+
 /* Instrumentation (no counterpart in the paper): kernel classes of the PCG
  * loop. When profiling is enabled, every launch of a class is bracketed by
  * CUDA events on the context's stream and its duration accumulated; launch

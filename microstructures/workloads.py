@@ -15,7 +15,7 @@ from dataclasses import dataclass, asdict, field
 import numpy as np
 
 from .fractals import sierpinski_carpet, random_carpet, random_sponge, porosity
-from .splitmix import derive_key, standard_normal
+from .splitmix import derive_key, standard_normal, uniform01
 
 
 @dataclass
@@ -139,3 +139,29 @@ def gaussian_pore_eigenstrain(phase, seed, mean=1e-3, std=2e-4):
     """Per-voxel eigenstrain N(mean, std^2) in the pores, 0 in the solid."""
     z = standard_normal(derive_key(seed, 0xE16), phase.size).reshape(phase.shape)
     return np.where(phase == 0, mean + std * z, 0.0)
+
+
+def mixed_batch(n3=256, n2=64, steps=20, tol=1e-8, sizes3=(81, 243, 729), sizes2=(128, 256, 512, 1024),
+                seed3=0, seed2=1000):
+    """Batch of uneven 2D grids: n3 random 3x3 carpets with n drawn uniformly
+    from sizes3 (seeds seed3 ..), n2 random 2x2 carpets with n drawn from
+    sizes2 (seeds seed2 ..); target porosity uniform in [0.2, 0.45] per
+    problem; each a transient-diffusion staggered workload as
+    carpet_transient (left-face source, dt = (n/4)^2 / steps). The draws use
+    the SplitMix64 stream of each seed."""
+    out = []
+    for base, count, sizes, s0 in ((3, n3, sizes3, seed3), (2, n2, sizes2, seed2)):
+        for i in range(count):
+            seed = s0 + i
+            u = uniform01(derive_key(seed, 0xB47C), 2)
+            n = sizes[min(int(u[0] * len(sizes)), len(sizes) - 1)]
+            eta = 0.2 + 0.25 * float(u[1])
+            phase, _ = random_carpet(n, eta, seed, base=base)
+            out.append(Workload(
+                name=f"random-carpet{base}-{n}x{n}", phase=phase, materials=Materials(),
+                h=H_MECH, h_diff=H_DIFF, steps=steps, diffusion_mode=DIFF_TRANSIENT,
+                eig_mode=EIG_FROM_PRECIPITATE, eig=np.zeros(phase.shape), eig_ramp=[1.0] * steps,
+                dt=(n / 4.0) ** 2 / steps, dirichlet_mask=left_face_mask(phase),
+                dirichlet_value=1.0, c0=np.zeros(phase.shape), tol=tol,
+                extra={"seed": seed, "porosity": porosity(phase), "target_porosity": eta}))
+    return out

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "fftmech.h"
@@ -21,23 +22,30 @@ constexpr int kPartialSlots = 16;    // doubles per block in `partials`
 // ---------------------------------------------------------------- plans
 // Device twiddles for a context (FP64 values from the host, also rounded to
 // float).
+// Device buffers of a plan: twiddles (tw_smem_twiddles bytes) followed by
+// the pass multipliers, tw_smem_bytes in all, for float and double.
+template <typename T>
+cudaError_t upload_plan(const HostPlan& p, const cx<double>* hd, cx<T>** dst) {
+  const size_t bytes = tw_smem_bytes<T>(p.n), twb = tw_smem_twiddles<T>(p.n);
+  std::vector<unsigned char> buf(bytes, 0);
+  cx<T>* tw = reinterpret_cast<cx<T>*>(buf.data());
+  for (int i = 0; i < p.n - 1; ++i) {
+    tw[i].re = (T)hd[i].re;
+    tw[i].im = (T)hd[i].im;
+  }
+  plan_multipliers(p.n, p.npass, p.radix, reinterpret_cast<unsigned int*>(buf.data() + twb));
+  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, buf.data(), bytes, cudaMemcpyHostToDevice);
+}
+
 cudaError_t make_plan(int n, HostPlan& p) {
   factor_plan(n, p);
-  const int nt = std::max(twiddle_count(p), 1);
-  std::vector<cx<double>> hd(nt);
-  std::vector<cx<float>> hf(nt);
+  std::vector<cx<double>> hd(std::max(n, 1));
   fill_twiddles(p, hd.data());
-  for (int i = 0; i < nt; ++i) {
-    hf[i].re = (float)hd[i].re;
-    hf[i].im = (float)hd[i].im;
-  }
-  cudaError_t e = cudaMalloc(&p.tw_f, nt * sizeof(cx<float>));
+  cudaError_t e = upload_plan<float>(p, hd.data(), &p.tw_f);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&p.tw_d, nt * sizeof(cx<double>));
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpy(p.tw_f, hf.data(), nt * sizeof(cx<float>), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return e;
-  return cudaMemcpy(p.tw_d, hd.data(), nt * sizeof(cx<double>), cudaMemcpyHostToDevice);
+  return upload_plan<double>(p, hd.data(), &p.tw_d);
 }
 
 void free_plan(HostPlan& p) {
@@ -843,8 +851,8 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
     shp = fp64 ? choose_shape3<double>(ctx->px, ctx->py, ctx->pz, ctx->nsm, ctx->optin, batch, ctx->shape3)
                : choose_shape3<float>(ctx->px, ctx->py, ctx->pz, ctx->nsm, ctx->optin, batch, ctx->shape3);
   else
-    shp = fp64 ? choose_shape<double>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape)
-               : choose_shape<float>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape);
+    shp = fp64 ? choose_shape<double>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape, batch)
+               : choose_shape<float>(ctx->px, ctx->py, ctx->nsm, ctx->optin, ctx->shape, batch);
   if (shp) {
     const int spec3 = three ? (int)nxs_of(ctx->nx, 3) : ctx->nx;
     shp = fp64 ? choose_line_shape<double>(ctx->px, ctx->ny * ctx->nz, grid->dim, spec3, ctx->nsm, ctx->optin,
@@ -865,14 +873,9 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   size_t widest;
   if (three) {
     const Shape3& t = ctx->shape3;
-    const size_t bricks = (size_t)((ctx->ny + t.ry_upd - 1) / t.ry_upd) * ((ctx->nz + t.zc_upd - 1) / t.zc_upd);
-    const size_t bricks_d = (size_t)((ctx->ny + t.ry_dir - 1) / t.ry_dir) * ((ctx->nz + t.zc_dir - 1) / t.zc_dir);
-    const size_t zstrips = (size_t)ctx->ny * ((nxs_of(ctx->nx, 3) + t.cw_z - 1) / t.cw_z);
-    widest = std::max(std::max(bricks, bricks_d), zstrips);
+    widest = (size_t)ctx->ny * ((nxs_of(ctx->nx, 3) + t.cw_z - 1) / t.cw_z);  // z-pass blocks
   } else {
-    const size_t row_tiles = (ctx->ny + ctx->shape.rows_dir - 1) / ctx->shape.rows_dir;
-    const size_t strips = (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;
-    widest = std::max(row_tiles, strips);
+    widest = (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;  // column strips
   }
   {
     const StenShape& t = ctx->sshape;
@@ -1163,6 +1166,28 @@ fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
   if ((rc = stage_out(ctx, state->damage, dd, N * 8)) != FFTMECH_OK) return rc;
   CK(cudaStreamSynchronize(st));
   return worst;
+}
+
+fftmech_status fftmech_staggered_step_many(fftmech_ctx* const* ctxs, int n, fftmech_state* const* states,
+                                           const fftmech_step_params* const* params,
+                                           fftmech_solve_info* const* infos) {
+  if (!ctxs || !states || !params || !infos || n < 0) return FFTMECH_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || !states[i] || !params[i] || !infos[i]) return FFTMECH_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) return FFTMECH_ERR_INVALID_ARG;
+  }
+  std::vector<fftmech_status> rc(n, FFTMECH_OK);
+  std::vector<std::thread> workers;
+  workers.reserve(n);
+  for (int i = 0; i < n; ++i)
+    workers.emplace_back([&, i]() { rc[i] = fftmech_staggered_step(ctxs[i], states[i], params[i], infos[i]); });
+  for (auto& w : workers) w.join();
+  for (int i = 0; i < n; ++i)
+    if (is_hard_error(rc[i])) return rc[i];
+  for (int i = 0; i < n; ++i)
+    if (rc[i] != FFTMECH_OK) return rc[i];
+  return FFTMECH_OK;
 }
 
 fftmech_status fftmech_profile_enable(fftmech_ctx* ctx, int enable) {

@@ -1,0 +1,6 @@
+// 2D column passes for columns of 1024 points (compile-time FFT, float).
+#include "kernels2d.cuh"
+
+namespace fftmech {
+FFTMECH_INST_COL_FIXED(1024)
+}  // namespace fftmech

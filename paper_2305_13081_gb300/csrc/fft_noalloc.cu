@@ -15,10 +15,11 @@ using namespace fftmech;
 namespace {
 
 constexpr int kMaxN = FFTMECH_FFT_NOALLOC_MAX_N;
-// Layout: x and y twiddles in double, then x and y twiddles in float, each
-// slot kMaxN entries (a plan of length n uses n - 1 of them).
-constexpr size_t kSlotD = (size_t)kMaxN * sizeof(cx<double>);
-constexpr size_t kSlotF = (size_t)kMaxN * sizeof(cx<float>);
+// Layout: x and y plans in double, then x and y plans in float; a slot holds
+// the twiddles and pass multipliers of a plan of length up to kMaxN (the
+// layout the transform kernels copy to shared memory).
+constexpr size_t kSlotD = tw_smem_bytes<double>(kMaxN);
+constexpr size_t kSlotF = tw_smem_bytes<float>(kMaxN);
 constexpr size_t kScratchBytes = 2 * kSlotD + 2 * kSlotF;
 constexpr int kMaxDevices = 64;
 
@@ -32,8 +33,19 @@ namespace {
 
 std::mutex g_mu;                      // serialises calls: host buffers and the device array
 void* g_scratch_dev[kMaxDevices];     // device address of the array, per device
-cx<double> g_tw_d[2 * kMaxN];         // host staging of the twiddles (no heap use)
-cx<float> g_tw_f[2 * kMaxN];
+cx<double> g_tw[2 * kMaxN];           // host FP64 twiddles of the x and y plans (no heap use)
+alignas(16) unsigned char g_stage[kScratchBytes];  // host image of the slots
+
+// One slot image: twiddles rounded to T, then the pass multipliers.
+template <typename T>
+void fill_slot(const HostPlan& p, const cx<double>* tw, unsigned char* slot) {
+  cx<T>* t = reinterpret_cast<cx<T>*>(slot);
+  for (int i = 0; i < p.n - 1; ++i) {
+    t[i].re = (T)tw[i].re;
+    t[i].im = (T)tw[i].im;
+  }
+  plan_multipliers(p.n, p.npass, p.radix, reinterpret_cast<unsigned int*>(slot + tw_smem_twiddles<T>(p.n)));
+}
 
 // Device address of the scratch array on `dev` (current device). The first
 // call on a device looks it up; later calls reuse it.
@@ -94,32 +106,32 @@ extern "C" fftmech_status fftmech_fft_noalloc(int ndim, const int n[3], int prec
   HostPlan px, py;
   factor_plan(nx, px);
   factor_plan(ny, py);
-  const int cx_ = twiddle_count(px), cy = twiddle_count(py);
-  fill_twiddles(px, g_tw_d);
-  fill_twiddles(py, g_tw_d + kMaxN);
+  fill_twiddles(px, g_tw);
+  fill_twiddles(py, g_tw + kMaxN);
   cudaStream_t st = (cudaStream_t)stream;
   const bool fp64 = precision == FFTMECH_FP64;
   px.tw_d = reinterpret_cast<cx<double>*>(base);
   py.tw_d = reinterpret_cast<cx<double>*>(base + kSlotD);
   px.tw_f = reinterpret_cast<cx<float>*>(base + 2 * kSlotD);
   py.tw_f = reinterpret_cast<cx<float>*>(base + 2 * kSlotD + kSlotF);
-  // Every twiddle a launch reads is written here first, so nothing in the
-  // array has to start at zero; entries past n - 1 are never read.
+  // Every byte a launch reads (twiddles and multipliers, the first
+  // tw_smem_bytes(n) bytes of a slot) is written here first, so nothing in
+  // the array has to start at zero.
   cudaError_t e = cudaSuccess;
   if (fp64) {
-    if (cx_) e = cudaMemcpyAsync(px.tw_d, g_tw_d, cx_ * sizeof(cx<double>), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && cy)
-      e = cudaMemcpyAsync(py.tw_d, g_tw_d + kMaxN, cy * sizeof(cx<double>), cudaMemcpyHostToDevice, st);
+    fill_slot<double>(px, g_tw, g_stage);
+    fill_slot<double>(py, g_tw + kMaxN, g_stage + kSlotD);
+    e = cudaMemcpyAsync(px.tw_d, g_stage, tw_smem_bytes<double>(nx), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(py.tw_d, g_stage + kSlotD, tw_smem_bytes<double>(ny), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = run<double>(px, py, inverse, data, nsm, (size_t)optin, st);
   } else {
-    for (int i = 0; i < cx_; ++i) { g_tw_f[i].re = (float)g_tw_d[i].re; g_tw_f[i].im = (float)g_tw_d[i].im; }
-    for (int i = 0; i < cy; ++i) {
-      g_tw_f[kMaxN + i].re = (float)g_tw_d[kMaxN + i].re;
-      g_tw_f[kMaxN + i].im = (float)g_tw_d[kMaxN + i].im;
-    }
-    if (cx_) e = cudaMemcpyAsync(px.tw_f, g_tw_f, cx_ * sizeof(cx<float>), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && cy)
-      e = cudaMemcpyAsync(py.tw_f, g_tw_f + kMaxN, cy * sizeof(cx<float>), cudaMemcpyHostToDevice, st);
+    fill_slot<float>(px, g_tw, g_stage + 2 * kSlotD);
+    fill_slot<float>(py, g_tw + kMaxN, g_stage + 2 * kSlotD + kSlotF);
+    e = cudaMemcpyAsync(px.tw_f, g_stage + 2 * kSlotD, tw_smem_bytes<float>(nx), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(py.tw_f, g_stage + 2 * kSlotD + kSlotF, tw_smem_bytes<float>(ny), cudaMemcpyHostToDevice,
+                          st);
     if (e == cudaSuccess) e = run<float>(px, py, inverse, data, nsm, (size_t)optin, st);
   }
   if (e == cudaErrorInvalidConfiguration) return FFTMECH_ERR_UNSUPPORTED_SIZE;

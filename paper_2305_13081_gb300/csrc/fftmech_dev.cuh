@@ -132,7 +132,10 @@ __device__ __forceinline__ void dft(cx<T>* v) {
 struct FastDiv {
   unsigned int m;
   int d;
-  __device__ __forceinline__ explicit FastDiv(int d_) : m(d_ > 1 ? 0xFFFFFFFFu / (unsigned)d_ + 1u : 0u), d(d_) {}
+  __host__ __device__ static unsigned int magic(int d_) { return d_ > 1 ? 0xFFFFFFFFu / (unsigned)d_ + 1u : 0u; }
+  __device__ __forceinline__ explicit FastDiv(int d_) : m(magic(d_)), d(d_) {}
+  // from a multiplier computed elsewhere (no division in the kernel)
+  __device__ __forceinline__ FastDiv(unsigned int m_, int d_) : m(m_), d(d_) {}
   __device__ __forceinline__ int div(int x) const { return d > 1 ? (int)__umulhi((unsigned)x, m) : x; }
 };
 
@@ -272,6 +275,12 @@ struct FftPlanDev {
   int npass;
   unsigned long long rcode;
   const cx<T>* tw;
+  // FastDiv multipliers of pass s: mag[s] for Ns (sub-transform length
+  // before the pass), mag[kMaxPass + s] for n / r (butterflies per line).
+  // They follow the twiddles in the plan's buffer (at byte offset
+  // tw_smem_twiddles(n)); kernels copy both to shared memory and point mag
+  // there (NULL: computed in place).
+  const unsigned int* mag;
 };
 
 // Butterflies a thread keeps in registers per pass: about nine points for
@@ -286,13 +295,14 @@ struct PassBatch {
 // stored [i][line]); otherwise consecutive butterflies of one line.
 template <typename T, int R, int S>
 __device__ __forceinline__ void stockham_pass(cx<T>* buf, int n, int Ns, const cx<T>* __restrict__ tw,
-                                              int nlines, int ls, int is, bool lines_fast) {
+                                              int nlines, int ls, int is, bool lines_fast, const FastDiv& dlines,
+                                              unsigned int mnb, const FastDiv& dn) {
   constexpr int BM = PassBatch<R>::value;
   const int nb = n / R;
   const int total = nb * nlines;
+  const FastDiv dl = lines_fast ? dlines : FastDiv(mnb, nb);
   cx<T> v[BM][R];
   int lj[BM];
-  const FastDiv dl(lines_fast ? nlines : nb);
 #pragma unroll
   for (int b = 0; b < BM; ++b) {
     const int idx = threadIdx.x + b * blockDim.x;
@@ -307,7 +317,6 @@ __device__ __forceinline__ void stockham_pass(cx<T>* buf, int n, int Ns, const c
     }
   }
   __syncthreads();
-  const FastDiv dn(Ns);
 #pragma unroll
   for (int b = 0; b < BM; ++b) {
     const int idx = threadIdx.x + b * blockDim.x;
@@ -355,23 +364,26 @@ __device__ void fft_lines(cx<T>* buf, const FftPlanDev<T>& p, int nlines, int ls
   int off = 0;
   const int n = p.n;
   const unsigned long long code = p.rcode;
+  const FastDiv dlines(nlines);  // the only division of the transform
   for (int s = 0; s < p.npass; ++s) {
     const int r = (int)((code >> (4 * s)) & 15ull);
     const cx<T>* tw = p.tw + off;
+    const FastDiv dn(p.mag ? p.mag[s] : FastDiv::magic(Ns), Ns);
+    const unsigned int mnb = p.mag ? p.mag[kMaxPass + s] : FastDiv::magic(n / r);
     if constexpr (FamilyHas<FAM, 9>::value) {
-      if (r == 9) stockham_pass<T, 9, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+      if (r == 9) stockham_pass<T, 9, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast, dlines, mnb, dn);
     }
     if constexpr (FamilyHas<FAM, 8>::value) {
-      if (r == 8) stockham_pass<T, 8, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+      if (r == 8) stockham_pass<T, 8, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast, dlines, mnb, dn);
     }
     if constexpr (FamilyHas<FAM, 4>::value) {
-      if (r == 4) stockham_pass<T, 4, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+      if (r == 4) stockham_pass<T, 4, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast, dlines, mnb, dn);
     }
     if constexpr (FamilyHas<FAM, 3>::value) {
-      if (r == 3) stockham_pass<T, 3, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+      if (r == 3) stockham_pass<T, 3, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast, dlines, mnb, dn);
     }
     if constexpr (FamilyHas<FAM, 2>::value) {
-      if (r == 2) stockham_pass<T, 2, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast);
+      if (r == 2) stockham_pass<T, 2, S>(buf, n, Ns, tw, nlines, ls, is, lines_fast, dlines, mnb, dn);
     }
     off += Ns * (r - 1);
     Ns *= r;
@@ -382,15 +394,34 @@ __device__ void fft_lines(cx<T>* buf, const FftPlanDev<T>& p, int nlines, int ls
 // the start of their dynamic shared memory (with the other staged loads,
 // before their first barrier) so the passes read them with short latency.
 template <typename T>
-__host__ __device__ inline size_t tw_smem_bytes(int n) {
+__host__ __device__ constexpr size_t tw_smem_twiddles(int n) {
   return ((size_t)(n > 1 ? n - 1 : 0) * sizeof(cx<T>) + 15) & ~size_t(15);
 }
 template <typename T>
+__host__ __device__ constexpr size_t tw_smem_bytes(int n) {
+  return tw_smem_twiddles<T>(n) + 2 * kMaxPass * sizeof(unsigned int);
+}
+template <typename T>
 __device__ __forceinline__ FftPlanDev<T> plan_to_smem(const FftPlanDev<T>& p, cx<T>* dst) {
-  g2s_vec<4, true>(dst, p.tw, p.n > 1 ? p.n - 1 : 0);
+  // twiddles, padding and multipliers: one contiguous 16-byte multiple
+  g2s_vec<4, true>(reinterpret_cast<int4*>(dst), reinterpret_cast<const int4*>(p.tw),
+                   (int)(tw_smem_bytes<T>(p.n) / sizeof(int4)));
   FftPlanDev<T> q = p;
   q.tw = dst;
+  q.mag = reinterpret_cast<const unsigned int*>(reinterpret_cast<const unsigned char*>(dst) +
+                                                tw_smem_twiddles<T>(p.n));
   return q;
+}
+
+// Host: the multipliers that follow a plan's twiddles (see FftPlanDev).
+inline void plan_multipliers(int n, int npass, const int* radix, unsigned int* out) {
+  for (int s = 0; s < 2 * kMaxPass; ++s) out[s] = 0u;
+  int Ns = 1;
+  for (int s = 0; s < npass; ++s) {
+    out[s] = FastDiv::magic(Ns);
+    out[kMaxPass + s] = FastDiv::magic(n / radix[s]);
+    Ns *= radix[s];
+  }
 }
 
 // fft_lines as a real call: a kernel that keeps much state live across a
@@ -403,12 +434,17 @@ __device__ __noinline__ void fft_lines_call(cx<T>* buf, const FftPlanDev<T> p, i
 }
 
 // ---------------------------------------------------------------- reductions
+// Linear thread index and thread count of the block (kernels with 2D
+// blocks reduce too).
+__device__ __forceinline__ int flat_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
+__device__ __forceinline__ int flat_nthreads() { return blockDim.x * blockDim.y * blockDim.z; }
 // Sum of K doubles over the block; result valid in thread 0. Uses `scratch`
 // (>= 32 * K doubles of shared memory). Deterministic for a fixed launch.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
+  const int tid = flat_tid();
+  const int lane = tid & 31, wid = tid >> 5;
+  const int nw = (flat_nthreads() + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
 #pragma unroll
@@ -457,8 +493,9 @@ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
 // Block sum of double-float values, returned as double in thread 0 (others
 // get a partial). scratch: 64 floats of shared memory.
 __device__ __forceinline__ double block_sum_df(dfloat v, float* scratch) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
+  const int tid = flat_tid();
+  const int lane = tid & 31, wid = tid >> 5;
+  const int nw = (flat_nthreads() + 31) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const dfloat w{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
@@ -488,7 +525,7 @@ template <int K>
 __device__ __forceinline__ bool publish_partials(const double (&v)[K], double* partials,
                                                  unsigned int* counter) {
   __shared__ int am_last;
-  if (threadIdx.x == 0) {
+  if (flat_tid() == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) partials[(size_t)blockIdx.x * K + k] = v[k];
     __threadfence();
@@ -509,14 +546,14 @@ __device__ __forceinline__ void gather_partials(double (&tot)[K], const double* 
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = 0.0;
   // fixed assignment: thread t sums blocks t, t + bd, ... in order
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = flat_tid(); b < (int)gridDim.x; b += flat_nthreads()) {
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] += __ldcg(partials + (size_t)b * K + k);
   }
   block_sum<K>(v, scratch);
 #pragma unroll
   for (int k = 0; k < K; ++k) tot[k] = v[k];
-  if (threadIdx.x == 0) *counter = 0u;
+  if (flat_tid() == 0) *counter = 0u;
 }
 
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }

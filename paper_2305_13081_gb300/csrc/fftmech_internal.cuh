@@ -137,14 +137,12 @@ struct Shape2 {
   int threads_plain;
 };
 
-// 3D launch shapes: x-line bricks of ry lines x zc planes, and strips of
-// cw spectral columns for the y and z passes.
+// 3D launch shapes: FP64 residual bricks of ry lines x zc planes, and
+// strips of cw spectral columns for the y and z passes.
 struct Shape3 {
   int batch;
   int nx, ny, nz;
   long long sst;  // complex numbers per problem in the spectral buffer
-  int ry_upd, zc_upd, thr_upd;
-  int ry_dir, zc_dir, thr_dir;
   int ry_res, zc_res, thr_res;
   int cw_y, thr_y;
   int cw_z, thr_z;
@@ -161,6 +159,7 @@ struct LineShape {
 struct StenShape {
   int batch;
   int tx, ty, zc, threads;
+  int grid;  // blocks per problem (they loop over the tiles)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -169,19 +168,28 @@ struct StenShape {
 template <typename T, int D, int FX>
 cudaError_t launch_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                             const Shape2& sh, int zero_u, int filter, cudaStream_t st);
-template <typename T, int D, int FX>
-cudaError_t launch_update(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
-                          const Shape2& sh, cudaStream_t st);
-template <typename T, int D, int FX>
-cudaError_t launch_direction(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
-                             const Shape2& sh, cudaStream_t st);
-template <typename T, int FY>
+template <typename T, int FY, int NY, int CWC>
 cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec<T>& sp,
                            const Shape2& sh, int mode, int inverse, double* partials,
                            SolverScalars* sc, const int* pmode, cudaStream_t st);
 template <typename T, int FX>
 cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int inverse,
                           const Shape2& sh, cudaStream_t st);
+
+// Line lengths with compile-time FFT kernels (float): the benchmark grids
+// (3^4 .. 3^7 and 2^7 .. 2^10).
+#define FFTMECH_FIXED_SWITCH(n, CALL) \
+  switch (n) {                        \
+    case 81: return CALL(81);         \
+    case 243: return CALL(243);       \
+    case 729: return CALL(729);       \
+    case 2187: return CALL(2187);     \
+    case 128: return CALL(128);       \
+    case 256: return CALL(256);       \
+    case 512: return CALL(512);       \
+    case 1024: return CALL(1024);     \
+    default: break;                   \
+  }
 
 #define FFTMECH_FAMILY_SWITCH(fam, CALL)      \
   switch (fam) {                              \
@@ -199,26 +207,22 @@ inline cudaError_t launch_residual_f(int fx, const Op<T>& op, const Vec2<T>& v,
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
-template <typename T, int D>
-inline cudaError_t launch_update_f(int fx, const Op<T>& op, const Vec2<T>& v,
-                                   const FftPlanDev<T>& px, const Shape2& sh, cudaStream_t st) {
-#define FFTMECH_C(F) launch_update<T, D, F>(op, v, px, sh, st)
-  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
-#undef FFTMECH_C
-}
-template <typename T, int D>
-inline cudaError_t launch_direction_f(int fx, const Op<T>& op, const Vec2<T>& v,
-                                      const FftPlanDev<T>& px, const Shape2& sh, cudaStream_t st) {
-#define FFTMECH_C(F) launch_direction<T, D, F>(op, v, px, sh, st)
-  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
-#undef FFTMECH_C
-}
 template <typename T>
 inline cudaError_t launch_colpass_f(int fy, int nx, int ny, cx<T>* S, const FftPlanDev<T>& py,
                                     const Spec<T>& sp, const Shape2& sh, int mode, int inverse,
                                     double* partials, SolverScalars* sc, const int* pmode,
                                     cudaStream_t st) {
-#define FFTMECH_C(F) launch_colpass<T, F>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st)
+  if constexpr (sizeof(T) == 4) {
+    // compile-time column plans for the benchmark lengths and strip widths
+#define FFTMECH_CW(NY)                                                                                \
+  (sh.cols == 8 ? launch_colpass<T, FAM_ALL, NY, 8>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st) \
+                : launch_colpass<T, FAM_ALL, NY, 4>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st))
+    if (sh.cols == 4 || sh.cols == 8) {
+      FFTMECH_FIXED_SWITCH(ny, FFTMECH_CW)
+    }
+#undef FFTMECH_CW
+  }
+#define FFTMECH_C(F) launch_colpass<T, F, 0, 0>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st)
   FFTMECH_FAMILY_SWITCH(fy, FFTMECH_C)
 #undef FFTMECH_C
 }
@@ -235,13 +239,7 @@ inline cudaError_t launch_rowfft_f(int fx, int nx, int ny, cx<T>* S, const FftPl
 template <typename T, int D, int FX>
 cudaError_t launch3_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
                              int zero_u, int filter, cudaStream_t st);
-template <typename T, int D, int FX>
-cudaError_t launch3_update(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
-                           cudaStream_t st);
-template <typename T, int D, int FX>
-cudaError_t launch3_direction(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
-                              cudaStream_t st);
-template <typename T, int FL>
+template <typename T, int FL, int NL, int CWC>
 cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage, const FftPlanDev<T>& pl,
                           const Spec<T>& sp, int mode, double* partials, SolverScalars* sc, const int* pmode,
                           cudaStream_t st);
@@ -253,37 +251,32 @@ inline cudaError_t launch3_residual_f(int fx, const Op<T>& op, const Vec2<T>& v,
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
-template <typename T, int D>
-inline cudaError_t launch3_update_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
-                                    const Shape3& sh, cudaStream_t st) {
-#define FFTMECH_C(F) launch3_update<T, D, F>(op, v, px, sh, st)
-  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
-#undef FFTMECH_C
-}
-template <typename T, int D>
-inline cudaError_t launch3_direction_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
-                                       const Shape3& sh, cudaStream_t st) {
-#define FFTMECH_C(F) launch3_direction<T, D, F>(op, v, px, sh, st)
-  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
-#undef FFTMECH_C
-}
 template <typename T>
 inline cudaError_t launch3_lines_f(int fl, cx<T>* S, const Shape3& sh, int D, int axis, int stage,
                                    const FftPlanDev<T>& pl, const Spec<T>& sp, int mode, double* partials,
                                    SolverScalars* sc, const int* pmode, cudaStream_t st) {
-#define FFTMECH_C(F) launch3_lines<T, F>(S, sh, D, axis, stage, pl, sp, mode, partials, sc, pmode, st)
+  if constexpr (sizeof(T) == 4) {
+    const int cw = axis == 1 ? sh.cw_y : sh.cw_z;
+    if (cw == 16) {
+#define FFTMECH_C(NL) launch3_lines<T, FAM_ALL, NL, 16>(S, sh, D, axis, stage, pl, sp, mode, partials, sc, pmode, st)
+      FFTMECH_FIXED_SWITCH(pl.n, FFTMECH_C)
+#undef FFTMECH_C
+    }
+  }
+#define FFTMECH_C(F) launch3_lines<T, F, 0, 0>(S, sh, D, axis, stage, pl, sp, mode, partials, sc, pmode, st)
   FFTMECH_FAMILY_SWITCH(fl, FFTMECH_C)
 #undef FFTMECH_C
 }
 
 // Split iteration launchers; x-line kernels take the radix family of the x
 // transform, DIM the grid dimension.
-template <typename T, int D, int FX, int DIM>
+template <typename T, int D, int FX, int DIM, int NX>
 cudaError_t launch_xdir(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
                         cudaStream_t st);
-template <typename T, int D, int FX, int DIM>
+template <typename T, int D, int FX, int DIM, int NX>
 cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
                         cudaStream_t st);
+
 template <typename T, int D>
 cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss, cudaStream_t st);
 template <typename T, int D>
@@ -292,14 +285,24 @@ cudaError_t launch_sten3(const Op<T>& op, const Vec2<T>& v, const StenShape& ss,
 template <typename T, int D, int DIM>
 inline cudaError_t launch_xdir_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                                  const LineShape& ls, cudaStream_t st) {
-#define FFTMECH_C(F) launch_xdir<T, D, F, DIM>(op, v, px, ls, st)
+  if constexpr (sizeof(T) == 4) {
+#define FFTMECH_C(NX) launch_xdir<T, D, FAM_ALL, DIM, NX>(op, v, px, ls, st)
+    FFTMECH_FIXED_SWITCH(px.n, FFTMECH_C)
+#undef FFTMECH_C
+  }
+#define FFTMECH_C(F) launch_xdir<T, D, F, DIM, 0>(op, v, px, ls, st)
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
 template <typename T, int D, int DIM>
 inline cudaError_t launch_xupd_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                                  const LineShape& ls, cudaStream_t st) {
-#define FFTMECH_C(F) launch_xupd<T, D, F, DIM>(op, v, px, ls, st)
+  if constexpr (sizeof(T) == 4) {
+#define FFTMECH_C(NX) launch_xupd<T, D, FAM_ALL, DIM, NX>(op, v, px, ls, st)
+    FFTMECH_FIXED_SWITCH(px.n, FFTMECH_C)
+#undef FFTMECH_C
+  }
+#define FFTMECH_C(F) launch_xupd<T, D, F, DIM, 0>(op, v, px, ls, st)
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
@@ -358,37 +361,6 @@ cudaError_t launch3_history(long long N, int batch, const uint8_t* phase, double
 // (byte offsets, each region 16-byte aligned), used by host and device.
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// update: [P: D (R+2) rows, reused by the packed row spectrum (R complex
-// rows)] [SG: 3 (R+1) rows] [RS: old residual, D R rows] [MG: g or c0 field,
-// R+1 rows] [PH: phase bytes, R+1 rows] [MK: mask bytes, R rows]
-struct UpdLayout {
-  size_t a, b, c, d, e, f, total;
-  __host__ __device__ UpdLayout(int nx, int R, int es, int D) {
-    const size_t rowsA = (size_t)(D * (R + 2) > 2 * R ? D * (R + 2) : 2 * R);
-    a = 0;
-    b = a + align16(rowsA * nx * es);
-    c = b + align16((size_t)3 * (R + 1) * nx * es);
-    d = c + align16((size_t)D * R * nx * es);
-    e = d + align16((size_t)(R + 1) * nx * es);
-    f = e + align16((size_t)(R + 1) * nx);
-    total = f + align16((size_t)R * nx);
-  }
-};
-
-// direction: [F: R+1 complex rows] [P: D (R+1) rows] [MG: R rows]
-// [PH: R byte rows] [MK: R+1 byte rows]
-struct DirLayout {
-  size_t a, b, c, d, e, total;
-  __host__ __device__ DirLayout(int nx, int R, int es, int D) {
-    a = 0;
-    b = a + align16((size_t)2 * (R + 1) * nx * es);
-    c = b + align16((size_t)D * (R + 1) * nx * es);
-    d = c + align16((size_t)R * nx * es);
-    e = d + align16((size_t)R * nx);
-    total = e + align16((size_t)(R + 1) * nx);
-  }
-};
-
 // residual (FP64 stencil): [P: max(D (R+2) doubles, 2 R T) per column]
 // [SG: 3 (R+1) doubles per column]
 template <typename T, int D>
@@ -400,42 +372,24 @@ inline size_t smem_residual(int nx, int R) {
 // and the z component's half spectrum (nx/2 + 1); D = 1 the half spectrum.
 __host__ __device__ inline int nxs_of(int nx, int D) { return (D == 3 ? nx : 0) + nx / 2 + 1; }
 
-// 3D x-line kernels (stencil rows: update, kind 0, and FP64 residual, kind
-// 1): [P: two planes x D (R+2) lines, compute type] [SP: in-plane stress or
-// flux, NP (R+1) lines] [SZ: z-differenced components, two planes x NZ
-// (R+1) lines] [RS: old residual, D R lines (kind 0)] [F: NF R complex
-// lines] [MG: g or c0 field, R+1 lines] [PH: phase bytes, R+1 lines]
-// [MK: mask bytes, R lines]
+// 3D FP64 residual bricks: [P: two planes x D (R+2) lines, double] [SP:
+// in-plane stress or flux, NP (R+1) lines] [SZ: z-differenced components,
+// two planes x NZ (R+1) lines] [F: NF R complex lines of T] [MG: g or c0
+// field, R+1 lines of T] [PH: phase bytes, R+1 lines] [MK: mask bytes, R
+// lines]
 struct Row3Layout {
-  size_t P, SP, SZ, RS, F, MG, PH, MK, total;
-  __host__ __device__ Row3Layout(int nx, int R, int cs, int ts, int D, int kind) {
+  size_t P, SP, SZ, F, MG, PH, MK, total;
+  __host__ __device__ Row3Layout(int nx, int R, int cs, int ts, int D) {
     const size_t np = D == 3 ? 3 : 2, nzc = D == 3 ? 3 : 1, nf = D == 3 ? 2 : 1;
     const size_t L = (size_t)nx;
     P = 0;
     SP = P + align16((size_t)2 * D * (R + 2) * L * cs);
     SZ = SP + align16(np * (R + 1) * L * cs);
-    RS = SZ + align16(2 * nzc * (R + 1) * L * cs);
-    F = RS + (kind == 0 ? align16((size_t)D * R * L * cs) : 0);
+    F = SZ + align16(2 * nzc * (R + 1) * L * cs);
     MG = F + align16(nf * R * L * 2 * ts);
     PH = MG + align16((size_t)(R + 1) * L * ts);
     MK = PH + align16((size_t)(R + 1) * L);
     total = MK + align16((size_t)R * L);
-  }
-};
-
-// 3D direction: [F: NF (R+1) complex lines] [P: two planes x D (R+1) lines]
-// [MG: R lines] [PH: R byte lines] [MK: R+1 byte lines]
-struct Dir3Layout {
-  size_t F, P, MG, PH, MK, total;
-  __host__ __device__ Dir3Layout(int nx, int R, int ts, int D) {
-    const size_t nf = D == 3 ? 2 : 1;
-    const size_t L = (size_t)nx;
-    F = 0;
-    P = F + align16(nf * (R + 1) * L * 2 * ts);
-    MG = P + align16((size_t)2 * D * (R + 1) * L * ts);
-    PH = MG + align16((size_t)R * L * ts);
-    MK = PH + align16((size_t)R * L);
-    total = MK + align16((size_t)(R + 1) * L);
   }
 };
 
@@ -462,9 +416,6 @@ inline size_t sten3_smem(int tx, int ty, int D) {
   return ((size_t)2 * D * (ty + 2) * (tx + 2) + np * sgs + 2 * nzc * sgs + sgs) * sizeof(T) + sgs;
 }
 
-template <typename T, int D>
-inline size_t smem_update(int nx, int R) { return UpdLayout(nx, R, (int)sizeof(T), D).total; }
-template <typename T, int D>
-inline size_t smem_direction(int nx, int R) { return DirLayout(nx, R, (int)sizeof(T), D).total; }
+
 
 }  // namespace fftmech

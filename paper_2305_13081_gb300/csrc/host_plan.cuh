@@ -94,6 +94,7 @@ inline FftPlanDev<T> dev_plan(const HostPlan& p) {
   d.npass = p.npass;
   d.rcode = p.rcode;
   if constexpr (sizeof(T) == 4) d.tw = p.tw_f; else d.tw = p.tw_d;
+  d.mag = nullptr;
   return d;
 }
 
@@ -112,35 +113,41 @@ inline int need_threads(const HostPlan& p, int nlines) {
   return need;
 }
 
-// Launch shapes for an nx x ny grid: rows per block so that the row grids
-// have about two blocks per SM while the shared memory stays within the
-// budget, and enough threads for the widest FFT pass. Returns false if even
-// one row / one column does not fit.
+// 2D launch shapes of the residual and column kernels: one row per residual
+// block; strips of CW columns (8 for float, 4 for double), halved while the
+// batch would have fewer than two strips per SM, within the shared-memory
+// budget and the widest column pass fitting 512 threads. Returns false if
+// even one row / one column does not fit.
 template <typename T>
-bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_total, Shape2& s) {
+bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_total, Shape2& s, int batch = 1) {
   const int nx = px.n, ny = py.n;
   const size_t optin = optin_total - 1024;  // room for the kernels' static shared memory
   const int tmax = 512;
   const size_t budget = std::min<size_t>(optin, sizeof(T) == 4 ? 100 * 1024 : 110 * 1024);
   const size_t twx = tw_smem_bytes<T>(nx), twy = tw_smem_bytes<T>(ny);
-  auto fits = [&](int r, size_t lim) {
-    return smem_update<T, 2>(nx, r) + twx <= lim && smem_direction<T, 2>(nx, r) + twx <= lim &&
-           smem_update<T, 1>(nx, r) + twx <= lim && smem_direction<T, 1>(nx, r) + twx <= lim &&
-           need_threads(px, r + 1) <= tmax;
-  };
-  int R = std::max(1, std::min(ny, ny / (2 * nsm)));
-  while (R > 1 && !fits(R, budget)) --R;
-  if (!fits(R, optin)) return false;
+  s = Shape2();
   s.batch = 1;
-  s.rows_update = R;
-  s.rows_dir = R;
-  s.threads_update = std::min(tmax, std::max(256, round32(need_threads(px, R + 1))));
-  s.threads_dir = s.threads_update;
+  s.rows_update = s.rows_dir = 1;  // (row FFT of the bare transform only)
+  s.threads_update = s.threads_dir = std::min(tmax, std::max(256, round32(need_threads(px, 1))));
   s.rows_res = 1;
   if (smem_residual<T, 2>(nx, 1) + twx > optin || smem_residual<T, 1>(nx, 1) + twx > optin) return false;
   s.threads_res = std::min(tmax, std::max(256, round32(need_threads(px, 1))));
   int CW = sizeof(T) == 4 ? 8 : 4;
-  while (CW > 2 && (nx + CW - 1) / CW < 2 * nsm) CW /= 2;  // at least two strips per SM when possible
+  const bool fixed = sizeof(T) == 4 && (ny == 81 || ny == 243 || ny == 729 || ny == 2187 || ny == 128 ||
+                                        ny == 256 || ny == 512 || ny == 1024);
+  if (fixed) {
+    // compile-time column plans (512 threads, several butterflies each):
+    // 64-byte (or 32-byte for 2187) row segments; 4 columns when the batch
+    // has fewer than two 8-column strips per SM
+    if (ny >= 1024 || (long long)((nx + 7) / 8) * batch < 2LL * nsm) CW = 4;
+    if ((size_t)ny * CW * sizeof(cx<T>) + twy > optin) return false;
+    s.cols = CW;
+    s.threads_col = 512;
+    s.threads_plain = s.threads_update;
+    return true;
+  }
+  // at least two strips per SM (over the batch) when possible
+  while (CW > 2 && (long long)((nx + CW - 1) / CW) * batch < 2LL * nsm) CW /= 2;
   while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) + twy > budget || need_threads(py, CW) > tmax)) CW /= 2;
   if ((size_t)ny * CW * sizeof(cx<T>) + twy > optin || need_threads(py, CW) > tmax) return false;
   s.cols = CW;
@@ -149,11 +156,10 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   return true;
 }
 
-// Launch shapes for an nx x ny x nz grid (3D kernels). Bricks of R lines:
-// the largest R whose shared memory stays within a budget that lets two
-// blocks share an SM (for both D = 1 and D = 3), with (R + 2) nx < 2^16 for
-// the kernels' integer division; Zc planes per brick so that a launch has
-// about six blocks per SM. Line passes: strips of CW spectral columns.
+// 3D launch shapes of the FP64 residual bricks (R lines x Zc planes, the
+// largest R <= 4 that fits, (R + 2) nx < 2^16 for the kernel's integer
+// division, Zc giving about six blocks per SM) and of the y / z line passes
+// (strips of CW spectral columns: 16 for float, 8 for double).
 template <typename T>
 bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, int nsm, size_t optin_total,
                    int batch, Shape3& s) {
@@ -168,45 +174,23 @@ bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, i
   s.ny = ny;
   s.nz = nz;
   s.sst = (long long)(nx + nx / 2 + 1) * ny * nz;
-  auto idx_ok = [&](int r) { return (long long)(r + 2) * nx < 65536 && (long long)r * nxs_of(nx, 3) < 65536; };
   const size_t twx = tw_smem_bytes<T>(nx);
-  auto upd_fits = [&](int r, size_t lim) {
-    return idx_ok(r) && Row3Layout(nx, r, es, es, 3, 0).total + twx <= lim &&
-           Row3Layout(nx, r, es, es, 1, 0).total + twx <= lim && need_threads(px, 2 * r) <= 256;
+  auto res_fits = [&](int r) {
+    return (long long)(r + 2) * nx < 65536 && (long long)r * nxs_of(nx, 3) < 65536 &&
+           Row3Layout(nx, r, 8, es, 3).total + twx <= optin && Row3Layout(nx, r, 8, es, 1).total + twx <= optin &&
+           need_threads(px, 2 * r) <= tmax;
   };
-  auto dir_fits = [&](int r, size_t lim) {
-    return idx_ok(r) && Dir3Layout(nx, r, es, 3).total + twx <= lim && Dir3Layout(nx, r, es, 1).total + twx <= lim &&
-           need_threads(px, 2 * (r + 1)) <= 256;
-  };
-  auto res_fits = [&](int r, size_t lim) {
-    return idx_ok(r) && Row3Layout(nx, r, 8, es, 3, 1).total + twx <= lim &&
-           Row3Layout(nx, r, 8, es, 1, 1).total + twx <= lim && need_threads(px, 2 * r) <= tmax;
-  };
-  auto pick = [&](auto fits) {
-    int r = std::min(ny, 8);
-    while (r > 1 && !fits(r, budget)) --r;
-    return fits(r, optin) ? r : 0;
-  };
-  s.ry_upd = pick(upd_fits);
-  s.ry_dir = pick(dir_fits);
   int rr = std::min(ny, 4);
-  while (rr > 1 && !res_fits(rr, optin)) --rr;
-  s.ry_res = res_fits(rr, optin) ? rr : 0;
-  if (!s.ry_upd || !s.ry_dir || !s.ry_res) return false;
-  auto zchunk = [&](int r) {
-    const long long nty = (ny + r - 1) / r;
-    const long long target = 6LL * nsm;
-    long long nzc = (target + nty * batch - 1) / (nty * batch);
+  while (rr > 1 && !res_fits(rr)) --rr;
+  if (!res_fits(rr)) return false;
+  s.ry_res = rr;
+  {
+    const long long nty = (ny + rr - 1) / rr;
+    long long nzc = (6LL * nsm + nty * batch - 1) / (nty * batch);
     nzc = std::max(1LL, std::min<long long>(nzc, nz));
-    int zc = (int)((nz + nzc - 1) / nzc);
-    return std::max(std::min(4, nz), zc);
-  };
-  s.zc_upd = zchunk(s.ry_upd);
-  s.zc_dir = zchunk(s.ry_dir);
-  s.zc_res = zchunk(s.ry_res);
-  s.thr_upd = std::max(128, round32(need_threads(px, 2 * s.ry_upd)));
-  s.thr_dir = std::max(128, round32(need_threads(px, 2 * (s.ry_dir + 1))));
-  s.thr_res = std::min(tmax, std::max(128, round32(need_threads(px, 2 * s.ry_res))));
+    s.zc_res = std::max(std::min(4, nz), (int)((nz + nzc - 1) / nzc));
+  }
+  s.thr_res = std::min(tmax, std::max(128, round32(need_threads(px, 2 * rr))));
   auto strip = [&](const HostPlan& pl, int& cw, int& thr) {
     int c = sizeof(T) == 4 ? 16 : 8;
     const size_t tw = tw_smem_bytes<T>(pl.n);
@@ -219,7 +203,7 @@ bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, i
     return true;
   };
   if (!strip(py, s.cw_y, s.thr_y) || !strip(pz, s.cw_z, s.thr_z)) return false;
-  if ((long long)batch * std::max(ny, nz) > 65535) return false;  // grid.y of the line passes
+  if ((long long)batch > 65535) return false;  // grid.y of the line passes
   return true;
 }
 
@@ -262,6 +246,7 @@ inline void choose_sten_shape(int nx, int ny, int nz, int dim, int nsm, int batc
   s = StenShape();
   s.batch = batch;
   s.threads = 256;
+  s.grid = std::max(1, (8 * nsm + batch - 1) / batch);  // blocks per problem, looping over tiles
   if (dim == 2) {
     s.tx = std::min(nx, 64);
     s.ty = std::min(ny, 16);

@@ -13,9 +13,12 @@
 // half is rebuilt by conjugate symmetry before the inverse transform.
 #pragma once
 
+#include <atomic>
+
 #include "fftmech_internal.cuh"
 #include "fftmech.h"
 #include "pcg_dev.cuh"
+#include "fftc.cuh"
 
 namespace fftmech {
 
@@ -55,7 +58,7 @@ __device__ __forceinline__ void line_views(Op<T>& op, Vec2<T>& v, int b, size_t 
 // Lines l0 .. l0 + L - 1 (flattened (z, y) index): z = x-IFFT(S), masked
 // voxels (D = 1) 0, p = z + beta p_old. Shared memory: [twiddles]
 // [F: NF L complex lines] [PO: old direction, D L lines].
-template <typename T, int D, int FX, int DIM>
+template <typename T, int D, int FX, int DIM, int NX>
 __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst) {
   using LL = LineLayout<DIM, D>;
   const int nx = op.nx;
@@ -83,10 +86,26 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   if constexpr (DIM == 2) {
     g2s_vec<8, true>(F, v.S + t0, nl * nx);
   } else {
-    for (int l = 0; l < nl; ++l) {
-      const cx<T>* Srow = v.S + (size_t)(l0 + l) * nxs;
-      if constexpr (D == 3) g2s_vec<8, true>(F + (size_t)l * nx, Srow, nx);
-      g2s_vec<8, true>(FB + (size_t)l * nx, Srow + nxa, nxh);
+    // the block's spectral rows are one contiguous run of nl nxs numbers:
+    // one flattened loop keeps eight loads in flight per thread
+    const cx<T>* Sb = v.S + (size_t)l0 * nxs;
+    const int ne = nl * nxs;
+    const FastDiv dns(nxs);
+    const int bd = blockDim.x;
+    for (int i = threadIdx.x; i < ne; i += 8 * bd) {
+      cx<T> t[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (i + k * bd < ne) t[k] = Sb[i + k * bd];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int e = i + k * bd;
+        if (e < ne) {
+          const int l = dns.div(e), c = e - l * nxs;
+          if (c < nxa) F[(size_t)l * nx + c] = t[k];
+          else FB[(size_t)l * nx + (c - nxa)] = t[k];
+        }
+      }
     }
   }
   if (with_old) {
@@ -96,14 +115,16 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   __syncthreads();
   if constexpr (LL::HALF) {
     const int nup = nx - nxh;
+    const FastDiv dup(nup);
     for (int i = threadIdx.x; i < nl * nup; i += blockDim.x) {
-      const int l = i / nup, k = nxh + (i - l * nup);
+      const int l = dup.div(i), k = nxh + (i - l * nup);
       const cx<T> w = FB[(size_t)l * nx + (nx - k)];
       FB[(size_t)l * nx + k] = mk(w.re, -w.im);
     }
     __syncthreads();
   }
-  fft_lines<T, 1, FX>(F, px_s, LL::NF * nl, nx, 1, false);
+  if constexpr (NX > 0) fftc<T, 1, NX, false>(F, px_s.tw, LL::NF * nl);
+  else fft_lines<T, 1, FX>(F, px_s, LL::NF * nl, nx, 1, false);
   const bool masked = (D == 1) && op.mask;
   for (int i = threadIdx.x; i < nl * nx; i += blockDim.x) {
     T z[D];
@@ -133,7 +154,7 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
 // u += alpha p (double or double-float iterate), r -= alpha q, S = x-FFT(r)
 // on lines l0 .. l0 + L - 1. Reliable-update iterations (mode 1) move the
 // iterate only. Shared memory: [twiddles] [F: NF L complex lines].
-template <typename T, int D, int FX, int DIM>
+template <typename T, int D, int FX, int DIM, int NX>
 __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst) {
   using LL = LineLayout<DIM, D>;
   const int nx = op.nx;
@@ -190,26 +211,46 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;
-  // residual update and packing
-  for (int i = tid; i < n; i += bd) {
-    T r[D];
+  // residual update and packing, U voxels per thread in flight
+  constexpr int U = 4;
+  for (int i0 = tid; i0 < n; i0 += U * bd) {
+    T r[U][D], q[U][D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) r[c] = v.r[c * N + t0 + i] - a * v.q[c * N + t0 + i];
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * bd;
+      if (i < n) {
 #pragma unroll
-    for (int c = 0; c < D; ++c) v.r[c * N + t0 + i] = r[c];
-    if constexpr (DIM == 2) {
-      F[i] = mk(r[0], D == 2 ? r[D - 1] : T(0));
-    } else {
-      if constexpr (D == 3) {
-        F[i] = mk(r[0], r[1]);
-        FB[i] = mk(r[2], T(0));
-      } else {
-        FB[i] = mk(r[0], T(0));
+        for (int c = 0; c < D; ++c) {
+          r[u][c] = v.r[c * N + t0 + i];
+          q[u][c] = v.q[c * N + t0 + i];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * bd;
+      if (i < n) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          r[u][c] -= a * q[u][c];
+          v.r[c * N + t0 + i] = r[u][c];
+        }
+        if constexpr (DIM == 2) {
+          F[i] = mk(r[u][0], D == 2 ? r[u][D - 1] : T(0));
+        } else {
+          if constexpr (D == 3) {
+            F[i] = mk(r[u][0], r[u][1]);
+            FB[i] = mk(r[u][2], T(0));
+          } else {
+            FB[i] = mk(r[u][0], T(0));
+          }
+        }
       }
     }
   }
   __syncthreads();
-  fft_lines<T, -1, FX>(F, px_s, LL::NF * nl, nx, 1, false);
+  if constexpr (NX > 0) fftc<T, -1, NX, false>(F, px_s.tw, LL::NF * nl);
+  else fft_lines<T, -1, FX>(F, px_s, LL::NF * nl, nx, 1, false);
   if constexpr (DIM == 2) {
     s2g(v.S + t0, F, n);
   } else {
@@ -226,7 +267,7 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
 
 // ---------------------------------------------------------------- launchers
 template <typename K>
-static cudaError_t set_smem_l(K kernel, size_t bytes, int& configured) {
+static cudaError_t set_smem_l(K kernel, size_t bytes, std::atomic<int>& configured) {
   if (configured) return cudaSuccess;
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -243,43 +284,49 @@ static cudaError_t set_smem_l(K kernel, size_t bytes, int& configured) {
   return e;
 }
 
-template <typename T, int D, int FX, int DIM>
+template <typename T, int D, int FX, int DIM, int NX>
 cudaError_t launch_xdir(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
                         cudaStream_t st) {
   const int L = ls.L_dir;
   const size_t sm = xdir_smem<T>(op.nx, L, D, DIM);
-  static int cfg = 0;
-  cudaError_t e = set_smem_l(k_xdir<T, D, FX, DIM>, sm, cfg);
+  static std::atomic<int> cfg{0};
+  cudaError_t e = set_smem_l(k_xdir<T, D, FX, DIM, NX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const int nlines = op.ny * op.nz;
   const dim3 grid((nlines + L - 1) / L, ls.batch);
-  k_xdir<T, D, FX, DIM><<<grid, ls.thr_dir, sm, st>>>(op, v, px, L, ls.sst);
+  k_xdir<T, D, FX, DIM, NX><<<grid, ls.thr_dir, sm, st>>>(op, v, px, L, ls.sst);
   return cudaGetLastError();
 }
 
-template <typename T, int D, int FX, int DIM>
+template <typename T, int D, int FX, int DIM, int NX>
 cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
                         cudaStream_t st) {
   const int L = ls.L_upd;
   const size_t sm = xupd_smem<T>(op.nx, L, D, DIM);
-  static int cfg = 0;
-  cudaError_t e = set_smem_l(k_xupd<T, D, FX, DIM>, sm, cfg);
+  static std::atomic<int> cfg{0};
+  cudaError_t e = set_smem_l(k_xupd<T, D, FX, DIM, NX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const int nlines = op.ny * op.nz;
   const dim3 grid((nlines + L - 1) / L, ls.batch);
-  k_xupd<T, D, FX, DIM><<<grid, ls.thr_upd, sm, st>>>(op, v, px, L, ls.sst);
+  k_xupd<T, D, FX, DIM, NX><<<grid, ls.thr_upd, sm, st>>>(op, v, px, L, ls.sst);
   return cudaGetLastError();
 }
 
-#define FFTMECH_INST_LINES_TD(T, D, F, DIM)                                                                     \
-  template cudaError_t launch_xdir<T, D, F, DIM>(const Op<T>&, const Vec2<T>&, const FftPlanDev<T>&,          \
-                                                 const LineShape&, cudaStream_t);                             \
-  template cudaError_t launch_xupd<T, D, F, DIM>(const Op<T>&, const Vec2<T>&, const FftPlanDev<T>&,          \
-                                                 const LineShape&, cudaStream_t);
-#define FFTMECH_INST_LINES_T(T, F)      \
-  FFTMECH_INST_LINES_TD(T, 1, F, 2)     \
-  FFTMECH_INST_LINES_TD(T, 2, F, 2)     \
-  FFTMECH_INST_LINES_TD(T, 1, F, 3)     \
-  FFTMECH_INST_LINES_TD(T, 3, F, 3)
+#define FFTMECH_INST_LINES_TD(T, D, F, DIM, NX)                                                                 \
+  template cudaError_t launch_xdir<T, D, F, DIM, NX>(const Op<T>&, const Vec2<T>&, const FftPlanDev<T>&,      \
+                                                     const LineShape&, cudaStream_t);                         \
+  template cudaError_t launch_xupd<T, D, F, DIM, NX>(const Op<T>&, const Vec2<T>&, const FftPlanDev<T>&,      \
+                                                     const LineShape&, cudaStream_t);
+#define FFTMECH_INST_LINES_T(T, F)         \
+  FFTMECH_INST_LINES_TD(T, 1, F, 2, 0)     \
+  FFTMECH_INST_LINES_TD(T, 2, F, 2, 0)     \
+  FFTMECH_INST_LINES_TD(T, 1, F, 3, 0)     \
+  FFTMECH_INST_LINES_TD(T, 3, F, 3, 0)
+// x lines of a compile-time length (float): FX unused
+#define FFTMECH_INST_LINES_FIXED(NX)                  \
+  FFTMECH_INST_LINES_TD(float, 1, FAM_ALL, 2, NX)     \
+  FFTMECH_INST_LINES_TD(float, 2, FAM_ALL, 2, NX)     \
+  FFTMECH_INST_LINES_TD(float, 1, FAM_ALL, 3, NX)     \
+  FFTMECH_INST_LINES_TD(float, 3, FAM_ALL, 3, NX)
 
 }  // namespace fftmech

@@ -114,7 +114,7 @@ template <int K>
 __device__ __forceinline__ bool publish_partials_at(const double (&v)[K], double* partials, int slot,
                                                     int total, unsigned int* counter) {
   __shared__ int am_last;
-  if (threadIdx.x == 0) {
+  if (flat_tid() == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) partials[(size_t)slot * K + k] = v[k];
     __threadfence();
@@ -132,14 +132,14 @@ __device__ __forceinline__ void gather_partials_n(double (&tot)[K], const double
   double v[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = 0.0;
-  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+  for (int b = flat_tid(); b < total; b += flat_nthreads()) {
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] += __ldcg(partials + (size_t)b * K + k);
   }
   block_sum<K>(v, scratch);
 #pragma unroll
   for (int k = 0; k < K; ++k) tot[k] = v[k];
-  if (threadIdx.x == 0) *counter = 0u;
+  if (flat_tid() == 0) *counter = 0u;
 }
 
 }  // namespace fftmech

@@ -128,6 +128,8 @@ def load_library(path=LIB_PATH):
         "fftmech_phasefield_solve": (i, [vp, vp, vp, vp, vp, vp, P(fftmech_solve_info)]),
         "fftmech_staggered_step": (i, [vp, P(fftmech_state), P(fftmech_step_params),
                                        P(fftmech_solve_info)]),
+        "fftmech_staggered_step_many": (i, [P(vp), i, P(P(fftmech_state)), P(P(fftmech_step_params)),
+                                            P(P(fftmech_solve_info))]),
         "fftmech_fft": (i, [i, P(i), i, i, vp, vp]),
         "fftmech_fft_noalloc": (i, [i, P(i), i, i, vp, vp]),
         "fftmech_profile_enable": (i, [vp, i]),
@@ -283,6 +285,21 @@ def fftmech_fft_noalloc(ndim, n, precision, inverse, data, stream=None):
                                             stream)
     _check(rc)
     return rc
+
+
+def fftmech_staggered_step_many(ctxs, states, params, infos=None):
+    """Staggered steps of several contexts concurrently; returns the list of
+    per-context info arrays (3 records per problem)."""
+    n = len(ctxs)
+    infos = infos or [_infos(c, 3) for c in ctxs]
+    c_arr = (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    s_arr = (ctypes.POINTER(fftmech_state) * n)(*[ctypes.pointer(s) for s in states])
+    p_arr = (ctypes.POINTER(fftmech_step_params) * n)(*[ctypes.pointer(p) for p in params])
+    i_arr = (ctypes.POINTER(fftmech_solve_info) * n)(*[ctypes.cast(x, ctypes.POINTER(fftmech_solve_info))
+                                                       for x in infos])
+    rc = load_library().fftmech_staggered_step_many(c_arr, n, s_arr, p_arr, i_arr)
+    _check(rc, None, _SOLVER_OK)
+    return infos
 
 
 def fftmech_profile_enable(ctx, enable):

@@ -8,7 +8,9 @@ Tolerances as in the 2D parity tests: FP64 within 1e-10 relative L2 of the
 oracle (both at a 1e-12 relative residual); mixed within 1e-5 relative L2
 on strain and stress, 1e-6 relative on concentration, 1e-4 max-abs on
 damage. The non-cubic grid (12, 18, 24) has an even nx (the half-spectrum
-column kx = nx/2 counts once) and radix-2 passes along every axis.
+column kx = nx/2 counts once) and radix-2 passes along every axis; the
+(9, 9, 243) and (243, 9, 9) grids put a 243-point axis (compile-time
+transform plans in the mixed path) along x and along z.
 """
 
 import numpy as np
@@ -105,7 +107,7 @@ def test_equilibrium3d_fp64_matches_oracle(shape):
     assert info.elastic_energy == pytest.approx(en, rel=1e-9)
 
 
-@pytest.mark.parametrize("shape", [(27, 27, 27), (12, 18, 24)])
+@pytest.mark.parametrize("shape", [(27, 27, 27), (12, 18, 24), (9, 9, 243), (243, 9, 9)])
 def test_equilibrium3d_mixed_matches_oracle(shape):
     phase, eig, dmg = case3(shape, 22)
     g = phasefield.degradation(dmg, MAT.kappa)

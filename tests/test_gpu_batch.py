@@ -130,3 +130,59 @@ def test_batched_staggered_step_matches_oracle():
         assert rel(strain[b], refs[b]["strain"]) < 1e-9
         assert rel(d[b], refs[b]["d"]) < 1e-9
     assert refs[0]["eig"].max() > 0 and refs[0]["d"].max() > 1e-4
+
+
+def _transient_state(ctx_shape, phases, mat, dt):
+    """Device state of a uniform batch for a transient staggered step."""
+    n = phases[0].size
+    B = len(phases)
+    f64 = torch.float64
+    bufs = {k: torch.zeros(m * n * B, dtype=f64, device="cuda") for k, m in
+            [("c", 1), ("c_ppt", 1), ("eig", 1), ("u", 2), ("strain", 3), ("stress", 3), ("H", 1),
+             ("damage", 1)]}
+    bufs["phase"] = torch.as_tensor(np.concatenate([p.ravel() for p in phases])).cuda()
+    bufs["mask"] = torch.as_tensor(np.concatenate([left_face_mask(p).ravel() for p in phases])).cuda()
+    st = fm.fftmech_state()
+    for k in ("phase", "c", "c_ppt", "eig", "u", "strain", "stress", "H", "damage"):
+        setattr(st, k, bufs[k].data_ptr())
+    p = fm.fftmech_step_params()
+    p.diffusion_mode = fm.FFTMECH_DIFF_TRANSIENT
+    p.dt = dt
+    p.dirichlet_mask = bufs["mask"].data_ptr()
+    p.dirichlet_value = 1.0
+    p.eig_mode = fm.FFTMECH_EIG_FROM_PRECIPITATE
+    return bufs, st, p
+
+
+def test_many_contexts_equal_separate_steps():
+    """Uneven grids (27^2 x 2 and 81^2 x 1) stepped together through
+    fftmech_staggered_step_many give the fields of separate steps."""
+    mat = Materials(E_pore=2e9, M_ppt=2.2)
+    groups = [[random_carpet(27, 0.30, s)[0] for s in (1, 2)], [random_carpet(81, 0.30, 3)[0]]]
+    results = {}
+    for mode in ("many", "separate"):
+        ctxs, states, params, keep = [], [], [], []
+        for phases in groups:
+            n = phases[0].shape[0]
+            ctx = fm.Context(phases[0].shape, mat, fm.FFTMECH_FP64, h=H, h_diff=1.0, tol=1e-12, batch=len(phases))
+            bufs, st, p = _transient_state(phases[0].shape, phases, mat, (n / 4.0) ** 2 / 10)
+            ctxs.append(ctx)
+            states.append(st)
+            params.append(p)
+            keep.append(bufs)
+        for _ in range(2):
+            if mode == "many":
+                infos = fm.fftmech_staggered_step_many([c.handle for c in ctxs], states, params)
+                for inf in infos:
+                    assert all(inf[i].status == fm.FFTMECH_OK for i in range(len(inf)))
+            else:
+                for c, st, p in zip(ctxs, states, params):
+                    inf = fm.fftmech_staggered_step(c.handle, st, p)
+        torch.cuda.synchronize()
+        results[mode] = [{k: b[k].cpu().numpy() for k in ("c", "strain", "damage")} for b in keep]
+        for c in ctxs:
+            c.close()
+    for a, b in zip(results["many"], results["separate"]):
+        for k in a:
+            assert np.array_equal(a[k], b[k])
+    assert results["many"][1]["damage"].max() > 0
