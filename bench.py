@@ -38,6 +38,7 @@ N_SIDE = 729
 SEED = 2305
 TOTAL_STEPS = 200
 L2_FLUSH_BYTES = 512 << 20
+LAUNCH_MODE = 0  # 0: programmatic dependent launches (the library default); 1: plain stream order
 METRIC = "FFT-Galerkin CG voxel-iterations/s"
 UNIT = "voxel-iterations/s"
 
@@ -234,7 +235,8 @@ def run_arm(torch, fm, w, prec, steps, warmup, device, profile=True, flush=None)
     ws = w if isinstance(w, list) else [w]
     w = ws[0]
     ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=w.tol,
-                     max_iter=20000, replace_residual=1, check_every=16, stream=stream.cuda_stream,
+                     max_iter=20000, replace_residual=1, check_every=16, launch_mode=LAUNCH_MODE,
+                     stream=stream.cuda_stream,
                      batch=len(ws))
     bufs, st, p = make_state(torch, fm, ws, prec, device)
     for s in range(warmup):
@@ -285,7 +287,7 @@ def run_many(torch, fm, ws, prec, steps, warmup, device, profile=False, flush=No
     for g in groups:
         w = g[0]
         ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=w.tol, max_iter=20000,
-                         replace_residual=1, check_every=16, batch=len(g))
+                         replace_residual=1, check_every=16, launch_mode=LAUNCH_MODE, batch=len(g))
         bufs, st, p = make_state(torch, fm, g, prec, device)
         ctxs.append(ctx)
         states.append(st)
@@ -336,7 +338,7 @@ def run_e2e(torch, fm, w, prec, steps, warmup, device):
     ws = w if isinstance(w, list) else [w]
     w = ws[0]
     ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=w.tol,
-                     max_iter=20000, replace_residual=1, check_every=16, batch=len(ws))
+                     max_iter=20000, replace_residual=1, check_every=16, launch_mode=LAUNCH_MODE, batch=len(ws))
     bufs, st, p = make_state(torch, fm, ws, prec, device, pinned_host=True)
     for s in range(warmup):
         set_step(p, w, s)
@@ -475,7 +477,8 @@ def mixed_main(args, torch, fm, device, rank, world, dist):
                    "voxels": voxels, "groups": prof_run["groups"], "precision": "mixed", "tol": 1e-8,
                    "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before each timed step",
                    "parallelism": f"{world} independent replicas; one context per grid size, "
-                                  "stepped concurrently (one host thread and stream each)"},
+                                  "stepped concurrently (one host thread and stream each)",
+                   "launches": "plain stream order" if LAUNCH_MODE else "programmatic dependent"},
         "kernels": kernels, "roofline": roofline, "gpu_launches": run["launches"], "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu:
@@ -512,11 +515,16 @@ def main():
                          "729^2 and 64 2x2 carpets of 128^2 .. 1024^2, all stepped together")
     ap.add_argument("--mixed-counts", type=int, nargs=2, default=[256, 64],
                     help="--workload mixed: numbers of 3x3 and 2x2 carpets")
+    ap.add_argument("--plain-launches", action="store_true",
+                    help="launch the PCG kernels in plain stream order instead of as programmatic "
+                         "dependent launches (for comparison)")
     ap.add_argument("--n", type=int, default=None,
                     help="grid side (3^k); defaults 729 (carpet) and 243 (sponge); larger carpet "
                          "sides (2187) give working sets above L2 for profiling")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    global LAUNCH_MODE
+    LAUNCH_MODE = 1 if args.plain_launches else 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -628,7 +636,8 @@ def main():
                    "seed": w.extra.get("seed", SEED), "precision": "mixed", "tol": w.tol,
                    "porosity": w.extra["porosity"], "steps_per_run": w.steps,
                    "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before each timed step",
-                   "parallelism": f"{world} independent RVE replicas"},
+                   "parallelism": f"{world} independent RVE replicas",
+                   "launches": "plain stream order" if LAUNCH_MODE else "programmatic dependent"},
         "breakdown": breakdown,
         "kernels": kernels,
         "roofline": roofline,

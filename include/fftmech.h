@@ -106,12 +106,17 @@ typedef struct {
  * reliable updates; at every host poll (every check_every iterations) the
  * library checks whether r.M^-1 r has fallen 100-fold since the last
  * replacement and, if so, replaces the float recursive residual by the FP64
- * true residual b - K u at the next iteration (search direction kept). */
+ * true residual b - K u at the next iteration (search direction kept).
+ * launch_mode: 0 (default) launches the kernels of a PCG iteration as
+ * programmatic dependent launches (each kernel starts launching while the
+ * previous one finishes and waits on the device for its results); 1 uses
+ * plain stream order. Both give bit-identical results. */
 typedef struct {
   double tol;
   int max_iter;
   int replace_residual;
   int check_every;
+  int launch_mode;
 } fftmech_solver_opts;
 
 /* Per-solve report (host struct). All averages in FP64 over every voxel. */

@@ -14,6 +14,10 @@
 
 using namespace fftmech;
 
+namespace fftmech {
+thread_local int tl_dependent_launch = 0;
+}
+
 namespace {
 
 constexpr int kMaxBlocks = 8192;     // upper bound on reduction partials per launch
@@ -288,6 +292,7 @@ struct Solve {
 template <typename T, int D>
 fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Spec<T>& sp_in,
                        std::vector<Solve>& out) {
+  const DepLaunchScope dep(ctx->opts.launch_mode == 0);
   cudaStream_t st = ctx->stream;
   const int B = ctx->B;
   const Shape2& sh = ctx->shape;
@@ -805,7 +810,8 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
       !(mat->nu_solid > -1) || !(mat->nu_pore > -1) || !(mat->D_solid > 0) || !(mat->D_pore > 0) ||
       !(mat->Gc > 0) || !(mat->l0 > 0) || !(mat->kappa >= 0))
     return FFTMECH_ERR_INVALID_ARG;
-  if (!(opts->tol >= 0) || opts->max_iter < 0) return FFTMECH_ERR_INVALID_ARG;
+  if (!(opts->tol >= 0) || opts->max_iter < 0 || opts->launch_mode < 0 || opts->launch_mode > 1)
+    return FFTMECH_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -975,7 +981,8 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
 
 fftmech_status fftmech_set_solver_opts(fftmech_ctx* ctx, const fftmech_solver_opts* opts) {
   if (!ctx || !opts) return FFTMECH_ERR_INVALID_ARG;
-  if (!(opts->tol >= 0) || opts->max_iter < 0) return FFTMECH_ERR_INVALID_ARG;
+  if (!(opts->tol >= 0) || opts->max_iter < 0 || opts->launch_mode < 0 || opts->launch_mode > 1)
+    return FFTMECH_ERR_INVALID_ARG;
   ctx->opts = *opts;
   if (ctx->opts.check_every <= 0) ctx->opts.check_every = 16;
   return FFTMECH_OK;

@@ -15,6 +15,18 @@
 
 namespace fftmech {
 
+// Programmatic dependent launch: wait until the kernel launched before this
+// one on the stream has completed and its writes are visible, then allow the
+// next kernel of the stream to begin launching (its blocks take free SM slots
+// and run up to their own wait). A kernel launched with the programmatic
+// stream-serialisation attribute must call this in every block before it
+// reads or writes anything another kernel writes or reads, and before it can
+// return; under a plain launch both instructions return at once.
+__device__ __forceinline__ void grid_dep_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename T>
 struct __align__(2 * sizeof(T)) cx {
   T re, im;

@@ -6,9 +6,42 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "fftmech_dev.cuh"
 
 namespace fftmech {
+
+// Launch mode of the calling host thread for the PCG kernels: nonzero =
+// programmatic dependent launches (each kernel's launch and constant
+// prologue overlap the end of the previous kernel on the stream), 0 = plain
+// stream order. The solver sets it for the duration of a solve (DepLaunchScope).
+extern thread_local int tl_dependent_launch;
+
+struct DepLaunchScope {
+  int saved;
+  explicit DepLaunchScope(int on) : saved(tl_dependent_launch) { tl_dependent_launch = on; }
+  ~DepLaunchScope() { tl_dependent_launch = saved; }
+};
+
+// Launch a kernel that calls grid_dep_sync() first in every block (only
+// such kernels may be launched this way), with the programmatic
+// stream-serialisation attribute when the thread's mode asks for it.
+template <typename... KA, typename... A>
+cudaError_t launch_dep(void (*kernel)(KA...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = tl_dependent_launch ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // Scalars of one PCG run, resident in device memory. The last block of a
 // reduction kernel updates them; every iteration kernel reads `done` first.

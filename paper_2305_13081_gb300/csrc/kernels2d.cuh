@@ -32,6 +32,7 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
   const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
+  grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
   const int bp = blockIdx.y;
@@ -214,14 +215,15 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   S += (size_t)bp * nx * ny;
   if (sc) sc += bp;
   if (partials) partials += (size_t)bp * gridDim.x;
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(py.n);
+  const FftPlanDev<T> py_s = plan_to_smem(py, reinterpret_cast<cx<T>*>(smem_all));
+  grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
   if (mode == COL_ITER && pmode && pmode[bp] == 1) mode = COL_TRUE;  // reliable update of this problem
   if (mode == COL_RESTART && !(pmode && pmode[bp] == 2)) return;      // only restarting problems
   if (mode != COL_PLAIN && mode != COL_NORM && mode != COL_TRUENORM && mode != COL_RESTART &&
       done_flag(sc))
     return;
-  extern __shared__ __align__(16) unsigned char smem_all[];
-  unsigned char* smem = smem_all + tw_smem_bytes<T>(py.n);
-  const FftPlanDev<T> py_s = plan_to_smem(py, reinterpret_cast<cx<T>*>(smem_all));
   __shared__ double red[32];
   __shared__ float redf[64];
   cx<T>* B = reinterpret_cast<cx<T>*>(smem);
@@ -284,8 +286,7 @@ cudaError_t launch_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<
   cudaError_t e = set_smem(k_residual<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid((op.ny + R - 1) / R, sh.batch);
-  k_residual<T, D, FX><<<grid, sh.threads_res, sm, st>>>(op, v, px, R, zero_u, filter);
-  return cudaGetLastError();
+  return launch_dep(k_residual<T, D, FX>, grid, dim3(sh.threads_res), sm, st, op, v, px, R, zero_u, filter);
 }
 
 template <typename T, int FY, int NY, int CWC>
@@ -298,9 +299,8 @@ cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, co
   cudaError_t e = set_smem(k_colpass<T, FY, NY, CWC>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid((nx + CW - 1) / CW, sh.batch > 0 ? sh.batch : 1);
-  k_colpass<T, FY, NY, CWC><<<grid, NY > 0 ? kColThreads : sh.threads_col, sm, st>>>(nx, ny, S, py, sp, CW, mode, inverse, partials, sc,
-                                                     pmode);
-  return cudaGetLastError();
+  return launch_dep(k_colpass<T, FY, NY, CWC>, grid, dim3(NY > 0 ? kColThreads : sh.threads_col), sm, st, nx, ny,
+                    S, py, sp, CW, mode, inverse, partials, sc, pmode);
 }
 
 template <typename T, int FX>

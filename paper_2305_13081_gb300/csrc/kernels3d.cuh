@@ -105,6 +105,7 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
   const size_t plane = (size_t)nx * ny;
   const size_t N = plane * nz;
   const int bp = blockIdx.y;
+  grid_dep_sync();
   if (filter && !(v.mode && v.mode[bp] != 0)) return;
   problem_views3<T, D>(op, v, bp, N, sst);
   extern __shared__ __align__(16) unsigned char smem_all[];
@@ -256,11 +257,12 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
                                          int CW, int stage, int mode, double* partials, SolverScalars* sc,
                                          const int* pmode) {
   const int b = blockIdx.y;
-  if (sc && !col_active(mode, pmode ? pmode + b : nullptr, sc + b)) return;
-  if (stage == 1 && mode == COL_ITER && pmode && pmode[b] == 1) mode = COL_TRUE;  // reliable update
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(pl.n);
   const FftPlanDev<T> pl_s = plan_to_smem(pl, reinterpret_cast<cx<T>*>(smem_all));
+  grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
+  if (sc && !col_active(mode, pmode ? pmode + b : nullptr, sc + b)) return;
+  if (stage == 1 && mode == COL_ITER && pmode && pmode[b] == 1) mode = COL_TRUE;  // reliable update
   __shared__ double red[32];
   __shared__ float redf[64];
   cx<T>* B = reinterpret_cast<cx<T>*>(smem);
@@ -369,8 +371,8 @@ cudaError_t launch3_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev
   cudaError_t e = set_smem3(k3_residual<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid(((op.ny + R - 1) / R) * ((op.nz + Z - 1) / Z), sh.batch);
-  k3_residual<T, D, FX><<<grid, sh.thr_res, sm, st>>>(op, v, px, R, Z, sh.sst, zero_u, filter);
-  return cudaGetLastError();
+  return launch_dep(k3_residual<T, D, FX>, grid, dim3(sh.thr_res), sm, st, op, v, px, R, Z, sh.sst, zero_u,
+                    filter);
 }
 
 template <typename T, int FL, int NL, int CWC>
@@ -390,9 +392,8 @@ cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage
   cudaError_t e = set_smem3(k3_lines<T, FL, NL, CWC>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid(nset * ((nxs + CW - 1) / CW), sh.batch);
-  k3_lines<T, FL, NL, CWC><<<grid, NL > 0 ? kLineThreads : thr, sm, st>>>(S, sh.sst, nset, set_stride, nl, line_stride, nxs, pl, sp, CW, stage, mode,
-                                         partials, sc, pmode);
-  return cudaGetLastError();
+  return launch_dep(k3_lines<T, FL, NL, CWC>, grid, dim3(NL > 0 ? kLineThreads : thr), sm, st, S, sh.sst, nset,
+                    set_stride, nl, line_stride, nxs, pl, sp, CW, stage, mode, partials, sc, pmode);
 }
 
 #define FFTMECH_INST3_TD(T, D, F)                                                                    \

@@ -66,10 +66,11 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const size_t N = (size_t)nx * nlines;
   const int bp = blockIdx.y;
   line_views<T, D>(op, v, bp, N, sst);
-  if (done_flag(v.sc)) return;
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
   const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
+  grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
+  if (done_flag(v.sc)) return;
   T b;
   if constexpr (sizeof(T) == 4) b = vol_readf(&v.sc->beta_f);
   else b = vol_read(&v.sc->beta);
@@ -161,6 +162,10 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const int nlines = op.ny * op.nz;
   const size_t N = (size_t)nx * nlines;
   const int bp = blockIdx.y;
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
+  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
+  grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
   const int u_only = v.mode ? (v.mode[bp] == 1) : 0;
   line_views<T, D>(op, v, bp, N, sst);
   if (done_flag(v.sc)) return;
@@ -206,9 +211,6 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
     }
   }
   if (u_only) return;
-  extern __shared__ __align__(16) unsigned char smem_all[];
-  unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
-  const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;
   // residual update and packing, U voxels per thread in flight
@@ -294,8 +296,7 @@ cudaError_t launch_xdir(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& 
   if (e != cudaSuccess) return e;
   const int nlines = op.ny * op.nz;
   const dim3 grid((nlines + L - 1) / L, ls.batch);
-  k_xdir<T, D, FX, DIM, NX><<<grid, ls.thr_dir, sm, st>>>(op, v, px, L, ls.sst);
-  return cudaGetLastError();
+  return launch_dep(k_xdir<T, D, FX, DIM, NX>, grid, dim3(ls.thr_dir), sm, st, op, v, px, L, ls.sst);
 }
 
 template <typename T, int D, int FX, int DIM, int NX>
@@ -308,8 +309,7 @@ cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& 
   if (e != cudaSuccess) return e;
   const int nlines = op.ny * op.nz;
   const dim3 grid((nlines + L - 1) / L, ls.batch);
-  k_xupd<T, D, FX, DIM, NX><<<grid, ls.thr_upd, sm, st>>>(op, v, px, L, ls.sst);
-  return cudaGetLastError();
+  return launch_dep(k_xupd<T, D, FX, DIM, NX>, grid, dim3(ls.thr_upd), sm, st, op, v, px, L, ls.sst);
 }
 
 #define FFTMECH_INST_LINES_TD(T, D, F, DIM, NX)                                                                 \

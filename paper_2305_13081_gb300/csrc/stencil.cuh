@@ -41,6 +41,8 @@ __device__ __forceinline__ void sten_views(Op<T>& op, Vec2<T>& v, int b, size_t 
 // tiles that touch the grid's edge.
 static __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+constexpr int kSten2Rows = 4;  // thread rows of a 2D stencil block
+
 // ---------------------------------------------------------------- 2D
 // Shared memory: [P: D (TY+2)(TX+2)] [SG: 3 (TY+1)(TX+1)] [MG: (TY+1)(TX+1)]
 // [PH: (TY+1)(TX+1) bytes]; P row yy, column xx holds voxel
@@ -54,6 +56,7 @@ __global__ void FFTMECH_BOUNDS_S k_sten2(Op<T> op, Vec2<T> v) {
   const size_t N = (size_t)nx * ny;
   const int bp = blockIdx.y;
   sten_views<T, D>(op, v, bp, N);
+  grid_dep_sync();
   if (done_flag(v.sc)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
@@ -64,7 +67,8 @@ __global__ void FFTMECH_BOUNDS_S k_sten2(Op<T> op, Vec2<T> v) {
   uint8_t* PH = reinterpret_cast<uint8_t*>(MG + SS);
   const T* matg = (D == 2) ? op.g : op.c0f;
   const bool masked = (D == 1) && op.mask;
-  const int tx = threadIdx.x, ty = threadIdx.y, TY4 = blockDim.y;
+  constexpr int TY4 = kSten2Rows;  // thread rows (blockDim.y)
+  const int tx = threadIdx.x, ty = threadIdx.y;
   const T ih = op.ih_t;
   const T lam0 = op.lam_t[0], lam1 = op.lam_t[1], mu0 = op.mu_t[0], mu1 = op.mu_t[1];
   const T kap0 = op.kap_t[0], kap1 = op.kap_t[1];
@@ -83,29 +87,40 @@ __global__ void FFTMECH_BOUNDS_S k_sten2(Op<T> op, Vec2<T> v) {
     const bool hb = tx < 2 && TX + tx < wx + 2;
     const int xb = wrap1(x0 - 1 + TX + tx, nx);
     const bool ha = tx < wx + 2;
-    // load: direction tile with halo, material at the stress positions
-    for (int yy = ty; yy < wy + 2; yy += TY4) {
-      const size_t rowg = (size_t)wrap1(y0 - 1 + yy, ny) * nx;
-      T va[D], vb[D];
+    // load: direction tile with halo, material at the stress positions; all
+    // of this thread's global loads are issued before any shared store
+    constexpr int RI = (TY + 2 + TY4 - 1) / TY4;  // row iterations per thread
+    T va[RI][D], vb[RI][D], ma[RI], mb[RI];
+    uint8_t pa[RI], pb[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+      const int yy = ty + r * TY4;
+      const bool row = yy < wy + 2, srow = yy <= wy;
+      const size_t rowg = (size_t)wrap1(y0 - 1 + (row ? yy : 0), ny) * nx;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        va[c] = ha ? v.p_in[c * N + rowg + xa] : T(0);
-        vb[c] = hb ? v.p_in[c * N + rowg + xb] : T(0);
+        va[r][c] = (row && ha) ? v.p_in[c * N + rowg + xa] : T(0);
+        vb[r][c] = (row && hb) ? v.p_in[c * N + rowg + xb] : T(0);
       }
-      T ma = T(0), mb = T(0);
-      uint8_t pa = 0, pb = 0;
-      if (yy <= wy) {
-        if (ha && tx <= wx) { ma = matg ? matg[rowg + xa] : T(0); pa = op.phase[rowg + xa]; }
-        if (hb && TX + tx <= wx) { mb = matg ? matg[rowg + xb] : T(0); pb = op.phase[rowg + xb]; }
-      }
+      const bool sa = srow && ha && tx <= wx, sb = srow && hb && TX + tx <= wx;
+      ma[r] = (sa && matg) ? matg[rowg + xa] : T(0);
+      pa[r] = sa ? op.phase[rowg + xa] : 0;
+      mb[r] = (sb && matg) ? matg[rowg + xb] : T(0);
+      pb[r] = sb ? op.phase[rowg + xb] : 0;
+    }
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        if (ha) P[c * PS + yy * PW + tx] = va[c];
-        if (hb) P[c * PS + yy * PW + TX + tx] = vb[c];
+    for (int r = 0; r < RI; ++r) {
+      const int yy = ty + r * TY4;
+      if (yy < wy + 2) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          if (ha) P[c * PS + yy * PW + tx] = va[r][c];
+          if (hb) P[c * PS + yy * PW + TX + tx] = vb[r][c];
+        }
       }
       if (yy <= wy) {
-        if (ha && tx <= wx) { MG[yy * SW + tx] = ma; PH[yy * SW + tx] = pa; }
-        if (hb && TX + tx <= wx) { MG[yy * SW + TX + tx] = mb; PH[yy * SW + TX + tx] = pb; }
+        if (ha && tx <= wx) { MG[yy * SW + tx] = ma[r]; PH[yy * SW + tx] = pa[r]; }
+        if (hb && TX + tx <= wx) { MG[yy * SW + TX + tx] = mb[r]; PH[yy * SW + TX + tx] = pb[r]; }
       }
     }
     __syncthreads();
@@ -191,6 +206,7 @@ __global__ void FFTMECH_BOUNDS_S k_sten3(Op<T> op, Vec2<T> v, int Zc) {
   const size_t N = plane * nz;
   const int bp = blockIdx.y;
   sten_views<T, D>(op, v, bp, N);
+  grid_dep_sync();
   if (done_flag(v.sc)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
@@ -376,8 +392,7 @@ cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss,
   if (e != cudaSuccess) return e;
   const int tiles = ((op.nx + kSten2TX - 1) / kSten2TX) * ((op.ny + kSten2TY - 1) / kSten2TY);
   const dim3 grid(ss.grid > 0 ? std::min(ss.grid, tiles) : tiles, ss.batch);
-  k_sten2<T, D, kSten2TX, kSten2TY><<<grid, dim3(kSten2TX, 4), sm, st>>>(op, v);
-  return cudaGetLastError();
+  return launch_dep(k_sten2<T, D, kSten2TX, kSten2TY>, grid, dim3(kSten2TX, kSten2Rows), sm, st, op, v);
 }
 
 template <typename T, int D>
@@ -389,8 +404,7 @@ cudaError_t launch_sten3(const Op<T>& op, const Vec2<T>& v, const StenShape& ss,
   const int bricks = ((op.nx + kSten3TX - 1) / kSten3TX) * ((op.ny + kSten3TY - 1) / kSten3TY) *
                      ((op.nz + ss.zc - 1) / ss.zc);
   const dim3 grid(ss.grid > 0 ? std::min(ss.grid, bricks) : bricks, ss.batch);
-  k_sten3<T, D, kSten3TX, kSten3TY><<<grid, dim3(kSten3TX, kSten3TY), sm, st>>>(op, v, ss.zc);
-  return cudaGetLastError();
+  return launch_dep(k_sten3<T, D, kSten3TX, kSten3TY>, grid, dim3(kSten3TX, kSten3TY), sm, st, op, v, ss.zc);
 }
 
 }  // namespace fftmech

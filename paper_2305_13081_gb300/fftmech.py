@@ -62,7 +62,8 @@ class fftmech_materials(ctypes.Structure):
 
 class fftmech_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("replace_residual", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("replace_residual", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("launch_mode", ctypes.c_int)]
 
 
 class fftmech_solve_info(ctypes.Structure):
@@ -334,12 +335,13 @@ def make_materials(m):
     return out
 
 
-def make_opts(tol=1e-8, max_iter=20000, replace_residual=1, check_every=16):
+def make_opts(tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, launch_mode=0):
     o = fftmech_solver_opts()
     o.tol = tol
     o.max_iter = max_iter
     o.replace_residual = replace_residual
     o.check_every = check_every
+    o.launch_mode = launch_mode
     return o
 
 
@@ -347,13 +349,14 @@ class Context:
     """Owns one fftmech context (create / destroy)."""
 
     def __init__(self, shape, materials, precision=FFTMECH_FP64, h=5e-6, h_diff=1.0,
-                 tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, stream=None, batch=1):
+                 tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, stream=None, batch=1,
+                 launch_mode=0):
         self.shape = tuple(shape)
         self.precision = precision
         self.batch = batch
         self.grid = make_grid(shape, h, h_diff)
         self.mat = make_materials(materials)
-        self.opts = make_opts(tol, max_iter, replace_residual, check_every)
+        self.opts = make_opts(tol, max_iter, replace_residual, check_every, launch_mode)
         if batch == 1:
             self.handle = fftmech_create(self.grid, self.mat, precision, self.opts, stream)
         else:
