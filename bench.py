@@ -39,6 +39,12 @@ SEED = 2305
 TOTAL_STEPS = 200
 L2_FLUSH_BYTES = 512 << 20
 LAUNCH_MODE = 0  # 0: programmatic dependent launches (the library default); 1: plain stream order
+# DRAM bytes (read + write) per launch of a workload's dominant kernel class,
+# from one ncu capture (L2 flushed before the launch) of the kernels as they
+# stand; an entry is removed when its kernel changes.
+NCU_TRAFFIC = {
+    ("random-carpet-729x729-transient-staggered", "column"): 4327424 + 0,  # k_colpass<float, 4, 729, 4>
+}
 METRIC = "FFT-Galerkin CG voxel-iterations/s"
 UNIT = "voxel-iterations/s"
 
@@ -623,7 +629,8 @@ def main():
     if dom:
         a = kernels[dom]["achieved_gbs"]
         roofline = {"kernel": dom, "bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": a / hbm_peak, "peak_source": peak_src, "traffic": None,
+                    "frac": a / hbm_peak, "peak_source": peak_src,
+                    "traffic": NCU_TRAFFIC.get((workload_name(w, args.batch), dom)),
                     "note": ("working set is L2-resident at this size; achieved counts algorithmic bytes"
                              if N * (60 if w.dim == 2 else 100) < (120 << 20) else "achieved counts algorithmic bytes")}
 
