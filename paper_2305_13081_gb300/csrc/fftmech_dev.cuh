@@ -232,6 +232,28 @@ __device__ __forceinline__ void g2s_rows(E* dst, const E* __restrict__ src, int 
   }
 }
 
+// Contiguous global -> shared copy with asynchronous copies (cp.async, no
+// registers held while the data is in flight): element i of src to dst[i].
+// E of 4, 8 or 16 bytes, both arrays aligned to sizeof(E). The copies
+// complete at g2s_async_wait(); a __syncthreads() after it makes them
+// visible to the whole block.
+template <typename E>
+__device__ __forceinline__ void g2s_async(E* dst, const E* src, int n) {
+  static_assert(sizeof(E) == 4 || sizeof(E) == 8 || sizeof(E) == 16, "cp.async copies 4, 8 or 16 bytes");
+  const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned d = base + (unsigned)(i * (int)sizeof(E));
+    const E* s = src + i;
+    if constexpr (sizeof(E) == 16)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(s) : "memory");
+    else if constexpr (sizeof(E) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(s) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(s) : "memory");
+  }
+}
+__device__ __forceinline__ void g2s_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Contiguous shared -> global copy.
 template <typename E>
 __device__ __forceinline__ void s2g(E* __restrict__ dst, const E* __restrict__ src, int n) {

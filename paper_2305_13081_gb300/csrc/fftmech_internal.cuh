@@ -430,7 +430,8 @@ struct Row3Layout {
 template <typename T>
 inline size_t xdir_smem(int nx, int L, int D, int dim) {
   const int nf = (dim == 3 && D == 3) ? 2 : 1;
-  return tw_smem_bytes<T>(nx) + align16((size_t)nf * L * nx * sizeof(cx<T>)) + (size_t)D * L * nx * sizeof(T);
+  return tw_smem_bytes<T>(nx) + align16((size_t)nf * L * nx * sizeof(cx<T>)) +
+         align16((size_t)D * L * nx * sizeof(T)) + (size_t)L * nx;  // + Dirichlet mask bytes
 }
 template <typename T>
 inline size_t xupd_smem(int nx, int L, int D, int dim) {

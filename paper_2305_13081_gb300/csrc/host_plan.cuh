@@ -125,6 +125,8 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   const int tmax = 512;
   const size_t budget = std::min<size_t>(optin, sizeof(T) == 4 ? 100 * 1024 : 110 * 1024);
   const size_t twx = tw_smem_bytes<T>(nx), twy = tw_smem_bytes<T>(ny);
+  // strip buffer, twiddles and the strip's symbol tables
+  auto col_smem = [&](int cw) { return (size_t)ny * cw * sizeof(cx<T>) + twy + (size_t)(ny + cw) * sizeof(T); };
   s = Shape2();
   s.batch = 1;
   s.rows_update = s.rows_dir = 1;  // (row FFT of the bare transform only)
@@ -140,7 +142,7 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
     // 64-byte (or 32-byte for 2187) row segments; 4 columns when the batch
     // has fewer than two 8-column strips per SM
     if (ny >= 1024 || (long long)((nx + 7) / 8) * batch < 2LL * nsm) CW = 4;
-    if ((size_t)ny * CW * sizeof(cx<T>) + twy > optin) return false;
+    if (col_smem(CW) > optin) return false;
     s.cols = CW;
     s.threads_col = 512;
     s.threads_plain = s.threads_update;
@@ -148,8 +150,8 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   }
   // at least two strips per SM (over the batch) when possible
   while (CW > 2 && (long long)((nx + CW - 1) / CW) * batch < 2LL * nsm) CW /= 2;
-  while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) + twy > budget || need_threads(py, CW) > tmax)) CW /= 2;
-  if ((size_t)ny * CW * sizeof(cx<T>) + twy > optin || need_threads(py, CW) > tmax) return false;
+  while (CW > 1 && (col_smem(CW) > budget || need_threads(py, CW) > tmax)) CW /= 2;
+  if (col_smem(CW) > optin || need_threads(py, CW) > tmax) return false;
   s.cols = CW;
   s.threads_col = std::min(tmax, std::max(128, round32(need_threads(py, CW))));
   s.threads_plain = s.threads_update;
@@ -283,8 +285,9 @@ bool choose_shape_fft(const HostPlan& px, const HostPlan& py, int nsm, size_t op
   int CW = sizeof(T) == 4 ? 8 : 4;
   while (CW > 2 && (nx + CW - 1) / CW < 2 * nsm) CW /= 2;
   const size_t twy = tw_smem_bytes<T>(ny);
-  while (CW > 1 && ((size_t)ny * CW * sizeof(cx<T>) + twy > optin || need_threads(py, CW) > tmax)) CW /= 2;
-  if ((size_t)ny * CW * sizeof(cx<T>) + twy > optin || need_threads(py, CW) > tmax) return false;
+  auto col_smem = [&](int cw) { return (size_t)ny * cw * sizeof(cx<T>) + twy + (size_t)(ny + cw) * sizeof(T); };
+  while (CW > 1 && (col_smem(CW) > optin || need_threads(py, CW) > tmax)) CW /= 2;
+  if (col_smem(CW) > optin || need_threads(py, CW) > tmax) return false;
   s.cols = CW;
   s.threads_col = std::min(tmax, std::max(128, round32(need_threads(py, CW))));
   return true;

@@ -143,8 +143,8 @@ __device__ __forceinline__ void col_fft(cx<T>* B, const FftPlanDev<T>& p, int nc
 // One strip of the column pass (see k_colpass).
 template <typename T, int FY, int NY, int CWC>
 __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* S, cx<T>* B, const FftPlanDev<T>& py_s,
-                                              const Spec<T>& sp, int CW, int mode, int inverse, int bp,
-                                              Acc<T>& acc) {
+                                              const Spec<T>& sp, const T* lamx_s, const T* lamy_s, int CW, int mode,
+                                              int inverse, int bp, Acc<T>& acc) {
   const int bd = blockDim.x;
   const int x0 = strip * CW;
   const int nc = min(CW, nx - x0);
@@ -184,7 +184,7 @@ __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* 
     for (int i = threadIdx.x; i < n; i += bd) {
       const int ky = dc.div(i), c = i - ky * ncs;
       if (c >= nc) continue;
-      const T den = m0 + m1 * (sp.lamx[x0 + c] + sp.lamy[ky]);
+      const T den = m0 + m1 * (lamx_s[c] + lamy_s[ky]);
       T m;
       if constexpr (sizeof(T) == 4) m = den > T(0) ? __fdividef(1.0f, den) : T(0);
       else m = den > T(0) ? T(1) / den : T(0);
@@ -218,7 +218,15 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(py.n);
   const FftPlanDev<T> py_s = plan_to_smem(py, reinterpret_cast<cx<T>*>(smem_all));
-  grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
+  // the strip's symbol tables (constant) behind the strip buffer
+  T* LY = reinterpret_cast<T*>(smem + (size_t)ny * CW * sizeof(cx<T>));
+  T* LX = LY + ny;
+  if (sp.lamy) {
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) LY[i] = sp.lamy[i];
+    const int x0 = blockIdx.x * CW;
+    if (threadIdx.x < CW) LX[threadIdx.x] = x0 + (int)threadIdx.x < nx ? sp.lamx[x0 + threadIdx.x] : T(0);
+  }
+  grid_dep_sync();  // plan and tables are constant; everything below follows the previous kernel
   if (mode == COL_ITER && pmode && pmode[bp] == 1) mode = COL_TRUE;  // reliable update of this problem
   if (mode == COL_RESTART && !(pmode && pmode[bp] == 2)) return;      // only restarting problems
   if (mode != COL_PLAIN && mode != COL_NORM && mode != COL_TRUENORM && mode != COL_RESTART &&
@@ -230,7 +238,7 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   // one strip per block (a loop over strips around the transform costs the
   // compiler about twice the registers)
   Acc<T> acc;
-  colpass_strip<T, FY, NY, CWC>(blockIdx.x, nx, ny, S, B, py_s, sp, CW, mode, inverse, bp, acc);
+  colpass_strip<T, FY, NY, CWC>(blockIdx.x, nx, ny, S, B, py_s, sp, LX, LY, CW, mode, inverse, bp, acc);
   if (mode == COL_PLAIN) return;
   const double bt[1] = {acc.block_total(redf, red)};
   if (publish_partials<1>(bt, partials, &sc->cnt[1])) {
@@ -294,7 +302,7 @@ cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, co
                            const Shape2& sh, int mode, int inverse, double* partials,
                            SolverScalars* sc, const int* pmode, cudaStream_t st) {
   const int CW = sh.cols;
-  const size_t sm = (size_t)ny * CW * sizeof(cx<T>) + tw_smem_bytes<T>(ny);
+  const size_t sm = (size_t)ny * CW * sizeof(cx<T>) + tw_smem_bytes<T>(ny) + (size_t)(ny + CW) * sizeof(T);
   static std::atomic<int> cfg{0};
   cudaError_t e = set_smem(k_colpass<T, FY, NY, CWC>, sm, cfg);
   if (e != cudaSuccess) return e;

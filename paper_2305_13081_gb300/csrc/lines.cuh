@@ -57,7 +57,7 @@ __device__ __forceinline__ void line_views(Op<T>& op, Vec2<T>& v, int b, size_t 
 // ---------------------------------------------------------------- direction
 // Lines l0 .. l0 + L - 1 (flattened (z, y) index): z = x-IFFT(S), masked
 // voxels (D = 1) 0, p = z + beta p_old. Shared memory: [twiddles]
-// [F: NF L complex lines] [PO: old direction, D L lines].
+// [F: NF L complex lines] [PO: old direction, D L lines] [MK: L nx mask bytes].
 template <typename T, int D, int FX, int DIM, int NX>
 __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst) {
   using LL = LineLayout<DIM, D>;
@@ -84,8 +84,14 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;  // the half-spectrum field's lines (DIM 3)
   T* PO = reinterpret_cast<T*>(smem + align16((size_t)LL::NF * L * nx * sizeof(cx<T>)));
   const size_t t0 = (size_t)l0 * nx;
+  // the old direction and the 2D spectral rows by asynchronous copies; the
+  // mask and the 3D spectral rows by loads in flight meanwhile; one wait
+  if (with_old) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) g2s_async(PO + (size_t)c * nl * nx, v.p_in + c * N + t0, nl * nx);
+  }
   if constexpr (DIM == 2) {
-    g2s_vec<8, true>(F, v.S + t0, nl * nx);
+    g2s_async(F, v.S + t0, nl * nx);
   } else {
     // the block's spectral rows are one contiguous run of nl nxs numbers:
     // one flattened loop keeps eight loads in flight per thread
@@ -109,10 +115,9 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
       }
     }
   }
-  if (with_old) {
-#pragma unroll
-    for (int c = 0; c < D; ++c) g2s_vec<8, true>(PO + (size_t)c * nl * nx, v.p_in + c * N + t0, nl * nx);
-  }
+  if (D == 1 && op.mask)
+    g2s_vec<8, true>(reinterpret_cast<uint8_t*>(PO) + align16((size_t)D * L * nx * sizeof(T)), op.mask + t0, nl * nx);
+  g2s_async_wait();
   __syncthreads();
   if constexpr (LL::HALF) {
     const int nup = nx - nxh;
@@ -127,6 +132,7 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   if constexpr (NX > 0) fftc<T, 1, NX, false>(F, px_s.tw, LL::NF * nl);
   else fft_lines<T, 1, FX>(F, px_s, LL::NF * nl, nx, 1, false);
   const bool masked = (D == 1) && op.mask;
+  const uint8_t* MK = reinterpret_cast<const uint8_t*>(PO) + align16((size_t)D * L * nx * sizeof(T));
   for (int i = threadIdx.x; i < nl * nx; i += blockDim.x) {
     T z[D];
     if constexpr (DIM == 2) {
@@ -141,7 +147,7 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
         z[0] = FB[i].re;
       }
     }
-    if (masked && op.mask[t0 + i]) z[0] = T(0);
+    if (masked && MK[i]) z[0] = T(0);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       T p = z[c];
@@ -183,73 +189,116 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const size_t t0 = (size_t)l0 * nx;
   const int n = nl * nx;
   const int tid = threadIdx.x, bd = blockDim.x;
-  // iterate update (every mode)
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const T* p = v.p_in + c * N + t0;
-    if constexpr (sizeof(T) == 4) {
-      float* uh = v.uh + c * N + t0;
-      float* ul = v.ul + c * N + t0;
-      for (int i = tid; i < n; i += 2 * bd) {
-        const int i2 = i + bd;
-        float h0 = uh[i], l0v = ul[i];
-        const float p0 = (float)p[i];
-        float h1 = 0.f, l1 = 0.f, p1 = 0.f;
-        if (i2 < n) { h1 = uh[i2]; l1 = ul[i2]; p1 = (float)p[i2]; }
-        df_axpy(h0, l0v, ah, al, p0);
-        uh[i] = h0;
-        ul[i] = l0v;
-        if (i2 < n) {
-          df_axpy(h1, l1, ah, al, p1);
-          uh[i2] = h1;
-          ul[i2] = l1;
-        }
-      }
-    } else {
-      double* u = v.u + c * N + t0;
-      for (int i = tid; i < n; i += bd) u[i] += alpha * (double)p[i];
-    }
-  }
-  if (u_only) return;
   cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;
-  // residual update and packing, U voxels per thread in flight
-  constexpr int U = 4;
-  for (int i0 = tid; i0 < n; i0 += U * bd) {
-    T r[U][D], q[U][D];
+  // iterate update (every mode), residual update and packing (not in a
+  // reliable-update iteration) in one pass: all global loads of U voxels are
+  // issued before any of their stores. Three components at once would keep
+  // fifteen 64-bit addresses live: D = 3 takes one component per pass.
+  if constexpr (D == 3) {
+    constexpr int U3 = 4;
+#pragma unroll 1
+    for (int c = 0; c < D; ++c) {
+      const size_t gc = (size_t)c * N + t0;
+      for (int i0 = tid; i0 < n; i0 += U3 * bd) {
+        T p[U3], r[U3], q[U3];
+        float uh[U3], ul[U3];
+        double ud[U3];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * bd;
-      if (i < n) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          r[u][c] = v.r[c * N + t0 + i];
-          q[u][c] = v.q[c * N + t0 + i];
+        for (int u = 0; u < U3; ++u) {
+          const int i = i0 + u * bd;
+          if (i < n) {
+            p[u] = v.p_in[gc + i];
+            if constexpr (sizeof(T) == 4) {
+              uh[u] = v.uh[gc + i];
+              ul[u] = v.ul[gc + i];
+            } else {
+              ud[u] = v.u[gc + i];
+            }
+            if (!u_only) {
+              r[u] = v.r[gc + i];
+              q[u] = v.q[gc + i];
+            }
+          }
         }
-      }
-    }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * bd;
-      if (i < n) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          r[u][c] -= a * q[u][c];
-          v.r[c * N + t0 + i] = r[u][c];
-        }
-        if constexpr (DIM == 2) {
-          F[i] = mk(r[u][0], D == 2 ? r[u][D - 1] : T(0));
-        } else {
-          if constexpr (D == 3) {
-            F[i] = mk(r[u][0], r[u][1]);
-            FB[i] = mk(r[u][2], T(0));
-          } else {
-            FB[i] = mk(r[u][0], T(0));
+        for (int u = 0; u < U3; ++u) {
+          const int i = i0 + u * bd;
+          if (i < n) {
+            if constexpr (sizeof(T) == 4) {
+              df_axpy(uh[u], ul[u], ah, al, (float)p[u]);
+              v.uh[gc + i] = uh[u];
+              v.ul[gc + i] = ul[u];
+            } else {
+              v.u[gc + i] = ud[u] + alpha * (double)p[u];
+            }
+            if (!u_only) {
+              r[u] -= a * q[u];
+              v.r[gc + i] = r[u];
+              // packed pair (x, y) in F, z in the half-spectrum field FB
+              if (c == 0) F[i].re = r[u];
+              else if (c == 1) F[i].im = r[u];
+              else FB[i] = mk(r[u], T(0));
+            }
           }
         }
       }
     }
+  } else {
+  constexpr int U = D == 1 ? 4 : 2;
+  for (int i0 = tid; i0 < n; i0 += U * bd) {
+    T p[U][D], r[U][D], q[U][D];
+    float uh[U][D], ul[U][D];
+    double ud[U][D];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * bd;
+      if (i < n) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const size_t g = (size_t)c * N + t0 + i;
+          p[u][c] = v.p_in[g];
+          if constexpr (sizeof(T) == 4) {
+            uh[u][c] = v.uh[g];
+            ul[u][c] = v.ul[g];
+          } else {
+            ud[u][c] = v.u[g];
+          }
+          if (!u_only) {
+            r[u][c] = v.r[g];
+            q[u][c] = v.q[g];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * bd;
+      if (i < n) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const size_t g = (size_t)c * N + t0 + i;
+          if constexpr (sizeof(T) == 4) {
+            df_axpy(uh[u][c], ul[u][c], ah, al, (float)p[u][c]);
+            v.uh[g] = uh[u][c];
+            v.ul[g] = ul[u][c];
+          } else {
+            v.u[g] = ud[u][c] + alpha * (double)p[u][c];
+          }
+          if (!u_only) {
+            r[u][c] -= a * q[u][c];
+            v.r[g] = r[u][c];
+          }
+        }
+        if (!u_only) {
+          if constexpr (DIM == 2) F[i] = mk(r[u][0], D == 2 ? r[u][D - 1] : T(0));
+          else FB[i] = mk(r[u][0], T(0));
+        }
+      }
+    }
   }
+  }
+  if (u_only) return;
   __syncthreads();
   if constexpr (NX > 0) fftc<T, -1, NX, false>(F, px_s.tw, LL::NF * nl);
   else fft_lines<T, -1, FX>(F, px_s, LL::NF * nl, nx, 1, false);
