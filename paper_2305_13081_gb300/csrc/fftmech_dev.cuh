@@ -553,6 +553,16 @@ __device__ __forceinline__ double block_sum_df(dfloat v, float* scratch) {
   return (double)v.h + (double)v.l;
 }
 
+// One ticket of a last-block reduction: an atomic increment with
+// acquire-release semantics at GPU scope (it orders the caller's earlier
+// partial stores before the increment, and the last block's later loads
+// of the other blocks' partials after it).
+__device__ __forceinline__ unsigned int ticket_acq_rel(unsigned int* counter) {
+  unsigned int prev;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(counter) : "memory");
+  return prev;
+}
+
 // Publish this block's K partial sums; returns true in every thread of the
 // last block to finish, after which partials of all blocks are visible.
 template <int K>
@@ -562,28 +572,49 @@ __device__ __forceinline__ bool publish_partials(const double (&v)[K], double* p
   if (flat_tid() == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) partials[(size_t)blockIdx.x * K + k] = v[k];
-    __threadfence();
-    const unsigned int prev = atomicAdd(counter, 1u);
+    const unsigned int prev = ticket_acq_rel(counter);
     am_last = (prev == gridDim.x - 1);
   }
   __syncthreads();
   return am_last != 0;
 }
 
+// v[k] = sum of partials[b K + k] over this thread's blocks b = t, t + bd,
+// ... in increasing order (for small K four loads in flight; the additions
+// keep that order, so the result does not depend on the unrolling).
+template <int K>
+__device__ __forceinline__ void sum_partials_ordered(double (&v)[K], const double* partials, int total) {
+  constexpr int UN = K <= 2 ? 4 : 1;
+  const int nt = flat_nthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = 0.0;
+  for (int b0 = flat_tid(); b0 < total; b0 += UN * nt) {
+    double x[UN][K];
+#pragma unroll
+    for (int j = 0; j < UN; ++j) {
+      const int b = b0 + j * nt;
+#pragma unroll
+      for (int k = 0; k < K; ++k) x[j][k] = b < total ? __ldcg(partials + (size_t)b * K + k) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < UN; ++j) {
+      if (b0 + j * nt < total) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += x[j][k];
+      }
+    }
+  }
+}
+
 // In the last block: totals[k] = sum over blocks in index order (thread 0
-// returns them; the counter is reset for the next launch).
+// returns them; the counter is reset for the next launch). The ticket's
+// acquire by thread 0 and the barrier after it order these loads after
+// every block's partial stores.
 template <int K>
 __device__ __forceinline__ void gather_partials(double (&tot)[K], const double* partials,
                                                 unsigned int* counter, double* scratch) {
-  __threadfence();
   double v[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = 0.0;
-  // fixed assignment: thread t sums blocks t, t + bd, ... in order
-  for (int b = flat_tid(); b < (int)gridDim.x; b += flat_nthreads()) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] += __ldcg(partials + (size_t)b * K + k);
-  }
+  sum_partials_ordered<K>(v, partials, (int)gridDim.x);
   block_sum<K>(v, scratch);
 #pragma unroll
   for (int k = 0; k < K; ++k) tot[k] = v[k];

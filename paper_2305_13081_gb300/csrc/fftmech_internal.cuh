@@ -439,11 +439,6 @@ inline size_t xupd_smem(int nx, int L, int D, int dim) {
   return tw_smem_bytes<T>(nx) + (size_t)nf * L * nx * sizeof(cx<T>);
 }
 template <typename T>
-inline size_t sten2_smem(int tx, int ty, int D) {
-  const size_t sgs = (size_t)(ty + 1) * (tx + 1);
-  return ((size_t)D * (ty + 2) * (tx + 2) + 3 * sgs + sgs) * sizeof(T) + sgs;
-}
-template <typename T>
 inline size_t sten3_smem(int tx, int ty, int D) {
   const size_t np = D == 3 ? 3 : 2, nzc = D == 3 ? 3 : 1;
   const size_t sgs = (size_t)(ty + 1) * (tx + 1);

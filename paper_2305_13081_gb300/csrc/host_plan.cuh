@@ -250,8 +250,9 @@ inline void choose_sten_shape(int nx, int ny, int nz, int dim, int nsm, int batc
   s.threads = 256;
   s.grid = std::max(1, (8 * nsm + batch - 1) / batch);  // blocks per problem, looping over tiles
   if (dim == 2) {
-    s.tx = std::min(nx, 64);
-    s.ty = std::min(ny, 16);
+    // warp strips of 31 columns; 16 rows once there are enough strips
+    s.tx = 31;
+    s.ty = (long long)((nx + 30) / 31) * ((ny + 15) / 16) * batch >= 32LL * nsm ? 16 : 8;
     s.zc = 1;
     return;
   }

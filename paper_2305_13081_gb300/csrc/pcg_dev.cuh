@@ -117,8 +117,7 @@ __device__ __forceinline__ bool publish_partials_at(const double (&v)[K], double
   if (flat_tid() == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) partials[(size_t)slot * K + k] = v[k];
-    __threadfence();
-    const unsigned int prev = atomicAdd(counter, 1u);
+    const unsigned int prev = ticket_acq_rel(counter);
     am_last = (prev == (unsigned int)total - 1);
   }
   __syncthreads();
@@ -128,14 +127,8 @@ __device__ __forceinline__ bool publish_partials_at(const double (&v)[K], double
 template <int K>
 __device__ __forceinline__ void gather_partials_n(double (&tot)[K], const double* partials, int total,
                                                   unsigned int* counter, double* scratch) {
-  __threadfence();
   double v[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = 0.0;
-  for (int b = flat_tid(); b < total; b += flat_nthreads()) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] += __ldcg(partials + (size_t)b * K + k);
-  }
+  sum_partials_ordered<K>(v, partials, total);
   block_sum<K>(v, scratch);
 #pragma unroll
   for (int k = 0; k < K; ++k) tot[k] = v[k];

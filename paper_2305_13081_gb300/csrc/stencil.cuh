@@ -4,9 +4,10 @@
 // alpha = <r, M^-1 r> / <p, K p>. K = grad+^T [g C sym grad+] (Eq. solid
 // with the forward-difference gradient of Sec. 2.6) or c0 + grad+^T kap
 // grad+ (Eqs. diffusion-final, crack-fft); masked voxels (Dirichlet) get
-// q = 0. Tiles of TX x TY voxels with a one-voxel halo in shared memory;
-// 3D tiles march through Zc planes keeping two planes of the direction and
-// of the z-differenced stress (or flux) components.
+// q = 0. 2D: warps march down column strips with the stencil's neighbours
+// in registers and shuffles. 3D: tiles of TX x TY voxels with a one-voxel
+// halo in shared memory march through Zc planes keeping two planes of the
+// direction and of the z-differenced stress (or flux) components.
 #pragma once
 
 #include <atomic>
@@ -35,159 +36,150 @@ __device__ __forceinline__ void sten_views(Op<T>& op, Vec2<T>& v, int b, size_t 
   v.sc += b;
 }
 
-// Thread layout: blockDim = (TX, TY4): thread (tx, ty) owns tile column tx
-// (and the two halo columns TX, TX + 1 when tx < 2) and tile rows ty,
-// ty + TY4, ... . Every index is a shift or an add; wrapping happens only on
-// tiles that touch the grid's edge.
+// Wrap an index at most one period outside [0, n).
 static __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-constexpr int kSten2Rows = 4;  // thread rows of a 2D stencil block
-
 // ---------------------------------------------------------------- 2D
-// Shared memory: [P: D (TY+2)(TX+2)] [SG: 3 (TY+1)(TX+1)] [MG: (TY+1)(TX+1)]
-// [PH: (TY+1)(TX+1) bytes]; P row yy, column xx holds voxel
-// (x0 - 1 + xx, y0 - 1 + yy); SG / MG / PH the same origin, one fewer row
-// and column.
-template <typename T, int D, int TX, int TY>
-__global__ void FFTMECH_BOUNDS_S k_sten2(Op<T> op, Vec2<T> v) {
-  constexpr int PW = TX + 2, SW = TX + 1;
-  constexpr size_t PS = (size_t)(TY + 2) * PW, SS = (size_t)(TY + 1) * SW;
+// One warp marches down a strip of kStrip2 = 31 columns: lane l >= 1 owns
+// column x0 + l - 1, lane 0 the halo column x0 - 1; rows y0 - 1 (halo) to
+// y0 + wy - 1. Each lane keeps its column's direction and the stress (flux)
+// of the row above in registers; the left neighbour's stress comes from the
+// lane to the left and the right neighbour's direction from the lane to the
+// right (lane 31 loads it). Loads of the next row are issued before the
+// current row is computed. No shared memory and no barrier inside a strip;
+// warps take strips warp-stride over the grid, one reduction ticket per block.
+constexpr int kStrip2 = 31;
+constexpr int kSten2Threads = 256;
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v, int TY) {
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
   const int bp = blockIdx.y;
   sten_views<T, D>(op, v, bp, N);
   grid_dep_sync();
   if (done_flag(v.sc)) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ float redf[64];
-  T* P = reinterpret_cast<T*>(smem);
-  T* SG = P + D * PS;
-  T* MG = SG + 3 * SS;
-  uint8_t* PH = reinterpret_cast<uint8_t*>(MG + SS);
-  const T* matg = (D == 2) ? op.g : op.c0f;
-  const bool masked = (D == 1) && op.mask;
-  constexpr int TY4 = kSten2Rows;  // thread rows (blockDim.y)
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const T* __restrict__ P = v.p_in;
+  const T* __restrict__ matg = (D == 2) ? op.g : op.c0f;
+  const uint8_t* __restrict__ ph = op.phase;
+  const uint8_t* __restrict__ msk = (D == 1) ? op.mask : nullptr;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
   const T ih = op.ih_t;
   const T lam0 = op.lam_t[0], lam1 = op.lam_t[1], mu0 = op.mu_t[0], mu1 = op.mu_t[1];
   const T kap0 = op.kap_t[0], kap1 = op.kap_t[1];
   const T c0c = op.c0c_t;
-  const int ntx = (nx + TX - 1) / TX;
-  const int ntiles = ntx * ((ny + TY - 1) / TY);
+  const int nsx = (nx + kStrip2 - 1) / kStrip2;
+  const int items = nsx * ((ny + TY - 1) / TY);
   Acc<T> acc;
-  // tiles blockIdx.x, blockIdx.x + gridDim.x, ...: one reduction ticket per block
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    T part = T(0);
-    const int tyi = tile / ntx, txi = tile - tyi * ntx;
-    const int x0 = txi * TX, y0 = tyi * TY;
-    const int wx = min(TX, nx - x0), wy = min(TY, ny - y0);
-    // this thread's columns: xx = tx and, for tx < 2, xx = TX + tx
-    const int xa = wrap1(x0 - 1 + tx, nx);
-    const bool hb = tx < 2 && TX + tx < wx + 2;
-    const int xb = wrap1(x0 - 1 + TX + tx, nx);
-    const bool ha = tx < wx + 2;
-    // load: direction tile with halo, material at the stress positions; all
-    // of this thread's global loads are issued before any shared store
-    constexpr int RI = (TY + 2 + TY4 - 1) / TY4;  // row iterations per thread
-    T va[RI][D], vb[RI][D], ma[RI], mb[RI];
-    uint8_t pa[RI], pb[RI];
-#pragma unroll
-    for (int r = 0; r < RI; ++r) {
-      const int yy = ty + r * TY4;
-      const bool row = yy < wy + 2, srow = yy <= wy;
-      const size_t rowg = (size_t)wrap1(y0 - 1 + (row ? yy : 0), ny) * nx;
+  for (int item = blockIdx.x * nwarps + (int)(threadIdx.x >> 5); item < items; item += gridDim.x * nwarps) {
+    const int sy = item / nsx, sx = item - sy * nsx;
+    const int x0 = sx * kStrip2, y0 = sy * TY;
+    const int wx = min(kStrip2, nx - x0), wy = min(TY, ny - y0);
+    const int x = (x0 - 1 + lane + nx) % nx;  // lane 0: the halo column
+    const int xr = x + 1 == nx ? 0 : x + 1;   // right neighbour (loaded by lane 31)
+    const bool own = lane >= 1 && lane - 1 < wx;
+    int j = (y0 - 1 + ny) % ny;
+    // registers of row j (c) and row j + 1 (n)
+    T pc[D], pn[D], rc[D];
+    T gc = T(0);
+    bool sc = false, mc = false;
+    {
+      const int jn = j + 1 == ny ? 0 : j + 1;
+      const size_t rj = (size_t)j * nx, rn = (size_t)jn * nx;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        va[r][c] = (row && ha) ? v.p_in[c * N + rowg + xa] : T(0);
-        vb[r][c] = (row && hb) ? v.p_in[c * N + rowg + xb] : T(0);
+        pc[c] = P[c * N + rj + x];
+        pn[c] = P[c * N + rn + x];
+        rc[c] = lane == 31 ? P[c * N + rj + xr] : T(0);
       }
-      const bool sa = srow && ha && tx <= wx, sb = srow && hb && TX + tx <= wx;
-      ma[r] = (sa && matg) ? matg[rowg + xa] : T(0);
-      pa[r] = sa ? op.phase[rowg + xa] : 0;
-      mb[r] = (sb && matg) ? matg[rowg + xb] : T(0);
-      pb[r] = sb ? op.phase[rowg + xb] : 0;
+      sc = ph[rj + x] != 0;
+      if (matg) gc = matg[rj + x];
     }
-#pragma unroll
-    for (int r = 0; r < RI; ++r) {
-      const int yy = ty + r * TY4;
-      if (yy < wy + 2) {
+    // stress (flux) of the row above: D = 2 (sxy, syy), D = 1 (Jy)
+    T up0 = T(0), up1 = T(0);
+    T part = T(0);
+    for (int k = 0; k <= wy; ++k) {
+      const int jn = j + 1 == ny ? 0 : j + 1;
+      const int jnn = jn + 1 == ny ? 0 : jn + 1;
+      // next row's loads
+      T pnn[D], rn[D];
+      T gn = T(0);
+      bool sn = false, mn = false;
+      if (k < wy) {
+        const size_t rjn = (size_t)jn * nx, rjnn = (size_t)jnn * nx;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          if (ha) P[c * PS + yy * PW + tx] = va[r][c];
-          if (hb) P[c * PS + yy * PW + TX + tx] = vb[r][c];
+          pnn[c] = P[c * N + rjnn + x];
+          rn[c] = lane == 31 ? P[c * N + rjn + xr] : T(0);
         }
+        sn = ph[rjn + x] != 0;
+        if (matg) gn = matg[rjn + x];
+        if (msk) mn = msk[rjn + x] != 0;
       }
-      if (yy <= wy) {
-        if (ha && tx <= wx) { MG[yy * SW + tx] = ma[r]; PH[yy * SW + tx] = pa[r]; }
-        if (hb && TX + tx <= wx) { MG[yy * SW + TX + tx] = mb[r]; PH[yy * SW + TX + tx] = pb[r]; }
-      }
-    }
-    __syncthreads();
-    // stress / flux at positions (yy, xx), yy <= wy, xx <= wx; energy at the interior
-    for (int yy = ty; yy <= wy; yy += TY4) {
+      // this row: the right neighbour's direction, the stress (flux) at (x, j)
+      T pr[D];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int xx = h == 0 ? tx : TX + tx;
-        if (xx > wx || (h == 1 && tx >= 1)) continue;  // columns 0 .. wx (xx = TX only from tx = 0)
-        const int c = yy * PW + xx, i = yy * SW + xx;
-        const bool sol = PH[i] != 0;
-        const bool inner = xx >= 1 && yy >= 1;
-        if constexpr (D == 2) {
-          const T* Ux = P;
-          const T* Uy = P + PS;
-          const T exx = (Ux[c + 1] - Ux[c]) * ih;
-          const T eyy = (Uy[c + PW] - Uy[c]) * ih;
-          const T exy = T(0.5) * ((Ux[c + PW] - Ux[c]) + (Uy[c + 1] - Uy[c])) * ih;
-          const T gg = matg ? MG[i] : T(1);
-          const T lam = gg * (sol ? lam1 : lam0), mu = gg * (sol ? mu1 : mu0);
-          const T lt = lam * (exx + eyy);
-          const T sxx = lt + T(2) * mu * exx, syy = lt + T(2) * mu * eyy, sxy = T(2) * mu * exy;
-          SG[i] = sxx;
-          SG[SS + i] = syy;
-          SG[2 * SS + i] = sxy;
-          if (inner) part += exx * sxx + eyy * syy + T(2) * exy * sxy;
-        } else {
-          const T p = P[c];
-          const T kap = sol ? kap1 : kap0;
-          const T gx = (P[c + 1] - p) * ih, gy = (P[c + PW] - p) * ih;
-          SG[i] = kap * gx;
-          SG[SS + i] = kap * gy;
-          if (inner) part += (c0c + (matg ? MG[i] : T(0))) * p * p + kap * (gx * gx + gy * gy);
-        }
+      for (int c = 0; c < D; ++c) {
+        const T t = __shfl_down_sync(FULL, pc[c], 1);
+        pr[c] = lane == 31 ? rc[c] : t;
       }
-    }
-    __syncthreads();
-    // q = K p on the tile (rows yr = yy - 1, columns xr = tx)
-    if (tx < wx) {
-      for (int yr = ty; yr < wy; yr += TY4) {
-        const int s = (yr + 1) * SW + (tx + 1);
-        const size_t gi = (size_t)(y0 + yr) * nx + x0 + tx;
-        if constexpr (D == 2) {
-          const T* Sxx = SG;
-          const T* Syy = SG + SS;
-          const T* Sxy = SG + 2 * SS;
-          v.q[gi] = ((Sxx[s - 1] - Sxx[s]) + (Sxy[s - SW] - Sxy[s])) * ih;
-          v.q[N + gi] = ((Sxy[s - 1] - Sxy[s]) + (Syy[s - SW] - Syy[s])) * ih;
-        } else {
-          const T* Jx = SG;
-          const T* Jy = SG + SS;
-          const T p = P[(yr + 1) * PW + tx + 1];
-          T q = (c0c + (matg ? MG[s] : T(0))) * p + ((Jx[s - 1] - Jx[s]) + (Jy[s - SW] - Jy[s])) * ih;
-          if (masked && op.mask[gi]) q = T(0);
+      if constexpr (D == 2) {
+        const T exx = (pr[0] - pc[0]) * ih;
+        const T eyy = (pn[1] - pc[1]) * ih;
+        const T exy = T(0.5) * ((pn[0] - pc[0]) + (pr[1] - pc[1])) * ih;
+        const T gg = matg ? gc : T(1);
+        const T lam = gg * (sc ? lam1 : lam0), mu = gg * (sc ? mu1 : mu0);
+        const T lt = lam * (exx + eyy);
+        const T sxx = lt + T(2) * mu * exx, syy = lt + T(2) * mu * eyy, sxy = T(2) * mu * exy;
+        const T lxx = __shfl_up_sync(FULL, sxx, 1), lxy = __shfl_up_sync(FULL, sxy, 1);
+        if (k >= 1 && own) {
+          const size_t gi = (size_t)j * nx + x;
+          v.q[gi] = ((lxx - sxx) + (up0 - sxy)) * ih;
+          v.q[N + gi] = ((lxy - sxy) + (up1 - syy)) * ih;
+          part += exx * sxx + eyy * syy + T(2) * exy * sxy;
+        }
+        up0 = sxy;
+        up1 = syy;
+      } else {
+        const T p = pc[0];
+        const T kap = sc ? kap1 : kap0;
+        const T gx = (pr[0] - p) * ih, gy = (pn[0] - p) * ih;
+        const T jx = kap * gx, jy = kap * gy;
+        const T ljx = __shfl_up_sync(FULL, jx, 1);
+        if (k >= 1 && own) {
+          const size_t gi = (size_t)j * nx + x;
+          const T c0 = c0c + gc;
+          T q = c0 * p + ((ljx - jx) + (up0 - jy)) * ih;
+          if (mc) q = T(0);
           v.q[gi] = q;
+          part += c0 * p * p + kap * (gx * gx + gy * gy);
         }
+        up0 = jy;
       }
+      // advance one row
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        pc[c] = pn[c];
+        pn[c] = pnn[c];
+        rc[c] = rn[c];
+      }
+      gc = gn;
+      sc = sn;
+      mc = mn;
+      j = jn;
     }
     acc.add(part);
-    __syncthreads();  // the next tile reuses the shared buffers
   }
   const double bt[1] = {acc.block_total(redf, red)};
   double* partials = v.partials + (size_t)bp * gridDim.x;
   if (publish_partials<1>(bt, partials, &v.sc->cnt[0])) {
     double tot[1];
     gather_partials<1>(tot, partials, &v.sc->cnt[0], red);
-    if (threadIdx.x == 0 && threadIdx.y == 0) finalize_direction(v.sc, tot[0]);
+    if (threadIdx.x == 0) finalize_direction(v.sc, tot[0]);
   }
 }
 
@@ -195,7 +187,8 @@ __global__ void FFTMECH_BOUNDS_S k_sten2(Op<T> op, Vec2<T> v) {
 // Shared memory: [P: 2 planes x D (TY+2)(TX+2)] [SP: NP (TY+1)(TX+1)]
 // [SZ: 2 planes x NZ (TY+1)(TX+1)] [MG: (TY+1)(TX+1)] [PH: bytes]; NP
 // in-plane components (sxx, syy, sxy or Jx, Jy), NZ z-differenced ones
-// (sxz, syz, szz or Jz). Thread layout as in 2D with TY4 = TY.
+// (sxz, syz, szz or Jz). blockDim = (TX, TY): thread (tx, ty) owns tile
+// column tx (and the halo columns TX, TX + 1 when tx < 2) and tile row ty.
 template <typename T, int D, int TX, int TY>
 __global__ void FFTMECH_BOUNDS_S k_sten3(Op<T> op, Vec2<T> v, int Zc) {
   constexpr int NP = D == 3 ? 3 : 2, NZ = D == 3 ? 3 : 1;
@@ -381,18 +374,16 @@ static cudaError_t set_smem_s(K kernel, size_t bytes, std::atomic<int>& configur
   return e;
 }
 
-// Tiles: 64 x 16 voxels per 64 x 4 threads (2D); 32 x 8 per 32 x 8 (3D).
-constexpr int kSten2TX = 64, kSten2TY = 16, kSten3TX = 32, kSten3TY = 8;
+// 3D tiles: 32 x 8 voxels per 32 x 8 threads.
+constexpr int kSten3TX = 32, kSten3TY = 8;
 
 template <typename T, int D>
 cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss, cudaStream_t st) {
-  const size_t sm = sten2_smem<T>(kSten2TX, kSten2TY, D);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem_s(k_sten2<T, D, kSten2TX, kSten2TY>, sm, cfg);
-  if (e != cudaSuccess) return e;
-  const int tiles = ((op.nx + kSten2TX - 1) / kSten2TX) * ((op.ny + kSten2TY - 1) / kSten2TY);
-  const dim3 grid(ss.grid > 0 ? std::min(ss.grid, tiles) : tiles, ss.batch);
-  return launch_dep(k_sten2<T, D, kSten2TX, kSten2TY>, grid, dim3(kSten2TX, kSten2Rows), sm, st, op, v);
+  const int items = ((op.nx + kStrip2 - 1) / kStrip2) * ((op.ny + ss.ty - 1) / ss.ty);
+  const int wpb = kSten2Threads / 32;
+  const int blocks = (items + wpb - 1) / wpb;
+  const dim3 grid(ss.grid > 0 ? std::min(ss.grid, blocks) : blocks, ss.batch);
+  return launch_dep(k_sten2<T, D>, grid, dim3(kSten2Threads), 0, st, op, v, ss.ty);
 }
 
 template <typename T, int D>
