@@ -250,9 +250,10 @@ inline void choose_sten_shape(int nx, int ny, int nz, int dim, int nsm, int batc
   s.threads = 256;
   s.grid = std::max(1, (8 * nsm + batch - 1) / batch);  // blocks per problem, looping over tiles
   if (dim == 2) {
-    // warp strips of 31 columns; 16 rows once there are enough strips
-    s.tx = 31;
-    s.ty = (long long)((nx + 30) / 31) * ((ny + 15) / 16) * batch >= 32LL * nsm ? 16 : 8;
+    // warp strips of 30 columns and 8 rows; 4 rows when that gives fewer
+    // than 32 strips per SM (small problems: latency, not bandwidth)
+    s.tx = 30;
+    s.ty = (long long)((nx + 29) / 30) * ((ny + 7) / 8) * batch >= 32LL * nsm ? 8 : 4;
     s.zc = 1;
     return;
   }

@@ -40,19 +40,20 @@ __device__ __forceinline__ void sten_views(Op<T>& op, Vec2<T>& v, int b, size_t 
 static __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // ---------------------------------------------------------------- 2D
-// One warp marches down a strip of kStrip2 = 31 columns: lane l >= 1 owns
-// column x0 + l - 1, lane 0 the halo column x0 - 1; rows y0 - 1 (halo) to
-// y0 + wy - 1. Each lane keeps its column's direction and the stress (flux)
-// of the row above in registers; the left neighbour's stress comes from the
-// lane to the left and the right neighbour's direction from the lane to the
-// right (lane 31 loads it). Loads of the next row are issued before the
-// current row is computed. No shared memory and no barrier inside a strip;
-// warps take strips warp-stride over the grid, one reduction ticket per block.
-constexpr int kStrip2 = 31;
+// One warp takes a strip of kStrip2 = 30 columns and TY rows: lane l holds
+// column x0 + l - 1 (lane 0 the left halo column, lane 31 the right one;
+// lanes 1 .. 30 produce q). The warp first loads every value it needs (the
+// direction on rows y0 - 1 .. y0 + TY, the material on rows y0 - 1 ..
+// y0 + TY - 1) into registers, so a strip costs one memory round trip; then
+// it walks down the rows: the right neighbour's direction and the left
+// neighbour's stress (flux) come from warp shuffles, the row above's stress
+// from the previous step. No shared memory and no barrier; warps take
+// strips warp-stride over the grid, one reduction ticket per block.
+constexpr int kStrip2 = 30;
 constexpr int kSten2Threads = 256;
 
-template <typename T, int D>
-__global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v, int TY) {
+template <typename T, int D, int TY>
+__global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v) {
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
   const int bp = blockIdx.y;
@@ -79,65 +80,45 @@ __global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v, in
     const int sy = item / nsx, sx = item - sy * nsx;
     const int x0 = sx * kStrip2, y0 = sy * TY;
     const int wx = min(kStrip2, nx - x0), wy = min(TY, ny - y0);
-    const int x = (x0 - 1 + lane + nx) % nx;  // lane 0: the halo column
-    const int xr = x + 1 == nx ? 0 : x + 1;   // right neighbour (loaded by lane 31)
-    const bool own = lane >= 1 && lane - 1 < wx;
-    int j = (y0 - 1 + ny) % ny;
-    // registers of row j (c) and row j + 1 (n)
-    T pc[D], pn[D], rc[D];
-    T gc = T(0);
-    bool sc = false, mc = false;
-    {
-      const int jn = j + 1 == ny ? 0 : j + 1;
-      const size_t rj = (size_t)j * nx, rn = (size_t)jn * nx;
+    const int x = (x0 - 1 + lane + nx) % nx;
+    const bool own = lane >= 1 && lane <= kStrip2 && lane - 1 < wx;
+    // row k of the strip is grid row y0 - 1 + k (wrapped)
+    int row[TY + 2];
+    row[0] = (y0 - 1 + ny) % ny;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        pc[c] = P[c * N + rj + x];
-        pn[c] = P[c * N + rn + x];
-        rc[c] = lane == 31 ? P[c * N + rj + xr] : T(0);
+    for (int k = 1; k < TY + 2; ++k) row[k] = row[k - 1] + 1 == ny ? 0 : row[k - 1] + 1;
+    T p[TY + 2][D], g[TY + 1];
+    bool sol[TY + 1], mk[TY + 1];
+#pragma unroll
+    for (int k = 0; k < TY + 2; ++k) {
+      const size_t o = (size_t)row[k] * nx + x;
+#pragma unroll
+      for (int c = 0; c < D; ++c) p[k][c] = P[c * N + o];
+      if (k < TY + 1) {
+        sol[k] = ph[o] != 0;
+        g[k] = matg ? matg[o] : T(0);
+        mk[k] = msk ? msk[o] != 0 : false;
       }
-      sc = ph[rj + x] != 0;
-      if (matg) gc = matg[rj + x];
     }
-    // stress (flux) of the row above: D = 2 (sxy, syy), D = 1 (Jy)
-    T up0 = T(0), up1 = T(0);
+    T up0 = T(0), up1 = T(0);  // the row above: D = 2 (sxy, syy), D = 1 (Jy)
     T part = T(0);
-    for (int k = 0; k <= wy; ++k) {
-      const int jn = j + 1 == ny ? 0 : j + 1;
-      const int jnn = jn + 1 == ny ? 0 : jn + 1;
-      // next row's loads
-      T pnn[D], rn[D];
-      T gn = T(0);
-      bool sn = false, mn = false;
-      if (k < wy) {
-        const size_t rjn = (size_t)jn * nx, rjnn = (size_t)jnn * nx;
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          pnn[c] = P[c * N + rjnn + x];
-          rn[c] = lane == 31 ? P[c * N + rjn + xr] : T(0);
-        }
-        sn = ph[rjn + x] != 0;
-        if (matg) gn = matg[rjn + x];
-        if (msk) mn = msk[rjn + x] != 0;
-      }
-      // this row: the right neighbour's direction, the stress (flux) at (x, j)
+    for (int k = 0; k < TY + 1; ++k) {
+      const bool out = own && k >= 1 && k <= wy;
       T pr[D];
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const T t = __shfl_down_sync(FULL, pc[c], 1);
-        pr[c] = lane == 31 ? rc[c] : t;
-      }
+      for (int c = 0; c < D; ++c) pr[c] = __shfl_down_sync(FULL, p[k][c], 1);
       if constexpr (D == 2) {
-        const T exx = (pr[0] - pc[0]) * ih;
-        const T eyy = (pn[1] - pc[1]) * ih;
-        const T exy = T(0.5) * ((pn[0] - pc[0]) + (pr[1] - pc[1])) * ih;
-        const T gg = matg ? gc : T(1);
-        const T lam = gg * (sc ? lam1 : lam0), mu = gg * (sc ? mu1 : mu0);
+        const T exx = (pr[0] - p[k][0]) * ih;
+        const T eyy = (p[k + 1][1] - p[k][1]) * ih;
+        const T exy = T(0.5) * ((p[k + 1][0] - p[k][0]) + (pr[1] - p[k][1])) * ih;
+        const T gg = matg ? g[k] : T(1);
+        const T lam = gg * (sol[k] ? lam1 : lam0), mu = gg * (sol[k] ? mu1 : mu0);
         const T lt = lam * (exx + eyy);
         const T sxx = lt + T(2) * mu * exx, syy = lt + T(2) * mu * eyy, sxy = T(2) * mu * exy;
         const T lxx = __shfl_up_sync(FULL, sxx, 1), lxy = __shfl_up_sync(FULL, sxy, 1);
-        if (k >= 1 && own) {
-          const size_t gi = (size_t)j * nx + x;
+        if (out) {
+          const size_t gi = (size_t)row[k] * nx + x;
           v.q[gi] = ((lxx - sxx) + (up0 - sxy)) * ih;
           v.q[N + gi] = ((lxy - sxy) + (up1 - syy)) * ih;
           part += exx * sxx + eyy * syy + T(2) * exy * sxy;
@@ -145,32 +126,21 @@ __global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v, in
         up0 = sxy;
         up1 = syy;
       } else {
-        const T p = pc[0];
-        const T kap = sc ? kap1 : kap0;
-        const T gx = (pr[0] - p) * ih, gy = (pn[0] - p) * ih;
+        const T pk = p[k][0];
+        const T kap = sol[k] ? kap1 : kap0;
+        const T gx = (pr[0] - pk) * ih, gy = (p[k + 1][0] - pk) * ih;
         const T jx = kap * gx, jy = kap * gy;
         const T ljx = __shfl_up_sync(FULL, jx, 1);
-        if (k >= 1 && own) {
-          const size_t gi = (size_t)j * nx + x;
-          const T c0 = c0c + gc;
-          T q = c0 * p + ((ljx - jx) + (up0 - jy)) * ih;
-          if (mc) q = T(0);
+        if (out) {
+          const size_t gi = (size_t)row[k] * nx + x;
+          const T c0 = c0c + g[k];
+          T q = c0 * pk + ((ljx - jx) + (up0 - jy)) * ih;
+          if (mk[k]) q = T(0);
           v.q[gi] = q;
-          part += c0 * p * p + kap * (gx * gx + gy * gy);
+          part += c0 * pk * pk + kap * (gx * gx + gy * gy);
         }
         up0 = jy;
       }
-      // advance one row
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        pc[c] = pn[c];
-        pn[c] = pnn[c];
-        rc[c] = rn[c];
-      }
-      gc = gn;
-      sc = sn;
-      mc = mn;
-      j = jn;
     }
     acc.add(part);
   }
@@ -383,7 +353,8 @@ cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss,
   const int wpb = kSten2Threads / 32;
   const int blocks = (items + wpb - 1) / wpb;
   const dim3 grid(ss.grid > 0 ? std::min(ss.grid, blocks) : blocks, ss.batch);
-  return launch_dep(k_sten2<T, D>, grid, dim3(kSten2Threads), 0, st, op, v, ss.ty);
+  if (ss.ty == 4) return launch_dep(k_sten2<T, D, 4>, grid, dim3(kSten2Threads), 0, st, op, v);
+  return launch_dep(k_sten2<T, D, 8>, grid, dim3(kSten2Threads), 0, st, op, v);
 }
 
 template <typename T, int D>
