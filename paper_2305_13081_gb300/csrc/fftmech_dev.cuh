@@ -252,6 +252,19 @@ __device__ __forceinline__ void g2s_async(E* dst, const E* src, int n) {
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(s) : "memory");
   }
 }
+// dst[2 i] = src[i] (one component of interleaved pairs), 4- or 8-byte E.
+template <typename E>
+__device__ __forceinline__ void g2s_async_stride2(E* dst, const E* src, int n) {
+  static_assert(sizeof(E) == 4 || sizeof(E) == 8, "cp.async.ca copies 4 or 8 bytes");
+  const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned d = base + (unsigned)(2 * i * (int)sizeof(E));
+    if constexpr (sizeof(E) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + i) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + i) : "memory");
+  }
+}
 __device__ __forceinline__ void g2s_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Contiguous shared -> global copy.

@@ -188,6 +188,7 @@ struct LineShape {
   long long sst;  // complex numbers per problem in the spectral buffer
   int L_dir, thr_dir;
   int L_upd, thr_upd;
+  int stage_upd;  // 2D update kernel stages all its inputs in shared memory
 };
 struct StenShape {
   int batch;
@@ -437,6 +438,13 @@ template <typename T>
 inline size_t xupd_smem(int nx, int L, int D, int dim) {
   const int nf = (dim == 3 && D == 3) ? 2 : 1;
   return tw_smem_bytes<T>(nx) + (size_t)nf * L * nx * sizeof(cx<T>);
+}
+// 2D update with staged inputs: [twiddles] [F: L nx complex] [Q, P: D L nx
+// T each] [iterate: D L nx double, or hi and lo floats].
+template <typename T>
+inline size_t xupd_stage_smem(int nx, int L, int D) {
+  const size_t n = (size_t)L * nx;
+  return tw_smem_bytes<T>(nx) + align16(n * sizeof(cx<T>)) + 2 * D * n * sizeof(T) + D * n * 8;
 }
 template <typename T>
 inline size_t sten3_smem(int tx, int ty, int D) {

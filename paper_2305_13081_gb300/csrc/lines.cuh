@@ -160,9 +160,10 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
 // ---------------------------------------------------------------- update
 // u += alpha p (double or double-float iterate), r -= alpha q, S = x-FFT(r)
 // on lines l0 .. l0 + L - 1. Reliable-update iterations (mode 1) move the
-// iterate only. Shared memory: [twiddles] [F: NF L complex lines].
+// iterate only. Shared memory: [twiddles] [F: NF L complex lines], and with
+// `stage` (2D) the staged inputs behind F (xupd_stage_smem).
 template <typename T, int D, int FX, int DIM, int NX>
-__global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst) {
+__global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst, int stage) {
   using LL = LineLayout<DIM, D>;
   const int nx = op.nx;
   const int nlines = op.ny * op.nz;
@@ -191,6 +192,55 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const int tid = threadIdx.x, bd = blockDim.x;
   cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;
+  if (DIM == 2 && stage) {
+    // every input of the block by asynchronous copies, one wait: the
+    // residual into the packed rows F (component c at F[i].re / .im), K p,
+    // the direction and the iterate into their own arrays
+    T* Q = reinterpret_cast<T*>(smem + align16((size_t)n * sizeof(cx<T>)));
+    T* PU = Q + (size_t)D * n;
+    float* UH = reinterpret_cast<float*>(PU + (size_t)D * n);
+    float* UL = UH + (size_t)D * n;
+    double* UD = reinterpret_cast<double*>(PU + (size_t)D * n);
+    T* FT = reinterpret_cast<T*>(F);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const size_t gc = (size_t)c * N + t0;
+      g2s_async(PU + (size_t)c * n, v.p_in + gc, n);
+      if constexpr (sizeof(T) == 4) {
+        g2s_async(UH + (size_t)c * n, v.uh + gc, n);
+        g2s_async(UL + (size_t)c * n, v.ul + gc, n);
+      } else {
+        g2s_async(UD + (size_t)c * n, v.u + gc, n);
+      }
+      if (!u_only) {
+        g2s_async(Q + (size_t)c * n, v.q + gc, n);
+        g2s_async_stride2(FT + c, v.r + gc, n);
+      }
+    }
+    g2s_async_wait();
+    __syncthreads();
+    for (int i = tid; i < n; i += bd) {
+      T r[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const size_t g = (size_t)c * N + t0 + i;
+        const T pc = PU[(size_t)c * n + i];
+        if constexpr (sizeof(T) == 4) {
+          float h = UH[(size_t)c * n + i], l = UL[(size_t)c * n + i];
+          df_axpy(h, l, ah, al, (float)pc);
+          v.uh[g] = h;
+          v.ul[g] = l;
+        } else {
+          v.u[g] = UD[(size_t)c * n + i] + alpha * (double)pc;
+        }
+        if (!u_only) {
+          r[c] = FT[2 * (size_t)i + c] - a * Q[(size_t)c * n + i];
+          v.r[g] = r[c];
+        }
+      }
+      if (!u_only) F[i] = mk(r[0], D == 2 ? r[D - 1] : T(0));
+    }
+  } else
   // iterate update (every mode), residual update and packing (not in a
   // reliable-update iteration) in one pass: all global loads of U voxels are
   // issued before any of their stores. Three components at once would keep
@@ -245,58 +295,58 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
       }
     }
   } else {
-  constexpr int U = D == 1 ? 4 : 2;
-  for (int i0 = tid; i0 < n; i0 += U * bd) {
-    T p[U][D], r[U][D], q[U][D];
-    float uh[U][D], ul[U][D];
-    double ud[U][D];
+    constexpr int U = D == 1 ? 4 : 2;
+    for (int i0 = tid; i0 < n; i0 += U * bd) {
+      T p[U][D], r[U][D], q[U][D];
+      float uh[U][D], ul[U][D];
+      double ud[U][D];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * bd;
-      if (i < n) {
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * bd;
+        if (i < n) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          const size_t g = (size_t)c * N + t0 + i;
-          p[u][c] = v.p_in[g];
-          if constexpr (sizeof(T) == 4) {
-            uh[u][c] = v.uh[g];
-            ul[u][c] = v.ul[g];
-          } else {
-            ud[u][c] = v.u[g];
+          for (int c = 0; c < D; ++c) {
+            const size_t g = (size_t)c * N + t0 + i;
+            p[u][c] = v.p_in[g];
+            if constexpr (sizeof(T) == 4) {
+              uh[u][c] = v.uh[g];
+              ul[u][c] = v.ul[g];
+            } else {
+              ud[u][c] = v.u[g];
+            }
+            if (!u_only) {
+              r[u][c] = v.r[g];
+              q[u][c] = v.q[g];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * bd;
+        if (i < n) {
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const size_t g = (size_t)c * N + t0 + i;
+            if constexpr (sizeof(T) == 4) {
+              df_axpy(uh[u][c], ul[u][c], ah, al, (float)p[u][c]);
+              v.uh[g] = uh[u][c];
+              v.ul[g] = ul[u][c];
+            } else {
+              v.u[g] = ud[u][c] + alpha * (double)p[u][c];
+            }
+            if (!u_only) {
+              r[u][c] -= a * q[u][c];
+              v.r[g] = r[u][c];
+            }
           }
           if (!u_only) {
-            r[u][c] = v.r[g];
-            q[u][c] = v.q[g];
+            if constexpr (DIM == 2) F[i] = mk(r[u][0], D == 2 ? r[u][D - 1] : T(0));
+            else FB[i] = mk(r[u][0], T(0));
           }
         }
       }
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * bd;
-      if (i < n) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          const size_t g = (size_t)c * N + t0 + i;
-          if constexpr (sizeof(T) == 4) {
-            df_axpy(uh[u][c], ul[u][c], ah, al, (float)p[u][c]);
-            v.uh[g] = uh[u][c];
-            v.ul[g] = ul[u][c];
-          } else {
-            v.u[g] = ud[u][c] + alpha * (double)p[u][c];
-          }
-          if (!u_only) {
-            r[u][c] -= a * q[u][c];
-            v.r[g] = r[u][c];
-          }
-        }
-        if (!u_only) {
-          if constexpr (DIM == 2) F[i] = mk(r[u][0], D == 2 ? r[u][D - 1] : T(0));
-          else FB[i] = mk(r[u][0], T(0));
-        }
-      }
-    }
-  }
   }
   if (u_only) return;
   __syncthreads();
@@ -352,13 +402,14 @@ template <typename T, int D, int FX, int DIM, int NX>
 cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
                         cudaStream_t st) {
   const int L = ls.L_upd;
-  const size_t sm = xupd_smem<T>(op.nx, L, D, DIM);
+  const int stage = DIM == 2 ? ls.stage_upd : 0;
+  const size_t sm = stage ? xupd_stage_smem<T>(op.nx, L, D) : xupd_smem<T>(op.nx, L, D, DIM);
   static std::atomic<int> cfg{0};
   cudaError_t e = set_smem_l(k_xupd<T, D, FX, DIM, NX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const int nlines = op.ny * op.nz;
   const dim3 grid((nlines + L - 1) / L, ls.batch);
-  return launch_dep(k_xupd<T, D, FX, DIM, NX>, grid, dim3(ls.thr_upd), sm, st, op, v, px, L, ls.sst);
+  return launch_dep(k_xupd<T, D, FX, DIM, NX>, grid, dim3(ls.thr_upd), sm, st, op, v, px, L, ls.sst, stage);
 }
 
 #define FFTMECH_INST_LINES_TD(T, D, F, DIM, NX)                                                                 \
