@@ -110,6 +110,7 @@ struct fftmech_ctx {
   void* wcol3 = nullptr;    // 3D: Parseval weight per spectral column
   void* wcol1 = nullptr;
   double* partials = nullptr;
+  double* partials_col = nullptr;  // 2D column pass (deferred reductions)
   double* results = nullptr;   // 16 per problem
   double* m0b = nullptr;       // per-problem preconditioner constants
   double* m1b = nullptr;
@@ -322,7 +323,7 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
   CK(cudaMemcpyAsync(ctx->sc, ctx->h_sc, sizeof(SolverScalars) * B, cudaMemcpyHostToDevice, st));
   if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
   T* pbuf[2] = {(T*)ctx->p[0], (T*)ctx->p[1]};
-  Vec2<T> v;
+  Vec2<T> v{};
   v.u = u;
   v.uh = ctx->uh;
   v.ul = ctx->ul;
@@ -334,6 +335,12 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
   v.partials = ctx->partials;
   v.sc = ctx->sc;
   v.mode = ctx->mode;
+  // 2D: deferred reductions (the stencil's <p, K p> summed by the update
+  // kernel, the column pass's <r, M^-1 r> by the next direction kernel)
+  const bool defer = ctx->dim == 2;
+  const int ncol_blocks = defer ? (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols : 0;
+  v.pcol = ctx->partials_col;
+  v.nsten = defer ? sten2_blocks(ctx->nx, ctx->ny, ctx->sshape) : 0;
   const long long nU = (long long)D * ctx->N * B;
   const bool mixed = sizeof(T) == 4;
   if (mixed) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_df_split(nU, u, ctx->uh, ctx->ul, st));
@@ -379,7 +386,7 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
   // 2D: one column pass; 3D: y-FFT, z pass (multiplier, <r, M^-1 r>), y-IFFT
   auto colpass = [&](int mode) -> cudaError_t {
     if (!three)
-      return launch_colpass_f<T>(fy, nx, ny, v.S, py, sp, sh, mode, 0, ctx->partials, ctx->sc, ctx->mode, st);
+      return launch_colpass_f<T>(fy, nx, ny, v.S, py, sp, sh, mode, 0, ctx->partials_col, ctx->sc, ctx->mode, st);
     cudaError_t e = launch3_lines_f<T>(fy, v.S, sh3, D, 1, 0, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
     if (e != cudaSuccess) return e;
     e = launch3_lines_f<T>(fz, v.S, sh3, D, 2, 1, pz, sp, mode, ctx->partials, ctx->sc, ctx->mode, st);
@@ -420,6 +427,7 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
     return true;
   };
   bool pending = false;  // some problem has mode 1 queued for the next iteration
+  bool col_deferred = false;  // the last column pass left its reduction to the next direction kernel
   int pi = 0;
   int it = 0;
   for (int restart = 0;; ++restart) {
@@ -427,15 +435,19 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
       Vec2<T> va = v;
       va.p_in = pbuf[pi];
       va.p_out = pbuf[1 - pi];
+      va.ncol = col_deferred ? ncol_blocks : 0;
       FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, direction(va));
       Vec2<T> vb = v;
       vb.p_in = pbuf[1 - pi];
+      vb.defer_rz = col_deferred ? 1 : 0;
       FFTMECH_LAUNCH(FFTMECH_K_STENCIL, stencil(vb));
       FFTMECH_LAUNCH(FFTMECH_K_UPDATE, update(vb));
       const bool replace = pending;
       // reliable update: u += alpha p only (update kernel), then the FP64 true residual
       if (replace) FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 1));
-      FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_ITER));
+      // a replacement iteration finalises at once (the host reads rz_true next)
+      col_deferred = defer && !replace;
+      FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(col_deferred ? (COL_ITER | COL_DEFER) : COL_ITER));
       pi = 1 - pi;
       ++it;
       if (replace) {
@@ -459,6 +471,12 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
           pending = true;
         }
       }
+    }
+    // the iteration limit stopped the loop right after a deferred column pass
+    if (col_deferred) {
+      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_col_finalize(ctx->partials_col, ncol_blocks, ctx->sc, B,
+                                                          1.0 / (double)ctx->N, st));
+      col_deferred = false;
     }
     // FP64 true residual of every iterate
     FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 0));
@@ -920,6 +938,7 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
     alloc(&ctx->wcol1, (size_t)nxs_of(ctx->nx, 1) * es);
   }
   alloc((void**)&ctx->partials, slots * 8);
+  if (!three) alloc((void**)&ctx->partials_col, (size_t)batch * ctx->nx * 8);
   alloc((void**)&ctx->results, (size_t)kResultsPerProblem * batch * 8);
   alloc((void**)&ctx->m0b, (size_t)batch * 8);
   alloc((void**)&ctx->m1b, (size_t)batch * 8);
@@ -956,7 +975,7 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   void* bufs[] = {ctx->r, ctx->q, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
                   ctx->cn, ctx->lamx, ctx->lamy, ctx->lamz, ctx->lamc3, ctx->lamc1, ctx->wcol3, ctx->wcol1,
-                  ctx->partials, ctx->results, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc};
+                  ctx->partials, ctx->partials_col, ctx->results, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < ST_COUNT; ++i)

@@ -252,19 +252,6 @@ __device__ __forceinline__ void g2s_async(E* dst, const E* src, int n) {
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(s) : "memory");
   }
 }
-// dst[2 i] = src[i] (one component of interleaved pairs), 4- or 8-byte E.
-template <typename E>
-__device__ __forceinline__ void g2s_async_stride2(E* dst, const E* src, int n) {
-  static_assert(sizeof(E) == 4 || sizeof(E) == 8, "cp.async.ca copies 4 or 8 bytes");
-  const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const unsigned d = base + (unsigned)(2 * i * (int)sizeof(E));
-    if constexpr (sizeof(E) == 8)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + i) : "memory");
-    else
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + i) : "memory");
-  }
-}
 __device__ __forceinline__ void g2s_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Contiguous shared -> global copy.
@@ -593,11 +580,10 @@ __device__ __forceinline__ bool publish_partials(const double (&v)[K], double* p
 }
 
 // v[k] = sum of partials[b K + k] over this thread's blocks b = t, t + bd,
-// ... in increasing order (for small K four loads in flight; the additions
-// keep that order, so the result does not depend on the unrolling).
-template <int K>
+// ... in increasing order (UN loads in flight; the additions keep that
+// order, so the result does not depend on the unrolling).
+template <int K, int UN = 1>
 __device__ __forceinline__ void sum_partials_ordered(double (&v)[K], const double* partials, int total) {
-  constexpr int UN = K <= 2 ? 4 : 1;
   const int nt = flat_nthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = 0.0;

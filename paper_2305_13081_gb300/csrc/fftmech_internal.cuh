@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "fftmech_dev.cuh"
@@ -54,6 +55,11 @@ struct SolverScalars {
   double rz_true;  // <r, M^-1 r> right after the last true-residual replacement
   int iter, max_iter, done, status;
   unsigned int cnt[4];  // last-block counters: 0 direction, 1 column pass, 2 stats
+  // deferred reductions (2D): <r, M^-1 r> of the last column pass, taken by
+  // the direction kernel's blocks and committed to rz by the update
+  // kernel's block 0; col_true: that column pass followed a reliable update
+  double rz_next;
+  int col_true, pad_i;
   // float copies for the float kernels (no FP64 instruction in their hot
   // path): alpha = alpha_h + alpha_l, beta rounded
   float alpha_h, alpha_l, beta_f, pad_f;
@@ -68,6 +74,9 @@ enum ColMode {
   COL_ITER = 0, COL_NORM = 1, COL_INIT = 2, COL_PLAIN = 3, COL_TRUE = 4, COL_TRUENORM = 5,
   COL_RESTART = 6
 };
+// Flag or-ed into COL_ITER (2D): store one partial per block and leave the
+// finalisation to the next direction kernel (deferred reduction).
+constexpr int COL_DEFER = 16;
 
 // Material / operator description for the row kernels (2D: nz = 1).
 // Vector (D = d, elasticity): K u = grad+^T [g C_omega : sym grad+ u];
@@ -114,6 +123,12 @@ struct Vec2 {
   T* q;           // K p (split iteration), D x N
   double* partials;
   SolverScalars* sc;  // one per problem of the batch
+  // deferred reductions (2D): the column pass's partials and their count
+  // per problem (0: the last column pass finalised itself), the stencil's
+  // partial count per problem (0: the stencil finalised alpha itself), and
+  // whether rz_next holds the residual norm to commit
+  const double* pcol;
+  int ncol, nsten, defer_rz;
   const int* mode;    // per problem: 0 normal, 1 reliable update, 2 restart (NULL = all 0)
 };
 
@@ -188,13 +203,21 @@ struct LineShape {
   long long sst;  // complex numbers per problem in the spectral buffer
   int L_dir, thr_dir;
   int L_upd, thr_upd;
-  int stage_upd;  // 2D update kernel stages all its inputs in shared memory
 };
 struct StenShape {
   int batch;
   int tx, ty, zc, threads;
   int grid;  // blocks per problem (they loop over the tiles)
 };
+
+// Blocks per problem of the 2D stencil (warp strips of 30 columns and s.ty
+// rows, 8 warps a block, at most s.grid blocks).
+inline int sten2_blocks(int nx, int ny, const StenShape& s) {
+  const int items = ((nx + 29) / 30) * ((ny + s.ty - 1) / s.ty);
+  const int blocks = (items + 7) / 8;
+  return s.grid > 0 ? std::min(s.grid, blocks) : blocks;
+}
+
 
 // ---------------------------------------------------------------- launchers
 // Row kernels take the radix family of the x transform (FX), column kernels
@@ -372,6 +395,9 @@ cudaError_t launch_set_masked(long long N, const uint8_t* mask, double value, do
 template <typename T>
 cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t st);
 cudaError_t launch_df_split(long long n, const double* u, float* uh, float* ul, cudaStream_t st);
+// Deferred column-pass finalisation (see k_col_finalize), one block per problem.
+cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc, int batch, double invN,
+                                cudaStream_t st);
 cudaError_t launch_df_merge(long long n, const float* uh, const float* ul, double* u, cudaStream_t st);
 
 // 3D post-processing (post3d.cu): results[b * 13 + k] (6 stress sums, 6
@@ -438,13 +464,6 @@ template <typename T>
 inline size_t xupd_smem(int nx, int L, int D, int dim) {
   const int nf = (dim == 3 && D == 3) ? 2 : 1;
   return tw_smem_bytes<T>(nx) + (size_t)nf * L * nx * sizeof(cx<T>);
-}
-// 2D update with staged inputs: [twiddles] [F: L nx complex] [Q, P: D L nx
-// T each] [iterate: D L nx double, or hi and lo floats].
-template <typename T>
-inline size_t xupd_stage_smem(int nx, int L, int D) {
-  const size_t n = (size_t)L * nx;
-  return tw_smem_bytes<T>(nx) + align16(n * sizeof(cx<T>)) + 2 * D * n * sizeof(T) + D * n * 8;
 }
 template <typename T>
 inline size_t sten3_smem(int tx, int ty, int D) {

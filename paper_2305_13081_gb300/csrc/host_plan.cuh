@@ -241,9 +241,6 @@ bool choose_line_shape(const HostPlan& px, int nlines, int dim, int nxs3, int ns
   if (!s.L_dir || !s.L_upd) return false;
   s.thr_dir = std::min(512, std::max(256, round32(need_threads(px, nf * s.L_dir))));
   s.thr_upd = std::min(512, std::max(256, round32(need_threads(px, nf * s.L_upd))));
-  // 2D: stage every input of the update kernel with asynchronous copies
-  // (one memory round trip per block) when that fits in 100 KB
-  s.stage_upd = dim == 2 && xupd_stage_smem<T>(nx, s.L_upd, 2) <= std::min<size_t>(optin, 100 * 1024) ? 1 : 0;
   return true;
 }
 

@@ -209,8 +209,9 @@ __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* 
 
 template <typename T, int FY, int NY, int CWC>
 __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev<T> py, Spec<T> sp, int CW,
-                                            int mode, int inverse, double* partials, SolverScalars* sc,
+                                            int mode_arg, int inverse, double* partials, SolverScalars* sc,
                                             const int* pmode) {
+  int mode = mode_arg & ~COL_DEFER;
   const int bp = blockIdx.y;
   S += (size_t)bp * nx * ny;
   if (sc) sc += bp;
@@ -241,6 +242,13 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   colpass_strip<T, FY, NY, CWC>(blockIdx.x, nx, ny, S, B, py_s, sp, LX, LY, CW, mode, inverse, bp, acc);
   if (mode == COL_PLAIN) return;
   const double bt[1] = {acc.block_total(redf, red)};
+  if ((mode_arg & COL_DEFER) && (mode == COL_ITER || mode == COL_TRUE)) {  // finalised by the next direction kernel
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = bt[0];
+      if (blockIdx.x == 0) sc->col_true = mode == COL_TRUE;
+    }
+    return;
+  }
   if (publish_partials<1>(bt, partials, &sc->cnt[1])) {
     double tot[1];
     gather_partials<1>(tot, partials, &sc->cnt[1], red);

@@ -72,8 +72,49 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
   if (done_flag(v.sc)) return;
   T b;
-  if constexpr (sizeof(T) == 4) b = vol_readf(&v.sc->beta_f);
-  else b = vol_read(&v.sc->beta);
+  if (v.ncol > 0) {
+    // deferred reduction of the last column pass (an ITER or TRUE pass):
+    // <r, M^-1 r>, convergence and beta in every block; block 0 writes the
+    // scalars that nothing in this kernel reads (rz_next, rz_true, beta; rz
+    // and iter only when the problem stops here)
+    __shared__ double redx[32];
+    SolverScalars* s = v.sc;
+    const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
+    const double tot = block_total_partials(v.pcol + (size_t)bp * v.ncol, v.ncol, redx) * (1.0 / (double)N);
+    const int is_true = vol_readi(&s->col_true);
+    if (!isfinite(tot)) {
+      if (b0) {
+        s->rz = tot;
+        s->done = 1;
+        s->status = FFTMECH_ERR_NONFINITE;
+      }
+      return;
+    }
+    if (tot <= s->tol2 * s->rz0) {
+      if (b0) {
+        s->iter += 1;
+        if (is_true) s->rz_true = tot;
+        s->rz = tot;
+        s->done = 1;
+        s->status = FFTMECH_OK;
+      }
+      return;
+    }
+    double beta = tot / vol_read(&s->rz);
+    // a replaced residual larger than the recursive one it replaces means the
+    // float recursion had drifted: restart the direction instead of mixing
+    if (is_true && beta > 1.0) beta = 0.0;
+    if (b0) {
+      s->rz_next = tot;
+      if (is_true) s->rz_true = tot;
+      set_beta(s, beta);
+    }
+    b = (T)beta;
+  } else if constexpr (sizeof(T) == 4) {
+    b = vol_readf(&v.sc->beta_f);
+  } else {
+    b = vol_read(&v.sc->beta);
+  }
   const bool with_old = b != T(0);  // the first iteration has p = z
   const int l0 = blockIdx.x * L;
   const int nl = min(L, nlines - l0);
@@ -160,10 +201,9 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
 // ---------------------------------------------------------------- update
 // u += alpha p (double or double-float iterate), r -= alpha q, S = x-FFT(r)
 // on lines l0 .. l0 + L - 1. Reliable-update iterations (mode 1) move the
-// iterate only. Shared memory: [twiddles] [F: NF L complex lines], and with
-// `stage` (2D) the staged inputs behind F (xupd_stage_smem).
+// iterate only. Shared memory: [twiddles] [F: NF L complex lines].
 template <typename T, int D, int FX, int DIM, int NX>
-__global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst, int stage) {
+__global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst) {
   using LL = LineLayout<DIM, D>;
   const int nx = op.nx;
   const int nlines = op.ny * op.nz;
@@ -178,7 +218,35 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   if (done_flag(v.sc)) return;
   double alpha = 0.0;
   float ah = 0.f, al = 0.f;
-  if constexpr (sizeof(T) == 4) {
+  if (v.nsten > 0) {
+    // deferred reduction: <p, K p> from the stencil's partials, alpha =
+    // <r, M^-1 r> / <p, K p> in every block; block 0 writes the scalars
+    __shared__ double redx[32];
+    const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
+    const double pq = block_total_partials(v.partials + (size_t)bp * v.nsten, v.nsten, redx);
+    const double rz = v.defer_rz ? vol_read(&v.sc->rz_next) : vol_read(&v.sc->rz);
+    if (b0 && v.defer_rz) {
+      v.sc->rz = rz;
+      v.sc->iter += 1;
+    }
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      if (b0) {
+        v.sc->pq = pq;
+        v.sc->done = 1;
+        v.sc->status = FFTMECH_ERR_NONFINITE;
+      }
+      return;
+    }
+    alpha = rz / pq;
+    ah = (float)alpha;
+    al = (float)(alpha - (double)ah);
+    if (b0) {
+      v.sc->pq = pq;
+      v.sc->alpha = alpha;
+      v.sc->alpha_h = ah;
+      v.sc->alpha_l = al;
+    }
+  } else if constexpr (sizeof(T) == 4) {
     ah = vol_readf(&v.sc->alpha_h);
     al = vol_readf(&v.sc->alpha_l);
   } else {
@@ -192,55 +260,6 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const int tid = threadIdx.x, bd = blockDim.x;
   cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;
-  if (DIM == 2 && stage) {
-    // every input of the block by asynchronous copies, one wait: the
-    // residual into the packed rows F (component c at F[i].re / .im), K p,
-    // the direction and the iterate into their own arrays
-    T* Q = reinterpret_cast<T*>(smem + align16((size_t)n * sizeof(cx<T>)));
-    T* PU = Q + (size_t)D * n;
-    float* UH = reinterpret_cast<float*>(PU + (size_t)D * n);
-    float* UL = UH + (size_t)D * n;
-    double* UD = reinterpret_cast<double*>(PU + (size_t)D * n);
-    T* FT = reinterpret_cast<T*>(F);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const size_t gc = (size_t)c * N + t0;
-      g2s_async(PU + (size_t)c * n, v.p_in + gc, n);
-      if constexpr (sizeof(T) == 4) {
-        g2s_async(UH + (size_t)c * n, v.uh + gc, n);
-        g2s_async(UL + (size_t)c * n, v.ul + gc, n);
-      } else {
-        g2s_async(UD + (size_t)c * n, v.u + gc, n);
-      }
-      if (!u_only) {
-        g2s_async(Q + (size_t)c * n, v.q + gc, n);
-        g2s_async_stride2(FT + c, v.r + gc, n);
-      }
-    }
-    g2s_async_wait();
-    __syncthreads();
-    for (int i = tid; i < n; i += bd) {
-      T r[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const size_t g = (size_t)c * N + t0 + i;
-        const T pc = PU[(size_t)c * n + i];
-        if constexpr (sizeof(T) == 4) {
-          float h = UH[(size_t)c * n + i], l = UL[(size_t)c * n + i];
-          df_axpy(h, l, ah, al, (float)pc);
-          v.uh[g] = h;
-          v.ul[g] = l;
-        } else {
-          v.u[g] = UD[(size_t)c * n + i] + alpha * (double)pc;
-        }
-        if (!u_only) {
-          r[c] = FT[2 * (size_t)i + c] - a * Q[(size_t)c * n + i];
-          v.r[g] = r[c];
-        }
-      }
-      if (!u_only) F[i] = mk(r[0], D == 2 ? r[D - 1] : T(0));
-    }
-  } else
   // iterate update (every mode), residual update and packing (not in a
   // reliable-update iteration) in one pass: all global loads of U voxels are
   // issued before any of their stores. Three components at once would keep
@@ -402,14 +421,13 @@ template <typename T, int D, int FX, int DIM, int NX>
 cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
                         cudaStream_t st) {
   const int L = ls.L_upd;
-  const int stage = DIM == 2 ? ls.stage_upd : 0;
-  const size_t sm = stage ? xupd_stage_smem<T>(op.nx, L, D) : xupd_smem<T>(op.nx, L, D, DIM);
+  const size_t sm = xupd_smem<T>(op.nx, L, D, DIM);
   static std::atomic<int> cfg{0};
   cudaError_t e = set_smem_l(k_xupd<T, D, FX, DIM, NX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const int nlines = op.ny * op.nz;
   const dim3 grid((nlines + L - 1) / L, ls.batch);
-  return launch_dep(k_xupd<T, D, FX, DIM, NX>, grid, dim3(ls.thr_upd), sm, st, op, v, px, L, ls.sst, stage);
+  return launch_dep(k_xupd<T, D, FX, DIM, NX>, grid, dim3(ls.thr_upd), sm, st, op, v, px, L, ls.sst);
 }
 
 #define FFTMECH_INST_LINES_TD(T, D, F, DIM, NX)                                                                 \

@@ -79,6 +79,23 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
   set_beta(sc, beta);
 }
 
+// Deferred reductions (2D): a producer kernel stores one partial per block
+// and takes no ticket; every block of the consuming kernel sums the
+// partials itself, in the fixed order of sum_partials_ordered and
+// block_sum, so that all blocks obtain the same total (returned in every
+// thread). The kernel boundary orders the partial stores before these loads.
+static __device__ double block_total_partials(const double* partials, int n, double* scratch) {
+  __shared__ double tot_s;
+  double v[1];
+  sum_partials_ordered<1, 4>(v, partials, n);
+  block_sum<1>(v, scratch);
+  if (flat_tid() == 0) tot_s = v[0];
+  __syncthreads();
+  return tot_s;
+}
+
+static __device__ __forceinline__ int vol_readi(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
 // Per-thread accumulator of a block reduction: double-float for float
 // kernels (no FP64 instruction), double for the FP64 path.
 template <typename T>

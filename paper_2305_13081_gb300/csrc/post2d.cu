@@ -1,6 +1,7 @@
 // Pointwise physics and FP64 post-processing reductions (2D).
 #include "fftmech_internal.cuh"
 #include "fftmech.h"
+#include "pcg_dev.cuh"
 
 namespace fftmech {
 
@@ -363,5 +364,22 @@ cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t 
 
 FFTMECH_POST_INST(float)
 FFTMECH_POST_INST(double)
+
+// Finalise a deferred column pass that no direction kernel followed (the
+// solve stopped at its iteration limit): one block per problem.
+static __global__ void __launch_bounds__(256) k_col_finalize(const double* pcol, int ncol, SolverScalars* sc,
+                                                             double invN) {
+  __shared__ double red[32];
+  sc += blockIdx.x;
+  if (done_flag(sc)) return;
+  const double tot = block_total_partials(pcol + (size_t)blockIdx.x * ncol, ncol, red);
+  if (threadIdx.x == 0) finalize_col(sc, vol_readi(&sc->col_true) ? COL_TRUE : COL_ITER, tot * invN);
+}
+
+cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc, int batch, double invN,
+                                cudaStream_t st) {
+  k_col_finalize<<<batch, 256, 0, st>>>(pcol, ncol, sc, invN);
+  return cudaGetLastError();
+}
 
 }  // namespace fftmech

@@ -146,6 +146,10 @@ __global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v) {
   }
   const double bt[1] = {acc.block_total(redf, red)};
   double* partials = v.partials + (size_t)bp * gridDim.x;
+  if (v.nsten > 0) {  // deferred: the update kernel's blocks sum the partials
+    if (threadIdx.x == 0) partials[blockIdx.x] = bt[0];
+    return;
+  }
   if (publish_partials<1>(bt, partials, &v.sc->cnt[0])) {
     double tot[1];
     gather_partials<1>(tot, partials, &v.sc->cnt[0], red);
@@ -349,10 +353,8 @@ constexpr int kSten3TX = 32, kSten3TY = 8;
 
 template <typename T, int D>
 cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss, cudaStream_t st) {
-  const int items = ((op.nx + kStrip2 - 1) / kStrip2) * ((op.ny + ss.ty - 1) / ss.ty);
-  const int wpb = kSten2Threads / 32;
-  const int blocks = (items + wpb - 1) / wpb;
-  const dim3 grid(ss.grid > 0 ? std::min(ss.grid, blocks) : blocks, ss.batch);
+  static_assert(kStrip2 == 30 && kSten2Threads == 256, "sten2_blocks assumes 30-column strips, 8 warps");
+  const dim3 grid(sten2_blocks(op.nx, op.ny, ss), ss.batch);
   if (ss.ty == 4) return launch_dep(k_sten2<T, D, 4>, grid, dim3(kSten2Threads), 0, st, op, v);
   return launch_dep(k_sten2<T, D, 8>, grid, dim3(kSten2Threads), 0, st, op, v);
 }
