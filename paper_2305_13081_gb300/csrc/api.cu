@@ -475,7 +475,7 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
     // the iteration limit stopped the loop right after a deferred column pass
     if (col_deferred) {
       FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_col_finalize(ctx->partials_col, ncol_blocks, ctx->sc, B,
-                                                          1.0 / (double)ctx->N, st));
+                                                          1.0 / (double)ctx->N, mixed ? 1 : 0, st));
       col_deferred = false;
     }
     // FP64 true residual of every iterate

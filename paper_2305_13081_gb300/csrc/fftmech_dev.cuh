@@ -524,9 +524,9 @@ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
   const float h2 = s + l;
   return dfloat{h2, l - (h2 - s)};
 }
-// Block sum of double-float values, returned as double in thread 0 (others
-// get a partial). scratch: 64 floats of shared memory.
-__device__ __forceinline__ double block_sum_df(dfloat v, float* scratch) {
+// Block sum of double-float values, returned in thread 0 (others get a
+// partial). scratch: 64 floats of shared memory.
+__device__ __forceinline__ dfloat block_sum_df2(dfloat v, float* scratch) {
   const int tid = flat_tid();
   const int lane = tid & 31, wid = tid >> 5;
   const int nw = (flat_nthreads() + 31) >> 5;
@@ -550,7 +550,11 @@ __device__ __forceinline__ double block_sum_df(dfloat v, float* scratch) {
     }
   }
   __syncthreads();
-  return (double)v.h + (double)v.l;
+  return v;
+}
+__device__ __forceinline__ double block_sum_df(dfloat v, float* scratch) {
+  const dfloat t = block_sum_df2(v, scratch);
+  return (double)t.h + (double)t.l;
 }
 
 // One ticket of a last-block reduction: an atomic increment with

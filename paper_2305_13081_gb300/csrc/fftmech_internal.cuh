@@ -396,7 +396,7 @@ template <typename T>
 cudaError_t launch_to_real(long long N, const double* src, T* dst, cudaStream_t st);
 cudaError_t launch_df_split(long long n, const double* u, float* uh, float* ul, cudaStream_t st);
 // Deferred column-pass finalisation (see k_col_finalize), one block per problem.
-cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc, int batch, double invN,
+cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc, int batch, double invN, int fp32,
                                 cudaStream_t st);
 cudaError_t launch_df_merge(long long n, const float* uh, const float* ul, double* u, cudaStream_t st);
 

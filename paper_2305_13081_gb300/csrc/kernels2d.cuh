@@ -241,14 +241,12 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   Acc<T> acc;
   colpass_strip<T, FY, NY, CWC>(blockIdx.x, nx, ny, S, B, py_s, sp, LX, LY, CW, mode, inverse, bp, acc);
   if (mode == COL_PLAIN) return;
-  const double bt[1] = {acc.block_total(redf, red)};
   if ((mode_arg & COL_DEFER) && (mode == COL_ITER || mode == COL_TRUE)) {  // finalised by the next direction kernel
-    if (threadIdx.x == 0) {
-      partials[blockIdx.x] = bt[0];
-      if (blockIdx.x == 0) sc->col_true = mode == COL_TRUE;
-    }
+    store_deferred_partial<T>(acc, partials + blockIdx.x, redf, red);
+    if (threadIdx.x == 0 && blockIdx.x == 0) sc->col_true = mode == COL_TRUE;
     return;
   }
+  const double bt[1] = {acc.block_total(redf, red)};
   if (publish_partials<1>(bt, partials, &sc->cnt[1])) {
     double tot[1];
     gather_partials<1>(tot, partials, &sc->cnt[1], red);

@@ -77,39 +77,49 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
     // <r, M^-1 r>, convergence and beta in every block; block 0 writes the
     // scalars that nothing in this kernel reads (rz_next, rz_true, beta; rz
     // and iter only when the problem stops here)
+    // (the decisions in thread 0 only: FP64 runs at a small fraction of FP32)
+    __shared__ float redfx[64];
     __shared__ double redx[32];
+    __shared__ T b_s;
+    __shared__ int stop_s;
     SolverScalars* s = v.sc;
-    const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
-    const double tot = block_total_partials(v.pcol + (size_t)bp * v.ncol, v.ncol, redx) * (1.0 / (double)N);
-    const int is_true = vol_readi(&s->col_true);
-    if (!isfinite(tot)) {
-      if (b0) {
-        s->rz = tot;
-        s->done = 1;
-        s->status = FFTMECH_ERR_NONFINITE;
+    const double tsum = deferred_total<T>(v.pcol + (size_t)bp * v.ncol, v.ncol, redfx, redx);
+    if (threadIdx.x == 0) {
+      const bool w0 = blockIdx.x == 0;
+      const double tot = tsum * (1.0 / (double)N);
+      const int is_true = vol_readi(&s->col_true);
+      stop_s = 1;
+      if (!isfinite(tot)) {
+        if (w0) {
+          s->rz = tot;
+          s->done = 1;
+          s->status = FFTMECH_ERR_NONFINITE;
+        }
+      } else if (tot <= s->tol2 * s->rz0) {
+        if (w0) {
+          s->iter += 1;
+          if (is_true) s->rz_true = tot;
+          s->rz = tot;
+          s->done = 1;
+          s->status = FFTMECH_OK;
+        }
+      } else {
+        double beta = tot / vol_read(&s->rz);
+        // a replaced residual larger than the recursive one it replaces means
+        // the float recursion had drifted: restart the direction instead
+        if (is_true && beta > 1.0) beta = 0.0;
+        if (w0) {
+          s->rz_next = tot;
+          if (is_true) s->rz_true = tot;
+          set_beta(s, beta);
+        }
+        b_s = (T)beta;
+        stop_s = 0;
       }
-      return;
     }
-    if (tot <= s->tol2 * s->rz0) {
-      if (b0) {
-        s->iter += 1;
-        if (is_true) s->rz_true = tot;
-        s->rz = tot;
-        s->done = 1;
-        s->status = FFTMECH_OK;
-      }
-      return;
-    }
-    double beta = tot / vol_read(&s->rz);
-    // a replaced residual larger than the recursive one it replaces means the
-    // float recursion had drifted: restart the direction instead of mixing
-    if (is_true && beta > 1.0) beta = 0.0;
-    if (b0) {
-      s->rz_next = tot;
-      if (is_true) s->rz_true = tot;
-      set_beta(s, beta);
-    }
-    b = (T)beta;
+    __syncthreads();
+    if (stop_s) return;
+    b = b_s;
   } else if constexpr (sizeof(T) == 4) {
     b = vol_readf(&v.sc->beta_f);
   } else {
@@ -221,30 +231,49 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   if (v.nsten > 0) {
     // deferred reduction: <p, K p> from the stencil's partials, alpha =
     // <r, M^-1 r> / <p, K p> in every block; block 0 writes the scalars
+    // (the decisions in thread 0 only: FP64 runs at a small fraction of FP32)
+    __shared__ float redfx[64];
     __shared__ double redx[32];
-    const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
-    const double pq = block_total_partials(v.partials + (size_t)bp * v.nsten, v.nsten, redx);
-    const double rz = v.defer_rz ? vol_read(&v.sc->rz_next) : vol_read(&v.sc->rz);
-    if (b0 && v.defer_rz) {
-      v.sc->rz = rz;
-      v.sc->iter += 1;
-    }
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      if (b0) {
-        v.sc->pq = pq;
-        v.sc->done = 1;
-        v.sc->status = FFTMECH_ERR_NONFINITE;
+    __shared__ double a_s;
+    __shared__ float ah_s, al_s;
+    __shared__ int stop_s;
+    const double pq = deferred_total<T>(v.partials + (size_t)bp * v.nsten, v.nsten, redfx, redx);
+    if (threadIdx.x == 0) {
+      SolverScalars* s = v.sc;
+      const bool w0 = blockIdx.x == 0;
+      const double rz = v.defer_rz ? vol_read(&s->rz_next) : vol_read(&s->rz);
+      if (w0 && v.defer_rz) {
+        s->rz = rz;
+        s->iter += 1;
       }
-      return;
+      stop_s = !(pq > 0.0) || !isfinite(pq);
+      if (stop_s) {
+        if (w0) {
+          s->pq = pq;
+          s->done = 1;
+          s->status = FFTMECH_ERR_NONFINITE;
+        }
+      } else {
+        const double a0 = rz / pq;
+        const float h = (float)a0;
+        a_s = a0;
+        ah_s = h;
+        al_s = (float)(a0 - (double)h);
+        if (w0) {
+          s->pq = pq;
+          s->alpha = a0;
+          s->alpha_h = ah_s;
+          s->alpha_l = al_s;
+        }
+      }
     }
-    alpha = rz / pq;
-    ah = (float)alpha;
-    al = (float)(alpha - (double)ah);
-    if (b0) {
-      v.sc->pq = pq;
-      v.sc->alpha = alpha;
-      v.sc->alpha_h = ah;
-      v.sc->alpha_l = al;
+    __syncthreads();
+    if (stop_s) return;
+    if constexpr (sizeof(T) == 4) {
+      ah = ah_s;
+      al = al_s;
+    } else {
+      alpha = a_s;
     }
   } else if constexpr (sizeof(T) == 4) {
     ah = vol_readf(&v.sc->alpha_h);

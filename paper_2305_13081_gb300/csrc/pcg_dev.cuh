@@ -80,26 +80,47 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
 }
 
 // Deferred reductions (2D): a producer kernel stores one partial per block
-// and takes no ticket; every block of the consuming kernel sums the
-// partials itself, in the fixed order of sum_partials_ordered and
-// block_sum, so that all blocks obtain the same total (returned in every
-// thread). The kernel boundary orders the partial stores before these loads.
-static __device__ double block_total_partials(const double* partials, int n, double* scratch) {
-  __shared__ double tot_s;
-  double v[1];
-  sum_partials_ordered<1, 4>(v, partials, n);
-  block_sum<1>(v, scratch);
-  if (flat_tid() == 0) tot_s = v[0];
-  __syncthreads();
-  return tot_s;
+// (store_deferred_partial) and takes no ticket; every block of the consuming
+// kernel sums the partials itself (deferred_total), in a fixed order, so that
+// all blocks obtain the same total. The kernel boundary orders the partial
+// stores before these loads. Float kernels keep both sides in double-float
+// arithmetic (a partial is the float pair h, l in the 8-byte slot): GB300
+// runs FP64 at a small fraction of FP32, and every block of the consumer
+// repeats the sum.
+template <typename T>
+struct Acc;
+template <typename T>
+__device__ __forceinline__ void store_deferred_partial(Acc<T>& acc, double* slot, float* redf, double* red);
+
+// Total of n partials, valid in thread 0 of the block.
+template <typename T>
+__device__ __forceinline__ double deferred_total(const double* partials, int n, float* redf, double* red) {
+  if constexpr (sizeof(T) == 4) {
+    const float2* p2 = reinterpret_cast<const float2*>(partials);
+    const int nt = flat_nthreads();
+    dfloat s{0.f, 0.f};
+    for (int b0 = flat_tid(); b0 < n; b0 += 4 * nt) {
+      float2 x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = b0 + j * nt < n ? __ldcg(p2 + b0 + j * nt) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (b0 + j * nt < n) s = df_add(s, dfloat{x[j].x, x[j].y});
+    }
+    const dfloat t = block_sum_df2(s, redf);
+    return flat_tid() == 0 ? (double)t.h + (double)t.l : 0.0;
+  } else {
+    double v[1];
+    sum_partials_ordered<1, 4>(v, partials, n);
+    block_sum<1>(v, red);
+    return v[0];
+  }
 }
 
 static __device__ __forceinline__ int vol_readi(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
 // Per-thread accumulator of a block reduction: double-float for float
 // kernels (no FP64 instruction), double for the FP64 path.
-template <typename T>
-struct Acc;
 template <>
 struct Acc<float> {
   dfloat v{0.f, 0.f};
@@ -116,6 +137,17 @@ struct Acc<double> {
     return a[0];
   }
 };
+
+template <>
+__device__ __forceinline__ void store_deferred_partial<float>(Acc<float>& acc, double* slot, float* redf, double*) {
+  const dfloat t = block_sum_df2(acc.v, redf);
+  if (flat_tid() == 0) *reinterpret_cast<float2*>(slot) = make_float2(t.h, t.l);
+}
+template <>
+__device__ __forceinline__ void store_deferred_partial<double>(Acc<double>& acc, double* slot, float*, double* red) {
+  const double t = acc.block_total(nullptr, red);
+  if (flat_tid() == 0) *slot = t;
+}
 
 // A column / line pass runs for problem b in this mode: ITER and TRUE skip
 // converged problems, RESTART runs only for the problems being restarted.

@@ -367,18 +367,21 @@ FFTMECH_POST_INST(double)
 
 // Finalise a deferred column pass that no direction kernel followed (the
 // solve stopped at its iteration limit): one block per problem.
+template <typename T>
 static __global__ void __launch_bounds__(256) k_col_finalize(const double* pcol, int ncol, SolverScalars* sc,
                                                              double invN) {
+  __shared__ float redf[64];
   __shared__ double red[32];
   sc += blockIdx.x;
   if (done_flag(sc)) return;
-  const double tot = block_total_partials(pcol + (size_t)blockIdx.x * ncol, ncol, red);
+  const double tot = deferred_total<T>(pcol + (size_t)blockIdx.x * ncol, ncol, redf, red);
   if (threadIdx.x == 0) finalize_col(sc, vol_readi(&sc->col_true) ? COL_TRUE : COL_ITER, tot * invN);
 }
 
-cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc, int batch, double invN,
+cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc, int batch, double invN, int fp32,
                                 cudaStream_t st) {
-  k_col_finalize<<<batch, 256, 0, st>>>(pcol, ncol, sc, invN);
+  if (fp32) k_col_finalize<float><<<batch, 256, 0, st>>>(pcol, ncol, sc, invN);
+  else k_col_finalize<double><<<batch, 256, 0, st>>>(pcol, ncol, sc, invN);
   return cudaGetLastError();
 }
 

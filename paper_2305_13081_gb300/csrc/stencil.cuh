@@ -144,12 +144,12 @@ __global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v) {
     }
     acc.add(part);
   }
-  const double bt[1] = {acc.block_total(redf, red)};
   double* partials = v.partials + (size_t)bp * gridDim.x;
   if (v.nsten > 0) {  // deferred: the update kernel's blocks sum the partials
-    if (threadIdx.x == 0) partials[blockIdx.x] = bt[0];
+    store_deferred_partial<T>(acc, partials + blockIdx.x, redf, red);
     return;
   }
+  const double bt[1] = {acc.block_total(redf, red)};
   if (publish_partials<1>(bt, partials, &v.sc->cnt[0])) {
     double tot[1];
     gather_partials<1>(tot, partials, &v.sc->cnt[0], red);
