@@ -241,16 +241,22 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   Acc<T> acc;
   colpass_strip<T, FY, NY, CWC>(blockIdx.x, nx, ny, S, B, py_s, sp, LX, LY, CW, mode, inverse, bp, acc);
   if (mode == COL_PLAIN) return;
+  // every mode stores its partial in the deferred format, so a total formed
+  // here (last block) and one formed by the next direction kernel agree bit
+  // for bit
+  store_deferred_partial<T>(acc, partials + blockIdx.x, redf, red);
   if ((mode_arg & COL_DEFER) && (mode == COL_ITER || mode == COL_TRUE)) {  // finalised by the next direction kernel
-    store_deferred_partial<T>(acc, partials + blockIdx.x, redf, red);
     if (threadIdx.x == 0 && blockIdx.x == 0) sc->col_true = mode == COL_TRUE;
     return;
   }
-  const double bt[1] = {acc.block_total(redf, red)};
-  if (publish_partials<1>(bt, partials, &sc->cnt[1])) {
-    double tot[1];
-    gather_partials<1>(tot, partials, &sc->cnt[1], red);
-    if (threadIdx.x == 0) finalize_col(sc, mode, tot[0] * sp.invN);
+  __shared__ int am_last;
+  if (threadIdx.x == 0) am_last = ticket_acq_rel(&sc->cnt[1]) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last) return;
+  const double tot = deferred_total<T>(partials, gridDim.x, redf, red);
+  if (threadIdx.x == 0) {
+    sc->cnt[1] = 0u;
+    finalize_col(sc, mode, tot * sp.invN);
   }
 }
 

@@ -92,28 +92,70 @@ struct Acc;
 template <typename T>
 __device__ __forceinline__ void store_deferred_partial(Acc<T>& acc, double* slot, float* redf, double* red);
 
-// Total of n partials, valid in thread 0 of the block.
+// Total of n partials, valid in thread 0 of the block. The first
+// kDeferredWidth threads take part in a fixed pattern (thread t sums
+// partials t, t + W, ... in order; then a shuffle tree in each of the W / 32
+// warps; then the warp totals in order), so the total does not depend on the
+// block size of the kernel that forms it. The block needs >= W threads.
+constexpr int kDeferredWidth = 128;
 template <typename T>
 __device__ __forceinline__ double deferred_total(const double* partials, int n, float* redf, double* red) {
+  constexpr int W = kDeferredWidth;
+  const int tid = flat_tid(), lane = tid & 31, wid = tid >> 5;
   if constexpr (sizeof(T) == 4) {
     const float2* p2 = reinterpret_cast<const float2*>(partials);
-    const int nt = flat_nthreads();
     dfloat s{0.f, 0.f};
-    for (int b0 = flat_tid(); b0 < n; b0 += 4 * nt) {
-      float2 x[4];
+    if (tid < W) {
+      for (int b0 = tid; b0 < n; b0 += 4 * W) {
+        float2 x[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) x[j] = b0 + j * nt < n ? __ldcg(p2 + b0 + j * nt) : make_float2(0.f, 0.f);
+        for (int j = 0; j < 4; ++j) x[j] = b0 + j * W < n ? __ldcg(p2 + b0 + j * W) : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (b0 + j * nt < n) s = df_add(s, dfloat{x[j].x, x[j].y});
+        for (int j = 0; j < 4; ++j)
+          if (b0 + j * W < n) s = df_add(s, dfloat{x[j].x, x[j].y});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const dfloat w{__shfl_down_sync(0xffffffffu, s.h, o), __shfl_down_sync(0xffffffffu, s.l, o)};
+        s = df_add(s, w);
+      }
+      if (lane == 0) {
+        redf[2 * wid] = s.h;
+        redf[2 * wid + 1] = s.l;
+      }
     }
-    const dfloat t = block_sum_df2(s, redf);
-    return flat_tid() == 0 ? (double)t.h + (double)t.l : 0.0;
+    __syncthreads();
+    double tot = 0.0;
+    if (tid == 0) {
+      dfloat t{redf[0], redf[1]};
+      for (int w = 1; w < W / 32; ++w) t = df_add(t, dfloat{redf[2 * w], redf[2 * w + 1]});
+      tot = (double)t.h + (double)t.l;
+    }
+    __syncthreads();
+    return tot;
   } else {
-    double v[1];
-    sum_partials_ordered<1, 4>(v, partials, n);
-    block_sum<1>(v, red);
-    return v[0];
+    double s = 0.0;
+    if (tid < W) {
+      for (int b0 = tid; b0 < n; b0 += 4 * W) {
+        double x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = b0 + j * W < n ? __ldcg(partials + b0 + j * W) : 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (b0 + j * W < n) s += x[j];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) red[wid] = s;
+    }
+    __syncthreads();
+    double tot = 0.0;
+    if (tid == 0) {
+      tot = red[0];
+      for (int w = 1; w < W / 32; ++w) tot += red[w];
+    }
+    __syncthreads();
+    return tot;
   }
 }
 
