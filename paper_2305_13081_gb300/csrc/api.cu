@@ -335,12 +335,18 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
   v.partials = ctx->partials;
   v.sc = ctx->sc;
   v.mode = ctx->mode;
-  // 2D: deferred reductions (the stencil's <p, K p> summed by the update
-  // kernel, the column pass's <r, M^-1 r> by the next direction kernel)
-  const bool defer = ctx->dim == 2;
+  // Deferred reductions where the grid is latency-bound (up to 2^21 voxels
+  // per launch): the stencil's <p, K p> summed by the update kernel (2D and
+  // 3D), the column pass's <r, M^-1 r> by the next direction kernel (2D).
+  // Larger grids keep the last-block reductions: there every consumer block
+  // re-reading all partials costs more than the ticket saves.
+  const bool small = (long long)ctx->N * B <= (1LL << 21);
+  const bool defer = small && ctx->dim == 2;
   const int ncol_blocks = defer ? (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols : 0;
   v.pcol = ctx->partials_col;
-  v.nsten = defer ? sten2_blocks(ctx->nx, ctx->ny, ctx->sshape) : 0;
+  v.nsten = !small ? 0
+            : ctx->dim == 2 ? sten2_blocks(ctx->nx, ctx->ny, ctx->sshape)
+                            : sten3_blocks(ctx->nx, ctx->ny, ctx->nz, ctx->sshape);
   const long long nU = (long long)D * ctx->N * B;
   const bool mixed = sizeof(T) == 4;
   if (mixed) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_df_split(nU, u, ctx->uh, ctx->ul, st));

@@ -217,6 +217,13 @@ inline int sten2_blocks(int nx, int ny, const StenShape& s) {
   const int blocks = (items + 7) / 8;
   return s.grid > 0 ? std::min(s.grid, blocks) : blocks;
 }
+// Blocks per problem of the 3D stencil (bricks of 30 columns, s.ty rows and
+// s.zc planes, 8 warps a block, at most s.grid blocks).
+inline int sten3_blocks(int nx, int ny, int nz, const StenShape& s) {
+  const long long items = (long long)((nx + 29) / 30) * ((ny + s.ty - 1) / s.ty) * ((nz + s.zc - 1) / s.zc);
+  const long long blocks = (items + 7) / 8;
+  return (int)(s.grid > 0 ? std::min<long long>(s.grid, blocks) : blocks);
+}
 
 
 // ---------------------------------------------------------------- launchers
@@ -464,12 +471,6 @@ template <typename T>
 inline size_t xupd_smem(int nx, int L, int D, int dim) {
   const int nf = (dim == 3 && D == 3) ? 2 : 1;
   return tw_smem_bytes<T>(nx) + (size_t)nf * L * nx * sizeof(cx<T>);
-}
-template <typename T>
-inline size_t sten3_smem(int tx, int ty, int D) {
-  const size_t np = D == 3 ? 3 : 2, nzc = D == 3 ? 3 : 1;
-  const size_t sgs = (size_t)(ty + 1) * (tx + 1);
-  return ((size_t)2 * D * (ty + 2) * (tx + 2) + np * sgs + 2 * nzc * sgs + sgs) * sizeof(T) + sgs;
 }
 
 

@@ -257,12 +257,14 @@ inline void choose_sten_shape(int nx, int ny, int nz, int dim, int nsm, int batc
     s.zc = 1;
     return;
   }
-  s.tx = std::min(nx, 32);
-  s.ty = std::min(ny, 8);
-  const long long tiles = (long long)((nx + s.tx - 1) / s.tx) * ((ny + s.ty - 1) / s.ty) * batch;
-  long long nzc = (8LL * nsm + tiles - 1) / tiles;
-  nzc = std::max(1LL, std::min<long long>(nzc, nz));
-  s.zc = std::max(std::min(nz, 4), (int)((nz + nzc - 1) / nzc));
+  // warp bricks of 30 columns, 4 rows and zc planes: zc from 2 to 16, as
+  // long as the bricks give at least 32 warps per SM
+  s.tx = 30;
+  s.ty = 4;
+  const long long strips = (long long)((nx + 29) / 30) * ((ny + 3) / 4) * batch;
+  const long long chunks = (32LL * nsm + strips - 1) / strips;
+  const long long zc = (nz + chunks - 1) / chunks;
+  s.zc = (int)std::max(1LL, std::min<long long>(std::min<long long>(16, nz), std::max(2LL, zc)));
 }
 
 // Launch shapes for the bare transform (row FFT + column FFT only), which

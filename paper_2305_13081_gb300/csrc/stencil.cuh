@@ -20,7 +20,6 @@
 
 namespace fftmech {
 
-#define FFTMECH_BOUNDS_S __launch_bounds__(256)
 
 static __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -158,16 +157,16 @@ __global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v) {
 }
 
 // ---------------------------------------------------------------- 3D
-// Shared memory: [P: 2 planes x D (TY+2)(TX+2)] [SP: NP (TY+1)(TX+1)]
-// [SZ: 2 planes x NZ (TY+1)(TX+1)] [MG: (TY+1)(TX+1)] [PH: bytes]; NP
-// in-plane components (sxx, syy, sxy or Jx, Jy), NZ z-differenced ones
-// (sxz, syz, szz or Jz). blockDim = (TX, TY): thread (tx, ty) owns tile
-// column tx (and the halo columns TX, TX + 1 when tx < 2) and tile row ty.
-template <typename T, int D, int TX, int TY>
-__global__ void FFTMECH_BOUNDS_S k_sten3(Op<T> op, Vec2<T> v, int Zc) {
-  constexpr int NP = D == 3 ? 3 : 2, NZ = D == 3 ? 3 : 1;
-  constexpr int PW = TX + 2, SW = TX + 1;
-  constexpr size_t PS = (size_t)(TY + 2) * PW, SS = (size_t)(TY + 1) * SW;
+// One warp takes a brick of kStrip2 = 30 columns (lanes 0 and 31 are halo
+// columns), R rows and Zc planes, and marches through the planes from the
+// halo plane z0 - 1. For each plane it walks the R + 1 rows y0 - 1 ..
+// y0 + R - 1: the stress (flux) at a row needs the direction on the row, the
+// row below and the next plane; x neighbours come from shuffles, the row
+// above's stress from the previous row step and the previous plane's
+// z-differenced components from registers kept per row.
+template <typename T, int D, int R>
+__global__ void __launch_bounds__(kSten2Threads) k_sten3(Op<T> op, Vec2<T> v, int Zc) {
+  constexpr int NZ = D == 3 ? 3 : 1;  // z-differenced components (sxz, syz, szz) or Jz
   const int nx = op.nx, ny = op.ny, nz = op.nz;
   const size_t plane = (size_t)nx * ny;
   const size_t N = plane * nz;
@@ -175,182 +174,150 @@ __global__ void FFTMECH_BOUNDS_S k_sten3(Op<T> op, Vec2<T> v, int Zc) {
   sten_views<T, D>(op, v, bp, N);
   grid_dep_sync();
   if (done_flag(v.sc)) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ float redf[64];
-  T* P = reinterpret_cast<T*>(smem);
-  T* SP = P + 2 * D * PS;
-  T* SZ = SP + NP * SS;
-  T* MG = SZ + 2 * NZ * SS;
-  uint8_t* PH = reinterpret_cast<uint8_t*>(MG + SS);
-  const T* matg = (D == 3) ? op.g : op.c0f;
-  const bool masked = (D == 1) && op.mask;
-  const int tx = threadIdx.x, ty = threadIdx.y, TY4 = blockDim.y;
+  const T* __restrict__ P = v.p_in;
+  const T* __restrict__ matg = (D == 3) ? op.g : op.c0f;
+  const uint8_t* __restrict__ ph = op.phase;
+  const uint8_t* __restrict__ msk = (D == 1) ? op.mask : nullptr;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
   const T ih = op.ih_t;
   const T lam0 = op.lam_t[0], lam1 = op.lam_t[1], mu0 = op.mu_t[0], mu1 = op.mu_t[1];
   const T kap0 = op.kap_t[0], kap1 = op.kap_t[1];
   const T c0c = op.c0c_t;
-  const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY;
-  const int nitems = ntx * nty * ((nz + Zc - 1) / Zc);
+  const int nsx = (nx + kStrip2 - 1) / kStrip2, nsy = (ny + R - 1) / R;
+  const int items = nsx * nsy * ((nz + Zc - 1) / Zc);
   Acc<T> acc;
-  // bricks blockIdx.x, blockIdx.x + gridDim.x, ...: one reduction ticket per block
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    T part = T(0);
+  for (int item = blockIdx.x * nwarps + (int)(threadIdx.x >> 5); item < items; item += gridDim.x * nwarps) {
     int t = item;
-    const int txi = t % ntx;
-    t /= ntx;
-    const int tyi = t % nty;
-    const int tzi = t / nty;
-    const int x0 = txi * TX, y0 = tyi * TY, z0 = tzi * Zc;
-    const int wx = min(TX, nx - x0), wy = min(TY, ny - y0), planes = min(Zc, nz - z0);
-    const int xa = wrap1(x0 - 1 + tx, nx);
-    const bool ha = tx < wx + 2;
-    const bool hb = tx < 2 && TX + tx < wx + 2;
-    const int xb = wrap1(x0 - 1 + TX + tx, nx);
-    // direction of plane z into ring slot s (tile with halo)
-    auto load_p = [&](int z, int slot) {
-      const size_t pz = (size_t)wrap1(z, nz) * plane;
-      T* dst = P + (size_t)slot * D * PS;
-      for (int yy = ty; yy < wy + 2; yy += TY4) {
-        const size_t rowg = pz + (size_t)wrap1(y0 - 1 + yy, ny) * nx;
-        T va[D], vb[D];
+    const int sx = t % nsx;
+    t /= nsx;
+    const int sy = t % nsy;
+    const int sz = t / nsy;
+    const int x0 = sx * kStrip2, y0 = sy * R, z0 = sz * Zc;
+    const int wx = min(kStrip2, nx - x0), wy = min(R, ny - y0), planes = min(Zc, nz - z0);
+    const int x = (x0 - 1 + lane + nx) % nx;
+    const bool own = lane >= 1 && lane <= kStrip2 && lane - 1 < wx;
+    size_t rowo[R + 2];  // offsets of rows y0 - 1 .. y0 + R (wrapped) within a plane
+    {
+      int y = (y0 - 1 + ny) % ny;
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          va[c] = ha ? v.p_in[c * N + rowg + xa] : T(0);
-          vb[c] = hb ? v.p_in[c * N + rowg + xb] : T(0);
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          if (ha) dst[c * PS + yy * PW + tx] = va[c];
-          if (hb) dst[c * PS + yy * PW + TX + tx] = vb[c];
-        }
+      for (int r = 0; r < R + 2; ++r) {
+        rowo[r] = (size_t)y * nx + x;
+        y = y + 1 == ny ? 0 : y + 1;
       }
-    };
-    load_p(z0 - 1, 0);
-    for (int zz = z0 - 1; zz < z0 + planes; ++zz) {
-      const int cur = (zz - z0 + 1) & 1, nxt = cur ^ 1;
-      const bool inner_plane = zz >= z0;
-      const size_t pz = (size_t)wrap1(zz, nz) * plane;
-      load_p(zz + 1, nxt);
-      for (int yy = ty; yy <= wy; yy += TY4) {
-        const size_t rowg = pz + (size_t)wrap1(y0 - 1 + yy, ny) * nx;
-        if (ha && tx <= wx) {
-          MG[yy * SW + tx] = matg ? matg[rowg + xa] : T(0);
-          PH[yy * SW + tx] = op.phase[rowg + xa];
-        }
-        if (hb && TX + tx <= wx) {
-          MG[yy * SW + TX + tx] = matg ? matg[rowg + xb] : T(0);
-          PH[yy * SW + TX + tx] = op.phase[rowg + xb];
-        }
-      }
-      __syncthreads();
-      const T* Pc = P + (size_t)cur * D * PS;
-      const T* Pn = P + (size_t)nxt * D * PS;
-      T* Zc_ = SZ + (size_t)cur * NZ * SS;
-      const T* Zp = SZ + (size_t)nxt * NZ * SS;  // previous plane
-      for (int yy = ty; yy <= wy; yy += TY4) {
+    }
+    int z = (z0 - 1 + nz) % nz;
+    T pc[R + 2][D];
+    {
+      const size_t pz = (size_t)z * plane;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int xx = h == 0 ? tx : TX + tx;
-          if (xx > wx || (h == 1 && tx >= 1)) continue;
-          const int c = yy * PW + xx, i = yy * SW + xx;
-          const bool sol = PH[i] != 0;
-          const bool inner = inner_plane && xx >= 1 && yy >= 1;
-          if constexpr (D == 3) {
-            const T* Ux = Pc;
-            const T* Uy = Pc + PS;
-            const T* Uz = Pc + 2 * PS;
-            const T ux = Ux[c], uy = Uy[c], uz = Uz[c];
-            const T exx = (Ux[c + 1] - ux) * ih;
-            const T eyy = (Uy[c + PW] - uy) * ih;
-            const T ezz = (Pn[2 * PS + c] - uz) * ih;
-            const T eyz = T(0.5) * ((Pn[PS + c] - uy) + (Uz[c + PW] - uz)) * ih;
-            const T exz = T(0.5) * ((Pn[c] - ux) + (Uz[c + 1] - uz)) * ih;
-            const T exy = T(0.5) * ((Ux[c + PW] - ux) + (Uy[c + 1] - uy)) * ih;
-            const T gg = matg ? MG[i] : T(1);
-            const T lam = gg * (sol ? lam1 : lam0), mu = gg * (sol ? mu1 : mu0);
-            const T lt = lam * (exx + eyy + ezz), m2 = T(2) * mu;
-            const T sxx = lt + m2 * exx, syy = lt + m2 * eyy, szz = lt + m2 * ezz;
-            const T syz = m2 * eyz, sxz = m2 * exz, sxy = m2 * exy;
-            SP[i] = sxx;
-            SP[SS + i] = syy;
-            SP[2 * SS + i] = sxy;
-            Zc_[i] = sxz;
-            Zc_[SS + i] = syz;
-            Zc_[2 * SS + i] = szz;
-            if (inner) part += exx * sxx + eyy * syy + ezz * szz + T(2) * (eyz * syz + exz * sxz + exy * sxy);
-          } else {
-            const T p = Pc[c];
-            const T kap = sol ? kap1 : kap0;
-            const T gx = (Pc[c + 1] - p) * ih, gy = (Pc[c + PW] - p) * ih, gz = (Pn[c] - p) * ih;
-            SP[i] = kap * gx;
-            SP[SS + i] = kap * gy;
-            Zc_[i] = kap * gz;
-            if (inner) part += (c0c + (matg ? MG[i] : T(0))) * p * p + kap * (gx * gx + gy * gy + gz * gz);
+      for (int r = 0; r < R + 2; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) pc[r][c] = P[c * N + pz + rowo[r]];
+    }
+    T zprev[R][NZ];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) zprev[r][c] = T(0);
+    T part = T(0);
+    for (int k = 0; k <= planes; ++k) {  // k = 0: halo plane z0 - 1
+      const int zn = z + 1 == nz ? 0 : z + 1;
+      const size_t pz = (size_t)z * plane, pzn = (size_t)zn * plane;
+      // this plane's material and the next plane's direction
+      T pn[R + 2][D], g[R + 1];
+      bool sol[R + 1], mk[R + 1];
+#pragma unroll
+      for (int r = 0; r < R + 2; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) pn[r][c] = P[c * N + pzn + rowo[r]];
+#pragma unroll
+      for (int r = 0; r < R + 1; ++r) {
+        sol[r] = ph[pz + rowo[r]] != 0;
+        g[r] = matg ? matg[pz + rowo[r]] : T(0);
+        mk[r] = (msk && r >= 1) ? msk[pz + rowo[r]] != 0 : false;
+      }
+      const bool inner = k >= 1;
+      T yp0 = T(0), yp1 = T(0), yp2 = T(0);  // row above: (sxy, syy, syz) or Jy
+#pragma unroll
+      for (int r = 0; r < R + 1; ++r) {
+        const bool out = inner && own && r >= 1 && r <= wy;
+        T pr[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) pr[c] = __shfl_down_sync(FULL, pc[r][c], 1);
+        if constexpr (D == 3) {
+          const T ux = pc[r][0], uy = pc[r][1], uz = pc[r][2];
+          const T exx = (pr[0] - ux) * ih;
+          const T eyy = (pc[r + 1][1] - uy) * ih;
+          const T ezz = (pn[r][2] - uz) * ih;
+          const T eyz = T(0.5) * ((pn[r][1] - uy) + (pc[r + 1][2] - uz)) * ih;
+          const T exz = T(0.5) * ((pn[r][0] - ux) + (pr[2] - uz)) * ih;
+          const T exy = T(0.5) * ((pc[r + 1][0] - ux) + (pr[1] - uy)) * ih;
+          const T gg = matg ? g[r] : T(1);
+          const T lam = gg * (sol[r] ? lam1 : lam0), mu = gg * (sol[r] ? mu1 : mu0);
+          const T lt = lam * (exx + eyy + ezz), m2 = T(2) * mu;
+          const T sxx = lt + m2 * exx, syy = lt + m2 * eyy, szz = lt + m2 * ezz;
+          const T syz = m2 * eyz, sxz = m2 * exz, sxy = m2 * exy;
+          const T lxx = __shfl_up_sync(FULL, sxx, 1), lxy = __shfl_up_sync(FULL, sxy, 1),
+                  lxz = __shfl_up_sync(FULL, sxz, 1);
+          if (out) {
+            const size_t gi = pz + rowo[r];
+            v.q[gi] = ((lxx - sxx) + (yp0 - sxy) + (zprev[r - 1][0] - sxz)) * ih;
+            v.q[N + gi] = ((lxy - sxy) + (yp1 - syy) + (zprev[r - 1][1] - syz)) * ih;
+            v.q[2 * N + gi] = ((lxz - sxz) + (yp2 - syz) + (zprev[r - 1][2] - szz)) * ih;
+            part += exx * sxx + eyy * syy + ezz * szz + T(2) * (eyz * syz + exz * sxz + exy * sxy);
           }
-        }
-      }
-      __syncthreads();
-      if (inner_plane && tx < wx) {
-        for (int yr = ty; yr < wy; yr += TY4) {
-          const int s = (yr + 1) * SW + (tx + 1);
-          const size_t gi = pz + (size_t)(y0 + yr) * nx + x0 + tx;
-          if constexpr (D == 3) {
-            const T* Sxx = SP;
-            const T* Syy = SP + SS;
-            const T* Sxy = SP + 2 * SS;
-            const T* Sxz = Zc_;
-            const T* Syz = Zc_ + SS;
-            const T* Szz = Zc_ + 2 * SS;
-            v.q[gi] = ((Sxx[s - 1] - Sxx[s]) + (Sxy[s - SW] - Sxy[s]) + (Zp[s] - Sxz[s])) * ih;
-            v.q[N + gi] = ((Sxy[s - 1] - Sxy[s]) + (Syy[s - SW] - Syy[s]) + (Zp[SS + s] - Syz[s])) * ih;
-            v.q[2 * N + gi] = ((Sxz[s - 1] - Sxz[s]) + (Syz[s - SW] - Syz[s]) + (Zp[2 * SS + s] - Szz[s])) * ih;
-          } else {
-            const T* Jx = SP;
-            const T* Jy = SP + SS;
-            const T p = Pc[(yr + 1) * PW + tx + 1];
-            T q = (c0c + (matg ? MG[s] : T(0))) * p +
-                  ((Jx[s - 1] - Jx[s]) + (Jy[s - SW] - Jy[s]) + (Zp[s] - Zc_[s])) * ih;
-            if (masked && op.mask[gi]) q = T(0);
+          if (r >= 1) {
+            zprev[r - 1][0] = sxz;
+            zprev[r - 1][1] = syz;
+            zprev[r - 1][2] = szz;
+          }
+          yp0 = sxy;
+          yp1 = syy;
+          yp2 = syz;
+        } else {
+          const T p = pc[r][0];
+          const T kap = sol[r] ? kap1 : kap0;
+          const T gx = (pr[0] - p) * ih, gy = (pc[r + 1][0] - p) * ih, gz = (pn[r][0] - p) * ih;
+          const T jx = kap * gx, jy = kap * gy, jz = kap * gz;
+          const T ljx = __shfl_up_sync(FULL, jx, 1);
+          if (out) {
+            const size_t gi = pz + rowo[r];
+            const T c0 = c0c + g[r];
+            T q = c0 * p + ((ljx - jx) + (yp0 - jy) + (zprev[r - 1][0] - jz)) * ih;
+            if (mk[r]) q = T(0);
             v.q[gi] = q;
+            part += c0 * p * p + kap * (gx * gx + gy * gy + gz * gz);
           }
+          if (r >= 1) zprev[r - 1][0] = jz;
+          yp0 = jy;
         }
       }
-      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < R + 2; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) pc[r][c] = pn[r][c];
+      z = zn;
     }
     acc.add(part);
   }
-  const double bt[1] = {acc.block_total(redf, red)};
   double* partials = v.partials + (size_t)bp * gridDim.x;
+  if (v.nsten > 0) {  // deferred: the update kernel's blocks sum the partials
+    store_deferred_partial<T>(acc, partials + blockIdx.x, redf, red);
+    return;
+  }
+  const double bt[1] = {acc.block_total(redf, red)};
   if (publish_partials<1>(bt, partials, &v.sc->cnt[0])) {
     double tot[1];
     gather_partials<1>(tot, partials, &v.sc->cnt[0], red);
-    if (threadIdx.x == 0 && threadIdx.y == 0) finalize_direction(v.sc, tot[0]);
+    if (threadIdx.x == 0) finalize_direction(v.sc, tot[0]);
   }
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename K>
-static cudaError_t set_smem_s(K kernel, size_t bytes, std::atomic<int>& configured) {
-  if (configured) return cudaSuccess;
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, kernel);
-  if (e != cudaSuccess) return e;
-  const int dyn_max = optin - (int)fa.sharedSizeBytes;
-  if ((long long)bytes > (long long)dyn_max) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
-  if (e == cudaSuccess) configured = 1;
-  return e;
-}
-
-// 3D tiles: 32 x 8 voxels per 32 x 8 threads.
-constexpr int kSten3TX = 32, kSten3TY = 8;
-
 template <typename T, int D>
 cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss, cudaStream_t st) {
   static_assert(kStrip2 == 30 && kSten2Threads == 256, "sten2_blocks assumes 30-column strips, 8 warps");
@@ -361,14 +328,9 @@ cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss,
 
 template <typename T, int D>
 cudaError_t launch_sten3(const Op<T>& op, const Vec2<T>& v, const StenShape& ss, cudaStream_t st) {
-  const size_t sm = sten3_smem<T>(kSten3TX, kSten3TY, D);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem_s(k_sten3<T, D, kSten3TX, kSten3TY>, sm, cfg);
-  if (e != cudaSuccess) return e;
-  const int bricks = ((op.nx + kSten3TX - 1) / kSten3TX) * ((op.ny + kSten3TY - 1) / kSten3TY) *
-                     ((op.nz + ss.zc - 1) / ss.zc);
-  const dim3 grid(ss.grid > 0 ? std::min(ss.grid, bricks) : bricks, ss.batch);
-  return launch_dep(k_sten3<T, D, kSten3TX, kSten3TY>, grid, dim3(kSten3TX, kSten3TY), sm, st, op, v, ss.zc);
+  const dim3 grid(sten3_blocks(op.nx, op.ny, op.nz, ss), ss.batch);
+  if (ss.ty != 4) return cudaErrorInvalidValue;
+  return launch_dep(k_sten3<T, D, 4>, grid, dim3(kSten2Threads), 0, st, op, v, ss.zc);
 }
 
 }  // namespace fftmech
