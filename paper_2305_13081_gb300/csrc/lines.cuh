@@ -71,6 +71,23 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
   if (done_flag(v.sc)) return;
+  const int l0 = blockIdx.x * L;
+  const int nl = min(L, nlines - l0);
+  const int nxs = spec_row(nx, D, DIM);
+  const int nxa = (DIM == 3 && D == 3) ? nx : 0;  // packed field's length in a 3D row
+  const int nxh = nx / 2 + 1;
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
+  cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;  // the half-spectrum field's lines (DIM 3)
+  T* PO = reinterpret_cast<T*>(smem + align16((size_t)LL::NF * L * nx * sizeof(cx<T>)));
+  const size_t t0 = (size_t)l0 * nx;
+  // 2D with a deferred reduction: the copies of the spectral rows and the
+  // old direction do not depend on beta, so they start before the reduction
+  const bool early = DIM == 2 && v.ncol > 0;
+  if (early) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) g2s_async(PO + (size_t)c * nl * nx, v.p_in + c * N + t0, nl * nx);
+    g2s_async(F, v.S + t0, nl * nx);
+  }
   T b;
   if (v.ncol > 0) {
     // deferred reduction of the last column pass (an ITER or TRUE pass):
@@ -118,7 +135,10 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
       }
     }
     __syncthreads();
-    if (stop_s) return;
+    if (stop_s) {
+      g2s_async_wait();
+      return;
+    }
     b = b_s;
   } else if constexpr (sizeof(T) == 4) {
     b = vol_readf(&v.sc->beta_f);
@@ -126,23 +146,15 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
     b = vol_read(&v.sc->beta);
   }
   const bool with_old = b != T(0);  // the first iteration has p = z
-  const int l0 = blockIdx.x * L;
-  const int nl = min(L, nlines - l0);
-  const int nxs = spec_row(nx, D, DIM);
-  const int nxa = (DIM == 3 && D == 3) ? nx : 0;  // packed field's length in a 3D row
-  const int nxh = nx / 2 + 1;
-  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
-  cx<T>* FB = F + (size_t)(LL::NF - 1) * nl * nx;  // the half-spectrum field's lines (DIM 3)
-  T* PO = reinterpret_cast<T*>(smem + align16((size_t)LL::NF * L * nx * sizeof(cx<T>)));
-  const size_t t0 = (size_t)l0 * nx;
-  // the old direction and the 2D spectral rows by asynchronous copies; the
-  // mask and the 3D spectral rows by loads in flight meanwhile; one wait
-  if (with_old) {
+  // the old direction and the 2D spectral rows by asynchronous copies (unless
+  // already started); the mask and the 3D spectral rows by loads in flight
+  // meanwhile; one wait
+  if (with_old && !early) {
 #pragma unroll
     for (int c = 0; c < D; ++c) g2s_async(PO + (size_t)c * nl * nx, v.p_in + c * N + t0, nl * nx);
   }
   if constexpr (DIM == 2) {
-    g2s_async(F, v.S + t0, nl * nx);
+    if (!early) g2s_async(F, v.S + t0, nl * nx);
   } else {
     // the block's spectral rows are one contiguous run of nl nxs numbers:
     // one flattened loop keeps eight loads in flight per thread
