@@ -40,8 +40,15 @@ __host__ __device__ constexpr bool fixed_len_ok(int n) {
 // b < BM: PassBatch<R> for rows; for columns with THR > 0 (the block has
 // exactly THR threads) as many as the pass needs. All loads precede the
 // barrier, all stores follow it.
-template <typename T, int S, int N, int R, int NS, bool COL, int CW, int THR>
-__device__ __forceinline__ void fftc_pass(cx<T>* buf, const cx<T>* __restrict__ tw, int nlines, int tid) {
+// No post-processing of a pass's outputs.
+struct NoPost {
+  template <typename T>
+  __device__ __forceinline__ void operator()(cx<T>&, int, int) const {}
+};
+
+template <typename T, int S, int N, int R, int NS, bool COL, int CW, int THR, class Post>
+__device__ __forceinline__ void fftc_pass(cx<T>* buf, const cx<T>* __restrict__ tw, int nlines, int tid,
+                                          Post& post) {
   constexpr int BM = (COL && THR > 0) ? ((N / R) * CW + THR - 1) / THR : PassBatch<R>::value;
   constexpr int NB = N / R;
   const int total = COL ? NB * CW : NB * nlines;
@@ -88,6 +95,10 @@ __device__ __forceinline__ void fftc_pass(cx<T>* buf, const cx<T>* __restrict__ 
         }
       }
       dft<T, R, S>(v[b]);
+      if constexpr (NS * R == N) {  // the last pass: outputs are final (frequency q NS R + k + t NS)
+#pragma unroll
+        for (int t = 0; t < R; ++t) post(v[b][t], q * NS * R + k + t * NS, base0);
+      }
       const int out = (q * NS * R + k) * (COL ? CW : 1) + base0;
 #pragma unroll
       for (int t = 0; t < R; ++t) buf[out + t * NS * (COL ? CW : 1)] = v[b][t];
@@ -96,13 +107,13 @@ __device__ __forceinline__ void fftc_pass(cx<T>* buf, const cx<T>* __restrict__ 
   __syncthreads();
 }
 
-template <typename T, int S, int N, int P, int NS, bool COL, int CW, int THR>
-__device__ __forceinline__ void fftc_from(cx<T>* buf, const cx<T>* tw, int nlines, int tid) {
+template <typename T, int S, int N, int P, int NS, bool COL, int CW, int THR, class Post>
+__device__ __forceinline__ void fftc_from(cx<T>* buf, const cx<T>* tw, int nlines, int tid, Post& post) {
   if constexpr (NS < N) {
     constexpr int R = radix_at(N, P);
     static_assert(R > 1 && N % (NS * R) == 0, "plan mismatch");
-    fftc_pass<T, S, N, R, NS, COL, CW, THR>(buf, tw, nlines, tid);
-    fftc_from<T, S, N, P + 1, NS * R, COL, CW, THR>(buf, tw + NS * (R - 1), nlines, tid);
+    fftc_pass<T, S, N, R, NS, COL, CW, THR>(buf, tw, nlines, tid, post);
+    fftc_from<T, S, N, P + 1, NS * R, COL, CW, THR>(buf, tw + NS * (R - 1), nlines, tid, post);
   }
 }
 
@@ -110,8 +121,10 @@ __device__ __forceinline__ void fftc_from(cx<T>* buf, const cx<T>* tw, int nline
 // (COL = true) in place; tw: the plan's twiddles (any memory space).
 // Requires, for every pass, lines * N / r <= PassBatch<r> * blockDim.x, or
 // for columns with THR > 0 a block of exactly THR threads.
-template <typename T, int S, int N, bool COL, int CW = 1, int THR = 0>
-__device__ __forceinline__ void fftc(cx<T>* buf, const cx<T>* tw, int nlines) {
+// post(value, frequency, line) is applied to every output of the last pass
+// before it is stored (for columns, line = the column in the strip).
+template <typename T, int S, int N, bool COL, int CW = 1, int THR = 0, class Post = NoPost>
+__device__ __forceinline__ void fftc(cx<T>* buf, const cx<T>* tw, int nlines, Post&& post = Post()) {
   static_assert(fixed_len_ok(N), "compile-time plans cover 2^a and 3^b");
   // opaque copies of the table pointer and the thread index: keep the
   // compiler from hoisting every pass's index arithmetic and twiddle loads
@@ -119,7 +132,7 @@ __device__ __forceinline__ void fftc(cx<T>* buf, const cx<T>* tw, int nlines) {
   const cx<T>* twl = tw;
   int tid = threadIdx.x;
   asm volatile("" : "+l"(twl), "+r"(tid));
-  fftc_from<T, S, N, 0, 1, COL, CW, THR>(buf, twl, nlines, tid);
+  fftc_from<T, S, N, 0, 1, COL, CW, THR>(buf, twl, nlines, tid, post);
 }
 
 }  // namespace fftmech

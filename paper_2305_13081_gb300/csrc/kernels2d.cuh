@@ -136,6 +136,33 @@ __device__ __forceinline__ void col_fft(cx<T>* B, const FftPlanDev<T>& p, int nc
   else fft_lines<T, S, FY>(B, p, nc, 1, nc, true);
 }
 
+// Multiplier of the column pass applied to one spectral value (frequency ky
+// of strip column c): m = 1 / (m0 + m1 (lamx[c] + lamy[ky])), sum m |w|^2
+// (Parseval), w <- w m / N unless the pass only measures the norm.
+template <typename T>
+struct ColMul {
+  const T* lx;
+  const T* ly;
+  T m0, m1, invN;
+  bool store;
+  T part;
+  int cnt;
+  Acc<T>* acc;
+  __device__ __forceinline__ void operator()(cx<T>& w, int ky, int c) {
+    const T den = m0 + m1 * (lx[c] + ly[ky]);
+    T m;
+    if constexpr (sizeof(T) == 4) m = den > T(0) ? __fdividef(1.0f, den) : T(0);
+    else m = den > T(0) ? T(1) / den : T(0);
+    part += m * (w.re * w.re + w.im * w.im);
+    if (++cnt == 16) {  // non-negative terms
+      acc->add(part);
+      part = T(0);
+      cnt = 0;
+    }
+    if (store) w = scal(w, m * invN);
+  }
+};
+
 // Strip of up to CW columns of S (stored [ky][c] in shared memory). Forward
 // column FFT, multiply by m(k) / N, accumulate sum m |S|^2 (Parseval:
 // <r, M^-1 r> = (1/N) sum_k m(k) |S(k)|^2 for the packed field), inverse
@@ -169,14 +196,25 @@ __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* 
       if (i + k * bd < n) B[i + k * bd] = t[k];
   }
   __syncthreads();
+  const bool store = (mode != COL_NORM && mode != COL_TRUENORM);
   if (mode == COL_PLAIN) {
     if (inverse) col_fft<T, 1, FY, NY, CWC>(B, py_s, ncs);
     else col_fft<T, -1, FY, NY, CWC>(B, py_s, ncs);
+  } else if constexpr (NY > 0) {
+    // compile-time plan: the multiplier and the Parseval sum are applied to
+    // the last forward pass's outputs before they are stored
+    const T m0 = sp.m0b ? (T)sp.m0b[bp] : sp.m0_t, m1 = sp.m1b ? (T)sp.m1b[bp] : sp.m1_t;
+    ColMul<T> mul{lamx_s, lamy_s, m0, m1, sp.invN_t, store, T(0), 0, &acc};
+    fftc<T, -1, NY, true, CWC, kColThreads>(B, py_s.tw, CWC, mul);
+    acc.add(mul.part);
+    if (store) {
+      __syncthreads();
+      col_fft<T, 1, FY, NY, CWC>(B, py_s, ncs);
+    }
   } else {
     col_fft<T, -1, FY, NY, CWC>(B, py_s, ncs);
   }
-  const bool store = (mode != COL_NORM && mode != COL_TRUENORM);
-  if (mode != COL_PLAIN) {
+  if (mode != COL_PLAIN && NY == 0) {
     const T m0 = sp.m0b ? (T)sp.m0b[bp] : sp.m0_t, m1 = sp.m1b ? (T)sp.m1b[bp] : sp.m1_t;
     const T invN = sp.invN_t;
     T part = T(0);

@@ -355,7 +355,7 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
       }
     }
   } else {
-    constexpr int U = D == 1 ? 4 : 2;
+    constexpr int U = sizeof(T) == 4 ? (D == 1 ? 6 : 3) : (D == 1 ? 4 : 2);
     for (int i0 = tid; i0 < n; i0 += U * bd) {
       T p[U][D], r[U][D], q[U][D];
       float uh[U][D], ul[U][D];
