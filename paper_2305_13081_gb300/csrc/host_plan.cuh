@@ -196,10 +196,10 @@ bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, i
   auto strip = [&](const HostPlan& pl, int& cw, int& thr) {
     int c = sizeof(T) == 4 ? 16 : 8;
     const size_t tw = tw_smem_bytes<T>(pl.n);
-    while (c > 1 && ((size_t)pl.n * c * sizeof(cx<T>) + tw > budget || need_threads(pl, c) > tmax ||
-                     (long long)pl.n * c >= 65536))
-      c /= 2;
-    if ((size_t)pl.n * c * sizeof(cx<T>) + tw > optin || need_threads(pl, c) > tmax) return false;
+    // strip buffer, twiddles and the z pass's symbol tables
+    auto bytes = [&](int cc) { return (size_t)pl.n * cc * sizeof(cx<T>) + tw + (size_t)(pl.n + 2 * cc) * sizeof(T); };
+    while (c > 1 && (bytes(c) > budget || need_threads(pl, c) > tmax || (long long)pl.n * c >= 65536)) c /= 2;
+    if (bytes(c) > optin || need_threads(pl, c) > tmax) return false;
     cw = c;
     thr = std::min(tmax, std::max(128, round32(need_threads(pl, c))));
     return true;

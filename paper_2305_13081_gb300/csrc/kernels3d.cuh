@@ -241,6 +241,34 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
   }
 }
 
+// Multiplier of the z pass applied to one spectral value (line frequency
+// kl of strip column c): m = 1 / (m0 + m1 (lamc[c] + lamj + laml[kl])),
+// Parseval sum wcol[c] m |w|^2, w <- w m / N unless only the norm is wanted.
+template <typename T>
+struct ZMul {
+  const T* lc;
+  const T* wc;
+  const T* ll;
+  T lj, m0, m1, invN;
+  bool store;
+  T part;
+  int cnt;
+  Acc<T>* acc;
+  __device__ __forceinline__ void operator()(cx<T>& w, int kl, int c) {
+    const T den = m0 + m1 * (lc[c] + lj + ll[kl]);
+    T m;
+    if constexpr (sizeof(T) == 4) m = den > T(0) ? __fdividef(1.0f, den) : T(0);
+    else m = den > T(0) ? T(1) / den : T(0);
+    part += wc[c] * m * (w.re * w.re + w.im * w.im);
+    if (++cnt == 16) {  // non-negative terms
+      acc->add(part);
+      part = T(0);
+      cnt = 0;
+    }
+    if (store) w = scal(w, m * invN);
+  }
+};
+
 // ---------------------------------------------------------------- line passes
 constexpr int kLineThreads = 512;  // block size of the compile-time-plan line passes
 // A strip of CW spectral columns of one line set: nlines complex numbers per
@@ -260,16 +288,29 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(pl.n);
   const FftPlanDev<T> pl_s = plan_to_smem(pl, reinterpret_cast<cx<T>*>(smem_all));
-  grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
+  const int bd = blockDim.x;
+  const int nstrips = (ncols + CW - 1) / CW;
+  const int item = blockIdx.x;  // (line set j, strip)
+  const int j = item / nstrips, strip = item - j * nstrips;
+  // the z pass's symbol tables (constant) behind the strip buffer: lambda
+  // along the lines, and lambda and the Parseval weight of the strip's columns
+  T* LL = reinterpret_cast<T*>(smem + (size_t)nlines * CW * sizeof(cx<T>));
+  T* LC = LL + nlines;
+  T* WC = LC + CW;
+  if (stage == 1 && sp.laml) {
+    for (int i = threadIdx.x; i < nlines; i += bd) LL[i] = sp.laml[i];
+    const int c = threadIdx.x, xc = strip * CW + c;
+    if (c < CW) {
+      LC[c] = xc < ncols ? sp.lamc[xc] : T(0);
+      WC[c] = xc < ncols ? sp.wcol[xc] : T(0);
+    }
+  }
+  grid_dep_sync();  // plan and tables are constant; everything below follows the previous kernel
   if (sc && !col_active(mode, pmode ? pmode + b : nullptr, sc + b)) return;
   if (stage == 1 && mode == COL_ITER && pmode && pmode[b] == 1) mode = COL_TRUE;  // reliable update
   __shared__ double red[32];
   __shared__ float redf[64];
   cx<T>* B = reinterpret_cast<cx<T>*>(smem);
-  const int bd = blockDim.x;
-  const int nstrips = (ncols + CW - 1) / CW;
-  const int item = blockIdx.x;  // (line set j, strip)
-  const int j = item / nstrips, strip = item - j * nstrips;
   cx<T>* Sj = S + (size_t)b * sst + (size_t)j * set_stride;
   const bool store = stage != 1 || (mode != COL_NORM && mode != COL_TRUENORM);
   const int x0 = strip * CW;
@@ -294,15 +335,29 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
       if (i + k * bd < n) B[i + k * bd] = t[k];
   }
   __syncthreads();
+  Acc<T> acc;
   if constexpr (NL > 0) {
-    if (stage == 2) fftc<T, 1, NL, true, CWC, kLineThreads>(B, pl_s.tw, CWC);
-    else fftc<T, -1, NL, true, CWC, kLineThreads>(B, pl_s.tw, CWC);
+    if (stage == 2) {
+      fftc<T, 1, NL, true, CWC, kLineThreads>(B, pl_s.tw, CWC);
+    } else if (stage == 1) {
+      // z pass: the multiplier and the Parseval sum on the last forward
+      // pass's outputs, then the inverse transform
+      const T m0 = sp.m0b ? (T)sp.m0b[b] : sp.m0_t, m1 = sp.m1b ? (T)sp.m1b[b] : sp.m1_t;
+      ZMul<T> mul{LC, WC, LL, sp.lamj[j], m0, m1, sp.invN_t, store, T(0), 0, &acc};
+      fftc<T, -1, NL, true, CWC, kLineThreads>(B, pl_s.tw, CWC, mul);
+      acc.add(mul.part);
+      if (store) {
+        __syncthreads();
+        fftc<T, 1, NL, true, CWC, kLineThreads>(B, pl_s.tw, CWC);
+      }
+    } else {
+      fftc<T, -1, NL, true, CWC, kLineThreads>(B, pl_s.tw, CWC);
+    }
   } else {
     if (stage == 2) fft_lines<T, 1, FL>(B, pl_s, nc, 1, nc, true);
     else fft_lines<T, -1, FL>(B, pl_s, nc, 1, nc, true);
   }
-  Acc<T> acc;
-  if (stage == 1) {
+  if (stage == 1 && NL == 0) {
     const T m0 = sp.m0b ? (T)sp.m0b[b] : sp.m0_t, m1 = sp.m1b ? (T)sp.m1b[b] : sp.m1_t;
     const T invN = sp.invN_t;
     const T lj = sp.lamj[j];
@@ -311,20 +366,19 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
     for (int i = threadIdx.x; i < n; i += bd) {
       const int kl = dc.div(i), c = i - kl * ncs;
       if (c >= nc) continue;
-      const T den = m0 + m1 * (sp.lamc[x0 + c] + lj + sp.laml[kl]);
+      const T den = m0 + m1 * (LC[c] + lj + LL[kl]);
       T m;
       if constexpr (sizeof(T) == 4) m = den > T(0) ? __fdividef(1.0f, den) : T(0);
       else m = den > T(0) ? T(1) / den : T(0);
       const cx<T> w = B[i];
-      part += sp.wcol[x0 + c] * m * (w.re * w.re + w.im * w.im);
+      part += WC[c] * m * (w.re * w.re + w.im * w.im);
       if (++cnt == 16) { acc.add(part); part = T(0); cnt = 0; }
       if (store) B[i] = scal(w, m * invN);
     }
     acc.add(part);
     if (store) {
       __syncthreads();
-      if constexpr (NL > 0) fftc<T, 1, NL, true, CWC, kLineThreads>(B, pl_s.tw, CWC);
-      else fft_lines<T, 1, FL>(B, pl_s, nc, 1, nc, true);
+      fft_lines<T, 1, FL>(B, pl_s, nc, 1, nc, true);
     }
   }
   if (store) {
@@ -387,7 +441,7 @@ cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage
   const int nset = axis == 1 ? nz : ny;
   const long long set_stride = axis == 1 ? (long long)ny * nxs : nxs;
   const long long line_stride = axis == 1 ? nxs : (long long)ny * nxs;
-  const size_t sm = (size_t)nl * CW * sizeof(cx<T>) + tw_smem_bytes<T>(nl);
+  const size_t sm = (size_t)nl * CW * sizeof(cx<T>) + tw_smem_bytes<T>(nl) + (size_t)(nl + 2 * CW) * sizeof(T);
   static std::atomic<int> cfg{0};
   cudaError_t e = set_smem3(k3_lines<T, FL, NL, CWC>, sm, cfg);
   if (e != cudaSuccess) return e;
