@@ -199,31 +199,4 @@ static __device__ __forceinline__ bool col_active(int mode, const int* pmode, co
   return true;
 }
 
-// publish_partials / gather_partials for launches whose blocks of one
-// problem are not just blockIdx.x: this block writes slot `slot` of `total`.
-template <int K>
-__device__ __forceinline__ bool publish_partials_at(const double (&v)[K], double* partials, int slot,
-                                                    int total, unsigned int* counter) {
-  __shared__ int am_last;
-  if (flat_tid() == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) partials[(size_t)slot * K + k] = v[k];
-    const unsigned int prev = ticket_acq_rel(counter);
-    am_last = (prev == (unsigned int)total - 1);
-  }
-  __syncthreads();
-  return am_last != 0;
-}
-
-template <int K>
-__device__ __forceinline__ void gather_partials_n(double (&tot)[K], const double* partials, int total,
-                                                  unsigned int* counter, double* scratch) {
-  double v[K];
-  sum_partials_ordered<K>(v, partials, total);
-  block_sum<K>(v, scratch);
-#pragma unroll
-  for (int k = 0; k < K; ++k) tot[k] = v[k];
-  if (flat_tid() == 0) *counter = 0u;
-}
-
 }  // namespace fftmech

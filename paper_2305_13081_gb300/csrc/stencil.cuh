@@ -10,8 +10,6 @@
 // direction and of the z-differenced stress (or flux) components.
 #pragma once
 
-#include <atomic>
-
 #include <algorithm>
 
 #include "fftmech_internal.cuh"
@@ -19,9 +17,6 @@
 #include "pcg_dev.cuh"
 
 namespace fftmech {
-
-
-static __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 template <typename T, int D>
 __device__ __forceinline__ void sten_views(Op<T>& op, Vec2<T>& v, int b, size_t N) {
@@ -35,8 +30,6 @@ __device__ __forceinline__ void sten_views(Op<T>& op, Vec2<T>& v, int b, size_t 
   v.sc += b;
 }
 
-// Wrap an index at most one period outside [0, n).
-static __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // ---------------------------------------------------------------- 2D
 // One warp takes a strip of kStrip2 = 30 columns and TY rows: lane l holds
