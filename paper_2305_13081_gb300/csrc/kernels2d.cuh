@@ -187,7 +187,7 @@ __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* 
     for (int k = 0; k < 8; ++k) {
       const int ii = i + k * bd;
       if (ii < n) {
-        const int y = dc.div(ii), c = ii - y * ncs;
+        const int y = NY > 0 ? ii / (CWC > 0 ? CWC : 1) : dc.div(ii), c = ii - y * ncs;
         t[k] = c < nc ? S[(size_t)y * nx + x0 + c] : mk(T(0), T(0));
       }
     }
@@ -239,7 +239,7 @@ __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* 
   }
   if (store) {
     for (int i = threadIdx.x; i < n; i += bd) {
-      const int y = dc.div(i), c = i - y * ncs;
+      const int y = NY > 0 ? i / (CWC > 0 ? CWC : 1) : dc.div(i), c = i - y * ncs;
       if (c < nc) S[(size_t)y * nx + x0 + c] = B[i];
     }
   }

@@ -326,7 +326,7 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
     for (int k = 0; k < 8; ++k) {
       const int ii = i + k * bd;
       if (ii < n) {
-        const int y = dc.div(ii), c = ii - y * ncs;
+        const int y = NL > 0 ? ii / (CWC > 0 ? CWC : 1) : dc.div(ii), c = ii - y * ncs;
         t[k] = c < nc ? Sj[(size_t)y * line_stride + x0 + c] : mk(T(0), T(0));
       }
     }
@@ -383,7 +383,7 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
   }
   if (store) {
     for (int i = threadIdx.x; i < n; i += bd) {
-      const int y = dc.div(i), c = i - y * ncs;
+      const int y = NL > 0 ? i / (CWC > 0 ? CWC : 1) : dc.div(i), c = i - y * ncs;
       if (c < nc) Sj[(size_t)y * line_stride + x0 + c] = B[i];
     }
   }
