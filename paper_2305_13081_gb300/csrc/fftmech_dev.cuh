@@ -254,19 +254,6 @@ __device__ __forceinline__ void g2s_async(E* dst, const E* src, int n) {
 }
 __device__ __forceinline__ void g2s_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Ask for the 128-byte lines of src[0, n) to be brought into L1 (no
-// register holds the data; the later loads hit L1). Every address touched is
-// inside the range. The block's threads share the lines.
-template <typename E>
-__device__ __forceinline__ void prefetch_l1(const E* src, int n) {
-  constexpr int PER = 128 / (int)sizeof(E);
-  const int lines = (n + PER - 1) / PER + 1;  // + 1: src need not start a line
-  for (int j = threadIdx.x; j < lines; j += blockDim.x) {
-    const E* a = src + min(j * PER, n - 1);
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-  }
-}
-
 // Contiguous shared -> global copy.
 template <typename E>
 __device__ __forceinline__ void s2g(E* __restrict__ dst, const E* __restrict__ src, int n) {

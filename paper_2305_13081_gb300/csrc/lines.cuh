@@ -238,28 +238,6 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   const int u_only = v.mode ? (v.mode[bp] == 1) : 0;
   line_views<T, D>(op, v, bp, N, sst);
   if (done_flag(v.sc)) return;
-  if (v.nsten > 0) {
-    // the block's inputs start moving into L1 while it sums the stencil's
-    // partials (the reduction's loads and these overlap)
-    const int pl0 = blockIdx.x * L;
-    const int pn = min(L, nlines - pl0) * nx;
-    const size_t pt0 = (size_t)pl0 * nx;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const size_t gc = (size_t)c * N + pt0;
-      prefetch_l1(v.p_in + gc, pn);
-      if constexpr (sizeof(T) == 4) {
-        prefetch_l1(v.uh + gc, pn);
-        prefetch_l1(v.ul + gc, pn);
-      } else {
-        prefetch_l1(v.u + gc, pn);
-      }
-      if (!u_only) {
-        prefetch_l1(v.r + gc, pn);
-        prefetch_l1(v.q + gc, pn);
-      }
-    }
-  }
   double alpha = 0.0;
   float ah = 0.f, al = 0.f;
   if (v.nsten > 0) {
