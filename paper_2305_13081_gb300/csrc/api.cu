@@ -488,13 +488,14 @@ fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Sp
     FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 0));
     FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_TRUENORM));
     if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-    // problems whose float recursion met tol while the true residual did not:
-    // continue from the true residual with a fresh direction
+    // problems whose float recursion met tol while the FP64 true residual did
+    // not: continue from the true residual with a fresh direction (at most
+    // three restarts)
     bool any = false;
     for (int b = 0; b < B; ++b) {
       const SolverScalars& q = ctx->h_sc[b];
       const bool gate = reliable && q.status == FFTMECH_OK && restart < 3 && q.iter < ctx->opts.max_iter &&
-                        q.rz_true > 4.0 * q.tol2 * q.rz0;
+                        q.rz_true > q.tol2 * q.rz0;
       ctx->h_mode[b] = gate ? 2 : 0;
       if (gate) {
         const int zero = 0;
