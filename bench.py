@@ -477,10 +477,11 @@ def mixed_main(args, torch, fm, device, rank, world, dist):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields / f64 iterates+reductions",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"mixed-batch-{n3}x3x3-{n2}x2x2-transient-staggered", "problems": len(ws),
-                   "voxels": voxels, "groups": prof_run["groups"], "precision": "mixed", "tol": 1e-8,
+                   "voxels": voxels, "groups": prof_run["groups"],
+                   "precision": "mixed: f32 fields and FFTs, double-float iterate and reductions", "tol": 1e-8,
                    "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before each timed step",
                    "parallelism": f"{world} independent replicas; one context per grid size, "
                                   "stepped concurrently (one host thread and stream each)",
@@ -637,10 +638,12 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields / f64 iterates+reductions",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": workload_name(w, args.batch), "voxels": N,
-                   "seed": w.extra.get("seed", SEED), "precision": "mixed", "tol": w.tol,
+                   "seed": w.extra.get("seed", SEED),
+                   "precision": "mixed: f32 fields and FFTs, double-float iterate and reductions",
+                   "tol": w.tol,
                    "porosity": w.extra["porosity"], "steps_per_run": w.steps,
                    "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before each timed step",
                    "parallelism": f"{world} independent RVE replicas",
