@@ -140,10 +140,8 @@ bool choose_shape(const HostPlan& px, const HostPlan& py, int nsm, size_t optin_
   if (fixed) {
     // compile-time column plans (512 threads, several butterflies each):
     // 64-byte (or 32-byte for 2187) row segments; 4 columns when the batch
-    // has fewer than two 8-column strips per SM, 2 columns (256-thread
-    // blocks) when it has fewer than two 4-column strips per SM
+    // has fewer than two 8-column strips per SM
     if (ny >= 1024 || (long long)((nx + 7) / 8) * batch < 2LL * nsm) CW = 4;
-    if ((long long)((nx + 3) / 4) * batch < 2LL * nsm) CW = 2;
     if (col_smem(CW) > optin) return false;
     s.cols = CW;
     s.threads_col = 512;
