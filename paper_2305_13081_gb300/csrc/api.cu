@@ -1,4 +1,4 @@
-// C ABI of libfftmech: contexts, FFT plans, workspace, the PCG driver and the
+// C ABI of libfftmech: contexts, FFT plans, workspace, the PCG loop and the
 // entry points declared in include/fftmech.h.
 #include <cmath>
 #include <cstdarg>
@@ -278,7 +278,7 @@ fftmech_status push_modes(fftmech_ctx* ctx) {
   return FFTMECH_OK;
 }
 
-// ---------------------------------------------------------------- PCG driver
+// ---------------------------------------------------------------- PCG loop
 struct Solve {
   int iters = 0;
   int status = FFTMECH_OK;

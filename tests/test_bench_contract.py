@@ -1,6 +1,6 @@
 """The benchmark script's JSON contract, checked on the CPU: the reference
-arm (the oracle timed on the host cores) prints one line with the keys the
-benchmark driver reads, and the GPU arm refuses to run without a CUDA
+arm (the oracle timed on the host cores) prints one line with the keys of
+the benchmark contract, and the GPU arm refuses to run without a CUDA
 device instead of falling back to the CPU."""
 
 import json
