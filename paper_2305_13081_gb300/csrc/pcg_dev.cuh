@@ -96,22 +96,24 @@ __device__ __forceinline__ void store_deferred_partial(Acc<T>& acc, double* slot
 // kDeferredWidth threads take part in a fixed pattern (thread t sums
 // partials t, t + W, ... in order; then a shuffle tree in each of the W / 32
 // warps; then the warp totals in order), so the total does not depend on the
-// block size of the kernel that forms it. The block needs >= W threads.
+// block size of the kernel that forms it nor on the unrolling. The block
+// needs >= W threads.
 constexpr int kDeferredWidth = 128;
 template <typename T>
 __device__ __forceinline__ double deferred_total(const double* partials, int n, float* redf, double* red) {
   constexpr int W = kDeferredWidth;
+  constexpr int UN = 8;  // loads in flight per thread: up to 1024 partials in one round trip
   const int tid = flat_tid(), lane = tid & 31, wid = tid >> 5;
   if constexpr (sizeof(T) == 4) {
     const float2* p2 = reinterpret_cast<const float2*>(partials);
     dfloat s{0.f, 0.f};
     if (tid < W) {
-      for (int b0 = tid; b0 < n; b0 += 4 * W) {
-        float2 x[4];
+      for (int b0 = tid; b0 < n; b0 += UN * W) {
+        float2 x[UN];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = b0 + j * W < n ? __ldcg(p2 + b0 + j * W) : make_float2(0.f, 0.f);
+        for (int j = 0; j < UN; ++j) x[j] = b0 + j * W < n ? __ldcg(p2 + b0 + j * W) : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < UN; ++j)
           if (b0 + j * W < n) s = df_add(s, dfloat{x[j].x, x[j].y});
       }
 #pragma unroll
@@ -136,12 +138,12 @@ __device__ __forceinline__ double deferred_total(const double* partials, int n, 
   } else {
     double s = 0.0;
     if (tid < W) {
-      for (int b0 = tid; b0 < n; b0 += 4 * W) {
-        double x[4];
+      for (int b0 = tid; b0 < n; b0 += UN * W) {
+        double x[UN];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = b0 + j * W < n ? __ldcg(partials + b0 + j * W) : 0.0;
+        for (int j = 0; j < UN; ++j) x[j] = b0 + j * W < n ? __ldcg(partials + b0 + j * W) : 0.0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < UN; ++j)
           if (b0 + j * W < n) s += x[j];
       }
 #pragma unroll
