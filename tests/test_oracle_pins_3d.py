@@ -5,13 +5,16 @@ homogeneous media (a uniform load is the solution; the per-mode closed form
 of the equilibrium with a heterogeneous eigenstrain), laminates (Reuss and
 harmonic / arithmetic means exact), closed forms of the positive energy
 density, the exact phase field of a uniform history, and the backward-Euler
-decay of single Fourier modes."""
+decay of single Fourier modes; and brute-force dense solves of the same
+discrete equations on a small two-phase grid."""
 
 import numpy as np
 import pytest
 
 from microstructures.workloads import Materials
 from oracle import spectral, elasticity, diffusion, phasefield
+
+import dense_reference as dense
 
 H = 5e-6
 MAT = Materials()
@@ -146,3 +149,47 @@ def test_transient_single_mode_decay_3d(k):
     lam_k /= h ** 2
     c1 = diffusion.transient_step(np.ones(shape, np.uint8), c0, mat, dt, h)
     assert np.abs(c1 - c0 / (1 + Dc * dt * lam_k)).max() < 1e-13
+
+
+# ---------------------------------------------------------------- dense direct solves in 3D
+# The same discrete equations assembled from real-space forward differences
+# and solved directly (tests/dense_reference.py), on a small two-phase grid
+# with damage, eigenstrain and a full macro strain.
+
+
+@pytest.fixture(scope="module")
+def small_case_3d():
+    rng = np.random.default_rng(11)
+    phase = (rng.random((4, 5, 6)) > 0.35).astype(np.uint8)
+    eig = np.where(phase == 0, 1e-3 + 2e-4 * rng.standard_normal(phase.shape), 0.0)
+    dmg = np.clip(0.5 * rng.random(phase.shape), 0, 1)
+    return phase, eig, dmg
+
+
+def test_dense_equilibrium_3d(small_case_3d):
+    phase, eig, dmg = small_case_3d
+    g = phasefield.degradation(dmg, MAT.kappa)
+    E = [2e-4, -1e-4, 3e-4, 5e-5, -4e-5, 6e-5]
+    ref = dense.elastic(phase, eig, g, E, MAT, H)
+    out = elasticity.equilibrium_solve(phase, eig, g, E, MAT, H, tol=1e-14)
+    assert rel(out["strain"], ref["strain"]) < 1e-10
+    assert rel(out["stress"], ref["stress"]) < 1e-10
+
+
+def test_dense_diffusion_3d(small_case_3d):
+    phase, _, _ = small_case_3d
+    G = (1.0, 0.3, -0.2)
+    ref = dense.homogenise(phase, MAT, G, 1.0, 1.0)
+    out = diffusion.homogenise(phase, MAT, G, 1.0, 1.0, tol=1e-14)
+    assert rel(out["c"], ref["c"]) < 1e-11
+    assert rel(out["grad_c"], ref["grad_c"]) < 1e-11
+    assert np.allclose(out["mean_flux"], ref["mean_flux"], rtol=1e-10)
+
+
+def test_dense_phasefield_3d(small_case_3d):
+    phase, _, _ = small_case_3d
+    rng = np.random.default_rng(12)
+    Hf = 1e5 * rng.random(phase.shape) ** 4
+    ref = dense.phasefield(Hf, MAT, H)
+    d, _ = phasefield.phasefield_solve(Hf, MAT, H, tol=1e-14)
+    assert rel(d, ref) < 1e-11
