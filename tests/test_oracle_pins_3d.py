@@ -193,3 +193,15 @@ def test_dense_phasefield_3d(small_case_3d):
     ref = dense.phasefield(Hf, MAT, H)
     d, _ = phasefield.phasefield_solve(Hf, MAT, H, tol=1e-14)
     assert rel(d, ref) < 1e-11
+
+
+def test_random_sponge_seeded_and_in_window():
+    from microstructures import random_sponge, porosity
+
+    p1, a1 = random_sponge(27, 0.35, 5)
+    p2, a2 = random_sponge(27, 0.35, 5)
+    assert p1.shape == (27, 27, 27) and p1.dtype == np.uint8
+    assert a1 == a2 and np.array_equal(p1, p2)
+    assert abs(porosity(p1) - 0.35) <= 0.02
+    p3, _ = random_sponge(27, 0.35, 6)
+    assert not np.array_equal(p1, p3)
