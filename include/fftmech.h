@@ -331,11 +331,15 @@ fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse,
  * FFTMECH_FFT_NOALLOC_MAX_N; larger sizes return
  * FFTMECH_ERR_UNSUPPORTED_SIZE before any work.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. All calls share the array and it keeps the last call's twiddles:
- * two calls whose transforms overlapped on the GPU would race, so calls are
- * serialised by a process-wide lock and each returns only after its
- * transform has completed on `stream`. */
+ * device, with that device current). No call may be made while `stream` is
+ * being captured into a CUDA graph (or, in global capture mode, while any
+ * stream is): every call copies from a host buffer and synchronises
+ * `stream`, which a capture does not allow (the capture would be
+ * invalidated). All calls share the array and it keeps the last call's
+ * twiddles: two calls whose transforms overlapped on the GPU would race, so
+ * calls are serialised by a process-wide lock and each returns only after
+ * its copies and transform have completed on `stream` (also when it returns
+ * an error). */
 #define FFTMECH_FFT_NOALLOC_MAX_N 2187
 fftmech_status fftmech_fft_noalloc(int ndim, const int n[3], int precision, int inverse,
                                    void* data, void* stream);

@@ -71,10 +71,7 @@ bool on_device(const void* p) {
 }
 
 template <typename T>
-cudaError_t run(HostPlan& px, HostPlan& py, int inverse, void* data, int nsm, size_t optin,
-                cudaStream_t st) {
-  Shape2 sh{};
-  if (!choose_shape_fft<T>(px, py, nsm, optin, sh)) return cudaErrorInvalidConfiguration;
+cudaError_t run(HostPlan& px, HostPlan& py, int inverse, void* data, const Shape2& sh, cudaStream_t st) {
   const int nx = px.n, ny = py.n;
   cudaError_t e = launch_rowfft_f<T>(px.fam, nx, ny, (cx<T>*)data, dev_plan<T>(px), inverse, sh, st);
   if (e == cudaSuccess && ny > 1) {
@@ -110,6 +107,12 @@ extern "C" fftmech_status fftmech_fft_noalloc(int ndim, const int n[3], int prec
   fill_twiddles(py, g_tw + kMaxN);
   cudaStream_t st = (cudaStream_t)stream;
   const bool fp64 = precision == FFTMECH_FP64;
+  // launch shapes first: a size the kernels cannot take is rejected before
+  // anything is queued on the stream
+  Shape2 sh{};
+  const bool shp = fp64 ? choose_shape_fft<double>(px, py, nsm, (size_t)optin, sh)
+                        : choose_shape_fft<float>(px, py, nsm, (size_t)optin, sh);
+  if (!shp) return FFTMECH_ERR_UNSUPPORTED_SIZE;
   px.tw_d = reinterpret_cast<cx<double>*>(base);
   py.tw_d = reinterpret_cast<cx<double>*>(base + kSlotD);
   px.tw_f = reinterpret_cast<cx<float>*>(base + 2 * kSlotD);
@@ -124,7 +127,7 @@ extern "C" fftmech_status fftmech_fft_noalloc(int ndim, const int n[3], int prec
     e = cudaMemcpyAsync(px.tw_d, g_stage, tw_smem_bytes<double>(nx), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(py.tw_d, g_stage + kSlotD, tw_smem_bytes<double>(ny), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = run<double>(px, py, inverse, data, nsm, (size_t)optin, st);
+    if (e == cudaSuccess) e = run<double>(px, py, inverse, data, sh, st);
   } else {
     fill_slot<float>(px, g_tw, g_stage + 2 * kSlotD);
     fill_slot<float>(py, g_tw + kMaxN, g_stage + 2 * kSlotD + kSlotF);
@@ -132,11 +135,12 @@ extern "C" fftmech_status fftmech_fft_noalloc(int ndim, const int n[3], int prec
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(py.tw_f, g_stage + 2 * kSlotD + kSlotF, tw_smem_bytes<float>(ny), cudaMemcpyHostToDevice,
                           st);
-    if (e == cudaSuccess) e = run<float>(px, py, inverse, data, nsm, (size_t)optin, st);
+    if (e == cudaSuccess) e = run<float>(px, py, inverse, data, sh, st);
   }
-  if (e == cudaErrorInvalidConfiguration) return FFTMECH_ERR_UNSUPPORTED_SIZE;
-  // the transform completes before the lock is released, so the next call
-  // cannot overwrite twiddles that are still being read
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // Whatever happened after the first copy was queued, the stream is drained
+  // before the lock is released: the next call may then overwrite the array
+  // and the host image without racing with copies or transforms of this one.
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = es;
   return e == cudaSuccess ? FFTMECH_OK : FFTMECH_ERR_CUDA;
 }

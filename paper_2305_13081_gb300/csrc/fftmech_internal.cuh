@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <utility>
 
 #include "fftmech_dev.cuh"
@@ -42,6 +43,32 @@ cudaError_t launch_dep(void (*kernel)(KA...), dim3 grid, dim3 block, size_t smem
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+// Opt a kernel into the device's full dynamic shared memory. The attribute
+// is per device, so the flag that skips repeated calls is one bit per device
+// (devices 0..63; a device beyond that is configured on every call).
+// Launches then pass their own, smaller, sizes.
+struct SmemOptIn {
+  std::atomic<unsigned long long> done{0};
+};
+template <typename K>
+static cudaError_t opt_in_smem(K kernel, size_t bytes, SmemOptIn& flag) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (flag.done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in limit
+  if ((long long)bytes > (long long)dyn_max) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  if (e == cudaSuccess && bit) flag.done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 // Scalars of one PCG run, resident in device memory. The last block of a

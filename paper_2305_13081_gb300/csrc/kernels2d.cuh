@@ -315,33 +315,14 @@ __global__ void FFTMECH_BOUNDS(T) k_rowfft(int nx, int ny, cx<T>* S, FftPlanDev<
 }
 
 // ---------------------------------------------------------------- launchers
-// Opt every row / column kernel into the device's full dynamic shared memory
-// once per process (launches then pass their own, smaller, sizes).
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes, std::atomic<int>& configured) {
-  if (configured) return cudaSuccess;
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, kernel);
-  if (e != cudaSuccess) return e;
-  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in limit
-  if ((long long)bytes > (long long)dyn_max) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
-  if (e == cudaSuccess) configured = 1;
-  return e;
-}
 
 template <typename T, int D, int FX>
 cudaError_t launch_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
                             const Shape2& sh, int zero_u, int filter, cudaStream_t st) {
   const int R = sh.rows_res;
   const size_t sm = smem_residual<T, D>(op.nx, R) + tw_smem_bytes<T>(op.nx);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem(k_residual<T, D, FX>, sm, cfg);
+  static SmemOptIn cfg;
+  cudaError_t e = opt_in_smem(k_residual<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid((op.ny + R - 1) / R, sh.batch);
   return launch_dep(k_residual<T, D, FX>, grid, dim3(sh.threads_res), sm, st, op, v, px, R, zero_u, filter);
@@ -353,8 +334,8 @@ cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, co
                            SolverScalars* sc, const int* pmode, cudaStream_t st) {
   const int CW = sh.cols;
   const size_t sm = (size_t)ny * CW * sizeof(cx<T>) + tw_smem_bytes<T>(ny) + (size_t)(ny + CW) * sizeof(T);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem(k_colpass<T, FY, NY, CWC>, sm, cfg);
+  static SmemOptIn cfg;
+  cudaError_t e = opt_in_smem(k_colpass<T, FY, NY, CWC>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid((nx + CW - 1) / CW, sh.batch > 0 ? sh.batch : 1);
   return launch_dep(k_colpass<T, FY, NY, CWC>, grid, dim3(NY > 0 ? kColThreads : sh.threads_col), sm, st, nx, ny,
@@ -366,8 +347,8 @@ cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int
                           const Shape2& sh, cudaStream_t st) {
   const int R = sh.rows_update;
   const size_t sm = (size_t)R * nx * sizeof(cx<T>) + tw_smem_bytes<T>(nx);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem(k_rowfft<T, FX>, sm, cfg);
+  static SmemOptIn cfg;
+  cudaError_t e = opt_in_smem(k_rowfft<T, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const int grid = (ny + R - 1) / R;
   k_rowfft<T, FX><<<grid, sh.threads_update, sm, st>>>(nx, ny, S, px, R, inverse);

@@ -398,31 +398,14 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename K>
-static cudaError_t set_smem3(K kernel, size_t bytes, std::atomic<int>& configured) {
-  if (configured) return cudaSuccess;
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, kernel);
-  if (e != cudaSuccess) return e;
-  const int dyn_max = optin - (int)fa.sharedSizeBytes;
-  if ((long long)bytes > (long long)dyn_max) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
-  if (e == cudaSuccess) configured = 1;
-  return e;
-}
 
 template <typename T, int D, int FX>
 cudaError_t launch3_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const Shape3& sh,
                              int zero_u, int filter, cudaStream_t st) {
   const int R = sh.ry_res, Z = sh.zc_res;
   const size_t sm = Row3Layout(op.nx, R, 8, (int)sizeof(T), D).total + tw_smem_bytes<T>(op.nx);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem3(k3_residual<T, D, FX>, sm, cfg);
+  static SmemOptIn cfg;
+  cudaError_t e = opt_in_smem(k3_residual<T, D, FX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid(((op.ny + R - 1) / R) * ((op.nz + Z - 1) / Z), sh.batch);
   return launch_dep(k3_residual<T, D, FX>, grid, dim3(sh.thr_res), sm, st, op, v, px, R, Z, sh.sst, zero_u,
@@ -442,8 +425,8 @@ cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage
   const long long set_stride = axis == 1 ? (long long)ny * nxs : nxs;
   const long long line_stride = axis == 1 ? nxs : (long long)ny * nxs;
   const size_t sm = (size_t)nl * CW * sizeof(cx<T>) + tw_smem_bytes<T>(nl) + (size_t)(nl + 2 * CW) * sizeof(T);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem3(k3_lines<T, FL, NL, CWC>, sm, cfg);
+  static SmemOptIn cfg;
+  cudaError_t e = opt_in_smem(k3_lines<T, FL, NL, CWC>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid(nset * ((nxs + CW - 1) / CW), sh.batch);
   return launch_dep(k3_lines<T, FL, NL, CWC>, grid, dim3(NL > 0 ? kLineThreads : thr), sm, st, S, sh.sst, nset,

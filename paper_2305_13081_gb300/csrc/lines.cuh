@@ -427,31 +427,14 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename K>
-static cudaError_t set_smem_l(K kernel, size_t bytes, std::atomic<int>& configured) {
-  if (configured) return cudaSuccess;
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, kernel);
-  if (e != cudaSuccess) return e;
-  const int dyn_max = optin - (int)fa.sharedSizeBytes;
-  if ((long long)bytes > (long long)dyn_max) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
-  if (e == cudaSuccess) configured = 1;
-  return e;
-}
 
 template <typename T, int D, int FX, int DIM, int NX>
 cudaError_t launch_xdir(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
                         cudaStream_t st) {
   const int L = ls.L_dir;
   const size_t sm = xdir_smem<T>(op.nx, L, D, DIM);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem_l(k_xdir<T, D, FX, DIM, NX>, sm, cfg);
+  static SmemOptIn cfg;
+  cudaError_t e = opt_in_smem(k_xdir<T, D, FX, DIM, NX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const int nlines = op.ny * op.nz;
   const dim3 grid((nlines + L - 1) / L, ls.batch);
@@ -463,8 +446,8 @@ cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& 
                         cudaStream_t st) {
   const int L = ls.L_upd;
   const size_t sm = xupd_smem<T>(op.nx, L, D, DIM);
-  static std::atomic<int> cfg{0};
-  cudaError_t e = set_smem_l(k_xupd<T, D, FX, DIM, NX>, sm, cfg);
+  static SmemOptIn cfg;
+  cudaError_t e = opt_in_smem(k_xupd<T, D, FX, DIM, NX>, sm, cfg);
   if (e != cudaSuccess) return e;
   const int nlines = op.ny * op.nz;
   const dim3 grid((nlines + L - 1) / L, ls.batch);

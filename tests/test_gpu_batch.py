@@ -126,9 +126,9 @@ def test_batched_staggered_step_matches_oracle():
     strain = bufs["strain"].cpu().numpy().reshape(B, 3, n, n)
     d = bufs["damage"].cpu().numpy().reshape(B, n, n)
     for b in range(B):
-        assert rel(c[b], refs[b]["c"]) < 1e-10
-        assert rel(strain[b], refs[b]["strain"]) < 1e-9
-        assert rel(d[b], refs[b]["d"]) < 1e-9
+        errs = (rel(c[b], refs[b]["c"]), rel(strain[b], refs[b]["strain"]), rel(d[b], refs[b]["d"]))
+        print("batched staggered problem", b, errs)
+        assert max(errs) < 1e-10
     assert refs[0]["eig"].max() > 0 and refs[0]["d"].max() > 1e-4
 
 

@@ -1,0 +1,120 @@
+"""Mixed-precision drift over the full transient carpet workload: 729 x 729
+random carpet (seed 2305), left-face source, 200 staggered steps of
+transient diffusion -> precipitate eigenstrain -> equilibrium -> history ->
+phase field (Algorithm 1).
+
+Tracks run in lockstep, each in its own context and buffers:
+- F12: the FP64 path solved to a 1e-12 relative residual (the converged
+  FP64 result the tolerances refer to);
+- F8: the FP64 path at the workload's tolerance 1e-8;
+- M8, M9: the mixed path at 1e-8 and 1e-9.
+Every 10 steps the relative L2 differences of strain, stress and
+concentration and the max-abs difference of damage against F12 are taken
+on the device. The curve is printed and, when FFTMECH_DRIFT_OUT names a
+file, written there as JSON.
+
+The stated bounds are relative L2 1e-5 on strain and stress, 1e-6 on the
+concentration and 1e-4 max-abs on damage, for the mixed path at the
+workload's tolerance, at every recorded step.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from microstructures.workloads import carpet_transient
+from paper_2305_13081_gb300 import build
+from paper_2305_13081_gb300 import fftmech as fm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    fm.load_library()
+
+
+class Track:
+    def __init__(self, w, prec, tol, phase, mask):
+        self.prec, self.tol = prec, tol
+        N = w.phase.size
+        ft = torch.float64 if prec == fm.FFTMECH_FP64 else torch.float32
+        self.ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=tol,
+                              max_iter=100000)
+        self.bufs = {k: torch.zeros(m * N, dtype=dt, device="cuda") for k, m, dt in
+                     [("c", 1, torch.float64), ("c_ppt", 1, ft), ("eig", 1, ft), ("u", 2, torch.float64),
+                      ("strain", 3, ft), ("stress", 3, ft), ("H", 1, ft), ("damage", 1, torch.float64)]}
+        self.bufs["phase"] = phase
+        self.st = fm.fftmech_state()
+        for k, v in self.bufs.items():
+            setattr(self.st, k, v.data_ptr())
+        self.p = fm.fftmech_step_params()
+        self.p.diffusion_mode = fm.FFTMECH_DIFF_TRANSIENT
+        self.p.dt = w.dt
+        self.p.dirichlet_mask = mask.data_ptr()
+        self.p.dirichlet_value = w.dirichlet_value
+        self.p.eig_mode = fm.FFTMECH_EIG_FROM_PRECIPITATE
+        self.ms = 0.0
+        self.iters = 0
+
+    def step(self):
+        infos = fm.fftmech_staggered_step(self.ctx.handle, self.st, self.p)
+        assert all(i.status == fm.FFTMECH_OK for i in infos), [i.status for i in infos]
+        self.ms += sum(i.device_ms for i in infos)
+        self.iters += sum(i.iters for i in infos)
+
+    def f(self, k):
+        return self.bufs[k].double()
+
+
+def rel(a, b):
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def test_mixed_drift_over_200_steps():
+    w = carpet_transient(729)
+    phase = torch.as_tensor(w.phase.ravel()).cuda()
+    mask = torch.as_tensor(w.dirichlet_mask.ravel()).cuda()
+    tracks = {"F12": Track(w, fm.FFTMECH_FP64, 1e-12, phase, mask),
+              "F8": Track(w, fm.FFTMECH_FP64, w.tol, phase, mask),
+              "M8": Track(w, fm.FFTMECH_MIXED, w.tol, phase, mask),
+              "M9": Track(w, fm.FFTMECH_MIXED, 1e-9, phase, mask)}
+    curve = []
+    for s in range(1, w.steps + 1):
+        for t in tracks.values():
+            t.step()
+        if s % 10 == 0 or s == 1:
+            torch.cuda.synchronize()
+            ref = tracks["F12"]
+            row = {"step": s}
+            for name in ("F8", "M8", "M9"):
+                t = tracks[name]
+                row[name] = {"strain": rel(t.f("strain"), ref.f("strain")),
+                             "stress": rel(t.f("stress"), ref.f("stress")),
+                             "c": rel(t.f("c"), ref.f("c")),
+                             "damage_maxabs": float((t.f("damage") - ref.f("damage")).abs().max())}
+            row["M8_vs_F8_stress"] = rel(tracks["M8"].f("stress"), tracks["F8"].f("stress"))
+            row["max_damage"] = float(ref.f("damage").max())
+            row["max_eig"] = float(ref.f("eig").max())
+            curve.append(row)
+            print(json.dumps(row))
+    summary = {name: {"device_ms": t.ms, "iters": t.iters} for name, t in tracks.items()}
+    print(json.dumps(summary))
+    out = os.environ.get("FFTMECH_DRIFT_OUT")
+    if out:
+        with open(out, "w") as fh:
+            json.dump({"curve": curve, "summary": summary}, fh, indent=1)
+    for t in tracks.values():
+        t.ctx.close()
+    worst = {k: max(r["M8"][k] for r in curve) for k in ("strain", "stress", "c", "damage_maxabs")}
+    print("worst M8 vs F12:", worst)
+    assert worst["strain"] < 1e-5 and worst["stress"] < 1e-5
+    assert worst["c"] < 1e-6
+    assert worst["damage_maxabs"] < 1e-4

@@ -54,6 +54,18 @@ def test_noalloc_matches_fft_on_two_calls_in_a_row(precision):
     assert _pair((1, 2187), precision, 0, 3) < tol
 
 
+@pytest.mark.parametrize("precision", [fm.FFTMECH_FP64, fm.FFTMECH_MIXED])
+def test_noalloc_largest_plans_in_both_directions(precision):
+    """The array's largest plan (2187 points) as the column and as the row
+    transform, and a power of two near the limit (2048, so the slot is used
+    up to its last pass multipliers), each against fftmech_fft."""
+    tol = 1e-13 if precision == fm.FFTMECH_FP64 else 2e-6
+    assert _pair((2187, 81), precision, 0, 4) < tol
+    assert _pair((81, 2187), precision, 1, 5) < tol
+    assert _pair((8, 2048), precision, 0, 6) < tol
+    assert _pair((2048, 8), precision, 1, 7) < tol
+
+
 def test_noalloc_rejects_sizes_beyond_its_array():
     t = torch.zeros((2, 4096), dtype=torch.complex128, device="cuda")
     with pytest.raises(fm.FftmechError) as ei:
