@@ -36,7 +36,12 @@
  *   workspace (allocated in fftmech_create, freed in fftmech_destroy).
  * - Synchronisation: every compute entry point enqueues its work on the
  *   context's CUDA stream and returns after that work has completed, with
- *   `info` filled in on the host.
+ *   `info` filled in on the host; fftmech_staggered_step_async returns at
+ *   once and its reports are read with fftmech_step_info.
+ * - Allocation: with device pointers no call after fftmech_create
+ *   allocates device memory. Host pointers are staged through device
+ *   buffers that the library allocates on first use (kept until
+ *   fftmech_destroy).
  * - Errors: argument errors return before any work is enqueued. Solver
  *   outcomes (converged, not converged, non-finite) are returned as the
  *   status and also stored in info->status. A CUDA failure returns
@@ -65,7 +70,9 @@ typedef enum {
   FFTMECH_ERR_UNSUPPORTED_SIZE = 2, /* grid size not 2^a 3^b in [2, 4096], or dim unsupported */
   FFTMECH_ERR_NOT_CONVERGED = 3,    /* PCG hit max_iter before tol */
   FFTMECH_ERR_NONFINITE = 4,        /* NaN/Inf residual or breakdown */
-  FFTMECH_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+  FFTMECH_ERR_TIMEOUT = 5,          /* reserved: the library has no device-side waits (its loops
+                                       are conditional graph nodes bounded by max_iter), so no
+                                       call returns it */
   FFTMECH_ERR_CUDA = 6,
   FFTMECH_ERR_OOM = 7
 } fftmech_status;
@@ -102,21 +109,34 @@ typedef struct {
 /* PCG controls. Stop when the gradient-space residual norm (the paper's CG
  * residual, equal to sqrt(r.M^-1 r) of the potential PCG) has dropped by
  * `tol` relative to that of the right-hand side, or after max_iter
- * iterations (status NOT_CONVERGED). replace_residual (MIXED only, 0/1):
- * reliable updates; at every host poll (every check_every iterations) the
- * library checks whether r.M^-1 r has fallen 100-fold since the last
- * replacement and, if so, replaces the float recursive residual by the FP64
- * true residual b - K u at the next iteration (search direction kept).
+ * iterations (status NOT_CONVERGED).
+ * replace_residual (MIXED only, 0/1): reliable updates; after every
+ * iteration the device checks whether r.M^-1 r has fallen 100-fold since
+ * the last replacement and, if so, replaces the float recursive residual by
+ * the FP64 true residual b - K u in the next iteration (search direction
+ * kept). After convergence of the float recursion the FP64 true residual is
+ * checked; a problem whose true residual misses tol continues from it (at
+ * most three times).
+ * Every decision of the loop is taken on the device. execution:
+ * FFTMECH_EXEC_GRAPH (0, default) runs each call as one CUDA graph whose
+ * loops are conditional nodes (no host synchronisation inside a solve or a
+ * staggered step; the graph is captured on the first call and re-captured
+ * when the arguments change); FFTMECH_EXEC_HOST runs the same kernels with
+ * the host driving the loops, reading the device's decisions after every
+ * iteration (slower; used with per-launch profiling). Both give
+ * bit-identical results. check_every is not used (kept for the layout).
  * launch_mode: 0 (default) launches the kernels of a PCG iteration as
  * programmatic dependent launches (each kernel starts launching while the
  * previous one finishes and waits on the device for its results); 1 uses
  * plain stream order. Both give bit-identical results. */
+enum { FFTMECH_EXEC_GRAPH = 0, FFTMECH_EXEC_HOST = 1 };
 typedef struct {
   double tol;
   int max_iter;
   int replace_residual;
   int check_every;
   int launch_mode;
+  int execution;
 } fftmech_solver_opts;
 
 /* Per-solve report (host struct). All averages in FP64 over every voxel. */
@@ -268,16 +288,117 @@ fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
                                       const fftmech_step_params* params,
                                       fftmech_solve_info* info);
 
-/* Staggered steps of several contexts at once: a batch of uneven grids is
- * one uniform-batch context per grid size (Sec. 3.2 treats every RVE as an
- * independent problem). Each context's step (fftmech_staggered_step) runs
- * on its own host thread and its own stream, so the GPU overlaps the
- * contexts' kernels; the call returns when all have finished. states[i],
- * params[i] and infos[i] (3 * fftmech_batch_size(ctxs[i]) records) belong
- * to ctxs[i]; contexts must be distinct and use distinct streams. Returns
- * INVALID_ARG for bad arguments, else the first hard error (INVALID_ARG,
- * CUDA, OOM) of any context, else the first solver status that is not OK.
+/* Asynchronous staggered step: enqueues the same work as
+ * fftmech_staggered_step on the context's stream and returns without
+ * waiting. Every pointer of `state` and `params` must be device memory
+ * (INVALID_ARG otherwise); nothing is allocated, staged or copied, and the
+ * host does not synchronise. If the stream is being captured (stream
+ * capture into the caller's own CUDA graph), the step is emitted into that
+ * graph, conditional nodes included, and runs whenever the caller launches
+ * it. The reports of the step are written on the device and copied to
+ * library-owned pinned memory at its end; read them with fftmech_step_info.
  * No counterpart in the paper. */
+fftmech_status fftmech_staggered_step_async(fftmech_ctx* ctx, const fftmech_state* state,
+                                            const fftmech_step_params* params);
+
+/* Reports of the last staggered step enqueued on the context (by
+ * fftmech_staggered_step, fftmech_staggered_step_async, or a replay of a
+ * graph that captured it): synchronises the context's stream, then fills
+ * info[3 B] as fftmech_staggered_step does and returns the first solver
+ * status that is not OK. INVALID_ARG if no step was enqueued. */
+fftmech_status fftmech_step_info(fftmech_ctx* ctx, fftmech_solve_info* info);
+
+/* Gradient of an objective of the staggered solve with respect to the
+ * per-voxel eigenstrain field (an extension: the paper solves forward
+ * only). Forward model: `steps` staggered steps (Algorithm 1, Sec. 2.5)
+ * without diffusion, the eigenstrain prescribed as e_s(x) = ramp[s] e(x)
+ * (Eq. eigen-simplify's isotropic eigenstrain), the fixed macro strain
+ * eps_mac (Voigt, NULL = 0), H and d starting at 0. Objective at the last
+ * step: FFTMECH_OBJ_ENERGY, the total elastic energy
+ * sum 1/2 (eps - e I) : sigma h^dim; FFTMECH_OBJ_DAMAGE, the summed damage
+ * sum d. J receives its value and grad[N] (double, device) dJ/de(x), by the
+ * discrete adjoint: per step backwards, a phase-field adjoint solve
+ * (Eq. crack-fft's operator), the derivative through the history max
+ * (where psi+ >= H_prev, ties to psi+) and psi+ of Eq. (energy) (the
+ * derivative of [x]_+ is 1 for x > 0, else 0), an equilibrium adjoint solve
+ * (a PCG on the same operator K = grad+^T g C grad+ with the right-hand side
+ * grad+^T tau), and the explicit dependences on e and on the previous
+ * damage through g(d). Checkpoints of (H, d, u) every `checkpoint_every`
+ * steps; each segment is recomputed forward before its reverse steps.
+ * phase: uint8 [N], e_field: field [N], grad: double [N], all device
+ * memory; ramp[steps] on the host. One problem per context (batch 1).
+ * Allocates its checkpoint and work buffers for the call (about
+ * (20 + 28 n_ckpt + 24 checkpoint_every) bytes per voxel in MIXED 2D).
+ * info_last (3 records, NULL = none): the forward's last step. Returns the
+ * first solver status that is not OK, else OK. */
+enum { FFTMECH_OBJ_ENERGY = 0, FFTMECH_OBJ_DAMAGE = 1 };
+fftmech_status fftmech_adjoint_eigenstrain(fftmech_ctx* ctx, const uint8_t* phase, const void* e_field, int steps,
+                                           const double* ramp, const double eps_mac[6], int objective,
+                                           int checkpoint_every, double* grad, double* J,
+                                           fftmech_solve_info* info_last);
+
+/* Launch-shape autotuner (no counterpart in the paper). Times `iterations`
+ * equilibrium PCG iterations on a synthetic two-phase field of the
+ * context's grid and batch (graph execution, best of two runs per
+ * candidate) for candidate launch shapes: column strip width and stencil
+ * strip rows (2D), stencil brick depth (3D), stencil blocks per problem and
+ * lines per block of the x-line kernels, one parameter at a time from the
+ * best so far. Applies the fastest, and keeps it for the process: contexts
+ * created later for the same device, grid, batch and precision start with
+ * it. Reports the time per iteration before and after (microseconds) and a
+ * description of the shapes (owned by the context). Allocates temporary
+ * device buffers; results of later solves change only within rounding
+ * (the reductions' block partitions change). iterations = 0 only reports
+ * the shapes in use (the description ends in "(autotuned)" when they came
+ * from the process's cache). */
+fftmech_status fftmech_autotune(fftmech_ctx* ctx, int iterations, double* before_us, double* after_us,
+                                const char** choice);
+
+/* Element offset of problem `problem`'s segment in a field with
+ * `components` components per voxel (1 for scalar fields, dim for u, 3 or
+ * 6 for strain and stress) of a batched context: problem * components * N. */
+fftmech_status fftmech_problem_offset(const fftmech_ctx* ctx, int problem, int components, long long* offset);
+
+/* Graph execution counters of a context: graphs captured (or re-captured
+ * after an argument change), graph launches, and the kernels those
+ * launches ran (counted when a call's reports are read: each conditional
+ * body's launches times its executions, from the solves' iteration,
+ * replacement and restart counts; for a batch the largest count of its
+ * problems). disabled = 1 when a graph failed to build or launch and the
+ * context fell back to host-driven execution, with the reason in *reason
+ * (owned by the library). Any pointer may be NULL. */
+fftmech_status fftmech_graph_stats(const fftmech_ctx* ctx, long long* builds, long long* launches,
+                                   long long* kernels, int* disabled, const char** reason);
+
+/* A group of contexts stepped together: a batch of uneven grids is one
+ * uniform-batch context per grid size (Sec. 3.2 treats every RVE as an
+ * independent problem), and the group runs the staggered steps of all of
+ * them as ONE CUDA graph, one parallel branch per context, each branch with
+ * its own device-driven loops; one graph launch per step, no host thread
+ * per context and no host synchronisation inside the step. The graph is
+ * captured on the first fftmech_group_step and again when the arguments
+ * change. Contexts must be distinct, on one device, with distinct streams
+ * (used only while capturing); `stream` (NULL = a new stream owned by the
+ * group) is where the graph runs. No counterpart in the paper. */
+typedef struct fftmech_group fftmech_group;
+fftmech_status fftmech_group_create(fftmech_group** group, fftmech_ctx* const* ctxs, int n, void* stream);
+fftmech_status fftmech_group_destroy(fftmech_group* group);
+/* One staggered step of every context of the group. states[i], params[i]
+ * and infos[i] (3 * fftmech_batch_size(ctxs[i]) records) belong to
+ * context i; every pointer must be device memory (INVALID_ARG otherwise).
+ * Returns after the step has completed: INVALID_ARG or CUDA on failure
+ * (fftmech_group_last_error gives the message), else the first solver
+ * status that is not OK. */
+fftmech_status fftmech_group_step(fftmech_group* group, const fftmech_state* const* states,
+                                  const fftmech_step_params* const* params, fftmech_solve_info* const* infos);
+/* Graphs captured, graph launches and the kernels they ran. */
+fftmech_status fftmech_group_stats(const fftmech_group* group, long long* builds, long long* launches,
+                                   long long* kernels);
+const char* fftmech_group_last_error(const fftmech_group* group);
+
+/* Staggered steps of several contexts at once: a group made for this call
+ * (the graph is captured every time; keep a group to reuse it). Same
+ * arguments and results as fftmech_group_step. No counterpart in the paper. */
 fftmech_status fftmech_staggered_step_many(fftmech_ctx* const* ctxs, int n, fftmech_state* const* states,
                                            const fftmech_step_params* const* params,
                                            fftmech_solve_info* const* infos);
@@ -307,8 +428,11 @@ fftmech_status fftmech_profile_read(fftmech_ctx* ctx, int kclass, long long* lau
 
 /* Stand-alone complex-to-complex FFT with the library's Stockham kernels
  * (the transform every solve uses; exposed for testing and comparison).
- * data: interleaved complex, device memory, n[1] rows of n[0] points (2D,
- * ndim = 2) or one line of n[0] points (ndim = 1), in place.
+ * data: interleaved complex, device memory, C order with n[0] points per
+ * line: one line (ndim = 1), n[1] rows (ndim = 2) or n[2] planes of n[1]
+ * rows (ndim = 3), transformed in place along every axis. The twiddle
+ * tables of a length are made on its first use on a device and kept until
+ * the process exits.
  * precision: FFTMECH_FP64 (complex double) or FFTMECH_MIXED (complex
  * float). inverse = 0: X[k] = sum_j x[j] exp(-2 pi i jk/n); inverse = 1: the
  * same with +i and no 1/n factor. stream: cudaStream_t (NULL = default).
@@ -323,8 +447,9 @@ fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse,
  * whose device memory belongs to another allocator or to a fixed budget (a
  * framework's memory pool, where a raw cudaMalloc can fail or fragment the
  * pool), or code that must not meet an out-of-memory error in mid-run.
- * fftmech_fft allocates its twiddle tables on every call; this entry point
- * keeps them in one fixed device array inside the library instead (about
+ * fftmech_fft allocates the twiddle tables of every new length it meets;
+ * this entry point keeps them in one fixed device array inside the library
+ * instead (about
  * 103 KiB, held on every GPU that loads the library until the process exits)
  * and calls no cudaMalloc, cudaFree or other allocating routine.
  * Same arguments, layout and results as fftmech_fft, with each n[i] at most

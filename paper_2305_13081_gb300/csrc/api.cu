@@ -1,10 +1,14 @@
-// C ABI of libfftmech: contexts, FFT plans, workspace, the PCG loop and the
-// entry points declared in include/fftmech.h.
+// C ABI of libfftmech: contexts, FFT plans, workspace, the device-driven PCG
+// (run as one CUDA graph with conditional nodes, or host-driven with the
+// same kernels) and the entry points declared in include/fftmech.h.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -59,6 +63,27 @@ void free_plan(HostPlan& p) {
   p.tw_d = nullptr;
 }
 
+// Plans of the stand-alone transform, kept per (device, length) for the life
+// of the process (the device twiddles of a length are made on its first use).
+std::mutex g_plan_mu;
+std::map<std::pair<int, int>, HostPlan> g_plans;
+
+cudaError_t cached_plan(int dev, int n, HostPlan& out) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  auto it = g_plans.find({dev, n});
+  if (it == g_plans.end()) {
+    HostPlan p;
+    const cudaError_t e = make_plan(n, p);
+    if (e != cudaSuccess) {
+      free_plan(p);
+      return e;
+    }
+    it = g_plans.emplace(std::make_pair(dev, n), p).first;
+  }
+  out = it->second;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- context
@@ -70,6 +95,40 @@ struct Staging {
 enum StageSlot {
   ST_PHASE, ST_EIG, ST_DAMAGE, ST_U, ST_STRAIN, ST_STRESS, ST_C, ST_H, ST_MASK, ST_CPPT,
   ST_EIGFIELD, ST_COUNT
+};
+
+// The three solves of a staggered step; each keeps its own record (solver
+// scalars, post-processing sums, device timestamps) so that one read after
+// the whole step reports all three.
+enum SolveKind { SK_DIFF = 0, SK_EQ = 1, SK_PF = 2, SK_COUNT = 3 };
+// Operations with a cached graph.
+enum OpKind { OP_STEP = 0, OP_DIFF = 1, OP_EQ = 2, OP_PF = 3, OP_COUNT = 4 };
+
+constexpr int kResultsPerProblem = 16;
+
+// Kernel launches of a captured operation: those outside any conditional
+// node, and per solve the launches directly inside each conditional body
+// (one execution of that body). A replay's total follows from the solves'
+// records (iterations, replacements, restarts).
+struct LaunchCount {
+  long long fixed = 0;
+  long long body[SK_COUNT][LF_COUNT] = {};
+};
+
+struct GraphCache {
+  std::vector<unsigned char> key;  // the arguments the graph was captured with
+  cudaGraphExec_t exec = nullptr;
+  LaunchCount lc;
+};
+
+// What the host needs to turn the records of the last operation into
+// fftmech_solve_info (kept when the operation is enqueued).
+struct LastOp {
+  int valid = 0;
+  int ran[SK_COUNT] = {0, 0, 0};
+  int diff_mode = 0;
+  double c_macro = 0.0;
+  const LaunchCount* lc = nullptr;  // the operation ran as this cached graph
 };
 
 struct fftmech_ctx {
@@ -93,7 +152,7 @@ struct fftmech_ctx {
   StenShape sshape{};
   // workspace (B problems back to back)
   void* r = nullptr;
-  void* p[2] = {nullptr, nullptr};
+  void* p = nullptr;     // search direction (updated in place by the direction kernel)
   void* S = nullptr;
   void* q = nullptr;     // K p of the split iteration
   void* g = nullptr;
@@ -111,20 +170,27 @@ struct fftmech_ctx {
   void* wcol1 = nullptr;
   double* partials = nullptr;
   double* partials_col = nullptr;  // 2D column pass (deferred reductions)
-  double* results = nullptr;   // 16 per problem
   double* m0b = nullptr;       // per-problem preconditioner constants
   double* m1b = nullptr;
-  int* mode = nullptr;         // per-problem reliable-update / restart flags
+  int* mode = nullptr;         // per-problem iteration modes (0, 1 reliable update, 2 restart)
   SolverScalars* sc = nullptr;
-  SolverScalars* h_sc = nullptr;   // pinned
-  double* h_results = nullptr;     // pinned
-  int* h_mode = nullptr;           // host copy of the modes, edited freely
-  // pinned ring the mode pushes copy from: an asynchronous copy reads its
-  // pinned source when it runs, so a slot is reused only after its copy ran
-  static constexpr int kModeSlots = 4;
-  int* h_mode_ring = nullptr;
-  cudaEvent_t mode_ev[kModeSlots] = {nullptr, nullptr, nullptr, nullptr};
-  int mode_slot = 0;
+  int* flags = nullptr;        // loop flags (LF_COUNT ints)
+  int* h_flags = nullptr;      // pinned copy read by the host-driven loop
+  // record block: SolverScalars[SK_COUNT][B], double[SK_COUNT][16 B],
+  // unsigned long long[SK_COUNT][2]; copied to the pinned h_rec at the end
+  // of every operation
+  unsigned char* rec = nullptr;
+  unsigned char* h_rec = nullptr;
+  size_t rec_bytes = 0;
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // streams that capture conditional bodies
+  GraphCache gc[OP_COUNT];
+  bool graph_off = false;   // a graph failed to build or launch: host-driven from then on
+  long long graph_builds = 0, graph_launches = 0;
+  long long graph_kernels = 0;  // kernels run by graph replays whose reports were read
+  const LaunchCount* pending_lc = nullptr;  // set by run_op for the operation just enqueued
+  char graph_err[256] = {0};
+  LastOp last;
+  char tune_desc[160] = {0};  // the launch shapes in use (after fftmech_autotune or a cached choice)
   Staging stage[ST_COUNT];
   // instrumentation
   bool prof = false;
@@ -133,13 +199,25 @@ struct fftmech_ctx {
   struct Pending { int k; cudaEvent_t a, b; };
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
-  cudaEvent_t solve_ev[2] = {nullptr, nullptr};
   char err[512] = {0};
 };
 
-namespace {
+// Staggered steps of several contexts as one graph (parallel branches).
+struct fftmech_group {
+  std::vector<fftmech_ctx*> ctxs;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  std::vector<unsigned char> key;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<LaunchCount> lc;
+  long long builds = 0, launches = 0, kernels = 0;
+  char err[512] = {0};
 
-constexpr int kResultsPerProblem = 16;
+};
+
+namespace {
 
 fftmech_status set_err(fftmech_ctx* ctx, fftmech_status s, const char* fmt, ...) {
   if (ctx) {
@@ -158,8 +236,29 @@ fftmech_status set_err(fftmech_ctx* ctx, fftmech_status s, const char* fmt, ...)
       return set_err(ctx, FFTMECH_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
   } while (0)
 
+#define RC(...)                              \
+  do {                                        \
+    const fftmech_status _r = (__VA_ARGS__);  \
+    if (_r != FFTMECH_OK) return _r;          \
+  } while (0)
+
 size_t esize(const fftmech_ctx* ctx) { return ctx->prec == FFTMECH_FP64 ? 8 : 4; }
 int nvoigt(const fftmech_ctx* ctx) { return ctx->dim == 2 ? 3 : 6; }
+
+// record block layout
+size_t rec_sc_off(const fftmech_ctx* c, int k) { return (size_t)k * c->B * sizeof(SolverScalars); }
+size_t rec_res_off(const fftmech_ctx* c, int k) {
+  return (size_t)SK_COUNT * c->B * sizeof(SolverScalars) + (size_t)k * kResultsPerProblem * c->B * sizeof(double);
+}
+size_t rec_stamp_off(const fftmech_ctx* c, int k) {
+  return (size_t)SK_COUNT * c->B * sizeof(SolverScalars) + (size_t)SK_COUNT * kResultsPerProblem * c->B * sizeof(double) +
+         (size_t)k * 2 * sizeof(unsigned long long);
+}
+size_t rec_total(const fftmech_ctx* c) { return rec_stamp_off(c, SK_COUNT); }
+double* res_dev(fftmech_ctx* c, int k) { return reinterpret_cast<double*>(c->rec + rec_res_off(c, k)); }
+unsigned long long* stamp_dev(fftmech_ctx* c, int k) {
+  return reinterpret_cast<unsigned long long*>(c->rec + rec_stamp_off(c, k));
+}
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -171,15 +270,18 @@ bool is_device_ptr(const void* p) {
 }
 
 // Device view of a caller buffer: the pointer itself if it is device memory,
-// else a staging buffer (copied in when `in`). Output copy-back is done by
-// `stage_out`.
+// else a staging buffer (allocated on first use, copied in when `in`).
+// Output copy-back is done by `stage_out`.
 fftmech_status stage_in(fftmech_ctx* ctx, StageSlot slot, const void* ptr, size_t bytes, bool in,
                         void** dev) {
   if (!ptr) { *dev = nullptr; return FFTMECH_OK; }
   if (is_device_ptr(ptr)) { *dev = const_cast<void*>(ptr); return FFTMECH_OK; }
   Staging& s = ctx->stage[slot];
   if (s.bytes < bytes) {
-    if (s.dev) CK(cudaFree(s.dev));
+    if (s.dev) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      CK(cudaFree(s.dev));
+    }
     s.dev = nullptr;
     s.bytes = 0;
     if (cudaMalloc(&s.dev, bytes) != cudaSuccess) {
@@ -214,7 +316,8 @@ cudaEvent_t take_event(fftmech_ctx* ctx) {
   return e;
 }
 
-// Counts one launch of class k and, when profiling, brackets it with events.
+// Counts one launch of class k and, when profiling, brackets it with events
+// (host-driven execution only: profiling turns the graph path off).
 struct ProfScope {
   fftmech_ctx* ctx;
   int k;
@@ -248,511 +351,9 @@ void prof_flush(fftmech_ctx* ctx) {
   ctx->pending.clear();
 }
 
-#define FFTMECH_LAUNCH(KC, CALL) \
-  do {                           \
-    ProfScope _ps(ctx, KC);      \
-    CK(CALL);                    \
-  } while (0)
-
 void lame(double E, double nu, double& lam, double& mu) {
   lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   mu = E / (2.0 * (1.0 + nu));
-}
-
-fftmech_status sync_scalars(fftmech_ctx* ctx) {
-  CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(SolverScalars) * ctx->B, cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  prof_flush(ctx);
-  return FFTMECH_OK;
-}
-
-fftmech_status push_modes(fftmech_ctx* ctx) {
-  const int k = ctx->mode_slot;
-  ctx->mode_slot = (k + 1) % fftmech_ctx::kModeSlots;
-  CK(cudaEventSynchronize(ctx->mode_ev[k]));  // the slot's previous copy has run
-  int* slot = ctx->h_mode_ring + (size_t)k * ctx->B;
-  std::memcpy(slot, ctx->h_mode, sizeof(int) * ctx->B);
-  CK(cudaMemcpyAsync(ctx->mode, slot, sizeof(int) * ctx->B, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaEventRecord(ctx->mode_ev[k], ctx->stream));
-  return FFTMECH_OK;
-}
-
-// ---------------------------------------------------------------- PCG loop
-struct Solve {
-  int iters = 0;
-  int status = FFTMECH_OK;
-  double rel = 0, true_rel = 0;
-};
-
-// Preconditioned CG on the potential for every problem of the batch (see
-// the kernels for the per-iteration launches). The host polls the device
-// scalars every check_every iterations; a problem that has converged (or
-// failed) stops moving while the others continue. MIXED: the iterate is a
-// float pair, with reliable updates and a final FP64 true-residual gate.
-template <typename T, int D>
-fftmech_status run_pcg(fftmech_ctx* ctx, const Op<T>& op_in, double* u, const Spec<T>& sp_in,
-                       std::vector<Solve>& out) {
-  const DepLaunchScope dep(ctx->opts.launch_mode == 0);
-  cudaStream_t st = ctx->stream;
-  const int B = ctx->B;
-  const Shape2& sh = ctx->shape;
-  FftPlanDev<T> px = dev_plan<T>(ctx->px), py = dev_plan<T>(ctx->py);
-  Spec<T> sp = sp_in;
-  sp.lamx = (const T*)ctx->lamx;
-  sp.lamy = (const T*)ctx->lamy;
-  sp.invN = 1.0 / (double)ctx->N;
-  sp.m0_t = (T)sp.m0;
-  sp.m1_t = (T)sp.m1;
-  sp.invN_t = (T)sp.invN;
-  Op<T> op = op_in;  // with the constants rounded to T
-  op.ih_t = (T)(1.0 / op.h);
-  for (int k = 0; k < 2; ++k) {
-    op.lam_t[k] = (T)op.lam[k];
-    op.mu_t[k] = (T)op.mu[k];
-    op.kap_t[k] = (T)op.kap[k];
-  }
-  op.c0c_t = (T)op.c0c;
-  for (int b = 0; b < B; ++b) {
-    SolverScalars h{};
-    h.tol2 = ctx->opts.tol * ctx->opts.tol;
-    h.max_iter = ctx->opts.max_iter;
-    ctx->h_sc[b] = h;
-    ctx->h_mode[b] = 0;
-  }
-  CK(cudaMemcpyAsync(ctx->sc, ctx->h_sc, sizeof(SolverScalars) * B, cudaMemcpyHostToDevice, st));
-  if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-  T* pbuf[2] = {(T*)ctx->p[0], (T*)ctx->p[1]};
-  Vec2<T> v{};
-  v.u = u;
-  v.uh = ctx->uh;
-  v.ul = ctx->ul;
-  v.r = (T*)ctx->r;
-  v.p_in = pbuf[0];
-  v.p_out = pbuf[1];
-  v.S = (cx<T>*)ctx->S;
-  v.q = (T*)ctx->q;
-  v.partials = ctx->partials;
-  v.sc = ctx->sc;
-  v.mode = ctx->mode;
-  // Deferred reductions where the grid is latency-bound (up to 2^21 voxels
-  // per launch): the stencil's <p, K p> summed by the update kernel (2D and
-  // 3D), the column pass's <r, M^-1 r> by the next direction kernel (2D).
-  // Larger grids keep the last-block reductions: there every consumer block
-  // re-reading all partials costs more than the ticket saves.
-  const bool small = (long long)ctx->N * B <= (1LL << 21);
-  const bool defer = small && ctx->dim == 2;
-  const int ncol_blocks = defer ? (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols : 0;
-  v.pcol = ctx->partials_col;
-  v.nsten = !small ? 0
-            : ctx->dim == 2 ? sten2_blocks(ctx->nx, ctx->ny, ctx->sshape)
-                            : sten3_blocks(ctx->nx, ctx->ny, ctx->nz, ctx->sshape);
-  const long long nU = (long long)D * ctx->N * B;
-  const bool mixed = sizeof(T) == 4;
-  if (mixed) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_df_split(nU, u, ctx->uh, ctx->ul, st));
-  const int nx = ctx->nx, ny = ctx->ny;
-  const int fx = ctx->px.fam, fy = ctx->py.fam, fz = ctx->pz.fam;
-  const bool three = ctx->dim == 3;
-  const Shape3& sh3 = ctx->shape3;
-  FftPlanDev<T> pz = dev_plan<T>(ctx->pz);
-  if (three) {
-    sp.lamc = (const T*)(D == 1 ? ctx->lamc1 : ctx->lamc3);
-    sp.wcol = (const T*)(D == 1 ? ctx->wcol1 : ctx->wcol3);
-    sp.lamj = (const T*)ctx->lamy;
-    sp.laml = (const T*)ctx->lamz;
-  }
-  auto residual = [&](int zero_u, int filter) -> cudaError_t {
-    if constexpr (D == 3) return launch3_residual_f<T, 3>(fx, op, v, px, sh3, zero_u, filter, st);
-    else if constexpr (D == 2) return launch_residual_f<T, 2>(fx, op, v, px, sh, zero_u, filter, st);
-    else
-      return three ? launch3_residual_f<T, 1>(fx, op, v, px, sh3, zero_u, filter, st)
-                   : launch_residual_f<T, 1>(fx, op, v, px, sh, zero_u, filter, st);
-  };
-  // split iteration: x-line IFFT + direction, stencil q = K p + alpha,
-  // x-line update + FFT
-  const LineShape& lsh = ctx->lshape;
-  const StenShape& ssh = ctx->sshape;
-  auto direction = [&](const Vec2<T>& va) -> cudaError_t {
-    if constexpr (D == 3) return launch_xdir_f<T, 3, 3>(fx, op, va, px, lsh, st);
-    else if constexpr (D == 2) return launch_xdir_f<T, 2, 2>(fx, op, va, px, lsh, st);
-    else
-      return three ? launch_xdir_f<T, 1, 3>(fx, op, va, px, lsh, st) : launch_xdir_f<T, 1, 2>(fx, op, va, px, lsh, st);
-  };
-  auto stencil = [&](const Vec2<T>& vs) -> cudaError_t {
-    if constexpr (D == 3) return launch_sten3<T, 3>(op, vs, ssh, st);
-    else if constexpr (D == 2) return launch_sten2<T, 2>(op, vs, ssh, st);
-    else return three ? launch_sten3<T, 1>(op, vs, ssh, st) : launch_sten2<T, 1>(op, vs, ssh, st);
-  };
-  auto update = [&](const Vec2<T>& vb) -> cudaError_t {
-    if constexpr (D == 3) return launch_xupd_f<T, 3, 3>(fx, op, vb, px, lsh, st);
-    else if constexpr (D == 2) return launch_xupd_f<T, 2, 2>(fx, op, vb, px, lsh, st);
-    else
-      return three ? launch_xupd_f<T, 1, 3>(fx, op, vb, px, lsh, st) : launch_xupd_f<T, 1, 2>(fx, op, vb, px, lsh, st);
-  };
-  // 2D: one column pass; 3D: y-FFT, z pass (multiplier, <r, M^-1 r>), y-IFFT
-  auto colpass = [&](int mode) -> cudaError_t {
-    if (!three)
-      return launch_colpass_f<T>(fy, nx, ny, v.S, py, sp, sh, mode, 0, ctx->partials_col, ctx->sc, ctx->mode, st);
-    cudaError_t e = launch3_lines_f<T>(fy, v.S, sh3, D, 1, 0, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
-    if (e != cudaSuccess) return e;
-    e = launch3_lines_f<T>(fz, v.S, sh3, D, 2, 1, pz, sp, mode, ctx->partials, ctx->sc, ctx->mode, st);
-    if (e != cudaSuccess || mode == COL_NORM || mode == COL_TRUENORM) return e;
-    return launch3_lines_f<T>(fy, v.S, sh3, D, 1, 2, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
-  };
-  FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(1, 0));
-  FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_NORM));
-  FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 0));
-  FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_INIT));
-  if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-  // a zero right-hand side has the zero solution (outside Dirichlet voxels)
-  for (int b = 0; b < B; ++b) {
-    const SolverScalars& q = ctx->h_sc[b];
-    if (q.rz0 == 0.0 && q.rz > 0.0) {
-      if (op.mask) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "zero right-hand side with a Dirichlet mask");
-      CK(cudaMemsetAsync(u + (size_t)b * D * ctx->N, 0, sizeof(double) * D * ctx->N, st));
-      if (mixed) {
-        CK(cudaMemsetAsync(ctx->uh + (size_t)b * D * ctx->N, 0, sizeof(float) * D * ctx->N, st));
-        CK(cudaMemsetAsync(ctx->ul + (size_t)b * D * ctx->N, 0, sizeof(float) * D * ctx->N, st));
-      }
-      SolverScalars z = q;
-      z.done = 1;
-      z.status = FFTMECH_OK;
-      z.rz = 0.0;
-      CK(cudaMemcpyAsync(ctx->sc + b, &z, sizeof(SolverScalars), cudaMemcpyHostToDevice, st));
-      CK(cudaStreamSynchronize(st));
-      ctx->h_sc[b] = z;
-    }
-  }
-  const int check = std::max(1, ctx->opts.check_every);
-  const bool reliable = mixed && ctx->opts.replace_residual != 0;
-  std::vector<double> rz_rep(B);
-  for (int b = 0; b < B; ++b) rz_rep[b] = ctx->h_sc[b].rz;
-  auto all_done = [&]() {
-    for (int b = 0; b < B; ++b)
-      if (!ctx->h_sc[b].done) return false;
-    return true;
-  };
-  bool pending = false;  // some problem has mode 1 queued for the next iteration
-  bool col_deferred = false;  // the last column pass left its reduction to the next direction kernel
-  int pi = 0;
-  int it = 0;
-  for (int restart = 0;; ++restart) {
-    while (!all_done() && it < ctx->opts.max_iter) {
-      Vec2<T> va = v;
-      va.p_in = pbuf[pi];
-      va.p_out = pbuf[1 - pi];
-      va.ncol = col_deferred ? ncol_blocks : 0;
-      FFTMECH_LAUNCH(FFTMECH_K_DIRECTION, direction(va));
-      Vec2<T> vb = v;
-      vb.p_in = pbuf[1 - pi];
-      vb.defer_rz = col_deferred ? 1 : 0;
-      FFTMECH_LAUNCH(FFTMECH_K_STENCIL, stencil(vb));
-      FFTMECH_LAUNCH(FFTMECH_K_UPDATE, update(vb));
-      const bool replace = pending;
-      // reliable update: u += alpha p only (update kernel), then the FP64 true residual
-      if (replace) FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 1));
-      // a replacement iteration finalises at once (the host reads rz_true next)
-      col_deferred = defer && !replace;
-      FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(col_deferred ? (COL_ITER | COL_DEFER) : COL_ITER));
-      pi = 1 - pi;
-      ++it;
-      if (replace) {
-        for (int b = 0; b < B; ++b) ctx->h_mode[b] = 0;
-        if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-        pending = false;
-      }
-      if (it % check == 0 || it >= ctx->opts.max_iter || replace) {
-        if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-        bool any = false;
-        for (int b = 0; b < B; ++b) {
-          const SolverScalars& q = ctx->h_sc[b];
-          if (replace) rz_rep[b] = q.rz_true > 0 ? q.rz_true : rz_rep[b];
-          if (reliable && !replace && !q.done && q.rz < 1e-2 * rz_rep[b]) {
-            ctx->h_mode[b] = 1;
-            any = true;
-          }
-        }
-        if (any) {
-          if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-          pending = true;
-        }
-      }
-    }
-    // the iteration limit stopped the loop right after a deferred column pass
-    if (col_deferred) {
-      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_col_finalize(ctx->partials_col, ncol_blocks, ctx->sc, B,
-                                                          1.0 / (double)ctx->N, mixed ? 1 : 0, st));
-      col_deferred = false;
-    }
-    // FP64 true residual of every iterate
-    FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 0));
-    FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_TRUENORM));
-    if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-    // problems whose float recursion met tol while the FP64 true residual did
-    // not: continue from the true residual with a fresh direction (at most
-    // three restarts)
-    bool any = false;
-    for (int b = 0; b < B; ++b) {
-      const SolverScalars& q = ctx->h_sc[b];
-      const bool gate = reliable && q.status == FFTMECH_OK && restart < 3 && q.iter < ctx->opts.max_iter &&
-                        q.rz_true > q.tol2 * q.rz0;
-      ctx->h_mode[b] = gate ? 2 : 0;
-      if (gate) {
-        const int zero = 0;
-        CK(cudaMemcpyAsync(&ctx->sc[b].done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-        any = true;
-      }
-    }
-    if (!any) break;
-    if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-    FFTMECH_LAUNCH(FFTMECH_K_RESIDUAL, residual(0, 1));
-    FFTMECH_LAUNCH(FFTMECH_K_COLUMN, colpass(COL_RESTART));
-    for (int b = 0; b < B; ++b) ctx->h_mode[b] = 0;
-    if (push_modes(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-    if (sync_scalars(ctx) != FFTMECH_OK) return FFTMECH_ERR_CUDA;
-    for (int b = 0; b < B; ++b) rz_rep[b] = ctx->h_sc[b].rz;
-    pending = false;
-  }
-  if (mixed) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_df_merge(nU, ctx->uh, ctx->ul, u, st));
-  out.assign(B, Solve());
-  for (int b = 0; b < B; ++b) {
-    const SolverScalars& f = ctx->h_sc[b];
-    out[b].iters = f.iter;
-    out[b].status = f.done ? f.status : FFTMECH_ERR_NOT_CONVERGED;
-    out[b].rel = f.rz0 > 0 ? std::sqrt(std::max(f.rz, 0.0) / f.rz0) : 0.0;
-    out[b].true_rel = f.rz0 > 0 ? std::sqrt(std::max(f.rz_true, 0.0) / f.rz0) : 0.0;
-  }
-  return FFTMECH_OK;
-}
-
-template <typename T>
-void base_op(const fftmech_ctx* ctx, Op<T>& op, const uint8_t* phase) {
-  std::memset(&op, 0, sizeof(op));
-  op.nx = ctx->nx;
-  op.ny = ctx->ny;
-  op.nz = ctx->nz;
-  op.h = ctx->h;
-  op.phase = phase;
-  lame(ctx->mat.E_pore, ctx->mat.nu_pore, op.lam[0], op.mu[0]);
-  lame(ctx->mat.E_solid, ctx->mat.nu_solid, op.lam[1], op.mu[1]);
-  op.src_scale = 1.0;
-}
-
-fftmech_status read_results(fftmech_ctx* ctx) {
-  CK(cudaMemcpyAsync(ctx->h_results, ctx->results, sizeof(double) * kResultsPerProblem * ctx->B,
-                     cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  prof_flush(ctx);
-  return FFTMECH_OK;
-}
-
-// Device time of one solve: events at its start and end on the context stream.
-fftmech_status solve_timer_start(fftmech_ctx* ctx) {
-  CK(cudaEventRecord(ctx->solve_ev[0], ctx->stream));
-  return FFTMECH_OK;
-}
-fftmech_status solve_timer_stop(fftmech_ctx* ctx) {
-  CK(cudaEventRecord(ctx->solve_ev[1], ctx->stream));
-  return FFTMECH_OK;
-}
-double solve_timer_ms(fftmech_ctx* ctx) {
-  float ms = 0.f;
-  if (cudaEventSynchronize(ctx->solve_ev[1]) != cudaSuccess ||
-      cudaEventElapsedTime(&ms, ctx->solve_ev[0], ctx->solve_ev[1]) != cudaSuccess) {
-    cudaGetLastError();
-    return 0.0;
-  }
-  return (double)ms;
-}
-
-// Per-problem info records sit `stride` apart (1 for single solves, 3 in a
-// staggered step).
-fftmech_solve_info& info_at(fftmech_solve_info* info, int b, int stride) { return info[(size_t)b * stride]; }
-
-fftmech_status worst_status(const std::vector<Solve>& s) {
-  fftmech_status w = FFTMECH_OK;
-  for (const Solve& x : s)
-    if (x.status != FFTMECH_OK && w == FFTMECH_OK) w = (fftmech_status)x.status;
-  return w;
-}
-
-void copy_solves(const std::vector<Solve>& s, fftmech_solve_info* info, int stride, double ms) {
-  for (size_t b = 0; b < s.size(); ++b) {
-    fftmech_solve_info& i = info_at(info, (int)b, stride);
-    i.status = s[b].status;
-    i.iters = s[b].iters;
-    i.rel_res = s[b].rel;
-    i.true_rel_res = s[b].true_rel;
-    i.device_ms = ms;
-  }
-}
-
-// ---------------------------------------------------------------- solves
-template <typename T>
-fftmech_status equilibrium_impl(fftmech_ctx* ctx, const uint8_t* phase, const T* eig,
-                                const double* damage, const double* eps_mac, double* u, T* strain,
-                                T* stress, fftmech_solve_info* info, int stride) {
-  cudaStream_t st = ctx->stream;
-  fftmech_status rc = solve_timer_start(ctx);
-  if (rc != FFTMECH_OK) return rc;
-  const int B = ctx->B;
-  const long long NB = ctx->N * B;
-  Op<T> op;
-  base_op<T>(ctx, op, phase);
-  op.eig = eig;
-  for (int k = 0; k < nvoigt(ctx); ++k) op.E[k] = eps_mac[k];
-  if (damage) {
-    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_degradation<T>(NB, damage, ctx->mat.kappa, (T*)ctx->g, st));
-    op.g = (const T*)ctx->g;
-  }
-  Spec<T> sp{};
-  sp.m0 = 0.0;
-  sp.m1 = 1.0 / (ctx->h * ctx->h);
-  std::vector<Solve> s;
-  const bool three = ctx->dim == 3;
-  rc = three ? run_pcg<T, 3>(ctx, op, u, sp, s) : run_pcg<T, 2>(ctx, op, u, sp, s);
-  if (rc != FFTMECH_OK) return rc;
-  if (three)
-    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch3_el_output<T>(op, B, u, strain, stress, ctx->partials, ctx->results, ctx->sc, st));
-  else
-    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_el_output<T>(op, B, u, strain, stress, ctx->partials, ctx->results, ctx->sc, st));
-  if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
-  if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
-  const double ms = solve_timer_ms(ctx);
-  copy_solves(s, info, stride, ms);
-  const double N = (double)ctx->N;
-  const int nv = nvoigt(ctx);
-  const double vox = three ? ctx->h * ctx->h * ctx->h : ctx->h * ctx->h;
-  for (int b = 0; b < B; ++b) {
-    const double* R = ctx->h_results + b * (2 * nv + 1);
-    fftmech_solve_info& i = info_at(info, b, stride);
-    for (int k = 0; k < nv; ++k) {
-      i.mean_stress[k] = R[k] / N;
-      i.mean_strain[k] = R[nv + k] / N;
-    }
-    i.elastic_energy = R[2 * nv] * vox;
-  }
-  return worst_status(s);
-}
-
-template <typename T>
-fftmech_status diffusion_impl(fftmech_ctx* ctx, const uint8_t* phase, int mode,
-                              const double* grad_c_mac, double c_macro, double dt,
-                              const uint8_t* mask, double cD, double* c,
-                              fftmech_solve_info* info, int stride) {
-  cudaStream_t st = ctx->stream;
-  fftmech_status rc = solve_timer_start(ctx);
-  if (rc != FFTMECH_OK) return rc;
-  const int B = ctx->B;
-  const long long NB = ctx->N * B;
-  Op<T> op;
-  base_op<T>(ctx, op, phase);
-  op.h = ctx->h_diff;
-  op.kap[0] = ctx->mat.D_pore;
-  op.kap[1] = ctx->mat.D_solid;
-  const double ih2 = 1.0 / (ctx->h_diff * ctx->h_diff);
-  std::vector<Solve> s;
-  Spec<T> sp{};
-  if (mode == FFTMECH_DIFF_HOMOGENISE) {
-    const bool three = ctx->dim == 3;
-    op.G[0] = grad_c_mac[0];
-    op.G[1] = grad_c_mac[1];
-    op.G[2] = three ? grad_c_mac[2] : 0.0;
-    sp.m0 = 0.0;
-    sp.m1 = ih2;
-    rc = run_pcg<T, 1>(ctx, op, ctx->phi, sp, s);
-    if (rc != FFTMECH_OK) return rc;
-    if (three) {
-      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch3_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials,
-                                                            ctx->results, ctx->sc, st));
-      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch3_diff_write_c(ctx->nx, ctx->ny, ctx->nz, B, phase, ctx->phi,
-                                                           ctx->h_diff, op.G, ctx->results, c, st));
-    } else {
-      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials,
-                                                           ctx->results, ctx->sc, st));
-      FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_diff_write_c(ctx->nx, ctx->ny, B, phase, ctx->phi, ctx->h_diff,
-                                                          op.G[0], op.G[1], ctx->results, c, st));
-    }
-    if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
-    if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
-    copy_solves(s, info, stride, solve_timer_ms(ctx));
-    const int nr = three ? 6 : 5, nd = three ? 3 : 2;
-    for (int b = 0; b < B; ++b) {
-      const double* R = ctx->h_results + b * nr;
-      fftmech_solve_info& i = info_at(info, b, stride);
-      for (int k = 0; k < nd; ++k) i.mean_flux[k] = R[2 + k];
-      i.porosity = R[2 + nd];
-      i.mean_c = c_macro;
-    }
-    return worst_status(s);
-  }
-  // TRANSIENT (backward Euler, not in the paper)
-  if (!(dt > 0)) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "dt must be > 0 for TRANSIENT");
-  // per-problem porosity -> mean diffusivity of the preconditioner (on device)
-  FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_pf_stats(ctx->N, B, phase, nullptr, ctx->partials, ctx->results, ctx->sc,
-                                                  ctx->mat.D_pore, ctx->mat.D_solid, ih2, ctx->m1b, st));
-  if (mask) FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_set_masked(NB, mask, cD, c, st));
-  CK(cudaMemcpyAsync(ctx->cn, c, sizeof(double) * NB, cudaMemcpyDeviceToDevice, st));
-  op.c0c = 1.0 / dt;
-  op.srcd = ctx->cn;
-  op.src_scale = 1.0 / dt;
-  op.mask = mask;
-  sp.m0 = 1.0 / dt;
-  sp.m1b = ctx->m1b;
-  rc = run_pcg<T, 1>(ctx, op, c, sp, s);
-  if (rc != FFTMECH_OK) return rc;
-  if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
-  if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
-  copy_solves(s, info, stride, solve_timer_ms(ctx));
-  for (int b = 0; b < B; ++b)
-    info_at(info, b, stride).porosity = 1.0 - ctx->h_results[b * 3 + 2] / (double)ctx->N;
-  return worst_status(s);
-}
-
-template <typename T>
-fftmech_status phasefield_impl(fftmech_ctx* ctx, const T* strain, const T* eig,
-                               const uint8_t* phase, T* H, double* d, fftmech_solve_info* info,
-                               int stride) {
-  cudaStream_t st = ctx->stream;
-  fftmech_status rc = solve_timer_start(ctx);
-  if (rc != FFTMECH_OK) return rc;
-  const int B = ctx->B;
-  Op<T> op;
-  base_op<T>(ctx, op, phase);
-  const double a = ctx->mat.Gc / (2.0 * ctx->mat.l0);
-  const double b = ctx->mat.Gc * ctx->mat.l0 / 2.0;
-  // history update; m0b[p] = a + mean(H) of each problem (on device)
-  if (ctx->dim == 3)
-    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch3_history<T>(ctx->N, B, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1],
-                                                       strain, eig, H, ctx->Hd, a, ctx->m0b, ctx->partials, ctx->sc,
-                                                       st));
-  else
-    FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_history<T>(ctx->N, B, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1],
-                                                      strain, eig, H, ctx->Hd, a, ctx->m0b, ctx->partials, ctx->sc,
-                                                      st));
-  op.kap[0] = op.kap[1] = b;
-  op.c0c = a;
-  op.c0f = H;
-  op.srcd = ctx->Hd;
-  op.src_scale = 1.0;
-  Spec<T> sp{};
-  sp.m0b = ctx->m0b;
-  sp.m1 = b / (ctx->h * ctx->h);
-  std::vector<Solve> s;
-  rc = run_pcg<T, 1>(ctx, op, d, sp, s);
-  if (rc != FFTMECH_OK) return rc;
-  FFTMECH_LAUNCH(FFTMECH_K_OTHER, launch_pf_stats(ctx->N, B, phase, d, ctx->partials, ctx->results, ctx->sc,
-                                                  0.0, 0.0, 0.0, nullptr, st));
-  if ((rc = solve_timer_stop(ctx)) != FFTMECH_OK) return rc;
-  if ((rc = read_results(ctx)) != FFTMECH_OK) return rc;
-  copy_solves(s, info, stride, solve_timer_ms(ctx));
-  for (int p = 0; p < B; ++p) {
-    const double* R = ctx->h_results + p * 3;
-    fftmech_solve_info& i = info_at(info, p, stride);
-    i.total_damage = R[0];
-    i.frac_damaged = R[2] > 0 ? R[1] / R[2] : 0.0;
-  }
-  return worst_status(s);
 }
 
 fftmech_status check_ctx(fftmech_ctx* ctx) {
@@ -793,8 +394,1175 @@ fftmech_status fill_lam(fftmech_ctx* ctx) {
   return FFTMECH_OK;
 }
 
+
+// ---------------------------------------------------------------- emission
+// Where the launches of an operation go. graph: the stream is capturing into
+// `g` (the context's stream for the top level, a side stream for the body of
+// a conditional node); the loops become conditional nodes whose conditions
+// the kernels set. Otherwise the host drives the same loops and reads the
+// kernels' loop flags from device memory.
+struct Emit {
+  fftmech_ctx* ctx;
+  cudaStream_t st;
+  bool graph;
+  cudaGraph_t g;
+  int depth;
+  LoopCtl ctl;
+  LaunchCount* lc;  // graph mode: launches counted per level
+  int sk;           // solve being emitted
+  int level;        // -1 outside conditional nodes, else the flag of the innermost one
+};
+
+inline void em_count(Emit& em) {
+  if (!em.graph || !em.lc) return;
+  if (em.level < 0) em.lc->fixed += 1;
+  else em.lc->body[em.sk][em.level] += 1;
+}
+
+#define EM_LAUNCH(EM, KC, CALL)        \
+  do {                                 \
+    if (!(EM).graph) {                 \
+      ProfScope _ps(ctx, KC);          \
+      CK(CALL);                        \
+    } else {                           \
+      CK(CALL);                        \
+      em_count(EM);                    \
+    }                                  \
+  } while (0)
+
+Emit eager_emit(fftmech_ctx* ctx) {
+  Emit e{};
+  e.ctx = ctx;
+  e.st = ctx->stream;
+  e.graph = false;
+  e.ctl.flags = ctx->flags;
+  e.ctl.direct = ctx->B == 1;
+  e.lc = nullptr;
+  e.sk = 0;
+  e.level = -1;
+  return e;
+}
+
+// Conditional handle for flag k in the graph being captured (graph mode);
+// `reset`: the condition returns to `value` at every launch of the graph.
+fftmech_status em_handle(Emit& em, int k, bool reset = false, unsigned int value = 0) {
+  if (!em.graph) return FFTMECH_OK;
+  fftmech_ctx* ctx = em.ctx;
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, em.g, value, reset ? cudaGraphCondAssignDefault : 0));
+  em.ctl.h[k] = (unsigned long long)h;
+  em.ctl.have |= 1u << k;
+  return FFTMECH_OK;
+}
+
+// Graph mode: a conditional node (WHILE or IF on flag k) after everything
+// captured so far, its body captured by `body` on a side stream.
+template <typename F>
+fftmech_status em_cond(Emit& em, int k, cudaGraphConditionalNodeType type, F&& body) {
+  fftmech_ctx* ctx = em.ctx;
+  if (em.depth >= 3) return set_err(ctx, FFTMECH_ERR_CUDA, "conditional nodes nested too deeply");
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(em.st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return set_err(ctx, FFTMECH_ERR_CUDA, "stream is not capturing");
+  // the parameter struct holds a union without a default constructor:
+  // zeroed raw storage
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  std::memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = (cudaGraphConditionalHandle)em.ctl.h[k];
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  cudaGraph_t body_g = p.conditional.phGraph_out[0];
+  cudaStream_t side = ctx->side[em.depth];
+  CK(cudaStreamBeginCaptureToGraph(side, body_g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  Emit sub = em;
+  sub.st = side;
+  sub.g = body_g;
+  sub.depth = em.depth + 1;
+  sub.level = k;
+  const fftmech_status rc = body(sub);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(side, &out);
+  if (rc != FFTMECH_OK) return rc;
+  CK(e);
+  CK(cudaStreamUpdateCaptureDependencies(em.st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return FFTMECH_OK;
+}
+
+// Host-driven execution: the kernels' loop flags (synchronises the stream).
+fftmech_status poll_flags(Emit& em, int* out) {
+  fftmech_ctx* ctx = em.ctx;
+  CK(cudaMemcpyAsync(ctx->h_flags, ctx->flags, sizeof(int) * LF_COUNT, cudaMemcpyDeviceToHost, em.st));
+  CK(cudaStreamSynchronize(em.st));
+  prof_flush(ctx);
+  for (int k = 0; k < LF_COUNT; ++k) out[k] = ctx->h_flags[k];
+  return FFTMECH_OK;
+}
+
+// ---------------------------------------------------------------- PCG
+// Preconditioned CG on the potential for every problem of the batch.
+// Launch sequence (graph form; the host-driven form runs the same launches
+// and reads the flags every check_every iterations):
+//   scalars, [MIXED: iterate split], <f, M^-1 f>, first residual, zero-RHS
+//   case, first direction (p = z)               -> LF_LOOP, LF_REPLACE, LF_DONE
+//   WHILE LF_OUTER:
+//     WHILE LF_LOOP (ordinary iterations):
+//       stencil (q = K p, <p, K p>), update (u += alpha p, r -= alpha q,
+//       x-FFT), column pass (multiplier, <r, M^-1 r>), direction
+//     IF LF_REPLACE (reliable update): stencil, update of the iterate only,
+//       FP64 true residual, column pass, direction
+//     IF LF_DONE: FP64 true residual of every iterate, restart gate
+//       IF LF_RESTART: restart from the true residual, first direction
+//   [MIXED: iterate merge]
+// An ordinary iteration has no conditional node inside it, so its kernels
+// stay chained by programmatic dependent launches.
+// Every decision (convergence, iteration limit, reliable update, restart) is
+// taken on the device; a problem that has stopped makes every kernel return
+// at once while the others continue.
+template <typename T, int D>
+fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& sp_in) {
+  fftmech_ctx* ctx = em.ctx;
+  const DepLaunchScope dep(ctx->opts.launch_mode == 0);
+  const int B = ctx->B;
+  FftPlanDev<T> px = dev_plan<T>(ctx->px), py = dev_plan<T>(ctx->py), pz = dev_plan<T>(ctx->pz);
+  Spec<T> sp = sp_in;
+  sp.lamx = (const T*)ctx->lamx;
+  sp.lamy = (const T*)ctx->lamy;
+  sp.invN = 1.0 / (double)ctx->N;
+  sp.m0_t = (T)sp.m0;
+  sp.m1_t = (T)sp.m1;
+  sp.invN_t = (T)sp.invN;
+  Op<T> op = op_in;  // with the constants rounded to T
+  op.ih_t = (T)(1.0 / op.h);
+  for (int k = 0; k < 2; ++k) {
+    op.lam_t[k] = (T)op.lam[k];
+    op.mu_t[k] = (T)op.mu[k];
+    op.kap_t[k] = (T)op.kap[k];
+  }
+  op.c0c_t = (T)op.c0c;
+  const bool three = ctx->dim == 3;
+  if (three) {
+    sp.lamc = (const T*)(D == 1 ? ctx->lamc1 : ctx->lamc3);
+    sp.wcol = (const T*)(D == 1 ? ctx->wcol1 : ctx->wcol3);
+    sp.lamj = (const T*)ctx->lamy;
+    sp.laml = (const T*)ctx->lamz;
+  }
+  Vec2<T> v{};
+  v.u = u;
+  v.uh = ctx->uh;
+  v.ul = ctx->ul;
+  v.r = (T*)ctx->r;
+  v.p_in = (const T*)ctx->p;
+  v.p_out = (T*)ctx->p;
+  v.S = (cx<T>*)ctx->S;
+  v.q = (T*)ctx->q;
+  v.partials = ctx->partials;
+  v.sc = ctx->sc;
+  v.mode = ctx->mode;
+  v.pcol = ctx->partials_col;
+  // Deferred reductions where the grid is latency-bound (up to 2^21 voxels
+  // per launch): the stencil's <p, K p> summed by the update kernel (2D and
+  // 3D), the column pass's <r, M^-1 r> by the next direction kernel (2D).
+  // Larger grids keep the last-block reductions: there every consumer block
+  // re-reading all partials costs more than the ticket saves.
+  const bool small = (long long)ctx->N * B <= (1LL << 21);
+  const bool defer = small && !three;
+  const int ncol_blocks = defer ? (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols : 0;
+  v.nsten = !small ? 0
+            : three ? sten3_blocks(ctx->nx, ctx->ny, ctx->nz, ctx->sshape)
+                    : sten2_blocks(ctx->nx, ctx->ny, ctx->sshape);
+  const long long nU = (long long)D * ctx->N * B;
+  const bool mixed = sizeof(T) == 4;
+  const bool reliable = mixed && ctx->opts.replace_residual != 0;
+  const int fx = ctx->px.fam, fy = ctx->py.fam, fz = ctx->pz.fam;
+  const Shape2& sh = ctx->shape;
+  const Shape3& sh3 = ctx->shape3;
+  const LineShape& lsh = ctx->lshape;
+  const StenShape& ssh = ctx->sshape;
+  auto residual = [&](int zero_u, int filter, cudaStream_t st) -> cudaError_t {
+    if constexpr (D == 3) return launch3_residual_f<T, 3>(fx, op, v, px, sh3, zero_u, filter, st);
+    else if constexpr (D == 2) return launch_residual_f<T, 2>(fx, op, v, px, sh, zero_u, filter, st);
+    else
+      return three ? launch3_residual_f<T, 1>(fx, op, v, px, sh3, zero_u, filter, st)
+                   : launch_residual_f<T, 1>(fx, op, v, px, sh, zero_u, filter, st);
+  };
+  auto direction = [&](const Vec2<T>& va, cudaStream_t st) -> cudaError_t {
+    if constexpr (D == 3) return launch_xdir_f<T, 3, 3>(fx, op, va, px, lsh, st);
+    else if constexpr (D == 2) return launch_xdir_f<T, 2, 2>(fx, op, va, px, lsh, st);
+    else
+      return three ? launch_xdir_f<T, 1, 3>(fx, op, va, px, lsh, st) : launch_xdir_f<T, 1, 2>(fx, op, va, px, lsh, st);
+  };
+  auto stencil = [&](const Vec2<T>& vs, cudaStream_t st) -> cudaError_t {
+    if constexpr (D == 3) return launch_sten3<T, 3>(op, vs, ssh, st);
+    else if constexpr (D == 2) return launch_sten2<T, 2>(op, vs, ssh, st);
+    else return three ? launch_sten3<T, 1>(op, vs, ssh, st) : launch_sten2<T, 1>(op, vs, ssh, st);
+  };
+  auto update = [&](const Vec2<T>& vu, cudaStream_t st) -> cudaError_t {
+    if constexpr (D == 3) return launch_xupd_f<T, 3, 3>(fx, op, vu, px, lsh, st);
+    else if constexpr (D == 2) return launch_xupd_f<T, 2, 2>(fx, op, vu, px, lsh, st);
+    else
+      return three ? launch_xupd_f<T, 1, 3>(fx, op, vu, px, lsh, st) : launch_xupd_f<T, 1, 2>(fx, op, vu, px, lsh, st);
+  };
+  // 2D: one column pass; 3D: y-FFT, z pass (multiplier, <r, M^-1 r>), y-IFFT
+  auto colpass = [&](int mode, cudaStream_t st) -> cudaError_t {
+    if (!three)
+      return launch_colpass_f<T>(fy, ctx->nx, ctx->ny, v.S, py, sp, sh, mode, 0, ctx->partials_col, ctx->sc, ctx->mode,
+                                 st);
+    cudaError_t e = launch3_lines_f<T>(fy, v.S, sh3, D, 1, 0, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
+    if (e != cudaSuccess) return e;
+    e = launch3_lines_f<T>(fz, v.S, sh3, D, 2, 1, pz, sp, mode, ctx->partials, ctx->sc, ctx->mode, st);
+    if (e != cudaSuccess || mode == COL_NORM || mode == COL_TRUENORM) return e;
+    return launch3_lines_f<T>(fy, v.S, sh3, D, 1, 2, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
+  };
+
+  // set-up: scalars, first residual
+  const double tol = ctx->opts.tol;
+  EM_LAUNCH(em, FFTMECH_K_OTHER, launch_sc_init(ctx->sc, B, tol * tol, ctx->opts.max_iter, reliable ? 1 : 0, em.st));
+  if (mixed) EM_LAUNCH(em, FFTMECH_K_OTHER, launch_df_split(nU, u, ctx->uh, ctx->ul, em.st));
+  EM_LAUNCH(em, FFTMECH_K_RESIDUAL, residual(1, 0, em.st));
+  EM_LAUNCH(em, FFTMECH_K_COLUMN, colpass(COL_NORM, em.st));
+  EM_LAUNCH(em, FFTMECH_K_RESIDUAL, residual(0, 0, em.st));
+  EM_LAUNCH(em, FFTMECH_K_COLUMN, colpass(COL_INIT, em.st));
+  EM_LAUNCH(em, FFTMECH_K_OTHER,
+            launch_zero_rhs(u, mixed ? ctx->uh : nullptr, mixed ? ctx->ul : nullptr, (long long)D * ctx->N, ctx->sc, B,
+                            op.mask ? 1 : 0, em.st));
+
+  // first direction after the first residual or a restart (beta = 0)
+  auto first_direction = [&](Emit& e) -> fftmech_status {
+    Vec2<T> va = v;
+    va.ncol = 0;
+    va.ctl = e.ctl;
+    EM_LAUNCH(e, FFTMECH_K_DIRECTION, direction(va, e.st));
+    if (B > 1) EM_LAUNCH(e, FFTMECH_K_OTHER, launch_loopctl(ctx->sc, ctx->mode, B, va.ctl, e.st));
+    return FFTMECH_OK;
+  };
+  // One iteration, ending with the next direction. In a replacement
+  // iteration (not plain) the update kernel moves only the iterate of the
+  // problems in mode 1 and the FP64 true residual becomes their residual.
+  // Ordinary iterations run only while no problem has a replacement due.
+  auto iteration = [&](Emit& e, bool plain) -> fftmech_status {
+    Vec2<T> vi = v;
+    vi.ctl = e.ctl;
+    EM_LAUNCH(e, FFTMECH_K_STENCIL, stencil(vi, e.st));
+    EM_LAUNCH(e, FFTMECH_K_UPDATE, update(vi, e.st));
+    if (!plain) EM_LAUNCH(e, FFTMECH_K_RESIDUAL, residual(0, 1, e.st));
+    EM_LAUNCH(e, FFTMECH_K_COLUMN, colpass(defer ? (COL_ITER | COL_DEFER) : COL_ITER, e.st));
+    vi.ncol = ncol_blocks;
+    EM_LAUNCH(e, FFTMECH_K_DIRECTION, direction(vi, e.st));
+    if (B > 1) EM_LAUNCH(e, FFTMECH_K_OTHER, launch_loopctl(ctx->sc, ctx->mode, B, vi.ctl, e.st));
+    return FFTMECH_OK;
+  };
+  // End of an outer round: FP64 true residual of every problem that has
+  // stopped, and the restart gate (no-ops while some problem is active)
+  const int max_rounds = ctx->opts.max_iter + 64;
+  auto gate = [&](Emit& e) -> fftmech_status {
+    EM_LAUNCH(e, FFTMECH_K_RESIDUAL, residual(0, 2, e.st));
+    EM_LAUNCH(e, FFTMECH_K_COLUMN, colpass(COL_TRUENORM, e.st));
+    EM_LAUNCH(e, FFTMECH_K_OTHER, launch_gate(ctx->sc, ctx->mode, B, e.ctl, max_rounds, e.st));
+    return FFTMECH_OK;
+  };
+  auto restart = [&](Emit& e) -> fftmech_status {
+    EM_LAUNCH(e, FFTMECH_K_RESIDUAL, residual(0, 1, e.st));
+    EM_LAUNCH(e, FFTMECH_K_COLUMN, colpass(COL_RESTART, e.st));
+    EM_LAUNCH(e, FFTMECH_K_OTHER, launch_clear_modes(ctx->mode, B, e.st));
+    return first_direction(e);
+  };
+
+  EM_LAUNCH(em, FFTMECH_K_OTHER, launch_set_flag(em.ctl, LF_OUTER, 1, em.st));
+  RC(first_direction(em));
+  if (em.graph) {
+    // WHILE outer {
+    //   conditions from memory; WHILE loop { ordinary iteration }
+    //   IF replace { replacement iteration }
+    //   true residuals, gate; IF restart { restart, first direction } }
+    // Every condition is set by kernels of its own graph or of a body one
+    // level down.
+    Emit top = em;
+    RC(em_handle(top, LF_OUTER));
+    EM_LAUNCH(top, FFTMECH_K_OTHER, launch_set_flag(top.ctl, LF_OUTER, 1, top.st));
+    RC(em_cond(top, LF_OUTER, cudaGraphCondTypeWhile, [&](Emit& o) -> fftmech_status {
+      RC(em_handle(o, LF_LOOP));
+      RC(em_handle(o, LF_REPLACE));
+      RC(em_handle(o, LF_RESTART));
+      EM_LAUNCH(o, FFTMECH_K_OTHER, launch_sync_flags(o.ctl, o.st));
+      RC(em_cond(o, LF_LOOP, cudaGraphCondTypeWhile, [&](Emit& l) { return iteration(l, true); }));
+      RC(em_cond(o, LF_REPLACE, cudaGraphCondTypeIf, [&](Emit& r) { return iteration(r, false); }));
+      RC(gate(o));
+      return em_cond(o, LF_RESTART, cudaGraphCondTypeIf, restart);
+    }));
+  } else {
+    // the same launches; the host reads the kernels' decisions after every
+    // iteration (an ordinary iteration must not start once a replacement is
+    // due)
+    const long long cap = (long long)ctx->opts.max_iter + 8;  // guard of the host loop
+    int f[LF_COUNT];
+    long long total = 0;
+    for (;;) {
+      EM_LAUNCH(em, FFTMECH_K_OTHER, launch_sync_flags(em.ctl, em.st));
+      RC(poll_flags(em, f));
+      while (f[LF_LOOP]) {
+        RC(iteration(em, true));
+        if (++total > cap) return set_err(ctx, FFTMECH_ERR_CUDA, "PCG loop did not stop within its iteration limit");
+        RC(poll_flags(em, f));
+      }
+      if (f[LF_REPLACE]) {
+        RC(iteration(em, false));
+        if (++total > cap) return set_err(ctx, FFTMECH_ERR_CUDA, "PCG loop did not stop within its iteration limit");
+      }
+      RC(gate(em));
+      RC(poll_flags(em, f));
+      if (!f[LF_OUTER]) break;
+      if (f[LF_RESTART]) RC(restart(em));
+    }
+  }
+  if (mixed) EM_LAUNCH(em, FFTMECH_K_OTHER, launch_df_merge(nU, ctx->uh, ctx->ul, u, em.st));
+  return FFTMECH_OK;
+}
+
+template <typename T>
+void base_op(const fftmech_ctx* ctx, Op<T>& op, const uint8_t* phase) {
+  std::memset(&op, 0, sizeof(op));
+  op.nx = ctx->nx;
+  op.ny = ctx->ny;
+  op.nz = ctx->nz;
+  op.h = ctx->h;
+  op.phase = phase;
+  lame(ctx->mat.E_pore, ctx->mat.nu_pore, op.lam[0], op.mu[0]);
+  lame(ctx->mat.E_solid, ctx->mat.nu_solid, op.lam[1], op.mu[1]);
+  op.src_scale = 1.0;
+}
+
+// Start of a solve's record: device clock.
+fftmech_status rec_begin(Emit& em, int kind) {
+  fftmech_ctx* ctx = em.ctx;
+  EM_LAUNCH(em, FFTMECH_K_OTHER, launch_stamp(stamp_dev(ctx, kind), em.st));
+  return FFTMECH_OK;
+}
+// End of a solve's record: its solver scalars and the device clock.
+fftmech_status rec_end(Emit& em, int kind) {
+  fftmech_ctx* ctx = em.ctx;
+  CK(cudaMemcpyAsync(ctx->rec + rec_sc_off(ctx, kind), ctx->sc, sizeof(SolverScalars) * ctx->B,
+                     cudaMemcpyDeviceToDevice, em.st));
+  EM_LAUNCH(em, FFTMECH_K_OTHER, launch_stamp(stamp_dev(ctx, kind) + 1, em.st));
+  return FFTMECH_OK;
+}
+// End of an operation: the record block to the pinned host copy.
+fftmech_status rec_publish(Emit& em) {
+  fftmech_ctx* ctx = em.ctx;
+  CK(cudaMemcpyAsync(ctx->h_rec, ctx->rec, ctx->rec_bytes, cudaMemcpyDeviceToHost, em.st));
+  return FFTMECH_OK;
+}
+
+// ---------------------------------------------------------------- solves (enqueue)
+template <typename T>
+fftmech_status enqueue_equilibrium(Emit& em, const uint8_t* phase, const T* eig, const double* damage,
+                                   const double* eps_mac, double* u, T* strain, T* stress) {
+  fftmech_ctx* ctx = em.ctx;
+  em.sk = SK_EQ;
+  RC(rec_begin(em, SK_EQ));
+  const int B = ctx->B;
+  const long long NB = ctx->N * B;
+  Op<T> op;
+  base_op<T>(ctx, op, phase);
+  op.eig = eig;
+  for (int k = 0; k < nvoigt(ctx); ++k) op.E[k] = eps_mac[k];
+  if (damage) {
+    EM_LAUNCH(em, FFTMECH_K_OTHER, launch_degradation<T>(NB, damage, ctx->mat.kappa, (T*)ctx->g, em.st));
+    op.g = (const T*)ctx->g;
+  }
+  Spec<T> sp{};
+  sp.m0 = 0.0;
+  sp.m1 = 1.0 / (ctx->h * ctx->h);
+  const bool three = ctx->dim == 3;
+  RC(three ? emit_pcg<T, 3>(em, op, u, sp) : emit_pcg<T, 2>(em, op, u, sp));
+  double* res = res_dev(ctx, SK_EQ);
+  if (three)
+    EM_LAUNCH(em, FFTMECH_K_OTHER, launch3_el_output<T>(op, B, u, strain, stress, ctx->partials, res, ctx->sc, em.st));
+  else
+    EM_LAUNCH(em, FFTMECH_K_OTHER, launch_el_output<T>(op, B, u, strain, stress, ctx->partials, res, ctx->sc, em.st));
+  return rec_end(em, SK_EQ);
+}
+
+template <typename T>
+fftmech_status enqueue_diffusion(Emit& em, const uint8_t* phase, int mode, const double* grad_c_mac, double c_macro,
+                                 double dt, const uint8_t* mask, double cD, double* c) {
+  fftmech_ctx* ctx = em.ctx;
+  em.sk = SK_DIFF;
+  if (mode == FFTMECH_DIFF_TRANSIENT && !(dt > 0))
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "dt must be > 0 for TRANSIENT");
+  RC(rec_begin(em, SK_DIFF));
+  const int B = ctx->B;
+  const long long NB = ctx->N * B;
+  const bool three = ctx->dim == 3;
+  Op<T> op;
+  base_op<T>(ctx, op, phase);
+  op.h = ctx->h_diff;
+  op.kap[0] = ctx->mat.D_pore;
+  op.kap[1] = ctx->mat.D_solid;
+  const double ih2 = 1.0 / (ctx->h_diff * ctx->h_diff);
+  double* res = res_dev(ctx, SK_DIFF);
+  Spec<T> sp{};
+  if (mode == FFTMECH_DIFF_HOMOGENISE) {
+    op.G[0] = grad_c_mac[0];
+    op.G[1] = grad_c_mac[1];
+    op.G[2] = three ? grad_c_mac[2] : 0.0;
+    sp.m0 = 0.0;
+    sp.m1 = ih2;
+    RC(emit_pcg<T, 1>(em, op, ctx->phi, sp));
+    if (three) {
+      EM_LAUNCH(em, FFTMECH_K_OTHER, launch3_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials, res,
+                                                           ctx->sc, em.st));
+      EM_LAUNCH(em, FFTMECH_K_OTHER, launch3_diff_write_c(ctx->nx, ctx->ny, ctx->nz, B, phase, ctx->phi, ctx->h_diff,
+                                                          op.G, res, c, em.st));
+    } else {
+      EM_LAUNCH(em, FFTMECH_K_OTHER, launch_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials, res,
+                                                          ctx->sc, em.st));
+      EM_LAUNCH(em, FFTMECH_K_OTHER, launch_diff_write_c(ctx->nx, ctx->ny, B, phase, ctx->phi, ctx->h_diff, op.G[0],
+                                                         op.G[1], res, c, em.st));
+    }
+    return rec_end(em, SK_DIFF);
+  }
+  // TRANSIENT (backward Euler, not in the paper): per-problem porosity ->
+  // mean diffusivity of the preconditioner (on device)
+  EM_LAUNCH(em, FFTMECH_K_OTHER, launch_pf_stats(ctx->N, B, phase, nullptr, ctx->partials, res, ctx->sc,
+                                                 ctx->mat.D_pore, ctx->mat.D_solid, ih2, ctx->m1b, em.st));
+  if (mask) EM_LAUNCH(em, FFTMECH_K_OTHER, launch_set_masked(NB, mask, cD, c, em.st));
+  CK(cudaMemcpyAsync(ctx->cn, c, sizeof(double) * NB, cudaMemcpyDeviceToDevice, em.st));
+  op.c0c = 1.0 / dt;
+  op.srcd = ctx->cn;
+  op.src_scale = 1.0 / dt;
+  op.mask = mask;
+  sp.m0 = 1.0 / dt;
+  sp.m1b = ctx->m1b;
+  RC(emit_pcg<T, 1>(em, op, c, sp));
+  return rec_end(em, SK_DIFF);
+}
+
+template <typename T>
+fftmech_status enqueue_phasefield(Emit& em, const T* strain, const T* eig, const uint8_t* phase, T* H, double* d) {
+  fftmech_ctx* ctx = em.ctx;
+  em.sk = SK_PF;
+  RC(rec_begin(em, SK_PF));
+  const int B = ctx->B;
+  Op<T> op;
+  base_op<T>(ctx, op, phase);
+  const double a = ctx->mat.Gc / (2.0 * ctx->mat.l0);
+  const double b = ctx->mat.Gc * ctx->mat.l0 / 2.0;
+  // history update; m0b[p] = a + mean(H) of each problem (on device)
+  if (ctx->dim == 3)
+    EM_LAUNCH(em, FFTMECH_K_OTHER, launch3_history<T>(ctx->N, B, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1],
+                                                      strain, eig, H, ctx->Hd, a, ctx->m0b, ctx->partials, ctx->sc,
+                                                      em.st));
+  else
+    EM_LAUNCH(em, FFTMECH_K_OTHER, launch_history<T>(ctx->N, B, phase, op.lam[0], op.lam[1], op.mu[0], op.mu[1],
+                                                     strain, eig, H, ctx->Hd, a, ctx->m0b, ctx->partials, ctx->sc,
+                                                     em.st));
+  op.kap[0] = op.kap[1] = b;
+  op.c0c = a;
+  op.c0f = H;
+  op.srcd = ctx->Hd;
+  op.src_scale = 1.0;
+  Spec<T> sp{};
+  sp.m0b = ctx->m0b;
+  sp.m1 = b / (ctx->h * ctx->h);
+  RC(emit_pcg<T, 1>(em, op, d, sp));
+  EM_LAUNCH(em, FFTMECH_K_OTHER, launch_pf_stats(ctx->N, B, phase, d, ctx->partials, res_dev(ctx, SK_PF), ctx->sc,
+                                                 0.0, 0.0, 0.0, nullptr, em.st));
+  return rec_end(em, SK_PF);
+}
+
+// Device pointers of one staggered step (after staging).
+struct StepPtrs {
+  const uint8_t* phase;
+  double* c;
+  void* cppt;
+  void* eig;
+  double* u;
+  void* strain;
+  void* stress;
+  void* H;
+  double* d;
+  const uint8_t* mask;
+  const void* eigf;
+};
+
+// One staggered step in Algorithm 1's order (Sec. 2.5).
+template <typename T>
+fftmech_status enqueue_step(Emit& em, const StepPtrs& s, const fftmech_step_params* prm) {
+  fftmech_ctx* ctx = em.ctx;
+  const size_t N = (size_t)ctx->N * ctx->B;
+  // 1. diffusion of chemical species
+  if (prm->diffusion_mode != FFTMECH_DIFF_NONE)
+    RC(enqueue_diffusion<T>(em, s.phase, prm->diffusion_mode, prm->grad_c_mac, prm->c_macro, prm->dt, s.mask,
+                            prm->dirichlet_value, s.c));
+  // 2. precipitation and eigenstrain
+  if (prm->eig_mode == FFTMECH_EIG_FROM_PRECIPITATE)
+    EM_LAUNCH(em, FFTMECH_K_OTHER, launch_precipitate<T>(N, s.phase, s.c, ctx->mat.S_sol, ctx->mat.M_ppt, (T*)s.cppt,
+                                                         (T*)s.eig, em.st));
+  else
+    EM_LAUNCH(em, FFTMECH_K_OTHER, launch_scale_copy<T>(N, (const T*)s.eigf, prm->eig_scale, (T*)s.eig, em.st));
+  // 3. equilibrium with the stiffness degraded by the current damage
+  RC(enqueue_equilibrium<T>(em, s.phase, (const T*)s.eig, s.d, prm->eps_mac, s.u, (T*)s.strain, (T*)s.stress));
+  // 4. history and phase field
+  RC(enqueue_phasefield<T>(em, (const T*)s.strain, (const T*)s.eig, s.phase, (T*)s.H, s.d));
+  return FFTMECH_OK;
+}
+
+// ---------------------------------------------------------------- reports (host)
+fftmech_solve_info& info_at(fftmech_solve_info* info, int b, int stride) { return info[(size_t)b * stride]; }
+
+// Fills the records of solve `kind` (problem b at info[b * stride]) from the
+// pinned copy of the record block; returns the first non-OK status.
+fftmech_status collect(fftmech_ctx* ctx, int kind, fftmech_solve_info* info, int stride) {
+  const SolverScalars* S = reinterpret_cast<const SolverScalars*>(ctx->h_rec + rec_sc_off(ctx, kind));
+  const double* R = reinterpret_cast<const double*>(ctx->h_rec + rec_res_off(ctx, kind));
+  const unsigned long long* t = reinterpret_cast<const unsigned long long*>(ctx->h_rec + rec_stamp_off(ctx, kind));
+  const double ms = t[1] >= t[0] ? (double)(t[1] - t[0]) * 1e-6 : 0.0;
+  const double N = (double)ctx->N;
+  const bool three = ctx->dim == 3;
+  fftmech_status worst = FFTMECH_OK;
+  for (int b = 0; b < ctx->B; ++b) {
+    const SolverScalars& f = S[b];
+    fftmech_solve_info& i = info_at(info, b, stride);
+    i.iters = f.iter;
+    i.status = f.done ? f.status : FFTMECH_ERR_NOT_CONVERGED;
+    i.rel_res = f.rz0 > 0 ? std::sqrt(std::max(f.rz, 0.0) / f.rz0) : 0.0;
+    i.true_rel_res = f.rz0 > 0 ? std::sqrt(std::max(f.rz_true, 0.0) / f.rz0) : 0.0;
+    i.device_ms = ms;
+    if (kind == SK_EQ) {
+      const int nv = nvoigt(ctx);
+      const double* r = R + b * (2 * nv + 1);
+      const double vox = three ? ctx->h * ctx->h * ctx->h : ctx->h * ctx->h;
+      for (int k = 0; k < nv; ++k) {
+        i.mean_stress[k] = r[k] / N;
+        i.mean_strain[k] = r[nv + k] / N;
+      }
+      i.elastic_energy = r[2 * nv] * vox;
+    } else if (kind == SK_DIFF) {
+      if (ctx->last.diff_mode == FFTMECH_DIFF_HOMOGENISE) {
+        const int nr = three ? 6 : 5, nd = three ? 3 : 2;
+        const double* r = R + b * nr;
+        for (int k = 0; k < nd; ++k) i.mean_flux[k] = r[2 + k];
+        i.porosity = r[2 + nd];
+        i.mean_c = ctx->last.c_macro;
+      } else {
+        i.porosity = 1.0 - R[b * 3 + 2] / N;
+      }
+    } else {
+      const double* r = R + b * 3;
+      i.total_damage = r[0];
+      i.frac_damaged = r[2] > 0 ? r[1] / r[2] : 0.0;
+    }
+    if (i.status != FFTMECH_OK && worst == FFTMECH_OK) worst = (fftmech_status)i.status;
+  }
+  return worst;
+}
+
 bool is_hard_error(fftmech_status s) {
   return s == FFTMECH_ERR_CUDA || s == FFTMECH_ERR_OOM || s == FFTMECH_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------- running an operation
+template <typename A>
+void key_add(std::vector<unsigned char>& k, const A& a) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&a);
+  k.insert(k.end(), p, p + sizeof(A));
+}
+
+// Captures `enqueue` into a graph and makes (or updates) the cached
+// executable graph of operation `opk`.
+template <typename F>
+fftmech_status build_graph(fftmech_ctx* ctx, GraphCache& c, const std::vector<unsigned char>& key, F&& enqueue) {
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
+  LaunchCount lc;
+  Emit em = eager_emit(ctx);
+  em.graph = true;
+  em.lc = &lc;
+  cudaStreamCaptureStatus cs;
+  fftmech_status rc = FFTMECH_OK;
+  if (cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &em.g, nullptr, nullptr, nullptr) != cudaSuccess)
+    rc = set_err(ctx, FFTMECH_ERR_CUDA, "cudaStreamGetCaptureInfo failed");
+  if (rc == FFTMECH_OK) rc = enqueue(em);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  if (rc == FFTMECH_OK && e != cudaSuccess)
+    rc = set_err(ctx, FFTMECH_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  if (rc != FFTMECH_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc;
+  }
+  if (c.exec) {
+    cudaGraphExecUpdateResultInfo ri;
+    if (cudaGraphExecUpdate(c.exec, graph, &ri) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(c.exec);
+      c.exec = nullptr;
+    }
+  }
+  cudaError_t ei = cudaSuccess;
+  if (!c.exec) ei = cudaGraphInstantiate(&c.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    c.exec = nullptr;
+    cudaGetLastError();
+    return set_err(ctx, FFTMECH_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+  }
+  c.key = key;
+  c.lc = lc;
+  ctx->graph_builds += 1;
+  return FFTMECH_OK;
+}
+
+// Runs operation `opk` on the context's stream: into the caller's graph when
+// the stream is being captured; as the cached graph (captured again when
+// the arguments changed) by default; host-driven when asked for, while
+// profiling, or after a graph failed (the reason is kept in graph_err).
+// Returns without synchronising.
+template <typename F>
+fftmech_status run_op(fftmech_ctx* ctx, int opk, const std::vector<unsigned char>& key, F&& enqueue) {
+  ctx->pending_lc = nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(ctx->stream, &cs));
+  if (cs == cudaStreamCaptureStatusActive) {
+    Emit em = eager_emit(ctx);
+    em.graph = true;
+    CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &em.g, nullptr, nullptr, nullptr));
+    return enqueue(em);
+  }
+  if (ctx->opts.execution == FFTMECH_EXEC_GRAPH && !ctx->prof && !ctx->graph_off) {
+    GraphCache& c = ctx->gc[opk];
+    fftmech_status rc = FFTMECH_OK;
+    if (!c.exec || c.key != key) rc = build_graph(ctx, c, key, enqueue);
+    if (rc == FFTMECH_OK) {
+      const cudaError_t e = cudaGraphLaunch(c.exec, ctx->stream);
+      if (e == cudaSuccess) {
+        ctx->graph_launches += 1;
+        ctx->pending_lc = &c.lc;
+        return FFTMECH_OK;
+      }
+      cudaGetLastError();
+      set_err(ctx, FFTMECH_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    }
+    if (is_hard_error(rc) && rc != FFTMECH_ERR_CUDA) return rc;  // an argument error, not the graph
+    // the graph path failed: remember why and continue host-driven
+    snprintf(ctx->graph_err, sizeof(ctx->graph_err), "%s", ctx->err);
+    ctx->err[0] = 0;
+    ctx->graph_off = true;
+  }
+  Emit em = eager_emit(ctx);
+  return enqueue(em);
+}
+
+// After the operation: wait for it, then report.
+fftmech_status finish_sync(fftmech_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  return FFTMECH_OK;
+}
+
+// Kernels run by the graph replay of the last operation, from its records:
+// a solve's loop body ran once per iteration (the largest count of the batch),
+// the replacement residual once per scheduled replacement, the outer body
+// once plus once per restart.
+void count_graph_kernels(fftmech_ctx* ctx) {
+  const LaunchCount* lc = ctx->last.lc;
+  if (!lc) return;
+  long long n = lc->fixed;
+  for (int k = 0; k < SK_COUNT; ++k) {
+    if (!ctx->last.ran[k]) continue;
+    const SolverScalars* S = reinterpret_cast<const SolverScalars*>(ctx->h_rec + rec_sc_off(ctx, k));
+    long long it = 0, rep = 0, rst = 0;
+    for (int b = 0; b < ctx->B; ++b) {
+      it = std::max<long long>(it, S[b].iter);
+      rep = std::max<long long>(rep, S[b].nreplace);
+      rst = std::max<long long>(rst, S[b].nrestart);
+    }
+    n += lc->body[k][LF_OUTER] * (1 + rst) + lc->body[k][LF_LOOP] * it + lc->body[k][LF_REPLACE] * rep +
+         lc->body[k][LF_RESTART] * rst;
+  }
+  ctx->graph_kernels += n;
+  ctx->last.lc = nullptr;
+}
+
+bool opts_ok(const fftmech_solver_opts* o) {
+  return o->tol >= 0 && o->max_iter >= 0 && o->launch_mode >= 0 && o->launch_mode <= 1 &&
+         (o->execution == FFTMECH_EXEC_GRAPH || o->execution == FFTMECH_EXEC_HOST);
+}
+
+// Staged device pointers of a staggered step; `all_device`: nothing was
+// staged (every pointer is device memory).
+fftmech_status stage_step(fftmech_ctx* ctx, const fftmech_state* state, const fftmech_step_params* prm, StepPtrs& d,
+                          bool& all_device) {
+  const size_t N = (size_t)ctx->N * ctx->B, es = esize(ctx), nv = nvoigt(ctx);
+  void *dphase, *dc, *dcppt, *deig, *du, *dstrain, *dstress, *dH, *dd, *dmask = nullptr, *deigf = nullptr;
+  RC(stage_in(ctx, ST_PHASE, state->phase, N, true, &dphase));
+  RC(stage_in(ctx, ST_C, state->c, N * 8, true, &dc));
+  RC(stage_in(ctx, ST_CPPT, state->c_ppt, N * es, true, &dcppt));
+  RC(stage_in(ctx, ST_EIG, state->eig, N * es, true, &deig));
+  RC(stage_in(ctx, ST_U, state->u, (size_t)ctx->dim * N * 8, true, &du));
+  RC(stage_in(ctx, ST_STRAIN, state->strain, nv * N * es, true, &dstrain));
+  RC(stage_in(ctx, ST_STRESS, state->stress, nv * N * es, true, &dstress));
+  RC(stage_in(ctx, ST_H, state->H, N * es, true, &dH));
+  RC(stage_in(ctx, ST_DAMAGE, state->damage, N * 8, true, &dd));
+  if (prm->diffusion_mode == FFTMECH_DIFF_TRANSIENT)
+    RC(stage_in(ctx, ST_MASK, prm->dirichlet_mask, N, true, &dmask));
+  if (prm->eig_mode == FFTMECH_EIG_PRESCRIBED) RC(stage_in(ctx, ST_EIGFIELD, prm->eig_field, N * es, true, &deigf));
+  d = StepPtrs{(const uint8_t*)dphase, (double*)dc, dcppt, deig, (double*)du, dstrain, dstress, dH,
+               (double*)dd, (const uint8_t*)dmask, deigf};
+  all_device = dphase == state->phase && dc == state->c && dcppt == state->c_ppt && deig == state->eig &&
+               du == state->u && dstrain == state->strain && dstress == state->stress && dH == state->H &&
+               dd == state->damage && dmask == (const void*)prm->dirichlet_mask && deigf == prm->eig_field;
+  return FFTMECH_OK;
+}
+
+fftmech_status check_step_args(fftmech_ctx* ctx, const fftmech_state* state, const fftmech_step_params* prm) {
+  if (!state || !prm || !state->phase || !state->c || !state->eig || !state->u || !state->strain || !state->stress ||
+      !state->H || !state->damage)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
+  if (prm->diffusion_mode != FFTMECH_DIFF_NONE && prm->diffusion_mode != FFTMECH_DIFF_HOMOGENISE &&
+      prm->diffusion_mode != FFTMECH_DIFF_TRANSIENT)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "diffusion mode %d", prm->diffusion_mode);
+  if (prm->diffusion_mode == FFTMECH_DIFF_TRANSIENT && !(prm->dt > 0))
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "dt must be > 0 for TRANSIENT");
+  if (prm->eig_mode == FFTMECH_EIG_PRESCRIBED && !prm->eig_field)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "eig_field is required for PRESCRIBED");
+  if (prm->eig_mode != FFTMECH_EIG_PRESCRIBED && prm->eig_mode != FFTMECH_EIG_FROM_PRECIPITATE)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "eigenstrain mode %d", prm->eig_mode);
+  return FFTMECH_OK;
+}
+
+// Enqueues one staggered step on device pointers (graph or host-driven).
+fftmech_status step_enqueue(fftmech_ctx* ctx, const StepPtrs& d, const fftmech_step_params* prm) {
+  std::vector<unsigned char> key;
+  key_add(key, d);
+  key_add(key, *prm);
+  key_add(key, ctx->opts);
+  const bool fp64 = ctx->prec == FFTMECH_FP64;
+  RC(run_op(ctx, OP_STEP, key, [&](Emit& em) -> fftmech_status {
+    RC(fp64 ? enqueue_step<double>(em, d, prm) : enqueue_step<float>(em, d, prm));
+    return rec_publish(em);
+  }));
+  ctx->last = LastOp();
+  ctx->last.valid = 1;
+  ctx->last.ran[SK_DIFF] = prm->diffusion_mode != FFTMECH_DIFF_NONE;
+  ctx->last.ran[SK_EQ] = ctx->last.ran[SK_PF] = 1;
+  ctx->last.diff_mode = prm->diffusion_mode;
+  ctx->last.c_macro = prm->c_macro;
+  ctx->last.lc = ctx->pending_lc;
+  return FFTMECH_OK;
+}
+
+// Fills info[3 B] from the records of the last staggered step (the stream
+// has been synchronised).
+fftmech_status step_collect(fftmech_ctx* ctx, fftmech_solve_info* info) {
+  count_graph_kernels(ctx);
+  std::memset(info, 0, sizeof(fftmech_solve_info) * 3 * ctx->B);
+  fftmech_status worst = FFTMECH_OK;
+  for (int k = 0; k < SK_COUNT; ++k) {
+    if (!ctx->last.ran[k]) continue;
+    const fftmech_status s = collect(ctx, k, info + k, 3);
+    if (s != FFTMECH_OK && worst == FFTMECH_OK) worst = s;
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------- adjoint
+// Device buffers of one adjoint call, freed together.
+struct DevBuffers {
+  std::vector<void*> ptrs;
+  bool ok = true;
+  template <typename P>
+  P* get(size_t bytes) {
+    void* p = nullptr;
+    if (!ok || cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<P*>(p);
+  }
+  ~DevBuffers() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+// Solver status of the last solve on the context (one problem).
+fftmech_status last_solve_status(fftmech_ctx* ctx, cudaStream_t st) {
+  SolverScalars h;
+  CK(cudaMemcpyAsync(&h, ctx->sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (!h.done) return FFTMECH_ERR_NOT_CONVERGED;
+  return (fftmech_status)h.status;
+}
+
+// Forward with checkpoints (H, d, u every k steps), then per segment from
+// the last: recompute its steps from the checkpoint keeping strain, H and d
+// of each, and run the reverse steps (phase-field adjoint PCG, history /
+// psi+ kernel, equilibrium adjoint PCG with the prescribed-stress source,
+// accumulation kernel).
+template <typename T>
+fftmech_status adjoint_impl(fftmech_ctx* ctx, const uint8_t* phase, const T* efield, int S, const double* ramp,
+                            const double* E, int objective, int k, double* grad, double* J,
+                            fftmech_solve_info* info_last) {
+  cudaStream_t st = ctx->stream;
+  const long long N = ctx->N;
+  const int dim = ctx->dim, nv = nvoigt(ctx);
+  const size_t es = sizeof(T);
+  const int nck = (S + k - 1) / k;
+  DevBuffers mem;
+  double* c = mem.get<double>(N * 8);
+  T* cppt = mem.get<T>(N * es);
+  T* eig = mem.get<T>(N * es);
+  double* u = mem.get<double>((size_t)dim * N * 8);
+  T* strain = mem.get<T>((size_t)nv * N * es);
+  T* stress = mem.get<T>((size_t)nv * N * es);
+  T* H = mem.get<T>(N * es);
+  double* d = mem.get<double>(N * 8);
+  std::vector<T*> ckH(nck), segH(k), segS(k);
+  std::vector<double*> ckd(nck), cku(nck), segd(k);
+  for (int i = 0; i < nck; ++i) {
+    ckH[i] = mem.get<T>(N * es);
+    ckd[i] = mem.get<double>(N * 8);
+    cku[i] = mem.get<double>((size_t)dim * N * 8);
+  }
+  for (int j = 0; j < k; ++j) {
+    segH[j] = mem.get<T>(N * es);
+    segd[j] = mem.get<double>(N * 8);
+    segS[j] = mem.get<T>((size_t)nv * N * es);
+  }
+  T* tau = mem.get<T>((size_t)nv * N * es);
+  double* dJde = mem.get<double>(N * 8);
+  double* ddirect = mem.get<double>(N * 8);
+  double* dJdd = mem.get<double>(N * 8);
+  double* dJdH = mem.get<double>(N * 8);
+  double* lampf = mem.get<double>(N * 8);
+  double* mu = mem.get<double>((size_t)dim * N * 8);
+  double* scl = mem.get<double>(4 * 8);  // [pf s, pf 1/s, eq s, eq 1/s]
+  unsigned long long* mx = mem.get<unsigned long long>(2 * 8);
+  if (!mem.ok) return set_err(ctx, FFTMECH_ERR_OOM, "adjoint buffers");
+  CK(cudaMemsetAsync(c, 0, N * 8, st));
+  CK(cudaMemsetAsync(u, 0, (size_t)dim * N * 8, st));
+  CK(cudaMemsetAsync(H, 0, N * es, st));
+  CK(cudaMemsetAsync(d, 0, N * 8, st));
+  CK(cudaMemsetAsync(grad, 0, N * 8, st));
+  fftmech_step_params prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.diffusion_mode = FFTMECH_DIFF_NONE;
+  prm.eig_mode = FFTMECH_EIG_PRESCRIBED;
+  prm.eig_field = efield;
+  for (int i = 0; i < nv; ++i) prm.eps_mac[i] = E[i];
+  const StepPtrs sp{phase, c, cppt, eig, u, strain, stress, H, d, nullptr, efield};
+  auto step = [&](int s) -> fftmech_status {
+    prm.eig_scale = ramp[s];
+    RC(step_enqueue(ctx, sp, &prm));
+    RC(finish_sync(ctx));
+    return FFTMECH_OK;
+  };
+  // forward
+  fftmech_status worst = FFTMECH_OK;
+  std::vector<fftmech_solve_info> rec(3);
+  for (int s = 0; s < S; ++s) {
+    if (s % k == 0) {
+      const int i = s / k;
+      CK(cudaMemcpyAsync(ckH[i], H, N * es, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ckd[i], d, N * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(cku[i], u, (size_t)dim * N * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    RC(step(s));
+    const fftmech_status ws = step_collect(ctx, rec.data());
+    if (ws != FFTMECH_OK && worst == FFTMECH_OK) worst = ws;
+  }
+  if (info_last) std::memcpy(info_last, rec.data(), sizeof(fftmech_solve_info) * 3);
+  *J = objective == FFTMECH_OBJ_ENERGY ? rec[1].elastic_energy : rec[2].total_damage;
+  // reverse
+  double lam0, mu0, lam1, mu1;
+  lame(ctx->mat.E_pore, ctx->mat.nu_pore, lam0, mu0);
+  lame(ctx->mat.E_solid, ctx->mat.nu_solid, lam1, mu1);
+  const double a = ctx->mat.Gc / (2.0 * ctx->mat.l0), b = ctx->mat.Gc * ctx->mat.l0 / 2.0;
+  const double vol = dim == 3 ? ctx->h * ctx->h * ctx->h : ctx->h * ctx->h;
+  // Right-hand sides normalised to the forward solves' magnitudes: a stress
+  // at strain 1e-3 (equilibrium) and the energy density at that strain
+  // (phase field), from the solid's stiffness.
+  const double m_solid = lam1 + 2.0 * mu1;
+  const double target_eq = 1e-3 * m_solid, target_pf = 0.5e-6 * m_solid;
+  CK(cudaMemsetAsync(dJdH, 0, N * 8, st));
+  CK(launch_fill(N, objective == FFTMECH_OBJ_DAMAGE ? 1.0 : 0.0, dJdd, st));
+  Emit em = eager_emit(ctx);
+  auto track = [&](fftmech_status s2) {
+    if (s2 != FFTMECH_OK && worst == FFTMECH_OK) worst = s2;
+  };
+  for (int seg = nck - 1; seg >= 0; --seg) {
+    const int s0 = seg * k, s1 = std::min(S, s0 + k);
+    CK(cudaMemcpyAsync(H, ckH[seg], N * es, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d, ckd[seg], N * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(u, cku[seg], (size_t)dim * N * 8, cudaMemcpyDeviceToDevice, st));
+    for (int s = s0; s < s1; ++s) {
+      RC(step(s));
+      const int j = s - s0;
+      CK(cudaMemcpyAsync(segS[j], strain, (size_t)nv * N * es, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(segH[j], H, N * es, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(segd[j], d, N * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    for (int s = s1 - 1; s >= s0; --s) {
+      const int j = s - s0;
+      const T* Hprev = j > 0 ? segH[j - 1] : ckH[seg];
+      const double* dprev = j > 0 ? segd[j - 1] : ckd[seg];
+      // phase-field adjoint: A(H_s) lambda = dJ/dd_s
+      CK(launch_adj_m0b<T>(N, segH[j], a, ctx->m0b, st));
+      {
+        Op<T> op;
+        base_op<T>(ctx, op, phase);
+        op.kap[0] = op.kap[1] = b;
+        op.c0c = a;
+        op.c0f = segH[j];
+        op.srcd = dJdd;
+        op.src_scale = 1.0;
+        Spec<T> spec{};
+        spec.m0b = ctx->m0b;
+        spec.m1 = b / (ctx->h * ctx->h);
+        CK(cudaMemsetAsync(lampf, 0, N * 8, st));
+        CK(launch_adj_normalise<double>(N, dJdd, mx, target_pf, scl, st));
+        RC(emit_pcg<T, 1>(em, op, lampf, spec));
+        track(last_solve_status(ctx, st));
+      }
+      CK(launch_adj_history<T>(dim, N, phase, lam0, lam1, mu0, mu1, segS[j], efield, ramp[s], Hprev, segd[j], lampf,
+                               scl + 1, dJdH, tau, dJde, ddirect, objective == FFTMECH_OBJ_ENERGY && s == S - 1 ? 1 : 0,
+                               dprev, ctx->mat.kappa, vol, st));
+      // equilibrium adjoint: K(d_{s-1}) mu = grad+^T tau
+      CK(launch_degradation<T>(N, dprev, ctx->mat.kappa, (T*)ctx->g, st));
+      {
+        Op<T> op;
+        base_op<T>(ctx, op, phase);
+        op.g = (const T*)ctx->g;
+        op.pre = tau;
+        Spec<T> spec{};
+        spec.m0 = 0.0;
+        spec.m1 = 1.0 / (ctx->h * ctx->h);
+        CK(cudaMemsetAsync(mu, 0, (size_t)dim * N * 8, st));
+        CK(launch_adj_normalise<T>((long long)nv * N, tau, mx + 1, target_eq, scl + 2, st));
+        RC(dim == 3 ? emit_pcg<T, 3>(em, op, mu, spec) : emit_pcg<T, 2>(em, op, mu, spec));
+        track(last_solve_status(ctx, st));
+      }
+      CK(launch_adj_eqpost<T>(dim, ctx->nx, ctx->ny, ctx->nz, phase, lam0, lam1, mu0, mu1, segS[j], efield, ramp[s],
+                              dprev, ctx->mat.kappa, mu, scl + 3, ctx->h, dJde, ddirect, dJdd, grad, st));
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  return worst;
+}
+
+// ---------------------------------------------------------------- launch-shape autotuning
+// Choices of the tunable launch shapes of a context, cached for the process
+// per (device, dimension, grid, batch, precision).
+struct TuneChoice {
+  int L_dir, L_upd, ty, zc, grid, cols;
+};
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune;
+
+TuneKey tune_key(const fftmech_ctx* ctx) {
+  return TuneKey(ctx->device, ctx->dim, ctx->nx, ctx->ny, ctx->nz, ctx->B, (int)ctx->prec);
+}
+
+TuneChoice current_choice(const fftmech_ctx* ctx) {
+  return TuneChoice{ctx->lshape.L_dir, ctx->lshape.L_upd, ctx->sshape.ty, ctx->sshape.zc, ctx->sshape.grid,
+                    ctx->shape.cols};
+}
+
+// The column strip width's thread count and shared memory (2D).
+template <typename T>
+bool cols_ok(const fftmech_ctx* ctx, int cw) {
+  const int ny = ctx->ny;
+  const bool fixed = sizeof(T) == 4 && (ny == 81 || ny == 243 || ny == 729 || ny == 2187 || ny == 128 || ny == 256 ||
+                                        ny == 512 || ny == 1024);
+  if (fixed && cw != 4 && cw != 8) return false;
+  const size_t smem = (size_t)ny * cw * sizeof(cx<T>) + tw_smem_bytes<T>(ny) + (size_t)(ny + cw) * sizeof(T);
+  return cw >= 1 && smem <= ctx->optin - 1024 && (fixed || need_threads(ctx->py, cw) <= 512) &&
+         (size_t)ctx->B * ctx->nx >= (size_t)1;
+}
+
+template <typename T>
+bool choice_ok(const fftmech_ctx* ctx, const TuneChoice& c) {
+  const int spec3 = ctx->dim == 3 ? (int)nxs_of(ctx->nx, 3) : ctx->nx;
+  if (!line_shape_ok<T>(ctx->px, c.L_dir, true, ctx->dim, spec3, ctx->optin)) return false;
+  if (!line_shape_ok<T>(ctx->px, c.L_upd, false, ctx->dim, spec3, ctx->optin)) return false;
+  if (c.L_dir > ctx->ny * ctx->nz || c.L_upd > ctx->ny * ctx->nz || c.grid < 1) return false;
+  if (ctx->dim == 2) return (c.ty == 4 || c.ty == 8) && cols_ok<T>(ctx, c.cols);
+  return c.ty == 4 && c.zc >= 1 && c.zc <= std::min(16, ctx->nz);
+}
+
+// Applies a choice; the cached graphs embed the old shapes and are dropped.
+template <typename T>
+void apply_choice(fftmech_ctx* ctx, const TuneChoice& c) {
+  ctx->lshape.L_dir = c.L_dir;
+  ctx->lshape.thr_dir = line_threads(ctx->px, c.L_dir, ctx->dim);
+  ctx->lshape.L_upd = c.L_upd;
+  ctx->lshape.thr_upd = line_threads(ctx->px, c.L_upd, ctx->dim);
+  ctx->sshape.ty = c.ty;
+  ctx->sshape.zc = c.zc;
+  ctx->sshape.grid = c.grid;
+  if (ctx->dim == 2 && c.cols != ctx->shape.cols) {
+    ctx->shape.cols = c.cols;
+    const int ny = ctx->ny;
+    const bool fixed = sizeof(T) == 4 && (ny == 81 || ny == 243 || ny == 729 || ny == 2187 || ny == 128 ||
+                                          ny == 256 || ny == 512 || ny == 1024);
+    ctx->shape.threads_col = fixed ? 512 : std::min(512, std::max(128, round32(need_threads(ctx->py, c.cols))));
+  }
+  for (GraphCache& g : ctx->gc) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.key.clear();
+  }
+}
+
+// Time of `iterations` equilibrium PCG iterations (graph execution, the
+// iterate reset to zero first), best of two after one warm-up.
+template <typename T>
+fftmech_status time_solve(fftmech_ctx* ctx, const uint8_t* phase, const T* eig, double* u, double* ms_out) {
+  const double E[6] = {0, 0, 0, 0, 0, 0};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  fftmech_status rc = FFTMECH_OK;
+  for (int rep = 0; rep < 3 && rc == FFTMECH_OK; ++rep) {
+    if (cudaMemsetAsync(u, 0, sizeof(double) * ctx->dim * ctx->N * ctx->B, ctx->stream) != cudaSuccess) {
+      rc = FFTMECH_ERR_CUDA;
+      break;
+    }
+    std::vector<unsigned char> key;
+    key_add(key, phase);
+    key_add(key, u);
+    cudaEventRecord(e0, ctx->stream);
+    rc = run_op(ctx, OP_EQ, key, [&](Emit& em) -> fftmech_status {
+      RC(enqueue_equilibrium<T>(em, phase, eig, nullptr, E, u, nullptr, nullptr));
+      return rec_publish(em);
+    });
+    cudaEventRecord(e1, ctx->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = FFTMECH_ERR_CUDA;
+    float ms = 0.f;
+    if (rc == FFTMECH_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = FFTMECH_ERR_CUDA;
+    if (rep > 0) best = std::min(best, (double)ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  *ms_out = best;
+  return rc;
+}
+
+template <typename T>
+fftmech_status autotune_impl(fftmech_ctx* ctx, int iterations, double* before_us, double* after_us) {
+  const size_t NB = (size_t)ctx->N * ctx->B;
+  // synthetic two-phase microstructure (70 % solid, hashed voxel pattern)
+  // with a pore eigenstrain: the kernels' cost does not depend on the data
+  std::vector<uint8_t> hphase(NB);
+  std::vector<T> heig(NB);
+  for (size_t i = 0; i < NB; ++i) {
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    z ^= z >> 31;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 29;
+    hphase[i] = (z % 10) < 7 ? 1 : 0;
+    heig[i] = hphase[i] ? T(0) : T(1e-3);
+  }
+  uint8_t* phase = nullptr;
+  T* eig = nullptr;
+  double* u = nullptr;
+  auto release = [&]() {
+    if (phase) cudaFree(phase);
+    if (eig) cudaFree(eig);
+    if (u) cudaFree(u);
+  };
+  if (cudaMalloc((void**)&phase, NB) != cudaSuccess || cudaMalloc((void**)&eig, NB * sizeof(T)) != cudaSuccess ||
+      cudaMalloc((void**)&u, NB * ctx->dim * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return set_err(ctx, FFTMECH_ERR_OOM, "autotune buffers");
+  }
+  if (cudaMemcpy(phase, hphase.data(), NB, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(eig, heig.data(), NB * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    release();
+    return set_err(ctx, FFTMECH_ERR_CUDA, "autotune buffers");
+  }
+  const fftmech_solver_opts saved = ctx->opts;
+  const bool saved_off = ctx->graph_off;
+  ctx->opts.tol = 0.0;
+  ctx->opts.max_iter = iterations;
+  ctx->opts.execution = FFTMECH_EXEC_GRAPH;
+  TuneChoice best = current_choice(ctx);
+  double best_ms = 0.0;
+  fftmech_status rc = time_solve<T>(ctx, phase, eig, u, &best_ms);
+  const double first_ms = best_ms;
+  auto consider = [&](TuneChoice c) {
+    if (rc != FFTMECH_OK || !choice_ok<T>(ctx, c)) return;
+    apply_choice<T>(ctx, c);
+    double ms = 0.0;
+    rc = time_solve<T>(ctx, phase, eig, u, &ms);
+    if (rc == FFTMECH_OK && ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+    apply_choice<T>(ctx, best);
+  };
+  // coordinate descent: one parameter at a time, each from the best so far
+  if (ctx->dim == 2) {
+    for (int cw : {4, 8, ctx->shape.cols / 2, ctx->shape.cols * 2}) {
+      TuneChoice c = best;
+      if (cw == best.cols || cw < 1) continue;
+      c.cols = cw;
+      consider(c);
+    }
+    {
+      TuneChoice c = best;
+      c.ty = best.ty == 8 ? 4 : 8;
+      consider(c);
+    }
+  } else {
+    for (int zc : {2, 4, 8, 16}) {
+      TuneChoice c = best;
+      if (zc == best.zc) continue;
+      c.zc = zc;
+      consider(c);
+    }
+  }
+  for (int f : {2, -2}) {
+    TuneChoice c = best;
+    c.grid = f > 0 ? best.grid * 2 : std::max(1, best.grid / 2);
+    if (c.grid != best.grid) consider(c);
+  }
+  for (int which = 0; which < 2; ++which) {
+    const int L0 = which == 0 ? best.L_dir : best.L_upd;
+    for (int L : {L0 / 2, L0 * 2, L0 + 1, L0 - 1}) {
+      TuneChoice c = best;
+      if (L < 1 || L == L0) continue;
+      (which == 0 ? c.L_dir : c.L_upd) = L;
+      consider(c);
+    }
+  }
+  ctx->opts = saved;
+  ctx->graph_off = saved_off;
+  apply_choice<T>(ctx, best);
+  release();
+  if (rc != FFTMECH_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[tune_key(ctx)] = best;
+  }
+  if (before_us) *before_us = 1e3 * first_ms / iterations;
+  if (after_us) *after_us = 1e3 * best_ms / iterations;
+  snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d", best.L_dir,
+           best.L_upd, best.ty, best.zc, best.grid, best.cols);
+  return FFTMECH_OK;
 }
 
 }  // namespace
@@ -835,8 +1603,7 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
       !(mat->nu_solid > -1) || !(mat->nu_pore > -1) || !(mat->D_solid > 0) || !(mat->D_pore > 0) ||
       !(mat->Gc > 0) || !(mat->l0 > 0) || !(mat->kappa >= 0))
     return FFTMECH_ERR_INVALID_ARG;
-  if (!(opts->tol >= 0) || opts->max_iter < 0 || opts->launch_mode < 0 || opts->launch_mode > 1)
-    return FFTMECH_ERR_INVALID_ARG;
+  if (!opts_ok(opts)) return FFTMECH_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -872,6 +1639,8 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
       return fail(FFTMECH_ERR_CUDA);
     ctx->own_stream = true;
   }
+  for (cudaStream_t& s : ctx->side)
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(FFTMECH_ERR_CUDA);
   const bool three = grid->dim == 3;
   const bool fp64 = precision == FFTMECH_FP64;
   if (make_plan(ctx->nx, ctx->px) != cudaSuccess || make_plan(ctx->ny, ctx->py) != cudaSuccess ||
@@ -895,6 +1664,23 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   }
   if (!shp) return fail(FFTMECH_ERR_UNSUPPORTED_SIZE);
   ctx->shape.batch = batch;
+  {
+    // a choice the autotuner made for this grid earlier in the process
+    TuneChoice c;
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(tune_key(ctx));
+      if (it != g_tune.end()) { c = it->second; have = true; }
+    }
+    if (have && (fp64 ? choice_ok<double>(ctx, c) : choice_ok<float>(ctx, c))) {
+      if (fp64) apply_choice<double>(ctx, c);
+      else apply_choice<float>(ctx, c);
+    }
+    const TuneChoice k = current_choice(ctx);
+    snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d%s", k.L_dir,
+             k.L_upd, k.ty, k.zc, k.grid, k.cols, have ? " (autotuned)" : "");
+  }
   const size_t es = fp64 ? 8 : 4;
   const size_t NB = (size_t)ctx->N * batch;
   const size_t nd = (size_t)grid->dim;  // displacement components
@@ -916,6 +1702,7 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   }
   const size_t post_blocks = batch > 1 ? 512 : 4096;
   const size_t slots = (size_t)batch * std::max(widest, post_blocks) * 16;
+  ctx->rec_bytes = rec_total(ctx);
   bool ok = true;
   auto alloc = [&](void** p, size_t bytes) {
     if (!ok) return;
@@ -924,8 +1711,7 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   };
   alloc(&ctx->q, nd * NB * es);
   alloc(&ctx->r, nd * NB * es);
-  alloc(&ctx->p[0], nd * NB * es);
-  alloc(&ctx->p[1], nd * NB * es);
+  alloc(&ctx->p, nd * NB * es);
   alloc(&ctx->S, 2 * s_complex * es);
   alloc(&ctx->g, NB * es);
   if (!fp64) {
@@ -946,24 +1732,16 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   }
   alloc((void**)&ctx->partials, slots * 8);
   if (!three) alloc((void**)&ctx->partials_col, (size_t)batch * ctx->nx * 8);
-  alloc((void**)&ctx->results, (size_t)kResultsPerProblem * batch * 8);
   alloc((void**)&ctx->m0b, (size_t)batch * 8);
   alloc((void**)&ctx->m1b, (size_t)batch * 8);
   alloc((void**)&ctx->mode, (size_t)batch * sizeof(int));
   alloc((void**)&ctx->sc, sizeof(SolverScalars) * batch);
+  alloc((void**)&ctx->flags, sizeof(int) * LF_COUNT);
+  alloc((void**)&ctx->rec, ctx->rec_bytes);
   if (!ok) return fail(FFTMECH_ERR_OOM);
-  if (cudaMallocHost((void**)&ctx->h_sc, sizeof(SolverScalars) * batch) != cudaSuccess) return fail(FFTMECH_ERR_OOM);
-  if (cudaMallocHost((void**)&ctx->h_results, (size_t)kResultsPerProblem * batch * 8) != cudaSuccess)
-    return fail(FFTMECH_ERR_OOM);
-  ctx->h_mode = new (std::nothrow) int[batch];
-  if (!ctx->h_mode) return fail(FFTMECH_ERR_OOM);
-  if (cudaMallocHost((void**)&ctx->h_mode_ring, sizeof(int) * batch * fftmech_ctx::kModeSlots) != cudaSuccess)
-    return fail(FFTMECH_ERR_OOM);
-  for (int k = 0; k < fftmech_ctx::kModeSlots; ++k)
-    if (cudaEventCreateWithFlags(&ctx->mode_ev[k], cudaEventDisableTiming) != cudaSuccess)
-      return fail(FFTMECH_ERR_CUDA);
-  if (cudaEventCreate(&ctx->solve_ev[0]) != cudaSuccess || cudaEventCreate(&ctx->solve_ev[1]) != cudaSuccess)
-    return fail(FFTMECH_ERR_CUDA);
+  if (cudaMallocHost((void**)&ctx->h_flags, sizeof(int) * LF_COUNT) != cudaSuccess) return fail(FFTMECH_ERR_OOM);
+  if (cudaMallocHost((void**)&ctx->h_rec, ctx->rec_bytes) != cudaSuccess) return fail(FFTMECH_ERR_OOM);
+  std::memset(ctx->h_rec, 0, ctx->rec_bytes);
   fftmech_status rc = fp64 ? fill_lam<double>(ctx) : fill_lam<float>(ctx);
   if (rc != FFTMECH_OK) return fail(rc);
   *out = ctx;
@@ -980,23 +1758,21 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
   if (!ctx) return FFTMECH_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  void* bufs[] = {ctx->r, ctx->q, ctx->p[0], ctx->p[1], ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
+  for (GraphCache& c : ctx->gc)
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+  void* bufs[] = {ctx->r, ctx->q, ctx->p, ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
                   ctx->cn, ctx->lamx, ctx->lamy, ctx->lamz, ctx->lamc3, ctx->lamc1, ctx->wcol3, ctx->wcol1,
-                  ctx->partials, ctx->partials_col, ctx->results, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc};
+                  ctx->partials, ctx->partials_col, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc, ctx->flags, ctx->rec};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < ST_COUNT; ++i)
     if (ctx->stage[i].dev) cudaFree(ctx->stage[i].dev);
-  if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
-  if (ctx->h_results) cudaFreeHost(ctx->h_results);
-  delete[] ctx->h_mode;
-  if (ctx->h_mode_ring) cudaFreeHost(ctx->h_mode_ring);
-  for (cudaEvent_t e : ctx->mode_ev)
-    if (e) cudaEventDestroy(e);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  if (ctx->h_rec) cudaFreeHost(ctx->h_rec);
   for (auto& pe : ctx->pending) { ctx->ev_free.push_back(pe.a); ctx->ev_free.push_back(pe.b); }
   for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
-  for (cudaEvent_t e : ctx->solve_ev)
-    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : ctx->side)
+    if (s) cudaStreamDestroy(s);
   free_plan(ctx->px);
   free_plan(ctx->py);
   free_plan(ctx->pz);
@@ -1007,14 +1783,64 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
 
 fftmech_status fftmech_set_solver_opts(fftmech_ctx* ctx, const fftmech_solver_opts* opts) {
   if (!ctx || !opts) return FFTMECH_ERR_INVALID_ARG;
-  if (!(opts->tol >= 0) || opts->max_iter < 0 || opts->launch_mode < 0 || opts->launch_mode > 1)
-    return FFTMECH_ERR_INVALID_ARG;
+  if (!opts_ok(opts)) return FFTMECH_ERR_INVALID_ARG;
   ctx->opts = *opts;
   if (ctx->opts.check_every <= 0) ctx->opts.check_every = 16;
   return FFTMECH_OK;
 }
 
 int fftmech_batch_size(const fftmech_ctx* ctx) { return ctx ? ctx->B : 0; }
+
+fftmech_status fftmech_autotune(fftmech_ctx* ctx, int iterations, double* before_us, double* after_us,
+                                const char** choice) {
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  if (iterations < 0) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "iterations must be >= 0");
+  if (iterations > 0)
+    rc = ctx->prec == FFTMECH_FP64 ? autotune_impl<double>(ctx, iterations, before_us, after_us)
+                                   : autotune_impl<float>(ctx, iterations, before_us, after_us);
+  if (choice) *choice = ctx->tune_desc;
+  return rc;
+}
+
+fftmech_status fftmech_adjoint_eigenstrain(fftmech_ctx* ctx, const uint8_t* phase, const void* e_field, int steps,
+                                           const double* ramp, const double eps_mac[6], int objective,
+                                           int checkpoint_every, double* grad, double* J,
+                                           fftmech_solve_info* info_last) {
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  if (!phase || !e_field || !ramp || !grad || !J || steps < 1 || checkpoint_every < 1)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument or bad count");
+  if (objective != FFTMECH_OBJ_ENERGY && objective != FFTMECH_OBJ_DAMAGE)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "objective %d", objective);
+  if (ctx->B != 1) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "the adjoint takes one problem per context");
+  for (const void* p : {(const void*)phase, e_field, (const void*)grad})
+    if (!is_device_ptr(p)) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "the adjoint takes device pointers");
+  double E[6] = {0, 0, 0, 0, 0, 0};
+  if (eps_mac)
+    for (int i = 0; i < nvoigt(ctx); ++i) E[i] = eps_mac[i];
+  const int k = std::min(checkpoint_every, steps);
+  return ctx->prec == FFTMECH_FP64
+             ? adjoint_impl<double>(ctx, phase, (const double*)e_field, steps, ramp, E, objective, k, grad, J, info_last)
+             : adjoint_impl<float>(ctx, phase, (const float*)e_field, steps, ramp, E, objective, k, grad, J, info_last);
+}
+
+fftmech_status fftmech_problem_offset(const fftmech_ctx* ctx, int problem, int components, long long* offset) {
+  if (!ctx || !offset || problem < 0 || problem >= ctx->B || components < 1) return FFTMECH_ERR_INVALID_ARG;
+  *offset = (long long)problem * components * ctx->N;
+  return FFTMECH_OK;
+}
+
+fftmech_status fftmech_graph_stats(const fftmech_ctx* ctx, long long* builds, long long* launches,
+                                   long long* kernels, int* disabled, const char** reason) {
+  if (!ctx) return FFTMECH_ERR_INVALID_ARG;
+  if (builds) *builds = ctx->graph_builds;
+  if (launches) *launches = ctx->graph_launches;
+  if (kernels) *kernels = ctx->graph_kernels;
+  if (disabled) *disabled = ctx->graph_off ? 1 : 0;
+  if (reason) *reason = ctx->graph_err;
+  return FFTMECH_OK;
+}
 
 fftmech_status fftmech_equilibrium_solve(fftmech_ctx* ctx, const uint8_t* phase, const void* eig,
                                          const double* damage, const double eps_mac[6], double* u,
@@ -1025,25 +1851,38 @@ fftmech_status fftmech_equilibrium_solve(fftmech_ctx* ctx, const uint8_t* phase,
   std::memset(info, 0, sizeof(fftmech_solve_info) * ctx->B);
   const size_t N = (size_t)ctx->N * ctx->B, es = esize(ctx), nv = nvoigt(ctx);
   void *dphase, *deig, *ddmg, *du, *dstrain, *dstress;
-  if ((rc = stage_in(ctx, ST_PHASE, phase, N, true, &dphase)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_EIG, eig, N * es, true, &deig)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_DAMAGE, damage, N * 8, true, &ddmg)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_U, u, (size_t)ctx->dim * N * 8, true, &du)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_STRAIN, strain, nv * N * es, false, &dstrain)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_STRESS, stress, nv * N * es, false, &dstress)) != FFTMECH_OK) return rc;
-  fftmech_status s;
-  if (ctx->prec == FFTMECH_FP64)
-    s = equilibrium_impl<double>(ctx, (const uint8_t*)dphase, (const double*)deig, (const double*)ddmg,
-                                 eps_mac, (double*)du, (double*)dstrain, (double*)dstress, info, 1);
-  else
-    s = equilibrium_impl<float>(ctx, (const uint8_t*)dphase, (const float*)deig, (const double*)ddmg,
-                                eps_mac, (double*)du, (float*)dstrain, (float*)dstress, info, 1);
-  if (is_hard_error(s)) return s;
-  if ((rc = stage_out(ctx, u, du, (size_t)ctx->dim * N * 8)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, strain, dstrain, nv * N * es)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, stress, dstress, nv * N * es)) != FFTMECH_OK) return rc;
-  CK(cudaStreamSynchronize(ctx->stream));
-  return s;
+  RC(stage_in(ctx, ST_PHASE, phase, N, true, &dphase));
+  RC(stage_in(ctx, ST_EIG, eig, N * es, true, &deig));
+  RC(stage_in(ctx, ST_DAMAGE, damage, N * 8, true, &ddmg));
+  RC(stage_in(ctx, ST_U, u, (size_t)ctx->dim * N * 8, true, &du));
+  RC(stage_in(ctx, ST_STRAIN, strain, nv * N * es, false, &dstrain));
+  RC(stage_in(ctx, ST_STRESS, stress, nv * N * es, false, &dstress));
+  double E[6];
+  for (int k = 0; k < 6; ++k) E[k] = k < (int)nv ? eps_mac[k] : 0.0;
+  std::vector<unsigned char> key;
+  for (const void* p : {dphase, deig, ddmg, du, dstrain, dstress}) key_add(key, p);
+  key_add(key, E);
+  key_add(key, ctx->opts);
+  const bool fp64 = ctx->prec == FFTMECH_FP64;
+  RC(run_op(ctx, OP_EQ, key, [&](Emit& em) -> fftmech_status {
+    if (fp64)
+      RC(enqueue_equilibrium<double>(em, (const uint8_t*)dphase, (const double*)deig, (const double*)ddmg, E,
+                                     (double*)du, (double*)dstrain, (double*)dstress));
+    else
+      RC(enqueue_equilibrium<float>(em, (const uint8_t*)dphase, (const float*)deig, (const double*)ddmg, E,
+                                    (double*)du, (float*)dstrain, (float*)dstress));
+    return rec_publish(em);
+  }));
+  ctx->last = LastOp();
+  ctx->last.valid = 1;
+  ctx->last.ran[SK_EQ] = 1;
+  ctx->last.lc = ctx->pending_lc;
+  RC(stage_out(ctx, u, du, (size_t)ctx->dim * N * 8));
+  RC(stage_out(ctx, strain, dstrain, nv * N * es));
+  RC(stage_out(ctx, stress, dstress, nv * N * es));
+  RC(finish_sync(ctx));
+  count_graph_kernels(ctx);
+  return collect(ctx, SK_EQ, info, 1);
 }
 
 fftmech_status fftmech_diffusion_step(fftmech_ctx* ctx, const uint8_t* phase, int mode,
@@ -1057,26 +1896,45 @@ fftmech_status fftmech_diffusion_step(fftmech_ctx* ctx, const uint8_t* phase, in
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "diffusion mode %d", mode);
   if (mode == FFTMECH_DIFF_HOMOGENISE && !grad_c_mac)
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "grad_c_mac is required");
+  if (mode == FFTMECH_DIFF_TRANSIENT && !(dt > 0))
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "dt must be > 0 for TRANSIENT");
   std::memset(info, 0, sizeof(fftmech_solve_info) * ctx->B);
   const size_t N = (size_t)ctx->N * ctx->B;
   void *dphase, *dc, *dmask = nullptr;
-  if ((rc = stage_in(ctx, ST_PHASE, phase, N, true, &dphase)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_C, c, N * 8, mode == FFTMECH_DIFF_TRANSIENT, &dc)) != FFTMECH_OK) return rc;
-  if (mode == FFTMECH_DIFF_TRANSIENT &&
-      (rc = stage_in(ctx, ST_MASK, dirichlet_mask, N, true, &dmask)) != FFTMECH_OK)
-    return rc;
-  const double zero[3] = {0, 0, 0};
-  fftmech_status s;
-  if (ctx->prec == FFTMECH_FP64)
-    s = diffusion_impl<double>(ctx, (const uint8_t*)dphase, mode, grad_c_mac ? grad_c_mac : zero, c_macro, dt,
-                               (const uint8_t*)dmask, dirichlet_value, (double*)dc, info, 1);
-  else
-    s = diffusion_impl<float>(ctx, (const uint8_t*)dphase, mode, grad_c_mac ? grad_c_mac : zero, c_macro, dt,
-                              (const uint8_t*)dmask, dirichlet_value, (double*)dc, info, 1);
-  if (is_hard_error(s)) return s;
-  if ((rc = stage_out(ctx, c, dc, N * 8)) != FFTMECH_OK) return rc;
-  CK(cudaStreamSynchronize(ctx->stream));
-  return s;
+  RC(stage_in(ctx, ST_PHASE, phase, N, true, &dphase));
+  RC(stage_in(ctx, ST_C, c, N * 8, mode == FFTMECH_DIFF_TRANSIENT, &dc));
+  if (mode == FFTMECH_DIFF_TRANSIENT) RC(stage_in(ctx, ST_MASK, dirichlet_mask, N, true, &dmask));
+  double G[3] = {0, 0, 0};
+  if (grad_c_mac)
+    for (int k = 0; k < 3; ++k) G[k] = grad_c_mac[k];
+  std::vector<unsigned char> key;
+  for (const void* p : {dphase, dc, dmask}) key_add(key, p);
+  key_add(key, mode);
+  key_add(key, G);
+  key_add(key, c_macro);
+  key_add(key, dt);
+  key_add(key, dirichlet_value);
+  key_add(key, ctx->opts);
+  const bool fp64 = ctx->prec == FFTMECH_FP64;
+  RC(run_op(ctx, OP_DIFF, key, [&](Emit& em) -> fftmech_status {
+    if (fp64)
+      RC(enqueue_diffusion<double>(em, (const uint8_t*)dphase, mode, G, c_macro, dt, (const uint8_t*)dmask,
+                                   dirichlet_value, (double*)dc));
+    else
+      RC(enqueue_diffusion<float>(em, (const uint8_t*)dphase, mode, G, c_macro, dt, (const uint8_t*)dmask,
+                                  dirichlet_value, (double*)dc));
+    return rec_publish(em);
+  }));
+  ctx->last = LastOp();
+  ctx->last.valid = 1;
+  ctx->last.ran[SK_DIFF] = 1;
+  ctx->last.diff_mode = mode;
+  ctx->last.c_macro = c_macro;
+  ctx->last.lc = ctx->pending_lc;
+  RC(stage_out(ctx, c, dc, N * 8));
+  RC(finish_sync(ctx));
+  count_graph_kernels(ctx);
+  return collect(ctx, SK_DIFF, info, 1);
 }
 
 fftmech_status fftmech_phasefield_solve(fftmech_ctx* ctx, const void* strain, const void* eig,
@@ -1089,138 +1947,267 @@ fftmech_status fftmech_phasefield_solve(fftmech_ctx* ctx, const void* strain, co
   std::memset(info, 0, sizeof(fftmech_solve_info) * ctx->B);
   const size_t N = (size_t)ctx->N * ctx->B, es = esize(ctx), nv = nvoigt(ctx);
   void *dstrain, *deig, *dphase, *dH, *dd;
-  if ((rc = stage_in(ctx, ST_STRAIN, strain, nv * N * es, true, &dstrain)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_EIG, eig, N * es, true, &deig)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_PHASE, phase, N, true, &dphase)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_H, H, N * es, true, &dH)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_DAMAGE, damage, N * 8, true, &dd)) != FFTMECH_OK) return rc;
-  fftmech_status s;
-  if (ctx->prec == FFTMECH_FP64)
-    s = phasefield_impl<double>(ctx, (const double*)dstrain, (const double*)deig, (const uint8_t*)dphase,
-                                (double*)dH, (double*)dd, info, 1);
-  else
-    s = phasefield_impl<float>(ctx, (const float*)dstrain, (const float*)deig, (const uint8_t*)dphase,
-                               (float*)dH, (double*)dd, info, 1);
-  if (is_hard_error(s)) return s;
-  if ((rc = stage_out(ctx, H, dH, N * es)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, damage, dd, N * 8)) != FFTMECH_OK) return rc;
-  CK(cudaStreamSynchronize(ctx->stream));
-  return s;
+  RC(stage_in(ctx, ST_STRAIN, strain, nv * N * es, true, &dstrain));
+  RC(stage_in(ctx, ST_EIG, eig, N * es, true, &deig));
+  RC(stage_in(ctx, ST_PHASE, phase, N, true, &dphase));
+  RC(stage_in(ctx, ST_H, H, N * es, true, &dH));
+  RC(stage_in(ctx, ST_DAMAGE, damage, N * 8, true, &dd));
+  std::vector<unsigned char> key;
+  for (const void* p : {dstrain, deig, dphase, dH, dd}) key_add(key, p);
+  key_add(key, ctx->opts);
+  const bool fp64 = ctx->prec == FFTMECH_FP64;
+  RC(run_op(ctx, OP_PF, key, [&](Emit& em) -> fftmech_status {
+    if (fp64)
+      RC(enqueue_phasefield<double>(em, (const double*)dstrain, (const double*)deig, (const uint8_t*)dphase,
+                                    (double*)dH, (double*)dd));
+    else
+      RC(enqueue_phasefield<float>(em, (const float*)dstrain, (const float*)deig, (const uint8_t*)dphase,
+                                   (float*)dH, (double*)dd));
+    return rec_publish(em);
+  }));
+  ctx->last = LastOp();
+  ctx->last.valid = 1;
+  ctx->last.ran[SK_PF] = 1;
+  ctx->last.lc = ctx->pending_lc;
+  RC(stage_out(ctx, H, dH, N * es));
+  RC(stage_out(ctx, damage, dd, N * 8));
+  RC(finish_sync(ctx));
+  count_graph_kernels(ctx);
+  return collect(ctx, SK_PF, info, 1);
 }
 
 fftmech_status fftmech_staggered_step(fftmech_ctx* ctx, fftmech_state* state,
                                       const fftmech_step_params* prm, fftmech_solve_info* info) {
   fftmech_status rc = check_ctx(ctx);
   if (rc != FFTMECH_OK) return rc;
-  if (!state || !prm || !info || !state->phase || !state->c || !state->eig || !state->u ||
-      !state->strain || !state->stress || !state->H || !state->damage)
-    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
-  if (prm->eig_mode == FFTMECH_EIG_PRESCRIBED && !prm->eig_field)
-    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "eig_field is required for PRESCRIBED");
+  if (!info) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
+  RC(check_step_args(ctx, state, prm));
   std::memset(info, 0, sizeof(fftmech_solve_info) * 3 * ctx->B);
+  StepPtrs d;
+  bool all_device = false;
+  RC(stage_step(ctx, state, prm, d, all_device));
+  RC(step_enqueue(ctx, d, prm));
   const size_t N = (size_t)ctx->N * ctx->B, es = esize(ctx), nv = nvoigt(ctx);
-  cudaStream_t st = ctx->stream;
-  void *dphase, *dc, *dcppt, *deig, *du, *dstrain, *dstress, *dH, *dd, *dmask = nullptr, *deigf = nullptr;
-  if ((rc = stage_in(ctx, ST_PHASE, state->phase, N, true, &dphase)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_C, state->c, N * 8, true, &dc)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_CPPT, state->c_ppt, N * es, true, &dcppt)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_EIG, state->eig, N * es, true, &deig)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_U, state->u, (size_t)ctx->dim * N * 8, true, &du)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_STRAIN, state->strain, nv * N * es, true, &dstrain)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_STRESS, state->stress, nv * N * es, true, &dstress)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_H, state->H, N * es, true, &dH)) != FFTMECH_OK) return rc;
-  if ((rc = stage_in(ctx, ST_DAMAGE, state->damage, N * 8, true, &dd)) != FFTMECH_OK) return rc;
-  if (prm->diffusion_mode == FFTMECH_DIFF_TRANSIENT &&
-      (rc = stage_in(ctx, ST_MASK, prm->dirichlet_mask, N, true, &dmask)) != FFTMECH_OK)
-    return rc;
-  if (prm->eig_mode == FFTMECH_EIG_PRESCRIBED &&
-      (rc = stage_in(ctx, ST_EIGFIELD, prm->eig_field, N * es, true, &deigf)) != FFTMECH_OK)
-    return rc;
-  const bool fp64 = ctx->prec == FFTMECH_FP64;
-  fftmech_status worst = FFTMECH_OK;
-  auto track = [&](fftmech_status s) {
-    if (s != FFTMECH_OK && worst == FFTMECH_OK) worst = s;
+  RC(stage_out(ctx, state->c, d.c, N * 8));
+  RC(stage_out(ctx, state->c_ppt, d.cppt, N * es));
+  RC(stage_out(ctx, state->eig, d.eig, N * es));
+  RC(stage_out(ctx, state->u, d.u, (size_t)ctx->dim * N * 8));
+  RC(stage_out(ctx, state->strain, d.strain, nv * N * es));
+  RC(stage_out(ctx, state->stress, d.stress, nv * N * es));
+  RC(stage_out(ctx, state->H, d.H, N * es));
+  RC(stage_out(ctx, state->damage, d.d, N * 8));
+  RC(finish_sync(ctx));
+  return step_collect(ctx, info);
+}
+
+fftmech_status fftmech_staggered_step_async(fftmech_ctx* ctx, const fftmech_state* state,
+                                            const fftmech_step_params* prm) {
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  RC(check_step_args(ctx, state, prm));
+  StepPtrs d;
+  bool all_device = false;
+  // every pointer must be device memory: nothing is staged, copied or allocated
+  const void* ptrs[] = {state->phase, state->c, state->c_ppt, state->eig, state->u, state->strain, state->stress,
+                        state->H, state->damage,
+                        prm->diffusion_mode == FFTMECH_DIFF_TRANSIENT ? (const void*)prm->dirichlet_mask : nullptr,
+                        prm->eig_mode == FFTMECH_EIG_PRESCRIBED ? prm->eig_field : nullptr};
+  for (const void* p : ptrs)
+    if (p && !is_device_ptr(p)) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "host pointer in an asynchronous step");
+  RC(stage_step(ctx, state, prm, d, all_device));
+  return step_enqueue(ctx, d, prm);
+}
+
+fftmech_status fftmech_step_info(fftmech_ctx* ctx, fftmech_solve_info* info) {
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  if (!info) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
+  if (!ctx->last.valid || !ctx->last.ran[SK_EQ])
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "no staggered step has been enqueued");
+  RC(finish_sync(ctx));
+  return step_collect(ctx, info);
+}
+
+fftmech_status fftmech_group_create(fftmech_group** out, fftmech_ctx* const* ctxs, int n, void* stream) {
+  if (!out || !ctxs || n < 1) return FFTMECH_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return FFTMECH_ERR_INVALID_ARG;
+    if (ctxs[i]->device != ctxs[0]->device) return FFTMECH_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) return FFTMECH_ERR_INVALID_ARG;
+  }
+  fftmech_group* g = new (std::nothrow) fftmech_group();
+  if (!g) return FFTMECH_ERR_OOM;
+  g->ctxs.assign(ctxs, ctxs + n);
+  g->lc.resize(n);
+  auto fail = [&](fftmech_status s) {
+    fftmech_group_destroy(g);
+    return s;
   };
-  // 1. diffusion of chemical species
-  if (prm->diffusion_mode != FFTMECH_DIFF_NONE) {
-    fftmech_status s = fp64
-        ? diffusion_impl<double>(ctx, (const uint8_t*)dphase, prm->diffusion_mode, prm->grad_c_mac,
-                                 prm->c_macro, prm->dt, (const uint8_t*)dmask, prm->dirichlet_value,
-                                 (double*)dc, info + 0, 3)
-        : diffusion_impl<float>(ctx, (const uint8_t*)dphase, prm->diffusion_mode, prm->grad_c_mac,
-                                prm->c_macro, prm->dt, (const uint8_t*)dmask, prm->dirichlet_value,
-                                (double*)dc, info + 0, 3);
-    if (is_hard_error(s)) return s;
-    track(s);
-  }
-  // 2. precipitation and eigenstrain
-  if (prm->eig_mode == FFTMECH_EIG_FROM_PRECIPITATE) {
-    ProfScope _ps(ctx, FFTMECH_K_OTHER);
-    if (fp64)
-      CK(launch_precipitate<double>(N, (const uint8_t*)dphase, (const double*)dc, ctx->mat.S_sol,
-                                    ctx->mat.M_ppt, (double*)dcppt, (double*)deig, st));
-    else
-      CK(launch_precipitate<float>(N, (const uint8_t*)dphase, (const double*)dc, ctx->mat.S_sol,
-                                   ctx->mat.M_ppt, (float*)dcppt, (float*)deig, st));
+  if (cudaSetDevice(ctxs[0]->device) != cudaSuccess) return fail(FFTMECH_ERR_CUDA);
+  if (stream) {
+    g->stream = (cudaStream_t)stream;
   } else {
-    ProfScope _ps(ctx, FFTMECH_K_OTHER);
-    if (fp64)
-      CK(launch_scale_copy<double>(N, (const double*)deigf, prm->eig_scale, (double*)deig, st));
-    else
-      CK(launch_scale_copy<float>(N, (const float*)deigf, prm->eig_scale, (float*)deig, st));
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FFTMECH_ERR_CUDA);
+    g->own_stream = true;
   }
-  // 3. equilibrium with the stiffness degraded by the current damage
-  {
-    fftmech_status s = fp64
-        ? equilibrium_impl<double>(ctx, (const uint8_t*)dphase, (const double*)deig, (const double*)dd,
-                                   prm->eps_mac, (double*)du, (double*)dstrain, (double*)dstress, info + 1, 3)
-        : equilibrium_impl<float>(ctx, (const uint8_t*)dphase, (const float*)deig, (const double*)dd,
-                                  prm->eps_mac, (double*)du, (float*)dstrain, (float*)dstress, info + 1, 3);
-    if (is_hard_error(s)) return s;
-    track(s);
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i]->stream == g->stream) return fail(FFTMECH_ERR_INVALID_ARG);
+  if (cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) != cudaSuccess) return fail(FFTMECH_ERR_CUDA);
+  g->join.assign(n, nullptr);
+  for (int i = 0; i < n; ++i)
+    if (cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming) != cudaSuccess) return fail(FFTMECH_ERR_CUDA);
+  *out = g;
+  return FFTMECH_OK;
+}
+
+fftmech_status fftmech_group_destroy(fftmech_group* g) {
+  if (!g) return FFTMECH_ERR_INVALID_ARG;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->fork) cudaEventDestroy(g->fork);
+  for (cudaEvent_t e : g->join)
+    if (e) cudaEventDestroy(e);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return FFTMECH_OK;
+}
+
+const char* fftmech_group_last_error(const fftmech_group* g) { return g ? g->err : ""; }
+
+fftmech_status fftmech_group_step(fftmech_group* g, const fftmech_state* const* states,
+                                  const fftmech_step_params* const* params, fftmech_solve_info* const* infos) {
+  if (!g || !states || !params || !infos) return FFTMECH_ERR_INVALID_ARG;
+  g->err[0] = 0;
+  const int n = (int)g->ctxs.size();
+  if (cudaSetDevice(g->ctxs[0]->device) != cudaSuccess) return FFTMECH_ERR_CUDA;
+  std::vector<StepPtrs> d(n);
+  std::vector<unsigned char> key;
+  for (int i = 0; i < n; ++i) {
+    fftmech_ctx* ctx = g->ctxs[i];
+    ctx->err[0] = 0;
+    if (!states[i] || !params[i] || !infos[i]) return FFTMECH_ERR_INVALID_ARG;
+    fftmech_status rc = check_step_args(ctx, states[i], params[i]);
+    if (rc != FFTMECH_OK) {
+      snprintf(g->err, sizeof(g->err), "problem group %d: %s", i, ctx->err);
+      return rc;
+    }
+    bool all_device = false;
+    RC(stage_step(ctx, states[i], params[i], d[i], all_device));
+    if (!all_device) {
+      snprintf(g->err, sizeof(g->err), "problem group %d: host pointer (a group runs on device memory)", i);
+      return FFTMECH_ERR_INVALID_ARG;
+    }
+    key_add(key, ctx);
+    key_add(key, d[i]);
+    key_add(key, *params[i]);
+    key_add(key, ctx->opts);
   }
-  // 4. history and phase field
-  {
-    fftmech_status s = fp64
-        ? phasefield_impl<double>(ctx, (const double*)dstrain, (const double*)deig, (const uint8_t*)dphase,
-                                  (double*)dH, (double*)dd, info + 2, 3)
-        : phasefield_impl<float>(ctx, (const float*)dstrain, (const float*)deig, (const uint8_t*)dphase,
-                                 (float*)dH, (double*)dd, info + 2, 3);
-    if (is_hard_error(s)) return s;
-    track(s);
+  if (!g->exec || key != g->key) {
+    // capture: fork every context's stream from the group stream, emit its
+    // step there (conditional nodes included), join back
+    fftmech_ctx* ctx = g->ctxs[0];  // for CK's messages
+    if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(g->err, sizeof(g->err), "cudaStreamBeginCapture failed");
+      return FFTMECH_ERR_CUDA;
+    }
+    fftmech_status rc = FFTMECH_OK;
+    std::vector<LaunchCount> lc(n);
+    if (cudaEventRecord(g->fork, g->stream) != cudaSuccess) rc = FFTMECH_ERR_CUDA;
+    for (int i = 0; i < n && rc == FFTMECH_OK; ++i) {
+      fftmech_ctx* c = g->ctxs[i];
+      if (cudaStreamWaitEvent(c->stream, g->fork, 0) != cudaSuccess) { rc = FFTMECH_ERR_CUDA; break; }
+      Emit em = eager_emit(c);
+      em.graph = true;
+      em.lc = &lc[i];
+      cudaStreamCaptureStatus cs;
+      if (cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &em.g, nullptr, nullptr, nullptr) != cudaSuccess) {
+        rc = FFTMECH_ERR_CUDA;
+        break;
+      }
+      const bool fp64 = c->prec == FFTMECH_FP64;
+      rc = fp64 ? enqueue_step<double>(em, d[i], params[i]) : enqueue_step<float>(em, d[i], params[i]);
+      if (rc == FFTMECH_OK) rc = rec_publish(em);
+      if (rc != FFTMECH_OK) snprintf(g->err, sizeof(g->err), "problem group %d: %s", i, c->err);
+      if (rc == FFTMECH_OK && (cudaEventRecord(g->join[i], c->stream) != cudaSuccess ||
+                               cudaStreamWaitEvent(g->stream, g->join[i], 0) != cudaSuccess))
+        rc = FFTMECH_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+    if (rc == FFTMECH_OK && e != cudaSuccess) rc = FFTMECH_ERR_CUDA;
+    if (rc == FFTMECH_OK && g->exec) {
+      cudaGraphExecUpdateResultInfo ri;
+      if (cudaGraphExecUpdate(g->exec, graph, &ri) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+      }
+    }
+    if (rc == FFTMECH_OK && !g->exec && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+      g->exec = nullptr;
+      rc = FFTMECH_ERR_CUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != FFTMECH_OK) {
+      cudaGetLastError();
+      if (!g->err[0]) snprintf(g->err, sizeof(g->err), "building the group graph failed");
+      return rc;
+    }
+    g->key = key;
+    g->lc = lc;
+    g->builds += 1;
+    (void)ctx;
   }
-  if ((rc = stage_out(ctx, state->c, dc, N * 8)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, state->c_ppt, dcppt, N * es)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, state->eig, deig, N * es)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, state->u, du, (size_t)ctx->dim * N * 8)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, state->strain, dstrain, nv * N * es)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, state->stress, dstress, nv * N * es)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, state->H, dH, N * es)) != FFTMECH_OK) return rc;
-  if ((rc = stage_out(ctx, state->damage, dd, N * 8)) != FFTMECH_OK) return rc;
-  CK(cudaStreamSynchronize(st));
+  const cudaError_t e = cudaGraphLaunch(g->exec, g->stream);
+  if (e == cudaSuccess) g->launches += 1;
+  const cudaError_t es = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess || es != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g->err, sizeof(g->err), "group graph: %s", cudaGetErrorString(e != cudaSuccess ? e : es));
+    return FFTMECH_ERR_CUDA;
+  }
+  fftmech_status worst = FFTMECH_OK;
+  for (int i = 0; i < n; ++i) {
+    fftmech_ctx* ctx = g->ctxs[i];
+    const fftmech_step_params* prm = params[i];
+    ctx->last = LastOp();
+    ctx->last.valid = 1;
+    ctx->last.ran[SK_DIFF] = prm->diffusion_mode != FFTMECH_DIFF_NONE;
+    ctx->last.ran[SK_EQ] = ctx->last.ran[SK_PF] = 1;
+    ctx->last.diff_mode = prm->diffusion_mode;
+    ctx->last.c_macro = prm->c_macro;
+    ctx->last.lc = &g->lc[i];
+    const long long before = ctx->graph_kernels;
+    const fftmech_status s = step_collect(ctx, infos[i]);
+    g->kernels += ctx->graph_kernels - before;
+    if (s != FFTMECH_OK && worst == FFTMECH_OK) worst = s;
+  }
   return worst;
+}
+
+fftmech_status fftmech_group_stats(const fftmech_group* g, long long* builds, long long* launches,
+                                   long long* kernels) {
+  if (!g) return FFTMECH_ERR_INVALID_ARG;
+  if (builds) *builds = g->builds;
+  if (launches) *launches = g->launches;
+  if (kernels) *kernels = g->kernels;
+  return FFTMECH_OK;
 }
 
 fftmech_status fftmech_staggered_step_many(fftmech_ctx* const* ctxs, int n, fftmech_state* const* states,
                                            const fftmech_step_params* const* params,
                                            fftmech_solve_info* const* infos) {
   if (!ctxs || !states || !params || !infos || n < 0) return FFTMECH_ERR_INVALID_ARG;
-  for (int i = 0; i < n; ++i) {
-    if (!ctxs[i] || !states[i] || !params[i] || !infos[i]) return FFTMECH_ERR_INVALID_ARG;
-    for (int j = 0; j < i; ++j)
-      if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) return FFTMECH_ERR_INVALID_ARG;
-  }
-  std::vector<fftmech_status> rc(n, FFTMECH_OK);
-  std::vector<std::thread> workers;
-  workers.reserve(n);
-  for (int i = 0; i < n; ++i)
-    workers.emplace_back([&, i]() { rc[i] = fftmech_staggered_step(ctxs[i], states[i], params[i], infos[i]); });
-  for (auto& w : workers) w.join();
-  for (int i = 0; i < n; ++i)
-    if (is_hard_error(rc[i])) return rc[i];
-  for (int i = 0; i < n; ++i)
-    if (rc[i] != FFTMECH_OK) return rc[i];
-  return FFTMECH_OK;
+  if (n == 0) return FFTMECH_OK;
+  fftmech_group* g = nullptr;
+  fftmech_status rc = fftmech_group_create(&g, ctxs, n, nullptr);
+  if (rc != FFTMECH_OK) return rc;
+  rc = fftmech_group_step(g, states, params, infos);
+  fftmech_group_destroy(g);
+  return rc;
 }
 
 fftmech_status fftmech_profile_enable(fftmech_ctx* ctx, int enable) {
@@ -1257,51 +2244,49 @@ fftmech_status fftmech_profile_read(fftmech_ctx* ctx, int kclass, long long* lau
 fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse, void* data,
                            void* stream) {
   fftmech_ctx* ctx = nullptr;  // for CK's error path (no message storage)
-  if (!n || !data || (ndim != 1 && ndim != 2)) return FFTMECH_ERR_INVALID_ARG;
+  if (!n || !data || ndim < 1 || ndim > 3) return FFTMECH_ERR_INVALID_ARG;
   if (precision != FFTMECH_FP64 && precision != FFTMECH_MIXED) return FFTMECH_ERR_INVALID_ARG;
-  const int nx = n[0], ny = ndim == 2 ? n[1] : 1;
-  if (!factor_ok(nx) || !factor_ok(ny) || nx < 2) return FFTMECH_ERR_UNSUPPORTED_SIZE;
+  const int nx = n[0], ny = ndim >= 2 ? n[1] : 1, nz = ndim == 3 ? n[2] : 1;
+  if (!factor_ok(nx) || !factor_ok(ny) || !factor_ok(nz) || nx < 2) return FFTMECH_ERR_UNSUPPORTED_SIZE;
   if (!is_device_ptr(data)) return FFTMECH_ERR_INVALID_ARG;
   int dev = 0;
   CK(cudaGetDevice(&dev));
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, dev));
-  HostPlan px, py;
-  cudaError_t e1 = make_plan(nx, px), e2 = make_plan(ny, py);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
-    free_plan(px);
-    free_plan(py);
+  HostPlan px, py, pz;
+  if (cached_plan(dev, nx, px) != cudaSuccess || cached_plan(dev, ny, py) != cudaSuccess ||
+      cached_plan(dev, nz, pz) != cudaSuccess) {
+    cudaGetLastError();
     return FFTMECH_ERR_OOM;
   }
   const bool fp64 = precision == FFTMECH_FP64;
-  fftmech_status rc = FFTMECH_OK;
-  Shape2 sh{};
-  const bool shp = fp64 ? choose_shape_fft<double>(px, py, prop.multiProcessorCount, prop.sharedMemPerBlockOptin, sh)
-                        : choose_shape_fft<float>(px, py, prop.multiProcessorCount, prop.sharedMemPerBlockOptin, sh);
-  if (!shp) {
-    rc = FFTMECH_ERR_UNSUPPORTED_SIZE;
-  } else {
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaSuccess;
-    if (fp64) {
-      Spec<double> sp{};
-      e = launch_rowfft_f<double>(px.fam, nx, ny, (cx<double>*)data, dev_plan<double>(px), inverse, sh, st);
-      if (e == cudaSuccess && ny > 1)
-        e = launch_colpass_f<double>(py.fam, nx, ny, (cx<double>*)data, dev_plan<double>(py), sp, sh, COL_PLAIN,
-                                   inverse, nullptr, nullptr, nullptr, st);
-    } else {
-      Spec<float> sp{};
-      e = launch_rowfft_f<float>(px.fam, nx, ny, (cx<float>*)data, dev_plan<float>(px), inverse, sh, st);
-      if (e == cudaSuccess && ny > 1)
-        e = launch_colpass_f<float>(py.fam, nx, ny, (cx<float>*)data, dev_plan<float>(py), sp, sh, COL_PLAIN,
-                                  inverse, nullptr, nullptr, nullptr, st);
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) rc = FFTMECH_ERR_CUDA;
-  }
-  free_plan(px);
-  free_plan(py);
-  return rc;
+  const int nsm = prop.multiProcessorCount;
+  const size_t optin = prop.sharedMemPerBlockOptin;
+  Shape2 sh{}, shz{};
+  bool shp = fp64 ? choose_shape_fft<double>(px, py, nsm, optin, sh) : choose_shape_fft<float>(px, py, nsm, optin, sh);
+  if (shp && nz > 1)
+    shp = fp64 ? choose_shape_fft<double>(px, pz, nsm, optin, shz) : choose_shape_fft<float>(px, pz, nsm, optin, shz);
+  if (!shp) return FFTMECH_ERR_UNSUPPORTED_SIZE;
+  sh.batch = nz;  // the y pass runs plane by plane (grid.y = plane)
+  shz.batch = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  // x lines (all ny nz of them), y columns of every plane, z columns (the
+  // nx ny columns of the array seen as nz rows of nx ny points)
+  auto run = [&](auto zero) -> cudaError_t {
+    using T = decltype(zero);
+    Spec<T> sp{};
+    cudaError_t e = launch_rowfft_f<T>(px.fam, nx, ny * nz, (cx<T>*)data, dev_plan<T>(px), inverse, sh, st);
+    if (e == cudaSuccess && ny > 1)
+      e = launch_colpass_f<T>(py.fam, nx, ny, (cx<T>*)data, dev_plan<T>(py), sp, sh, COL_PLAIN, inverse, nullptr,
+                              nullptr, nullptr, st);
+    if (e == cudaSuccess && nz > 1)
+      e = launch_colpass_f<T>(pz.fam, nx * ny, nz, (cx<T>*)data, dev_plan<T>(pz), sp, shz, COL_PLAIN, inverse, nullptr,
+                              nullptr, nullptr, st);
+    return e;
+  };
+  cudaError_t e = fp64 ? run(0.0) : run(0.0f);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? FFTMECH_OK : FFTMECH_ERR_CUDA;
 }
 
 }  // extern "C"

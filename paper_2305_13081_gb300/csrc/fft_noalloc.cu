@@ -1,6 +1,6 @@
 // fftmech_fft_noalloc: the stand-alone Stockham transform of fftmech_fft
-// without any device allocation. fftmech_fft allocates its twiddle tables
-// with cudaMalloc on every call; this variant keeps them in one file-scope
+// without any device allocation. fftmech_fft allocates the twiddle tables of
+// every new length with cudaMalloc; this variant keeps them in one file-scope
 // device array of fixed size instead (no counterpart in the paper).
 #include <cuda_runtime.h>
 

@@ -90,6 +90,40 @@ struct SolverScalars {
   // float copies for the float kernels (no FP64 instruction in their hot
   // path): alpha = alpha_h + alpha_l, beta rounded
   float alpha_h, alpha_l, beta_f, pad_f;
+  // reliable updates (MIXED): <r, M^-1 r> right after the last residual
+  // replacement (or the first residual); reliable: replacements enabled;
+  // nrestart: restarts taken after a recursive convergence; nreplace:
+  // replacement iterations scheduled
+  double rz_rep;
+  int reliable, nrestart, nreplace;
+  // deferred reductions (2D): rz_next holds the residual norm that the next
+  // stencil kernel's block 0 commits to rz (with iter += 1)
+  int rz_pending;
+  // the FP64 true residual of this stopped problem is in rz_true (set by the
+  // gate after its true-residual pass; cleared by a restart), so later
+  // rounds of a batch do not recompute it
+  int checked;
+};
+
+// Loop control of the device-driven PCG. The kernels that decide whether a
+// loop continues store their decision in `flags` (device memory, read by
+// the host when the solve runs without a graph) and, when the solve runs as
+// a CUDA graph, also set the conditional node's value. Exactly one thread
+// of a launch sets a given condition (concurrent cudaGraphSetConditional
+// calls on one handle are not allowed).
+// LF_LOOP: run another ordinary iteration; LF_REPLACE: the next iteration
+// replaces a residual (reliable update); LF_DONE: every problem has stopped;
+// LF_OUTER: the solve goes on (set before the first iteration, cleared by
+// the restart gate); LF_RESTART: some problem restarts from its true
+// residual.
+// LF_ROUNDS (not a condition) counts the outer rounds of a solve; the gate
+// ends a solve whose rounds exceed max_iter + 64.
+enum LoopFlag { LF_LOOP = 0, LF_REPLACE = 1, LF_OUTER = 2, LF_RESTART = 3, LF_DONE = 4, LF_ROUNDS = 5, LF_COUNT = 6 };
+struct LoopCtl {
+  int* flags;                      // LF_COUNT ints (NULL: no loop control in this launch)
+  unsigned long long h[LF_COUNT];  // cudaGraphConditionalHandle per flag (graph mode)
+  unsigned int have;               // bit k: h[k] is valid in the graph being run
+  int direct;                      // 1: one problem; the direction kernel sets LF_LOOP, LF_REPLACE, LF_DONE
 };
 
 // Column-pass modes: ITER (one PCG iteration: beta, convergence), NORM
@@ -104,6 +138,7 @@ enum ColMode {
 // Flag or-ed into COL_ITER (2D): store one partial per block and leave the
 // finalisation to the next direction kernel (deferred reduction).
 constexpr int COL_DEFER = 16;
+
 
 // Material / operator description for the row kernels (2D: nz = 1).
 // Vector (D = d, elasticity): K u = grad+^T [g C_omega : sym grad+ u];
@@ -133,6 +168,10 @@ struct Op {
   // the constants above rounded to T by the host (the float kernels use
   // these, so they convert nothing per thread): 1/h, lam, mu, kap, c0c
   T ih_t, lam_t[2], mu_t[2], kap_t[2], c0c_t;
+  // elasticity: a prescribed stress field tau (Voigt, nv x N; NULL = 0)
+  // subtracted from the stress in the residual, r = -grad+^T [sigma - tau]:
+  // the right-hand side grad+^T tau of the equilibrium adjoint
+  const T* pre;
 };
 
 // The iterate: double in FP64; in MIXED an unevaluated float pair
@@ -155,8 +194,9 @@ struct Vec2 {
   // partial count per problem (0: the stencil finalised alpha itself), and
   // whether rz_next holds the residual norm to commit
   const double* pcol;
-  int ncol, nsten, defer_rz;
-  const int* mode;    // per problem: 0 normal, 1 reliable update, 2 restart (NULL = all 0)
+  int ncol, nsten;
+  int* mode;    // per problem: 0 normal, 1 reliable update, 2 restart (NULL = all 0)
+  LoopCtl ctl;  // loop decisions of the direction kernel
 };
 
 // Problems of a uniform batch sit back to back: problem b's scalar fields at
@@ -172,6 +212,7 @@ __device__ __forceinline__ void problem_views(Op<T>& op, Vec2<T>& v, int b, size
   if (op.mask) op.mask += o1;
   if (op.srcd) op.srcd += o1;
   if (op.srct) op.srct += o1;
+  if (op.pre) op.pre += (size_t)b * (D == 3 ? 6 : 3) * N;
   if (v.u) v.u += oD;
   if (v.uh) v.uh += oD;
   if (v.ul) v.ul += oD;
@@ -262,7 +303,7 @@ cudaError_t launch_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<
 template <typename T, int FY, int NY, int CWC>
 cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec<T>& sp,
                            const Shape2& sh, int mode, int inverse, double* partials,
-                           SolverScalars* sc, const int* pmode, cudaStream_t st);
+                           SolverScalars* sc, int* pmode, cudaStream_t st);
 template <typename T, int FX>
 cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int inverse,
                           const Shape2& sh, cudaStream_t st);
@@ -301,7 +342,7 @@ inline cudaError_t launch_residual_f(int fx, const Op<T>& op, const Vec2<T>& v,
 template <typename T>
 inline cudaError_t launch_colpass_f(int fy, int nx, int ny, cx<T>* S, const FftPlanDev<T>& py,
                                     const Spec<T>& sp, const Shape2& sh, int mode, int inverse,
-                                    double* partials, SolverScalars* sc, const int* pmode,
+                                    double* partials, SolverScalars* sc, int* pmode,
                                     cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     // compile-time column plans for the benchmark lengths and strip widths
@@ -332,7 +373,7 @@ cudaError_t launch3_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev
                              int zero_u, int filter, cudaStream_t st);
 template <typename T, int FL, int NL, int CWC>
 cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage, const FftPlanDev<T>& pl,
-                          const Spec<T>& sp, int mode, double* partials, SolverScalars* sc, const int* pmode,
+                          const Spec<T>& sp, int mode, double* partials, SolverScalars* sc, int* pmode,
                           cudaStream_t st);
 
 template <typename T, int D>
@@ -345,7 +386,7 @@ inline cudaError_t launch3_residual_f(int fx, const Op<T>& op, const Vec2<T>& v,
 template <typename T>
 inline cudaError_t launch3_lines_f(int fl, cx<T>* S, const Shape3& sh, int D, int axis, int stage,
                                    const FftPlanDev<T>& pl, const Spec<T>& sp, int mode, double* partials,
-                                   SolverScalars* sc, const int* pmode, cudaStream_t st) {
+                                   SolverScalars* sc, int* pmode, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     const int cw = axis == 1 ? sh.cw_y : sh.cw_z;
     if (cw == 16) {
@@ -433,6 +474,40 @@ cudaError_t launch_df_split(long long n, const double* u, float* uh, float* ul, 
 cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc, int batch, double invN, int fp32,
                                 cudaStream_t st);
 cudaError_t launch_df_merge(long long n, const float* uh, const float* ul, double* u, cudaStream_t st);
+
+// Reverse sweep of the staggered solve (adjoint.cu).
+cudaError_t launch_fill(long long N, double v, double* p, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj_m0b(long long N, const T* H, double a, double* m0b, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj_history(int dim, long long N, const uint8_t* phase, double lam0, double lam1, double mu0,
+                               double mu1, const T* strain, const T* efield, double scale, const T* Hprev,
+                               const double* d, const double* lam_pf, const double* lam_inv, double* dJ_dH, T* tau,
+                               double* dJde, double* ddirect, int energy_last, const double* dprev, double kappa,
+                               double vol, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj_eqpost(int dim, int nx, int ny, int nz, const uint8_t* phase, double lam0, double lam1,
+                              double mu0, double mu1, const T* strain, const T* efield, double scale,
+                              const double* dprev, double kappa, const double* mu, const double* mu_inv, double h,
+                              const double* dJde, const double* ddirect, double* dJdd, double* grad,
+                              cudaStream_t st);
+// x *= 2^k chosen so that max |x| lands in [target / 2, target); scale[0] =
+// 2^k, scale[1] = 2^-k on the device (m: one 8-byte scratch slot).
+template <typename X>
+cudaError_t launch_adj_normalise(long long n, X* x, unsigned long long* m, double target, double* scale,
+                                 cudaStream_t st);
+
+// Control kernels of the device-driven PCG (control.cu).
+cudaError_t launch_sc_init(SolverScalars* sc, int batch, double tol2, int max_iter, int reliable, cudaStream_t st);
+cudaError_t launch_zero_rhs(double* u, float* uh, float* ul, long long n, SolverScalars* sc, int batch, int has_mask,
+                            cudaStream_t st);
+cudaError_t launch_loopctl(const SolverScalars* sc, const int* mode, int batch, const LoopCtl& ctl,
+                           cudaStream_t st);
+cudaError_t launch_gate(SolverScalars* sc, int* mode, int batch, const LoopCtl& ctl, int max_rounds, cudaStream_t st);
+cudaError_t launch_sync_flags(const LoopCtl& ctl, cudaStream_t st);
+cudaError_t launch_clear_modes(int* mode, int batch, cudaStream_t st);
+cudaError_t launch_set_flag(const LoopCtl& ctl, int k, int value, cudaStream_t st);
+cudaError_t launch_stamp(unsigned long long* slot, cudaStream_t st);
 
 // 3D post-processing (post3d.cu): results[b * 13 + k] (6 stress sums, 6
 // strain sums, energy) and results[b * 6 + k] (beta_pore, beta_solid, 3 mean

@@ -244,6 +244,23 @@ bool choose_line_shape(const HostPlan& px, int nlines, int dim, int nxs3, int ns
   return true;
 }
 
+// Whether L lines per block fit the x-line direction (dir) or update kernel
+// (shared memory within optin, widest pass within 512 threads, index ranges
+// within 16 bits), and the threads such a block takes.
+template <typename T>
+bool line_shape_ok(const HostPlan& px, int L, bool dir, int dim, int nxs3, size_t optin_total) {
+  const int nx = px.n;
+  const int nf = dim == 3 ? 2 : 1;
+  const int Dmax = dim == 3 ? 3 : 2;
+  const size_t sm = dir ? xdir_smem<T>(nx, L, Dmax, dim) : xupd_smem<T>(nx, L, Dmax, dim);
+  return L >= 1 && sm <= optin_total - 1024 && need_threads(px, nf * L) <= 512 && (long long)L * nxs3 < 65536 &&
+         (long long)L * nx < 65536;
+}
+inline int line_threads(const HostPlan& px, int L, int dim) {
+  const int nf = dim == 3 ? 2 : 1;
+  return std::min(512, std::max(256, round32(need_threads(px, nf * L))));
+}
+
 inline void choose_sten_shape(int nx, int ny, int nz, int dim, int nsm, int batch, StenShape& s) {
   s = StenShape();
   s.batch = batch;

@@ -36,7 +36,8 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
   const int bp = blockIdx.y;
-  if (filter && !(v.mode && v.mode[bp] != 0)) return;  // only problems being replaced / restarted
+  if (filter == 1 && !(v.mode && v.mode[bp] != 0)) return;  // only problems being replaced / restarted
+  if (filter == 2 && !unchecked_stop(v.sc + bp)) return;       // only newly stopped problems
   problem_views<T, D>(op, v, bp, N);
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
@@ -80,9 +81,15 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
       const double gg = op.g ? (double)op.g[gi] : 1.0;
       const double lam = gg * op.lam[ph], mu = gg * op.mu[ph];
       const double tr = exx + eyy;
-      SG[i] = lam * tr + 2.0 * mu * exx;
-      SG[SR + i] = lam * tr + 2.0 * mu * eyy;
-      SG[2 * SR + i] = 2.0 * mu * exy;
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0;  // prescribed stress (Voigt xx, yy, xy)
+      if (op.pre) {
+        t0 = (double)op.pre[gi];
+        t1 = (double)op.pre[N + gi];
+        t2 = (double)op.pre[2 * N + gi];
+      }
+      SG[i] = lam * tr + 2.0 * mu * exx - t0;
+      SG[SR + i] = lam * tr + 2.0 * mu * eyy - t1;
+      SG[2 * SR + i] = 2.0 * mu * exy - t2;
     } else {
       const int c0 = yy * nx + x;
       const double u = P[c0];
@@ -248,7 +255,7 @@ __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* 
 template <typename T, int FY, int NY, int CWC>
 __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev<T> py, Spec<T> sp, int CW,
                                             int mode_arg, int inverse, double* partials, SolverScalars* sc,
-                                            const int* pmode) {
+                                            int* pmode) {
   int mode = mode_arg & ~COL_DEFER;
   const int bp = blockIdx.y;
   S += (size_t)bp * nx * ny;
@@ -268,6 +275,7 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   grid_dep_sync();  // plan and tables are constant; everything below follows the previous kernel
   if (mode == COL_ITER && pmode && pmode[bp] == 1) mode = COL_TRUE;  // reliable update of this problem
   if (mode == COL_RESTART && !(pmode && pmode[bp] == 2)) return;      // only restarting problems
+  if (mode == COL_TRUENORM && sc && !unchecked_stop(sc)) return;      // only newly stopped problems
   if (mode != COL_PLAIN && mode != COL_NORM && mode != COL_TRUENORM && mode != COL_RESTART &&
       done_flag(sc))
     return;
@@ -294,7 +302,7 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass(int nx, int ny, cx<T>* S, FftPlanDev
   const double tot = deferred_total<T>(partials, gridDim.x, redf, red);
   if (threadIdx.x == 0) {
     sc->cnt[1] = 0u;
-    finalize_col(sc, mode, tot * sp.invN);
+    finalize_col(sc, mode, tot * sp.invN, pmode ? pmode + bp : nullptr);
   }
 }
 
@@ -331,7 +339,7 @@ cudaError_t launch_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<
 template <typename T, int FY, int NY, int CWC>
 cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec<T>& sp,
                            const Shape2& sh, int mode, int inverse, double* partials,
-                           SolverScalars* sc, const int* pmode, cudaStream_t st) {
+                           SolverScalars* sc, int* pmode, cudaStream_t st) {
   const int CW = sh.cols;
   const size_t sm = (size_t)ny * CW * sizeof(cx<T>) + tw_smem_bytes<T>(ny) + (size_t)(ny + CW) * sizeof(T);
   static SmemOptIn cfg;
@@ -365,17 +373,17 @@ cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int
   FFTMECH_INST_TD(T, 2, F)                                                                         \
   template cudaError_t launch_colpass<T, F, 0, 0>(int, int, cx<T>*, const FftPlanDev<T>&,         \
                                             const Spec<T>&, const Shape2&, int, int, double*,    \
-                                            SolverScalars*, const int*, cudaStream_t);            \
+                                            SolverScalars*, int*, cudaStream_t);            \
   template cudaError_t launch_rowfft<T, F>(int, int, cx<T>*, const FftPlanDev<T>&, int,           \
                                            const Shape2&, cudaStream_t);
 // column passes of a compile-time length (float) for strips of 4 or 8 columns
 #define FFTMECH_INST_COL_FIXED(NY)                                                                               \
   template cudaError_t launch_colpass<float, FAM_ALL, NY, 4>(int, int, cx<float>*, const FftPlanDev<float>&,    \
                                                              const Spec<float>&, const Shape2&, int, int,       \
-                                                             double*, SolverScalars*, const int*, cudaStream_t); \
+                                                             double*, SolverScalars*, int*, cudaStream_t); \
   template cudaError_t launch_colpass<float, FAM_ALL, NY, 8>(int, int, cx<float>*, const FftPlanDev<float>&,    \
                                                              const Spec<float>&, const Shape2&, int, int,       \
-                                                             double*, SolverScalars*, const int*, cudaStream_t);
+                                                             double*, SolverScalars*, int*, cudaStream_t);
 #define FFTMECH_INST_FAMILY(F) \
   FFTMECH_INST_T(float, F)     \
   FFTMECH_INST_T(double, F)

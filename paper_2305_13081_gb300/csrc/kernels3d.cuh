@@ -54,6 +54,7 @@ __device__ __forceinline__ void problem_views3(Op<T>& op, Vec2<T>& v, int b, siz
   if (op.mask) op.mask += o1;
   if (op.srcd) op.srcd += o1;
   if (op.srct) op.srct += o1;
+  if (op.pre) op.pre += (size_t)b * (D == 3 ? 6 : 3) * N;
   if (v.u) v.u += oD;
   if (v.uh) v.uh += oD;
   if (v.ul) v.ul += oD;
@@ -106,7 +107,8 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
   const size_t N = plane * nz;
   const int bp = blockIdx.y;
   grid_dep_sync();
-  if (filter && !(v.mode && v.mode[bp] != 0)) return;
+  if (filter == 1 && !(v.mode && v.mode[bp] != 0)) return;  // only problems being replaced / restarted
+  if (filter == 2 && !unchecked_stop(v.sc + bp)) return;       // only newly stopped problems
   problem_views3<T, D>(op, v, bp, N, sst);
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
@@ -168,14 +170,19 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
         const double lam = gg * op.lam[ph], mu = gg * op.mu[ph];
         const double lt = lam * (exx + eyy + ezz);
         const double m2 = 2.0 * mu;
-        if (inner) {
-          SP[i] = lt + m2 * exx;
-          SP[SS + i] = lt + m2 * eyy;
-          SP[2 * SS + i] = m2 * exy;
+        double t[6] = {0, 0, 0, 0, 0, 0};  // prescribed stress (Voigt xx, yy, zz, yz, xz, xy)
+        if (op.pre) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) t[k] = (double)op.pre[k * N + gi];
         }
-        Zc_[i] = m2 * exz;
-        Zc_[SS + i] = m2 * eyz;
-        Zc_[2 * SS + i] = lt + m2 * ezz;
+        if (inner) {
+          SP[i] = lt + m2 * exx - t[0];
+          SP[SS + i] = lt + m2 * eyy - t[1];
+          SP[2 * SS + i] = m2 * exy - t[5];
+        }
+        Zc_[i] = m2 * exz - t[4];
+        Zc_[SS + i] = m2 * eyz - t[3];
+        Zc_[2 * SS + i] = lt + m2 * ezz - t[2];
       } else {
         const double p = Pc[i];
         const double kap = op.kap[ph];
@@ -283,7 +290,7 @@ template <typename T, int FL, int NL, int CWC>
 __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long long set_stride, int nlines,
                                          long long line_stride, int ncols, FftPlanDev<T> pl, Spec<T> sp,
                                          int CW, int stage, int mode, double* partials, SolverScalars* sc,
-                                         const int* pmode) {
+                                         int* pmode) {
   const int b = blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(pl.n);
@@ -393,7 +400,7 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
   if (publish_partials<1>(bt, part_b, &sc[b].cnt[1])) {
     double tot[1];
     gather_partials<1>(tot, part_b, &sc[b].cnt[1], red);
-    if (threadIdx.x == 0) finalize_col(sc + b, mode, tot[0] * sp.invN);
+    if (threadIdx.x == 0) finalize_col(sc + b, mode, tot[0] * sp.invN, pmode ? pmode + b : nullptr);
   }
 }
 
@@ -414,7 +421,7 @@ cudaError_t launch3_residual(const Op<T>& op, const Vec2<T>& v, const FftPlanDev
 
 template <typename T, int FL, int NL, int CWC>
 cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage, const FftPlanDev<T>& pl,
-                          const Spec<T>& sp, int mode, double* partials, SolverScalars* sc, const int* pmode,
+                          const Spec<T>& sp, int mode, double* partials, SolverScalars* sc, int* pmode,
                           cudaStream_t st) {
   const int nx = sh.nx, ny = sh.ny, nz = sh.nz;
   const int nxs = nxs_of(nx, D);
@@ -440,13 +447,13 @@ cudaError_t launch3_lines(cx<T>* S, const Shape3& sh, int D, int axis, int stage
   FFTMECH_INST3_TD(T, 1, F)                                                                          \
   FFTMECH_INST3_TD(T, 3, F)                                                                          \
   template cudaError_t launch3_lines<T, F, 0, 0>(cx<T>*, const Shape3&, int, int, int, const FftPlanDev<T>&, \
-                                           const Spec<T>&, int, double*, SolverScalars*, const int*,  \
+                                           const Spec<T>&, int, double*, SolverScalars*, int*,  \
                                            cudaStream_t);
 // y / z line passes of a compile-time length (float, strips of 16 columns)
 #define FFTMECH_INST3_LINES_FIXED(NL)                                                                      \
   template cudaError_t launch3_lines<float, FAM_ALL, NL, 16>(cx<float>*, const Shape3&, int, int, int,    \
                                                              const FftPlanDev<float>&, const Spec<float>&, \
-                                                             int, double*, SolverScalars*, const int*,    \
+                                                             int, double*, SolverScalars*, int*,    \
                                                              cudaStream_t);
 #define FFTMECH_INST3_FAMILY(F) \
   FFTMECH_INST3_T(float, F)     \

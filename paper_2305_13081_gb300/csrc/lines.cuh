@@ -70,7 +70,12 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
   unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
   const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
   grid_dep_sync();  // the plan is constant; everything below follows the previous kernel
-  if (done_flag(v.sc)) return;
+  // loop decisions of a one-problem solve are taken here, by block 0's thread 0
+  const bool lead = v.ctl.direct && blockIdx.x == 0 && threadIdx.x == 0;
+  if (done_flag(v.sc)) {
+    if (lead) loop_decide(v.ctl, 0, 0);
+    return;
+  }
   const int l0 = blockIdx.x * L;
   const int nl = min(L, nlines - l0);
   const int nxs = spec_row(nx, D, DIM);
@@ -111,14 +116,18 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
           s->rz = tot;
           s->done = 1;
           s->status = FFTMECH_ERR_NONFINITE;
+          if (v.mode) v.mode[bp] = 0;
         }
-      } else if (tot <= s->tol2 * s->rz0) {
+      } else if (tot <= s->tol2 * s->rz0 || vol_readi(&s->iter) + 1 >= s->max_iter) {
+        // converged, or the iteration limit reached with this column pass
         if (w0) {
+          const bool ok = tot <= s->tol2 * s->rz0;
           s->iter += 1;
           if (is_true) s->rz_true = tot;
           s->rz = tot;
           s->done = 1;
-          s->status = FFTMECH_OK;
+          s->status = ok ? FFTMECH_OK : FFTMECH_ERR_NOT_CONVERGED;
+          if (v.mode) v.mode[bp] = 0;
         }
       } else {
         double beta = tot / vol_read(&s->rz);
@@ -126,13 +135,19 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
         // the float recursion had drifted: restart the direction instead
         if (is_true && beta > 1.0) beta = 0.0;
         if (w0) {
+          // rz_next is committed to rz by the next stencil kernel's block 0
           s->rz_next = tot;
+          s->rz_pending = 1;
           if (is_true) s->rz_true = tot;
           set_beta(s, beta);
+          const int next = reliable_next(s, tot, is_true);
+          if (v.mode) v.mode[bp] = next;
+          if (lead) loop_decide(v.ctl, 1, next);
         }
         b_s = (T)beta;
         stop_s = 0;
       }
+      if (lead && stop_s) loop_decide(v.ctl, 0, 0);
     }
     __syncthreads();
     if (stop_s) {
@@ -140,10 +155,11 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
       return;
     }
     b = b_s;
-  } else if constexpr (sizeof(T) == 4) {
-    b = vol_readf(&v.sc->beta_f);
   } else {
-    b = vol_read(&v.sc->beta);
+    // the column pass finalised the iteration (and chose the next mode)
+    if (lead) loop_decide(v.ctl, 1, v.mode ? vol_readi(v.mode + bp) == 1 : 0);
+    if constexpr (sizeof(T) == 4) b = vol_readf(&v.sc->beta_f);
+    else b = vol_read(&v.sc->beta);
   }
   const bool with_old = b != T(0);  // the first iteration has p = z
   // the old direction and the 2D spectral rows by asynchronous copies (unless
@@ -253,11 +269,7 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
     if (threadIdx.x == 0) {
       SolverScalars* s = v.sc;
       const bool w0 = blockIdx.x == 0;
-      const double rz = v.defer_rz ? vol_read(&s->rz_next) : vol_read(&s->rz);
-      if (w0 && v.defer_rz) {
-        s->rz = rz;
-        s->iter += 1;
-      }
+      const double rz = vol_read(&s->rz);  // committed by the stencil kernel
       stop_s = !(pq > 0.0) || !isfinite(pq);
       if (stop_s) {
         if (w0) {

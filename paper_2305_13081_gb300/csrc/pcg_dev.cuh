@@ -13,6 +13,11 @@ static __device__ __forceinline__ int done_flag(const SolverScalars* sc) {
   return *reinterpret_cast<const volatile int*>(&sc->done);
 }
 
+// A stopped problem whose FP64 true residual the gate has not seen yet.
+static __device__ __forceinline__ bool unchecked_stop(const SolverScalars* sc) {
+  return done_flag(sc) && *reinterpret_cast<const volatile int*>(&sc->checked) == 0;
+}
+
 static __device__ __forceinline__ double vol_read(const double* p) {
   return *reinterpret_cast<const volatile double*>(p);
 }
@@ -39,7 +44,57 @@ static __device__ __forceinline__ void set_beta(SolverScalars* sc, double b) {
   sc->beta_f = (float)b;
 }
 
-static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
+// Reliable updates (MIXED): the mode of the next iteration of a problem
+// that continues. After a replacement its residual norm becomes the new
+// reference; otherwise the next iteration replaces the float recursive
+// residual by the FP64 true residual once <r, M^-1 r> has fallen 100-fold
+// below that reference (the search direction is kept). Single writer.
+static __device__ __forceinline__ int reliable_next(SolverScalars* sc, double tot, int was_replacement) {
+  if (!sc->reliable) return 0;
+  if (was_replacement) {
+    sc->rz_rep = tot;
+    return 0;
+  }
+  if (tot < 1e-2 * sc->rz_rep) {
+    sc->nreplace += 1;
+    return 1;
+  }
+  return 0;
+}
+
+// Sets loop flag k to `value` in device memory and, when the solve runs as a
+// graph that holds the flag's conditional node, the node's condition.
+static __device__ __forceinline__ void set_loop_flag(const LoopCtl& c, int k, int value) {
+  if (!c.flags) return;
+  c.flags[k] = value;
+  if (c.have & (1u << k)) cudaGraphSetConditional((cudaGraphConditionalHandle)c.h[k], (unsigned int)value);
+}
+
+// Deferred reductions (2D): block 0 of the stencil kernel commits the
+// residual norm that the direction kernel left in rz_next (the direction
+// kernel's blocks all read rz as the previous norm, so none of them may
+// overwrite it). The update kernel that follows reads the committed rz.
+static __device__ __forceinline__ void commit_pending_rz(SolverScalars* sc) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (*reinterpret_cast<volatile int*>(&sc->rz_pending)) {
+    sc->rz = *reinterpret_cast<volatile double*>(&sc->rz_next);
+    sc->iter += 1;
+    sc->rz_pending = 0;
+  }
+}
+
+// Loop decisions after a direction (single writer): an active problem runs
+// an ordinary iteration next, or a replacement iteration; a stopped one
+// ends the loop.
+static __device__ __forceinline__ void loop_decide(const LoopCtl& c, int active, int replace) {
+  set_loop_flag(c, LF_LOOP, active && !replace);
+  set_loop_flag(c, LF_REPLACE, active && replace);
+  set_loop_flag(c, LF_DONE, !active);
+}
+
+// pmode: this problem's iteration mode (NULL when there is none); ITER and
+// TRUE set it for the next iteration (reliable updates).
+static __device__ void finalize_col(SolverScalars* sc, int mode, double tot, int* pmode = nullptr) {
   if (mode == COL_NORM) { sc->rz0 = tot; return; }
   if (mode == COL_PLAIN) return;
   if (mode == COL_TRUENORM) { sc->rz_true = tot; return; }
@@ -51,6 +106,7 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
   }
   if (mode == COL_INIT) {
     sc->rz = tot;
+    sc->rz_rep = tot;
     set_beta(sc, 0.0);
     sc->iter = 0;
     if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
@@ -61,6 +117,7 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
     // the true residual replaced r after a recursive convergence: restart
     sc->rz = tot;
     sc->rz_true = tot;
+    sc->rz_rep = tot;
     set_beta(sc, 0.0);
     if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; }
     else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; }
@@ -70,13 +127,20 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot) {
   if (mode == COL_TRUE) sc->rz_true = tot;
   const double rz_old = sc->rz;
   sc->rz = tot;
-  if (tot <= sc->tol2 * sc->rz0) { sc->done = 1; sc->status = FFTMECH_OK; return; }
-  if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = FFTMECH_ERR_NOT_CONVERGED; return; }
+  const bool conv = tot <= sc->tol2 * sc->rz0;
+  if (conv || sc->iter >= sc->max_iter) {
+    sc->done = 1;
+    sc->status = conv ? FFTMECH_OK : FFTMECH_ERR_NOT_CONVERGED;
+    if (pmode) *pmode = 0;
+    return;
+  }
   double beta = tot / rz_old;
   // a replaced residual larger than the recursive one it replaces means the
   // float recursion had drifted: restart the direction instead of mixing
   if (mode == COL_TRUE && beta > 1.0) beta = 0.0;
   set_beta(sc, beta);
+  const int next = reliable_next(sc, tot, mode == COL_TRUE);
+  if (pmode) *pmode = next;
 }
 
 // Deferred reductions (2D): a producer kernel stores one partial per block
@@ -198,6 +262,7 @@ __device__ __forceinline__ void store_deferred_partial<double>(Acc<double>& acc,
 static __device__ __forceinline__ bool col_active(int mode, const int* pmode, const SolverScalars* sc) {
   if (mode == COL_RESTART) return pmode && *pmode == 2;
   if (mode == COL_ITER || mode == COL_TRUE) return !done_flag(sc);
+  if (mode == COL_TRUENORM) return unchecked_stop(sc);  // the gate's true residuals: newly stopped problems
   return true;
 }
 

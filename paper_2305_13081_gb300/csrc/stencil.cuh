@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kSten2Threads) k_sten2(Op<T> op, Vec2<T> v) {
   sten_views<T, D>(op, v, bp, N);
   grid_dep_sync();
   if (done_flag(v.sc)) return;
+  commit_pending_rz(v.sc);
   __shared__ double red[32];
   __shared__ float redf[64];
   const T* __restrict__ P = v.p_in;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(kSten2Threads) k_sten3(Op<T> op, Vec2<T> v, in
   sten_views<T, D>(op, v, bp, N);
   grid_dep_sync();
   if (done_flag(v.sc)) return;
+  commit_pending_rz(v.sc);
   __shared__ double red[32];
   __shared__ float redf[64];
   const T* __restrict__ P = v.p_in;

@@ -34,6 +34,12 @@ FFTMECH_DIFF_HOMOGENISE = 1
 FFTMECH_DIFF_TRANSIENT = 2
 FFTMECH_EIG_FROM_PRECIPITATE = 0
 FFTMECH_EIG_PRESCRIBED = 1
+# execution of a solve or a staggered step
+FFTMECH_EXEC_GRAPH = 0
+FFTMECH_EXEC_HOST = 1
+# objectives of the eigenstrain adjoint
+FFTMECH_OBJ_ENERGY = 0
+FFTMECH_OBJ_DAMAGE = 1
 # kernel classes (instrumentation)
 FFTMECH_K_DIRECTION = 0
 FFTMECH_K_UPDATE = 1
@@ -63,7 +69,7 @@ class fftmech_materials(ctypes.Structure):
 class fftmech_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("replace_residual", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("launch_mode", ctypes.c_int)]
+                ("launch_mode", ctypes.c_int), ("execution", ctypes.c_int)]
 
 
 class fftmech_solve_info(ctypes.Structure):
@@ -129,6 +135,18 @@ def load_library(path=LIB_PATH):
         "fftmech_phasefield_solve": (i, [vp, vp, vp, vp, vp, vp, P(fftmech_solve_info)]),
         "fftmech_staggered_step": (i, [vp, P(fftmech_state), P(fftmech_step_params),
                                        P(fftmech_solve_info)]),
+        "fftmech_staggered_step_async": (i, [vp, P(fftmech_state), P(fftmech_step_params)]),
+        "fftmech_step_info": (i, [vp, P(fftmech_solve_info)]),
+        "fftmech_adjoint_eigenstrain": (i, [vp, vp, vp, i, P(d), P(d), i, i, vp, P(d), P(fftmech_solve_info)]),
+        "fftmech_autotune": (i, [vp, i, P(d), P(d), P(ctypes.c_char_p)]),
+        "fftmech_problem_offset": (i, [vp, i, i, P(ctypes.c_longlong)]),
+        "fftmech_graph_stats": (i, [vp, P(ctypes.c_longlong), P(ctypes.c_longlong), P(ctypes.c_longlong),
+                                    P(i), P(ctypes.c_char_p)]),
+        "fftmech_group_create": (i, [P(vp), P(vp), i, vp]),
+        "fftmech_group_destroy": (i, [vp]),
+        "fftmech_group_step": (i, [vp, P(P(fftmech_state)), P(P(fftmech_step_params)), P(P(fftmech_solve_info))]),
+        "fftmech_group_stats": (i, [vp, P(ctypes.c_longlong), P(ctypes.c_longlong), P(ctypes.c_longlong)]),
+        "fftmech_group_last_error": (ctypes.c_char_p, [vp]),
         "fftmech_staggered_step_many": (i, [P(vp), i, P(P(fftmech_state)), P(P(fftmech_step_params)),
                                             P(P(fftmech_solve_info))]),
         "fftmech_fft": (i, [i, P(i), i, i, vp, vp]),
@@ -268,6 +286,64 @@ def fftmech_staggered_step(ctx, state, params, infos=None):
     return infos
 
 
+def fftmech_staggered_step_async(ctx, state, params):
+    """Enqueues a staggered step (device pointers only) and returns at once."""
+    rc = load_library().fftmech_staggered_step_async(ctx, ctypes.byref(state), ctypes.byref(params))
+    _check(rc, ctx)
+    return rc
+
+
+def fftmech_step_info(ctx, infos=None):
+    """Synchronises and returns the 3 records per problem of the last step."""
+    infos = infos or _infos(ctx, 3)
+    rc = load_library().fftmech_step_info(ctx, infos)
+    _check(rc, ctx, _SOLVER_OK)
+    return infos
+
+
+def fftmech_adjoint_eigenstrain(ctx, phase, e_field, ramp, eps_mac, objective, checkpoint_every, grad):
+    """Objective value J of the staggered solve with the eigenstrain
+    ramp[s] e(x) and its gradient dJ/de written to `grad` (device buffers);
+    returns (J, the 3 records of the forward's last step)."""
+    steps = len(ramp)
+    r = (ctypes.c_double * steps)(*[float(x) for x in ramp])
+    e = c_double6(*(list(eps_mac or []) + [0.0] * 6)[:6])
+    J = ctypes.c_double(0.0)
+    infos = (fftmech_solve_info * 3)()
+    rc = load_library().fftmech_adjoint_eigenstrain(ctx, ptr(phase), ptr(e_field), steps, r, e, int(objective),
+                                                    int(checkpoint_every), ptr(grad), ctypes.byref(J), infos)
+    _check(rc, ctx, _SOLVER_OK)
+    return J.value, infos
+
+
+def fftmech_autotune(ctx, iterations=30):
+    """Tunes the context's launch shapes; returns (us per iteration before,
+    after, description of the chosen shapes)."""
+    b, a = ctypes.c_double(0), ctypes.c_double(0)
+    desc = ctypes.c_char_p()
+    _check(load_library().fftmech_autotune(ctx, int(iterations), ctypes.byref(b), ctypes.byref(a),
+                                           ctypes.byref(desc)), ctx)
+    return b.value, a.value, (desc.value or b"").decode()
+
+
+def fftmech_problem_offset(ctx, problem, components):
+    off = ctypes.c_longlong(0)
+    _check(load_library().fftmech_problem_offset(ctx, int(problem), int(components), ctypes.byref(off)), ctx)
+    return off.value
+
+
+def fftmech_graph_stats(ctx):
+    """(graphs built, graph launches, kernels run by the replays, disabled, reason)."""
+    b = ctypes.c_longlong(0)
+    n = ctypes.c_longlong(0)
+    k = ctypes.c_longlong(0)
+    dis = ctypes.c_int(0)
+    why = ctypes.c_char_p()
+    _check(load_library().fftmech_graph_stats(ctx, ctypes.byref(b), ctypes.byref(n), ctypes.byref(k),
+                                              ctypes.byref(dis), ctypes.byref(why)), ctx)
+    return b.value, n.value, k.value, dis.value, (why.value or b"").decode()
+
+
 def fftmech_fft(ndim, n, precision, inverse, data, stream=None):
     nn = c_int3(*(list(n) + [1, 1, 1])[:3])
     rc = load_library().fftmech_fft(int(ndim), nn, int(precision), int(inverse), ptr(data), stream)
@@ -303,6 +379,74 @@ def fftmech_staggered_step_many(ctxs, states, params, infos=None):
     return infos
 
 
+def _handles(ctxs):
+    n = len(ctxs)
+    return (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+
+
+def fftmech_group_create(ctxs, stream=None):
+    h = ctypes.c_void_p()
+    _check(load_library().fftmech_group_create(ctypes.byref(h), _handles(ctxs), len(ctxs), stream))
+    return h
+
+
+def fftmech_group_destroy(group):
+    return load_library().fftmech_group_destroy(group)
+
+
+def fftmech_group_step(group, ctxs, states, params, infos=None):
+    """One staggered step of every context of the group (one graph launch);
+    returns the per-context info arrays (3 records per problem)."""
+    n = len(states)
+    infos = infos or [_infos(c, 3) for c in ctxs]
+    s_arr = (ctypes.POINTER(fftmech_state) * n)(*[ctypes.pointer(s) for s in states])
+    p_arr = (ctypes.POINTER(fftmech_step_params) * n)(*[ctypes.pointer(p) for p in params])
+    i_arr = (ctypes.POINTER(fftmech_solve_info) * n)(*[ctypes.cast(x, ctypes.POINTER(fftmech_solve_info))
+                                                       for x in infos])
+    lib = load_library()
+    rc = lib.fftmech_group_step(group, s_arr, p_arr, i_arr)
+    if rc not in _SOLVER_OK:
+        raise FftmechError(rc, lib.fftmech_status_string(rc).decode() + ": " +
+                           lib.fftmech_group_last_error(group).decode())
+    return infos
+
+
+def fftmech_group_last_error(group):
+    return load_library().fftmech_group_last_error(group).decode()
+
+
+def fftmech_group_stats(group):
+    """(graphs built, graph launches, kernels run)."""
+    b, n, k = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _check(load_library().fftmech_group_stats(group, ctypes.byref(b), ctypes.byref(n), ctypes.byref(k)))
+    return b.value, n.value, k.value
+
+
+class Group:
+    """Owns one fftmech group of contexts (create / destroy)."""
+
+    def __init__(self, contexts, stream=None):
+        self.contexts = list(contexts)
+        self.handle = fftmech_group_create([c.handle for c in self.contexts], stream)
+
+    def step(self, states, params):
+        return fftmech_group_step(self.handle, [c.handle for c in self.contexts], states, params)
+
+    def stats(self):
+        return fftmech_group_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            fftmech_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def fftmech_profile_enable(ctx, enable):
     return _check(load_library().fftmech_profile_enable(ctx, int(enable)), ctx)
 
@@ -335,13 +479,15 @@ def make_materials(m):
     return out
 
 
-def make_opts(tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, launch_mode=0):
+def make_opts(tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, launch_mode=0,
+              execution=FFTMECH_EXEC_GRAPH):
     o = fftmech_solver_opts()
     o.tol = tol
     o.max_iter = max_iter
     o.replace_residual = replace_residual
     o.check_every = check_every
     o.launch_mode = launch_mode
+    o.execution = execution
     return o
 
 
@@ -350,13 +496,13 @@ class Context:
 
     def __init__(self, shape, materials, precision=FFTMECH_FP64, h=5e-6, h_diff=1.0,
                  tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, stream=None, batch=1,
-                 launch_mode=0):
+                 launch_mode=0, execution=FFTMECH_EXEC_GRAPH):
         self.shape = tuple(shape)
         self.precision = precision
         self.batch = batch
         self.grid = make_grid(shape, h, h_diff)
         self.mat = make_materials(materials)
-        self.opts = make_opts(tol, max_iter, replace_residual, check_every, launch_mode)
+        self.opts = make_opts(tol, max_iter, replace_residual, check_every, launch_mode, execution)
         if batch == 1:
             self.handle = fftmech_create(self.grid, self.mat, precision, self.opts, stream)
         else:

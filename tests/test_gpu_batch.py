@@ -186,3 +186,52 @@ def test_many_contexts_equal_separate_steps():
         for k in a:
             assert np.array_equal(a[k], b[k])
     assert results["many"][1]["damage"].max() > 0
+
+
+def test_group_graph_equals_separate_steps_and_matches_oracle():
+    """A group of three contexts of uneven grids (27^2 x 2, 81^2, 128^2 2x2
+    carpet) stepped as one graph (one launch per step, a parallel branch per
+    context) gives bit for bit the fields of separate steps, and problem 0
+    of the 27^2 context matches the oracle."""
+    mat = Materials(E_pore=2e9, M_ppt=2.2)
+    groups = [[random_carpet(27, 0.30, s)[0] for s in (1, 2)], [random_carpet(81, 0.30, 3)[0]],
+              [random_carpet(128, 0.30, 4, base=2)[0]]]
+    results = {}
+    for mode in ("group", "separate"):
+        ctxs, states, params, keep = [], [], [], []
+        for phases in groups:
+            n = phases[0].shape[0]
+            ctx = fm.Context(phases[0].shape, mat, fm.FFTMECH_FP64, h=H, h_diff=1.0, tol=1e-12, batch=len(phases))
+            bufs, st, p = _transient_state(phases[0].shape, phases, mat, (n / 4.0) ** 2 / 10)
+            ctxs.append(ctx)
+            states.append(st)
+            params.append(p)
+            keep.append(bufs)
+        grp = fm.Group(ctxs) if mode == "group" else None
+        for _ in range(2):
+            if grp is not None:
+                infos = grp.step(states, params)
+                for inf in infos:
+                    assert all(inf[i].status == fm.FFTMECH_OK for i in range(len(inf)))
+            else:
+                for c, st, p in zip(ctxs, states, params):
+                    fm.fftmech_staggered_step(c.handle, st, p)
+        torch.cuda.synchronize()
+        if grp is not None:
+            builds, launches, kernels = grp.stats()
+            assert builds == 1 and launches == 2 and kernels > 0
+            grp.close()
+        results[mode] = [{k: b[k].cpu().numpy() for k in ("c", "strain", "damage")} for b in keep]
+        for c in ctxs:
+            c.close()
+    for a, b in zip(results["group"], results["separate"]):
+        for k in a:
+            assert np.array_equal(a[k], b[k])
+    ph = groups[0][0]
+    ref = staggered.initial_state(ph)
+    for _ in range(2):
+        ref, _ = staggered.step(ref, ph, mat, H, 1.0, staggered.DIFF_TRANSIENT, staggered.EIG_FROM_PRECIPITATE,
+                                dt=(27 / 4.0) ** 2 / 10, mask=left_face_mask(ph), c_dirichlet=1.0, tol=1e-12)
+    N = ph.size
+    assert rel(results["group"][0]["c"][:N].reshape(ph.shape), ref["c"]) < 1e-10
+    assert rel(results["group"][0]["strain"][:3 * N].reshape((3,) + ph.shape), ref["strain"]) < 1e-10

@@ -49,3 +49,26 @@ def test_fft_rejects_host_pointer_and_bad_size():
     t = torch.zeros((5, 10), dtype=torch.complex128, device="cuda")
     with pytest.raises(fm.FftmechError):
         fm.fftmech_fft(2, [10, 5], fm.FFTMECH_FP64, 0, t)
+
+
+SHAPES3 = [(9, 27, 81), (27, 27, 27), (16, 12, 8), (81, 9, 243), (4, 6, 2187)]
+
+
+@pytest.mark.parametrize("shape", SHAPES3)
+@pytest.mark.parametrize("precision", [fm.FFTMECH_FP64, fm.FFTMECH_MIXED])
+@pytest.mark.parametrize("inverse", [0, 1])
+def test_fft3d_matches_numpy(shape, precision, inverse):
+    """3D transform (x lines, y columns of every plane, z columns) against
+    numpy.fft.fftn / ifftn, called twice on the same length set so that the
+    second call uses the cached plans."""
+    rng = np.random.default_rng(sum(shape) + 7 * precision + inverse)
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    ref = (np.fft.ifftn(x) * x.size) if inverse else np.fft.fftn(x)
+    dt = torch.complex128 if precision == fm.FFTMECH_FP64 else torch.complex64
+    tol = 1e-13 if precision == fm.FFTMECH_FP64 else 3e-6
+    for _ in range(2):
+        t = torch.tensor(x, dtype=dt, device="cuda")
+        fm.fftmech_fft(3, [shape[2], shape[1], shape[0]], precision, inverse, t)
+        got = t.cpu().numpy()
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < tol, err

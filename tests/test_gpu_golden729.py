@@ -6,7 +6,9 @@ tests/golden/carpet729_steps1to3.npz by tests/golden/make_carpet729_golden.py
 voxels and the sum and L2 norm of every component over all voxels.
 
 FP64 GPU path (solved to 1e-13; the oracle to 1e-12): sampled values within
-1e-10 relative L2, sums and norms within 1e-10 relative. Mixed path at the
+1e-10 relative L2; norms within 1e-10 relative, sums within 1e-10 of
+sqrt(N) times the norm (the strain's sum is the macro strain times N, zero
+here, so it has no scale of its own). Mixed path at the
 workload's tolerance 1e-8: strain and stress within 1e-5, concentration
 within 1e-6 (relative L2 over the samples), damage within 1e-4 max-abs.
 """
@@ -46,7 +48,7 @@ def run(prec, tol, steps):
     w = carpet_transient(729)
     N = w.phase.size
     ft = torch.float64 if prec == fm.FFTMECH_FP64 else torch.float32
-    ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=tol, max_iter=100000)
+    ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=tol, max_iter=30000)
     bufs = {k: torch.zeros(m * N, dtype=dt, device="cuda") for k, m, dt in
             [("c", 1, torch.float64), ("c_ppt", 1, ft), ("eig", 1, ft), ("u", 2, torch.float64),
              ("strain", 3, ft), ("stress", 3, ft), ("H", 1, ft), ("damage", 1, torch.float64)]}
@@ -86,9 +88,14 @@ def test_carpet729_first_three_steps_match_oracle_golden(prec):
             got = fields[buf]
             errs[name] = rel(got[:, idx], ref_at)
             if prec == fm.FFTMECH_FP64:
-                for stat, fn in (("sum", lambda a: a.sum(axis=1)), ("l2", lambda a: np.sqrt((a * a).sum(axis=1)))):
+                # Sums on the scale sqrt(N) |a|_2 >= sum |a| (Cauchy-Schwarz):
+                # a fluctuating field's sum can vanish (the strain's mean is
+                # the macro strain, 0 here), so its own value is no scale.
+                l2 = g[f"s{s}_{name}_l2"]
+                N = got.shape[1]
+                for stat, fn, scale in (("sum", lambda a: a.sum(axis=1), np.sqrt(N) * np.abs(l2).max()),
+                                        ("l2", lambda a: np.sqrt((a * a).sum(axis=1)), np.abs(l2).max())):
                     ref = g[f"s{s}_{name}_{stat}"]
-                    scale = np.abs(ref).max()
                     if scale > 0:
                         errs[f"{name}_{stat}"] = float(np.abs(fn(got) - ref).max() / scale)
         errs["d_maxabs"] = float(np.abs(steps[s]["damage"][:, idx] - g[f"s{s}_d_at"]).max())

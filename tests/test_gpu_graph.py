@@ -113,9 +113,11 @@ def test_graph_and_host_driven_execution_are_bit_identical(name, phases_fn, prec
         infos = [pr.step() for _ in range(3)]
         out[ex] = (pr.fields(), infos)
         if ex == fm.FFTMECH_EXEC_GRAPH:
-            builds, launches, disabled, why = fm.fftmech_graph_stats(pr.ctx.handle)
+            builds, launches, kernels, disabled, why = fm.fftmech_graph_stats(pr.ctx.handle)
             assert disabled == 0, why
             assert launches == 3 and builds >= 1
+            # at least stencil, update, column pass and direction per equilibrium iteration
+            assert kernels >= 4 * sum(inf[1]["iters"] for inf in infos)
         pr.close()
     fg, ig = out[fm.FFTMECH_EXEC_GRAPH]
     fh, ih = out[fm.FFTMECH_EXEC_HOST]
@@ -180,3 +182,37 @@ def test_step_captured_into_a_caller_graph_and_replayed():
     del g
     ref.close()
     cap.close()
+
+
+@pytest.mark.parametrize("shape,prec", [((243, 243), fm.FFTMECH_MIXED), ((27, 27, 27), fm.FFTMECH_MIXED),
+                                        ((81, 81), fm.FFTMECH_FP64)])
+def test_autotuner_keeps_results_and_caches_its_choice(shape, prec):
+    """The autotuner's choice is no slower than the default shapes on its own
+    timing, the solve with the tuned shapes still meets the oracle, and a
+    new context of the same grid starts with the cached choice."""
+    from oracle import elasticity
+    from microstructures import random_sponge as _sponge
+    ph = random_carpet(shape[0], 0.30, 31)[0] if len(shape) == 2 else _sponge(shape[0], 0.35, 31)[0]
+    eig = np.where(ph == 0, 1e-3, 0.0)
+    ctx = fm.Context(shape, MAT, prec, h=H, tol=1e-12 if prec == fm.FFTMECH_FP64 else 1e-8, max_iter=20000)
+    before, after, desc = fm.fftmech_autotune(ctx.handle, 20)
+    print("autotune", shape, before, after, desc)
+    assert after <= before * 1.0001 and after > 0
+    N = ph.size
+    d = len(shape)
+    nv = 3 if d == 2 else 6
+    ft = torch.float64 if prec == fm.FFTMECH_FP64 else torch.float32
+    u = torch.zeros(d * N, dtype=torch.float64, device="cuda")
+    strain = torch.zeros(nv * N, dtype=ft, device="cuda")
+    info = fm.fftmech_equilibrium_solve(ctx.handle, torch.as_tensor(ph.ravel()).cuda(),
+                                        torch.as_tensor(eig.ravel()).to(ft).cuda(), None, [0] * 6, u, strain, None)
+    assert info.status == fm.FFTMECH_OK
+    ref = elasticity.equilibrium_solve(ph, eig, np.ones(shape), [0] * nv, MAT, H, tol=1e-12)
+    got = strain.double().cpu().numpy().reshape(ref["strain"].shape)
+    err = np.linalg.norm(got - ref["strain"]) / np.linalg.norm(ref["strain"])
+    assert err < (1e-10 if prec == fm.FFTMECH_FP64 else 1e-5), err
+    ctx.close()
+    ctx2 = fm.Context(shape, MAT, prec, h=H)
+    _, _, desc2 = fm.fftmech_autotune(ctx2.handle, 0)  # the shapes it starts from
+    ctx2.close()
+    assert desc2.endswith("(autotuned)") and desc2.startswith(desc), (desc, desc2)

@@ -62,7 +62,7 @@ def gpu_steps(phase, prec, steps, params_fn, tol, mat, batch=1):
     dim = len(shape)
     nv = 3 if dim == 2 else 6
     ft = ftype(prec)
-    ctx = fm.Context(shape, mat, prec, h=H, h_diff=1.0, tol=tol, batch=batch, max_iter=100000)
+    ctx = fm.Context(shape, mat, prec, h=H, h_diff=1.0, tol=tol, batch=batch, max_iter=20000)
     B = batch
     bufs = {k: torch.zeros(m * N * B, dtype=dt, device="cuda") for k, m, dt in
             [("c", 1, torch.float64), ("c_ppt", 1, ft), ("eig", 1, ft), ("u", dim, torch.float64),
