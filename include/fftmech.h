@@ -263,7 +263,13 @@ typedef struct {
  * fftmech_diffusion_step. eig_mode FFTMECH_EIG_FROM_PRECIPITATE:
  * c_ppt = (c - S_sol)_+ and e = (c_ppt M_ppt - 1)_+ in the pores, 0 in the
  * solid (Sec. 2.2); FFTMECH_EIG_PRESCRIBED: e = eig_scale * eig_field
- * (eig_field: field [N]). eps_mac: macro strain (Voigt). */
+ * (eig_field: field [N]). eps_mac: macro strain (Voigt).
+ * c_macro_each / grad_c_mac_each (HOMOGENISE, optional; device memory, read
+ * when the step runs): per-problem macro concentration [B] and gradient
+ * [3 * B] of a batch, replacing c_macro and grad_c_mac (a macroscale
+ * driver gives each RVE its material point's c(X) and grad c(X), Sec. 3.2;
+ * new values need no re-capture of the step's graph). NULL: the scalars for
+ * every problem. info.mean_c reports each problem's c_macro. */
 typedef struct {
   int diffusion_mode;
   double grad_c_mac[3];
@@ -275,6 +281,8 @@ typedef struct {
   const void* eig_field;
   double eig_scale;
   double eps_mac[6];
+  const double* c_macro_each;
+  const double* grad_c_mac_each;
 } fftmech_step_params;
 
 /* One staggered load step in Algorithm 1's order (Sec. 2.5): diffusion ->
@@ -343,14 +351,15 @@ fftmech_status fftmech_adjoint_eigenstrain(fftmech_ctx* ctx, const uint8_t* phas
  * candidate) for candidate launch shapes: column strip width and stencil
  * strip rows (2D), stencil brick depth (3D), stencil blocks per problem and
  * lines per block of the x-line kernels, one parameter at a time from the
- * best so far. Applies the fastest, and keeps it for the process: contexts
- * created later for the same device, grid, batch and precision start with
- * it. Reports the time per iteration before and after (microseconds) and a
- * description of the shapes (owned by the context). Allocates temporary
- * device buffers; results of later solves change only within rounding
- * (the reductions' block partitions change). iterations = 0 only reports
- * the shapes in use (the description ends in "(autotuned)" when they came
- * from the process's cache). */
+ * best so far. Applies the fastest and keeps it for the process: a later
+ * call on another context of the same device, grid, batch and precision
+ * applies it without timing (the description then ends in "(cached)"; the
+ * times are those of the original tuning). New contexts always start from
+ * the rule-based shapes. Reports the time per iteration before and after
+ * (microseconds) and a description of the shapes (owned by the context).
+ * Allocates temporary device buffers; results of later solves change only
+ * within rounding (the reductions' block partitions change).
+ * iterations = 0 only reports the shapes in use. */
 fftmech_status fftmech_autotune(fftmech_ctx* ctx, int iterations, double* before_us, double* after_us,
                                 const char** choice);
 
@@ -402,6 +411,40 @@ const char* fftmech_group_last_error(const fftmech_group* group);
 fftmech_status fftmech_staggered_step_many(fftmech_ctx* const* ctxs, int n, fftmech_state* const* states,
                                            const fftmech_step_params* const* params,
                                            fftmech_solve_info* const* infos);
+
+/* Macroscale bar of the multiscale diffusion (Sec. 3.2): a bar along X whose
+ * face X = 0 (the steel-concrete interface) takes a constant influx
+ * `flux_in` and whose far end is closed, coupled to the M RVEs of a batched
+ * context (M = fftmech_batch_size(ctx)). The paper does not give its
+ * finite-difference scheme; this one: nodes X_m = m dX (m = 0 .. M,
+ * dX = length / M) hold the macro concentration c_m in device memory;
+ * element e (nodes e, e + 1) carries RVE e at its midpoint, which receives
+ * grad c_mac = ((c_{e+1} - c_e) / dX, 0, 0) along its x axis and
+ * c_macro = (c_e + c_{e+1}) / 2; lumped masses w = dX inside and dX / 2 at
+ * the ends, forward Euler
+ *   c_m += dt / w_m (J_{m-1/2} - J_{m+1/2}),  J_{e+1/2} = <j_x> of RVE e,
+ *   J_{-1/2} = flux_in, J_{M+1/2} = 0.
+ * length is in the RVE's length unit (h_diff per voxel); dt must satisfy
+ * dt <= dX^2 / (2 max(D_pore, D_solid)) (INVALID_ARG otherwise).
+ * c0: M + 1 host values (NULL = 0). The bar owns M + 1 + 4 M doubles of
+ * device memory. */
+typedef struct fftmech_bar fftmech_bar;
+fftmech_status fftmech_bar_create(fftmech_bar** bar, fftmech_ctx* ctx, double length, double dt, double flux_in,
+                                  const double* c0);
+fftmech_status fftmech_bar_destroy(fftmech_bar* bar);
+/* One macro time step: the element inputs from c^n, one staggered step of
+ * all RVEs (Algorithm 1 with diffusion_mode HOMOGENISE and the per-element
+ * c_macro / grad c_mac; the other fields of `params` as in
+ * fftmech_staggered_step: eigenstrain mode, eps_mac, ...), then c^{n+1}
+ * from the RVEs' mean fluxes, all enqueued on the context's stream as one
+ * CUDA graph (captured on the first call). state: device pointers of the
+ * batch. info: 3 M records as fftmech_staggered_step fills them (mean_flux
+ * and mean_c of each RVE in its diffusion record). */
+fftmech_status fftmech_bar_step(fftmech_bar* bar, const fftmech_state* state, const fftmech_step_params* params,
+                                fftmech_solve_info* info);
+/* Nodal concentrations c_0 .. c_M to / from host memory. */
+fftmech_status fftmech_bar_read(const fftmech_bar* bar, double* c_host);
+fftmech_status fftmech_bar_write(fftmech_bar* bar, const double* c_host);
 
 /* Instrumentation (no counterpart in the paper): kernel classes of the PCG
  * loop. When profiling is enabled, every launch of a class is bracketed by

@@ -135,6 +135,19 @@ def sponge_ramp(n=243, seed=13081, target_porosity=0.35, steps=50, e_final=5e-3)
         extra={"seed": seed, "porosity": porosity(phase)})
 
 
+def carpet_adjoint(n=2187, seed=7, e_seed=8, target_porosity=0.30, steps=30):
+    """Random 3x3 carpet on n^2 with a per-voxel pore eigenstrain
+    N(1e-3, (2e-4)^2) (seed e_seed), 0 in the solid, ramped linearly over
+    `steps` staggered steps (scale (s + 1) / steps); no diffusion. The
+    workload of the eigenstrain adjoint."""
+    phase, _ = random_carpet(n, target_porosity, seed)
+    return Workload(
+        name=f"random-carpet-{n}x{n}-eigenstrain-adjoint", phase=phase, materials=Materials(), h=H_MECH,
+        h_diff=H_DIFF, steps=steps, diffusion_mode=DIFF_NONE, eig_mode=EIG_PRESCRIBED,
+        eig=gaussian_pore_eigenstrain(phase, e_seed), eig_ramp=[(s + 1) / steps for s in range(steps)],
+        extra={"seed": seed, "e_seed": e_seed, "porosity": porosity(phase)})
+
+
 def gaussian_pore_eigenstrain(phase, seed, mean=1e-3, std=2e-4):
     """Per-voxel eigenstrain N(mean, std^2) in the pores, 0 in the solid."""
     z = standard_normal(derive_key(seed, 0xE16), phase.size).reshape(phase.shape)

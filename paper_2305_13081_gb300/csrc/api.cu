@@ -102,7 +102,7 @@ enum StageSlot {
 // the whole step reports all three.
 enum SolveKind { SK_DIFF = 0, SK_EQ = 1, SK_PF = 2, SK_COUNT = 3 };
 // Operations with a cached graph.
-enum OpKind { OP_STEP = 0, OP_DIFF = 1, OP_EQ = 2, OP_PF = 3, OP_COUNT = 4 };
+enum OpKind { OP_STEP = 0, OP_DIFF = 1, OP_EQ = 2, OP_PF = 3, OP_BAR = 4, OP_COUNT = 5 };
 
 constexpr int kResultsPerProblem = 16;
 
@@ -214,7 +214,21 @@ struct fftmech_group {
   std::vector<LaunchCount> lc;
   long long builds = 0, launches = 0, kernels = 0;
   char err[512] = {0};
+};
 
+// The device arrays and constants of a macroscale bar (Sec. 3.2).
+struct BarDev {
+  int M = 0;
+  double dX = 0, dt = 0, flux_in = 0;
+  double* c = nullptr;     // M + 1 nodal concentrations
+  double* cbar = nullptr;  // M element concentrations
+  double* G = nullptr;     // 3 M element gradients
+};
+
+struct fftmech_bar {
+  fftmech_ctx* ctx = nullptr;
+  BarDev d;
+  double* mem = nullptr;
 };
 
 namespace {
@@ -791,7 +805,8 @@ fftmech_status enqueue_equilibrium(Emit& em, const uint8_t* phase, const T* eig,
 
 template <typename T>
 fftmech_status enqueue_diffusion(Emit& em, const uint8_t* phase, int mode, const double* grad_c_mac, double c_macro,
-                                 double dt, const uint8_t* mask, double cD, double* c) {
+                                 double dt, const uint8_t* mask, double cD, double* c, const double* Gp = nullptr,
+                                 const double* cmp = nullptr) {
   fftmech_ctx* ctx = em.ctx;
   em.sk = SK_DIFF;
   if (mode == FFTMECH_DIFF_TRANSIENT && !(dt > 0))
@@ -812,6 +827,8 @@ fftmech_status enqueue_diffusion(Emit& em, const uint8_t* phase, int mode, const
     op.G[0] = grad_c_mac[0];
     op.G[1] = grad_c_mac[1];
     op.G[2] = three ? grad_c_mac[2] : 0.0;
+    op.Gp = Gp;
+    op.cmp = cmp;
     sp.m0 = 0.0;
     sp.m1 = ih2;
     RC(emit_pcg<T, 1>(em, op, ctx->phi, sp));
@@ -819,12 +836,12 @@ fftmech_status enqueue_diffusion(Emit& em, const uint8_t* phase, int mode, const
       EM_LAUNCH(em, FFTMECH_K_OTHER, launch3_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials, res,
                                                            ctx->sc, em.st));
       EM_LAUNCH(em, FFTMECH_K_OTHER, launch3_diff_write_c(ctx->nx, ctx->ny, ctx->nz, B, phase, ctx->phi, ctx->h_diff,
-                                                          op.G, res, c, em.st));
+                                                          op.G, Gp, res, c, em.st));
     } else {
       EM_LAUNCH(em, FFTMECH_K_OTHER, launch_diff_stats<T>(op, B, ctx->phi, ctx->h_diff, c_macro, ctx->partials, res,
                                                           ctx->sc, em.st));
       EM_LAUNCH(em, FFTMECH_K_OTHER, launch_diff_write_c(ctx->nx, ctx->ny, B, phase, ctx->phi, ctx->h_diff, op.G[0],
-                                                         op.G[1], res, c, em.st));
+                                                         op.G[1], Gp, res, c, em.st));
     }
     return rec_end(em, SK_DIFF);
   }
@@ -900,7 +917,7 @@ fftmech_status enqueue_step(Emit& em, const StepPtrs& s, const fftmech_step_para
   // 1. diffusion of chemical species
   if (prm->diffusion_mode != FFTMECH_DIFF_NONE)
     RC(enqueue_diffusion<T>(em, s.phase, prm->diffusion_mode, prm->grad_c_mac, prm->c_macro, prm->dt, s.mask,
-                            prm->dirichlet_value, s.c));
+                            prm->dirichlet_value, s.c, prm->grad_c_mac_each, prm->c_macro_each));
   // 2. precipitation and eigenstrain
   if (prm->eig_mode == FFTMECH_EIG_FROM_PRECIPITATE)
     EM_LAUNCH(em, FFTMECH_K_OTHER, launch_precipitate<T>(N, s.phase, s.c, ctx->mat.S_sol, ctx->mat.M_ppt, (T*)s.cppt,
@@ -946,11 +963,11 @@ fftmech_status collect(fftmech_ctx* ctx, int kind, fftmech_solve_info* info, int
       i.elastic_energy = r[2 * nv] * vox;
     } else if (kind == SK_DIFF) {
       if (ctx->last.diff_mode == FFTMECH_DIFF_HOMOGENISE) {
-        const int nr = three ? 6 : 5, nd = three ? 3 : 2;
+        const int nr = three ? 7 : 6, nd = three ? 3 : 2;
         const double* r = R + b * nr;
         for (int k = 0; k < nd; ++k) i.mean_flux[k] = r[2 + k];
         i.porosity = r[2 + nd];
-        i.mean_c = ctx->last.c_macro;
+        i.mean_c = r[3 + nd];
       } else {
         i.porosity = 1.0 - R[b * 3 + 2] / N;
       }
@@ -1135,18 +1152,28 @@ fftmech_status check_step_args(fftmech_ctx* ctx, const fftmech_state* state, con
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "eig_field is required for PRESCRIBED");
   if (prm->eig_mode != FFTMECH_EIG_PRESCRIBED && prm->eig_mode != FFTMECH_EIG_FROM_PRECIPITATE)
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "eigenstrain mode %d", prm->eig_mode);
+  for (const double* p : {prm->c_macro_each, prm->grad_c_mac_each})
+    if (p && !is_device_ptr(p))
+      return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "c_macro_each / grad_c_mac_each must be device memory");
   return FFTMECH_OK;
 }
 
-// Enqueues one staggered step on device pointers (graph or host-driven).
-fftmech_status step_enqueue(fftmech_ctx* ctx, const StepPtrs& d, const fftmech_step_params* prm) {
+// Enqueues one staggered step on device pointers (graph or host-driven);
+// with a bar, framed by the bar's element inputs and nodal update.
+fftmech_status step_enqueue(fftmech_ctx* ctx, const StepPtrs& d, const fftmech_step_params* prm,
+                            const BarDev* bar = nullptr) {
   std::vector<unsigned char> key;
   key_add(key, d);
   key_add(key, *prm);
   key_add(key, ctx->opts);
+  if (bar) key_add(key, *bar);
   const bool fp64 = ctx->prec == FFTMECH_FP64;
-  RC(run_op(ctx, OP_STEP, key, [&](Emit& em) -> fftmech_status {
+  RC(run_op(ctx, bar ? OP_BAR : OP_STEP, key, [&](Emit& em) -> fftmech_status {
+    if (bar) EM_LAUNCH(em, FFTMECH_K_OTHER, launch_bar_inputs(bar->M, bar->dX, bar->c, bar->cbar, bar->G, em.st));
     RC(fp64 ? enqueue_step<double>(em, d, prm) : enqueue_step<float>(em, d, prm));
+    if (bar)
+      EM_LAUNCH(em, FFTMECH_K_OTHER, launch_bar_update(bar->M, bar->dX, bar->dt, bar->flux_in, bar->c,
+                                                       res_dev(ctx, SK_DIFF), ctx->dim == 3 ? 7 : 6, em.st));
     return rec_publish(em);
   }));
   ctx->last = LastOp();
@@ -1366,8 +1393,12 @@ struct TuneChoice {
   int L_dir, L_upd, ty, zc, grid, cols;
 };
 using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+struct TuneEntry {
+  TuneChoice choice;
+  double before_us, after_us;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, TuneChoice> g_tune;
+std::map<TuneKey, TuneEntry> g_tune;
 
 TuneKey tune_key(const fftmech_ctx* ctx) {
   return TuneKey(ctx->device, ctx->dim, ctx->nx, ctx->ny, ctx->nz, ctx->B, (int)ctx->prec);
@@ -1556,7 +1587,7 @@ fftmech_status autotune_impl(fftmech_ctx* ctx, int iterations, double* before_us
   if (rc != FFTMECH_OK) return rc;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[tune_key(ctx)] = best;
+    g_tune[tune_key(ctx)] = TuneEntry{best, 1e3 * first_ms / iterations, 1e3 * best_ms / iterations};
   }
   if (before_us) *before_us = 1e3 * first_ms / iterations;
   if (after_us) *after_us = 1e3 * best_ms / iterations;
@@ -1665,21 +1696,12 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   if (!shp) return fail(FFTMECH_ERR_UNSUPPORTED_SIZE);
   ctx->shape.batch = batch;
   {
-    // a choice the autotuner made for this grid earlier in the process
-    TuneChoice c;
-    bool have = false;
-    {
-      std::lock_guard<std::mutex> lock(g_tune_mu);
-      auto it = g_tune.find(tune_key(ctx));
-      if (it != g_tune.end()) { c = it->second; have = true; }
-    }
-    if (have && (fp64 ? choice_ok<double>(ctx, c) : choice_ok<float>(ctx, c))) {
-      if (fp64) apply_choice<double>(ctx, c);
-      else apply_choice<float>(ctx, c);
-    }
+    // the rule-based shapes (a context never inherits another's tuning: its
+    // reductions' block partitions, and so its last bits, depend only on
+    // its own arguments and fftmech_autotune calls)
     const TuneChoice k = current_choice(ctx);
-    snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d%s", k.L_dir,
-             k.L_upd, k.ty, k.zc, k.grid, k.cols, have ? " (autotuned)" : "");
+    snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d", k.L_dir,
+             k.L_upd, k.ty, k.zc, k.grid, k.cols);
   }
   const size_t es = fp64 ? 8 : 4;
   const size_t NB = (size_t)ctx->N * batch;
@@ -1796,9 +1818,33 @@ fftmech_status fftmech_autotune(fftmech_ctx* ctx, int iterations, double* before
   fftmech_status rc = check_ctx(ctx);
   if (rc != FFTMECH_OK) return rc;
   if (iterations < 0) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "iterations must be >= 0");
-  if (iterations > 0)
-    rc = ctx->prec == FFTMECH_FP64 ? autotune_impl<double>(ctx, iterations, before_us, after_us)
-                                   : autotune_impl<float>(ctx, iterations, before_us, after_us);
+  const bool fp64 = ctx->prec == FFTMECH_FP64;
+  if (iterations > 0) {
+    // a choice tuned earlier in the process for the same device, grid,
+    // batch and precision is applied without timing again
+    TuneEntry c;
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(tune_key(ctx));
+      if (it != g_tune.end()) {
+        c = it->second;
+        have = true;
+      }
+    }
+    if (have && (fp64 ? choice_ok<double>(ctx, c.choice) : choice_ok<float>(ctx, c.choice))) {
+      if (fp64) apply_choice<double>(ctx, c.choice);
+      else apply_choice<float>(ctx, c.choice);
+      if (before_us) *before_us = c.before_us;
+      if (after_us) *after_us = c.after_us;
+      const TuneChoice& k = c.choice;
+      snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d (cached)",
+               k.L_dir, k.L_upd, k.ty, k.zc, k.grid, k.cols);
+    } else {
+      rc = fp64 ? autotune_impl<double>(ctx, iterations, before_us, after_us)
+                : autotune_impl<float>(ctx, iterations, before_us, after_us);
+    }
+  }
   if (choice) *choice = ctx->tune_desc;
   return rc;
 }
@@ -2026,6 +2072,103 @@ fftmech_status fftmech_step_info(fftmech_ctx* ctx, fftmech_solve_info* info) {
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "no staggered step has been enqueued");
   RC(finish_sync(ctx));
   return step_collect(ctx, info);
+}
+
+fftmech_status fftmech_bar_create(fftmech_bar** out, fftmech_ctx* ctx, double length, double dt, double flux_in,
+                                  const double* c0) {
+  if (!out) return FFTMECH_ERR_INVALID_ARG;
+  *out = nullptr;
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  const int M = ctx->B;
+  if (!(length > 0) || !(dt > 0) || !std::isfinite(flux_in))
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "bar length and dt must be > 0");
+  const double dX = length / M;
+  const double dmax = std::max(ctx->mat.D_pore, ctx->mat.D_solid);
+  if (dt > dX * dX / (2.0 * dmax))
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "dt %g above the explicit bound dX^2 / (2 D_max) = %g", dt,
+                   dX * dX / (2.0 * dmax));
+  fftmech_bar* b = new (std::nothrow) fftmech_bar();
+  if (!b) return FFTMECH_ERR_OOM;
+  b->ctx = ctx;
+  const size_t n = (size_t)(M + 1) + 4 * (size_t)M;
+  if (cudaMalloc(&b->mem, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return set_err(ctx, FFTMECH_ERR_OOM, "bar buffers");
+  }
+  b->d.M = M;
+  b->d.dX = dX;
+  b->d.dt = dt;
+  b->d.flux_in = flux_in;
+  b->d.c = b->mem;
+  b->d.cbar = b->mem + M + 1;
+  b->d.G = b->d.cbar + M;
+  std::vector<double> h(n, 0.0);
+  if (c0) std::memcpy(h.data(), c0, sizeof(double) * (M + 1));
+  if (cudaMemcpy(b->mem, h.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->mem);
+    delete b;
+    return set_err(ctx, FFTMECH_ERR_CUDA, "bar upload");
+  }
+  *out = b;
+  return FFTMECH_OK;
+}
+
+fftmech_status fftmech_bar_destroy(fftmech_bar* bar) {
+  if (!bar) return FFTMECH_ERR_INVALID_ARG;
+  if (bar->ctx) cudaStreamSynchronize(bar->ctx->stream);
+  cudaFree(bar->mem);
+  delete bar;
+  return FFTMECH_OK;
+}
+
+fftmech_status fftmech_bar_step(fftmech_bar* bar, const fftmech_state* state, const fftmech_step_params* params,
+                                fftmech_solve_info* info) {
+  if (!bar) return FFTMECH_ERR_INVALID_ARG;
+  fftmech_ctx* ctx = bar->ctx;
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  if (!params || !info) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
+  fftmech_step_params prm = *params;
+  prm.diffusion_mode = FFTMECH_DIFF_HOMOGENISE;
+  prm.c_macro = 0.0;
+  for (double& g : prm.grad_c_mac) g = 0.0;
+  prm.c_macro_each = bar->d.cbar;
+  prm.grad_c_mac_each = bar->d.G;
+  RC(check_step_args(ctx, state, &prm));
+  const void* ptrs[] = {state->phase, state->c, state->c_ppt, state->eig, state->u, state->strain, state->stress,
+                        state->H, state->damage,
+                        prm.eig_mode == FFTMECH_EIG_PRESCRIBED ? prm.eig_field : nullptr};
+  for (const void* p : ptrs)
+    if (p && !is_device_ptr(p)) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "the bar takes device pointers");
+  StepPtrs d;
+  bool all_device = false;
+  RC(stage_step(ctx, state, &prm, d, all_device));
+  RC(step_enqueue(ctx, d, &prm, &bar->d));
+  RC(finish_sync(ctx));
+  return step_collect(ctx, info);
+}
+
+fftmech_status fftmech_bar_read(const fftmech_bar* bar, double* c_host) {
+  if (!bar || !c_host) return FFTMECH_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(bar->ctx->stream) != cudaSuccess ||
+      cudaMemcpy(c_host, bar->d.c, sizeof(double) * (bar->d.M + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return FFTMECH_ERR_CUDA;
+  }
+  return FFTMECH_OK;
+}
+
+fftmech_status fftmech_bar_write(fftmech_bar* bar, const double* c_host) {
+  if (!bar || !c_host) return FFTMECH_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(bar->ctx->stream) != cudaSuccess ||
+      cudaMemcpy(bar->d.c, c_host, sizeof(double) * (bar->d.M + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return FFTMECH_ERR_CUDA;
+  }
+  return FFTMECH_OK;
 }
 
 fftmech_status fftmech_group_create(fftmech_group** out, fftmech_ctx* const* ctxs, int n, void* stream) {

@@ -162,6 +162,10 @@ struct Op {
   const T* c0f;
   const uint8_t* mask;
   double G[3];
+  // per-problem macro gradient (3 per problem) and macro concentration of a
+  // batch (device; NULL: G and the call's c_macro for every problem)
+  const double* Gp;
+  const double* cmp;
   const double* srcd;
   const T* srct;
   double src_scale;
@@ -173,6 +177,12 @@ struct Op {
   // the right-hand side grad+^T tau of the equilibrium adjoint
   const T* pre;
 };
+
+// Macro concentration gradient component k of problem b.
+template <typename T>
+__device__ __forceinline__ double macro_grad(const Op<T>& op, int b, int k) {
+  return op.Gp ? op.Gp[3 * b + k] : op.G[k];
+}
 
 // The iterate: double in FP64; in MIXED an unevaluated float pair
 // u = uh + ul (double-float arithmetic: Knuth's TwoSum, Dekker's product
@@ -448,7 +458,7 @@ cudaError_t launch_diff_stats(const Op<T>& op, int batch, const double* phi, dou
                               double c_macro, double* partials, double* results, SolverScalars* sc,
                               cudaStream_t st);
 cudaError_t launch_diff_write_c(int nx, int ny, int batch, const uint8_t* phase, const double* phi,
-                                double hdiff, double G0, double G1, const double* beta_dev,
+                                double hdiff, double G0, double G1, const double* Gp, const double* beta_dev,
                                 double* c, cudaStream_t st);
 template <typename T>
 cudaError_t launch_history(long long N, int batch, const uint8_t* phase, double lam0, double lam1,
@@ -474,6 +484,11 @@ cudaError_t launch_df_split(long long n, const double* u, float* uh, float* ul, 
 cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc, int batch, double invN, int fp32,
                                 cudaStream_t st);
 cudaError_t launch_df_merge(long long n, const float* uh, const float* ul, double* u, cudaStream_t st);
+
+// Macroscale bar (bar.cu).
+cudaError_t launch_bar_inputs(int M, double dX, const double* c, double* cbar, double* G, cudaStream_t st);
+cudaError_t launch_bar_update(int M, double dX, double dt, double flux_in, double* c, const double* res, int stride,
+                              cudaStream_t st);
 
 // Reverse sweep of the staggered solve (adjoint.cu).
 cudaError_t launch_fill(long long N, double v, double* p, cudaStream_t st);
@@ -519,8 +534,8 @@ template <typename T>
 cudaError_t launch3_diff_stats(const Op<T>& op, int batch, const double* phi, double hdiff, double c_macro,
                                double* partials, double* results, SolverScalars* sc, cudaStream_t st);
 cudaError_t launch3_diff_write_c(int nx, int ny, int nz, int batch, const uint8_t* phase, const double* phi,
-                                 double hdiff, const double G[3], const double* beta_dev, double* c,
-                                 cudaStream_t st);
+                                 double hdiff, const double G[3], const double* Gp, const double* beta_dev,
+                                 double* c, cudaStream_t st);
 template <typename T>
 cudaError_t launch3_history(long long N, int batch, const uint8_t* phase, double lam0, double lam1, double mu0,
                             double mu1, const T* strain, const T* eig, T* H, double* Hd, double a, double* m0b,

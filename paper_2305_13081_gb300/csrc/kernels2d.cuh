@@ -94,8 +94,8 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
       const int c0 = yy * nx + x;
       const double u = P[c0];
       const double kap = op.kap[ph];
-      SG[i] = kap * ((P[yy * nx + xp] - u) * ih + op.G[0]);
-      SG[SR + i] = kap * ((P[c0 + nx] - u) * ih + op.G[1]);
+      SG[i] = kap * ((P[yy * nx + xp] - u) * ih + macro_grad(op, bp, 0));
+      SG[SR + i] = kap * ((P[c0 + nx] - u) * ih + macro_grad(op, bp, 1));
       SG[2 * SR + i] = u;
     }
   }

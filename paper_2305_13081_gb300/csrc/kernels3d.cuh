@@ -186,8 +186,9 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
       } else {
         const double p = Pc[i];
         const double kap = op.kap[ph];
-        const double gx = (Pc[ix] - p) * ih + op.G[0], gy = (Pc[i + nx] - p) * ih + op.G[1];
-        const double gz = (Pn[i] - p) * ih + op.G[2];
+        const double gx = (Pc[ix] - p) * ih + macro_grad(op, bp, 0);
+        const double gy = (Pc[i + nx] - p) * ih + macro_grad(op, bp, 1);
+        const double gz = (Pn[i] - p) * ih + macro_grad(op, bp, 2);
         if (inner) {
           SP[i] = kap * gx;
           SP[SS + i] = kap * gy;

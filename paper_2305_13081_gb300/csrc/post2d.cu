@@ -65,8 +65,8 @@ __global__ void k_el_output(Op<T> op, const double* __restrict__ u, T* strain, T
 
 // Phase statistics of the homogenised diffusion solution (Eq. psi-two-values)
 // and the mean flux; the last block of each problem turns them into
-// beta_pore, beta_solid. results[b * 5 + .]: beta_pore, beta_solid, <jx>,
-// <jy>, porosity.
+// beta_pore, beta_solid. results[b * 6 + .]: beta_pore, beta_solid, <jx>,
+// <jy>, porosity, c_macro of the problem.
 template <typename T>
 __global__ void k_diff_stats(Op<T> op, const double* __restrict__ phi, double hdiff,
                              double c_macro, double* partials, double* results, SolverScalars* sc) {
@@ -78,6 +78,8 @@ __global__ void k_diff_stats(Op<T> op, const double* __restrict__ phi, double hd
   const uint8_t* phase = op.phase + (size_t)b * N;
   partials += (size_t)b * gridDim.x * 10;
   const double ih = 1.0 / hdiff;
+  const double G0 = macro_grad(op, b, 0), G1 = macro_grad(op, b, 1);
+  if (op.cmp) c_macro = op.cmp[b];
   double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
        gi += (long long)gridDim.x * blockDim.x) {
@@ -85,13 +87,13 @@ __global__ void k_diff_stats(Op<T> op, const double* __restrict__ phi, double hd
     const long long ixp = (long long)y * nx + (x + 1 == nx ? 0 : x + 1);
     const long long iyp = (long long)(y + 1 == ny ? 0 : y + 1) * nx + x;
     const int s = phase[gi] ? 1 : 0;  // 0 pore, 1 solid
-    const double ramp = op.G[0] * (x * hdiff) + op.G[1] * (y * hdiff);
+    const double ramp = G0 * (x * hdiff) + G1 * (y * hdiff);
     acc[s] += 1.0;
     acc[2 + s] += phi[gi];
     acc[4 + s] += ramp;
     const double D = op.kap[s];
-    acc[6] += -D * (op.G[0] + (phi[ixp] - phi[gi]) * ih);
-    acc[7] += -D * (op.G[1] + (phi[iyp] - phi[gi]) * ih);
+    acc[6] += -D * (G0 + (phi[ixp] - phi[gi]) * ih);
+    acc[7] += -D * (G1 + (phi[iyp] - phi[gi]) * ih);
   }
   block_sum<10>(acc, red);
   if (publish_partials<10>(acc, partials, &sc[b].cnt[2])) {
@@ -100,28 +102,32 @@ __global__ void k_diff_stats(Op<T> op, const double* __restrict__ phi, double hd
     if (threadIdx.x == 0) {
       const double np = tot[0], ns = tot[1];
       const double eta = np / (double)N;
-      double* r = results + b * 5;
+      double* r = results + b * 6;
       r[0] = np > 0 ? c_macro / eta - (tot[4] + tot[2]) / np : 0.0;
       r[1] = ns > 0 ? -(tot[5] + tot[3]) / ns : 0.0;
       r[2] = tot[6] / (double)N;
       r[3] = tot[7] / (double)N;
       r[4] = eta;
+      r[5] = c_macro;
     }
   }
 }
 
 // c = grad c_mac . x + phi + beta_phase (Eqs. concentration, concentration-correct),
-// beta of problem b from results[b * 5 + 0 / 1].
+// beta of problem b from results[b * 6 + 0 / 1]; Gp: per-problem gradients
+// (NULL: G0, G1 for all).
 __global__ void k_diff_write_c(int nx, int ny, long long total, const uint8_t* __restrict__ phase,
                                const double* __restrict__ phi, double hdiff, double G0, double G1,
-                               const double* __restrict__ beta, double* __restrict__ c) {
+                               const double* __restrict__ Gp, const double* __restrict__ beta,
+                               double* __restrict__ c) {
   const long long N = (long long)nx * ny;
   for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
        gi += (long long)gridDim.x * blockDim.x) {
     const long long b = gi / N, li = gi - b * N;
     const int y = (int)(li / nx), x = (int)(li - (long long)y * nx);
-    const double bt = phase[gi] ? beta[b * 5 + 1] : beta[b * 5 + 0];
-    c[gi] = G0 * (x * hdiff) + G1 * (y * hdiff) + phi[gi] + bt;
+    const double bt = phase[gi] ? beta[b * 6 + 1] : beta[b * 6 + 0];
+    const double g0 = Gp ? Gp[3 * b] : G0, g1 = Gp ? Gp[3 * b + 1] : G1;
+    c[gi] = g0 * (x * hdiff) + g1 * (y * hdiff) + phi[gi] + bt;
   }
 }
 
@@ -290,10 +296,10 @@ cudaError_t launch_diff_stats(const Op<T>& op, int batch, const double* phi, dou
   return cudaGetLastError();
 }
 cudaError_t launch_diff_write_c(int nx, int ny, int batch, const uint8_t* phase, const double* phi,
-                                double hdiff, double G0, double G1, const double* beta_dev,
+                                double hdiff, double G0, double G1, const double* Gp, const double* beta_dev,
                                 double* c, cudaStream_t st) {
   const long long total = (long long)nx * ny * batch;
-  k_diff_write_c<<<post_grid(total), kPostThreads, 0, st>>>(nx, ny, total, phase, phi, hdiff, G0, G1,
+  k_diff_write_c<<<post_grid(total), kPostThreads, 0, st>>>(nx, ny, total, phase, phi, hdiff, G0, G1, Gp,
                                                             beta_dev, c);
   return cudaGetLastError();
 }

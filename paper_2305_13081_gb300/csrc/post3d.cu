@@ -94,8 +94,8 @@ __global__ void k3_el_output(Op<T> op, const double* __restrict__ u, T* strain, 
 }
 
 // Phase statistics of the homogenised diffusion solution (Eq. psi-two-values)
-// and the mean flux; results[b * 6 + .]: beta_pore, beta_solid, <jx>, <jy>,
-// <jz>, porosity.
+// and the mean flux; results[b * 7 + .]: beta_pore, beta_solid, <jx>, <jy>,
+// <jz>, porosity, c_macro of the problem.
 template <typename T>
 __global__ void k3_diff_stats(Op<T> op, const double* __restrict__ phi, double hdiff, double c_macro,
                               double* partials, double* results, SolverScalars* sc) {
@@ -107,19 +107,21 @@ __global__ void k3_diff_stats(Op<T> op, const double* __restrict__ phi, double h
   const uint8_t* phase = op.phase + (size_t)b * N;
   partials += (size_t)b * gridDim.x * 9;
   const double ih = 1.0 / hdiff;
+  const double G0 = macro_grad(op, b, 0), G1 = macro_grad(op, b, 1), G2 = macro_grad(op, b, 2);
+  if (op.cmp) c_macro = op.cmp[b];
   double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < N;
        gi += (long long)gridDim.x * blockDim.x) {
     const Nbr3 q(gi, nx, ny, nz);
     const int s = phase[gi] ? 1 : 0;  // 0 pore, 1 solid
-    const double ramp = op.G[0] * (q.x * hdiff) + op.G[1] * (q.y * hdiff) + op.G[2] * (q.z * hdiff);
+    const double ramp = G0 * (q.x * hdiff) + G1 * (q.y * hdiff) + G2 * (q.z * hdiff);
     acc[s] += 1.0;
     acc[2 + s] += phi[gi];
     acc[4 + s] += ramp;
     const double D = op.kap[s];
-    acc[6] += -D * (op.G[0] + (phi[q.ixp] - phi[gi]) * ih);
-    acc[7] += -D * (op.G[1] + (phi[q.iyp] - phi[gi]) * ih);
-    acc[8] += -D * (op.G[2] + (phi[q.izp] - phi[gi]) * ih);
+    acc[6] += -D * (G0 + (phi[q.ixp] - phi[gi]) * ih);
+    acc[7] += -D * (G1 + (phi[q.iyp] - phi[gi]) * ih);
+    acc[8] += -D * (G2 + (phi[q.izp] - phi[gi]) * ih);
   }
   block_sum<9>(acc, red);
   if (publish_partials<9>(acc, partials, &sc[b].cnt[2])) {
@@ -128,29 +130,34 @@ __global__ void k3_diff_stats(Op<T> op, const double* __restrict__ phi, double h
     if (threadIdx.x == 0) {
       const double np = tot[0], ns = tot[1];
       const double eta = np / (double)N;
-      double* r = results + b * 6;
+      double* r = results + b * 7;
       r[0] = np > 0 ? c_macro / eta - (tot[4] + tot[2]) / np : 0.0;
       r[1] = ns > 0 ? -(tot[5] + tot[3]) / ns : 0.0;
       r[2] = tot[6] / (double)N;
       r[3] = tot[7] / (double)N;
       r[4] = tot[8] / (double)N;
       r[5] = eta;
+      r[6] = c_macro;
     }
   }
 }
 
 // c = grad c_mac . x + phi + beta_phase (Eqs. concentration,
-// concentration-correct), beta of problem b from results[b * 6 + 0 / 1].
+// concentration-correct), beta of problem b from results[b * 7 + 0 / 1];
+// Gp: per-problem gradients (NULL: G0, G1, G2 for all).
 __global__ void k3_diff_write_c(int nx, int ny, int nz, long long total, const uint8_t* __restrict__ phase,
                                 const double* __restrict__ phi, double hdiff, double G0, double G1, double G2,
-                                const double* __restrict__ beta, double* __restrict__ c) {
+                                const double* __restrict__ Gp, const double* __restrict__ beta,
+                                double* __restrict__ c) {
   const long long N = (long long)nx * ny * nz;
   for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
        gi += (long long)gridDim.x * blockDim.x) {
     const long long b = gi / N, li = gi - b * N;
     const Nbr3 q(li, nx, ny, nz);
-    const double bt = phase[gi] ? beta[b * 6 + 1] : beta[b * 6 + 0];
-    c[gi] = G0 * (q.x * hdiff) + G1 * (q.y * hdiff) + G2 * (q.z * hdiff) + phi[gi] + bt;
+    const double bt = phase[gi] ? beta[b * 7 + 1] : beta[b * 7 + 0];
+    const double* g = Gp ? Gp + 3 * b : nullptr;
+    const double g0 = g ? g[0] : G0, g1 = g ? g[1] : G1, g2 = g ? g[2] : G2;
+    c[gi] = g0 * (q.x * hdiff) + g1 * (q.y * hdiff) + g2 * (q.z * hdiff) + phi[gi] + bt;
   }
 }
 
@@ -213,13 +220,13 @@ cudaError_t launch3_diff_stats(const Op<T>& op, int batch, const double* phi, do
   return cudaGetLastError();
 }
 cudaError_t launch3_diff_write_c(int nx, int ny, int nz, int batch, const uint8_t* phase, const double* phi,
-                                 double hdiff, const double G[3], const double* beta_dev, double* c,
-                                 cudaStream_t st) {
+                                 double hdiff, const double G[3], const double* Gp, const double* beta_dev,
+                                 double* c, cudaStream_t st) {
   const long long total = (long long)nx * ny * nz * batch;
   long long g = (total + kPost3Threads - 1) / kPost3Threads;
   if (g > 4096) g = 4096;
   k3_diff_write_c<<<(unsigned)(g < 1 ? 1 : g), kPost3Threads, 0, st>>>(nx, ny, nz, total, phase, phi, hdiff, G[0],
-                                                                       G[1], G[2], beta_dev, c);
+                                                                       G[1], G[2], Gp, beta_dev, c);
   return cudaGetLastError();
 }
 template <typename T>

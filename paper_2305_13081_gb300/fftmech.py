@@ -100,7 +100,8 @@ class fftmech_step_params(ctypes.Structure):
                 ("c_macro", ctypes.c_double), ("dt", ctypes.c_double),
                 ("dirichlet_mask", ctypes.c_void_p), ("dirichlet_value", ctypes.c_double),
                 ("eig_mode", ctypes.c_int), ("eig_field", ctypes.c_void_p),
-                ("eig_scale", ctypes.c_double), ("eps_mac", c_double6)]
+                ("eig_scale", ctypes.c_double), ("eps_mac", c_double6),
+                ("c_macro_each", ctypes.c_void_p), ("grad_c_mac_each", ctypes.c_void_p)]
 
 
 _lib = None
@@ -149,6 +150,11 @@ def load_library(path=LIB_PATH):
         "fftmech_group_last_error": (ctypes.c_char_p, [vp]),
         "fftmech_staggered_step_many": (i, [P(vp), i, P(P(fftmech_state)), P(P(fftmech_step_params)),
                                             P(P(fftmech_solve_info))]),
+        "fftmech_bar_create": (i, [P(vp), vp, d, d, d, P(d)]),
+        "fftmech_bar_destroy": (i, [vp]),
+        "fftmech_bar_step": (i, [vp, P(fftmech_state), P(fftmech_step_params), P(fftmech_solve_info)]),
+        "fftmech_bar_read": (i, [vp, P(d)]),
+        "fftmech_bar_write": (i, [vp, P(d)]),
         "fftmech_fft": (i, [i, P(i), i, i, vp, vp]),
         "fftmech_fft_noalloc": (i, [i, P(i), i, i, vp, vp]),
         "fftmech_profile_enable": (i, [vp, i]),
@@ -420,6 +426,40 @@ def fftmech_group_stats(group):
     b, n, k = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
     _check(load_library().fftmech_group_stats(group, ctypes.byref(b), ctypes.byref(n), ctypes.byref(k)))
     return b.value, n.value, k.value
+
+
+def fftmech_bar_create(ctx, length, dt, flux_in, c0=None):
+    """Macroscale bar over the RVEs of a batched context (Sec. 3.2)."""
+    h = ctypes.c_void_p()
+    arr = None
+    if c0 is not None:
+        arr = (ctypes.c_double * len(c0))(*[float(x) for x in c0])
+    _check(load_library().fftmech_bar_create(ctypes.byref(h), ctx, float(length), float(dt), float(flux_in), arr), ctx)
+    return h
+
+
+def fftmech_bar_destroy(bar):
+    return load_library().fftmech_bar_destroy(bar)
+
+
+def fftmech_bar_step(bar, ctx, state, params):
+    """One macro time step (one staggered step of every RVE); returns the
+    3 records per RVE."""
+    infos = _infos(ctx, 3)
+    rc = load_library().fftmech_bar_step(bar, ctypes.byref(state), ctypes.byref(params), infos)
+    _check(rc, ctx, _SOLVER_OK)
+    return infos
+
+
+def fftmech_bar_read(bar, n):
+    out = (ctypes.c_double * n)()
+    _check(load_library().fftmech_bar_read(bar, out))
+    return list(out)
+
+
+def fftmech_bar_write(bar, values):
+    arr = (ctypes.c_double * len(values))(*[float(x) for x in values])
+    _check(load_library().fftmech_bar_write(bar, arr))
 
 
 class Group:

@@ -188,8 +188,9 @@ def test_step_captured_into_a_caller_graph_and_replayed():
                                         ((81, 81), fm.FFTMECH_FP64)])
 def test_autotuner_keeps_results_and_caches_its_choice(shape, prec):
     """The autotuner's choice is no slower than the default shapes on its own
-    timing, the solve with the tuned shapes still meets the oracle, and a
-    new context of the same grid starts with the cached choice."""
+    timing, the solve with the tuned shapes still meets the oracle, a new
+    context of the same grid starts from the rule-based shapes, and tuning
+    it applies the cached choice without timing again."""
     from oracle import elasticity
     from microstructures import random_sponge as _sponge
     ph = random_carpet(shape[0], 0.30, 31)[0] if len(shape) == 2 else _sponge(shape[0], 0.35, 31)[0]
@@ -213,6 +214,9 @@ def test_autotuner_keeps_results_and_caches_its_choice(shape, prec):
     assert err < (1e-10 if prec == fm.FFTMECH_FP64 else 1e-5), err
     ctx.close()
     ctx2 = fm.Context(shape, MAT, prec, h=H)
-    _, _, desc2 = fm.fftmech_autotune(ctx2.handle, 0)  # the shapes it starts from
+    _, _, desc0 = fm.fftmech_autotune(ctx2.handle, 0)  # the shapes it starts from
+    b2, a2, desc2 = fm.fftmech_autotune(ctx2.handle, 20)
     ctx2.close()
-    assert desc2.endswith("(autotuned)") and desc2.startswith(desc), (desc, desc2)
+    assert not desc0.endswith(")")
+    assert desc2.endswith("(cached)") and desc2.startswith(desc), (desc, desc2)
+    assert (b2, a2) == (before, after)
