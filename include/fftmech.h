@@ -110,11 +110,11 @@ typedef struct {
  * residual, equal to sqrt(r.M^-1 r) of the potential PCG) has dropped by
  * `tol` relative to that of the right-hand side, or after max_iter
  * iterations (status NOT_CONVERGED).
- * replace_residual (MIXED only, 0/1): reliable updates; after every
+ * replace_residual (MIXED only, 0/1): reliable updates; after every 16th
  * iteration the device checks whether r.M^-1 r has fallen 100-fold since
  * the last replacement and, if so, replaces the float recursive residual by
  * the FP64 true residual b - K u in the next iteration (search direction
- * kept). After convergence of the float recursion the FP64 true residual is
+ * kept; the problems of a batch due at that point are replaced together). After convergence of the float recursion the FP64 true residual is
  * checked; a problem whose true residual misses tol continues from it (at
  * most three times).
  * Every decision of the loop is taken on the device. execution:

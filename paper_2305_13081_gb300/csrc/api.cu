@@ -522,17 +522,19 @@ fftmech_status poll_flags(Emit& em, int* out) {
 // ---------------------------------------------------------------- PCG
 // Preconditioned CG on the potential for every problem of the batch.
 // Launch sequence (graph form; the host-driven form runs the same launches
-// and reads the flags every check_every iterations):
+// and reads the flags after every iteration):
 //   scalars, [MIXED: iterate split], <f, M^-1 f>, first residual, zero-RHS
-//   case, first direction (p = z)               -> LF_LOOP, LF_REPLACE, LF_DONE
+//   case, first direction (p = z)               -> LF_LOOP, LF_REPLACE, LF_GATE
 //   WHILE LF_OUTER:
+//     conditions from memory
 //     WHILE LF_LOOP (ordinary iterations):
 //       stencil (q = K p, <p, K p>), update (u += alpha p, r -= alpha q,
 //       x-FFT), column pass (multiplier, <r, M^-1 r>), direction
 //     IF LF_REPLACE (reliable update): stencil, update of the iterate only,
 //       FP64 true residual, column pass, direction
-//     IF LF_DONE: FP64 true residual of every iterate, restart gate
-//       IF LF_RESTART: restart from the true residual, first direction
+//     IF LF_GATE: FP64 true residual of the problems that stopped unchecked
+//     restart gate
+//     IF LF_RESTART: restart from the true residual, first direction
 //   [MIXED: iterate merge]
 // An ordinary iteration has no conditional node inside it, so its kernels
 // stay chained by programmatic dependent launches.
@@ -672,12 +674,17 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
     if (B > 1) EM_LAUNCH(e, FFTMECH_K_OTHER, launch_loopctl(ctx->sc, ctx->mode, B, vi.ctl, e.st));
     return FFTMECH_OK;
   };
-  // End of an outer round: FP64 true residual of every problem that has
-  // stopped, and the restart gate (no-ops while some problem is active)
+  // End of an outer round: the FP64 true residual of every problem that has
+  // stopped since the last check (only when the last decision saw one: in
+  // a batch most rounds end with a replacement and check nothing), then the
+  // restart gate (a no-op while some problem is active)
   const int max_rounds = ctx->opts.max_iter + 64;
-  auto gate = [&](Emit& e) -> fftmech_status {
+  auto truecheck = [&](Emit& e) -> fftmech_status {
     EM_LAUNCH(e, FFTMECH_K_RESIDUAL, residual(0, 2, e.st));
     EM_LAUNCH(e, FFTMECH_K_COLUMN, colpass(COL_TRUENORM, e.st));
+    return FFTMECH_OK;
+  };
+  auto gate = [&](Emit& e) -> fftmech_status {
     EM_LAUNCH(e, FFTMECH_K_OTHER, launch_gate(ctx->sc, ctx->mode, B, e.ctl, max_rounds, e.st));
     return FFTMECH_OK;
   };
@@ -694,7 +701,7 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
     // WHILE outer {
     //   conditions from memory; WHILE loop { ordinary iteration }
     //   IF replace { replacement iteration }
-    //   true residuals, gate; IF restart { restart, first direction } }
+    //   IF gate { true residuals }; gate; IF restart { restart, first direction } }
     // Every condition is set by kernels of its own graph or of a body one
     // level down.
     Emit top = em;
@@ -704,9 +711,11 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
       RC(em_handle(o, LF_LOOP));
       RC(em_handle(o, LF_REPLACE));
       RC(em_handle(o, LF_RESTART));
+      RC(em_handle(o, LF_GATE));
       EM_LAUNCH(o, FFTMECH_K_OTHER, launch_sync_flags(o.ctl, o.st));
       RC(em_cond(o, LF_LOOP, cudaGraphCondTypeWhile, [&](Emit& l) { return iteration(l, true); }));
       RC(em_cond(o, LF_REPLACE, cudaGraphCondTypeIf, [&](Emit& r) { return iteration(r, false); }));
+      RC(em_cond(o, LF_GATE, cudaGraphCondTypeIf, truecheck));
       RC(gate(o));
       return em_cond(o, LF_RESTART, cudaGraphCondTypeIf, restart);
     }));
@@ -728,7 +737,9 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
       if (f[LF_REPLACE]) {
         RC(iteration(em, false));
         if (++total > cap) return set_err(ctx, FFTMECH_ERR_CUDA, "PCG loop did not stop within its iteration limit");
+        RC(poll_flags(em, f));
       }
+      if (f[LF_GATE]) RC(truecheck(em));
       RC(gate(em));
       RC(poll_flags(em, f));
       if (!f[LF_OUTER]) break;
@@ -1101,8 +1112,10 @@ void count_graph_kernels(fftmech_ctx* ctx) {
       rep = std::max<long long>(rep, S[b].nreplace);
       rst = std::max<long long>(rst, S[b].nrestart);
     }
-    n += lc->body[k][LF_OUTER] * (1 + rst) + lc->body[k][LF_LOOP] * it + lc->body[k][LF_REPLACE] * rep +
-         lc->body[k][LF_RESTART] * rst;
+    // rounds: one plus one per replacement and per restart; the gate's
+    // true-residual body once plus once per restart
+    n += lc->body[k][LF_OUTER] * (1 + rep + rst) + lc->body[k][LF_LOOP] * std::max(0LL, it - rep) +
+         lc->body[k][LF_REPLACE] * rep + lc->body[k][LF_GATE] * (1 + rst) + lc->body[k][LF_RESTART] * rst;
   }
   ctx->graph_kernels += n;
   ctx->last.lc = nullptr;

@@ -50,18 +50,22 @@ __global__ void k_zero_rhs(double* u, float* uh, float* ul, long long n, SolverS
 // Loop decisions of a batch after a direction (the direction kernel takes
 // them itself for one problem): ordinary iterations continue while some
 // problem is active and none replaces its residual next; a replacement
-// iteration (which the others run as an ordinary one) comes first otherwise.
+// iteration (which the others run as an ordinary one) comes first
+// otherwise; the gate's true-residual passes run when some problem has
+// stopped unchecked.
 __global__ void __launch_bounds__(kCtlThreads) k_loopctl(const SolverScalars* sc, const int* mode, int batch,
                                                          LoopCtl ctl) {
-  int active = 0, rep = 0;
+  int active = 0, rep = 0, gate = 0;
   for (int b = threadIdx.x; b < batch; b += blockDim.x) {
     const int a = !done_flag(sc + b);
     active |= a;
     if (a && mode && vol_readi(mode + b) == 1) rep = 1;
+    if (unchecked_stop(sc + b)) gate = 1;
   }
   active = __syncthreads_or(active);
   rep = __syncthreads_or(rep);
-  if (threadIdx.x == 0) loop_decide(ctl, active, rep);
+  gate = __syncthreads_or(gate);
+  if (threadIdx.x == 0) loop_decide(ctl, active, rep, gate);
 }
 
 // End of an outer round. Problems that stopped in this round have their
@@ -130,12 +134,13 @@ __global__ void __launch_bounds__(kCtlThreads) k_gate(SolverScalars* sc, int* mo
   }
 }
 
-// Start of an outer round: the loop and replacement conditions take the
-// values the last decision stored in device memory.
+// Start of an outer round: the loop, replacement and gate conditions take
+// the values the last decision stored in device memory.
 __global__ void k_sync_flags(LoopCtl ctl) {
   if (threadIdx.x != 0 || !ctl.flags) return;
   set_loop_flag(ctl, LF_LOOP, vol_readi(ctl.flags + LF_LOOP));
   set_loop_flag(ctl, LF_REPLACE, vol_readi(ctl.flags + LF_REPLACE));
+  set_loop_flag(ctl, LF_GATE, vol_readi(ctl.flags + LF_GATE));
 }
 
 // Restarted problems return to ordinary iterations.

@@ -112,18 +112,19 @@ struct SolverScalars {
 // of a launch sets a given condition (concurrent cudaGraphSetConditional
 // calls on one handle are not allowed).
 // LF_LOOP: run another ordinary iteration; LF_REPLACE: the next iteration
-// replaces a residual (reliable update); LF_DONE: every problem has stopped;
-// LF_OUTER: the solve goes on (set before the first iteration, cleared by
-// the restart gate); LF_RESTART: some problem restarts from its true
-// residual.
+// replaces a residual (reliable update); LF_GATE: some problem has stopped
+// and its FP64 true residual has not been checked yet (the gate's
+// true-residual passes run); LF_OUTER: the solve goes on (set before the
+// first iteration, cleared by the restart gate); LF_RESTART: some problem
+// restarts from its true residual.
 // LF_ROUNDS (not a condition) counts the outer rounds of a solve; the gate
 // ends a solve whose rounds exceed max_iter + 64.
-enum LoopFlag { LF_LOOP = 0, LF_REPLACE = 1, LF_OUTER = 2, LF_RESTART = 3, LF_DONE = 4, LF_ROUNDS = 5, LF_COUNT = 6 };
+enum LoopFlag { LF_LOOP = 0, LF_REPLACE = 1, LF_OUTER = 2, LF_RESTART = 3, LF_GATE = 4, LF_ROUNDS = 5, LF_COUNT = 6 };
 struct LoopCtl {
   int* flags;                      // LF_COUNT ints (NULL: no loop control in this launch)
   unsigned long long h[LF_COUNT];  // cudaGraphConditionalHandle per flag (graph mode)
   unsigned int have;               // bit k: h[k] is valid in the graph being run
-  int direct;                      // 1: one problem; the direction kernel sets LF_LOOP, LF_REPLACE, LF_DONE
+  int direct;                      // 1: one problem; the direction kernel sets LF_LOOP, LF_REPLACE, LF_GATE
 };
 
 // Column-pass modes: ITER (one PCG iteration: beta, convergence), NORM

@@ -140,7 +140,7 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
           s->rz_pending = 1;
           if (is_true) s->rz_true = tot;
           set_beta(s, beta);
-          const int next = reliable_next(s, tot, is_true);
+          const int next = reliable_next(s, tot, is_true, vol_readi(&s->iter) + 1);
           if (v.mode) v.mode[bp] = next;
           if (lead) loop_decide(v.ctl, 1, next);
         }

@@ -48,14 +48,21 @@ static __device__ __forceinline__ void set_beta(SolverScalars* sc, double b) {
 // that continues. After a replacement its residual norm becomes the new
 // reference; otherwise the next iteration replaces the float recursive
 // residual by the FP64 true residual once <r, M^-1 r> has fallen 100-fold
-// below that reference (the search direction is kept). Single writer.
-static __device__ __forceinline__ int reliable_next(SolverScalars* sc, double tot, int was_replacement) {
+// below that reference (the search direction is kept). The test is taken
+// only after every kReplacePeriod-th iteration, so that the problems of a
+// batch that fall due close together are replaced in the same iteration
+// (each replacement iteration ends a round of the device-driven loop, with
+// its own launches). Single writer.
+constexpr int kReplacePeriod = 16;
+
+static __device__ __forceinline__ int reliable_next(SolverScalars* sc, double tot, int was_replacement,
+                                                    int iter_after) {
   if (!sc->reliable) return 0;
   if (was_replacement) {
     sc->rz_rep = tot;
     return 0;
   }
-  if (tot < 1e-2 * sc->rz_rep) {
+  if (tot < 1e-2 * sc->rz_rep && iter_after % kReplacePeriod == 0) {
     sc->nreplace += 1;
     return 1;
   }
@@ -86,10 +93,15 @@ static __device__ __forceinline__ void commit_pending_rz(SolverScalars* sc) {
 // Loop decisions after a direction (single writer): an active problem runs
 // an ordinary iteration next, or a replacement iteration; a stopped one
 // ends the loop.
-static __device__ __forceinline__ void loop_decide(const LoopCtl& c, int active, int replace) {
+// gate: some problem has stopped and awaits its true-residual check (one
+// problem: it has stopped).
+static __device__ __forceinline__ void loop_decide(const LoopCtl& c, int active, int replace, int gate) {
   set_loop_flag(c, LF_LOOP, active && !replace);
   set_loop_flag(c, LF_REPLACE, active && replace);
-  set_loop_flag(c, LF_DONE, !active);
+  set_loop_flag(c, LF_GATE, gate);
+}
+static __device__ __forceinline__ void loop_decide(const LoopCtl& c, int active, int replace) {
+  loop_decide(c, active, replace, !active);
 }
 
 // pmode: this problem's iteration mode (NULL when there is none); ITER and
@@ -139,7 +151,7 @@ static __device__ void finalize_col(SolverScalars* sc, int mode, double tot, int
   // float recursion had drifted: restart the direction instead of mixing
   if (mode == COL_TRUE && beta > 1.0) beta = 0.0;
   set_beta(sc, beta);
-  const int next = reliable_next(sc, tot, mode == COL_TRUE);
+  const int next = reliable_next(sc, tot, mode == COL_TRUE, sc->iter);
   if (pmode) *pmode = next;
 }
 
