@@ -49,7 +49,13 @@ LAUNCH_MODE = 0  # 0: programmatic dependent launches (the library default); 1: 
 # DRAM bytes (read + write) per launch of a workload's dominant kernel class,
 # from one ncu capture (L2 flushed before the launch) of the kernels as they
 # stand; an entry is removed when its kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 243^3 sponge, D = 3 (profiles/traffic_sponge243.md): the three line passes of one iteration
+    ("random-sponge-243^3-eigenstrain-ramp-staggered", "column"): 857.5e6,
+    ("random-sponge-243^3-eigenstrain-ramp-staggered", "update"): 1489.0e6,
+    ("random-sponge-243^3-eigenstrain-ramp-staggered", "direction"): 468.6e6,
+    ("random-sponge-243^3-eigenstrain-ramp-staggered", "stencil"): 391.3e6,
+}
 METRIC = "FFT-Galerkin CG voxel-iterations/s"
 UNIT = "voxel-iterations/s"
 
@@ -242,7 +248,8 @@ AUTOTUNE_ITERS = 30  # 0 disables the launch-shape autotuner
 TUNED = {}  # workload name -> (us per iteration before, after, shapes)
 
 
-def run_arm(torch, fm, w, prec, steps, warmup, device, profile=False, flush=None, tol=None, execution=None):
+def run_arm(torch, fm, w, prec, steps, warmup, device, profile=False, flush=None, tol=None, execution=None,
+            precond=0):
     """W warm-up steps, then `steps` timed staggered steps (L2 flushed before
     each), timed with CUDA events on the library's stream. profile=True runs
     the host-driven loop with per-launch events (per kernel class times).
@@ -253,7 +260,7 @@ def run_arm(torch, fm, w, prec, steps, warmup, device, profile=False, flush=None
     ex = execution if execution is not None else (fm.FFTMECH_EXEC_HOST if profile else fm.FFTMECH_EXEC_GRAPH)
     ctx = fm.Context(w.phase.shape, w.materials, prec, h=w.h, h_diff=w.h_diff, tol=tol or w.tol,
                      max_iter=20000, replace_residual=1, check_every=16, launch_mode=LAUNCH_MODE,
-                     stream=stream.cuda_stream, batch=len(ws), execution=ex)
+                     stream=stream.cuda_stream, batch=len(ws), execution=ex, precond=precond)
     bufs, st, p = make_state(torch, fm, ws, prec, device)
     if AUTOTUNE_ITERS:  # times once per workload; later contexts take the cached choice
         TUNED.setdefault((workload_name(w, len(ws)), prec), fm.fftmech_autotune(ctx.handle, AUTOTUNE_ITERS))
@@ -694,6 +701,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the 243^3 sponge and the uneven batch")
     ap.add_argument("--no-fft", action="store_true", help="skip the cuFFT comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the eigenstrain adjoint timing")
+    ap.add_argument("--no-precond", action="store_true", help="skip the reference-medium preconditioner run")
+    ap.add_argument("--host-driven", action="store_true",
+                    help="run the headline steps host-driven (no CUDA graph; for profilers)")
     ap.add_argument("--adjoint-n", type=int, default=2187, help="carpet side of the adjoint timing")
     ap.add_argument("--extra-steps", type=int, default=4, help="timed steps of the extra workloads")
     ap.add_argument("--cpu-iters", type=int, default=40)
@@ -766,7 +776,8 @@ def main():
     barrier()
     sampler.start()
     t_wall = time.perf_counter()
-    mixed = run_arm(torch, fm, ws, fm.FFTMECH_MIXED, args.steps, args.warmup, device, flush=flush)
+    mixed = run_arm(torch, fm, ws, fm.FFTMECH_MIXED, args.steps, args.warmup, device, flush=flush,
+                    execution=fm.FFTMECH_EXEC_HOST if args.host_driven else None)
     barrier()
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
@@ -813,7 +824,8 @@ def main():
                    "porosity": w.extra["porosity"], "steps_per_run": w.steps,
                    "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before each timed step",
                    "parallelism": f"{world} independent RVE replicas",
-                   "execution": "one CUDA graph per staggered step (device-driven loops)",
+                   "execution": ("host-driven loops (flags read after every iteration)" if args.host_driven
+                                 else "one CUDA graph per staggered step (device-driven loops)"),
                    "launches": "plain stream order" if LAUNCH_MODE else "programmatic dependent"},
         "breakdown": breakdown,
         "kernels": kernels,
@@ -848,6 +860,22 @@ def main():
             "note": "tol 1e-9 keeps strain, stress, c and damage within 1e-5 / 1e-5 / 1e-6 / 1e-4 of the "
                     "FP64 result at 1e-12 over all 200 steps (tests/test_gpu_drift.py); at 1e-8 both "
                     "paths drift past 1e-5"}
+    if rank == 0 and not args.no_precond and w.dim == 2:
+        # the reference-medium preconditioner on the same steps: the same
+        # solution in fewer equilibrium iterations
+        ref = run_arm(torch, fm, ws, fm.FFTMECH_MIXED, args.steps, args.warmup, device, flush=flush,
+                      precond=fm.FFTMECH_PRECOND_REFERENCE)
+        eq_it = lambda run: sum(inf[3 * b + 1]["iters"] for inf in run["infos"] for b in range(len(inf) // 3))
+        errs = {}
+        for k in ("strain", "stress"):
+            a, b = ref["state"][k], mixed["state"][k]
+            errs[k] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        out["precond_reference"] = {
+            "ms_per_step": float(np.mean(ref["ms"])), "laplace_ms_per_step": float(np.mean(mixed["ms"])),
+            "equilibrium_iters": eq_it(ref), "laplace_equilibrium_iters": eq_it(mixed),
+            "value": vi_of(ref, Np) / (sum(ref["ms"]) / 1e3), "unit": UNIT,
+            "fields_vs_laplace_rel": errs,
+            "note": "Moulinec-Suquet reference medium (lambda/mu of the solid) in the 2D equilibrium PCG"}
     if rank == 0 and not args.no_e2e:
         e2e = run_e2e(torch, fm, ws, fm.FFTMECH_MIXED, args.steps, args.warmup, device)
         out["e2e"] = {"value": e2e["value"] * world, "unit": UNIT,

@@ -128,8 +128,18 @@ typedef struct {
  * launch_mode: 0 (default) launches the kernels of a PCG iteration as
  * programmatic dependent launches (each kernel starts launching while the
  * previous one finishes and waits on the device for its results); 1 uses
- * plain stream order. Both give bit-identical results. */
+ * plain stream order. Both give bit-identical results.
+ * precond: preconditioner of the 2D equilibrium PCG. FFTMECH_PRECOND_LAPLACE
+ * (0, default): F^-1 (1 / |D|^2) F per component, the projection of App. A
+ * (Eq. g-42). FFTMECH_PRECOND_REFERENCE (1): the inverse of the Galerkin
+ * operator of a homogeneous isotropic reference medium, per mode the 2 x 2
+ * Hermitian matrix |D|^2 I + rho conj(D) D^T + D conj(D)^T inverted, with
+ * rho = lambda / mu of the solid (the Moulinec-Suquet reference medium the
+ * paper names as the classical scheme's preconditioner, Sec. 1; exact for a
+ * homogeneous medium of that Poisson ratio). Same solution, fewer
+ * iterations; diffusion, phase-field and 3D solves keep the Laplace one. */
 enum { FFTMECH_EXEC_GRAPH = 0, FFTMECH_EXEC_HOST = 1 };
+enum { FFTMECH_PRECOND_LAPLACE = 0, FFTMECH_PRECOND_REFERENCE = 1 };
 typedef struct {
   double tol;
   int max_iter;
@@ -137,6 +147,7 @@ typedef struct {
   int check_every;
   int launch_mode;
   int execution;
+  int precond;
 } fftmech_solver_opts;
 
 /* Per-solve report (host struct). All averages in FP64 over every voxel. */

@@ -189,3 +189,28 @@ def effective_stiffness(phase, mat, h, g=None, tol=1e-12):
         out = equilibrium_solve(phase, np.zeros(phase.shape), g, E, mat, h, tol=tol)
         C[:, J] = out["mean_stress"]
     return C
+
+
+def reference_medium_preconditioner(r, lam0, mu0, h):
+    """z = K0^-1 r for a displacement-space residual r (shape (d, *grid)),
+    K0 = grad+^T C0 grad+ the Galerkin operator of a homogeneous isotropic
+    reference medium C0 (lambda0, mu0): the Moulinec-Suquet reference medium
+    (Sec. 1), per Fourier mode with the forward-difference symbol D (Sec. 2.6).
+    From sigma_hat_ij = lambda0 delta_ij (D . u) + mu0 (D_j u_i + D_i u_j) and
+    (K0 u)_i = sum_j conj(D_j) sigma_hat_ij, each mode solves the d x d system
+        (mu0 |D|^2 I + lambda0 conj(D) D^T + mu0 D conj(D)^T) z_hat = r_hat
+    (numpy.linalg.solve per mode); z_hat = 0 at k = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    d = r.shape[0]
+    shape = r.shape[1:]
+    D = spectral.forward_difference_symbol(shape, h)
+    rh = np.stack([spectral.fft(r[i]) for i in range(d)])
+    zh = np.zeros_like(rh)
+    for idx in np.ndindex(*shape):
+        a = np.array([D[i][idx] for i in range(d)])
+        n2 = float(np.sum(np.abs(a) ** 2))
+        if n2 == 0.0:
+            continue
+        K = mu0 * n2 * np.eye(d) + lam0 * np.outer(np.conj(a), a) + mu0 * np.outer(a, np.conj(a))
+        zh[(slice(None),) + idx] = np.linalg.solve(K, rh[(slice(None),) + idx])
+    return np.stack([spectral.ifft(zh[i]).real for i in range(d)])

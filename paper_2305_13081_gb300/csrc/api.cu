@@ -168,6 +168,10 @@ struct fftmech_ctx {
   void* lamc1 = nullptr;
   void* wcol3 = nullptr;    // 3D: Parseval weight per spectral column
   void* wcol1 = nullptr;
+  void* ax = nullptr;       // 2D: D h per column kx = 0 .. nx / 2 (complex), reference medium
+  void* ay = nullptr;       // 2D: D h per row ky (complex)
+  double rho = 0;           // lambda / mu of the solid (reference medium)
+  int ms_cw = 0, ms_threads = 0;  // reference-medium column pass: strip width, threads (0: unavailable)
   double* partials = nullptr;
   double* partials_col = nullptr;  // 2D column pass (deferred reductions)
   double* m0b = nullptr;       // per-problem preconditioner constants
@@ -388,6 +392,20 @@ fftmech_status fill_lam(fftmech_ctx* ctx) {
   for (int k = 0; k < ctx->ny; ++k) ly[k] = sym(k, ctx->ny);
   CK(cudaMemcpy(ctx->lamx, lx.data(), sizeof(T) * ctx->nx, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->lamy, ly.data(), sizeof(T) * ctx->ny, cudaMemcpyHostToDevice));
+  if (ctx->dim == 2) {
+    // D h = e^{i theta} - 1 per mode (reference-medium preconditioner)
+    auto dh = [](int k, int n, T* out) {
+      const double th = 2.0 * M_PI * k / n;
+      out[0] = (T)(std::cos(th) - 1.0);
+      out[1] = (T)std::sin(th);
+    };
+    const int H = ctx->nx / 2 + 1;
+    std::vector<T> ax(2 * H), ay(2 * ctx->ny);
+    for (int k = 0; k < H; ++k) dh(k, ctx->nx, &ax[2 * k]);
+    for (int k = 0; k < ctx->ny; ++k) dh(k, ctx->ny, &ay[2 * k]);
+    CK(cudaMemcpy(ctx->ax, ax.data(), sizeof(T) * ax.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->ay, ay.data(), sizeof(T) * ay.size(), cudaMemcpyHostToDevice));
+  }
   if (ctx->dim == 3) {
     const int nx = ctx->nx, nxh = nx / 2 + 1;
     std::vector<T> lz(ctx->nz), c3, c1, w3, w1;
@@ -589,7 +607,16 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
   // re-reading all partials costs more than the ticket saves.
   const bool small = (long long)ctx->N * B <= (1LL << 21);
   const bool defer = small && !three;
-  const int ncol_blocks = defer ? (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols : 0;
+  // reference-medium preconditioner: 2D elasticity only
+  const bool ms = D == 2 && !three && ctx->opts.precond == FFTMECH_PRECOND_REFERENCE && ctx->ms_cw > 0;
+  if (ms) {
+    sp.ax = (const cx<T>*)ctx->ax;
+    sp.ay = (const cx<T>*)ctx->ay;
+    sp.rho_t = (T)ctx->rho;
+  }
+  const int ncol_blocks = !defer ? 0
+                          : ms   ? colpass_ms_blocks(ctx->nx, ctx->ms_cw)
+                                 : (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;
   v.nsten = !small ? 0
             : three ? sten3_blocks(ctx->nx, ctx->ny, ctx->nz, ctx->sshape)
                     : sten2_blocks(ctx->nx, ctx->ny, ctx->sshape);
@@ -627,6 +654,9 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
   };
   // 2D: one column pass; 3D: y-FFT, z pass (multiplier, <r, M^-1 r>), y-IFFT
   auto colpass = [&](int mode, cudaStream_t st) -> cudaError_t {
+    if (ms)
+      return launch_colpass_ms_f<T>(fy, ctx->nx, ctx->ny, v.S, py, sp, ctx->ms_cw, ctx->ms_threads, B, mode,
+                                    ctx->partials_col, ctx->sc, ctx->mode, st);
     if (!three)
       return launch_colpass_f<T>(fy, ctx->nx, ctx->ny, v.S, py, sp, sh, mode, 0, ctx->partials_col, ctx->sc, ctx->mode,
                                  st);
@@ -1123,7 +1153,8 @@ void count_graph_kernels(fftmech_ctx* ctx) {
 
 bool opts_ok(const fftmech_solver_opts* o) {
   return o->tol >= 0 && o->max_iter >= 0 && o->launch_mode >= 0 && o->launch_mode <= 1 &&
-         (o->execution == FFTMECH_EXEC_GRAPH || o->execution == FFTMECH_EXEC_HOST);
+         (o->execution == FFTMECH_EXEC_GRAPH || o->execution == FFTMECH_EXEC_HOST) &&
+         (o->precond == FFTMECH_PRECOND_LAPLACE || o->precond == FFTMECH_PRECOND_REFERENCE);
 }
 
 // Staged device pointers of a staggered step; `all_device`: nothing was
@@ -1708,6 +1739,23 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   }
   if (!shp) return fail(FFTMECH_ERR_UNSUPPORTED_SIZE);
   ctx->shape.batch = batch;
+  if (!three) {
+    // reference-medium column pass: the widest strip (4, 2 or 1 columns and
+    // their mirrors) that fits the shared memory and 512 threads
+    const size_t es2 = fp64 ? 16 : 8;  // complex element
+    for (int cw = 4; cw >= 1 && !ctx->ms_cw; cw /= 2) {
+      const size_t sm = (size_t)ctx->ny * 2 * cw * es2 + (size_t)(ctx->ny + cw) * es2 +
+                        (fp64 ? tw_smem_bytes<double>(ctx->ny) : tw_smem_bytes<float>(ctx->ny));
+      const int thr = need_threads(ctx->py, 2 * cw);
+      if (sm + 1024 <= ctx->optin && thr <= 512) {
+        ctx->ms_cw = cw;
+        ctx->ms_threads = std::min(512, std::max(128, round32(thr)));
+      }
+    }
+    double l1, m1s;
+    lame(mat->E_solid, mat->nu_solid, l1, m1s);
+    ctx->rho = l1 / m1s;
+  }
   {
     // the rule-based shapes (a context never inherits another's tuning: its
     // reductions' block partitions, and so its last bits, depend only on
@@ -1758,6 +1806,10 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   alloc((void**)&ctx->cn, NB * 8);
   alloc(&ctx->lamx, ctx->nx * es);
   alloc(&ctx->lamy, ctx->ny * es);
+  if (!three) {
+    alloc(&ctx->ax, (size_t)(ctx->nx / 2 + 1) * 2 * es);
+    alloc(&ctx->ay, (size_t)ctx->ny * 2 * es);
+  }
   if (three) {
     alloc(&ctx->lamz, ctx->nz * es);
     alloc(&ctx->lamc3, (size_t)nxs_of(ctx->nx, 3) * es);
@@ -1797,6 +1849,7 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
     if (c.exec) cudaGraphExecDestroy(c.exec);
   void* bufs[] = {ctx->r, ctx->q, ctx->p, ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
                   ctx->cn, ctx->lamx, ctx->lamy, ctx->lamz, ctx->lamc3, ctx->lamc1, ctx->wcol3, ctx->wcol1,
+                  ctx->ax, ctx->ay,
                   ctx->partials, ctx->partials_col, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc, ctx->flags, ctx->rec};
   for (void* b : bufs)
     if (b) cudaFree(b);

@@ -1,6 +1,9 @@
-// 2D column passes for columns of 81 points (compile-time FFT, float).
+// 2D column passes for columns of 81 points (compile-time FFT, float), Laplace and
+// reference-medium preconditioners.
 #include "kernels2d.cuh"
+#include "colpass_ms.cuh"
 
 namespace fftmech {
 FFTMECH_INST_COL_FIXED(81)
+FFTMECH_INST_COL_MS_FIXED(81)
 }  // namespace fftmech

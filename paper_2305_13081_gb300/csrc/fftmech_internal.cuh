@@ -252,6 +252,11 @@ struct Spec {
   const T* laml;
   const T* wcol;
   T m0_t, m1_t, invN_t;  // m0, m1, invN rounded to T by the host
+  // reference-medium preconditioner (2D elasticity; NULL = Laplace): D h per
+  // mode along x (columns 0 .. nx / 2) and y, and lambda0 / mu0
+  const cx<T>* ax;
+  const cx<T>* ay;
+  T rho_t;
 };
 
 // Launch shapes chosen by the host.
@@ -369,6 +374,14 @@ inline cudaError_t launch_colpass_f(int fy, int nx, int ny, cx<T>* S, const FftP
   FFTMECH_FAMILY_SWITCH(fy, FFTMECH_C)
 #undef FFTMECH_C
 }
+// Column pass with the reference-medium preconditioner (colpass_ms.cu): one
+// block per strip of CW columns kx <= nx / 2 and their mirrors nx - kx.
+inline int colpass_ms_blocks(int nx, int CW) { return (nx / 2 + 1 + CW - 1) / CW; }
+template <typename T>
+cudaError_t launch_colpass_ms_f(int fy, int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec<T>& sp,
+                                int CW, int threads, int batch, int mode, double* partials, SolverScalars* sc,
+                                int* pmode, cudaStream_t st);
+
 template <typename T>
 inline cudaError_t launch_rowfft_f(int fx, int nx, int ny, cx<T>* S, const FftPlanDev<T>& px,
                                    int inverse, const Shape2& sh, cudaStream_t st) {

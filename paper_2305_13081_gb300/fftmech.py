@@ -37,6 +37,9 @@ FFTMECH_EIG_PRESCRIBED = 1
 # execution of a solve or a staggered step
 FFTMECH_EXEC_GRAPH = 0
 FFTMECH_EXEC_HOST = 1
+# preconditioner of the 2D equilibrium PCG
+FFTMECH_PRECOND_LAPLACE = 0
+FFTMECH_PRECOND_REFERENCE = 1
 # objectives of the eigenstrain adjoint
 FFTMECH_OBJ_ENERGY = 0
 FFTMECH_OBJ_DAMAGE = 1
@@ -69,7 +72,7 @@ class fftmech_materials(ctypes.Structure):
 class fftmech_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("replace_residual", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("launch_mode", ctypes.c_int), ("execution", ctypes.c_int)]
+                ("launch_mode", ctypes.c_int), ("execution", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class fftmech_solve_info(ctypes.Structure):
@@ -520,7 +523,7 @@ def make_materials(m):
 
 
 def make_opts(tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, launch_mode=0,
-              execution=FFTMECH_EXEC_GRAPH):
+              execution=FFTMECH_EXEC_GRAPH, precond=FFTMECH_PRECOND_LAPLACE):
     o = fftmech_solver_opts()
     o.tol = tol
     o.max_iter = max_iter
@@ -528,6 +531,7 @@ def make_opts(tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, laun
     o.check_every = check_every
     o.launch_mode = launch_mode
     o.execution = execution
+    o.precond = precond
     return o
 
 
@@ -536,13 +540,13 @@ class Context:
 
     def __init__(self, shape, materials, precision=FFTMECH_FP64, h=5e-6, h_diff=1.0,
                  tol=1e-8, max_iter=20000, replace_residual=1, check_every=16, stream=None, batch=1,
-                 launch_mode=0, execution=FFTMECH_EXEC_GRAPH):
+                 launch_mode=0, execution=FFTMECH_EXEC_GRAPH, precond=FFTMECH_PRECOND_LAPLACE):
         self.shape = tuple(shape)
         self.precision = precision
         self.batch = batch
         self.grid = make_grid(shape, h, h_diff)
         self.mat = make_materials(materials)
-        self.opts = make_opts(tol, max_iter, replace_residual, check_every, launch_mode, execution)
+        self.opts = make_opts(tol, max_iter, replace_residual, check_every, launch_mode, execution, precond)
         if batch == 1:
             self.handle = fftmech_create(self.grid, self.mat, precision, self.opts, stream)
         else:
