@@ -50,8 +50,7 @@ LAUNCH_MODE = 0  # 0: programmatic dependent launches (the library default); 1: 
 # from one ncu capture (L2 flushed before the launch) of the kernels as they
 # stand; an entry is removed when its kernel changes.
 NCU_TRAFFIC = {
-    # 243^3 sponge, D = 3 (profiles/traffic_sponge243.md): the three line passes of one iteration
-    ("random-sponge-243^3-eigenstrain-ramp-staggered", "column"): 857.5e6,
+    # 243^3 sponge, D = 3 (profiles/traffic_sponge243.md)
     ("random-sponge-243^3-eigenstrain-ramp-staggered", "update"): 1489.0e6,
     ("random-sponge-243^3-eigenstrain-ramp-staggered", "direction"): 468.6e6,
     ("random-sponge-243^3-eigenstrain-ramp-staggered", "stencil"): 391.3e6,

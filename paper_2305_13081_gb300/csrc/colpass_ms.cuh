@@ -38,14 +38,16 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass_ms(int nx, int ny, cx<T>* S, FftPlan
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(py.n);
   const FftPlanDev<T> py_s = plan_to_smem(py, reinterpret_cast<cx<T>*>(smem_all));
-  const int ncs = 2 * CW;  // lower columns in slots 0 .. CW - 1, mirrors in CW .. 2 CW - 1
+  const int ncs = NY > 0 ? 8 : 2 * CW;  // lower columns in slots 0 .. CW - 1, mirrors in CW .. 2 CW - 1
+  const int bd = NY > 0 ? kColThreads : (int)blockDim.x;  // a constant with a compile-time plan
+  if constexpr (NY > 0) ny = NY;
   cx<T>* B = reinterpret_cast<cx<T>*>(smem);
   cx<T>* AY = B + (size_t)ny * ncs;
   cx<T>* AX = AY + ny;
   const int H = nx / 2 + 1;
   const int x0 = blockIdx.x * CW;
   const int nc = min(CW, H - x0);
-  for (int i = threadIdx.x; i < ny; i += blockDim.x) AY[i] = sp.ay[i];
+  for (int i = threadIdx.x; i < ny; i += bd) AY[i] = sp.ay[i];
   if ((int)threadIdx.x < CW) AX[threadIdx.x] = (int)threadIdx.x < nc ? sp.ax[x0 + threadIdx.x] : mk(T(0), T(0));
   grid_dep_sync();  // plan and tables are constant; everything below follows the previous kernel
   if (mode == COL_ITER && pmode && pmode[bp] == 1) mode = COL_TRUE;  // reliable update of this problem
@@ -56,13 +58,13 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass_ms(int nx, int ny, cx<T>* S, FftPlan
   __shared__ float redf[64];
   const int n = ny * ncs;
   const FastDiv dn(ncs);
-  for (int i = threadIdx.x; i < n; i += 8 * blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += 8 * bd) {
     cx<T> t[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int ii = i + k * blockDim.x;
+      const int ii = i + k * bd;
       if (ii < n) {
-        const int y = dn.div(ii), s = ii - y * ncs;
+        const int y = NY > 0 ? ii / 8 : dn.div(ii), s = ii - y * ncs;
         const int c = s < CW ? s : s - CW;
         const int kx = x0 + c;
         const int col = s < CW ? kx : (kx == 0 ? 0 : nx - kx);
@@ -71,7 +73,7 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass_ms(int nx, int ny, cx<T>* S, FftPlan
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      if (i + k * blockDim.x < n) B[i + k * blockDim.x] = t[k];
+      if (i + k * bd < n) B[i + k * bd] = t[k];
   }
   __syncthreads();
   if constexpr (NY > 0) fftc<T, -1, NY, true, 8, kColThreads>(B, py_s.tw, 8);  // CW = 4: 8 columns
@@ -85,7 +87,7 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass_ms(int nx, int ny, cx<T>* S, FftPlan
   T part = T(0);
   int cnt = 0;
   const FastDiv dc(nc);
-  for (int i = threadIdx.x; i < ny * nc; i += blockDim.x) {
+  for (int i = threadIdx.x; i < ny * nc; i += bd) {
     const int ky = dc.div(i), c = i - ky * nc;
     const int kx = x0 + c;
     const bool self = kx == 0 || 2 * kx == nx;
@@ -133,8 +135,8 @@ __global__ void FFTMECH_BOUNDS(T) k_colpass_ms(int nx, int ny, cx<T>* S, FftPlan
     if constexpr (NY > 0) fftc<T, 1, NY, true, 8, kColThreads>(B, py_s.tw, 8);
     else fft_lines<T, 1, FY>(B, py_s, ncs, 1, ncs, true);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int y = dn.div(i), s = i - y * ncs;
+    for (int i = threadIdx.x; i < n; i += bd) {
+      const int y = NY > 0 ? i / 8 : dn.div(i), s = i - y * ncs;
       const int c = s < CW ? s : s - CW;
       const int kx = x0 + c;
       if (c >= nc) continue;

@@ -52,11 +52,14 @@ __device__ __forceinline__ void fftc_pass(cx<T>* buf, const cx<T>* __restrict__ 
   constexpr int BM = (COL && THR > 0) ? ((N / R) * CW + THR - 1) / THR : PassBatch<R>::value;
   constexpr int NB = N / R;
   const int total = COL ? NB * CW : NB * nlines;
+  // the block size as a constant where it is one: the butterfly indices
+  // tid + b THR then fold into immediate offsets
+  const int bstride = (COL && THR > 0) ? THR : (int)blockDim.x;
   cx<T> v[BM][R];
   int jb[BM];
 #pragma unroll
   for (int b = 0; b < BM; ++b) {
-    const int idx = tid + b * blockDim.x;
+    const int idx = tid + b * bstride;
     if (idx < total) {
       int in;
       if constexpr (COL) {
@@ -74,7 +77,7 @@ __device__ __forceinline__ void fftc_pass(cx<T>* buf, const cx<T>* __restrict__ 
   __syncthreads();
 #pragma unroll
   for (int b = 0; b < BM; ++b) {
-    const int idx = tid + b * blockDim.x;
+    const int idx = tid + b * bstride;
     if (idx < total) {
       int j, base0;
       if constexpr (COL) {

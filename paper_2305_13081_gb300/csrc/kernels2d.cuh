@@ -179,7 +179,10 @@ template <typename T, int FY, int NY, int CWC>
 __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* S, cx<T>* B, const FftPlanDev<T>& py_s,
                                               const Spec<T>& sp, const T* lamx_s, const T* lamy_s, int CW, int mode,
                                               int inverse, int bp, Acc<T>& acc) {
-  const int bd = blockDim.x;
+  // with a compile-time plan the block size and the column length are
+  // constants: the strip loops' row and column indices fold into offsets
+  const int bd = NY > 0 ? kColThreads : (int)blockDim.x;
+  if constexpr (NY > 0) ny = NY;
   const int x0 = strip * CW;
   const int nc = min(CW, nx - x0);
   // shared rows: ncs columns; a compile-time plan always transforms CWC

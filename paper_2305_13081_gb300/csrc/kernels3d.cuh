@@ -296,7 +296,10 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(pl.n);
   const FftPlanDev<T> pl_s = plan_to_smem(pl, reinterpret_cast<cx<T>*>(smem_all));
-  const int bd = blockDim.x;
+  // with a compile-time plan the block size and the line length are
+  // constants: the strip loops' row and column indices fold into offsets
+  const int bd = NL > 0 ? kLineThreads : (int)blockDim.x;
+  if constexpr (NL > 0) nlines = NL;
   const int nstrips = (ncols + CW - 1) / CW;
   const int item = blockIdx.x;  // (line set j, strip)
   const int j = item / nstrips, strip = item - j * nstrips;
@@ -328,6 +331,7 @@ __global__ void FFTMECH_BOUNDS3 k3_lines(cx<T>* S, long long sst, int nset, long
   const int ncs = NL > 0 ? CWC : nc;
   const int n = nlines * ncs;
   const FastDiv dc(ncs);
+#pragma unroll 1
   for (int i = threadIdx.x; i < n; i += 8 * bd) {
     cx<T> t[8];
 #pragma unroll

@@ -8,7 +8,8 @@ Checked through the C ABI:
   1e-4, in 2D and 3D, with and without a tensile macro strain, over a load /
   unload / reload ramp (both branches of the history max);
 - against central differences (step 1e-6) of the GPU's own FP64 forward at
-  sampled voxels, within 1e-4 relative;
+  32 sampled voxels (28 pores, 4 solid) away from the kinks of the history
+  max and the Macaulay bracket, within 1e-4 relative;
 - the checkpoint interval changes nothing (bit for bit);
 - torch.autograd through the EigenstrainObjective function gives the same
   gradient.
@@ -104,7 +105,11 @@ def test_checkpoint_interval_changes_nothing():
 @pytest.mark.parametrize("kind", ["energy", "damage"])
 def test_adjoint_matches_central_differences_of_the_gpu_forward(kind):
     """81 x 81 carpet, FP64: central differences (step 1e-6) of J from the
-    library's own forward steps at 6 sampled voxels (5 pores, 1 solid)."""
+    library's own forward steps at 32 sampled voxels (28 pores, 4 solid)
+    away from the kinks: at every step the voxel's psi+ differs from H_prev
+    and its elastic-strain trace from zero by at least 1 % of their field
+    scales (the oracle's forward of the same case tells), far more than a
+    1e-6 change of e moves them."""
     phase, e = case(2, 81)
     E = macro(2, True)
     J, g = gpu_grad(phase, e, fm.FFTMECH_FP64, kind, E)
@@ -133,8 +138,15 @@ def test_adjoint_matches_central_differences_of_the_gpu_forward(kind):
 
     assert forward(e) == pytest.approx(J, rel=1e-12)
     rng = np.random.default_rng(17)
-    pores, solid = np.argwhere(phase == 0), np.argwhere(phase == 1)
-    picks = [tuple(p) for p in pores[rng.choice(len(pores), 5, replace=False)]] + [tuple(solid[0])]
+    ok = np.ones(phase.shape, dtype=bool)
+    for st_ in adjoint.forward(phase, e, MAT, H, RAMP, tol=1e-13, eps_mac=E):
+        el = st_["strain"][:2] - st_["e"]
+        tr = el[0] + el[1]
+        ok &= np.abs(st_["psi"] - st_["H_prev"]) > 1e-2 * np.abs(st_["psi"]).max()
+        ok &= np.abs(tr) > 1e-2 * np.abs(tr).max()
+    pores, solid = np.argwhere((phase == 0) & ok), np.argwhere((phase == 1) & ok)
+    picks = [tuple(p) for p in pores[rng.choice(len(pores), 28, replace=False)]] + \
+            [tuple(s) for s in solid[rng.choice(len(solid), 4, replace=False)]]
     scale = np.abs(g).max()
     for idx in picks:
         ep, em = e.copy(), e.copy()
