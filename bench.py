@@ -50,7 +50,8 @@ LAUNCH_MODE = 0  # 0: programmatic dependent launches (the library default); 1: 
 # from one ncu capture (L2 flushed before the launch) of the kernels as they
 # stand; an entry is removed when its kernel changes.
 NCU_TRAFFIC = {
-    # 243^3 sponge, D = 3 (profiles/traffic_sponge243.md)
+    # 243^3 sponge, D = 3 (profiles/traffic_sponge243.md): the three line passes of one iteration
+    ("random-sponge-243^3-eigenstrain-ramp-staggered", "column"): 859.8e6,
     ("random-sponge-243^3-eigenstrain-ramp-staggered", "update"): 1489.0e6,
     ("random-sponge-243^3-eigenstrain-ramp-staggered", "direction"): 468.6e6,
     ("random-sponge-243^3-eigenstrain-ramp-staggered", "stencil"): 391.3e6,
@@ -575,6 +576,42 @@ def adjoint_entry(args, torch, fm, device):
             "grad_l2": float(np.linalg.norm(g)), "grad_finite": bool(np.isfinite(g).all())}
 
 
+def operator_comparison(torch, fm, device, w):
+    """The gradient operators of Sec. 2.6 (Fig. 2) on the headline geometry:
+    homogenised diffusion with grad c_mac = (1, 0), FP64, through
+    fftmech_homogenise_operator. Per operator: PCG iterations, device time,
+    the mean flux, and the ringing of the flux j_x: the mean |second
+    difference along x| over pore voxels whose x neighbours are pores,
+    relative to the mean |j_x| there."""
+    from microstructures.workloads import Materials
+    phase = w.phase
+    mat = Materials()
+    N = phase.size
+    stream = torch.cuda.current_stream(device)
+    ph = torch.as_tensor(phase.ravel()).to(device)
+    gc = torch.zeros(2 * N, dtype=torch.float64, device=device)
+    D = np.where(phase == 0, mat.D_pore, mat.D_solid)
+    pore = phase == 0
+    inner = pore & np.roll(pore, 1, axis=1) & np.roll(pore, -1, axis=1)
+    out = {}
+    for name, op in (("forward", fm.FFTMECH_GRAD_FORWARD), ("central", fm.FFTMECH_GRAD_CENTRAL),
+                     ("central8", fm.FFTMECH_GRAD_CENTRAL8), ("fourier", fm.FFTMECH_GRAD_FOURIER)):
+        ctx = fm.Context(phase.shape, mat, fm.FFTMECH_FP64, h_diff=1.0, tol=1e-10, max_iter=20000,
+                         stream=stream.cuda_stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = fm.fftmech_homogenise_operator(ctx.handle, ph, op, [1.0, 0.0], None, gc)
+        e1.record(stream)
+        e1.synchronize()
+        ctx.close()
+        jx = -D * gc[:N].cpu().numpy().reshape(phase.shape)
+        d2 = np.abs(np.roll(jx, -1, axis=1) - 2 * jx + np.roll(jx, 1, axis=1))
+        out[name] = {"iters": info.iters, "ms": e0.elapsed_time(e1), "mean_flux_x": info.mean_flux[0],
+                     "ringing": float(d2[inner].mean() / np.abs(jx[pore]).mean())}
+    return out
+
+
 def fft_comparison(torch, fm, device, reps=20):
     """Our Stockham transform (fftmech_fft, in place) beside cuFFT
     (torch.fft.fftn) on the same complex64 arrays, CUDA events around each
@@ -701,6 +738,7 @@ def main():
     ap.add_argument("--no-fft", action="store_true", help="skip the cuFFT comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the eigenstrain adjoint timing")
     ap.add_argument("--no-precond", action="store_true", help="skip the reference-medium preconditioner run")
+    ap.add_argument("--no-operators", action="store_true", help="skip the gradient-operator comparison")
     ap.add_argument("--host-driven", action="store_true",
                     help="run the headline steps host-driven (no CUDA graph; for profilers)")
     ap.add_argument("--adjoint-n", type=int, default=2187, help="carpet side of the adjoint timing")
@@ -890,6 +928,8 @@ def main():
         out["adjoint"] = adjoint_entry(args, torch, fm, device)
     if rank == 0 and not args.no_fft:
         out["fft_vs_cufft"] = fft_comparison(torch, fm, device)
+    if rank == 0 and not args.no_operators and w.dim == 2:
+        out["operator_comparison"] = operator_comparison(torch, fm, device, w)
     if cpu is not None:
         out["cpu_baseline"] = cpu
     out["autotune"] = {f"{name} ({'fp64' if prec == fm.FFTMECH_FP64 else 'mixed'})":

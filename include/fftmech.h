@@ -374,6 +374,28 @@ fftmech_status fftmech_adjoint_eigenstrain(fftmech_ctx* ctx, const uint8_t* phas
 fftmech_status fftmech_autotune(fftmech_ctx* ctx, int iterations, double* before_us, double* after_us,
                                 const char** choice);
 
+/* Homogenised RVE diffusion (Sec. 2.1: Eqs. diffusion, diffusion-final,
+ * phi-fft) with a choice of gradient operator (Sec. 2.6, the comparison of
+ * Fig. 2): FFTMECH_GRAD_FORWARD (e^{i theta} - 1) / h, the operator of every
+ * other call; FFTMECH_GRAD_CENTRAL i sin(theta) / h (the garbled printed
+ * formula read as the central difference); FFTMECH_GRAD_CENTRAL8 the
+ * 8th-order central difference (coefficients from the moment conditions:
+ * 4/5, -1/5, 4/105, -1/280); FFTMECH_GRAD_FOURIER i xi (odd grid sizes only:
+ * UNSUPPORTED_SIZE otherwise). The Galerkin system D^H kappa(x) D phi =
+ * -D^H kappa(x) G is solved by PCG on the spectrum of phi with the
+ * preconditioner 1 / |D|^2 (0 where D vanishes), the operator applied by one
+ * inverse and one forward transform of the gradient per iteration. FP64
+ * whatever the context's precision; host-driven; one problem per context;
+ * allocates temporary device buffers. Uses the context's grid, h_diff,
+ * D_pore, D_solid, tol and max_iter. phase: uint8 [N]; grad_c_mac: the macro
+ * gradient; phi: double [N] (zero mean) or NULL; grad_c = G + D phi:
+ * double [dim N] or NULL (device pointers). info: iterations, residual,
+ * mean flux <j> = -<kappa grad c>. */
+enum { FFTMECH_GRAD_FORWARD = 0, FFTMECH_GRAD_CENTRAL = 1, FFTMECH_GRAD_CENTRAL8 = 2, FFTMECH_GRAD_FOURIER = 3 };
+fftmech_status fftmech_homogenise_operator(fftmech_ctx* ctx, const uint8_t* phase, int gradient,
+                                          const double grad_c_mac[3], double* phi, double* grad_c,
+                                          fftmech_solve_info* info);
+
 /* Element offset of problem `problem`'s segment in a field with
  * `components` components per voxel (1 for scalar fields, dim for u, 3 or
  * 6 for strain and stress) of a batched context: problem * components * N. */

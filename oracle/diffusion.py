@@ -46,15 +46,16 @@ def voxel_coordinates(shape, h):
     return out
 
 
-def homogenise(phase, mat, grad_c_mac, c_macro, h, tol=1e-12, max_iter=200000, record=False):
+def homogenise(phase, mat, grad_c_mac, c_macro, h, tol=1e-12, max_iter=200000, record=False, symbol="forward"):
     """Steady RVE diffusion (Eqs. diffusion, diffusion-final, phi-fft,
     psi-two-values, concentration-correct). Returns grad c, phi, c, the mean
-    flux <j> and the CG info."""
+    flux <j> and the CG info. symbol: the gradient operator of Sec. 2.6
+    (forward, central, central8, fourier; the paper's results use forward)."""
     phase = np.asarray(phase)
     shape = phase.shape
     d = phase.ndim
     Dx = diffusivity(phase, mat)
-    Dsym = spectral.forward_difference_symbol(shape, h)
+    Dsym = spectral.SYMBOLS[symbol](shape, h)
     ghat = spectral.projection_operator(Dsym)
     gmac = np.array([grad_c_mac[a] for a in range(d)], dtype=np.float64)
     gradc = np.broadcast_to(gmac.reshape((d,) + (1,) * d), (d,) + shape).copy()

@@ -61,6 +61,32 @@ def fourier_symbol(shape, h):
     return out
 
 
+# Coefficients c_m of the 8th-order central first derivative
+# u'(x) ~ sum_{m=1..4} c_m (u(x + m h) - u(x - m h)) / h: the solution of the
+# moment conditions sum_m 2 m^(2j-1) c_m = delta_{j1}, j = 1..4 (Taylor
+# expansion; the paper names the scheme without printing it, Sec. 2.6).
+def central8_coefficients():
+    A = np.array([[2.0 * m ** (2 * j - 1) for m in range(1, 5)] for j in range(1, 5)])
+    return np.linalg.solve(A, np.array([1.0, 0.0, 0.0, 0.0]))
+
+
+def central_difference_symbol(shape, h):
+    """(u(x + h e_alpha) - u(x - h e_alpha)) / (2 h): symbol i sin(theta) / h
+    (Sec. 2.6, the central difference; read as i sin(xi Delta) / Delta)."""
+    return [np.broadcast_to(1j * np.sin(th) / h, shape).copy() for th in phase_angles(shape)]
+
+
+def central8_symbol(shape, h):
+    """The 8th-order central difference: i sum_m 2 c_m sin(m theta) / h."""
+    c = central8_coefficients()
+    return [np.broadcast_to(1j * sum(2.0 * c[m - 1] * np.sin(m * th) for m in range(1, 5)) / h, shape).copy()
+            for th in phase_angles(shape)]
+
+
+SYMBOLS = {"forward": forward_difference_symbol, "central": central_difference_symbol,
+           "central8": central8_symbol, "fourier": fourier_symbol}
+
+
 def symbol_norm2(D):
     """D . conj(D) = sum_alpha |D_alpha|^2 per mode (denominator of Eq. g-42)."""
     return sum((Da * np.conj(Da)).real for Da in D)

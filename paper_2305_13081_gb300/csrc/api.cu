@@ -1642,6 +1642,230 @@ fftmech_status autotune_impl(fftmech_ctx* ctx, int iterations, double* before_us
 
 }  // namespace
 
+// Unnormalised in-place transform of an nz x ny x nx complex array (x
+// fastest) on `st`: x lines, then the y columns of every plane, then the z
+// columns (the array seen as nz rows of nx ny points). Plans are cached for
+// the process. Enqueues only.
+fftmech_status fft_inplace(int nx, int ny, int nz, bool fp64, bool inverse, void* data, cudaStream_t st) {
+  fftmech_ctx* ctx = nullptr;  // for CK's error path (no message storage)
+  if (!factor_ok(nx) || !factor_ok(ny) || !factor_ok(nz) || nx < 2) return FFTMECH_ERR_UNSUPPORTED_SIZE;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  HostPlan px, py, pz;
+  if (cached_plan(dev, nx, px) != cudaSuccess || cached_plan(dev, ny, py) != cudaSuccess ||
+      cached_plan(dev, nz, pz) != cudaSuccess) {
+    cudaGetLastError();
+    return FFTMECH_ERR_OOM;
+  }
+  const int nsm = prop.multiProcessorCount;
+  const size_t optin = prop.sharedMemPerBlockOptin;
+  Shape2 sh{}, shz{};
+  bool shp = fp64 ? choose_shape_fft<double>(px, py, nsm, optin, sh) : choose_shape_fft<float>(px, py, nsm, optin, sh);
+  if (shp && nz > 1)
+    shp = fp64 ? choose_shape_fft<double>(px, pz, nsm, optin, shz) : choose_shape_fft<float>(px, pz, nsm, optin, shz);
+  if (!shp) return FFTMECH_ERR_UNSUPPORTED_SIZE;
+  sh.batch = nz;  // the y pass runs plane by plane (grid.y = plane)
+  shz.batch = 1;
+  const int inv = inverse ? 1 : 0;
+  auto run = [&](auto zero) -> cudaError_t {
+    using T = decltype(zero);
+    Spec<T> sp{};
+    cudaError_t e = launch_rowfft_f<T>(px.fam, nx, ny * nz, (cx<T>*)data, dev_plan<T>(px), inv, sh, st);
+    if (e == cudaSuccess && ny > 1)
+      e = launch_colpass_f<T>(py.fam, nx, ny, (cx<T>*)data, dev_plan<T>(py), sp, sh, COL_PLAIN, inv, nullptr,
+                              nullptr, nullptr, st);
+    if (e == cudaSuccess && nz > 1)
+      e = launch_colpass_f<T>(pz.fam, nx * ny, nz, (cx<T>*)data, dev_plan<T>(pz), sp, shz, COL_PLAIN, inv, nullptr,
+                              nullptr, nullptr, st);
+    return e;
+  };
+  const cudaError_t e = fp64 ? run(0.0) : run(0.0f);
+  return e == cudaSuccess ? FFTMECH_OK : FFTMECH_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- gradient-operator variants
+// Symbol D(k) of a gradient operator of Sec. 2.6 along an axis of n points
+// (theta = 2 pi k / n): forward (e^{i theta} - 1) / h, central
+// i sin(theta) / h, 8th-order central i sum_m 2 c_m sin(m theta) / h, Fourier
+// i 2 pi k' / (n h) with k' folded to (-n/2, n/2].
+std::vector<cx<double>> grad_symbol(int op, int n, double h) {
+  // 8th-order central coefficients from the moment conditions
+  // sum_m 2 m^(2j - 1) c_m = delta_j1, j = 1 .. 4 (Gaussian elimination)
+  double c8[4] = {0, 0, 0, 0};
+  if (op == FFTMECH_GRAD_CENTRAL8) {
+    double A[4][5];
+    for (int j = 0; j < 4; ++j) {
+      for (int m = 0; m < 4; ++m) A[j][m] = 2.0 * std::pow((double)(m + 1), 2 * j + 1);
+      A[j][4] = j == 0 ? 1.0 : 0.0;
+    }
+    for (int col = 0; col < 4; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < 4; ++r)
+        if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+      for (int k = 0; k < 5; ++k) std::swap(A[col][k], A[piv][k]);
+      for (int r = 0; r < 4; ++r) {
+        if (r == col) continue;
+        const double f = A[r][col] / A[col][col];
+        for (int k = col; k < 5; ++k) A[r][k] -= f * A[col][k];
+      }
+    }
+    for (int m = 0; m < 4; ++m) c8[m] = A[m][4] / A[m][m];
+  }
+  std::vector<cx<double>> d(n);
+  for (int k = 0; k < n; ++k) {
+    const double th = 2.0 * M_PI * k / n;
+    cx<double> v{0.0, 0.0};
+    if (op == FFTMECH_GRAD_FORWARD) {
+      v.re = (std::cos(th) - 1.0) / h;
+      v.im = std::sin(th) / h;
+    } else if (op == FFTMECH_GRAD_CENTRAL) {
+      v.im = std::sin(th) / h;
+    } else if (op == FFTMECH_GRAD_CENTRAL8) {
+      double s = 0.0;
+      for (int m = 0; m < 4; ++m) s += 2.0 * c8[m] * std::sin((m + 1) * th);
+      v.im = s / h;
+    } else {
+      const int kf = k <= n / 2 ? k : k - n;
+      v.im = 2.0 * M_PI * kf / (n * h);
+    }
+    d[k] = v;
+  }
+  return d;
+}
+
+// Homogenised diffusion (Eqs. diffusion, diffusion-final, phi-fft) with the
+// gradient operator `op`: PCG on the spectral vector phi_hat (kernels in
+// variants.cu), the operator applied through one inverse and one forward
+// transform of the gradient per iteration, the preconditioner 1 / |D|^2.
+// FP64; host-driven (the scalars are read every iteration).
+fftmech_status homogenise_operator_impl(fftmech_ctx* ctx, const uint8_t* phase, int op, const double G[3],
+                                        double* phi, double* gradc, fftmech_solve_info* info) {
+  using cxd = cx<double>;
+  cudaStream_t st = ctx->stream;
+  const int nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, dim = ctx->dim;
+  const long long N = ctx->N;
+  const size_t cb = (size_t)N * sizeof(cxd);
+  DevBuffers mem;
+  cxd* P = mem.get<cxd>(cb);
+  cxd* R = mem.get<cxd>(cb);
+  cxd* X = mem.get<cxd>(cb);
+  cxd* Z = mem.get<cxd>(cb);
+  cxd* Q = mem.get<cxd>(cb);
+  cxd* W1 = mem.get<cxd>(cb);
+  cxd* W2 = dim == 3 ? mem.get<cxd>(cb) : nullptr;
+  cxd* dx = mem.get<cxd>((size_t)nx * sizeof(cxd));
+  cxd* dy = mem.get<cxd>((size_t)ny * sizeof(cxd));
+  cxd* dz = mem.get<cxd>((size_t)nz * sizeof(cxd));
+  const int nb = var_dot_blocks(N);
+  double* part = mem.get<double>((size_t)2 * nb * sizeof(double));
+  if (!mem.ok) return set_err(ctx, FFTMECH_ERR_OOM, "operator-variant buffers");
+  const double h = ctx->h_diff;
+  const auto tx = grad_symbol(op, nx, h), ty = grad_symbol(op, ny, h), tz = grad_symbol(op, nz, h);
+  CK(cudaMemcpyAsync(dx, tx.data(), nx * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dy, ty.data(), ny * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dz, tz.data(), nz * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  const VarGrid g{nx, ny, nz, dim, N, dx, dy, dz};
+  const double invN = 1.0 / (double)N;
+  const double kp = ctx->mat.D_pore, ks = ctx->mat.D_solid;
+  const double zero[3] = {0, 0, 0};
+  std::vector<double> hpart(2 * nb);
+  auto fft = [&](cxd* a, bool inv) -> fftmech_status { return fft_inplace(nx, ny, nz, true, inv, a, st); };
+  auto dot = [&](const cxd* a, const cxd* b, double& out) -> fftmech_status {
+    CK(launch_var_dot(N, a, b, part, st));
+    CK(cudaMemcpyAsync(hpart.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out = 0.0;
+    for (int i = 0; i < nb; ++i) out += hpart[i];
+    return FFTMECH_OK;
+  };
+  // q = s D^H F[kappa (F^-1(D p) / N + Gm)]; p = NULL: the gradient is 0
+  auto apply = [&](const cxd* p, cxd* q, const double* Gm, double s) -> fftmech_status {
+    if (p) {
+      CK(launch_var_grad(g, p, W1, W2, st));
+      RC(fft(W1, true));
+      if (W2) RC(fft(W2, true));
+    } else {
+      CK(cudaMemsetAsync(W1, 0, cb, st));
+      if (W2) CK(cudaMemsetAsync(W2, 0, cb, st));
+    }
+    CK(launch_var_flux(g, phase, kp, ks, Gm, invN, W1, W2, st));
+    RC(fft(W1, false));
+    if (W2) RC(fft(W2, false));
+    CK(launch_var_div(g, W1, W2, s, q, st));
+    return FFTMECH_OK;
+  };
+  RC(apply(nullptr, R, G, -1.0));  // f_hat = -D^H F[kappa G]
+  CK(cudaMemsetAsync(X, 0, cb, st));
+  CK(launch_var_precond(g, R, Z, st));
+  CK(cudaMemcpyAsync(P, Z, cb, cudaMemcpyDeviceToDevice, st));
+  double rz = 0.0;
+  RC(dot(R, Z, rz));
+  const double rz0 = rz;
+  const double tol2 = ctx->opts.tol * ctx->opts.tol;
+  int it = 0;
+  fftmech_status status = FFTMECH_OK;
+  while (rz0 > 0.0 && rz > tol2 * rz0) {
+    if (it >= ctx->opts.max_iter) {
+      status = FFTMECH_ERR_NOT_CONVERGED;
+      break;
+    }
+    RC(apply(P, Q, zero, 1.0));
+    double pq = 0.0;
+    RC(dot(P, Q, pq));
+    if (!(pq > 0.0) || !std::isfinite(pq)) {
+      status = FFTMECH_ERR_NONFINITE;
+      break;
+    }
+    const double alpha = rz / pq;
+    CK(launch_var_axpy(N, alpha, P, Q, X, R, st));
+    CK(launch_var_precond(g, R, Z, st));
+    double rzn = 0.0;
+    RC(dot(R, Z, rzn));
+    ++it;
+    CK(launch_var_dir(N, rzn / rz, Z, P, st));
+    rz = rzn;
+  }
+  // phi = F^-1(phi_hat) / N; grad c = G + F^-1(D phi_hat) / N; <j> = -<kappa grad c>
+  CK(cudaMemcpyAsync(W1, X, cb, cudaMemcpyDeviceToDevice, st));
+  RC(fft(W1, true));
+  if (phi) CK(launch_var_real(g, W1, nullptr, invN, phi, nullptr, nullptr, st));
+  CK(launch_var_grad(g, X, W1, W2, st));
+  RC(fft(W1, true));
+  if (W2) RC(fft(W2, true));
+  CK(launch_var_flux(g, phase, 1.0, 1.0, G, invN, W1, W2, st));  // grad c
+  if (gradc)
+    CK(launch_var_real(g, W1, W2, 1.0, gradc, dim >= 2 ? gradc + N : nullptr, dim == 3 ? gradc + 2 * N : nullptr,
+                       st));
+  CK(launch_var_flux(g, phase, kp, ks, zero, 1.0, W1, W2, st));  // kappa grad c
+  double mean[3] = {0, 0, 0};
+  for (int c = 0; c < (dim == 3 ? 2 : 1); ++c) {
+    CK(launch_var_sum(N, c == 0 ? W1 : W2, part, st));
+    CK(cudaMemcpyAsync(hpart.data(), part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      a += hpart[2 * i];
+      b += hpart[2 * i + 1];
+    }
+    if (c == 0) {
+      mean[0] = -a * invN;
+      mean[1] = -b * invN;
+    } else {
+      mean[2] = -a * invN;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  std::memset(info, 0, sizeof(*info));
+  info->status = status;
+  info->iters = it;
+  info->rel_res = rz0 > 0 ? std::sqrt(std::max(rz, 0.0) / rz0) : 0.0;
+  info->true_rel_res = info->rel_res;
+  for (int k = 0; k < dim; ++k) info->mean_flux[k] = mean[k];
+  return status;
+}
+
 // ================================================================ C ABI
 extern "C" {
 
@@ -1935,6 +2159,25 @@ fftmech_status fftmech_adjoint_eigenstrain(fftmech_ctx* ctx, const uint8_t* phas
   return ctx->prec == FFTMECH_FP64
              ? adjoint_impl<double>(ctx, phase, (const double*)e_field, steps, ramp, E, objective, k, grad, J, info_last)
              : adjoint_impl<float>(ctx, phase, (const float*)e_field, steps, ramp, E, objective, k, grad, J, info_last);
+}
+
+fftmech_status fftmech_homogenise_operator(fftmech_ctx* ctx, const uint8_t* phase, int gradient,
+                                          const double grad_c_mac[3], double* phi, double* grad_c,
+                                          fftmech_solve_info* info) {
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  if (!phase || !grad_c_mac || !info) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
+  if (gradient < FFTMECH_GRAD_FORWARD || gradient > FFTMECH_GRAD_FOURIER)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "gradient operator %d", gradient);
+  if (ctx->B != 1) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "one problem per context");
+  for (const void* p : {(const void*)phase, (const void*)phi, (const void*)grad_c})
+    if (p && !is_device_ptr(p)) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "device pointers only");
+  if (gradient == FFTMECH_GRAD_FOURIER && (ctx->nx % 2 == 0 || (ctx->dim >= 2 && ctx->ny % 2 == 0) ||
+                                           (ctx->dim == 3 && ctx->nz % 2 == 0)))
+    return set_err(ctx, FFTMECH_ERR_UNSUPPORTED_SIZE, "the Fourier gradient needs odd grid sizes");
+  double G[3] = {0, 0, 0};
+  for (int k = 0; k < ctx->dim; ++k) G[k] = grad_c_mac[k];
+  return homogenise_operator_impl(ctx, phase, gradient, G, phi, grad_c, info);
 }
 
 fftmech_status fftmech_problem_offset(const fftmech_ctx* ctx, int problem, int components, long long* offset) {
@@ -2452,50 +2695,14 @@ fftmech_status fftmech_profile_read(fftmech_ctx* ctx, int kclass, long long* lau
 
 fftmech_status fftmech_fft(int ndim, const int n[3], int precision, int inverse, void* data,
                            void* stream) {
-  fftmech_ctx* ctx = nullptr;  // for CK's error path (no message storage)
   if (!n || !data || ndim < 1 || ndim > 3) return FFTMECH_ERR_INVALID_ARG;
   if (precision != FFTMECH_FP64 && precision != FFTMECH_MIXED) return FFTMECH_ERR_INVALID_ARG;
-  const int nx = n[0], ny = ndim >= 2 ? n[1] : 1, nz = ndim == 3 ? n[2] : 1;
-  if (!factor_ok(nx) || !factor_ok(ny) || !factor_ok(nz) || nx < 2) return FFTMECH_ERR_UNSUPPORTED_SIZE;
   if (!is_device_ptr(data)) return FFTMECH_ERR_INVALID_ARG;
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  cudaDeviceProp prop;
-  CK(cudaGetDeviceProperties(&prop, dev));
-  HostPlan px, py, pz;
-  if (cached_plan(dev, nx, px) != cudaSuccess || cached_plan(dev, ny, py) != cudaSuccess ||
-      cached_plan(dev, nz, pz) != cudaSuccess) {
-    cudaGetLastError();
-    return FFTMECH_ERR_OOM;
-  }
-  const bool fp64 = precision == FFTMECH_FP64;
-  const int nsm = prop.multiProcessorCount;
-  const size_t optin = prop.sharedMemPerBlockOptin;
-  Shape2 sh{}, shz{};
-  bool shp = fp64 ? choose_shape_fft<double>(px, py, nsm, optin, sh) : choose_shape_fft<float>(px, py, nsm, optin, sh);
-  if (shp && nz > 1)
-    shp = fp64 ? choose_shape_fft<double>(px, pz, nsm, optin, shz) : choose_shape_fft<float>(px, pz, nsm, optin, shz);
-  if (!shp) return FFTMECH_ERR_UNSUPPORTED_SIZE;
-  sh.batch = nz;  // the y pass runs plane by plane (grid.y = plane)
-  shz.batch = 1;
+  const int nx = n[0], ny = ndim >= 2 ? n[1] : 1, nz = ndim == 3 ? n[2] : 1;
   cudaStream_t st = (cudaStream_t)stream;
-  // x lines (all ny nz of them), y columns of every plane, z columns (the
-  // nx ny columns of the array seen as nz rows of nx ny points)
-  auto run = [&](auto zero) -> cudaError_t {
-    using T = decltype(zero);
-    Spec<T> sp{};
-    cudaError_t e = launch_rowfft_f<T>(px.fam, nx, ny * nz, (cx<T>*)data, dev_plan<T>(px), inverse, sh, st);
-    if (e == cudaSuccess && ny > 1)
-      e = launch_colpass_f<T>(py.fam, nx, ny, (cx<T>*)data, dev_plan<T>(py), sp, sh, COL_PLAIN, inverse, nullptr,
-                              nullptr, nullptr, st);
-    if (e == cudaSuccess && nz > 1)
-      e = launch_colpass_f<T>(pz.fam, nx * ny, nz, (cx<T>*)data, dev_plan<T>(pz), sp, shz, COL_PLAIN, inverse, nullptr,
-                              nullptr, nullptr, st);
-    return e;
-  };
-  cudaError_t e = fp64 ? run(0.0) : run(0.0f);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? FFTMECH_OK : FFTMECH_ERR_CUDA;
+  fftmech_status rc = fft_inplace(nx, ny, nz, precision == FFTMECH_FP64, inverse != 0, data, st);
+  if (rc != FFTMECH_OK) return rc;
+  return cudaStreamSynchronize(st) == cudaSuccess ? FFTMECH_OK : FFTMECH_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -499,6 +499,30 @@ cudaError_t launch_col_finalize(const double* pcol, int ncol, SolverScalars* sc,
                                 cudaStream_t st);
 cudaError_t launch_df_merge(long long n, const float* uh, const float* ul, double* u, cudaStream_t st);
 
+// Homogenised diffusion with a chosen gradient operator (variants.cu).
+struct VarGrid {
+  int nx, ny, nz, dim;
+  long long N;
+  const cx<double>* dx;  // gradient symbol along x (nx values), y, z
+  const cx<double>* dy;
+  const cx<double>* dz;
+};
+int var_dot_blocks(long long n);
+cudaError_t launch_var_grad(const VarGrid& g, const cx<double>* P, cx<double>* W1, cx<double>* W2, cudaStream_t st);
+cudaError_t launch_var_flux(const VarGrid& g, const uint8_t* phase, double kp, double ks, const double G[3],
+                            double invN, cx<double>* W1, cx<double>* W2, cudaStream_t st);
+cudaError_t launch_var_div(const VarGrid& g, const cx<double>* Z1, const cx<double>* Z2, double s, cx<double>* Q,
+                           cudaStream_t st);
+cudaError_t launch_var_dot(long long n, const cx<double>* a, const cx<double>* b, double* partials,
+                           cudaStream_t st);
+cudaError_t launch_var_sum(long long n, const cx<double>* w, double* partials, cudaStream_t st);
+cudaError_t launch_var_axpy(long long n, double alpha, const cx<double>* p, const cx<double>* q, cx<double>* x,
+                            cx<double>* r, cudaStream_t st);
+cudaError_t launch_var_precond(const VarGrid& g, const cx<double>* r, cx<double>* z, cudaStream_t st);
+cudaError_t launch_var_dir(long long n, double beta, const cx<double>* z, cx<double>* p, cudaStream_t st);
+cudaError_t launch_var_real(const VarGrid& g, const cx<double>* W1, const cx<double>* W2, double scale, double* gx,
+                            double* gy, double* gz, cudaStream_t st);
+
 // Macroscale bar (bar.cu).
 cudaError_t launch_bar_inputs(int M, double dX, const double* c, double* cbar, double* G, cudaStream_t st);
 cudaError_t launch_bar_update(int M, double dX, double dt, double flux_in, double* c, const double* res, int stride,

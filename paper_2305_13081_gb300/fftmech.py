@@ -37,6 +37,11 @@ FFTMECH_EIG_PRESCRIBED = 1
 # execution of a solve or a staggered step
 FFTMECH_EXEC_GRAPH = 0
 FFTMECH_EXEC_HOST = 1
+# gradient operators (fftmech_homogenise_operator)
+FFTMECH_GRAD_FORWARD = 0
+FFTMECH_GRAD_CENTRAL = 1
+FFTMECH_GRAD_CENTRAL8 = 2
+FFTMECH_GRAD_FOURIER = 3
 # preconditioner of the 2D equilibrium PCG
 FFTMECH_PRECOND_LAPLACE = 0
 FFTMECH_PRECOND_REFERENCE = 1
@@ -153,6 +158,7 @@ def load_library(path=LIB_PATH):
         "fftmech_group_last_error": (ctypes.c_char_p, [vp]),
         "fftmech_staggered_step_many": (i, [P(vp), i, P(P(fftmech_state)), P(P(fftmech_step_params)),
                                             P(P(fftmech_solve_info))]),
+        "fftmech_homogenise_operator": (i, [vp, vp, i, P(d), vp, vp, P(fftmech_solve_info)]),
         "fftmech_bar_create": (i, [P(vp), vp, d, d, d, P(d)]),
         "fftmech_bar_destroy": (i, [vp]),
         "fftmech_bar_step": (i, [vp, P(fftmech_state), P(fftmech_step_params), P(fftmech_solve_info)]),
@@ -429,6 +435,17 @@ def fftmech_group_stats(group):
     b, n, k = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
     _check(load_library().fftmech_group_stats(group, ctypes.byref(b), ctypes.byref(n), ctypes.byref(k)))
     return b.value, n.value, k.value
+
+
+def fftmech_homogenise_operator(ctx, phase, gradient, grad_c_mac, phi=None, grad_c=None):
+    """Homogenised diffusion with the gradient operator `gradient`
+    (FFTMECH_GRAD_*); device buffers; returns the solve record."""
+    info = fftmech_solve_info()
+    g = c_double3(*(list(grad_c_mac) + [0.0] * 3)[:3])
+    rc = load_library().fftmech_homogenise_operator(ctx, ptr(phase), int(gradient), g, ptr(phi), ptr(grad_c),
+                                                    ctypes.byref(info))
+    _check(rc, ctx, _SOLVER_OK)
+    return info
 
 
 def fftmech_bar_create(ctx, length, dt, flux_in, c0=None):

@@ -1,0 +1,81 @@
+"""Pins of the gradient-operator symbols of Sec. 2.6 (oracle/spectral.py) and
+of the oracle's homogenised diffusion with each of them
+(oracle/diffusion.homogenise(symbol=...)):
+
+- each symbol acts in real space as its stencil (np.roll): forward
+  (u(x+h) - u(x))/h, central (u(x+h) - u(x-h))/(2h), 8th-order central
+  sum_m c_m (u(x+mh) - u(x-mh))/h; the Fourier symbol differentiates a
+  resolved sine exactly;
+- the 8th-order coefficients: the textbook values 4/5, -1/5, 4/105, -1/280,
+  and eighth-order convergence on a smooth periodic function;
+- homogenisation of laminates (odd grids): every symbol gives the harmonic
+  mean of D for layers normal to the gradient and the arithmetic mean for
+  layers parallel to it (the flux of a 1D layered problem is constant).
+"""
+
+import numpy as np
+import pytest
+
+from microstructures.workloads import Materials
+from oracle import diffusion, spectral
+
+H = 0.7
+
+
+def apply(D, u):
+    return np.fft.ifftn(D * np.fft.fftn(u)).real
+
+
+def test_symbols_act_as_their_stencils():
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((9, 11))
+    ax = 1  # x
+    fwd = (np.roll(u, -1, ax) - u) / H
+    cen = (np.roll(u, -1, ax) - np.roll(u, 1, ax)) / (2 * H)
+    c = spectral.central8_coefficients()
+    c8 = sum(c[m - 1] * (np.roll(u, -m, ax) - np.roll(u, m, ax)) for m in range(1, 5)) / H
+    assert np.abs(apply(spectral.forward_difference_symbol(u.shape, H)[0], u) - fwd).max() < 1e-12
+    assert np.abs(apply(spectral.central_difference_symbol(u.shape, H)[0], u) - cen).max() < 1e-12
+    assert np.abs(apply(spectral.central8_symbol(u.shape, H)[0], u) - c8).max() < 1e-12
+    # y direction of the central symbol
+    ceny = (np.roll(u, -1, 0) - np.roll(u, 1, 0)) / (2 * H)
+    assert np.abs(apply(spectral.central_difference_symbol(u.shape, H)[1], u) - ceny).max() < 1e-12
+
+
+def test_fourier_symbol_differentiates_a_sine_exactly():
+    n = 15
+    x = H * np.arange(n)
+    L = n * H
+    u = np.tile(np.sin(2 * np.pi * 3 * x / L), (5, 1))
+    du = np.tile(2 * np.pi * 3 / L * np.cos(2 * np.pi * 3 * x / L), (5, 1))
+    assert np.abs(apply(spectral.fourier_symbol(u.shape, H)[0], u) - du).max() < 1e-12
+
+
+def test_central8_coefficients_and_order():
+    c = spectral.central8_coefficients()
+    assert np.allclose(c, [4 / 5, -1 / 5, 4 / 105, -1 / 280], rtol=1e-13)
+    errs = []
+    for n in (32, 64):
+        h = 2 * np.pi / n
+        x = h * np.arange(n)
+        u = np.exp(np.sin(x)).reshape(1, n)
+        du = (np.cos(x) * np.exp(np.sin(x))).reshape(1, n)
+        errs.append(np.abs(apply(spectral.central8_symbol(u.shape, h)[0], u) - du).max())
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > 7.5, (errs, rate)
+
+
+@pytest.mark.parametrize("symbol", ["forward", "central", "central8", "fourier"])
+def test_laminates_give_harmonic_and_arithmetic_means(symbol):
+    mat = Materials()
+    n = 27
+    normal = np.zeros((9, n), dtype=np.uint8)
+    normal[:, 13:] = 1  # the phase varies along x
+    parallel = np.zeros((n, 9), dtype=np.uint8)
+    parallel[13:, :] = 1  # varies along y
+    D_n = np.where(normal[0] == 0, mat.D_pore, mat.D_solid)
+    D_p = np.where(parallel[:, 0] == 0, mat.D_pore, mat.D_solid)
+    out_n = diffusion.homogenise(normal, mat, [1.0, 0.0], 0.3, 1.0, tol=1e-13, symbol=symbol)
+    out_p = diffusion.homogenise(parallel, mat, [1.0, 0.0], 0.3, 1.0, tol=1e-13, symbol=symbol)
+    assert abs(out_n["mean_flux"][0] + 1.0 / np.mean(1.0 / D_n)) <= 1e-9 / np.mean(1.0 / D_n)
+    assert abs(out_p["mean_flux"][0] + np.mean(D_p)) <= 1e-9 * np.mean(D_p)
