@@ -350,13 +350,14 @@ def test_staggered_transient_precipitation(prec):
     c = out["c"].reshape(shape)
     errs = {"c": rel(c, ref["c"]), "eig": rel(out["eig"].reshape(shape), ref["eig"]),
             "strain": rel(out["strain"].reshape((3,) + shape), ref["strain"]),
+            "stress": rel(out["stress"].reshape((3,) + shape), ref["stress"]),
             "damage": rel(out["damage"].reshape(shape), ref["d"])}
     print("staggered transient", prec, errs)
     if prec == fm.FFTMECH_FP64:
         assert max(errs.values()) < 1e-10
     else:
         assert rel(c, ref["c"]) < 1e-6
-        assert rel(out["strain"].reshape((3,) + shape), ref["strain"]) < 1e-5
+        assert errs["strain"] < 1e-5 and errs["stress"] < 1e-5
         assert np.abs(out["damage"].reshape(shape) - ref["d"]).max() < 1e-4
     c_ppt = np.where(phase == 0, np.maximum(c - mat.S_sol, 0), 0)
     assert np.allclose(out["c_ppt"].reshape(shape), c_ppt, atol=1e-6 if prec else 1e-14)
