@@ -243,7 +243,7 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
 template <typename T, int D, int FX, int DIM, int NX>
 __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int L, long long sst) {
   using LL = LineLayout<DIM, D>;
-  const int nx = op.nx;
+  const int nx = NX > 0 ? NX : op.nx;  // a constant with a compile-time plan
   const int nlines = op.ny * op.nz;
   const size_t N = (size_t)nx * nlines;
   const int bp = blockIdx.y;
@@ -432,7 +432,7 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
     cx<T>* Srow = v.S + (size_t)l0 * nxs;
     const FastDiv dns(nxs);
     for (int i = tid; i < nl * nxs; i += bd) {
-      const int l = dns.div(i), k = i - l * nxs;
+      const int l = NX > 0 ? i / nxs : dns.div(i), k = i - l * nxs;
       Srow[i] = k < nxa ? F[(size_t)l * nx + k] : FB[(size_t)l * nx + (k - nxa)];
     }
   }
