@@ -220,3 +220,50 @@ def test_autotuner_keeps_results_and_caches_its_choice(shape, prec):
     assert not desc0.endswith(")")
     assert desc2.endswith("(cached)") and desc2.startswith(desc), (desc, desc2)
     assert (b2, a2) == (before, after)
+
+
+def test_carpet729_transient_workload_graph_equals_host_driven():
+    """The headline workload itself (729^2 random carpet, seed 2305, left-face
+    source, precipitate eigenstrain, tol 1e-8, mixed path): twelve staggered
+    steps as one graph launch each give the fields and iteration counts of
+    the host-driven execution bit for bit, with no host synchronisation
+    inside a step (one graph launch per step, graph path not disabled)."""
+    from microstructures.workloads import carpet_transient
+    w = carpet_transient(729)
+    N = w.phase.size
+    out = {}
+    for ex in (fm.FFTMECH_EXEC_GRAPH, fm.FFTMECH_EXEC_HOST):
+        ctx = fm.Context(w.phase.shape, w.materials, fm.FFTMECH_MIXED, h=w.h, h_diff=w.h_diff, tol=w.tol,
+                         execution=ex)
+        f32 = torch.float32
+        bufs = {k: torch.zeros(m * N, dtype=dt, device="cuda") for k, m, dt in
+                [("c", 1, torch.float64), ("c_ppt", 1, f32), ("eig", 1, f32), ("u", 2, torch.float64),
+                 ("strain", 3, f32), ("stress", 3, f32), ("H", 1, f32), ("damage", 1, torch.float64)]}
+        bufs["phase"] = torch.as_tensor(w.phase.ravel()).cuda()
+        mask = torch.as_tensor(w.dirichlet_mask.ravel()).cuda()
+        st = fm.fftmech_state()
+        for k, v in bufs.items():
+            setattr(st, k, v.data_ptr())
+        p = fm.fftmech_step_params()
+        p.diffusion_mode = fm.FFTMECH_DIFF_TRANSIENT
+        p.dt = w.dt
+        p.dirichlet_mask = mask.data_ptr()
+        p.dirichlet_value = w.dirichlet_value
+        p.eig_mode = fm.FFTMECH_EIG_FROM_PRECIPITATE
+        iters = []
+        for _ in range(12):
+            infos = fm.fftmech_staggered_step(ctx.handle, st, p)
+            iters.append([i.iters for i in infos])
+            assert all(i.status == fm.FFTMECH_OK for i in infos)
+        if ex == fm.FFTMECH_EXEC_GRAPH:
+            builds, launches, _, disabled, why = fm.fftmech_graph_stats(ctx.handle)
+            assert disabled == 0, why
+            assert launches == 12 and builds == 1
+        torch.cuda.synchronize()
+        out[ex] = ({k: v.cpu().numpy() for k, v in bufs.items()}, iters)
+        ctx.close()
+    fg, ig = out[fm.FFTMECH_EXEC_GRAPH]
+    fh, ih = out[fm.FFTMECH_EXEC_HOST]
+    assert ig == ih
+    assert sum(it[1] for it in ig) > 0  # the equilibrium solves ran
+    assert_same(fg, fh)
