@@ -524,6 +524,71 @@ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
   const float h2 = s + l;
   return dfloat{h2, l - (h2 - s)};
 }
+// Numbers of the true residual b - K u (the reliable updates and the
+// final check of the mixed path). The FP64 path computes it in double; the
+// mixed path in double-float: the pair dfloat (h, l) stands for h + l,
+// sums from Knuth's TwoSum, products from an FMA (the
+// exact rounding error of h1 h2), renormalised by FastTwoSum; about 2^-48
+// relative error per operation on the FP32 pipe, where GB300 runs FP64 at
+// a small fraction of that rate. The residual is stored in float, so
+// 2^-48 of |b| leaves it accurate to float precision down to |r| ~ 1e-7 |b|
+// and to 1e-4 relative at |r| ~ 1e-10 |b|.
+__device__ __forceinline__ dfloat df_fast(float s, float e) {
+  const float h = s + e;
+  return dfloat{h, e - (h - s)};
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = ((a.h - (s - bb)) + (b.h - bb)) + (a.l + b.l);
+  return df_fast(s, e);
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat{-a.h, -a.l}; }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+  return df_fast(p, e);
+}
+__device__ __forceinline__ dfloat operator*(dfloat a, float b) {
+  const float p = a.h * b;
+  const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
+  return df_fast(p, e);
+}
+// The residual's number type for a field type T, and its conversions.
+template <typename T>
+struct ResidNum {
+  using type = double;
+};
+template <>
+struct ResidNum<float> {
+  using type = dfloat;
+};
+template <typename RN>
+__device__ __forceinline__ RN rn_c(double x);  // from a double constant
+template <>
+__device__ __forceinline__ double rn_c<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ dfloat rn_c<dfloat>(double x) {
+  const float h = (float)x;
+  return dfloat{h, (float)(x - (double)h)};
+}
+template <typename RN>
+__device__ __forceinline__ RN rn_f(float x);  // from a float (exact)
+template <>
+__device__ __forceinline__ double rn_f<double>(float x) { return (double)x; }
+template <>
+__device__ __forceinline__ dfloat rn_f<dfloat>(float x) { return dfloat{x, 0.f}; }
+// a value of the field type T (double on the FP64 path, float on the mixed)
+template <typename RN, typename T>
+__device__ __forceinline__ RN rn_t(T x) {
+  if constexpr (sizeof(T) == 4) return rn_f<RN>((float)x);
+  else return rn_c<RN>((double)x);
+}
+// rounded to the field type
+__device__ __forceinline__ float rn_out(dfloat a) { return a.h + a.l; }
+__device__ __forceinline__ double rn_out(double a) { return a; }
+
 // Block sum of double-float values, returned in thread 0 (others get a
 // partial). scratch: 64 floats of shared memory.
 __device__ __forceinline__ dfloat block_sum_df2(dfloat v, float* scratch) {

@@ -23,12 +23,16 @@ namespace fftmech {
 #define FFTMECH_BOUNDS(T) __launch_bounds__(512)
 
 // ---------------------------------------------------------------- residual
-// r = b - K u in FP64 (u from the iterate, zero_u: u = 0 except Dirichlet
-// voxels), written as T and row-transformed into S. Shared memory:
-// [max(D (R+2) doubles, 2 R T) per column] + [3 (R+1) doubles per column].
+// r = b - K u in the residual's number type (FP64 path: double; mixed path:
+// double-float, ResidNum) with u from the iterate (zero_u: u = 0 except
+// Dirichlet voxels), written as T and row-transformed into S. Shared memory:
+// [max(D (R+2) numbers, 2 R T) per column] + [3 (R+1) numbers per column]
+// (a number is 8 bytes either way).
 template <typename T, int D, int FX>
 __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int zero_u,
                                              int filter) {
+  using RN = typename ResidNum<T>::type;
+  static_assert(sizeof(RN) == sizeof(double), "the shared-memory layout assumes 8-byte numbers");
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(px.n);
   const FftPlanDev<T> px_s = plan_to_smem(px, reinterpret_cast<cx<T>*>(smem_all));
@@ -42,12 +46,18 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
   const int y0 = blockIdx.x * R;
   const int rows = min(R, ny - y0);
   const int W = rows + 2;
-  const size_t reg0 = (size_t)max(D * (R + 2) * (int)sizeof(double), 2 * R * (int)sizeof(T)) * nx;
-  double* P = reinterpret_cast<double*>(smem);
-  double* SG = reinterpret_cast<double*>(smem + ((reg0 + 15) & ~size_t(15)));
+  const size_t reg0 = (size_t)max(D * (R + 2) * (int)sizeof(RN), 2 * R * (int)sizeof(T)) * nx;
+  RN* P = reinterpret_cast<RN*>(smem);
+  RN* SG = reinterpret_cast<RN*>(smem + ((reg0 + 15) & ~size_t(15)));
   cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   const int SR = (rows + 1) * nx;  // stride of one SG component
-  const double ih = 1.0 / op.h;
+  const RN zero = rn_f<RN>(0.f), one = rn_f<RN>(1.f);
+  const RN ih = rn_c<RN>(1.0 / op.h);
+  const RN E0 = rn_c<RN>(op.E[0]), E1 = rn_c<RN>(op.E[1]), E2 = rn_c<RN>(op.E[2]);
+  const RN LAM[2] = {rn_c<RN>(op.lam[0]), rn_c<RN>(op.lam[1])};
+  const RN MU[2] = {rn_c<RN>(op.mu[0]), rn_c<RN>(op.mu[1])};
+  const RN KAP[2] = {rn_c<RN>(op.kap[0]), rn_c<RN>(op.kap[1])};
+  const RN G0 = rn_c<RN>(D == 1 ? macro_grad(op, bp, 0) : 0.0), G1 = rn_c<RN>(D == 1 ? macro_grad(op, bp, 1) : 0.0);
 
   for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
     const int yy = i / nx, x = i - yy * nx;
@@ -55,10 +65,10 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
     const bool keep = (D == 1) && op.mask && op.mask[gi];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      double val;
-      if constexpr (sizeof(T) == 4) val = (double)v.uh[c * N + gi] + (double)v.ul[c * N + gi];
+      RN val;
+      if constexpr (sizeof(T) == 4) val = RN{v.uh[c * N + gi], v.ul[c * N + gi]};
       else val = v.u[c * N + gi];
-      if (zero_u && !keep) val = 0.0;
+      if (zero_u && !keep) val = zero;
       P[(size_t)c * W * nx + i] = val;
     }
   }
@@ -69,61 +79,62 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
     const size_t gi = (size_t)wrap_y(y0 - 1 + yy, ny) * nx + x;
     const int ph = op.phase[gi] ? 1 : 0;
     if constexpr (D == 2) {
-      const double* Ux = P;
-      const double* Uy = P + (size_t)W * nx;
+      const RN* Ux = P;
+      const RN* Uy = P + (size_t)W * nx;
       const int c0 = yy * nx + x;
-      double exx = (Ux[yy * nx + xp] - Ux[c0]) * ih + op.E[0];
-      double eyy = (Uy[c0 + nx] - Uy[c0]) * ih + op.E[1];
-      const double exy = 0.5 * ((Ux[c0 + nx] - Ux[c0]) + (Uy[yy * nx + xp] - Uy[c0])) * ih + op.E[2];
-      const double e = op.eig ? (double)op.eig[gi] : 0.0;
-      exx -= e;
-      eyy -= e;
-      const double gg = op.g ? (double)op.g[gi] : 1.0;
-      const double lam = gg * op.lam[ph], mu = gg * op.mu[ph];
-      const double tr = exx + eyy;
-      double t0 = 0.0, t1 = 0.0, t2 = 0.0;  // prescribed stress (Voigt xx, yy, xy)
+      RN exx = (Ux[yy * nx + xp] - Ux[c0]) * ih + E0;
+      RN eyy = (Uy[c0 + nx] - Uy[c0]) * ih + E1;
+      const RN exy = (((Ux[c0 + nx] - Ux[c0]) + (Uy[yy * nx + xp] - Uy[c0])) * ih) * 0.5f + E2;
+      const RN e = op.eig ? rn_t<RN>(op.eig[gi]) : zero;
+      exx = exx - e;
+      eyy = eyy - e;
+      const RN gg = op.g ? rn_t<RN>(op.g[gi]) : one;
+      const RN lam = gg * LAM[ph], mu = gg * MU[ph];
+      const RN tr = exx + eyy;
+      RN t0 = zero, t1 = zero, t2 = zero;  // prescribed stress (Voigt xx, yy, xy)
       if (op.pre) {
-        t0 = (double)op.pre[gi];
-        t1 = (double)op.pre[N + gi];
-        t2 = (double)op.pre[2 * N + gi];
+        t0 = rn_t<RN>(op.pre[gi]);
+        t1 = rn_t<RN>(op.pre[N + gi]);
+        t2 = rn_t<RN>(op.pre[2 * N + gi]);
       }
-      SG[i] = lam * tr + 2.0 * mu * exx - t0;
-      SG[SR + i] = lam * tr + 2.0 * mu * eyy - t1;
-      SG[2 * SR + i] = 2.0 * mu * exy - t2;
+      SG[i] = lam * tr + (mu * exx) * 2.0f - t0;
+      SG[SR + i] = lam * tr + (mu * eyy) * 2.0f - t1;
+      SG[2 * SR + i] = (mu * exy) * 2.0f - t2;
     } else {
       const int c0 = yy * nx + x;
-      const double u = P[c0];
-      const double kap = op.kap[ph];
-      SG[i] = kap * ((P[yy * nx + xp] - u) * ih + macro_grad(op, bp, 0));
-      SG[SR + i] = kap * ((P[c0 + nx] - u) * ih + macro_grad(op, bp, 1));
+      const RN u = P[c0];
+      const RN kap = KAP[ph];
+      SG[i] = kap * ((P[yy * nx + xp] - u) * ih + G0);
+      SG[SR + i] = kap * ((P[c0 + nx] - u) * ih + G1);
       SG[2 * SR + i] = u;
     }
   }
   __syncthreads();
+  const RN C0C = rn_c<RN>(op.c0c), SRCS = rn_c<RN>(op.src_scale);
   for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
     const int yr = i / nx, x = i - yr * nx;
     const int yy = yr + 1;
     const int xm = (x == 0) ? nx - 1 : x - 1;
     const size_t gi = (size_t)(y0 + yr) * nx + x;
     const int c = yy * nx + x;
-    double r0, r1 = 0.0;
+    RN r0, r1 = zero;
     if constexpr (D == 2) {
-      const double* Sxx = SG;
-      const double* Syy = SG + SR;
-      const double* Sxy = SG + 2 * SR;
-      r0 = -((Sxx[yy * nx + xm] - Sxx[c]) + (Sxy[c - nx] - Sxy[c])) * ih;
-      r1 = -((Sxy[yy * nx + xm] - Sxy[c]) + (Syy[c - nx] - Syy[c])) * ih;
+      const RN* Sxx = SG;
+      const RN* Syy = SG + SR;
+      const RN* Sxy = SG + 2 * SR;
+      r0 = -(((Sxx[yy * nx + xm] - Sxx[c]) + (Sxy[c - nx] - Sxy[c])) * ih);
+      r1 = -(((Sxy[yy * nx + xm] - Sxy[c]) + (Syy[c - nx] - Syy[c])) * ih);
     } else {
-      const double* Jx = SG;
-      const double* Jy = SG + SR;
-      const double div = ((Jx[yy * nx + xm] - Jx[c]) + (Jy[c - nx] - Jy[c])) * ih;
-      const double u = SG[2 * SR + c];
-      const double c0 = op.c0c + (op.c0f ? (double)op.c0f[gi] : 0.0);
-      const double src = op.srcd ? op.srcd[gi] : (op.srct ? (double)op.srct[gi] : 0.0);
-      r0 = op.src_scale * src - c0 * u - div;
-      if (op.mask && op.mask[gi]) r0 = 0.0;
+      const RN* Jx = SG;
+      const RN* Jy = SG + SR;
+      const RN div = ((Jx[yy * nx + xm] - Jx[c]) + (Jy[c - nx] - Jy[c])) * ih;
+      const RN u = SG[2 * SR + c];
+      const RN c0 = C0C + (op.c0f ? rn_t<RN>(op.c0f[gi]) : zero);
+      const RN src = op.srcd ? rn_c<RN>(op.srcd[gi]) : (op.srct ? rn_t<RN>(op.srct[gi]) : zero);
+      r0 = SRCS * src - c0 * u - div;
+      if (op.mask && op.mask[gi]) r0 = zero;
     }
-    const T t0 = (T)r0, t1 = (T)r1;
+    const T t0 = (T)rn_out(r0), t1 = (T)rn_out(r1);
     v.r[gi] = t0;
     if constexpr (D == 2) v.r[N + gi] = t1;
     F[i] = mk(t0, t1);

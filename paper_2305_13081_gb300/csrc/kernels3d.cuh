@@ -69,13 +69,13 @@ static __device__ __forceinline__ int wrap_z(int z, int nz) { return z < 0 ? z +
 
 // FP64 iterate of plane z (periodic) into ring slot s of P: lines y0 - 1 ..
 // y0 + W - 2 of every component (zero_u: 0 except on Dirichlet voxels).
-template <typename T, int D>
-__device__ __forceinline__ void load_iterate3(double* P, const Op<T>& op, const Vec2<T>& v, int z, int s, int y0,
+template <typename T, int D, typename RN>
+__device__ __forceinline__ void load_iterate3(RN* P, const Op<T>& op, const Vec2<T>& v, int z, int s, int y0,
                                               int W, size_t PS, size_t N, int zero_u) {
   const int nx = op.nx, ny = op.ny, nz = op.nz;
   const size_t plane = (size_t)nx * ny;
   const int zw = wrap_z(z, nz);
-  double* dst = P + (size_t)s * D * PS;
+  RN* dst = P + (size_t)s * D * PS;
   const FastDiv dnx(nx);
   for (int i = threadIdx.x; i < W * nx; i += blockDim.x) {
     const int l = dnx.div(i), x = i - l * nx;
@@ -83,25 +83,29 @@ __device__ __forceinline__ void load_iterate3(double* P, const Op<T>& op, const 
     const bool keep = (D == 1) && op.mask && op.mask[gi];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      double val;
-      if constexpr (sizeof(T) == 4) val = (double)v.uh[c * N + gi] + (double)v.ul[c * N + gi];
+      RN val;
+      if constexpr (sizeof(T) == 4) val = RN{v.uh[c * N + gi], v.ul[c * N + gi]};
       else val = v.u[c * N + gi];
-      if (zero_u && !keep) val = 0.0;
+      if (zero_u && !keep) val = rn_f<RN>(0.f);
       dst[c * PS + i] = val;
     }
   }
 }
 
 // ---------------------------------------------------------------- residual
-// r = b - K u in FP64 from the iterate (zero_u: u = 0 except on Dirichlet
-// voxels; filter: only problems with a nonzero mode), written as T; S =
-// x-FFT(r). Bricks of R lines march through Zc planes keeping two planes of
-// the iterate and of the z-differenced stress (or flux) components; plane
-// zz = z0 - 1 is the halo (its z-differenced components only).
+// r = b - K u in the residual's number type (FP64 path: double; mixed path:
+// double-float, ResidNum) from the iterate (zero_u: u = 0 except on
+// Dirichlet voxels; filter: only problems with a nonzero mode), written as
+// T; S = x-FFT(r). Bricks of R lines march through Zc planes keeping two
+// planes of the iterate and of the z-differenced stress (or flux)
+// components; plane zz = z0 - 1 is the halo (its z-differenced components
+// only).
 template <typename T, int D, int FX>
 __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> px, int R, int Zc, long long sst,
                                             int zero_u, int filter) {
   using C = Comp3<D>;
+  using RN = typename ResidNum<T>::type;
+  static_assert(sizeof(RN) == 8, "the shared-memory layout assumes 8-byte numbers");
   const int nx = op.nx, ny = op.ny, nz = op.nz;
   const size_t plane = (size_t)nx * ny;
   const size_t N = plane * nz;
@@ -119,10 +123,10 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
   const int z0 = tz * Zc, planes = min(Zc, nz - z0);
   const int tid = threadIdx.x, bd = blockDim.x;
   const int nxa = D == 3 ? nx : 0, nxh = nx / 2 + 1, nxs = nxa + nxh;
-  const Row3Layout L(nx, R, (int)sizeof(double), (int)sizeof(T), D);
-  double* P = reinterpret_cast<double*>(smem + L.P);
-  double* SP = reinterpret_cast<double*>(smem + L.SP);
-  double* SZ = reinterpret_cast<double*>(smem + L.SZ);
+  const Row3Layout L(nx, R, (int)sizeof(RN), (int)sizeof(T), D);
+  RN* P = reinterpret_cast<RN*>(smem + L.P);
+  RN* SP = reinterpret_cast<RN*>(smem + L.SP);
+  RN* SZ = reinterpret_cast<RN*>(smem + L.SZ);
   cx<T>* F = reinterpret_cast<cx<T>*>(smem + L.F);
   T* MG = reinterpret_cast<T*>(smem + L.MG);
   uint8_t* PH = smem + L.PH;
@@ -130,7 +134,15 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
   const size_t PS = (size_t)(R + 2) * nx;   // one component of one P slot
   const size_t SS = (size_t)(R + 1) * nx;   // one stress component of one plane
   const T* matg = (D == 3) ? op.g : op.c0f;
-  const double ih = 1.0 / op.h;
+  const RN zero = rn_f<RN>(0.f), one = rn_f<RN>(1.f);
+  const RN ih = rn_c<RN>(1.0 / op.h);
+  RN E[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) E[k] = rn_c<RN>(D == 3 ? op.E[k] : macro_grad(op, bp, k < 3 ? k : 0));
+  const RN LAM[2] = {rn_c<RN>(op.lam[0]), rn_c<RN>(op.lam[1])};
+  const RN MU[2] = {rn_c<RN>(op.mu[0]), rn_c<RN>(op.mu[1])};
+  const RN KAP[2] = {rn_c<RN>(op.kap[0]), rn_c<RN>(op.kap[1])};
+  const RN C0C = rn_c<RN>(op.c0c), SRCS = rn_c<RN>(op.src_scale);
   const FastDiv dnx(nx);
 
   load_iterate3<T, D>(P, op, v, z0 - 1, 0, y0, W, PS, N, zero_u);
@@ -143,10 +155,10 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
     if (matg) g2s_rows<4>(MG, matg + pz, y0 - 1, rows + 1, nx, ny);
     g2s_rows<4>(PH, op.phase + pz, y0 - 1, rows + 1, nx, ny);
     __syncthreads();
-    const double* Pc = P + (size_t)cur * D * PS;
-    const double* Pn = P + (size_t)nxt * D * PS;
-    double* Zc_ = SZ + (size_t)cur * C::NZ * SS;
-    const double* Zp = SZ + (size_t)nxt * C::NZ * SS;  // previous plane (same slot parity as the next)
+    const RN* Pc = P + (size_t)cur * D * PS;
+    const RN* Pn = P + (size_t)nxt * D * PS;
+    RN* Zc_ = SZ + (size_t)cur * C::NZ * SS;
+    const RN* Zp = SZ + (size_t)nxt * C::NZ * SS;  // previous plane (same slot parity as the next)
     // stress / flux of plane zz at lines y0 - 1 .. y0 + rows - 1
     for (int i = tid; i < (rows + 1) * nx; i += bd) {
       const int l = dnx.div(i), x = i - l * nx;
@@ -154,26 +166,26 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
       const int ix = l * nx + xp;
       const int ph = PH[i] != 0 ? 1 : 0;
       if constexpr (D == 3) {
-        const double* Ux = Pc;
-        const double* Uy = Pc + PS;
-        const double* Uz = Pc + 2 * PS;
-        const double ux = Ux[i], uy = Uy[i], uz = Uz[i];
+        const RN* Ux = Pc;
+        const RN* Uy = Pc + PS;
+        const RN* Uz = Pc + 2 * PS;
+        const RN ux = Ux[i], uy = Uy[i], uz = Uz[i];
         const size_t gi = pz + (size_t)wrap_y(y0 - 1 + l, ny) * nx + x;
-        const double e = op.eig ? (double)op.eig[gi] : 0.0;
-        const double exx = (Ux[ix] - ux) * ih + op.E[0] - e;
-        const double eyy = (Uy[i + nx] - uy) * ih + op.E[1] - e;
-        const double ezz = (Pn[2 * PS + i] - uz) * ih + op.E[2] - e;
-        const double eyz = 0.5 * ((Pn[PS + i] - uy) + (Uz[i + nx] - uz)) * ih + op.E[3];
-        const double exz = 0.5 * ((Pn[i] - ux) + (Uz[ix] - uz)) * ih + op.E[4];
-        const double exy = 0.5 * ((Ux[i + nx] - ux) + (Uy[ix] - uy)) * ih + op.E[5];
-        const double gg = matg ? (double)MG[i] : 1.0;
-        const double lam = gg * op.lam[ph], mu = gg * op.mu[ph];
-        const double lt = lam * (exx + eyy + ezz);
-        const double m2 = 2.0 * mu;
-        double t[6] = {0, 0, 0, 0, 0, 0};  // prescribed stress (Voigt xx, yy, zz, yz, xz, xy)
+        const RN e = op.eig ? rn_t<RN>(op.eig[gi]) : zero;
+        const RN exx = (Ux[ix] - ux) * ih + E[0] - e;
+        const RN eyy = (Uy[i + nx] - uy) * ih + E[1] - e;
+        const RN ezz = (Pn[2 * PS + i] - uz) * ih + E[2] - e;
+        const RN eyz = (((Pn[PS + i] - uy) + (Uz[i + nx] - uz)) * ih) * 0.5f + E[3];
+        const RN exz = (((Pn[i] - ux) + (Uz[ix] - uz)) * ih) * 0.5f + E[4];
+        const RN exy = (((Ux[i + nx] - ux) + (Uy[ix] - uy)) * ih) * 0.5f + E[5];
+        const RN gg = matg ? rn_t<RN>(MG[i]) : one;
+        const RN lam = gg * LAM[ph], mu = gg * MU[ph];
+        const RN lt = lam * ((exx + eyy) + ezz);
+        const RN m2 = mu * 2.0f;
+        RN t[6] = {zero, zero, zero, zero, zero, zero};  // prescribed stress (Voigt xx, yy, zz, yz, xz, xy)
         if (op.pre) {
 #pragma unroll
-          for (int k = 0; k < 6; ++k) t[k] = (double)op.pre[k * N + gi];
+          for (int k = 0; k < 6; ++k) t[k] = rn_t<RN>(op.pre[k * N + gi]);
         }
         if (inner) {
           SP[i] = lt + m2 * exx - t[0];
@@ -184,11 +196,11 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
         Zc_[SS + i] = m2 * eyz - t[3];
         Zc_[2 * SS + i] = lt + m2 * ezz - t[2];
       } else {
-        const double p = Pc[i];
-        const double kap = op.kap[ph];
-        const double gx = (Pc[ix] - p) * ih + macro_grad(op, bp, 0);
-        const double gy = (Pc[i + nx] - p) * ih + macro_grad(op, bp, 1);
-        const double gz = (Pn[i] - p) * ih + macro_grad(op, bp, 2);
+        const RN p = Pc[i];
+        const RN kap = KAP[ph];
+        const RN gx = (Pc[ix] - p) * ih + E[0];
+        const RN gy = (Pc[i + nx] - p) * ih + E[1];
+        const RN gz = (Pn[i] - p) * ih + E[2];
         if (inner) {
           SP[i] = kap * gx;
           SP[SS + i] = kap * gy;
@@ -206,29 +218,29 @@ __global__ void FFTMECH_BOUNDS3 k3_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> p
       const int c = l * nx + x, cxm = l * nx + xm;
       const size_t gi = pz + (size_t)(y0 + lr) * nx + x;
       if constexpr (D == 3) {
-        const double* Sxx = SP;
-        const double* Syy = SP + SS;
-        const double* Sxy = SP + 2 * SS;
-        const double* Sxz = Zc_;
-        const double* Syz = Zc_ + SS;
-        const double* Szz = Zc_ + 2 * SS;
-        const T r0 = (T)(-((Sxx[cxm] - Sxx[c]) + (Sxy[c - nx] - Sxy[c]) + (Zp[c] - Sxz[c])) * ih);
-        const T r1 = (T)(-((Sxy[cxm] - Sxy[c]) + (Syy[c - nx] - Syy[c]) + (Zp[SS + c] - Syz[c])) * ih);
-        const T r2 = (T)(-((Sxz[cxm] - Sxz[c]) + (Syz[c - nx] - Syz[c]) + (Zp[2 * SS + c] - Szz[c])) * ih);
+        const RN* Sxx = SP;
+        const RN* Syy = SP + SS;
+        const RN* Sxy = SP + 2 * SS;
+        const RN* Sxz = Zc_;
+        const RN* Syz = Zc_ + SS;
+        const RN* Szz = Zc_ + 2 * SS;
+        const T r0 = (T)rn_out(-((((Sxx[cxm] - Sxx[c]) + (Sxy[c - nx] - Sxy[c])) + (Zp[c] - Sxz[c])) * ih));
+        const T r1 = (T)rn_out(-((((Sxy[cxm] - Sxy[c]) + (Syy[c - nx] - Syy[c])) + (Zp[SS + c] - Syz[c])) * ih));
+        const T r2 = (T)rn_out(-((((Sxz[cxm] - Sxz[c]) + (Syz[c - nx] - Syz[c])) + (Zp[2 * SS + c] - Szz[c])) * ih));
         v.r[gi] = r0;
         v.r[N + gi] = r1;
         v.r[2 * N + gi] = r2;
         F[i] = mk(r0, r1);
         F[(size_t)rows * nx + i] = mk(r2, T(0));
       } else {
-        const double* Jx = SP;
-        const double* Jy = SP + SS;
-        const double div = ((Jx[cxm] - Jx[c]) + (Jy[c - nx] - Jy[c]) + (Zp[c] - Zc_[c])) * ih;
-        const double c0v = op.c0c + (matg ? (double)MG[c] : 0.0);
-        const double src = op.srcd ? op.srcd[gi] : (op.srct ? (double)op.srct[gi] : 0.0);
-        double rr = op.src_scale * src - c0v * Pc[c] - div;
-        if (op.mask && op.mask[gi]) rr = 0.0;
-        const T r0 = (T)rr;
+        const RN* Jx = SP;
+        const RN* Jy = SP + SS;
+        const RN div = (((Jx[cxm] - Jx[c]) + (Jy[c - nx] - Jy[c])) + (Zp[c] - Zc_[c])) * ih;
+        const RN c0v = C0C + (matg ? rn_t<RN>(MG[c]) : zero);
+        const RN src = op.srcd ? rn_c<RN>(op.srcd[gi]) : (op.srct ? rn_t<RN>(op.srct[gi]) : zero);
+        RN rr = SRCS * src - c0v * Pc[c] - div;
+        if (op.mask && op.mask[gi]) rr = zero;
+        const T r0 = (T)rn_out(rr);
         v.r[gi] = r0;
         F[i] = mk(r0, T(0));
       }
