@@ -45,7 +45,14 @@ N_SIDE = 729
 SEED = 2305
 TOTAL_STEPS = 200
 L2_FLUSH_BYTES = 512 << 20
-LAUNCH_MODE = 0  # 0: programmatic dependent launches (the library default); 1: plain stream order
+LAUNCH_MODE = 0  # bit 0: plain stream order instead of programmatic dependent launches;
+# bit 1: fused direction-stencil kernel on latency-bound 2D grids (fftmech_autotune's choice replaces it)
+
+
+def fused_ds(prof, dim):
+    """Whether a profiled 2D run used the fused direction-stencil kernel:
+    its iterations launched no separate stencil kernel."""
+    return dim == 2 and prof["stencil"][0] == 0 and prof["direction"][0] > 0
 # DRAM bytes (read + write) per launch of a workload's dominant kernel class,
 # from one ncu capture (L2 flushed before the launch) of the kernels as they
 # stand; an entry is removed when its kernel changes.
@@ -173,11 +180,14 @@ def kernel_bytes(kind, cls, s, dim=2, variant="full"):
     raise ValueError(cls)
 
 
-def class_bytes(infos_per_step, N, s, dim=2):
+def class_bytes(infos_per_step, N, s, dim=2, fused=False):
     """Total algorithmic bytes per kernel class over the timed steps. The few
     reliable-update iterations (2-4 per solve) run a lighter u-only update;
     they are counted as full updates (an overcount below 1 %). 3D runs three
-    line passes per iteration (y, z with the multiplier, y inverse)."""
+    line passes per iteration (y, z with the multiplier, y inverse). fused:
+    the direction class is the fused direction-stencil kernel (the bytes of
+    both but the stencil's read of p, which stays on chip) and the update
+    kernel also writes p back for the next direction."""
     tot = {"direction": 0.0, "stencil": 0.0, "update": 0.0, "column": 0.0}
     kinds = ["diffusion", "elastic", "phasefield"]
     passes = 1 if dim == 2 else 3
@@ -185,9 +195,15 @@ def class_bytes(infos_per_step, N, s, dim=2):
         for idx, info in enumerate(infos):
             kind = kinds[idx % 3]
             it = info["iters"]
-            tot["direction"] += N * it * kernel_bytes(kind, "direction", s, dim)
-            tot["stencil"] += N * it * kernel_bytes(kind, "stencil", s, dim)
-            tot["update"] += N * it * kernel_bytes(kind, "update", s, dim)
+            D = dim if kind == "elastic" else 1
+            if fused:
+                tot["direction"] += N * it * (kernel_bytes(kind, "direction", s, dim)
+                                              + kernel_bytes(kind, "stencil", s, dim) - D * s)
+                tot["update"] += N * it * (kernel_bytes(kind, "update", s, dim) + D * s)
+            else:
+                tot["direction"] += N * it * kernel_bytes(kind, "direction", s, dim)
+                tot["stencil"] += N * it * kernel_bytes(kind, "stencil", s, dim)
+                tot["update"] += N * it * kernel_bytes(kind, "update", s, dim)
             tot["column"] += N * (it + 2) * passes * kernel_bytes(kind, "column", s, dim)
     return tot
 
@@ -308,7 +324,7 @@ def vi_of(run, Np):
 def roofline_of(prof_run, Np, s, dim, hbm_peak, peak_src, name, unprofiled_ms_per_step, note):
     """Dominant kernel class of a profiled run: algorithmic bytes over its
     event-timed duration, against the measured copy peak."""
-    cb = class_bytes(prof_run["infos"], Np, s, dim)
+    cb = class_bytes(prof_run["infos"], Np, s, dim, fused_ds(prof_run["prof"], dim))
     kernels = {}
     for cls in ("direction", "stencil", "update", "column"):
         n, ms = prof_run["prof"][cls]
@@ -467,7 +483,7 @@ def uneven_batch_entry(args, torch, fm, device, rank, flush, hbm_peak, peak_src)
     # per-class roofline of the one-step profile (contexts alone, sequential)
     tot = {"direction": 0.0, "stencil": 0.0, "update": 0.0, "column": 0.0}
     for nv, recs in run["prof_infos"]:
-        cb = class_bytes([recs], nv, 4, 2)
+        cb = class_bytes([recs], nv, 4, 2, fused_ds(run["prof"], 2))
         for k in tot:
             tot[k] += cb[k]
     kernels = {}
@@ -756,11 +772,14 @@ def main():
     ap.add_argument("--plain-launches", action="store_true",
                     help="launch the PCG kernels in plain stream order instead of as programmatic "
                          "dependent launches (for comparison)")
+    ap.add_argument("--fuse-direction-stencil", action="store_true",
+                    help="ask for the fused direction-stencil kernel on 2D grids (an autotuned context makes "
+                         "its own choice)")
     ap.add_argument("--n", type=int, default=None,
                     help="grid side (3^k); defaults 729 (carpet) and 243 (sponge)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    LAUNCH_MODE = 1 if args.plain_launches else 0
+    LAUNCH_MODE = (1 if args.plain_launches else 0) | (2 if args.fuse_direction_stencil else 0)
     AUTOTUNE_ITERS = args.autotune
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -863,7 +882,8 @@ def main():
                    "parallelism": f"{world} independent RVE replicas",
                    "execution": ("host-driven loops (flags read after every iteration)" if args.host_driven
                                  else "one CUDA graph per staggered step (device-driven loops)"),
-                   "launches": "plain stream order" if LAUNCH_MODE else "programmatic dependent"},
+                   "launches": "plain stream order" if LAUNCH_MODE & 1 else "programmatic dependent",
+                   "direction_stencil": ("fused" if fused_ds(prof_run["prof"], w.dim) else "split")},
         "breakdown": breakdown,
         "kernels": kernels,
         "roofline": roofline,

@@ -113,8 +113,11 @@ typedef struct {
  * replace_residual (MIXED only, 0/1): reliable updates; after every 16th
  * iteration the device checks whether r.M^-1 r has fallen 100-fold since
  * the last replacement and, if so, replaces the float recursive residual by
- * the FP64 true residual b - K u in the next iteration (search direction
- * kept; the problems of a batch due at that point are replaced together). After convergence of the float recursion the FP64 true residual is
+ * the true residual b - K u in the next iteration (search direction kept;
+ * the problems of a batch due at that point are replaced together). The
+ * true residual is evaluated in double-float arithmetic (about 2^-48
+ * relative per operation) from the double-float iterate. After
+ * convergence of the float recursion the true residual is
  * checked; a problem whose true residual misses tol continues from it (at
  * most three times).
  * Every decision of the loop is taken on the device. execution:
@@ -125,10 +128,14 @@ typedef struct {
  * the host driving the loops, reading the device's decisions after every
  * iteration (slower; used with per-launch profiling). Both give
  * bit-identical results. check_every is not used (kept for the layout).
- * launch_mode: 0 (default) launches the kernels of a PCG iteration as
- * programmatic dependent launches (each kernel starts launching while the
- * previous one finishes and waits on the device for its results); 1 uses
- * plain stream order. Both give bit-identical results.
+ * launch_mode: bit 0 clear (default) launches the kernels of a PCG
+ * iteration as programmatic dependent launches (each kernel starts
+ * launching while the previous one finishes and waits on the device for
+ * its results), set uses plain stream order (bit-identical results). Bit 1
+ * set runs, on 2D grids of up to 2^21 voxels per launch, the direction and
+ * the next iteration's stencil as one kernel (the same iterates up to the
+ * summation order of <p, K p>); clear (default) keeps them apart.
+ * fftmech_autotune times both and its choice then replaces bit 1.
  * precond: preconditioner of the 2D equilibrium PCG. FFTMECH_PRECOND_LAPLACE
  * (0, default): F^-1 (1 / |D|^2) F per component, the projection of App. A
  * (Eq. g-42). FFTMECH_PRECOND_REFERENCE (1): the inverse of the Galerkin
@@ -360,8 +367,10 @@ fftmech_status fftmech_adjoint_eigenstrain(fftmech_ctx* ctx, const uint8_t* phas
  * equilibrium PCG iterations on a synthetic two-phase field of the
  * context's grid and batch (graph execution, best of two runs per
  * candidate) for candidate launch shapes: column strip width and stencil
- * strip rows (2D), stencil brick depth (3D), stencil blocks per problem and
- * lines per block of the x-line kernels, one parameter at a time from the
+ * strip rows (2D), stencil brick depth (3D), stencil blocks per problem,
+ * lines per block of the x-line kernels and, on 2D grids of up to 2^21
+ * voxels per launch, split or fused direction and stencil kernels (with
+ * the fused kernel's rows per block), one parameter at a time from the
  * best so far. Applies the fastest and keeps it for the process: a later
  * call on another context of the same device, grid, batch and precision
  * applies it without timing (the description then ends in "(cached)"; the
@@ -484,10 +493,10 @@ fftmech_status fftmech_bar_write(fftmech_bar* bar, const double* c_host);
  * CUDA events on the context's stream and its duration accumulated; launch
  * counts are kept whether or not profiling is on. */
 enum {
-  FFTMECH_K_DIRECTION = 0, /* x-line IFFT + new search direction */
+  FFTMECH_K_DIRECTION = 0, /* x-line IFFT + new search direction (2D fused: + q = K p) */
   FFTMECH_K_UPDATE = 1,    /* iterate / residual update + x-line FFT */
   FFTMECH_K_COLUMN = 2,    /* y (and z) line FFTs, Fourier multiplier, <r, M^-1 r>, inverse */
-  FFTMECH_K_RESIDUAL = 3,  /* FP64 true residual + x-line FFT */
+  FFTMECH_K_RESIDUAL = 3,  /* true residual + x-line FFT */
   FFTMECH_K_OTHER = 4,     /* pointwise and post-processing kernels */
   FFTMECH_K_STENCIL = 5,   /* q = K p and <p, K p> (stencil tiles) */
   FFTMECH_K_COUNT = 6

@@ -153,6 +153,12 @@ struct fftmech_ctx {
   // workspace (B problems back to back)
   void* r = nullptr;
   void* p = nullptr;     // search direction (updated in place by the direction kernel)
+  void* pn = nullptr;    // 2D: the new direction of the fused direction-stencil kernel
+  // fused direction-stencil kernel: -1 as launch_mode bit 1 asks, 0 split,
+  // 1 fused (fftmech_autotune's choice); ds_rule: its rows per block by the
+  // host's rule (0: no fused kernel on this grid)
+  int ds_choice = -1;
+  int ds_rule = 0;
   void* S = nullptr;
   void* q = nullptr;     // K p of the split iteration
   void* g = nullptr;
@@ -537,6 +543,13 @@ fftmech_status poll_flags(Emit& em, int* out) {
   return FFTMECH_OK;
 }
 
+// Whether a 2D solve may run the fused direction-stencil kernel (the grid
+// has one, and launch_mode bit 1 or fftmech_autotune chose it).
+inline bool ds_active(const fftmech_ctx* ctx) {
+  if (ctx->lshape.L_ds <= 0) return false;
+  return ctx->ds_choice < 0 ? (ctx->opts.launch_mode & 2) != 0 : ctx->ds_choice == 1;
+}
+
 // ---------------------------------------------------------------- PCG
 // Preconditioned CG on the potential for every problem of the batch.
 // Launch sequence (graph form; the host-driven form runs the same launches
@@ -549,20 +562,24 @@ fftmech_status poll_flags(Emit& em, int* out) {
 //       stencil (q = K p, <p, K p>), update (u += alpha p, r -= alpha q,
 //       x-FFT), column pass (multiplier, <r, M^-1 r>), direction
 //     IF LF_REPLACE (reliable update): stencil, update of the iterate only,
-//       FP64 true residual, column pass, direction
-//     IF LF_GATE: FP64 true residual of the problems that stopped unchecked
+//       true residual, column pass, direction
+//     IF LF_GATE: true residual of the problems that stopped unchecked
 //     restart gate
 //     IF LF_RESTART: restart from the true residual, first direction
 //   [MIXED: iterate merge]
 // An ordinary iteration has no conditional node inside it, so its kernels
-// stay chained by programmatic dependent launches.
+// stay chained by programmatic dependent launches. Where the 2D iteration
+// is latency-bound the direction and the next iteration's stencil are one
+// kernel: an iteration is then update, column pass, direction-stencil.
+// The true residual is FP64 on the FP64 path and double-float on the mixed
+// one.
 // Every decision (convergence, iteration limit, reliable update, restart) is
 // taken on the device; a problem that has stopped makes every kernel return
 // at once while the others continue.
 template <typename T, int D>
 fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& sp_in) {
   fftmech_ctx* ctx = em.ctx;
-  const DepLaunchScope dep(ctx->opts.launch_mode == 0);
+  const DepLaunchScope dep((ctx->opts.launch_mode & 1) == 0);
   const int B = ctx->B;
   FftPlanDev<T> px = dev_plan<T>(ctx->px), py = dev_plan<T>(ctx->py), pz = dev_plan<T>(ctx->pz);
   Spec<T> sp = sp_in;
@@ -607,6 +624,11 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
   // re-reading all partials costs more than the ticket saves.
   const bool small = (long long)ctx->N * B <= (1LL << 21);
   const bool defer = small && !three;
+  // there the direction and the stencil can run as one kernel
+  // (launch_mode bit 1, or fftmech_autotune's choice): it writes the new
+  // direction to pn, and the update kernel, which reads it, copies it back
+  // to p for the next direction
+  const bool fused = defer && ds_active(ctx);
   // reference-medium preconditioner: 2D elasticity only
   const bool ms = D == 2 && !three && ctx->opts.precond == FFTMECH_PRECOND_REFERENCE && ctx->ms_cw > 0;
   if (ms) {
@@ -619,6 +641,7 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
                                  : (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;
   v.nsten = !small ? 0
             : three ? sten3_blocks(ctx->nx, ctx->ny, ctx->nz, ctx->sshape)
+            : fused ? (ctx->ny + ctx->lshape.L_ds - 1) / ctx->lshape.L_ds
                     : sten2_blocks(ctx->nx, ctx->ny, ctx->sshape);
   const long long nU = (long long)D * ctx->N * B;
   const bool mixed = sizeof(T) == 4;
@@ -636,6 +659,12 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
                    : launch_residual_f<T, 1>(fx, op, v, px, sh, zero_u, filter, st);
   };
   auto direction = [&](const Vec2<T>& va, cudaStream_t st) -> cudaError_t {
+    if (fused) {
+      Vec2<T> vf = va;
+      vf.p_out = (T*)ctx->pn;
+      if constexpr (D == 2) return launch_xds_f<T, 2>(fx, op, vf, px, lsh, st);
+      else if constexpr (D == 1) return launch_xds_f<T, 1>(fx, op, vf, px, lsh, st);
+    }
     if constexpr (D == 3) return launch_xdir_f<T, 3, 3>(fx, op, va, px, lsh, st);
     else if constexpr (D == 2) return launch_xdir_f<T, 2, 2>(fx, op, va, px, lsh, st);
     else
@@ -646,7 +675,12 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
     else if constexpr (D == 2) return launch_sten2<T, 2>(op, vs, ssh, st);
     else return three ? launch_sten3<T, 1>(op, vs, ssh, st) : launch_sten2<T, 1>(op, vs, ssh, st);
   };
-  auto update = [&](const Vec2<T>& vu, cudaStream_t st) -> cudaError_t {
+  auto update = [&](const Vec2<T>& vu_in, cudaStream_t st) -> cudaError_t {
+    Vec2<T> vu = vu_in;
+    if (fused) {
+      vu.p_in = (const T*)ctx->pn;
+      vu.p_copy = (T*)ctx->p;
+    }
     if constexpr (D == 3) return launch_xupd_f<T, 3, 3>(fx, op, vu, px, lsh, st);
     else if constexpr (D == 2) return launch_xupd_f<T, 2, 2>(fx, op, vu, px, lsh, st);
     else
@@ -695,7 +729,7 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
   auto iteration = [&](Emit& e, bool plain) -> fftmech_status {
     Vec2<T> vi = v;
     vi.ctl = e.ctl;
-    EM_LAUNCH(e, FFTMECH_K_STENCIL, stencil(vi, e.st));
+    if (!fused) EM_LAUNCH(e, FFTMECH_K_STENCIL, stencil(vi, e.st));
     EM_LAUNCH(e, FFTMECH_K_UPDATE, update(vi, e.st));
     if (!plain) EM_LAUNCH(e, FFTMECH_K_RESIDUAL, residual(0, 1, e.st));
     EM_LAUNCH(e, FFTMECH_K_COLUMN, colpass(defer ? (COL_ITER | COL_DEFER) : COL_ITER, e.st));
@@ -1152,7 +1186,7 @@ void count_graph_kernels(fftmech_ctx* ctx) {
 }
 
 bool opts_ok(const fftmech_solver_opts* o) {
-  return o->tol >= 0 && o->max_iter >= 0 && o->launch_mode >= 0 && o->launch_mode <= 1 &&
+  return o->tol >= 0 && o->max_iter >= 0 && o->launch_mode >= 0 && o->launch_mode <= 3 &&
          (o->execution == FFTMECH_EXEC_GRAPH || o->execution == FFTMECH_EXEC_HOST) &&
          (o->precond == FFTMECH_PRECOND_LAPLACE || o->precond == FFTMECH_PRECOND_REFERENCE);
 }
@@ -1434,7 +1468,7 @@ fftmech_status adjoint_impl(fftmech_ctx* ctx, const uint8_t* phase, const T* efi
 // Choices of the tunable launch shapes of a context, cached for the process
 // per (device, dimension, grid, batch, precision).
 struct TuneChoice {
-  int L_dir, L_upd, ty, zc, grid, cols;
+  int L_dir, L_upd, ty, zc, grid, cols, L_ds;
 };
 using TuneKey = std::tuple<int, int, int, int, int, int, int>;
 struct TuneEntry {
@@ -1450,7 +1484,7 @@ TuneKey tune_key(const fftmech_ctx* ctx) {
 
 TuneChoice current_choice(const fftmech_ctx* ctx) {
   return TuneChoice{ctx->lshape.L_dir, ctx->lshape.L_upd, ctx->sshape.ty, ctx->sshape.zc, ctx->sshape.grid,
-                    ctx->shape.cols};
+                    ctx->shape.cols, ds_active(ctx) ? ctx->lshape.L_ds : 0};
 }
 
 // The column strip width's thread count and shared memory (2D).
@@ -1471,6 +1505,7 @@ bool choice_ok(const fftmech_ctx* ctx, const TuneChoice& c) {
   if (!line_shape_ok<T>(ctx->px, c.L_dir, true, ctx->dim, spec3, ctx->optin)) return false;
   if (!line_shape_ok<T>(ctx->px, c.L_upd, false, ctx->dim, spec3, ctx->optin)) return false;
   if (c.L_dir > ctx->ny * ctx->nz || c.L_upd > ctx->ny * ctx->nz || c.grid < 1) return false;
+  if (c.L_ds != 0 && (ctx->dim != 2 || !ds_shape_ok<T>(ctx->px, c.L_ds, ctx->ny, ctx->optin))) return false;
   if (ctx->dim == 2) return (c.ty == 4 || c.ty == 8) && cols_ok<T>(ctx, c.cols);
   return c.ty == 4 && c.zc >= 1 && c.zc <= std::min(16, ctx->nz);
 }
@@ -1482,6 +1517,11 @@ void apply_choice(fftmech_ctx* ctx, const TuneChoice& c) {
   ctx->lshape.thr_dir = line_threads(ctx->px, c.L_dir, ctx->dim);
   ctx->lshape.L_upd = c.L_upd;
   ctx->lshape.thr_upd = line_threads(ctx->px, c.L_upd, ctx->dim);
+  if (c.L_ds > 0) {
+    ctx->lshape.L_ds = c.L_ds;
+    ctx->lshape.thr_ds = ds_threads(ctx->px, c.L_ds);
+  }
+  ctx->ds_choice = c.L_ds > 0 ? 1 : 0;
   ctx->sshape.ty = c.ty;
   ctx->sshape.zc = c.zc;
   ctx->sshape.grid = c.grid;
@@ -1624,6 +1664,17 @@ fftmech_status autotune_impl(fftmech_ctx* ctx, int iterations, double* before_us
       consider(c);
     }
   }
+  // split or fused direction and stencil (2D grids where the iteration is
+  // latency-bound): the rule's rows per block, then its neighbours
+  if (ctx->dim == 2 && ctx->ds_rule > 0 && (long long)ctx->N * ctx->B <= (1LL << 21)) {
+    const int L0 = best.L_ds > 0 ? best.L_ds : ctx->ds_rule;
+    for (int L : {0, L0, L0 / 2, L0 * 2, L0 + 1, L0 - 1}) {
+      TuneChoice c = best;
+      if (L < 0 || L == best.L_ds) continue;
+      c.L_ds = L;
+      consider(c);
+    }
+  }
   ctx->opts = saved;
   ctx->graph_off = saved_off;
   apply_choice<T>(ctx, best);
@@ -1635,8 +1686,8 @@ fftmech_status autotune_impl(fftmech_ctx* ctx, int iterations, double* before_us
   }
   if (before_us) *before_us = 1e3 * first_ms / iterations;
   if (after_us) *after_us = 1e3 * best_ms / iterations;
-  snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d", best.L_dir,
-           best.L_upd, best.ty, best.zc, best.grid, best.cols);
+  snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d L_ds=%d",
+           best.L_dir, best.L_upd, best.ty, best.zc, best.grid, best.cols, best.L_ds);
   return FFTMECH_OK;
 }
 
@@ -1959,6 +2010,7 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
                : choose_line_shape<float>(ctx->px, ctx->ny * ctx->nz, grid->dim, spec3, ctx->nsm, ctx->optin,
                                           batch, ctx->lshape);
     ctx->lshape.sst = three ? ctx->shape3.sst : ctx->N;
+    ctx->ds_rule = ctx->lshape.L_ds;
     choose_sten_shape(ctx->nx, ctx->ny, ctx->nz, grid->dim, ctx->nsm, batch, ctx->sshape);
   }
   if (!shp) return fail(FFTMECH_ERR_UNSUPPORTED_SIZE);
@@ -1985,8 +2037,8 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
     // reductions' block partitions, and so its last bits, depend only on
     // its own arguments and fftmech_autotune calls)
     const TuneChoice k = current_choice(ctx);
-    snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d", k.L_dir,
-             k.L_upd, k.ty, k.zc, k.grid, k.cols);
+    snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d L_ds=%d",
+             k.L_dir, k.L_upd, k.ty, k.zc, k.grid, k.cols, k.L_ds);
   }
   const size_t es = fp64 ? 8 : 4;
   const size_t NB = (size_t)ctx->N * batch;
@@ -2019,6 +2071,7 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   alloc(&ctx->q, nd * NB * es);
   alloc(&ctx->r, nd * NB * es);
   alloc(&ctx->p, nd * NB * es);
+  if (!three) alloc(&ctx->pn, nd * NB * es);
   alloc(&ctx->S, 2 * s_complex * es);
   alloc(&ctx->g, NB * es);
   if (!fp64) {
@@ -2071,7 +2124,7 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (GraphCache& c : ctx->gc)
     if (c.exec) cudaGraphExecDestroy(c.exec);
-  void* bufs[] = {ctx->r, ctx->q, ctx->p, ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
+  void* bufs[] = {ctx->r, ctx->q, ctx->p, ctx->pn, ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
                   ctx->cn, ctx->lamx, ctx->lamy, ctx->lamz, ctx->lamc3, ctx->lamc1, ctx->wcol3, ctx->wcol1,
                   ctx->ax, ctx->ay,
                   ctx->partials, ctx->partials_col, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc, ctx->flags, ctx->rec};
@@ -2128,8 +2181,9 @@ fftmech_status fftmech_autotune(fftmech_ctx* ctx, int iterations, double* before
       if (before_us) *before_us = c.before_us;
       if (after_us) *after_us = c.after_us;
       const TuneChoice& k = c.choice;
-      snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d (cached)",
-               k.L_dir, k.L_upd, k.ty, k.zc, k.grid, k.cols);
+      snprintf(ctx->tune_desc, sizeof(ctx->tune_desc),
+               "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d L_ds=%d (cached)", k.L_dir, k.L_upd, k.ty, k.zc, k.grid,
+               k.cols, k.L_ds);
     } else {
       rc = fp64 ? autotune_impl<double>(ctx, iterations, before_us, after_us)
                 : autotune_impl<float>(ctx, iterations, before_us, after_us);

@@ -83,8 +83,9 @@ struct SolverScalars {
   int iter, max_iter, done, status;
   unsigned int cnt[4];  // last-block counters: 0 direction, 1 column pass, 2 stats
   // deferred reductions (2D): <r, M^-1 r> of the last column pass, taken by
-  // the direction kernel's blocks and committed to rz by the update
-  // kernel's block 0; col_true: that column pass followed a reliable update
+  // the direction kernel's blocks and committed to rz by block 0 of the
+  // kernel after them (commit_pending_rz); col_true: that column pass
+  // followed a reliable update
   double rz_next;
   int col_true, pad_i;
   // float copies for the float kernels (no FP64 instruction in their hot
@@ -96,8 +97,8 @@ struct SolverScalars {
   // replacement iterations scheduled
   double rz_rep;
   int reliable, nrestart, nreplace;
-  // deferred reductions (2D): rz_next holds the residual norm that the next
-  // stencil kernel's block 0 commits to rz (with iter += 1)
+  // deferred reductions (2D): rz_next holds the residual norm still to be
+  // committed to rz (with iter += 1)
   int rz_pending;
   // the FP64 true residual of this stopped problem is in rz_true (set by the
   // gate after its true-residual pass; cleared by a restart), so later
@@ -194,8 +195,9 @@ struct Vec2 {
   float* uh;      // MIXED: high part, D x N
   float* ul;      // MIXED: low part, D x N
   T* r;           // residual, D x N
-  const T* p_in;  // previous direction
+  const T* p_in;  // previous direction (update kernel: the current one)
   T* p_out;       // new direction
+  T* p_copy;      // update kernel: where it also stores the current direction (NULL: nowhere)
   cx<T>* S;       // spectral rows, N complex (components packed re / im)
   T* q;           // K p (split iteration), D x N
   double* partials;
@@ -287,6 +289,7 @@ struct LineShape {
   long long sst;  // complex numbers per problem in the spectral buffer
   int L_dir, thr_dir;
   int L_upd, thr_upd;
+  int L_ds, thr_ds;  // fused direction-stencil kernel (2D; L_ds = 0: not available)
 };
 struct StenShape {
   int batch;
@@ -433,6 +436,10 @@ template <typename T, int D, int FX, int DIM, int NX>
 cudaError_t launch_xupd(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
                         cudaStream_t st);
 
+template <typename T, int D, int FX, int NX>
+cudaError_t launch_xds(const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px, const LineShape& ls,
+                       cudaStream_t st);
+
 template <typename T, int D>
 cudaError_t launch_sten2(const Op<T>& op, const Vec2<T>& v, const StenShape& ss, cudaStream_t st);
 template <typename T, int D>
@@ -447,6 +454,18 @@ inline cudaError_t launch_xdir_f(int fx, const Op<T>& op, const Vec2<T>& v, cons
 #undef FFTMECH_C
   }
 #define FFTMECH_C(F) launch_xdir<T, D, F, DIM, 0>(op, v, px, ls, st)
+  FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
+#undef FFTMECH_C
+}
+template <typename T, int D>
+inline cudaError_t launch_xds_f(int fx, const Op<T>& op, const Vec2<T>& v, const FftPlanDev<T>& px,
+                                const LineShape& ls, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+#define FFTMECH_C(NX) launch_xds<T, D, FAM_ALL, NX>(op, v, px, ls, st)
+    FFTMECH_FIXED_SWITCH(px.n, FFTMECH_C)
+#undef FFTMECH_C
+  }
+#define FFTMECH_C(F) launch_xds<T, D, F, 0>(op, v, px, ls, st)
   FFTMECH_FAMILY_SWITCH(fx, FFTMECH_C)
 #undef FFTMECH_C
 }
@@ -612,6 +631,27 @@ struct Row3Layout {
     PH = MG + align16((size_t)(R + 1) * L * ts);
     MK = PH + align16((size_t)(R + 1) * L);
     total = MK + align16((size_t)R * L);
+  }
+};
+
+// Fused direction-stencil kernel (2D, L own rows per block): [F: max(L + 2
+// complex rows, NS (L + 1) rows of stress components)] [PO: D (L + 2) rows
+// of the direction] [MG: (L + 1) rows of the material field] [PH: (L + 1)
+// rows of phase bytes] [MK: (L + 2) rows of mask bytes], after the
+// twiddles.
+template <typename T, int D>
+struct DsLayout {
+  static constexpr int NS = D == 2 ? 3 : 2;  // stress (xx, yy, xy) or flux (x, y) components
+  size_t F, PO, MG, PH, MK, total;
+  __host__ __device__ DsLayout(int nx, int L) {
+    const size_t rows_f = (size_t)(L + 2) * nx * sizeof(cx<T>);
+    const size_t rows_s = (size_t)NS * (L + 1) * nx * sizeof(T);
+    F = 0;
+    PO = align16(rows_f > rows_s ? rows_f : rows_s);
+    MG = PO + align16((size_t)D * (L + 2) * nx * sizeof(T));
+    PH = MG + align16((size_t)(L + 1) * nx * sizeof(T));
+    MK = PH + align16((size_t)(L + 1) * nx);
+    total = MK + align16((size_t)(L + 2) * nx);
   }
 };
 

@@ -209,6 +209,11 @@ bool choose_shape3(const HostPlan& px, const HostPlan& py, const HostPlan& pz, i
   return true;
 }
 
+// Threads of the fused direction-stencil kernel with L own rows: 512 (its
+// element loops and loads gain from every warp; the L + 2 transformed rows
+// need at most 512, checked with the shape).
+inline int ds_threads(const HostPlan&, int) { return 512; }
+
 // Split iteration: lines per block for the x-line kernels. The largest L
 // (at most 16) whose shared memory leaves room for three blocks per SM and
 // whose widest FFT pass fits 512 threads, lowered while the launch would
@@ -241,7 +246,42 @@ bool choose_line_shape(const HostPlan& px, int nlines, int dim, int nxs3, int ns
   if (!s.L_dir || !s.L_upd) return false;
   s.thr_dir = std::min(512, std::max(256, round32(need_threads(px, nf * s.L_dir))));
   s.thr_upd = std::min(512, std::max(256, round32(need_threads(px, nf * s.L_upd))));
+  // the fused direction-stencil kernel (2D), 512 threads a block, at most
+  // two blocks per SM (its registers) and as many as its shared memory
+  // allows: the L whose launch takes the fewest waves, each wave costing
+  // its blocks' transformed rows (L + 2) plus a fixed latency of about four
+  // rows' worth; ties go to the larger L
+  s.L_ds = 0;
+  s.thr_ds = 0;
+  if (dim == 2) {
+    auto ok_ds = [&](int L, size_t lim) {
+      return L >= 1 && L <= nlines && DsLayout<T, 2>(nx, L).total + tw_smem_bytes<T>(nx) <= lim &&
+             need_threads(px, L + 2) <= 512 && (long long)(L + 2) * nx < 65536;
+    };
+    double best = 1e300;
+    for (int L = 1; L <= 16; ++L) {
+      if (!ok_ds(L, optin)) continue;
+      const size_t sm = DsLayout<T, 2>(nx, L).total + tw_smem_bytes<T>(nx) + 1024;
+      const long long per_sm = std::max<long long>(1, std::min<long long>(2, (long long)((optin_total + 1024) / sm)));
+      const long long blocks = (long long)((nlines + L - 1) / L) * batch;
+      const long long waves = (blocks + per_sm * nsm - 1) / (per_sm * nsm);
+      const double cost = (double)waves * (4.0 + L + 2);
+      if (cost <= best) {
+        best = cost;
+        s.L_ds = L;
+      }
+    }
+    if (s.L_ds > 0) s.thr_ds = ds_threads(px, s.L_ds);
+  }
   return true;
+}
+
+// Whether L own rows per block fit the fused direction-stencil kernel (2D).
+template <typename T>
+bool ds_shape_ok(const HostPlan& px, int L, int ny, size_t optin_total) {
+  const int nx = px.n;
+  return L >= 1 && L <= ny && DsLayout<T, 2>(nx, L).total + tw_smem_bytes<T>(nx) <= optin_total - 1024 &&
+         need_threads(px, L + 2) <= 512 && (long long)(L + 2) * nx < 65536;
 }
 
 // Whether L lines per block fit the x-line direction (dir) or update kernel

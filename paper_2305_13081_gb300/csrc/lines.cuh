@@ -49,9 +49,88 @@ __device__ __forceinline__ void line_views(Op<T>& op, Vec2<T>& v, int b, size_t 
   v.r += oD;
   if (v.p_in) v.p_in += oD;
   if (v.p_out) v.p_out += oD;
+  if (v.p_copy) v.p_copy += oD;
   if (v.q) v.q += oD;
   v.S += (size_t)b * sst;
   v.sc += b;
+}
+
+// The direction's scalars, for every thread of the block. With a deferred
+// reduction of the last column pass (an ITER or TRUE pass, ncol > 0):
+// <r, M^-1 r>, convergence and beta in every block; block 0 writes the
+// scalars that nothing in the kernel reads (rz_next, rz_true, beta; rz and
+// iter only when the problem stops here), the decisions in thread 0 only
+// (FP64 runs at a small fraction of FP32). Otherwise the column pass has
+// finalised the iteration and beta is read. lead: the thread that takes
+// the loop decisions of a one-problem solve. Returns true when the problem
+// stops here.
+template <typename T>
+__device__ __forceinline__ bool direction_scalars(const Vec2<T>& v, int bp, size_t N, bool lead, T& b) {
+  if (v.ncol > 0) {
+    // deferred reduction of the last column pass (an ITER or TRUE pass):
+    // <r, M^-1 r>, convergence and beta in every block; block 0 writes the
+    // scalars that nothing in this kernel reads (rz_next, rz_true, beta; rz
+    // and iter only when the problem stops here)
+    // (the decisions in thread 0 only: FP64 runs at a small fraction of FP32)
+    __shared__ float redfx[64];
+    __shared__ double redx[32];
+    __shared__ T b_s;
+    __shared__ int stop_s;
+    SolverScalars* s = v.sc;
+    const double tsum = deferred_total<T>(v.pcol + (size_t)bp * v.ncol, v.ncol, redfx, redx);
+    if (threadIdx.x == 0) {
+      const bool w0 = blockIdx.x == 0;
+      const double tot = tsum * (1.0 / (double)N);
+      const int is_true = vol_readi(&s->col_true);
+      stop_s = 1;
+      if (!isfinite(tot)) {
+        if (w0) {
+          s->rz = tot;
+          s->done = 1;
+          s->status = FFTMECH_ERR_NONFINITE;
+          if (v.mode) v.mode[bp] = 0;
+        }
+      } else if (tot <= s->tol2 * s->rz0 || vol_readi(&s->iter) + 1 >= s->max_iter) {
+        // converged, or the iteration limit reached with this column pass
+        if (w0) {
+          const bool ok = tot <= s->tol2 * s->rz0;
+          s->iter += 1;
+          if (is_true) s->rz_true = tot;
+          s->rz = tot;
+          s->done = 1;
+          s->status = ok ? FFTMECH_OK : FFTMECH_ERR_NOT_CONVERGED;
+          if (v.mode) v.mode[bp] = 0;
+        }
+      } else {
+        double beta = tot / vol_read(&s->rz);
+        // a replaced residual larger than the recursive one it replaces means
+        // the float recursion had drifted: restart the direction instead
+        if (is_true && beta > 1.0) beta = 0.0;
+        if (w0) {
+          // rz_next is committed to rz by block 0 of a later kernel
+          s->rz_next = tot;
+          s->rz_pending = 1;
+          if (is_true) s->rz_true = tot;
+          set_beta(s, beta);
+          const int next = reliable_next(s, tot, is_true, vol_readi(&s->iter) + 1);
+          if (v.mode) v.mode[bp] = next;
+          if (lead) loop_decide(v.ctl, 1, next);
+        }
+        b_s = (T)beta;
+        stop_s = 0;
+      }
+      if (lead && stop_s) loop_decide(v.ctl, 0, 0);
+    }
+    __syncthreads();
+    if (stop_s) return true;
+    b = b_s;
+  } else {
+    // the column pass finalised the iteration (and chose the next mode)
+    if (lead) loop_decide(v.ctl, 1, v.mode ? vol_readi(v.mode + bp) == 1 : 0);
+    if constexpr (sizeof(T) == 4) b = vol_readf(&v.sc->beta_f);
+    else b = vol_read(&v.sc->beta);
+  }
+  return false;
 }
 
 // ---------------------------------------------------------------- direction
@@ -94,72 +173,9 @@ __global__ void FFTMECH_BOUNDS_L k_xdir(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
     g2s_async(F, v.S + t0, nl * nx);
   }
   T b;
-  if (v.ncol > 0) {
-    // deferred reduction of the last column pass (an ITER or TRUE pass):
-    // <r, M^-1 r>, convergence and beta in every block; block 0 writes the
-    // scalars that nothing in this kernel reads (rz_next, rz_true, beta; rz
-    // and iter only when the problem stops here)
-    // (the decisions in thread 0 only: FP64 runs at a small fraction of FP32)
-    __shared__ float redfx[64];
-    __shared__ double redx[32];
-    __shared__ T b_s;
-    __shared__ int stop_s;
-    SolverScalars* s = v.sc;
-    const double tsum = deferred_total<T>(v.pcol + (size_t)bp * v.ncol, v.ncol, redfx, redx);
-    if (threadIdx.x == 0) {
-      const bool w0 = blockIdx.x == 0;
-      const double tot = tsum * (1.0 / (double)N);
-      const int is_true = vol_readi(&s->col_true);
-      stop_s = 1;
-      if (!isfinite(tot)) {
-        if (w0) {
-          s->rz = tot;
-          s->done = 1;
-          s->status = FFTMECH_ERR_NONFINITE;
-          if (v.mode) v.mode[bp] = 0;
-        }
-      } else if (tot <= s->tol2 * s->rz0 || vol_readi(&s->iter) + 1 >= s->max_iter) {
-        // converged, or the iteration limit reached with this column pass
-        if (w0) {
-          const bool ok = tot <= s->tol2 * s->rz0;
-          s->iter += 1;
-          if (is_true) s->rz_true = tot;
-          s->rz = tot;
-          s->done = 1;
-          s->status = ok ? FFTMECH_OK : FFTMECH_ERR_NOT_CONVERGED;
-          if (v.mode) v.mode[bp] = 0;
-        }
-      } else {
-        double beta = tot / vol_read(&s->rz);
-        // a replaced residual larger than the recursive one it replaces means
-        // the float recursion had drifted: restart the direction instead
-        if (is_true && beta > 1.0) beta = 0.0;
-        if (w0) {
-          // rz_next is committed to rz by the next stencil kernel's block 0
-          s->rz_next = tot;
-          s->rz_pending = 1;
-          if (is_true) s->rz_true = tot;
-          set_beta(s, beta);
-          const int next = reliable_next(s, tot, is_true, vol_readi(&s->iter) + 1);
-          if (v.mode) v.mode[bp] = next;
-          if (lead) loop_decide(v.ctl, 1, next);
-        }
-        b_s = (T)beta;
-        stop_s = 0;
-      }
-      if (lead && stop_s) loop_decide(v.ctl, 0, 0);
-    }
-    __syncthreads();
-    if (stop_s) {
-      g2s_async_wait();
-      return;
-    }
-    b = b_s;
-  } else {
-    // the column pass finalised the iteration (and chose the next mode)
-    if (lead) loop_decide(v.ctl, 1, v.mode ? vol_readi(v.mode + bp) == 1 : 0);
-    if constexpr (sizeof(T) == 4) b = vol_readf(&v.sc->beta_f);
-    else b = vol_read(&v.sc->beta);
+  if (direction_scalars<T>(v, bp, N, lead, b)) {
+    g2s_async_wait();
+    return;
   }
   const bool with_old = b != T(0);  // the first iteration has p = z
   // the old direction and the 2D spectral rows by asynchronous copies (unless
@@ -269,7 +285,10 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
     if (threadIdx.x == 0) {
       SolverScalars* s = v.sc;
       const bool w0 = blockIdx.x == 0;
-      const double rz = vol_read(&s->rz);  // committed by the stencil kernel
+      // the residual norm of the last direction: committed by a split
+      // stencil kernel, else pending (block 0 commits it here)
+      const double rz = rz_current(s);
+      if (w0) commit_pending_rz(s);
       stop_s = !(pq > 0.0) || !isfinite(pq);
       if (stop_s) {
         if (w0) {
@@ -407,6 +426,7 @@ __global__ void FFTMECH_BOUNDS_L k_xupd(Op<T> op, Vec2<T> v, FftPlanDev<T> px, i
             } else {
               v.u[g] = ud[u][c] + alpha * (double)p[u][c];
             }
+            if (v.p_copy) v.p_copy[g] = p[u][c];
             if (!u_only) {
               r[u][c] -= a * q[u][c];
               v.r[g] = r[u][c];

@@ -77,17 +77,27 @@ static __device__ __forceinline__ void set_loop_flag(const LoopCtl& c, int k, in
   if (c.have & (1u << k)) cudaGraphSetConditional((cudaGraphConditionalHandle)c.h[k], (unsigned int)value);
 }
 
-// Deferred reductions (2D): block 0 of the stencil kernel commits the
-// residual norm that the direction kernel left in rz_next (the direction
-// kernel's blocks all read rz as the previous norm, so none of them may
-// overwrite it). The update kernel that follows reads the committed rz.
+// Deferred reductions (2D): the direction kernel leaves the new residual
+// norm in rz_next (its blocks all read rz as the previous norm, so none of
+// them may overwrite it) and block 0 of a later kernel commits it: the
+// stencil kernel after a split direction, the update kernel after the fused
+// direction-stencil kernel. The commit stores rz before it clears
+// rz_pending (release); a block of the committing kernel reads rz_pending
+// first (acquire), so it sees either the pending norm in rz_next or the
+// committed rz, which are equal (rz_current).
 static __device__ __forceinline__ void commit_pending_rz(SolverScalars* sc) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   if (*reinterpret_cast<volatile int*>(&sc->rz_pending)) {
-    sc->rz = *reinterpret_cast<volatile double*>(&sc->rz_next);
-    sc->iter += 1;
-    sc->rz_pending = 0;
+    *reinterpret_cast<volatile double*>(&sc->rz) = *reinterpret_cast<volatile double*>(&sc->rz_next);
+    *reinterpret_cast<volatile int*>(&sc->iter) = *reinterpret_cast<volatile int*>(&sc->iter) + 1;
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(&sc->rz_pending), "r"(0) : "memory");
   }
+}
+static __device__ __forceinline__ double rz_current(const SolverScalars* sc) {
+  int pend;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(pend) : "l"(&sc->rz_pending) : "memory");
+  return pend ? *reinterpret_cast<const volatile double*>(&sc->rz_next)
+              : *reinterpret_cast<const volatile double*>(&sc->rz);
 }
 
 // Loop decisions after a direction (single writer): an active problem runs

@@ -1,8 +1,18 @@
-"""Programmatic dependent launches (the default launch mode) against plain
-stream order: every kernel waits on the device for its predecessor, so both
-modes must give bit-identical fields and the same iteration counts. A
-missing wait would show up here as a race (a field that differs between the
-modes or from run to run)."""
+"""Launch modes of the PCG iteration.
+
+- Programmatic dependent launches (bit 0 clear, the default) against plain
+  stream order: every kernel waits on the device for its predecessor, so
+  both must give bit-identical fields and the same iteration counts. A
+  missing wait would show up here as a race (a field that differs between
+  the modes or from run to run).
+- The fused direction-stencil kernel of latency-bound 2D grids (bit 1
+  set) against the split direction and stencil kernels (the default):
+  the same operator and direction, so a fixed number of iterations gives
+  the same iterate up to the rounding of the <p, K p> summation order
+  (FP64: 1e-12), on grids whose rows do not divide evenly into the fused
+  kernel's blocks, with a Dirichlet mask; whole staggered steps agree to
+  the solver tolerance.
+"""
 
 import numpy as np
 import pytest
@@ -53,7 +63,7 @@ def transient_state(phases, prec, dt):
 
 def run_steps(phases, prec, launch_mode, steps=2, tol=1e-8):
     shape = phases[0].shape
-    n = shape[0]
+    n = min(shape)
     ctx = fm.Context(shape, MAT, prec, h=H, h_diff=1.0, tol=tol, batch=len(phases), launch_mode=launch_mode)
     bufs, st, p = transient_state(phases, prec, (n / 4.0) ** 2 / 10)
     iters = []
@@ -67,12 +77,13 @@ def run_steps(phases, prec, launch_mode, steps=2, tol=1e-8):
     return {k: bufs[k].cpu().numpy() for k in ("c", "u", "strain", "stress", "damage")}, iters
 
 
+@pytest.mark.parametrize("fuse", [0, 2])
 @pytest.mark.parametrize("prec", [fm.FFTMECH_MIXED, fm.FFTMECH_FP64])
 @pytest.mark.parametrize("n,seeds", [(81, (7, 8)), (243, (9,))])
-def test_dependent_launches_bit_identical_2d(prec, n, seeds):
+def test_dependent_launches_bit_identical_2d(prec, n, seeds, fuse):
     phases = [random_carpet(n, 0.30, s)[0] for s in seeds]
-    a, ia = run_steps(phases, prec, 0)
-    b, ib = run_steps(phases, prec, 1)
+    a, ia = run_steps(phases, prec, 0 + fuse)
+    b, ib = run_steps(phases, prec, 1 + fuse)
     assert ia == ib
     for k in a:
         assert np.array_equal(a[k], b[k]), k
@@ -97,3 +108,79 @@ def test_dependent_launches_repeatable():
     assert ia == ib
     for k in a:
         assert np.array_equal(a[k], b[k]), k
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+GRIDS = [((729, 729), (21,)), ((243, 96), tuple(range(22, 30))), ((48, 81), (30,))]
+
+
+def cut_carpets(shape, seeds):
+    ny, nx = shape
+    return [np.ascontiguousarray(random_carpet(max(shape), 0.30, s)[0][:ny, :nx]) for s in seeds]
+
+
+def k_iterations(phases, prec, launch_mode, kind, k=12):
+    """The first k PCG iterations (tol 0) of a transient diffusion step with
+    a Dirichlet face (D = 1) or of an equilibrium solve with a pore
+    eigenstrain (D = 2): no residual replacement happens before the 16th."""
+    shape = phases[0].shape
+    B, N = len(phases), phases[0].size
+    ctx = fm.Context(shape, MAT, prec, h=H, h_diff=1.0, tol=0.0, max_iter=k, batch=B, launch_mode=launch_mode)
+    ph = torch.as_tensor(np.concatenate([p.ravel() for p in phases])).cuda()
+    rng = np.random.default_rng(5)
+    if kind == "diffusion":
+        mask = torch.as_tensor(np.concatenate([left_face_mask(p).ravel() for p in phases])).cuda()
+        c = torch.as_tensor(rng.random(B * N)).cuda()
+        fm.fftmech_diffusion_step(ctx.handle, ph, fm.FFTMECH_DIFF_TRANSIENT, [0.0, 0.0], 0.0, 20.0, mask, 1.0, c)
+        out = c
+    else:
+        ft = torch.float64 if prec == fm.FFTMECH_FP64 else torch.float32
+        eig = torch.where(ph == 0, 1e-3, 0.0).to(ft)
+        out = torch.zeros(2 * B * N, dtype=torch.float64, device="cuda")
+        fm.fftmech_equilibrium_solve(ctx.handle, ph, eig, None, [0.0] * 6, out, None, None)
+    torch.cuda.synchronize()
+    ctx.close()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind", ["diffusion", "equilibrium"])
+@pytest.mark.parametrize("prec", [fm.FFTMECH_MIXED, fm.FFTMECH_FP64])
+@pytest.mark.parametrize("shape,seeds", GRIDS)
+def test_fused_direction_stencil_iterate_for_iterate(prec, shape, seeds, kind):
+    """The host's rule gives 729 rows blocks of three own rows, a batch of
+    eight 243 x 96 grids blocks of seven ending with a five-row block, and
+    48 x 81 one row per block. Every grid has blocks whose halo rows wrap
+    around the periodic boundary. A wrong halo row or a misplaced q would
+    move the iterate at O(1)."""
+    phases = cut_carpets(shape, seeds)
+    a = k_iterations(phases, prec, 0, kind)
+    b = k_iterations(phases, prec, 2, kind)
+    e = rel(a, b)
+    print(kind, shape, e)
+    assert e < (1e-12 if prec == fm.FFTMECH_FP64 else 1e-5), e
+
+
+@pytest.mark.parametrize("prec", [fm.FFTMECH_MIXED, fm.FFTMECH_FP64])
+@pytest.mark.parametrize("shape,seeds", GRIDS)
+def test_fused_direction_stencil_matches_split(prec, shape, seeds):
+    """Whole staggered steps (tol 1e-8). The summation order moves the
+    iterates by rounding; over hundreds of iterations of the ill-conditioned
+    diffusion solve, CG's loss of orthogonality turns that into a path a
+    few iterations longer or shorter (the float recursion of the mixed
+    path more so), ending at the same tolerance."""
+    phases = cut_carpets(shape, seeds)
+    a, ia = run_steps(phases, prec, 0)
+    b, ib = run_steps(phases, prec, 2)
+    print("iterations fused", ia, "split", ib)
+    fp64 = prec == fm.FFTMECH_FP64
+    for step_a, step_b in zip(ia, ib):
+        for x, y in zip(step_a, step_b):
+            assert abs(x - y) <= 3 + (0.03 if fp64 else 0.1) * y, (ia, ib)
+    for k in a:
+        e = rel(a[k], b[k])
+        print(k, e)
+        assert e < 1e-5, (k, e)
+    assert a["damage"].max() > 0

@@ -112,7 +112,7 @@ def test_argument_errors_return_before_any_device_work(lib):
     o2 = fm.make_opts(tol=-1.0)
     assert L.fftmech_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(mat), 0,
                             ctypes.byref(o2), None) == fm.FFTMECH_ERR_INVALID_ARG
-    o3 = fm.make_opts(launch_mode=2)
+    o3 = fm.make_opts(launch_mode=4)
     assert L.fftmech_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(mat), 0,
                             ctypes.byref(o3), None) == fm.FFTMECH_ERR_INVALID_ARG
     assert L.fftmech_create(None, ctypes.byref(g), ctypes.byref(mat), 0,
