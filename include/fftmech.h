@@ -383,6 +383,15 @@ fftmech_status fftmech_adjoint_eigenstrain(fftmech_ctx* ctx, const uint8_t* phas
 fftmech_status fftmech_autotune(fftmech_ctx* ctx, int iterations, double* before_us, double* after_us,
                                 const char** choice);
 
+/* Applies launch shapes given as the description fftmech_autotune returns
+ * ("L_dir=2 L_upd=1 ty=8 zc=1 grid=1216 cols=4 L_ds=0": any subset of these
+ * keys, separated by spaces; a trailing "(cached)" is ignored), so that a
+ * tuning can be kept across processes. Keys left out keep their values.
+ * L_ds = 0 selects the split direction and stencil kernels, L_ds > 0 the
+ * fused kernel with that many rows per block. Returns INVALID_ARG (and
+ * changes nothing) for an unknown key or a shape the grid cannot take. */
+fftmech_status fftmech_set_launch_shapes(fftmech_ctx* ctx, const char* shapes);
+
 /* Homogenised RVE diffusion (Sec. 2.1: Eqs. diffusion, diffusion-final,
  * phi-fft) with a choice of gradient operator (Sec. 2.6, the comparison of
  * Fig. 2): FFTMECH_GRAD_FORWARD (e^{i theta} - 1) / h, the operator of every

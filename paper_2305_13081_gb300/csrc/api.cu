@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <string>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -1493,7 +1494,7 @@ bool cols_ok(const fftmech_ctx* ctx, int cw) {
   const int ny = ctx->ny;
   const bool fixed = sizeof(T) == 4 && (ny == 81 || ny == 243 || ny == 729 || ny == 2187 || ny == 128 || ny == 256 ||
                                         ny == 512 || ny == 1024);
-  if (fixed && cw != 4 && cw != 8) return false;
+  if (fixed && cw != 2 && cw != 4 && cw != 8) return false;
   const size_t smem = (size_t)ny * cw * sizeof(cx<T>) + tw_smem_bytes<T>(ny) + (size_t)(ny + cw) * sizeof(T);
   return cw >= 1 && smem <= ctx->optin - 1024 && (fixed || need_threads(ctx->py, cw) <= 512) &&
          (size_t)ctx->B * ctx->nx >= (size_t)1;
@@ -1530,7 +1531,8 @@ void apply_choice(fftmech_ctx* ctx, const TuneChoice& c) {
     const int ny = ctx->ny;
     const bool fixed = sizeof(T) == 4 && (ny == 81 || ny == 243 || ny == 729 || ny == 2187 || ny == 128 ||
                                           ny == 256 || ny == 512 || ny == 1024);
-    ctx->shape.threads_col = fixed ? 512 : std::min(512, std::max(128, round32(need_threads(ctx->py, c.cols))));
+    ctx->shape.threads_col = fixed ? (c.cols >= 4 ? 512 : 256)
+                                   : std::min(512, std::max(128, round32(need_threads(ctx->py, c.cols))));
   }
   for (GraphCache& g : ctx->gc) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -2155,6 +2157,40 @@ fftmech_status fftmech_set_solver_opts(fftmech_ctx* ctx, const fftmech_solver_op
 }
 
 int fftmech_batch_size(const fftmech_ctx* ctx) { return ctx ? ctx->B : 0; }
+
+fftmech_status fftmech_set_launch_shapes(fftmech_ctx* ctx, const char* shapes) {
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  if (!shapes) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "shapes must not be NULL");
+  TuneChoice c = current_choice(ctx);
+  const char* s = shapes;
+  for (;;) {
+    while (*s == ' ') ++s;
+    if (!*s || *s == '(') break;  // the end, or a "(cached)" note
+    char key[16] = {0};
+    int val = 0, used = 0;
+    if (std::sscanf(s, "%15[A-Za-z_]=%d%n", key, &val, &used) != 2 || used <= 0)
+      return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "shapes: expected key=value");
+    const std::string k(key);
+    if (k == "L_dir") c.L_dir = val;
+    else if (k == "L_upd") c.L_upd = val;
+    else if (k == "ty") c.ty = val;
+    else if (k == "zc") c.zc = val;
+    else if (k == "grid") c.grid = val;
+    else if (k == "cols") c.cols = val;
+    else if (k == "L_ds") c.L_ds = val;
+    else return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "shapes: unknown key");
+    s += used;
+  }
+  const bool fp64 = ctx->prec == FFTMECH_FP64;
+  if (c.L_ds < 0 || !(fp64 ? choice_ok<double>(ctx, c) : choice_ok<float>(ctx, c)))
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "shapes: not a valid launch shape for this grid");
+  if (fp64) apply_choice<double>(ctx, c);
+  else apply_choice<float>(ctx, c);
+  snprintf(ctx->tune_desc, sizeof(ctx->tune_desc), "L_dir=%d L_upd=%d ty=%d zc=%d grid=%d cols=%d L_ds=%d", c.L_dir,
+           c.L_upd, c.ty, c.zc, c.grid, c.cols, c.L_ds);
+  return FFTMECH_OK;
+}
 
 fftmech_status fftmech_autotune(fftmech_ctx* ctx, int iterations, double* before_us, double* after_us,
                                 const char** choice) {

@@ -365,10 +365,11 @@ inline cudaError_t launch_colpass_f(int fy, int nx, int ny, cx<T>* S, const FftP
                                     cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     // compile-time column plans for the benchmark lengths and strip widths
-#define FFTMECH_CW(NY)                                                                                \
-  (sh.cols == 8 ? launch_colpass<T, FAM_ALL, NY, 8>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st) \
-                : launch_colpass<T, FAM_ALL, NY, 4>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st))
-    if (sh.cols == 4 || sh.cols == 8) {
+#define FFTMECH_CW(NY)                                                                                  \
+  (sh.cols == 8   ? launch_colpass<T, FAM_ALL, NY, 8>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st) \
+   : sh.cols == 4 ? launch_colpass<T, FAM_ALL, NY, 4>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st) \
+                  : launch_colpass<T, FAM_ALL, NY, 2>(nx, ny, S, py, sp, sh, mode, inverse, partials, sc, pmode, st))
+    if (sh.cols == 2 || sh.cols == 4 || sh.cols == 8) {
       FFTMECH_FIXED_SWITCH(ny, FFTMECH_CW)
     }
 #undef FFTMECH_CW

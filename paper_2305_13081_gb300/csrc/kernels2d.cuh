@@ -146,11 +146,13 @@ __global__ void FFTMECH_BOUNDS(T) k_residual(Op<T> op, Vec2<T> v, FftPlanDev<T> 
 
 // ---------------------------------------------------------------- column pass
 // Column transform of a strip: the compile-time plan (NY > 0, CWC columns,
-// blocks of kColThreads threads) or the runtime one (nc columns).
+// blocks of col_threads<CWC>() threads) or the runtime one (nc columns).
 constexpr int kColThreads = 512;
+template <int CWC>
+__host__ __device__ constexpr int col_threads() { return CWC >= 4 ? kColThreads : 256; }
 template <typename T, int S, int FY, int NY, int CWC>
 __device__ __forceinline__ void col_fft(cx<T>* B, const FftPlanDev<T>& p, int nc) {
-  if constexpr (NY > 0) fftc<T, S, NY, true, CWC, kColThreads>(B, p.tw, CWC);
+  if constexpr (NY > 0) fftc<T, S, NY, true, CWC, col_threads<CWC>()>(B, p.tw, CWC);
   else fft_lines<T, S, FY>(B, p, nc, 1, nc, true);
 }
 
@@ -192,7 +194,7 @@ __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* 
                                               int inverse, int bp, Acc<T>& acc) {
   // with a compile-time plan the block size and the column length are
   // constants: the strip loops' row and column indices fold into offsets
-  const int bd = NY > 0 ? kColThreads : (int)blockDim.x;
+  const int bd = NY > 0 ? col_threads<CWC>() : (int)blockDim.x;
   if constexpr (NY > 0) ny = NY;
   const int x0 = strip * CW;
   const int nc = min(CW, nx - x0);
@@ -226,7 +228,7 @@ __device__ __forceinline__ void colpass_strip(int strip, int nx, int ny, cx<T>* 
     // the last forward pass's outputs before they are stored
     const T m0 = sp.m0b ? (T)sp.m0b[bp] : sp.m0_t, m1 = sp.m1b ? (T)sp.m1b[bp] : sp.m1_t;
     ColMul<T> mul{lamx_s, lamy_s, m0, m1, sp.invN_t, store, T(0), 0, &acc};
-    fftc<T, -1, NY, true, CWC, kColThreads>(B, py_s.tw, CWC, mul);
+    fftc<T, -1, NY, true, CWC, col_threads<CWC>()>(B, py_s.tw, CWC, mul);
     acc.add(mul.part);
     if (store) {
       __syncthreads();
@@ -360,7 +362,7 @@ cudaError_t launch_colpass(int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, co
   cudaError_t e = opt_in_smem(k_colpass<T, FY, NY, CWC>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid((nx + CW - 1) / CW, sh.batch > 0 ? sh.batch : 1);
-  return launch_dep(k_colpass<T, FY, NY, CWC>, grid, dim3(NY > 0 ? kColThreads : sh.threads_col), sm, st, nx, ny,
+  return launch_dep(k_colpass<T, FY, NY, CWC>, grid, dim3(NY > 0 ? col_threads<CWC>() : sh.threads_col), sm, st, nx, ny,
                     S, py, sp, CW, mode, inverse, partials, sc, pmode);
 }
 
@@ -392,6 +394,9 @@ cudaError_t launch_rowfft(int nx, int ny, cx<T>* S, const FftPlanDev<T>& px, int
                                            const Shape2&, cudaStream_t);
 // column passes of a compile-time length (float) for strips of 4 or 8 columns
 #define FFTMECH_INST_COL_FIXED(NY)                                                                               \
+  template cudaError_t launch_colpass<float, FAM_ALL, NY, 2>(int, int, cx<float>*, const FftPlanDev<float>&,    \
+                                                             const Spec<float>&, const Shape2&, int, int,       \
+                                                             double*, SolverScalars*, int*, cudaStream_t); \
   template cudaError_t launch_colpass<float, FAM_ALL, NY, 4>(int, int, cx<float>*, const FftPlanDev<float>&,    \
                                                              const Spec<float>&, const Shape2&, int, int,       \
                                                              double*, SolverScalars*, int*, cudaStream_t); \

@@ -148,6 +148,7 @@ def load_library(path=LIB_PATH):
         "fftmech_step_info": (i, [vp, P(fftmech_solve_info)]),
         "fftmech_adjoint_eigenstrain": (i, [vp, vp, vp, i, P(d), P(d), i, i, vp, P(d), P(fftmech_solve_info)]),
         "fftmech_autotune": (i, [vp, i, P(d), P(d), P(ctypes.c_char_p)]),
+        "fftmech_set_launch_shapes": (i, [vp, ctypes.c_char_p]),
         "fftmech_problem_offset": (i, [vp, i, i, P(ctypes.c_longlong)]),
         "fftmech_graph_stats": (i, [vp, P(ctypes.c_longlong), P(ctypes.c_longlong), P(ctypes.c_longlong),
                                     P(i), P(ctypes.c_char_p)]),
@@ -339,6 +340,11 @@ def fftmech_autotune(ctx, iterations=30):
     _check(load_library().fftmech_autotune(ctx, int(iterations), ctypes.byref(b), ctypes.byref(a),
                                            ctypes.byref(desc)), ctx)
     return b.value, a.value, (desc.value or b"").decode()
+
+
+def fftmech_set_launch_shapes(ctx, shapes):
+    """Applies launch shapes given as fftmech_autotune's description."""
+    _check(load_library().fftmech_set_launch_shapes(ctx, shapes.encode()), ctx)
 
 
 def fftmech_problem_offset(ctx, problem, components):

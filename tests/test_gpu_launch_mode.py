@@ -122,13 +122,16 @@ def cut_carpets(shape, seeds):
     return [np.ascontiguousarray(random_carpet(max(shape), 0.30, s)[0][:ny, :nx]) for s in seeds]
 
 
-def k_iterations(phases, prec, launch_mode, kind, k=12):
+def k_iterations(phases, prec, launch_mode, kind, k=12, shapes=None):
     """The first k PCG iterations (tol 0) of a transient diffusion step with
     a Dirichlet face (D = 1) or of an equilibrium solve with a pore
-    eigenstrain (D = 2): no residual replacement happens before the 16th."""
+    eigenstrain (D = 2): no residual replacement happens before the 16th.
+    shapes: launch shapes to apply first (fftmech_set_launch_shapes)."""
     shape = phases[0].shape
     B, N = len(phases), phases[0].size
     ctx = fm.Context(shape, MAT, prec, h=H, h_diff=1.0, tol=0.0, max_iter=k, batch=B, launch_mode=launch_mode)
+    if shapes:
+        fm.fftmech_set_launch_shapes(ctx.handle, shapes)
     ph = torch.as_tensor(np.concatenate([p.ravel() for p in phases])).cuda()
     rng = np.random.default_rng(5)
     if kind == "diffusion":
@@ -184,3 +187,34 @@ def test_fused_direction_stencil_matches_split(prec, shape, seeds):
         print(k, e)
         assert e < 1e-5, (k, e)
     assert a["damage"].max() > 0
+
+
+@pytest.mark.parametrize("kind", ["diffusion", "equilibrium"])
+@pytest.mark.parametrize("shapes", ["cols=2", "cols=8", "cols=2 L_ds=1", "cols=8 L_ds=2", "L_ds=4",
+                                    "L_dir=3 L_upd=1 ty=8 grid=300"])
+def test_launch_shapes_729(shapes, kind):
+    """Launch shapes that the autotuner may pick (applied through
+    fftmech_set_launch_shapes): every column strip width of the compile-time
+    729-point plan, fused kernels of one, two and four rows (the last two
+    ending with a one-row block), other line and stencil
+    shapes. Twelve iterations agree with the rule-based shapes to the
+    rounding of the reductions' block partitions (mixed path)."""
+    phases = cut_carpets((729, 729), (41,))
+    a = k_iterations(phases, fm.FFTMECH_MIXED, 0, kind)
+    b = k_iterations(phases, fm.FFTMECH_MIXED, 0, kind, shapes=shapes)
+    e = rel(b, a)
+    print(shapes, kind, e)
+    assert e < 1e-5, e
+
+
+def test_launch_shapes_round_trip_and_errors():
+    ctx = fm.Context((243, 243), MAT, fm.FFTMECH_MIXED, h=H)
+    fm.fftmech_set_launch_shapes(ctx.handle, "cols=2 L_ds=3")
+    _, _, desc = fm.fftmech_autotune(ctx.handle, 0)
+    assert "cols=2" in desc and "L_ds=3" in desc
+    fm.fftmech_set_launch_shapes(ctx.handle, desc + " (cached)")
+    for bad in ("cols=3", "L_ds=-1", "ty=5", "foo=1", "cols"):
+        with pytest.raises(RuntimeError):
+            fm.fftmech_set_launch_shapes(ctx.handle, bad)
+    assert fm.fftmech_autotune(ctx.handle, 0)[2] == desc
+    ctx.close()
