@@ -53,6 +53,8 @@ def fused_ds(prof, dim):
     """Whether a profiled 2D run used the fused direction-stencil kernel:
     its iterations launched no separate stencil kernel."""
     return dim == 2 and prof["stencil"][0] == 0 and prof["direction"][0] > 0
+
+
 # DRAM bytes (read + write) per launch of a workload's dominant kernel class,
 # from one ncu capture (L2 flushed before the launch) of the kernels as they
 # stand; an entry is removed when its kernel changes.
@@ -598,7 +600,8 @@ def operator_comparison(torch, fm, device, w):
     fftmech_homogenise_operator. Per operator: PCG iterations, device time,
     the mean flux, and the ringing of the flux j_x: the mean |second
     difference along x| over pore voxels whose x neighbours are pores,
-    relative to the mean |j_x| there."""
+    relative to the mean |j_x| there. Then the same for sigma_xx of the
+    equilibrium under eps_mac = 1e-2 xx (fftmech_equilibrium_operator)."""
     from microstructures.workloads import Materials
     phase = w.phase
     mat = Materials()
@@ -625,6 +628,28 @@ def operator_comparison(torch, fm, device, w):
         d2 = np.abs(np.roll(jx, -1, axis=1) - 2 * jx + np.roll(jx, 1, axis=1))
         out[name] = {"iters": info.iters, "ms": e0.elapsed_time(e1), "mean_flux_x": info.mean_flux[0],
                      "ringing": float(d2[inner].mean() / np.abs(jx[pore]).mean())}
+    # the stress panels: equilibrium under a uniaxial macro strain of 1e-2
+    # through fftmech_equilibrium_operator; ringing of sigma_xx over solid
+    # voxels whose x neighbours are solid
+    solid = phase == 1
+    inner_s = solid & np.roll(solid, 1, axis=1) & np.roll(solid, -1, axis=1)
+    sig = torch.zeros(3 * N, dtype=torch.float64, device=device)
+    for name, op in (("forward", fm.FFTMECH_GRAD_FORWARD), ("central", fm.FFTMECH_GRAD_CENTRAL),
+                     ("central8", fm.FFTMECH_GRAD_CENTRAL8), ("fourier", fm.FFTMECH_GRAD_FOURIER)):
+        ctx = fm.Context(phase.shape, mat, fm.FFTMECH_FP64, h=w.h, tol=1e-8, max_iter=20000,
+                         stream=stream.cuda_stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = fm.fftmech_equilibrium_operator(ctx.handle, ph, None, None, [1e-2, 0.0, 0.0], op, None, sig)
+        e1.record(stream)
+        e1.synchronize()
+        ctx.close()
+        sxx = sig[:N].cpu().numpy().reshape(phase.shape)
+        d2 = np.abs(np.roll(sxx, -1, axis=1) - 2 * sxx + np.roll(sxx, 1, axis=1))
+        out[name].update({"elastic_iters": info.iters, "elastic_ms": e0.elapsed_time(e1),
+                          "mean_stress_xx": info.mean_stress[0],
+                          "stress_ringing": float(d2[inner_s].mean() / np.abs(sxx[solid]).mean())})
     return out
 
 

@@ -414,6 +414,22 @@ fftmech_status fftmech_homogenise_operator(fftmech_ctx* ctx, const uint8_t* phas
                                           const double grad_c_mac[3], double* phi, double* grad_c,
                                           fftmech_solve_info* info);
 
+/* Mechanical equilibrium with a choice of gradient operator (Sec. 2.6
+ * applied to Eqs. solid and solid-final; the stress panels of Fig. 2):
+ * D^H F[g C : F^-1(sym D u)] = -D^H F[g C : (E - e I)] solved by PCG on the
+ * displacement spectra with the preconditioner 1 / |D|^2 per component,
+ * gradient one of FFTMECH_GRAD_* (FOURIER: odd grid sizes only). FP64
+ * whatever the context's precision; host-driven; one problem per context;
+ * allocates temporary device buffers. Uses the context's grid, h, the
+ * elastic constants, kappa, tol and max_iter. phase: uint8 [N]; eig:
+ * double [N] or NULL (0); damage: double [N] or NULL (g = 1), g = (1 -
+ * d)^2 + kappa; eps_mac: Voigt (tensor shears); strain = E + sym D u and
+ * stress = g C : (strain - e I): double [nv N] or NULL (device pointers).
+ * info: iterations, residual, <sigma>, <eps>. */
+fftmech_status fftmech_equilibrium_operator(fftmech_ctx* ctx, const uint8_t* phase, const double* eig,
+                                            const double* damage, const double eps_mac[6], int gradient,
+                                            double* strain, double* stress, fftmech_solve_info* info);
+
 /* Element offset of problem `problem`'s segment in a field with
  * `components` components per voxel (1 for scalar fields, dim for u, 3 or
  * 6 for strain and stress) of a batched context: problem * components * N. */

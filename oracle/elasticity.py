@@ -89,9 +89,11 @@ def to_voigt(T):
 
 
 def equilibrium_solve(phase, eig, g, eps_mac, mat, h, tol=1e-12, newton_tol=1e-8,
-                      max_newton=6, max_iter=200000, record=False):
+                      max_newton=6, max_iter=200000, record=False, symbol="forward"):
     """Newton-Raphson + CG for Eq. (solid-final) (Algorithm 1, Development of
-    stresses). eps_mac: Voigt components (len 3 in 2D, 6 in 3D).
+    stresses). eps_mac: Voigt components (len 3 in 2D, 6 in 3D). symbol:
+    the gradient operator of Sec. 2.6 (spectral.SYMBOLS; the paper's results
+    use the forward difference).
     Returns a dict with F, strain (Voigt), stress (Voigt), the CG info of the
     first Newton step and the total CG iterations."""
     phase = np.asarray(phase)
@@ -100,7 +102,7 @@ def equilibrium_solve(phase, eig, g, eps_mac, mat, h, tol=1e-12, newton_tol=1e-8
     lam, mu = phase_lame(phase, mat)
     e = np.asarray(eig, dtype=np.float64)
     g = np.asarray(g, dtype=np.float64)
-    D = spectral.forward_difference_symbol(shape, h)
+    D = spectral.SYMBOLS[symbol](shape, h)
     ghat = spectral.projection_operator(D)
     E = macro_tensor(eps_mac, d)
     F = np.broadcast_to(E[:, :, None, None] if d == 2 else E[:, :, None, None, None],

@@ -1919,6 +1919,150 @@ fftmech_status homogenise_operator_impl(fftmech_ctx* ctx, const uint8_t* phase, 
   return status;
 }
 
+// Mechanical equilibrium with a chosen gradient operator (Sec. 2.6 applied
+// to Eqs. solid and solid-final): the same spectral-operator PCG as the
+// diffusion above, on the d displacement spectra, with the stress formed in
+// real space from F^-1(sym D u). FP64, host-driven, one problem.
+fftmech_status equilibrium_operator_impl(fftmech_ctx* ctx, const uint8_t* phase, const double* eig,
+                                         const double* damage, const double E[6], int op, double* strain,
+                                         double* stress, fftmech_solve_info* info) {
+  using cxd = cx<double>;
+  cudaStream_t st = ctx->stream;
+  const int nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, dim = ctx->dim;
+  const long long N = ctx->N, nU = (long long)dim * N;
+  const size_t cb = (size_t)N * sizeof(cxd), cu = (size_t)nU * sizeof(cxd);
+  const VarElSpec spec = var_el_spec(dim);
+  DevBuffers mem;
+  cxd* P = mem.get<cxd>(cu);
+  cxd* R = mem.get<cxd>(cu);
+  cxd* X = mem.get<cxd>(cu);
+  cxd* Z = mem.get<cxd>(cu);
+  cxd* Q = mem.get<cxd>(cu);
+  cxd* W[3] = {nullptr, nullptr, nullptr};
+  for (int w = 0; w < spec.nw; ++w) W[w] = mem.get<cxd>(cb);
+  cxd* dx = mem.get<cxd>((size_t)nx * sizeof(cxd));
+  cxd* dy = mem.get<cxd>((size_t)ny * sizeof(cxd));
+  cxd* dz = mem.get<cxd>((size_t)nz * sizeof(cxd));
+  const int nb = var_dot_blocks(nU);
+  const int nbs = var_dot_blocks(N);
+  double* part = mem.get<double>((size_t)2 * std::max(nb, nbs) * sizeof(double));
+  if (!mem.ok) return set_err(ctx, FFTMECH_ERR_OOM, "operator-variant buffers");
+  const double h = ctx->h;
+  const auto tx = grad_symbol(op, nx, h), ty = grad_symbol(op, ny, h), tz = grad_symbol(op, nz, h);
+  CK(cudaMemcpyAsync(dx, tx.data(), nx * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dy, ty.data(), ny * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dz, tz.data(), nz * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  const VarGrid g{nx, ny, nz, dim, N, dx, dy, dz};
+  const double invN = 1.0 / (double)N;
+  double lam[2], mu[2];
+  lame(ctx->mat.E_pore, ctx->mat.nu_pore, lam[0], mu[0]);
+  lame(ctx->mat.E_solid, ctx->mat.nu_solid, lam[1], mu[1]);
+  const double kappa = ctx->mat.kappa;
+  const double zero[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<double> hpart(2 * std::max(nb, nbs));
+  auto fft_w = [&](bool inv) -> fftmech_status {
+    for (int w = 0; w < spec.nw; ++w) RC(fft_inplace(nx, ny, nz, true, inv, W[w], st));
+    return FFTMECH_OK;
+  };
+  auto dot = [&](const cxd* a, const cxd* b, double& out) -> fftmech_status {
+    CK(launch_var_dot(nU, a, b, part, st));
+    CK(cudaMemcpyAsync(hpart.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out = 0.0;
+    for (int i = 0; i < nb; ++i) out += hpart[i];
+    return FFTMECH_OK;
+  };
+  auto precond = [&](const cxd* r, cxd* z) -> fftmech_status {
+    for (int c = 0; c < dim; ++c) CK(launch_var_precond(g, r + (size_t)c * N, z + (size_t)c * N, st));
+    return FFTMECH_OK;
+  };
+  // q = s D^H F[g C : (F^-1(sym D p) / N + Em - e I)]; p = NULL: the strain is Em - e I
+  auto apply = [&](const cxd* p, cxd* q, const double* Em, const double* e, double s) -> fftmech_status {
+    if (p) {
+      CK(launch_varel_strain(g, spec, W, p, st));
+      RC(fft_w(true));
+    } else {
+      for (int w = 0; w < spec.nw; ++w) CK(cudaMemsetAsync(W[w], 0, cb, st));
+    }
+    CK(launch_varel_stress(g, spec, W, phase, e, damage, kappa, lam, mu, Em, invN, st));
+    RC(fft_w(false));
+    CK(launch_varel_div(g, spec, W, s, q, st));
+    return FFTMECH_OK;
+  };
+  RC(apply(nullptr, R, E, eig, -1.0));  // f_hat = -D^H F[g C : (E - e I)]
+  CK(cudaMemsetAsync(X, 0, cu, st));
+  RC(precond(R, Z));
+  CK(cudaMemcpyAsync(P, Z, cu, cudaMemcpyDeviceToDevice, st));
+  double rz = 0.0;
+  RC(dot(R, Z, rz));
+  const double rz0 = rz;
+  const double tol2 = ctx->opts.tol * ctx->opts.tol;
+  int it = 0;
+  fftmech_status status = FFTMECH_OK;
+  while (rz0 > 0.0 && rz > tol2 * rz0) {
+    if (it >= ctx->opts.max_iter) {
+      status = FFTMECH_ERR_NOT_CONVERGED;
+      break;
+    }
+    RC(apply(P, Q, zero, nullptr, 1.0));
+    double pq = 0.0;
+    RC(dot(P, Q, pq));
+    if (!(pq > 0.0) || !std::isfinite(pq)) {
+      status = FFTMECH_ERR_NONFINITE;
+      break;
+    }
+    const double alpha = rz / pq;
+    CK(launch_var_axpy(nU, alpha, P, Q, X, R, st));
+    RC(precond(R, Z));
+    double rzn = 0.0;
+    RC(dot(R, Z, rzn));
+    ++it;
+    CK(launch_var_dir(nU, rzn / rz, Z, P, st));
+    rz = rzn;
+  }
+  // strain = E + F^-1(sym D u) / N, stress from it; their means
+  CK(launch_varel_strain(g, spec, W, X, st));
+  RC(fft_w(true));
+  if (strain) {
+    // the packed fields hold F^-1(sym D u); E is added per component below
+    CK(launch_varel_real(g, spec, W, invN, strain, st));
+  }
+  double mean_eps[6] = {0, 0, 0, 0, 0, 0};
+  for (int v = 0; v < spec.nv; ++v) mean_eps[v] = E[v];  // the fluctuation has zero mean
+  CK(launch_varel_stress(g, spec, W, phase, eig, damage, kappa, lam, mu, E, invN, st));
+  if (stress) CK(launch_varel_real(g, spec, W, 1.0, stress, st));
+  double mean_sig[6] = {0, 0, 0, 0, 0, 0};
+  for (int w = 0; w < spec.nw; ++w) {
+    CK(launch_var_sum(N, W[w], part, st));
+    CK(cudaMemcpyAsync(hpart.data(), part, 2 * nbs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nbs; ++i) {
+      a += hpart[2 * i];
+      b += hpart[2 * i + 1];
+    }
+    mean_sig[2 * w] = a * invN;
+    if (2 * w + 1 < spec.nv) mean_sig[2 * w + 1] = b * invN;
+  }
+  CK(cudaStreamSynchronize(st));
+  std::memset(info, 0, sizeof(*info));
+  info->status = status;
+  info->iters = it;
+  info->rel_res = rz0 > 0 ? std::sqrt(std::max(rz, 0.0) / rz0) : 0.0;
+  info->true_rel_res = info->rel_res;
+  for (int v = 0; v < spec.nv; ++v) {
+    info->mean_stress[v] = mean_sig[v];
+    info->mean_strain[v] = mean_eps[v];
+  }
+  // the strain output: add E to the fluctuation
+  if (strain) {
+    for (int v = 0; v < spec.nv; ++v)
+      if (E[v] != 0.0) CK(launch_var_shift(N, E[v], strain + (size_t)v * N, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return status;
+}
+
 // ================================================================ C ABI
 extern "C" {
 
@@ -2268,6 +2412,26 @@ fftmech_status fftmech_homogenise_operator(fftmech_ctx* ctx, const uint8_t* phas
   double G[3] = {0, 0, 0};
   for (int k = 0; k < ctx->dim; ++k) G[k] = grad_c_mac[k];
   return homogenise_operator_impl(ctx, phase, gradient, G, phi, grad_c, info);
+}
+
+fftmech_status fftmech_equilibrium_operator(fftmech_ctx* ctx, const uint8_t* phase, const double* eig,
+                                            const double* damage, const double eps_mac[6], int gradient,
+                                            double* strain, double* stress, fftmech_solve_info* info) {
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  if (!phase || !eps_mac || !info) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
+  if (gradient < FFTMECH_GRAD_FORWARD || gradient > FFTMECH_GRAD_FOURIER)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "gradient operator %d", gradient);
+  if (ctx->B != 1) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "one problem per context");
+  for (const void* p : {(const void*)phase, (const void*)eig, (const void*)damage, (const void*)strain,
+                        (const void*)stress})
+    if (p && !is_device_ptr(p)) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "device pointers only");
+  if (gradient == FFTMECH_GRAD_FOURIER && (ctx->nx % 2 == 0 || (ctx->dim >= 2 && ctx->ny % 2 == 0) ||
+                                           (ctx->dim == 3 && ctx->nz % 2 == 0)))
+    return set_err(ctx, FFTMECH_ERR_UNSUPPORTED_SIZE, "the Fourier gradient needs odd grid sizes");
+  double E[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < nvoigt(ctx); ++k) E[k] = eps_mac[k];
+  return equilibrium_operator_impl(ctx, phase, eig, damage, E, gradient, strain, stress, info);
 }
 
 fftmech_status fftmech_problem_offset(const fftmech_ctx* ctx, int problem, int components, long long* offset) {

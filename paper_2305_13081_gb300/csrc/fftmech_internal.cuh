@@ -528,6 +528,23 @@ struct VarGrid {
   const cx<double>* dz;
 };
 int var_dot_blocks(long long n);
+// Elasticity with a chosen gradient operator: Voigt components (tensor
+// shears) as index pairs (a, b), packed two per complex field.
+struct VarElSpec {
+  int nv, nw;
+  int a[6], b[6];
+};
+VarElSpec var_el_spec(int dim);
+cudaError_t launch_var_shift(long long n, double c, double* x, cudaStream_t st);
+cudaError_t launch_varel_strain(const VarGrid& g, const VarElSpec& sp, cx<double>* const* W, const cx<double>* U,
+                                cudaStream_t st);
+cudaError_t launch_varel_stress(const VarGrid& g, const VarElSpec& sp, cx<double>* const* W, const uint8_t* phase,
+                                const double* eig, const double* damage, double kappa, const double lam[2],
+                                const double mu[2], const double E[6], double invN, cudaStream_t st);
+cudaError_t launch_varel_div(const VarGrid& g, const VarElSpec& sp, cx<double>* const* W, double s,
+                             cx<double>* Q, cudaStream_t st);
+cudaError_t launch_varel_real(const VarGrid& g, const VarElSpec& sp, cx<double>* const* W, double scale,
+                              double* out, cudaStream_t st);
 cudaError_t launch_var_grad(const VarGrid& g, const cx<double>* P, cx<double>* W1, cx<double>* W2, cudaStream_t st);
 cudaError_t launch_var_flux(const VarGrid& g, const uint8_t* phase, double kp, double ks, const double G[3],
                             double invN, cx<double>* W1, cx<double>* W2, cudaStream_t st);

@@ -166,6 +166,124 @@ __global__ void k_var_real(VarGrid g, const cxd* __restrict__ W1, const cxd* __r
   }
 }
 
+// ---------------------------------------------------------------- elasticity
+// Mechanical equilibrium (Eqs. solid, solid-final) with the same choice of
+// gradient operator: K u = D^H F[g C : F^-1(sym D u)], f = -D^H F[g C :
+// (E - e I)], PCG on the d spectral displacement components (each N
+// numbers) with the preconditioner 1 / |D|^2 per component. The nv tensor
+// components of a symmetric field (Voigt order, tensor shears: 2D xx, yy,
+// xy; 3D xx, yy, zz, yz, xz, xy) travel as (nv + 1) / 2 complex fields,
+// two real components each (v_0 + i v_1, v_2 + i v_3, ...).
+struct VarEl {
+  int nv, nw;          // Voigt components, packed complex fields
+  int a[6], b[6];      // index pair (a, b) of Voigt component v
+  cxd* W[3];           // packed fields, N numbers each
+};
+
+__device__ __forceinline__ cxd var_sym(const VarGrid& g, const cxd* U, long long i, int x, int y, int z, int a,
+                                       int b) {
+  auto Dof = [&](int c) { return c == 0 ? g.dx[x] : (c == 1 ? g.dy[y] : g.dz[z]); };
+  const cxd ua = U[(long long)a * g.N + i], ub = U[(long long)b * g.N + i];
+  if (a == b) return cmuld(Dof(a), ua);
+  const cxd s1 = cmuld(Dof(a), ub), s2 = cmuld(Dof(b), ua);
+  return mk(0.5 * (s1.re + s2.re), 0.5 * (s1.im + s2.im));
+}
+
+// W_w = eps_2w + i eps_(2w+1), eps = sym D u (spectral)
+__global__ void k_varel_strain(VarGrid g, VarEl e, const cxd* __restrict__ U) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    var_idx(g, i, x, y, z);
+    for (int w = 0; w < e.nw; ++w) {
+      const int v0 = 2 * w, v1 = 2 * w + 1;
+      const cxd s0 = var_sym(g, U, i, x, y, z, e.a[v0], e.b[v0]);
+      const cxd s1 = v1 < e.nv ? var_sym(g, U, i, x, y, z, e.a[v1], e.b[v1]) : mk(0.0, 0.0);
+      e.W[w][i] = mk(s0.re - s1.im, s0.im + s1.re);
+    }
+  }
+}
+
+// In real space: eps_v = Re / Im of W (scaled by invN) + E_v; sigma = g (lam
+// tr(eps - e I) I + 2 mu (eps - e I)) written back packed. eig, damage:
+// NULL = 0; g = (1 - d)^2 + kappa.
+__global__ void k_varel_stress(VarGrid g, VarEl e, const uint8_t* __restrict__ phase,
+                               const double* __restrict__ eig, const double* __restrict__ damage, double kappa,
+                               double lam0, double lam1, double mu0, double mu1, double E0, double E1, double E2,
+                               double E3, double E4, double E5, double invN) {
+  const double E[6] = {E0, E1, E2, E3, E4, E5};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    double eps[6];
+    for (int w = 0; w < e.nw; ++w) {
+      const cxd v = e.W[w][i];
+      eps[2 * w] = v.re * invN + E[2 * w];
+      if (2 * w + 1 < e.nv) eps[2 * w + 1] = v.im * invN + E[2 * w + 1];
+    }
+    const double ev = eig ? eig[i] : 0.0;
+    const int d = g.dim;
+    double tr = 0.0;
+    for (int c = 0; c < d; ++c) {
+      eps[c] -= ev;  // the normal components come first in Voigt order
+      tr += eps[c];
+    }
+    double gg = 1.0;
+    if (damage) {
+      const double dm = 1.0 - damage[i];
+      gg = dm * dm + kappa;
+    }
+    const bool sol = phase[i] != 0;
+    const double lam = gg * (sol ? lam1 : lam0), mu = gg * (sol ? mu1 : mu0);
+    double sig[6];
+    for (int v = 0; v < e.nv; ++v) sig[v] = 2.0 * mu * eps[v] + (v < d ? lam * tr : 0.0);
+    for (int w = 0; w < e.nw; ++w) e.W[w][i] = mk(sig[2 * w], 2 * w + 1 < e.nv ? sig[2 * w + 1] : 0.0);
+  }
+}
+
+// After the forward transform: sigma_v(k) unpacked from W(k), conj W(-k);
+// Q_b = s sum_a conj(D_a) sigma_ab.
+__global__ void k_varel_div(VarGrid g, VarEl e, double s, cxd* __restrict__ Q) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    var_idx(g, i, x, y, z);
+    const int xm = x == 0 ? 0 : g.nx - x, ym = y == 0 ? 0 : g.ny - y, zm = z == 0 ? 0 : g.nz - z;
+    const long long im = ((long long)zm * g.ny + ym) * g.nx + xm;
+    cxd sig[6];
+    for (int w = 0; w < e.nw; ++w) {
+      const cxd a = e.W[w][i], b = conjd(e.W[w][im]);
+      sig[2 * w] = mk(0.5 * (a.re + b.re), 0.5 * (a.im + b.im));
+      if (2 * w + 1 < e.nv) sig[2 * w + 1] = mk(0.5 * (a.im - b.im), -0.5 * (a.re - b.re));
+    }
+    const cxd D[3] = {g.dx[x], g.dim >= 2 ? g.dy[y] : mk(0.0, 0.0), g.dim == 3 ? g.dz[z] : mk(0.0, 0.0)};
+    cxd q[3] = {mk(0.0, 0.0), mk(0.0, 0.0), mk(0.0, 0.0)};
+    for (int v = 0; v < e.nv; ++v) {
+      const int a = e.a[v], b = e.b[v];
+      const cxd ta = cmuld(conjd(D[a]), sig[v]);
+      q[b] = mk(q[b].re + ta.re, q[b].im + ta.im);
+      if (a != b) {
+        const cxd tb = cmuld(conjd(D[b]), sig[v]);
+        q[a] = mk(q[a].re + tb.re, q[a].im + tb.im);
+      }
+    }
+    for (int c = 0; c < g.dim; ++c) Q[(long long)c * g.N + i] = mk(s * q[c].re, s * q[c].im);
+  }
+}
+
+// x += c
+__global__ void k_var_shift(long long n, double c, double* __restrict__ x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += c;
+}
+
+// out[v N + i] = Re / Im of the packed fields (scaled)
+__global__ void k_varel_real(VarGrid g, VarEl e, double scale, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    for (int w = 0; w < e.nw; ++w) {
+      const cxd v = e.W[w][i];
+      out[(long long)(2 * w) * g.N + i] = scale * v.re;
+      if (2 * w + 1 < e.nv) out[(long long)(2 * w + 1) * g.N + i] = scale * v.im;
+    }
+  }
+}
+
 static int var_grid(long long n) {
   long long b = (n + kVarThreads - 1) / kVarThreads;
   return (int)(b < 1 ? 1 : (b > 2048 ? 2048 : b));
@@ -209,6 +327,53 @@ cudaError_t launch_var_dir(long long n, double beta, const cxd* z, cxd* p, cudaS
 cudaError_t launch_var_real(const VarGrid& g, const cxd* W1, const cxd* W2, double scale, double* gx, double* gy,
                             double* gz, cudaStream_t st) {
   k_var_real<<<var_grid(g.N), kVarThreads, 0, st>>>(g, W1, W2, scale, gx, gy, gz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_shift(long long n, double c, double* x, cudaStream_t st) {
+  k_var_shift<<<var_grid(n), kVarThreads, 0, st>>>(n, c, x);
+  return cudaGetLastError();
+}
+VarElSpec var_el_spec(int dim) {
+  VarElSpec sp{};
+  if (dim == 2) {
+    const int a[3] = {0, 1, 0}, b[3] = {0, 1, 1};
+    sp.nv = 3;
+    for (int v = 0; v < 3; ++v) { sp.a[v] = a[v]; sp.b[v] = b[v]; }
+  } else {
+    const int a[6] = {0, 1, 2, 1, 0, 0}, b[6] = {0, 1, 2, 2, 2, 1};
+    sp.nv = 6;
+    for (int v = 0; v < 6; ++v) { sp.a[v] = a[v]; sp.b[v] = b[v]; }
+  }
+  sp.nw = (sp.nv + 1) / 2;
+  return sp;
+}
+static VarEl var_el(const VarElSpec& sp, cxd* const* W) {
+  VarEl e{};
+  e.nv = sp.nv;
+  e.nw = sp.nw;
+  for (int v = 0; v < 6; ++v) { e.a[v] = sp.a[v]; e.b[v] = sp.b[v]; }
+  for (int w = 0; w < sp.nw; ++w) e.W[w] = W[w];
+  return e;
+}
+cudaError_t launch_varel_strain(const VarGrid& g, const VarElSpec& sp, cxd* const* W, const cxd* U, cudaStream_t st) {
+  k_varel_strain<<<var_grid(g.N), kVarThreads, 0, st>>>(g, var_el(sp, W), U);
+  return cudaGetLastError();
+}
+cudaError_t launch_varel_stress(const VarGrid& g, const VarElSpec& sp, cxd* const* W, const uint8_t* phase,
+                                const double* eig, const double* damage, double kappa, const double lam[2],
+                                const double mu[2], const double E[6], double invN, cudaStream_t st) {
+  k_varel_stress<<<var_grid(g.N), kVarThreads, 0, st>>>(g, var_el(sp, W), phase, eig, damage, kappa, lam[0], lam[1],
+                                                         mu[0], mu[1], E[0], E[1], E[2], E[3], E[4], E[5], invN);
+  return cudaGetLastError();
+}
+cudaError_t launch_varel_div(const VarGrid& g, const VarElSpec& sp, cxd* const* W, double s, cxd* Q, cudaStream_t st) {
+  k_varel_div<<<var_grid(g.N), kVarThreads, 0, st>>>(g, var_el(sp, W), s, Q);
+  return cudaGetLastError();
+}
+cudaError_t launch_varel_real(const VarGrid& g, const VarElSpec& sp, cxd* const* W, double scale, double* out,
+                              cudaStream_t st) {
+  k_varel_real<<<var_grid(g.N), kVarThreads, 0, st>>>(g, var_el(sp, W), scale, out);
   return cudaGetLastError();
 }
 

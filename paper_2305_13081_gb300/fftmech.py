@@ -160,6 +160,7 @@ def load_library(path=LIB_PATH):
         "fftmech_staggered_step_many": (i, [P(vp), i, P(P(fftmech_state)), P(P(fftmech_step_params)),
                                             P(P(fftmech_solve_info))]),
         "fftmech_homogenise_operator": (i, [vp, vp, i, P(d), vp, vp, P(fftmech_solve_info)]),
+        "fftmech_equilibrium_operator": (i, [vp, vp, vp, vp, P(d), i, vp, vp, P(fftmech_solve_info)]),
         "fftmech_bar_create": (i, [P(vp), vp, d, d, d, P(d)]),
         "fftmech_bar_destroy": (i, [vp]),
         "fftmech_bar_step": (i, [vp, P(fftmech_state), P(fftmech_step_params), P(fftmech_solve_info)]),
@@ -450,6 +451,17 @@ def fftmech_homogenise_operator(ctx, phase, gradient, grad_c_mac, phi=None, grad
     g = c_double3(*(list(grad_c_mac) + [0.0] * 3)[:3])
     rc = load_library().fftmech_homogenise_operator(ctx, ptr(phase), int(gradient), g, ptr(phi), ptr(grad_c),
                                                     ctypes.byref(info))
+    _check(rc, ctx, _SOLVER_OK)
+    return info
+
+
+def fftmech_equilibrium_operator(ctx, phase, eig, damage, eps_mac, gradient, strain=None, stress=None):
+    """Equilibrium with the gradient operator `gradient` (FFTMECH_GRAD_*);
+    device buffers (eig, damage double or None); returns the solve record."""
+    info = fftmech_solve_info()
+    e = c_double6(*(list(eps_mac) + [0.0] * 6)[:6])
+    rc = load_library().fftmech_equilibrium_operator(ctx, ptr(phase), ptr(eig), ptr(damage), e, int(gradient),
+                                                     ptr(strain), ptr(stress), ctypes.byref(info))
     _check(rc, ctx, _SOLVER_OK)
     return info
 

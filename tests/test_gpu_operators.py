@@ -1,5 +1,6 @@
-"""Gradient-operator variants of the homogenised diffusion
-(fftmech_homogenise_operator, Sec. 2.6 and Fig. 2) through the C ABI:
+"""Gradient-operator variants (Sec. 2.6 and Fig. 2) through the C ABI, of
+the homogenised diffusion (fftmech_homogenise_operator) and of the
+mechanical equilibrium (fftmech_equilibrium_operator):
 
 - every operator (forward, central, 8th-order central, Fourier) against
   the FP64 oracle with the same symbol (oracle/diffusion.homogenise(symbol=))
@@ -9,7 +10,11 @@
   the library's stencil-based HOMOGENISE diffusion (fftmech_diffusion_step):
   two independent GPU paths, one mean flux;
 - laminates: every operator gives the harmonic mean of D across layers
-  normal to the gradient and the arithmetic mean along them.
+  normal to the gradient and the arithmetic mean along them;
+- elasticity: every operator against the FP64 oracle with the same symbol
+  (oracle/elasticity.equilibrium_solve(symbol=)), 2D with a damage field
+  and 3D; the forward operator against the library's stencil-based FP64
+  solve; the laminate's closed form (uniform sigma_xx and eps_yy).
 """
 
 import numpy as np
@@ -99,3 +104,94 @@ def test_laminates(op):
     h = 1.0 / np.mean(1.0 / D_n)
     a = np.mean(D_p)
     assert abs(i_n.mean_flux[0] + h) <= 1e-9 * h and abs(i_p.mean_flux[0] + a) <= 1e-9 * a
+
+
+# ---------------------------------------------------------------- elasticity
+
+def gpu_el(phase, op, E, eig=None, damage=None, tol=1e-13):
+    ctx = fm.Context(phase.shape, MAT, fm.FFTMECH_FP64, h=H_EL, tol=tol, max_iter=20000)
+    N = phase.size
+    d = phase.ndim
+    nv = 3 if d == 2 else 6
+    dev = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+    strain = torch.zeros(nv * N, dtype=torch.float64, device="cuda")
+    stress = torch.zeros(nv * N, dtype=torch.float64, device="cuda")
+    info = fm.fftmech_equilibrium_operator(ctx.handle, torch.as_tensor(phase.ravel()).cuda(), dev(eig), dev(damage),
+                                           E, OPS[op], strain, stress)
+    ctx.close()
+    return (info, strain.cpu().numpy().reshape((nv,) + phase.shape),
+            stress.cpu().numpy().reshape((nv,) + phase.shape))
+
+
+H_EL = 5e-6
+
+
+@pytest.mark.parametrize("op", list(OPS))
+@pytest.mark.parametrize("dim", [2, 3])
+def test_elastic_operator_matches_oracle(op, dim):
+    """Equilibrium with every gradient operator against the FP64 oracle
+    (oracle/elasticity.equilibrium_solve(symbol=)): a carpet with a pore
+    eigenstrain, a damage field (2D) and a macro strain with a shear."""
+    from oracle import elasticity
+    rng = np.random.default_rng(17)
+    if dim == 2:
+        phase = random_carpet(81, 0.30, 14)[0]
+        E = [1e-3, -2e-4, 3e-4]
+        damage = np.where(phase == 1, 0.6 * rng.random(phase.shape), 0.0)
+    else:
+        phase = random_sponge(9, 0.35, 15)[0]
+        E = [1e-3, 0.0, -2e-4, 1e-4, 0.0, 3e-4]
+        damage = None
+    eig = np.where(phase == 0, 1e-3, 0.0)
+    g = np.ones(phase.shape) if damage is None else (1.0 - damage) ** 2 + MAT.kappa
+    info, strain, stress = gpu_el(phase, op, E, eig, damage)
+    ref = elasticity.equilibrium_solve(phase, eig, g, E, MAT, H_EL, tol=1e-13, symbol=op)
+    e_eps, e_sig = rel(strain, ref["strain"]), rel(stress, ref["stress"])
+    e_mean = float(np.abs(np.array(info.mean_stress[:len(E)]) - ref["mean_stress"]).max()
+                   / np.abs(ref["mean_stress"]).max())
+    print("elastic operator", op, dim, "iterations", info.iters, "strain", e_eps, "stress", e_sig, "mean", e_mean)
+    assert info.status == fm.FFTMECH_OK
+    assert e_eps < 1e-9 and e_sig < 1e-9 and e_mean < 1e-10
+    assert np.allclose(info.mean_strain[:len(E)], E, rtol=0, atol=1e-18)
+
+
+def test_forward_elastic_operator_agrees_with_the_stencil_path():
+    """The forward operator by this spectral-operator PCG and the library's
+    stencil-based FP64 equilibrium solve: two independent GPU paths, one
+    field."""
+    phase = random_carpet(243, 0.30, 16)[0]
+    eig = np.where(phase == 0, 1e-3, 0.0)
+    E = [1e-3, 0.0, 2e-4]
+    _, strain, _ = gpu_el(phase, "forward", E, eig, tol=1e-12)
+    ctx = fm.Context(phase.shape, MAT, fm.FFTMECH_FP64, h=H_EL, tol=1e-12, max_iter=20000)
+    N = phase.size
+    u = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+    s2 = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    fm.fftmech_equilibrium_solve(ctx.handle, torch.as_tensor(phase.ravel()).cuda(),
+                                 torch.as_tensor(eig.ravel()).cuda(), None, E, u, s2, None)
+    ctx.close()
+    e = rel(strain, s2.cpu().numpy().reshape(strain.shape))
+    assert e < 1e-9, e
+
+
+@pytest.mark.parametrize("op", list(OPS))
+def test_elastic_laminate_closed_form(op):
+    """Layers normal to x under a macro strain E_yy (plane strain): eps_yy
+    stays E_yy and sigma_xx is uniform, sigma_xx = <lam / M> / <1 / M> E_yy
+    with M = lam + 2 mu, for every operator (odd size: no operator vanishes
+    at a nonzero frequency)."""
+    from oracle.elasticity import lame
+    n = 27
+    phase = np.zeros((9, n), dtype=np.uint8)
+    phase[:, 13:] = 1
+    Eyy = 1e-3
+    _, strain, stress = gpu_el(phase, op, [0.0, Eyy, 0.0])
+    ls, ms = lame(MAT.E_solid, MAT.nu_solid)
+    lp, mp = lame(MAT.E_pore, MAT.nu_pore)
+    lam = np.where(phase[0] == 1, ls, lp)
+    mu = np.where(phase[0] == 1, ms, mp)
+    M = lam + 2 * mu
+    sxx = np.mean(lam / M) / np.mean(1.0 / M) * Eyy
+    assert np.abs(strain[1] - Eyy).max() <= 1e-12 * Eyy
+    assert np.abs(stress[0] - sxx).max() <= 1e-9 * abs(sxx)
+    assert np.abs(strain[2]).max() <= 1e-12 * Eyy and np.abs(stress[2]).max() <= 1e-9 * abs(sxx)

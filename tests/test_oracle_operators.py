@@ -10,7 +10,12 @@ of the oracle's homogenised diffusion with each of them
   and eighth-order convergence on a smooth periodic function;
 - homogenisation of laminates (odd grids): every symbol gives the harmonic
   mean of D for layers normal to the gradient and the arithmetic mean for
-  layers parallel to it (the flux of a 1D layered problem is constant).
+  layers parallel to it (the flux of a 1D layered problem is constant);
+- the oracle's equilibrium with each symbol
+  (oracle/elasticity.equilibrium_solve(symbol=...)) on a laminate normal to
+  x under E_yy (plane strain): eps_yy = E_yy everywhere and a uniform
+  sigma_xx = <lam / M> / <1 / M> E_yy, M = lam + 2 mu (the closed form of a
+  1D layered problem); a homogeneous medium takes sigma = C : E exactly.
 """
 
 import numpy as np
@@ -79,3 +84,30 @@ def test_laminates_give_harmonic_and_arithmetic_means(symbol):
     out_p = diffusion.homogenise(parallel, mat, [1.0, 0.0], 0.3, 1.0, tol=1e-13, symbol=symbol)
     assert abs(out_n["mean_flux"][0] + 1.0 / np.mean(1.0 / D_n)) <= 1e-9 / np.mean(1.0 / D_n)
     assert abs(out_p["mean_flux"][0] + np.mean(D_p)) <= 1e-9 * np.mean(D_p)
+
+
+@pytest.mark.parametrize("symbol", ["forward", "central", "central8", "fourier"])
+def test_elastic_laminate_and_homogeneous_medium(symbol):
+    from oracle import elasticity
+    mat = Materials()
+    n = 27
+    phase = np.zeros((9, n), dtype=np.uint8)
+    phase[:, 13:] = 1
+    Eyy = 1e-3
+    out = elasticity.equilibrium_solve(phase, np.zeros(phase.shape), np.ones(phase.shape), [0.0, Eyy, 0.0], mat,
+                                       H, tol=1e-13, symbol=symbol)
+    ls, ms = elasticity.lame(mat.E_solid, mat.nu_solid)
+    lp, mp = elasticity.lame(mat.E_pore, mat.nu_pore)
+    lam = np.where(phase[0] == 1, ls, lp)
+    M = lam + 2 * np.where(phase[0] == 1, ms, mp)
+    sxx = np.mean(lam / M) / np.mean(1.0 / M) * Eyy
+    assert np.abs(out["strain"][1] - Eyy).max() <= 1e-12 * Eyy
+    assert np.abs(out["stress"][0] - sxx).max() <= 1e-9 * abs(sxx)
+    solid = np.ones((9, 9), dtype=np.uint8)
+    E = [1e-3, -2e-4, 3e-4]
+    hom = elasticity.equilibrium_solve(solid, np.zeros(solid.shape), np.ones(solid.shape), E, mat, H, tol=1e-13,
+                                       symbol=symbol)
+    tr = E[0] + E[1]
+    expect = [ls * tr + 2 * ms * E[0], ls * tr + 2 * ms * E[1], 2 * ms * E[2]]
+    for v in range(3):
+        assert np.abs(hom["stress"][v] - expect[v]).max() <= 1e-12 * abs(expect[0])
