@@ -136,15 +136,16 @@ typedef struct {
  * the next iteration's stencil as one kernel (the same iterates up to the
  * summation order of <p, K p>); clear (default) keeps them apart.
  * fftmech_autotune times both and its choice then replaces bit 1.
- * precond: preconditioner of the 2D equilibrium PCG. FFTMECH_PRECOND_LAPLACE
+ * precond: preconditioner of the equilibrium PCG. FFTMECH_PRECOND_LAPLACE
  * (0, default): F^-1 (1 / |D|^2) F per component, the projection of App. A
  * (Eq. g-42). FFTMECH_PRECOND_REFERENCE (1): the inverse of the Galerkin
- * operator of a homogeneous isotropic reference medium, per mode the 2 x 2
- * Hermitian matrix |D|^2 I + rho conj(D) D^T + D conj(D)^T inverted, with
- * rho = lambda / mu of the solid (the Moulinec-Suquet reference medium the
- * paper names as the classical scheme's preconditioner, Sec. 1; exact for a
- * homogeneous medium of that Poisson ratio). Same solution, fewer
- * iterations; diffusion, phase-field and 3D solves keep the Laplace one. */
+ * operator of a homogeneous isotropic reference medium, per mode the d x d
+ * Hermitian matrix |D|^2 I + rho conj(D) D^T + D conj(D)^T inverted (2D in
+ * the column pass, 3D in the z pass), with rho = lambda / mu of the solid
+ * (the Moulinec-Suquet reference medium the paper names as the classical
+ * scheme's preconditioner, Sec. 1; exact for a homogeneous medium of that
+ * Poisson ratio). Same solution, fewer iterations; diffusion and
+ * phase-field solves keep the Laplace one. */
 enum { FFTMECH_EXEC_GRAPH = 0, FFTMECH_EXEC_HOST = 1 };
 enum { FFTMECH_PRECOND_LAPLACE = 0, FFTMECH_PRECOND_REFERENCE = 1 };
 typedef struct {

@@ -168,6 +168,7 @@ struct fftmech_ctx {
   double* phi = nullptr;
   double* Hd = nullptr;
   double* cn = nullptr;
+  void* az = nullptr;     // 3D: D h along z (reference-medium preconditioner)
   void* lamx = nullptr;
   void* lamy = nullptr;
   void* lamz = nullptr;     // 3D: lambda_z(kz)
@@ -179,6 +180,7 @@ struct fftmech_ctx {
   void* ay = nullptr;       // 2D: D h per row ky (complex)
   double rho = 0;           // lambda / mu of the solid (reference medium)
   int ms_cw = 0, ms_threads = 0;  // reference-medium column pass: strip width, threads (0: unavailable)
+  int ms3_cw = 0, ms3_threads = 0;  // reference-medium z pass (3D): strip width, threads (0: unavailable)
   double* partials = nullptr;
   double* partials_col = nullptr;  // 2D column pass (deferred reductions)
   double* m0b = nullptr;       // per-problem preconditioner constants
@@ -399,19 +401,22 @@ fftmech_status fill_lam(fftmech_ctx* ctx) {
   for (int k = 0; k < ctx->ny; ++k) ly[k] = sym(k, ctx->ny);
   CK(cudaMemcpy(ctx->lamx, lx.data(), sizeof(T) * ctx->nx, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->lamy, ly.data(), sizeof(T) * ctx->ny, cudaMemcpyHostToDevice));
-  if (ctx->dim == 2) {
-    // D h = e^{i theta} - 1 per mode (reference-medium preconditioner)
+  {
+    // D h = e^{i theta} - 1 per mode (reference-medium preconditioner):
+    // columns 0 .. nx / 2 along x, every frequency along y and z
     auto dh = [](int k, int n, T* out) {
       const double th = 2.0 * M_PI * k / n;
       out[0] = (T)(std::cos(th) - 1.0);
       out[1] = (T)std::sin(th);
     };
     const int H = ctx->nx / 2 + 1;
-    std::vector<T> ax(2 * H), ay(2 * ctx->ny);
+    std::vector<T> ax(2 * H), ay(2 * ctx->ny), az(2 * ctx->nz);
     for (int k = 0; k < H; ++k) dh(k, ctx->nx, &ax[2 * k]);
     for (int k = 0; k < ctx->ny; ++k) dh(k, ctx->ny, &ay[2 * k]);
+    for (int k = 0; k < ctx->nz; ++k) dh(k, ctx->nz, &az[2 * k]);
     CK(cudaMemcpy(ctx->ax, ax.data(), sizeof(T) * ax.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->ay, ay.data(), sizeof(T) * ay.size(), cudaMemcpyHostToDevice));
+    if (ctx->dim == 3) CK(cudaMemcpy(ctx->az, az.data(), sizeof(T) * az.size(), cudaMemcpyHostToDevice));
   }
   if (ctx->dim == 3) {
     const int nx = ctx->nx, nxh = nx / 2 + 1;
@@ -630,11 +635,13 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
   // direction to pn, and the update kernel, which reads it, copies it back
   // to p for the next direction
   const bool fused = defer && ds_active(ctx);
-  // reference-medium preconditioner: 2D elasticity only
+  // reference-medium preconditioner: elasticity (2D column pass, 3D z pass)
   const bool ms = D == 2 && !three && ctx->opts.precond == FFTMECH_PRECOND_REFERENCE && ctx->ms_cw > 0;
-  if (ms) {
+  const bool ms3 = D == 3 && three && ctx->opts.precond == FFTMECH_PRECOND_REFERENCE && ctx->ms3_cw > 0;
+  if (ms || ms3) {
     sp.ax = (const cx<T>*)ctx->ax;
     sp.ay = (const cx<T>*)ctx->ay;
+    sp.az = (const cx<T>*)ctx->az;
     sp.rho_t = (T)ctx->rho;
   }
   const int ncol_blocks = !defer ? 0
@@ -697,7 +704,9 @@ fftmech_status emit_pcg(Emit& em, const Op<T>& op_in, double* u, const Spec<T>& 
                                  st);
     cudaError_t e = launch3_lines_f<T>(fy, v.S, sh3, D, 1, 0, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
     if (e != cudaSuccess) return e;
-    e = launch3_lines_f<T>(fz, v.S, sh3, D, 2, 1, pz, sp, mode, ctx->partials, ctx->sc, ctx->mode, st);
+    e = ms3 ? launch3_zpass_ms_f<T>(fz, v.S, sh3.sst, ctx->nx, ctx->ny, ctx->nz, (int)nxs_of(ctx->nx, 3), pz, sp,
+                                    ctx->ms3_cw, ctx->ms3_threads, B, mode, ctx->partials, ctx->sc, ctx->mode, st)
+            : launch3_lines_f<T>(fz, v.S, sh3, D, 2, 1, pz, sp, mode, ctx->partials, ctx->sc, ctx->mode, st);
     if (e != cudaSuccess || mode == COL_NORM || mode == COL_TRUENORM) return e;
     return launch3_lines_f<T>(fy, v.S, sh3, D, 1, 2, py, sp, mode, nullptr, ctx->sc, ctx->mode, st);
   };
@@ -2174,6 +2183,21 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
         ctx->ms_threads = std::min(512, std::max(128, round32(thr)));
       }
     }
+  } else {
+    // reference-medium z pass: the widest strip (4, 2 or 1 columns, six
+    // slots of them) that fits the shared memory and 512 threads
+    const int es2 = fp64 ? 16 : 8;
+    for (int cw = 4; cw >= 1 && !ctx->ms3_cw; cw /= 2) {
+      const size_t sm = zpass_ms_smem(ctx->nz, cw, es2,
+                                      fp64 ? tw_smem_bytes<double>(ctx->nz) : tw_smem_bytes<float>(ctx->nz));
+      const int thr = need_threads(ctx->pz, 6 * cw);
+      if (sm + 1024 <= ctx->optin && thr <= 512) {
+        ctx->ms3_cw = cw;
+        ctx->ms3_threads = std::min(512, std::max(128, round32(thr)));
+      }
+    }
+  }
+  {
     double l1, m1s;
     lame(mat->E_solid, mat->nu_solid, l1, m1s);
     ctx->rho = l1 / m1s;
@@ -2196,6 +2220,7 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   if (three) {
     const Shape3& t = ctx->shape3;
     widest = (size_t)ctx->ny * ((nxs_of(ctx->nx, 3) + t.cw_z - 1) / t.cw_z);  // z-pass blocks
+    if (ctx->ms3_cw > 0) widest = std::max(widest, (size_t)zpass_ms_blocks(ctx->nx, ctx->ny, ctx->ms3_cw));
   } else {
     widest = (ctx->nx + ctx->shape.cols - 1) / ctx->shape.cols;  // column strips
   }
@@ -2229,11 +2254,10 @@ fftmech_status fftmech_create_batched(fftmech_ctx** out, const fftmech_grid* gri
   alloc((void**)&ctx->cn, NB * 8);
   alloc(&ctx->lamx, ctx->nx * es);
   alloc(&ctx->lamy, ctx->ny * es);
-  if (!three) {
-    alloc(&ctx->ax, (size_t)(ctx->nx / 2 + 1) * 2 * es);
-    alloc(&ctx->ay, (size_t)ctx->ny * 2 * es);
-  }
+  alloc(&ctx->ax, (size_t)(ctx->nx / 2 + 1) * 2 * es);
+  alloc(&ctx->ay, (size_t)ctx->ny * 2 * es);
   if (three) {
+    alloc(&ctx->az, (size_t)ctx->nz * 2 * es);
     alloc(&ctx->lamz, ctx->nz * es);
     alloc(&ctx->lamc3, (size_t)nxs_of(ctx->nx, 3) * es);
     alloc(&ctx->wcol3, (size_t)nxs_of(ctx->nx, 3) * es);
@@ -2272,7 +2296,7 @@ fftmech_status fftmech_destroy(fftmech_ctx* ctx) {
     if (c.exec) cudaGraphExecDestroy(c.exec);
   void* bufs[] = {ctx->r, ctx->q, ctx->p, ctx->pn, ctx->S, ctx->g, ctx->uh, ctx->ul, ctx->phi, ctx->Hd,
                   ctx->cn, ctx->lamx, ctx->lamy, ctx->lamz, ctx->lamc3, ctx->lamc1, ctx->wcol3, ctx->wcol1,
-                  ctx->ax, ctx->ay,
+                  ctx->ax, ctx->ay, ctx->az,
                   ctx->partials, ctx->partials_col, ctx->m0b, ctx->m1b, ctx->mode, ctx->sc, ctx->flags, ctx->rec};
   for (void* b : bufs)
     if (b) cudaFree(b);

@@ -254,10 +254,11 @@ struct Spec {
   const T* laml;
   const T* wcol;
   T m0_t, m1_t, invN_t;  // m0, m1, invN rounded to T by the host
-  // reference-medium preconditioner (2D elasticity; NULL = Laplace): D h per
-  // mode along x (columns 0 .. nx / 2) and y, and lambda0 / mu0
+  // reference-medium preconditioner (elasticity; NULL = Laplace): D h per
+  // mode along x (columns 0 .. nx / 2), y and z (3D), and lambda0 / mu0
   const cx<T>* ax;
   const cx<T>* ay;
+  const cx<T>* az;
   T rho_t;
 };
 
@@ -381,6 +382,15 @@ inline cudaError_t launch_colpass_f(int fy, int nx, int ny, cx<T>* S, const FftP
 // Column pass with the reference-medium preconditioner (colpass_ms.cu): one
 // block per strip of CW columns kx <= nx / 2 and their mirrors nx - kx.
 inline int colpass_ms_blocks(int nx, int CW) { return (nx / 2 + 1 + CW - 1) / CW; }
+// z pass with the reference-medium preconditioner (zpass_ms.cu, 3D): one
+// block per pair of line sets (ky, ny - ky) and strip of CW columns
+// kx <= nx / 2; shared memory for nz rows of six CW-column slots.
+int zpass_ms_blocks(int nx, int ny, int CW);
+size_t zpass_ms_smem(int nz, int CW, int es_complex, size_t tw);
+template <typename T>
+cudaError_t launch3_zpass_ms_f(int fz, cx<T>* S, long long sst, int nx, int ny, int nz, int nxs,
+                               const FftPlanDev<T>& pz, const Spec<T>& sp, int CW, int threads, int batch, int mode,
+                               double* partials, SolverScalars* sc, int* pmode, cudaStream_t st);
 template <typename T>
 cudaError_t launch_colpass_ms_f(int fy, int nx, int ny, cx<T>* S, const FftPlanDev<T>& py, const Spec<T>& sp,
                                 int CW, int threads, int batch, int mode, double* partials, SolverScalars* sc,
