@@ -524,11 +524,24 @@ def sponge_entry(args, torch, fm, device, rank, flush, hbm_peak, peak_src):
     dev_s = sum(run["ms"]) / 1e3
     kernels, roofline = roofline_of(prof, w.voxels, 4, 3, hbm_peak, peak_src, workload_name(w),
                                     1e3 * dev_s / args.extra_steps, "achieved counts algorithmic bytes")
-    return {"value": vi_of(run, w.voxels) / dev_s, "unit": UNIT, "steps": args.extra_steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dev_s / args.extra_steps, "voxels": w.voxels, "gpu_launches": run["launches"],
-            "kernels": kernels, "roofline": roofline, "clocks": clocks,
-            "config": {"workload": workload_name(w), "seed": w.extra["seed"], "porosity": w.extra["porosity"],
-                       "precision": "mixed", "tol": w.tol}}
+    out = {"value": vi_of(run, w.voxels) / dev_s, "unit": UNIT, "steps": args.extra_steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dev_s / args.extra_steps, "voxels": w.voxels, "gpu_launches": run["launches"],
+           "kernels": kernels, "roofline": roofline, "clocks": clocks,
+           "config": {"workload": workload_name(w), "seed": w.extra["seed"], "porosity": w.extra["porosity"],
+                      "precision": "mixed", "tol": w.tol}}
+    if not args.no_precond:
+        # the reference-medium preconditioner (3D z pass) on the same steps
+        ref = run_arm(torch, fm, w, fm.FFTMECH_MIXED, args.extra_steps, args.warmup, device, flush=flush,
+                      precond=fm.FFTMECH_PRECOND_REFERENCE)
+        eq_it = lambda r: sum(inf[3 * b + 1]["iters"] for inf in r["infos"] for b in range(len(inf) // 3))
+        errs = {k: float(np.linalg.norm(ref["state"][k] - run["state"][k]) / np.linalg.norm(run["state"][k]))
+                for k in ("strain", "stress")}
+        out["precond_reference"] = {
+            "ms_per_step": float(np.mean(ref["ms"])), "laplace_ms_per_step": float(np.mean(run["ms"])),
+            "equilibrium_iters": eq_it(ref), "laplace_equilibrium_iters": eq_it(run),
+            "fields_vs_laplace_rel": errs,
+            "note": "Moulinec-Suquet reference medium (lambda/mu of the solid) in the 3D equilibrium z pass"}
+    return out
 
 
 # ---------------------------------------------------------------- cuFFT comparison
