@@ -614,7 +614,9 @@ def operator_comparison(torch, fm, device, w):
     the mean flux, and the ringing of the flux j_x: the mean |second
     difference along x| over pore voxels whose x neighbours are pores,
     relative to the mean |j_x| there. Then the same for sigma_xx of the
-    equilibrium under eps_mac = 1e-2 xx (fftmech_equilibrium_operator)."""
+    equilibrium under eps_mac = 1e-2 xx (fftmech_equilibrium_operator) and
+    for the damage of the phase field driven by that strain
+    (fftmech_phasefield_operator), each with the operator."""
     from microstructures.workloads import Materials
     phase = w.phase
     mat = Materials()
@@ -647,6 +649,9 @@ def operator_comparison(torch, fm, device, w):
     solid = phase == 1
     inner_s = solid & np.roll(solid, 1, axis=1) & np.roll(solid, -1, axis=1)
     sig = torch.zeros(3 * N, dtype=torch.float64, device=device)
+    eps = torch.zeros(3 * N, dtype=torch.float64, device=device)
+    Hf = torch.zeros(N, dtype=torch.float64, device=device)
+    dmg = torch.zeros(N, dtype=torch.float64, device=device)
     for name, op in (("forward", fm.FFTMECH_GRAD_FORWARD), ("central", fm.FFTMECH_GRAD_CENTRAL),
                      ("central8", fm.FFTMECH_GRAD_CENTRAL8), ("fourier", fm.FFTMECH_GRAD_FOURIER)):
         ctx = fm.Context(phase.shape, mat, fm.FFTMECH_FP64, h=w.h, tol=1e-8, max_iter=20000,
@@ -654,15 +659,22 @@ def operator_comparison(torch, fm, device, w):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        info = fm.fftmech_equilibrium_operator(ctx.handle, ph, None, None, [1e-2, 0.0, 0.0], op, None, sig)
+        info = fm.fftmech_equilibrium_operator(ctx.handle, ph, None, None, [1e-2, 0.0, 0.0], op, eps, sig)
         e1.record(stream)
         e1.synchronize()
+        # the damage panel: history from this strain and the phase field with the same operator
+        Hf.zero_()
+        pinfo = fm.fftmech_phasefield_operator(ctx.handle, ph, eps, None, op, Hf, dmg)
         ctx.close()
         sxx = sig[:N].cpu().numpy().reshape(phase.shape)
         d2 = np.abs(np.roll(sxx, -1, axis=1) - 2 * sxx + np.roll(sxx, 1, axis=1))
+        dd = dmg.cpu().numpy().reshape(phase.shape)
+        dd2 = np.abs(np.roll(dd, -1, axis=1) - 2 * dd + np.roll(dd, 1, axis=1))
         out[name].update({"elastic_iters": info.iters, "elastic_ms": e0.elapsed_time(e1),
                           "mean_stress_xx": info.mean_stress[0],
-                          "stress_ringing": float(d2[inner_s].mean() / np.abs(sxx[solid]).mean())})
+                          "stress_ringing": float(d2[inner_s].mean() / np.abs(sxx[solid]).mean()),
+                          "phasefield_iters": pinfo.iters, "mean_damage": pinfo.total_damage / N,
+                          "damage_ringing": float(dd2[inner_s].mean() / max(np.abs(dd[solid]).mean(), 1e-300))})
     return out
 
 

@@ -431,6 +431,21 @@ fftmech_status fftmech_equilibrium_operator(fftmech_ctx* ctx, const uint8_t* pha
                                             const double* damage, const double eps_mac[6], int gradient,
                                             double* strain, double* stress, fftmech_solve_info* info);
 
+/* History update and AT2 phase field with a choice of gradient operator
+ * (Eqs. energy, crack and crack-fft with the symbol of Sec. 2.6; the damage
+ * panels of Fig. 2): H = max(H, psi+(strain - e I)), then
+ * (a + H) d + b F^-1(|D|^2 F d) = H, a = Gc / (2 l0), b = Gc l0 / 2, by
+ * PCG on the spectrum of d with the preconditioner 1 / (a + <H> + b |D|^2),
+ * gradient one of FFTMECH_GRAD_* (FOURIER: odd grid sizes only). FP64;
+ * host-driven; one problem per context; allocates temporary device
+ * buffers. phase: uint8 [N]; strain: double [nv N] (Voigt, tensor shears);
+ * eig: double [N] or NULL; H: double [N], updated in place; d: double [N]
+ * output (device pointers). info: iterations, residual, total_damage (the
+ * sum of d over the voxels). */
+fftmech_status fftmech_phasefield_operator(fftmech_ctx* ctx, const uint8_t* phase, const double* strain,
+                                           const double* eig, int gradient, double* H, double* d,
+                                           fftmech_solve_info* info);
+
 /* Element offset of problem `problem`'s segment in a field with
  * `components` components per voxel (1 for scalar fields, dim for u, 3 or
  * 6 for strain and stress) of a batched context: problem * components * N. */

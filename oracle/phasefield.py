@@ -34,11 +34,13 @@ def degradation(d, kappa):
     return (1.0 - d) ** 2 + kappa
 
 
-def phasefield_solve(H, mat, h, tol=1e-12, max_iter=200000, d0=None):
-    """Solve Eq. (crack-fft) for d given the history field H."""
+def phasefield_solve(H, mat, h, tol=1e-12, max_iter=200000, d0=None, symbol="forward"):
+    """Solve Eq. (crack-fft) for d given the history field H. symbol: the
+    gradient operator of Sec. 2.6 (spectral.SYMBOLS; the paper's results use
+    the forward difference)."""
     H = np.asarray(H, dtype=np.float64)
     a, b = coefficients(mat)
-    D = spectral.forward_difference_symbol(H.shape, h)
+    D = spectral.SYMBOLS[symbol](H.shape, h)
     lam = spectral.symbol_norm2(D)
 
     def A(x):

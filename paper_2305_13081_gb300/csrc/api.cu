@@ -2072,6 +2072,120 @@ fftmech_status equilibrium_operator_impl(fftmech_ctx* ctx, const uint8_t* phase,
   return status;
 }
 
+// AT2 phase field with a chosen gradient operator (Eqs. crack, crack-fft with
+// the symbol of Sec. 2.6): the history update of the library, then PCG on
+// the spectrum of d. FP64, host-driven, one problem.
+fftmech_status phasefield_operator_impl(fftmech_ctx* ctx, const uint8_t* phase, const double* strain,
+                                        const double* eig, int op, double* H, double* d, fftmech_solve_info* info) {
+  using cxd = cx<double>;
+  cudaStream_t st = ctx->stream;
+  const int nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, dim = ctx->dim;
+  const long long N = ctx->N;
+  const size_t cb = (size_t)N * sizeof(cxd);
+  DevBuffers mem;
+  cxd* P = mem.get<cxd>(cb);
+  cxd* R = mem.get<cxd>(cb);
+  cxd* X = mem.get<cxd>(cb);
+  cxd* Z = mem.get<cxd>(cb);
+  cxd* Q = mem.get<cxd>(cb);
+  cxd* W = mem.get<cxd>(cb);
+  double* Hd = mem.get<double>((size_t)N * sizeof(double));
+  cxd* dx = mem.get<cxd>((size_t)nx * sizeof(cxd));
+  cxd* dy = mem.get<cxd>((size_t)ny * sizeof(cxd));
+  cxd* dz = mem.get<cxd>((size_t)nz * sizeof(cxd));
+  const int nb = var_dot_blocks(N);
+  double* part = mem.get<double>((size_t)2 * nb * sizeof(double));
+  if (!mem.ok) return set_err(ctx, FFTMECH_ERR_OOM, "operator-variant buffers");
+  const double h = ctx->h;
+  const auto tx = grad_symbol(op, nx, h), ty = grad_symbol(op, ny, h), tz = grad_symbol(op, nz, h);
+  CK(cudaMemcpyAsync(dx, tx.data(), nx * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dy, ty.data(), ny * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dz, tz.data(), nz * sizeof(cxd), cudaMemcpyHostToDevice, st));
+  const VarGrid g{nx, ny, nz, dim, N, dx, dy, dz};
+  const double invN = 1.0 / (double)N;
+  const double a = ctx->mat.Gc / (2.0 * ctx->mat.l0), b = ctx->mat.Gc * ctx->mat.l0 / 2.0;
+  double lam[2], mu[2];
+  lame(ctx->mat.E_pore, ctx->mat.nu_pore, lam[0], mu[0]);
+  lame(ctx->mat.E_solid, ctx->mat.nu_solid, lam[1], mu[1]);
+  // H = max(H, psi+(strain - e I)) (Eq. energy); m0 = a + <H>
+  if (dim == 3)
+    CK(launch3_history<double>(N, 1, phase, lam[0], lam[1], mu[0], mu[1], strain, eig, H, Hd, a, ctx->m0b,
+                               ctx->partials, ctx->sc, st));
+  else
+    CK(launch_history<double>(N, 1, phase, lam[0], lam[1], mu[0], mu[1], strain, eig, H, Hd, a, ctx->m0b,
+                              ctx->partials, ctx->sc, st));
+  double m0 = 0.0;
+  CK(cudaMemcpyAsync(&m0, ctx->m0b, sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<double> hpart(2 * nb);
+  auto fft = [&](cxd* v, bool inv) -> fftmech_status { return fft_inplace(nx, ny, nz, true, inv, v, st); };
+  auto dot = [&](const cxd* x, const cxd* y, double& out) -> fftmech_status {
+    CK(launch_var_dot(N, x, y, part, st));
+    CK(cudaMemcpyAsync(hpart.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out = 0.0;
+    for (int i = 0; i < nb; ++i) out += hpart[i];
+    return FFTMECH_OK;
+  };
+  // q = F[(a + H) F^-1(p) / N] + b |D|^2 p
+  auto apply = [&](const cxd* p, cxd* q) -> fftmech_status {
+    CK(cudaMemcpyAsync(W, p, cb, cudaMemcpyDeviceToDevice, st));
+    RC(fft(W, true));
+    CK(launch_varpf_react(N, Hd, a, invN, W, st));
+    RC(fft(W, false));
+    CK(launch_varpf_sum(g, b, W, p, q, st));
+    return FFTMECH_OK;
+  };
+  CK(launch_varpf_load(N, Hd, R, st));  // f_hat = F[H]
+  RC(fft(R, false));
+  CK(cudaStreamSynchronize(st));  // m0 on the host
+  CK(cudaMemsetAsync(X, 0, cb, st));
+  CK(launch_varpf_precond(g, m0, b, R, Z, st));
+  CK(cudaMemcpyAsync(P, Z, cb, cudaMemcpyDeviceToDevice, st));
+  double rz = 0.0;
+  RC(dot(R, Z, rz));
+  const double rz0 = rz;
+  const double tol2 = ctx->opts.tol * ctx->opts.tol;
+  int it = 0;
+  fftmech_status status = FFTMECH_OK;
+  while (rz0 > 0.0 && rz > tol2 * rz0) {
+    if (it >= ctx->opts.max_iter) {
+      status = FFTMECH_ERR_NOT_CONVERGED;
+      break;
+    }
+    RC(apply(P, Q));
+    double pq = 0.0;
+    RC(dot(P, Q, pq));
+    if (!(pq > 0.0) || !std::isfinite(pq)) {
+      status = FFTMECH_ERR_NONFINITE;
+      break;
+    }
+    const double alpha = rz / pq;
+    CK(launch_var_axpy(N, alpha, P, Q, X, R, st));
+    CK(launch_varpf_precond(g, m0, b, R, Z, st));
+    double rzn = 0.0;
+    RC(dot(R, Z, rzn));
+    ++it;
+    CK(launch_var_dir(N, rzn / rz, Z, P, st));
+    rz = rzn;
+  }
+  // d = F^-1(d_hat) / N; the total damage sum d = sum Re F^-1(d_hat) / N
+  CK(cudaMemcpyAsync(W, X, cb, cudaMemcpyDeviceToDevice, st));
+  RC(fft(W, true));
+  if (d) CK(launch_var_real(g, W, nullptr, invN, d, nullptr, nullptr, st));
+  CK(launch_var_sum(N, W, part, st));
+  CK(cudaMemcpyAsync(hpart.data(), part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double sd = 0.0;
+  for (int i = 0; i < nb; ++i) sd += hpart[2 * i];
+  std::memset(info, 0, sizeof(*info));
+  info->status = status;
+  info->iters = it;
+  info->rel_res = rz0 > 0 ? std::sqrt(std::max(rz, 0.0) / rz0) : 0.0;
+  info->true_rel_res = info->rel_res;
+  info->total_damage = sd * invN;
+  return status;
+}
+
 // ================================================================ C ABI
 extern "C" {
 
@@ -2456,6 +2570,23 @@ fftmech_status fftmech_equilibrium_operator(fftmech_ctx* ctx, const uint8_t* pha
   double E[6] = {0, 0, 0, 0, 0, 0};
   for (int k = 0; k < nvoigt(ctx); ++k) E[k] = eps_mac[k];
   return equilibrium_operator_impl(ctx, phase, eig, damage, E, gradient, strain, stress, info);
+}
+
+fftmech_status fftmech_phasefield_operator(fftmech_ctx* ctx, const uint8_t* phase, const double* strain,
+                                           const double* eig, int gradient, double* H, double* d,
+                                           fftmech_solve_info* info) {
+  fftmech_status rc = check_ctx(ctx);
+  if (rc != FFTMECH_OK) return rc;
+  if (!phase || !strain || !H || !d || !info) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
+  if (gradient < FFTMECH_GRAD_FORWARD || gradient > FFTMECH_GRAD_FOURIER)
+    return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "gradient operator %d", gradient);
+  if (ctx->B != 1) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "one problem per context");
+  for (const void* p : {(const void*)phase, (const void*)strain, (const void*)eig, (const void*)H, (const void*)d})
+    if (p && !is_device_ptr(p)) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "device pointers only");
+  if (gradient == FFTMECH_GRAD_FOURIER && (ctx->nx % 2 == 0 || (ctx->dim >= 2 && ctx->ny % 2 == 0) ||
+                                           (ctx->dim == 3 && ctx->nz % 2 == 0)))
+    return set_err(ctx, FFTMECH_ERR_UNSUPPORTED_SIZE, "the Fourier gradient needs odd grid sizes");
+  return phasefield_operator_impl(ctx, phase, strain, eig, gradient, H, d, info);
 }
 
 fftmech_status fftmech_problem_offset(const fftmech_ctx* ctx, int problem, int components, long long* offset) {

@@ -284,6 +284,52 @@ __global__ void k_varel_real(VarGrid g, VarEl e, double scale, double* __restric
   }
 }
 
+// ---------------------------------------------------------------- phase field
+// AT2 phase field (Eqs. crack, crack-fft) with the same choice of gradient
+// operator: K d = (a + H(x)) d + b F^-1(|D|^2 F d), f = H, PCG on the
+// spectrum of d with the preconditioner 1 / (m0 + b |D|^2), m0 = a + <H>.
+__device__ __forceinline__ double var_d2(const VarGrid& g, int x, int y, int z) {
+  double d2 = g.dx[x].re * g.dx[x].re + g.dx[x].im * g.dx[x].im;
+  if (g.dim >= 2) d2 += g.dy[y].re * g.dy[y].re + g.dy[y].im * g.dy[y].im;
+  if (g.dim == 3) d2 += g.dz[z].re * g.dz[z].re + g.dz[z].im * g.dz[z].im;
+  return d2;
+}
+
+// W = f (a real field as complex)
+__global__ void k_varpf_load(long long n, const double* __restrict__ f, cxd* __restrict__ W) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    W[i] = mk(f[i], 0.0);
+}
+
+// W <- (a + H) W / N (after the inverse transform)
+__global__ void k_varpf_react(long long n, const double* __restrict__ H, double a, double invN, cxd* __restrict__ W) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double c = (a + H[i]) * invN;
+    W[i] = mk(c * W[i].re, c * W[i].im);
+  }
+}
+
+// Q = W + b |D|^2 P (W: the transformed reaction term)
+__global__ void k_varpf_sum(VarGrid g, double b, const cxd* __restrict__ W, const cxd* __restrict__ P,
+                            cxd* __restrict__ Q) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    var_idx(g, i, x, y, z);
+    const double l = b * var_d2(g, x, y, z);
+    Q[i] = mk(W[i].re + l * P[i].re, W[i].im + l * P[i].im);
+  }
+}
+
+// z = r / (m0 + b |D|^2)
+__global__ void k_varpf_precond(VarGrid g, double m0, double b, const cxd* __restrict__ r, cxd* __restrict__ zz) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    var_idx(g, i, x, y, z);
+    const double m = 1.0 / (m0 + b * var_d2(g, x, y, z));
+    zz[i] = mk(m * r[i].re, m * r[i].im);
+  }
+}
+
 static int var_grid(long long n) {
   long long b = (n + kVarThreads - 1) / kVarThreads;
   return (int)(b < 1 ? 1 : (b > 2048 ? 2048 : b));
@@ -374,6 +420,23 @@ cudaError_t launch_varel_div(const VarGrid& g, const VarElSpec& sp, cxd* const* 
 cudaError_t launch_varel_real(const VarGrid& g, const VarElSpec& sp, cxd* const* W, double scale, double* out,
                               cudaStream_t st) {
   k_varel_real<<<var_grid(g.N), kVarThreads, 0, st>>>(g, var_el(sp, W), scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_varpf_load(long long n, const double* f, cxd* W, cudaStream_t st) {
+  k_varpf_load<<<var_grid(n), kVarThreads, 0, st>>>(n, f, W);
+  return cudaGetLastError();
+}
+cudaError_t launch_varpf_react(long long n, const double* H, double a, double invN, cxd* W, cudaStream_t st) {
+  k_varpf_react<<<var_grid(n), kVarThreads, 0, st>>>(n, H, a, invN, W);
+  return cudaGetLastError();
+}
+cudaError_t launch_varpf_sum(const VarGrid& g, double b, const cxd* W, const cxd* P, cxd* Q, cudaStream_t st) {
+  k_varpf_sum<<<var_grid(g.N), kVarThreads, 0, st>>>(g, b, W, P, Q);
+  return cudaGetLastError();
+}
+cudaError_t launch_varpf_precond(const VarGrid& g, double m0, double b, const cxd* r, cxd* z, cudaStream_t st) {
+  k_varpf_precond<<<var_grid(g.N), kVarThreads, 0, st>>>(g, m0, b, r, z);
   return cudaGetLastError();
 }
 

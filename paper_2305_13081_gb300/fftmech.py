@@ -161,6 +161,7 @@ def load_library(path=LIB_PATH):
                                             P(P(fftmech_solve_info))]),
         "fftmech_homogenise_operator": (i, [vp, vp, i, P(d), vp, vp, P(fftmech_solve_info)]),
         "fftmech_equilibrium_operator": (i, [vp, vp, vp, vp, P(d), i, vp, vp, P(fftmech_solve_info)]),
+        "fftmech_phasefield_operator": (i, [vp, vp, vp, vp, i, vp, vp, P(fftmech_solve_info)]),
         "fftmech_bar_create": (i, [P(vp), vp, d, d, d, P(d)]),
         "fftmech_bar_destroy": (i, [vp]),
         "fftmech_bar_step": (i, [vp, P(fftmech_state), P(fftmech_step_params), P(fftmech_solve_info)]),
@@ -462,6 +463,16 @@ def fftmech_equilibrium_operator(ctx, phase, eig, damage, eps_mac, gradient, str
     e = c_double6(*(list(eps_mac) + [0.0] * 6)[:6])
     rc = load_library().fftmech_equilibrium_operator(ctx, ptr(phase), ptr(eig), ptr(damage), e, int(gradient),
                                                      ptr(strain), ptr(stress), ctypes.byref(info))
+    _check(rc, ctx, _SOLVER_OK)
+    return info
+
+
+def fftmech_phasefield_operator(ctx, phase, strain, eig, gradient, H, d):
+    """History update and phase field with the gradient operator `gradient`
+    (FFTMECH_GRAD_*); device buffers (double); returns the solve record."""
+    info = fftmech_solve_info()
+    rc = load_library().fftmech_phasefield_operator(ctx, ptr(phase), ptr(strain), ptr(eig), int(gradient), ptr(H),
+                                                    ptr(d), ctypes.byref(info))
     _check(rc, ctx, _SOLVER_OK)
     return info
 

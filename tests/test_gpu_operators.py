@@ -195,3 +195,59 @@ def test_elastic_laminate_closed_form(op):
     assert np.abs(strain[1] - Eyy).max() <= 1e-12 * Eyy
     assert np.abs(stress[0] - sxx).max() <= 1e-9 * abs(sxx)
     assert np.abs(strain[2]).max() <= 1e-12 * Eyy and np.abs(stress[2]).max() <= 1e-9 * abs(sxx)
+
+
+# ---------------------------------------------------------------- phase field
+
+def gpu_pf(phase, op, strain, Hin, h):
+    ctx = fm.Context(phase.shape, MAT, fm.FFTMECH_FP64, h=h, tol=1e-13, max_iter=20000)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+    H = dev(Hin)
+    d = torch.zeros(phase.size, dtype=torch.float64, device="cuda")
+    info = fm.fftmech_phasefield_operator(ctx.handle, torch.as_tensor(phase.ravel()).cuda(), dev(strain), None,
+                                          OPS[op], H, d)
+    ctx.close()
+    return info, d.cpu().numpy().reshape(phase.shape), H.cpu().numpy().reshape(phase.shape)
+
+
+@pytest.mark.parametrize("op", list(OPS))
+@pytest.mark.parametrize("dim", [2, 3])
+def test_phasefield_operator_matches_oracle(op, dim):
+    """The phase field with every operator against the FP64 oracle
+    (oracle/phasefield.phasefield_solve(symbol=)) for a given history field
+    (zero strain leaves H unchanged); l0 = 2 voxels so that the gradient
+    term weighs as much as the reaction."""
+    from oracle import phasefield
+    phase = random_carpet(81, 0.30, 18)[0] if dim == 2 else random_sponge(9, 0.35, 19)[0]
+    nv = 3 if dim == 2 else 6
+    h = MAT.l0 / 2
+    a, _ = phasefield.coefficients(MAT)
+    Hin = a * np.random.default_rng(20).random(phase.shape) * (phase == 1)
+    info, d, Hout = gpu_pf(phase, op, np.zeros((nv,) + phase.shape), Hin, h)
+    ref, _ = phasefield.phasefield_solve(Hin, MAT, h, tol=1e-13, symbol=op)
+    e = rel(d, ref)
+    print("phase field operator", op, dim, "iterations", info.iters, "d", e)
+    assert info.status == fm.FFTMECH_OK
+    assert np.array_equal(Hout, Hin) and e < 1e-10
+    assert abs(info.total_damage - ref.sum()) <= 1e-10 * ref.sum()
+
+
+def test_forward_phasefield_operator_agrees_with_the_library_solve():
+    """History from a strain field and the phase field, forward operator:
+    this spectral-operator path against the library's FP64
+    fftmech_phasefield_solve (stencil PCG), two independent GPU paths."""
+    phase = random_carpet(243, 0.30, 21)[0]
+    N = phase.size
+    h = MAT.l0 / 2
+    ctx = fm.Context(phase.shape, MAT, fm.FFTMECH_FP64, h=h, tol=1e-13, max_iter=20000)
+    ph = torch.as_tensor(phase.ravel()).cuda()
+    u = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+    strain = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    fm.fftmech_equilibrium_solve(ctx.handle, ph, None, None, [1e-2, 0.0, 0.0], u, strain, None)
+    H1 = torch.zeros(N, dtype=torch.float64, device="cuda")
+    d1 = torch.zeros(N, dtype=torch.float64, device="cuda")
+    fm.fftmech_phasefield_solve(ctx.handle, strain, None, ph, H1, d1)
+    ctx.close()
+    _, d2, H2 = gpu_pf(phase, "forward", strain.cpu().numpy().reshape(3, *phase.shape), np.zeros(phase.shape), h)
+    assert rel(H2, H1.cpu().numpy().reshape(phase.shape)) < 1e-14
+    assert rel(d2, d1.cpu().numpy().reshape(phase.shape)) < 1e-10

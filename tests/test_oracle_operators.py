@@ -11,6 +11,10 @@ of the oracle's homogenised diffusion with each of them
 - homogenisation of laminates (odd grids): every symbol gives the harmonic
   mean of D for layers normal to the gradient and the arithmetic mean for
   layers parallel to it (the flux of a 1D layered problem is constant);
+- the oracle's phase field with each symbol
+  (oracle/phasefield.phasefield_solve(symbol=...)) against a dense direct
+  solve of (a + H) d + b G^T G d = H, G the operator's stencil matrix (the
+  Fourier operator from the explicit DFT matrix);
 - the oracle's equilibrium with each symbol
   (oracle/elasticity.equilibrium_solve(symbol=...)) on a laminate normal to
   x under E_yy (plane strain): eps_yy = E_yy everywhere and a uniform
@@ -111,3 +115,56 @@ def test_elastic_laminate_and_homogeneous_medium(symbol):
     expect = [ls * tr + 2 * ms * E[0], ls * tr + 2 * ms * E[1], 2 * ms * E[2]]
     for v in range(3):
         assert np.abs(hom["stress"][v] - expect[v]).max() <= 1e-12 * abs(expect[0])
+
+
+def stencil_matrix(shape, axis, symbol, h):
+    """Dense periodic matrix of the gradient operator along `axis`, built
+    from its stencil (Fourier: from the explicit DFT matrix), independent
+    of the FFT-based symbols."""
+    n = shape[axis]
+    if symbol == "fourier":
+        j = np.arange(n)
+        F = np.exp(-2j * np.pi * np.outer(j, j) / n)
+        k = np.where(j <= n // 2, j, j - n)
+        M1 = np.real(np.conj(F).T @ np.diag(2j * np.pi * k / (n * h)) @ F / n)
+    else:
+        if symbol == "forward":
+            coef = {1: 1.0, 0: -1.0}
+        elif symbol == "central":
+            coef = {1: 0.5, -1: -0.5}
+        else:
+            coef = {}
+            for m, c in enumerate(spectral.central8_coefficients(), start=1):
+                coef[m], coef[-m] = c, -c
+        M1 = np.zeros((n, n))
+        for i in range(n):
+            for off, c in coef.items():
+                M1[i, (i + off) % n] += c / h
+    mats = [np.eye(s) for s in shape]
+    mats[axis] = M1
+    M = mats[0]
+    for m in mats[1:]:
+        M = np.kron(M, m)
+    return M
+
+
+@pytest.mark.parametrize("symbol", ["forward", "central", "central8", "fourier"])
+def test_phasefield_with_each_symbol_matches_a_dense_solve(symbol):
+    """(a + H) d + b G^T G d = H with G the operator's dense stencil matrix,
+    solved directly, against oracle/phasefield.phasefield_solve(symbol=)."""
+    from oracle import phasefield
+    mat = Materials()
+    shape = (5, 7)
+    h = mat.l0 / 2  # the gradient term b |D|^2 ~ 4 a: a dropped or wrong term shows
+    rng = np.random.default_rng(9)
+    a, b = phasefield.coefficients(mat)
+    Hf = a * rng.random(shape)
+    A = np.diag(a + Hf.ravel())
+    for ax in range(2):
+        G = stencil_matrix(shape, ax, symbol, h)
+        A = A + b * G.T @ G
+    ref = np.linalg.solve(A, Hf.ravel()).reshape(shape)
+    d, _ = phasefield.phasefield_solve(Hf, mat, h, tol=1e-14, symbol=symbol)
+    assert np.abs(d - ref).max() <= 1e-10 * np.abs(ref).max()
+    lapless = np.linalg.solve(np.diag(a + Hf.ravel()), Hf.ravel()).reshape(shape)
+    assert np.abs(lapless - ref).max() > 1e-2 * np.abs(ref).max()  # the gradient term matters here
