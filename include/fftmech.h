@@ -411,6 +411,9 @@ fftmech_status fftmech_set_launch_shapes(fftmech_ctx* ctx, const char* shapes);
  * double [dim N] or NULL (device pointers). info: iterations, residual,
  * mean flux <j> = -<kappa grad c>. */
 enum { FFTMECH_GRAD_FORWARD = 0, FFTMECH_GRAD_CENTRAL = 1, FFTMECH_GRAD_CENTRAL8 = 2, FFTMECH_GRAD_FOURIER = 3 };
+/* OR'ed into the gradient of fftmech_phasefield_operator: the printed
+ * phase-field Laplacian read literally (see there). */
+enum { FFTMECH_PF_LITERAL = 256 };
 fftmech_status fftmech_homogenise_operator(fftmech_ctx* ctx, const uint8_t* phase, int gradient,
                                           const double grad_c_mac[3], double* phi, double* grad_c,
                                           fftmech_solve_info* info);
@@ -441,7 +444,12 @@ fftmech_status fftmech_equilibrium_operator(fftmech_ctx* ctx, const uint8_t* pha
  * buffers. phase: uint8 [N]; strain: double [nv N] (Voigt, tensor shears);
  * eig: double [N] or NULL; H: double [N], updated in place; d: double [N]
  * output (device pointers). info: iterations, residual, total_damage (the
- * sum of d over the voxels). */
+ * sum of d over the voxels). gradient | FFTMECH_PF_LITERAL reads the
+ * printed Laplacian "i xi . i xi" literally as sum_a D_a^2 (for the forward
+ * difference a non-symmetric one-sided second difference):
+ * (a + H) d - b F^-1(sum_a D_a^2 F d) = H, solved by restarted GMRES(40)
+ * (as the paper solves it) with the preconditioner above on the right;
+ * iterations then counts GMRES steps. */
 fftmech_status fftmech_phasefield_operator(fftmech_ctx* ctx, const uint8_t* phase, const double* strain,
                                            const double* eig, int gradient, double* H, double* d,
                                            fftmech_solve_info* info);

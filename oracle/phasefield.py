@@ -16,7 +16,7 @@ the same unique solution.
 import numpy as np
 
 from . import spectral
-from .krylov import cg
+from .krylov import cg, gmres
 
 
 def coefficients(mat):
@@ -34,14 +34,30 @@ def degradation(d, kappa):
     return (1.0 - d) ** 2 + kappa
 
 
-def phasefield_solve(H, mat, h, tol=1e-12, max_iter=200000, d0=None, symbol="forward"):
+def phasefield_solve(H, mat, h, tol=1e-12, max_iter=200000, d0=None, symbol="forward", literal=False):
     """Solve Eq. (crack-fft) for d given the history field H. symbol: the
     gradient operator of Sec. 2.6 (spectral.SYMBOLS; the paper's results use
-    the forward difference)."""
+    the forward difference). literal: the Laplacian as printed, "i xi . i
+    xi" read as sum_alpha D_alpha^2 (not symmetric under a difference
+    operator), solved by GMRES as the paper does, with the Galerkin
+    operator's diagonal 1 / (a + <H> + b |D|^2) as right preconditioner."""
     H = np.asarray(H, dtype=np.float64)
     a, b = coefficients(mat)
     D = spectral.SYMBOLS[symbol](H.shape, h)
     lam = spectral.symbol_norm2(D)
+    if literal:
+        DD = sum(Da * Da for Da in D)
+
+        def A_lit(x):
+            return -b * spectral.ifft(DD * spectral.fft(x)).real + a * x + H * x
+
+        m0 = a + H.mean()
+
+        def M(v):
+            return spectral.ifft(spectral.fft(v) / (m0 + b * lam)).real
+
+        d, info = gmres(A_lit, H.copy(), tol=tol, max_iter=max_iter, apply_M=M)
+        return d, info
 
     def A(x):
         lap = spectral.ifft(-lam * spectral.fft(x)).real  # F^-1(i xi . i xi x_hat)

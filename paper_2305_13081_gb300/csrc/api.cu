@@ -2076,7 +2076,8 @@ fftmech_status equilibrium_operator_impl(fftmech_ctx* ctx, const uint8_t* phase,
 // the symbol of Sec. 2.6): the history update of the library, then PCG on
 // the spectrum of d. FP64, host-driven, one problem.
 fftmech_status phasefield_operator_impl(fftmech_ctx* ctx, const uint8_t* phase, const double* strain,
-                                        const double* eig, int op, double* H, double* d, fftmech_solve_info* info) {
+                                        const double* eig, int op, bool literal, double* H, double* d,
+                                        fftmech_solve_info* info) {
   using cxd = cx<double>;
   cudaStream_t st = ctx->stream;
   const int nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, dim = ctx->dim;
@@ -2132,21 +2133,101 @@ fftmech_status phasefield_operator_impl(fftmech_ctx* ctx, const uint8_t* phase, 
     RC(fft(W, true));
     CK(launch_varpf_react(N, Hd, a, invN, W, st));
     RC(fft(W, false));
-    CK(launch_varpf_sum(g, b, W, p, q, st));
+    CK(launch_varpf_sum(g, b, literal ? 1 : 0, W, p, q, st));
     return FFTMECH_OK;
   };
   CK(launch_varpf_load(N, Hd, R, st));  // f_hat = F[H]
   RC(fft(R, false));
   CK(cudaStreamSynchronize(st));  // m0 on the host
   CK(cudaMemsetAsync(X, 0, cb, st));
-  CK(launch_varpf_precond(g, m0, b, R, Z, st));
-  CK(cudaMemcpyAsync(P, Z, cb, cudaMemcpyDeviceToDevice, st));
-  double rz = 0.0;
-  RC(dot(R, Z, rz));
-  const double rz0 = rz;
-  const double tol2 = ctx->opts.tol * ctx->opts.tol;
   int it = 0;
   fftmech_status status = FFTMECH_OK;
+  double rz = 0.0, rz0 = 0.0;
+  if (literal) {
+    // the printed Laplacian read literally is not symmetric: restarted
+    // GMRES(m) with the Galerkin operator's diagonal as right
+    // preconditioner, x = M y (Arnoldi by modified Gram-Schmidt, Givens
+    // rotations; the host holds the small Hessenberg problem)
+    constexpr int m = 40;
+    DevBuffers vm;
+    std::vector<cxd*> V(m + 1);
+    for (auto& v : V) v = vm.get<cxd>(cb);
+    cxd* Bv = vm.get<cxd>(cb);
+    if (!vm.ok) return set_err(ctx, FFTMECH_ERR_OOM, "GMRES basis");
+    CK(cudaMemcpyAsync(Bv, R, cb, cudaMemcpyDeviceToDevice, st));
+    double bnorm2 = 0.0;
+    RC(dot(Bv, Bv, bnorm2));
+    const double bnorm = std::sqrt(bnorm2), tol = ctx->opts.tol;
+    rz0 = bnorm2;
+    rz = bnorm2;
+    std::vector<double> Hm((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+    auto Hij = [&](int i, int j) -> double& { return Hm[(size_t)i * m + j]; };
+    while (bnorm > 0.0) {
+      // R = b - A x
+      if (it > 0) {
+        RC(apply(X, Q));
+        CK(cudaMemcpyAsync(R, Bv, cb, cudaMemcpyDeviceToDevice, st));
+        CK(launch_var_scal(N, -1.0, Q, R, 1, st));
+      }
+      double beta2 = 0.0;
+      RC(dot(R, R, beta2));
+      const double beta = std::sqrt(beta2);
+      rz = beta2;
+      if (beta <= tol * bnorm) break;
+      if (it >= ctx->opts.max_iter) {
+        status = FFTMECH_ERR_NOT_CONVERGED;
+        break;
+      }
+      CK(launch_var_scal(N, 1.0 / beta, R, V[0], 0, st));
+      std::fill(gv.begin(), gv.end(), 0.0);
+      gv[0] = beta;
+      int k = 0;
+      for (int j = 0; j < m && it < ctx->opts.max_iter; ++j) {
+        CK(launch_varpf_precond(g, m0, b, V[j], Z, st));
+        RC(apply(Z, V[j + 1]));
+        for (int i = 0; i <= j; ++i) {
+          RC(dot(V[i], V[j + 1], Hij(i, j)));
+          CK(launch_var_scal(N, -Hij(i, j), V[i], V[j + 1], 1, st));
+        }
+        double hn2 = 0.0;
+        RC(dot(V[j + 1], V[j + 1], hn2));
+        const double hn = std::sqrt(hn2);
+        if (hn > 0.0) CK(launch_var_scal(N, 1.0 / hn, V[j + 1], V[j + 1], 0, st));
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+          Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+          Hij(i, j) = t;
+        }
+        Hij(j + 1, j) = hn;
+        const double den = std::hypot(Hij(j, j), hn);
+        cs[j] = Hij(j, j) / den;
+        sn[j] = hn / den;
+        Hij(j, j) = den;
+        Hij(j + 1, j) = 0.0;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        k = j + 1;
+        ++it;
+        if (std::fabs(gv[j + 1]) <= tol * bnorm) break;
+      }
+      // x += M (sum y_i V_i), H y = g (upper triangular)
+      for (int i = k - 1; i >= 0; --i) {
+        double t = gv[i];
+        for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
+        y[i] = t / Hij(i, i);
+      }
+      CK(cudaMemsetAsync(P, 0, cb, st));
+      for (int i = 0; i < k; ++i) CK(launch_var_scal(N, y[i], V[i], P, 1, st));
+      CK(launch_varpf_precond(g, m0, b, P, Z, st));
+      CK(launch_var_scal(N, 1.0, Z, X, 1, st));
+    }
+  }
+  if (!literal) {
+  CK(launch_varpf_precond(g, m0, b, R, Z, st));
+  CK(cudaMemcpyAsync(P, Z, cb, cudaMemcpyDeviceToDevice, st));
+  RC(dot(R, Z, rz));
+  rz0 = rz;
+  const double tol2 = ctx->opts.tol * ctx->opts.tol;
   while (rz0 > 0.0 && rz > tol2 * rz0) {
     if (it >= ctx->opts.max_iter) {
       status = FFTMECH_ERR_NOT_CONVERGED;
@@ -2167,6 +2248,7 @@ fftmech_status phasefield_operator_impl(fftmech_ctx* ctx, const uint8_t* phase, 
     ++it;
     CK(launch_var_dir(N, rzn / rz, Z, P, st));
     rz = rzn;
+  }
   }
   // d = F^-1(d_hat) / N; the total damage sum d = sum Re F^-1(d_hat) / N
   CK(cudaMemcpyAsync(W, X, cb, cudaMemcpyDeviceToDevice, st));
@@ -2578,6 +2660,8 @@ fftmech_status fftmech_phasefield_operator(fftmech_ctx* ctx, const uint8_t* phas
   fftmech_status rc = check_ctx(ctx);
   if (rc != FFTMECH_OK) return rc;
   if (!phase || !strain || !H || !d || !info) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "null argument");
+  const bool literal = (gradient & FFTMECH_PF_LITERAL) != 0;
+  gradient &= ~FFTMECH_PF_LITERAL;
   if (gradient < FFTMECH_GRAD_FORWARD || gradient > FFTMECH_GRAD_FOURIER)
     return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "gradient operator %d", gradient);
   if (ctx->B != 1) return set_err(ctx, FFTMECH_ERR_INVALID_ARG, "one problem per context");
@@ -2586,7 +2670,7 @@ fftmech_status fftmech_phasefield_operator(fftmech_ctx* ctx, const uint8_t* phas
   if (gradient == FFTMECH_GRAD_FOURIER && (ctx->nx % 2 == 0 || (ctx->dim >= 2 && ctx->ny % 2 == 0) ||
                                            (ctx->dim == 3 && ctx->nz % 2 == 0)))
     return set_err(ctx, FFTMECH_ERR_UNSUPPORTED_SIZE, "the Fourier gradient needs odd grid sizes");
-  return phasefield_operator_impl(ctx, phase, strain, eig, gradient, H, d, info);
+  return phasefield_operator_impl(ctx, phase, strain, eig, gradient, literal, H, d, info);
 }
 
 fftmech_status fftmech_problem_offset(const fftmech_ctx* ctx, int problem, int components, long long* offset) {

@@ -549,8 +549,9 @@ cudaError_t launch_var_shift(long long n, double c, double* x, cudaStream_t st);
 // Phase field with a chosen gradient operator.
 cudaError_t launch_varpf_load(long long n, const double* f, cx<double>* W, cudaStream_t st);
 cudaError_t launch_varpf_react(long long n, const double* H, double a, double invN, cx<double>* W, cudaStream_t st);
-cudaError_t launch_varpf_sum(const VarGrid& g, double b, const cx<double>* W, const cx<double>* P, cx<double>* Q,
-                             cudaStream_t st);
+cudaError_t launch_varpf_sum(const VarGrid& g, double b, int literal, const cx<double>* W, const cx<double>* P,
+                             cx<double>* Q, cudaStream_t st);
+cudaError_t launch_var_scal(long long n, double c, const cx<double>* x, cx<double>* y, int add, cudaStream_t st);
 cudaError_t launch_varpf_precond(const VarGrid& g, double m0, double b, const cx<double>* r, cx<double>* z,
                                  cudaStream_t st);
 cudaError_t launch_varel_strain(const VarGrid& g, const VarElSpec& sp, cx<double>* const* W, const cx<double>* U,

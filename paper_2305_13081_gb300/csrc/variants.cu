@@ -309,14 +309,37 @@ __global__ void k_varpf_react(long long n, const double* __restrict__ H, double 
   }
 }
 
-// Q = W + b |D|^2 P (W: the transformed reaction term)
-__global__ void k_varpf_sum(VarGrid g, double b, const cxd* __restrict__ W, const cxd* __restrict__ P,
+// Q = W + b |D|^2 P (W: the transformed reaction term); literal: the printed
+// Laplacian "i xi . i xi" read as sum D_a^2, Q = W - b (sum D_a^2) P
+__global__ void k_varpf_sum(VarGrid g, double b, int literal, const cxd* __restrict__ W, const cxd* __restrict__ P,
                             cxd* __restrict__ Q) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
     var_idx(g, i, x, y, z);
-    const double l = b * var_d2(g, x, y, z);
-    Q[i] = mk(W[i].re + l * P[i].re, W[i].im + l * P[i].im);
+    if (literal) {
+      cxd s = cmuld(g.dx[x], g.dx[x]);
+      if (g.dim >= 2) {
+        const cxd t = cmuld(g.dy[y], g.dy[y]);
+        s = mk(s.re + t.re, s.im + t.im);
+      }
+      if (g.dim == 3) {
+        const cxd t = cmuld(g.dz[z], g.dz[z]);
+        s = mk(s.re + t.re, s.im + t.im);
+      }
+      const cxd t = cmuld(s, P[i]);
+      Q[i] = mk(W[i].re - b * t.re, W[i].im - b * t.im);
+    } else {
+      const double l = b * var_d2(g, x, y, z);
+      Q[i] = mk(W[i].re + l * P[i].re, W[i].im + l * P[i].im);
+    }
+  }
+}
+
+// y = c x (y = x when c = 1), or y += c x
+__global__ void k_var_scal(long long n, double c, const cxd* __restrict__ x, cxd* __restrict__ y, int add) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cxd v = mk(c * x[i].re, c * x[i].im);
+    y[i] = add ? mk(y[i].re + v.re, y[i].im + v.im) : v;
   }
 }
 
@@ -431,8 +454,13 @@ cudaError_t launch_varpf_react(long long n, const double* H, double a, double in
   k_varpf_react<<<var_grid(n), kVarThreads, 0, st>>>(n, H, a, invN, W);
   return cudaGetLastError();
 }
-cudaError_t launch_varpf_sum(const VarGrid& g, double b, const cxd* W, const cxd* P, cxd* Q, cudaStream_t st) {
-  k_varpf_sum<<<var_grid(g.N), kVarThreads, 0, st>>>(g, b, W, P, Q);
+cudaError_t launch_varpf_sum(const VarGrid& g, double b, int literal, const cxd* W, const cxd* P, cxd* Q,
+                             cudaStream_t st) {
+  k_varpf_sum<<<var_grid(g.N), kVarThreads, 0, st>>>(g, b, literal, W, P, Q);
+  return cudaGetLastError();
+}
+cudaError_t launch_var_scal(long long n, double c, const cxd* x, cxd* y, int add, cudaStream_t st) {
+  k_var_scal<<<var_grid(n), kVarThreads, 0, st>>>(n, c, x, y, add);
   return cudaGetLastError();
 }
 cudaError_t launch_varpf_precond(const VarGrid& g, double m0, double b, const cxd* r, cxd* z, cudaStream_t st) {

@@ -37,12 +37,13 @@ FFTMECH_EIG_PRESCRIBED = 1
 # execution of a solve or a staggered step
 FFTMECH_EXEC_GRAPH = 0
 FFTMECH_EXEC_HOST = 1
-# gradient operators (fftmech_homogenise_operator)
+# gradient operators (fftmech_*_operator)
 FFTMECH_GRAD_FORWARD = 0
 FFTMECH_GRAD_CENTRAL = 1
 FFTMECH_GRAD_CENTRAL8 = 2
 FFTMECH_GRAD_FOURIER = 3
-# preconditioner of the 2D equilibrium PCG
+FFTMECH_PF_LITERAL = 256  # phase field: the printed Laplacian read literally (GMRES)
+# preconditioner of the equilibrium PCG
 FFTMECH_PRECOND_LAPLACE = 0
 FFTMECH_PRECOND_REFERENCE = 1
 # objectives of the eigenstrain adjoint

@@ -251,3 +251,36 @@ def test_forward_phasefield_operator_agrees_with_the_library_solve():
     _, d2, H2 = gpu_pf(phase, "forward", strain.cpu().numpy().reshape(3, *phase.shape), np.zeros(phase.shape), h)
     assert rel(H2, H1.cpu().numpy().reshape(phase.shape)) < 1e-14
     assert rel(d2, d1.cpu().numpy().reshape(phase.shape)) < 1e-10
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_literal_phasefield_laplacian_by_gmres(dim):
+    """The printed phase-field Laplacian read literally (sum_a D_a^2 with the
+    forward difference: not symmetric), by the GPU's restarted GMRES,
+    against the oracle's GMRES on the same equation; the symmetric Galerkin
+    reading gives a different field. At h = 4 l0 every mode symbol of the
+    literal operator has a positive real part (at the paper's h = l0 / 2 it
+    does not, and neither GMRES converges: the reading of the oracle's
+    phasefield module)."""
+    from oracle import phasefield
+    phase = random_carpet(81, 0.30, 22)[0] if dim == 2 else random_sponge(9, 0.35, 23)[0]
+    nv = 3 if dim == 2 else 6
+    h = 4 * MAT.l0
+    a, _ = phasefield.coefficients(MAT)
+    Hin = a * np.random.default_rng(24).random(phase.shape) * (phase == 1)
+    ctx = fm.Context(phase.shape, MAT, fm.FFTMECH_FP64, h=h, tol=1e-12, max_iter=20000)
+    dev = lambda x: torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64).ravel()).cuda()
+    H = dev(Hin)
+    d = torch.zeros(phase.size, dtype=torch.float64, device="cuda")
+    info = fm.fftmech_phasefield_operator(ctx.handle, torch.as_tensor(phase.ravel()).cuda(),
+                                          dev(np.zeros((nv,) + phase.shape)), None,
+                                          fm.FFTMECH_GRAD_FORWARD | fm.FFTMECH_PF_LITERAL, H, d)
+    ctx.close()
+    got = d.cpu().numpy().reshape(phase.shape)
+    ref, rinfo = phasefield.phasefield_solve(Hin, MAT, h, tol=1e-12, literal=True)
+    gal, _ = phasefield.phasefield_solve(Hin, MAT, h, tol=1e-12)
+    e = rel(got, ref)
+    print("literal phase field", dim, "GMRES iterations", info.iters, "oracle", rinfo["iters"], "d", e,
+          "vs Galerkin", rel(gal, ref))
+    assert info.status == fm.FFTMECH_OK
+    assert e < 1e-9 and rel(gal, ref) > 1e-3

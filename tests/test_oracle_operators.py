@@ -15,6 +15,11 @@ of the oracle's homogenised diffusion with each of them
   (oracle/phasefield.phasefield_solve(symbol=...)) against a dense direct
   solve of (a + H) d + b G^T G d = H, G the operator's stencil matrix (the
   Fourier operator from the explicit DFT matrix);
+- oracle/krylov.gmres (restarted, right-preconditioned) against a direct
+  solve of a non-symmetric system; the literal reading of the printed
+  phase-field Laplacian (sum_alpha D_alpha^2, non-symmetric for the forward
+  difference) solved by it against the dense matrix diag(a + H) - b sum
+  G_alpha G_alpha;
 - the oracle's equilibrium with each symbol
   (oracle/elasticity.equilibrium_solve(symbol=...)) on a laminate normal to
   x under E_yy (plane strain): eps_yy = E_yy everywhere and a uniform
@@ -168,3 +173,63 @@ def test_phasefield_with_each_symbol_matches_a_dense_solve(symbol):
     assert np.abs(d - ref).max() <= 1e-10 * np.abs(ref).max()
     lapless = np.linalg.solve(np.diag(a + Hf.ravel()), Hf.ravel()).reshape(shape)
     assert np.abs(lapless - ref).max() > 1e-2 * np.abs(ref).max()  # the gradient term matters here
+
+
+def test_gmres_solves_a_nonsymmetric_system():
+    """oracle/krylov.gmres against numpy.linalg.solve on a random
+    non-symmetric, well-conditioned system, with and without a right
+    preconditioner, across restarts."""
+    from oracle.krylov import gmres
+    rng = np.random.default_rng(11)
+    n = 60
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    ref = np.linalg.solve(A, b)
+    x, info = gmres(lambda v: A @ v, b, tol=1e-13, restart=7)
+    assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max() and info["iters"] > 7
+    d = 1.0 / np.diag(A)
+    x2, _ = gmres(lambda v: A @ v, b, tol=1e-13, restart=10, apply_M=lambda v: d * v)
+    assert np.abs(x2 - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("symbol", ["forward", "central"])
+def test_literal_phasefield_laplacian_matches_a_dense_solve(symbol):
+    """The printed "i xi . i xi" read literally as sum_alpha D_alpha^2: the
+    dense matrix is diag(a + H) - b sum_alpha G_alpha G_alpha (not G^T G),
+    non-symmetric for the forward difference; the oracle's GMRES solve
+    matches its direct solution, and the literal and Galerkin readings
+    differ where the gradient term matters."""
+    from oracle import phasefield
+    mat = Materials()
+    shape = (5, 7)
+    h = mat.l0 / 2
+    rng = np.random.default_rng(12)
+    a, b = phasefield.coefficients(mat)
+    Hf = a * rng.random(shape)
+    L = sum(stencil_matrix(shape, ax, symbol, h) @ stencil_matrix(shape, ax, symbol, h) for ax in range(2))
+    A = np.diag(a + Hf.ravel()) - b * L
+    if symbol == "forward":
+        assert np.abs(A - A.T).max() > 1e-3 * np.abs(A).max()
+    ref = np.linalg.solve(A, Hf.ravel()).reshape(shape)
+    d, info = phasefield.phasefield_solve(Hf, mat, h, tol=1e-14, symbol=symbol, literal=True)
+    assert np.abs(d - ref).max() <= 1e-10 * np.abs(ref).max(), info
+    gal, _ = phasefield.phasefield_solve(Hf, mat, h, tol=1e-14, symbol=symbol)
+    if symbol == "forward":
+        assert np.abs(gal - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_literal_laplacian_is_indefinite_at_the_papers_length_scale():
+    """The literal mode symbol a + H - b sum_a D_a^2 of the forward
+    difference has real part a + H + 4 b / h^2 sum_a sin^2(theta_a / 2)
+    cos(theta_a): at the Nyquist corner a + H - 4 d b / h^2. With the
+    paper's l0 = 2 h (b / h^2 = 4 a) that is negative for every H <= a,
+    so the literal operator is indefinite there; at h = 4 l0 (b / h^2 =
+    a / 16) every mode has a positive real part."""
+    from oracle import phasefield
+    mat = Materials()
+    a, b = phasefield.coefficients(mat)
+    for h, sign in ((mat.l0 / 2, -1), (4 * mat.l0, 1)):
+        D = spectral.forward_difference_symbol((8, 8), h)
+        sym = a + a - b * sum(Da * Da for Da in D)  # H = a, the largest history of the tests
+        worst = sym.real.min()
+        assert np.sign(worst) == sign, (h, worst)
