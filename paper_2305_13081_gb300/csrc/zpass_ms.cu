@@ -81,7 +81,9 @@ __device__ __forceinline__ void ms_solve3(const cx<T> (&a)[3], T rho, T f, const
 // and half column kx of line set A, then the same of line set B.
 enum { MS_PA = 0, MS_PAM = 1, MS_HA = 2, MS_PB = 3, MS_PBM = 4, MS_HB = 5, MS_SLOTS = 6 };
 
-template <typename T, int FL>
+// NL > 0: a compile-time plan of NL points along z and strips of CWC
+// columns (float, kLineThreads threads); NL = 0: the runtime plan of family FL.
+template <typename T, int FL, int NL, int CWC>
 __global__ void FFTMECH_BOUNDS3 k3_zpass_ms(cx<T>* S, long long sst, int nx, int ny, int nz, int nxs,
                                             FftPlanDev<T> pz, Spec<T> sp, int CW, int mode, double* partials,
                                             SolverScalars* sc, int* pmode) {
@@ -89,6 +91,10 @@ __global__ void FFTMECH_BOUNDS3 k3_zpass_ms(cx<T>* S, long long sst, int nx, int
   extern __shared__ __align__(16) unsigned char smem_all[];
   unsigned char* smem = smem_all + tw_smem_bytes<T>(pz.n);
   const FftPlanDev<T> pz_s = plan_to_smem(pz, reinterpret_cast<cx<T>*>(smem_all));
+  if constexpr (NL > 0) {
+    nz = NL;
+    CW = CWC;
+  }
   const int ncs = MS_SLOTS * CW;
   cx<T>* Bf = reinterpret_cast<cx<T>*>(smem);        // [kz][slot]
   cx<T>* AZ = Bf + (size_t)nz * ncs;                 // a_z per line frequency
@@ -133,7 +139,8 @@ __global__ void FFTMECH_BOUNDS3 k3_zpass_ms(cx<T>* S, long long sst, int nx, int
       if (i + k * (int)blockDim.x < n) Bf[i + k * blockDim.x] = t[k];
   }
   __syncthreads();
-  fft_lines<T, -1, FL>(Bf, pz_s, ncs, 1, ncs, true);
+  if constexpr (NL > 0) fftc<T, -1, NL, true, MS_SLOTS * CWC, kLineThreads>(Bf, pz_s.tw, MS_SLOTS * CWC);
+  else fft_lines<T, -1, FL>(Bf, pz_s, ncs, 1, ncs, true);
   __syncthreads();
   const T m1 = sp.m1b ? (T)sp.m1b[bp] : sp.m1_t;
   const T rho = sp.rho_t;
@@ -189,7 +196,8 @@ __global__ void FFTMECH_BOUNDS3 k3_zpass_ms(cx<T>* S, long long sst, int nx, int
   acc.add(part);
   if (store) {
     __syncthreads();
-    fft_lines<T, 1, FL>(Bf, pz_s, ncs, 1, ncs, true);
+    if constexpr (NL > 0) fftc<T, 1, NL, true, MS_SLOTS * CWC, kLineThreads>(Bf, pz_s.tw, MS_SLOTS * CWC);
+    else fft_lines<T, 1, FL>(Bf, pz_s, ncs, 1, ncs, true);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int z = dn.div(i), sl = i - z * ncs;
@@ -222,25 +230,38 @@ size_t zpass_ms_smem(int nz, int CW, int es_complex, size_t tw) {
   return (size_t)nz * MS_SLOTS * CW * es_complex + (size_t)(nz + CW) * es_complex + tw;
 }
 
-template <typename T, int FL>
+template <typename T, int FL, int NL, int CWC>
 cudaError_t launch3_zpass_ms(cx<T>* S, long long sst, int nx, int ny, int nz, int nxs, const FftPlanDev<T>& pz,
                              const Spec<T>& sp, int CW, int threads, int batch, int mode, double* partials,
                              SolverScalars* sc, int* pmode, cudaStream_t st) {
   const size_t sm = zpass_ms_smem(nz, CW, (int)sizeof(cx<T>), tw_smem_bytes<T>(nz));
   static SmemOptIn cfg;
-  cudaError_t e = opt_in_smem(k3_zpass_ms<T, FL>, sm, cfg);
+  cudaError_t e = opt_in_smem(k3_zpass_ms<T, FL, NL, CWC>, sm, cfg);
   if (e != cudaSuccess) return e;
   const dim3 grid(zpass_ms_blocks(nx, ny, CW), batch > 0 ? batch : 1);
-  return launch_dep(k3_zpass_ms<T, FL>, grid, dim3(threads), sm, st, S, sst, nx, ny, nz, nxs, pz, sp, CW, mode,
-                    partials, sc, pmode);
+  return launch_dep(k3_zpass_ms<T, FL, NL, CWC>, grid, dim3(NL > 0 ? kLineThreads : threads), sm, st, S, sst, nx,
+                    ny, nz, nxs, pz, sp, CW, mode, partials, sc, pmode);
 }
 
 template <typename T>
 cudaError_t launch3_zpass_ms_f(int fz, cx<T>* S, long long sst, int nx, int ny, int nz, int nxs,
                                const FftPlanDev<T>& pz, const Spec<T>& sp, int CW, int threads, int batch, int mode,
                                double* partials, SolverScalars* sc, int* pmode, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    // compile-time plans for the benchmark lengths at the strip width the
+    // host picks for them (six slots of CW columns within 512 threads)
+    if (nz == 81 && CW == 4)
+      return launch3_zpass_ms<T, FAM_ALL, 81, 4>(S, sst, nx, ny, nz, nxs, pz, sp, CW, threads, batch, mode, partials,
+                                                  sc, pmode, st);
+    if (nz == 243 && CW == 2)
+      return launch3_zpass_ms<T, FAM_ALL, 243, 2>(S, sst, nx, ny, nz, nxs, pz, sp, CW, threads, batch, mode,
+                                                   partials, sc, pmode, st);
+    if (nz == 729 && CW == 1)
+      return launch3_zpass_ms<T, FAM_ALL, 729, 1>(S, sst, nx, ny, nz, nxs, pz, sp, CW, threads, batch, mode,
+                                                   partials, sc, pmode, st);
+  }
 #define FFTMECH_C(F) \
-  launch3_zpass_ms<T, F>(S, sst, nx, ny, nz, nxs, pz, sp, CW, threads, batch, mode, partials, sc, pmode, st)
+  launch3_zpass_ms<T, F, 0, 0>(S, sst, nx, ny, nz, nxs, pz, sp, CW, threads, batch, mode, partials, sc, pmode, st)
   FFTMECH_FAMILY_SWITCH(fz, FFTMECH_C)
 #undef FFTMECH_C
 }

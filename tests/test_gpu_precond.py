@@ -129,10 +129,13 @@ def test_large_batch_last_block_form_and_execution_modes():
 # ---------------------------------------------------------------- 3D
 
 def sponge(shape, seed):
-    """A random 3x3 sponge, or a 2x2 one tiled along x for other sizes."""
+    """A random 3x3 sponge, one tiled along z (nz a multiple of ny = nx, a
+    power of 3), or a 2x2 one tiled along x for other sizes."""
     nz, ny, nx = shape
     if nz == ny == nx and nx % 3 == 0:
         return random_sponge(nx, 0.35, seed)[0]
+    if ny == nx and nx % 3 == 0 and nz % nx == 0:
+        return np.ascontiguousarray(np.tile(random_sponge(nx, 0.35, seed)[0], (nz // nx, 1, 1)))
     return np.ascontiguousarray(np.tile(random_carpet(ny, 0.35, seed, base=2, dim=3)[0], (1, 1, nx // ny)))
 
 
@@ -150,8 +153,10 @@ def test_homogeneous_medium_converges_in_one_iteration_3d(shape, prec):
 
 
 @pytest.mark.parametrize("prec,tol,bound", [(fm.FFTMECH_FP64, 1e-12, 1e-10), (fm.FFTMECH_MIXED, 1e-8, 1e-5)])
-@pytest.mark.parametrize("shape,seeds", [((27, 27, 27), [51]), ((16, 16, 32), [52]), ((27, 27, 27), [53, 54])])
+@pytest.mark.parametrize("shape,seeds", [((27, 27, 27), [51]), ((16, 16, 32), [52]), ((27, 27, 27), [53, 54]),
+                                         ((81, 27, 27), [55]), ((243, 9, 9), [56])])
 def test_sponges_match_oracle_in_fewer_iterations(shape, seeds, prec, tol, bound):
+    """nz = 81 and 243 take the compile-time z plans on the mixed path."""
     phases = [sponge(shape, s) for s in seeds]
     e = [pore_eig(p, 17 + i) for i, p in enumerate(phases)]
     got, it_ms, st = solve(phases, e, prec, fm.FFTMECH_PRECOND_REFERENCE, tol)
