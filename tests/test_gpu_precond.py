@@ -178,3 +178,20 @@ def test_graph_and_host_driven_agree_3d():
                        execution=fm.FFTMECH_EXEC_HOST)
     assert all(s == fm.FFTMECH_OK for s in st)
     assert it_a == it_b and np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(729, 729), (243, 243, 243)])
+def test_full_size_reference_medium_and_laplace_agree(shape):
+    """At the benchmark sizes (729^2 carpet, 243^3 sponge; mixed, tol 1e-8)
+    the two preconditioners are independent routes to the same solution:
+    the strain fields agree within the solver tolerance's reach, and the
+    reference medium takes fewer iterations."""
+    seed = 81
+    ph = carpet(shape, seed) if len(shape) == 2 else sponge(shape, seed)
+    e = pore_eig(ph, seed + 1)
+    a, it_ms, st = solve([ph], [e], fm.FFTMECH_MIXED, fm.FFTMECH_PRECOND_REFERENCE, 1e-8)
+    b, it_lp, st2 = solve([ph], [e], fm.FFTMECH_MIXED, fm.FFTMECH_PRECOND_LAPLACE, 1e-8)
+    err = rel(a, b)
+    print("full size", shape, "iterations reference", it_ms, "laplace", it_lp, "strain rel", err)
+    assert st == [fm.FFTMECH_OK] and st2 == [fm.FFTMECH_OK]
+    assert err < 1e-5 and it_ms[0] < it_lp[0]
